@@ -1,0 +1,156 @@
+/*
+ * cr.h -- C ABI of the GB300-native multi-level constrained-realization (CR)
+ * solver for CMB skies (Seljebotn, Mardal, Jewell, Eriksen & Bull 2013,
+ * "A multi-level solver for Gaussian constrained CMB realizations").
+ *
+ * The system solved is (Section 2.3, Eqs. system-explicit and cr-system)
+ *     A x = b,   A = S^-1 + B Y^T N^-1 Y B,
+ * with S = diag(C_l) the prior, B = diag(b_l p_l) the beam and pixel window,
+ * N^-1 the per-pixel inverse noise (zero under the mask), Y spherical-harmonic
+ * synthesis to the HEALPix observation grid and Y^T its transpose (adjoint
+ * synthesis, Section 2.1 -- not analysis).
+ *
+ * Conventions shared by every entry point
+ *  - Spherical-harmonic vectors ("alm") are complex, m >= 0 only, stored
+ *    m-major with l = m..L contiguous: element (l, m) sits at
+ *    off_m + (l - m), off_m = m (L + 1) - m (m - 1) / 2, N_lm = (L+1)(L+2)/2.
+ *    Real and imaginary parts are interleaved (double2 / float2).  Im(a_l0)
+ *    is not a degree of freedom: outputs write it as 0 and inputs ignore it.
+ *    The inner product that makes Y^T the transpose of Y is
+ *    <a,b> = sum_l a_l0 b_l0 + 2 sum_{m>0} Re(a_lm conj b_lm).
+ *  - Coefficients whose C_l is 0 are not unknowns (the C_l -> 0 limit):
+ *    operators write 0 there.
+ *  - Maps are real, HEALPix RING order (or Gauss-Legendre ring order), north
+ *    to south.
+ *  - Units: uK for maps and alm, uK^2 for C_l, uK^-2 for N^-1.
+ *  - All data pointers are DEVICE pointers owned by the caller unless a
+ *    parameter says "host".  The plan owns only its own tables and
+ *    workspace.  Calls are asynchronous on the plan's stream unless stated.
+ *  - Every entry point returns an int status: CR_OK (0) or a negative error
+ *    code; cr_last_error() gives a one-line message for the calling thread.
+ *    An error leaves outputs undefined but the plan usable, except where
+ *    noted.
+ *  - dtype selects the arithmetic of a call: CR_F64 (double/double2 buffers)
+ *    or CR_F32 (float/float2 buffers).
+ */
+#ifndef CR_H_
+#define CR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CR_OK 0
+#define CR_EINVAL (-1)     /* bad argument or size */
+#define CR_ENOMEM (-2)     /* device or host allocation failed */
+#define CR_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define CR_EICC (-4)       /* incomplete Cholesky failed even with the largest ridge */
+#define CR_EDIVERGED (-5)  /* residual grew over two consecutive cycles */
+#define CR_EMAXITER (-6)   /* iteration cap reached before the tolerance */
+#define CR_ENONFINITE (-7) /* a NaN or Inf appeared in a vector */
+#define CR_ESTATE (-8)     /* call not valid in the plan's current state */
+#define CR_EIO (-9)        /* checkpoint file could not be read or written */
+
+/* arithmetic of a call */
+#define CR_F64 0
+#define CR_F32 1
+
+/* grid kinds */
+#define CR_GRID_HEALPIX 0
+#define CR_GRID_GL 1
+
+/* grid selector of the transform entry points */
+#define CR_OBS 0 /* the observation grid at the plan's lmax; level grids are CR_OBS + h, h >= 1 */
+
+typedef struct cr_plan cr_plan;
+
+/*
+ * Plan parameters.  struct_size must be sizeof(cr_params).
+ *   grid_kind   CR_GRID_HEALPIX (nside, a power of two >= 1) or CR_GRID_GL
+ *               (gl_ntheta rings at Gauss-Legendre nodes, gl_nphi pixels per
+ *               ring, gl_nphi even).
+ *   lmax        band limit L of the unknowns (>= 0).
+ *   cl, bl      HOST arrays [lmax+1]: prior C_l (>= 0) and b_l p_l.  NULL cl
+ *               means "transforms only" (no operator).  NULL bl means 1.
+ *   ninv        DEVICE array [npix] of doubles, N^-1 per pixel (0 = masked).
+ *               Copied into the plan at creation.  NULL means no noise term.
+ *   stream      cudaStream_t for every call on this plan (NULL = default).
+ */
+typedef struct cr_params {
+  int struct_size;
+  int grid_kind;
+  int nside;
+  int gl_ntheta;
+  int gl_nphi;
+  int lmax;
+  const double* cl;
+  const double* bl;
+  const double* ninv;
+  void* stream;
+} cr_params;
+
+/* One-line message describing the last error on the calling thread. */
+const char* cr_last_error(void);
+
+/*
+ * Create a plan: ring geometry (Section 2.1; HEALPix pixel centres of
+ * Gorski et al. 2005, or Gauss-Legendre nodes), Legendre recurrence tables,
+ * per-ring FFT tables, and the operator diagonals.  Synchronous.  *out is set
+ * only on success.  Errors: CR_EINVAL, CR_ENOMEM, CR_ECUDA.
+ */
+int cr_plan_create(cr_plan** out, const cr_params* p);
+
+/* Release every resource of the plan (NULL is accepted). */
+int cr_plan_destroy(cr_plan* plan);
+
+/* Sizes: pixels of grid `grid` (CR_OBS or level), rings, and N_lm at that
+ * grid's band limit.  Any output pointer may be NULL. */
+int cr_plan_sizes(const cr_plan* plan, int grid, int64_t* npix, int* nring, int* lmax, int64_t* nlm);
+
+/*
+ * Spherical-harmonic synthesis, map = Y alm (Section 2.1, Eq. sh-synthesis):
+ *   map(n_i) = sum_{l<=L, |m|<=l} a_lm Y_lm(n_i),  real field.
+ * alm: [nrhs][N_lm] complex; map: [nrhs][npix] real; dtype CR_F64/CR_F32.
+ * Band limits above what a ring resolves alias by folding m mod n_ring, so
+ * Y^T below stays its exact transpose.
+ */
+int cr_sht_synth(cr_plan* plan, int grid, const void* alm, void* map, int nrhs, int dtype);
+
+/*
+ * Adjoint synthesis, alm = Y^T map (Section 2.1: the transpose of Y, with no
+ * quadrature weights):  a_lm = sum_i conj(Y_lm(n_i)) map_i.
+ * map: [nrhs][npix]; alm: [nrhs][N_lm] (overwritten).
+ */
+int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs, int dtype);
+
+/*
+ * y = A x with A = S^-1 + B Y^T N^-1 Y B (Section 2.3, Eq. system-explicit):
+ * one synthesis, the pixel-diagonal N^-1, one adjoint synthesis and the
+ * diagonals.  level 0 is the full system; level h >= 1 applies the level
+ * operator A_h = D_h + B_h Y^T N^-1 Y B_h (Section 3.2, Eq. A_h) at that
+ * level's band limit.  x, y: [nrhs][N_lm]; x and y must not overlap.
+ * Requires a plan created with cl.  Errors: CR_EINVAL, CR_ESTATE, CR_ECUDA.
+ */
+int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int dtype);
+
+/*
+ * Per-stage timing (the per-level, per-action cost breakdown of the paper's
+ * Table "cycle-cost"): while enabled, every kernel stage launched by the plan
+ * is bracketed by CUDA events on the plan's stream and accumulated by stage
+ * name.  cr_plan_set_timing(plan, 1) clears and enables, 0 disables.
+ * cr_plan_timing synchronises the recorded events and reports stage i
+ * (0 <= i < *count) in name order: its name (NUL-terminated, truncated to
+ * name_cap), total milliseconds and number of launches; i < 0 only sets
+ * *count.  Any output pointer may be NULL.
+ */
+int cr_plan_set_timing(cr_plan* plan, int enable);
+int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CR_H_ */

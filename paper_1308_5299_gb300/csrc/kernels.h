@@ -1,0 +1,68 @@
+// Kernel argument blocks and launcher declarations shared between the
+// translation units of the CR solver library.
+#pragma once
+#include <algorithm>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace cr {
+
+template <typename T>
+struct LegArgs {
+  const typename Tr<T>::C* alm = nullptr;  // synthesis input, layout off_m(L)
+  typename Tr<T>::C* phase = nullptr;      // [nring][ldp]
+  int64_t ldp = 0;
+  int L = 0;       // band limit of the coefficient vector
+  int Lc = 0;      // band limit of the recurrence-table layout
+  const T* c = nullptr;
+  const T* s = nullptr;
+  const T* dl = nullptr;   // synthesis: per-l multiplier of a_lm (may be null)
+  const T* z = nullptr;    // cos(colatitude) per ring (north ring of each pair)
+  const T* seed = nullptr; // [m][pair]
+  const int* lev = nullptr;
+  int ld_seed = 0;
+  int npairs = 0, nring = 0;
+  typename Tr<T>::C* partial = nullptr;    // adjoint: [nblk][n_lm(L)]
+};
+
+template <typename T>
+struct FinalizeArgs {
+  const typename Tr<T>::C* partial = nullptr;
+  int nblk = 1;
+  int L = 0;
+  const T* dl_out = nullptr;               // per-l multiplier (may be null = 1)
+  const T* dadd = nullptr;                 // per-l multiplier of xadd (may be null)
+  const typename Tr<T>::C* xadd = nullptr;
+  int accumulate = 0;                      // out += result instead of out = result
+  typename Tr<T>::C* out = nullptr;
+};
+
+// Ring FFT stage: mode 0 = synthesis (phase -> map), 1 = adjoint
+// (map -> phase), 2 = both with a pixel diagonal in between (phase -> phase).
+template <typename T>
+struct RingArgs {
+  const RingFFT* fft = nullptr;
+  const typename Tr<T>::C* tab = nullptr;
+  const typename Tr<T>::C* vhat = nullptr;
+  const typename Tr<T>::C* tw = nullptr;
+  int Mmax = 1;
+  typename Tr<T>::C* phase = nullptr;
+  int64_t ldp = 0;
+  int L = 0;
+  T* map_out = nullptr;        // mode 0 output; mode 2 optional copy of Y x
+  const T* map_in = nullptr;   // mode 1 input
+  const T* pixdiag = nullptr;  // mode 2 diagonal
+  int nring = 0;
+};
+
+template <typename T> int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st);
+template <typename T> int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream_t st);
+int leg_partial_blocks(int npairs);
+template <typename T> int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st);
+
+// plan-time table builders (ringfft.cu)
+int build_fft_tables(Grid& g, cudaStream_t st);
+int build_seeds(Grid& g, int Lseed, cudaStream_t st);
+
+}  // namespace cr

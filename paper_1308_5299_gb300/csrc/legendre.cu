@@ -1,0 +1,392 @@
+// Legendre stages of spherical-harmonic synthesis Y and adjoint synthesis Y^T
+// (Section 2.1, Eq. sh-synthesis; normalised P~_lm of Section 3.3).
+//
+// For one m and one north/south ring pair (z, -z):
+//   synthesis  F_m(+-z) = sum_{l=m..L} a_lm P~_lm(+-z),
+//   adjoint    a_lm    += P~_lm(z) G_m(z) + P~_lm(-z) G_m(-z),
+// with P~_lm(-z) = (-1)^(l+m) P~_lm(z), so one recurrence serves both rings
+// through even/odd (l-m) accumulators.
+//
+// P~_lm is generated on the fly in registers by the three-term recurrence in
+// the rescaled form Q_l = P~_lm / s_lm,
+//   Q_l = c_lm z Q_{l-1} - Q_{l-2},
+// where s_lm and c_lm are plan-time tables (s_mm = s_{m+1,m} = 1).  Starting
+// from (Q_{m-1}, Q_{m-2}) = (0, -P~_mm) makes the first step return the seed,
+// so the loop is uniform from l = m.  a_lm is multiplied by s_lm when staged
+// (synthesis) and the adjoint result by s_lm when written.
+//
+// Seeds P~_mm(z) arrive in underflow-safe scaled form (value v, level lev<=0;
+// true value v * 2^(S lev)).  While lev < 0 a pair only advances its
+// recurrence (its terms are below 2^(THR-S), negligible) and is renormalised
+// when it grows past 2^THR; warps whose pairs are all at lev 0 run a loop
+// without these checks.
+//
+// Work decomposition: one CTA per (m, block of LEG_NT*LEG_RP ring pairs);
+// each thread owns LEG_RP ring pairs.  The a_lm of the CTA's m (synthesis) and
+// the recurrence coefficients are staged through shared memory in chunks of
+// LEG_CH l-values.  The adjoint reduces over ring pairs with a warp-shuffle
+// transpose reduction over 8 consecutive l (each lane ends with one l), a
+// fixed-order cross-warp sum, and one partial row per ring block summed in a
+// second, deterministic kernel.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cr {
+
+constexpr int LEG_NT = 128;
+constexpr int LEG_RP = 4;
+constexpr int LEG_CH = 256;
+constexpr int LEG_NW = LEG_NT / 32;
+
+template <typename T>
+__device__ __forceinline__ T dev_ldexp_up(int S) {
+  return (T)1.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a) {
+  using C = typename Tr<T>::C;
+  const int m = blockIdx.x;
+  const int L = a.L;
+  const int tid = threadIdx.x;
+  __shared__ C sa[LEG_CH];
+  __shared__ T sc[LEG_CH];
+  const T thr = (T)exp2((double)Tr<T>::THR);
+  const T down = (T)exp2(-(double)Tr<T>::S);
+
+  T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
+  int lev[LEG_RP];
+  C accE[LEG_RP], accO[LEG_RP];
+  const int pbase = blockIdx.y * (LEG_NT * LEG_RP) + tid;
+#pragma unroll
+  for (int j = 0; j < LEG_RP; ++j) {
+    const int p = pbase + j * LEG_NT;
+    if (p < a.npairs) {
+      zz[j] = a.z[p];
+      P2[j] = -a.seed[(int64_t)m * a.ld_seed + p];
+      lev[j] = a.lev[(int64_t)m * a.ld_seed + p];
+    } else {
+      zz[j] = 0;
+      P2[j] = 0;
+      lev[j] = 0;
+    }
+    P1[j] = 0;
+    accE[j] = mk((T)0, (T)0);
+    accO[j] = mk((T)0, (T)0);
+  }
+  const int64_t offa = lm_off(L, m);
+  const int64_t offc = lm_off(a.Lc, m);
+
+  for (int l0 = m; l0 <= L; l0 += LEG_CH) {
+    const int nl = min(LEG_CH, L - l0 + 1);
+    __syncthreads();
+    for (int i = tid; i < nl; i += LEG_NT) {
+      const int l = l0 + i;
+      C v = a.alm[offa + (l - m)];
+      if (m == 0) v.y = 0;
+      T f = a.s[offc + (l - m)];
+      if (a.dl) f *= a.dl[l];
+      sa[i] = cscale(v, f);
+      sc[i] = a.c[offc + (l - m)];
+    }
+    __syncthreads();
+    bool all0 = true;
+#pragma unroll
+    for (int j = 0; j < LEG_RP; ++j) all0 = all0 && (lev[j] == 0);
+    all0 = __all_sync(0xffffffffu, all0);
+    if (all0) {
+      int i = 0;
+      for (; i + 1 < nl; i += 2) {
+        const T c0 = sc[i], c1 = sc[i + 1];
+        const C a0 = sa[i], a1 = sa[i + 1];
+#pragma unroll
+        for (int j = 0; j < LEG_RP; ++j) {
+          T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
+          T q1 = fma(c1 * zz[j], q0, -P1[j]);
+          P2[j] = q0;
+          P1[j] = q1;
+          accE[j].x = fma(q0, a0.x, accE[j].x);
+          accE[j].y = fma(q0, a0.y, accE[j].y);
+          accO[j].x = fma(q1, a1.x, accO[j].x);
+          accO[j].y = fma(q1, a1.y, accO[j].y);
+        }
+      }
+      if (i < nl) {
+        const T c0 = sc[i];
+        const C a0 = sa[i];
+#pragma unroll
+        for (int j = 0; j < LEG_RP; ++j) {
+          T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
+          P2[j] = P1[j];
+          P1[j] = q0;
+          accE[j].x = fma(q0, a0.x, accE[j].x);
+          accE[j].y = fma(q0, a0.y, accE[j].y);
+        }
+      }
+    } else {
+      for (int i = 0; i < nl; ++i) {
+        const T c0 = sc[i];
+        const C a0 = sa[i];
+        const bool odd = i & 1;  // l0 - m is a multiple of LEG_CH (even)
+#pragma unroll
+        for (int j = 0; j < LEG_RP; ++j) {
+          T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
+          P2[j] = P1[j];
+          P1[j] = q0;
+          if (lev[j] == 0) {
+            if (odd) {
+              accO[j].x = fma(q0, a0.x, accO[j].x);
+              accO[j].y = fma(q0, a0.y, accO[j].y);
+            } else {
+              accE[j].x = fma(q0, a0.x, accE[j].x);
+              accE[j].y = fma(q0, a0.y, accE[j].y);
+            }
+          } else if (fabs(P1[j]) > thr) {
+            P1[j] *= down;
+            P2[j] *= down;
+            lev[j] += 1;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < LEG_RP; ++j) {
+    const int p = pbase + j * LEG_NT;
+    if (p < a.npairs) {
+      const int rn = p, rs = a.nring - 1 - p;
+      a.phase[(int64_t)rn * a.ldp + m] = cadd(accE[j], accO[j]);
+      if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = csub(accE[j], accO[j]);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_x(T v, int mask) {
+  return __shfl_xor_sync(0xffffffffu, v, mask);
+}
+
+// Transpose reduction of 8 complex values over the 32 lanes of a warp: on
+// return lane l holds in v[0] the warp sum of the value with index l >> 2.
+template <typename C>
+__device__ __forceinline__ void warp_reduce8(C v[8]) {
+  const int lane = threadIdx.x & 31;
+  {
+    const bool hi = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      C send = hi ? v[i] : v[i + 4];
+      C keep = hi ? v[i + 4] : v[i];
+      send.x = shfl_x(send.x, 16);
+      send.y = shfl_x(send.y, 16);
+      v[i] = cadd(keep, send);
+    }
+  }
+  {
+    const bool hi = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      C send = hi ? v[i] : v[i + 2];
+      C keep = hi ? v[i + 2] : v[i];
+      send.x = shfl_x(send.x, 8);
+      send.y = shfl_x(send.y, 8);
+      v[i] = cadd(keep, send);
+    }
+  }
+  {
+    const bool hi = lane & 4;
+    C send = hi ? v[0] : v[1];
+    C keep = hi ? v[1] : v[0];
+    send.x = shfl_x(send.x, 4);
+    send.y = shfl_x(send.y, 4);
+    v[0] = cadd(keep, send);
+  }
+  v[0].x += shfl_x(v[0].x, 2);
+  v[0].y += shfl_x(v[0].y, 2);
+  v[0].x += shfl_x(v[0].x, 1);
+  v[0].y += shfl_x(v[0].y, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a) {
+  using C = typename Tr<T>::C;
+  const int m = blockIdx.x;
+  const int L = a.L;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  __shared__ T sc[LEG_CH];
+  __shared__ C sacc[LEG_CH];
+  __shared__ C red[2][LEG_NW][8];
+  const T thr = (T)exp2((double)Tr<T>::THR);
+  const T down = (T)exp2(-(double)Tr<T>::S);
+
+  T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
+  int lev[LEG_RP];
+  C GE[LEG_RP], GO[LEG_RP];
+  const int pbase = blockIdx.y * (LEG_NT * LEG_RP) + tid;
+#pragma unroll
+  for (int j = 0; j < LEG_RP; ++j) {
+    const int p = pbase + j * LEG_NT;
+    P1[j] = 0;
+    if (p < a.npairs) {
+      zz[j] = a.z[p];
+      P2[j] = -a.seed[(int64_t)m * a.ld_seed + p];
+      lev[j] = a.lev[(int64_t)m * a.ld_seed + p];
+      const int rn = p, rs = a.nring - 1 - p;
+      const C gn = a.phase[(int64_t)rn * a.ldp + m];
+      const C gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : mk((T)0, (T)0);
+      GE[j] = cadd(gn, gs);
+      GO[j] = csub(gn, gs);
+    } else {
+      zz[j] = 0;
+      P2[j] = 0;
+      lev[j] = 0;
+      GE[j] = mk((T)0, (T)0);
+      GO[j] = mk((T)0, (T)0);
+    }
+  }
+  const int64_t offa = lm_off(L, m);
+  const int64_t offc = lm_off(a.Lc, m);
+  C* part = a.partial + (int64_t)blockIdx.y * n_lm(L);
+  int rb = 0;
+
+  for (int l0 = m; l0 <= L; l0 += LEG_CH) {
+    const int nl = min(LEG_CH, L - l0 + 1);
+    __syncthreads();
+    for (int i = tid; i < nl; i += LEG_NT) sc[i] = a.c[offc + (l0 - m) + i];
+    __syncthreads();
+    bool all0 = true;
+#pragma unroll
+    for (int j = 0; j < LEG_RP; ++j) all0 = all0 && (lev[j] == 0);
+    all0 = __all_sync(0xffffffffu, all0);
+    for (int i8 = 0; i8 < nl; i8 += 8) {
+      C acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = mk((T)0, (T)0);
+      if (all0) {
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          if (i8 + u < nl) {
+            const T c0 = sc[i8 + u];
+            const T c1 = (i8 + u + 1 < nl) ? sc[i8 + u + 1] : (T)0;
+#pragma unroll
+            for (int j = 0; j < LEG_RP; ++j) {
+              T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
+              T q1 = fma(c1 * zz[j], q0, -P1[j]);
+              P2[j] = q0;
+              P1[j] = q1;
+              acc[u].x = fma(q0, GE[j].x, acc[u].x);
+              acc[u].y = fma(q0, GE[j].y, acc[u].y);
+              acc[u + 1].x = fma(q1, GO[j].x, acc[u + 1].x);
+              acc[u + 1].y = fma(q1, GO[j].y, acc[u + 1].y);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (i8 + u < nl) {
+            const T c0 = sc[i8 + u];
+#pragma unroll
+            for (int j = 0; j < LEG_RP; ++j) {
+              T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
+              P2[j] = P1[j];
+              P1[j] = q0;
+              if (lev[j] == 0) {
+                const C g = (u & 1) ? GO[j] : GE[j];
+                acc[u].x = fma(q0, g.x, acc[u].x);
+                acc[u].y = fma(q0, g.y, acc[u].y);
+              } else if (fabs(P1[j]) > thr) {
+                P1[j] *= down;
+                P2[j] *= down;
+                lev[j] += 1;
+              }
+            }
+          }
+        }
+      }
+      warp_reduce8(acc);
+      if ((lane & 3) == 0) red[rb][warp][lane >> 2] = acc[0];
+      __syncthreads();
+      if (tid < 8) {
+        C s = red[rb][0][tid];
+#pragma unroll
+        for (int w = 1; w < LEG_NW; ++w) s = cadd(s, red[rb][w][tid]);
+        sacc[i8 + tid] = s;
+      }
+      rb ^= 1;
+    }
+    __syncthreads();
+    for (int i = tid; i < nl; i += LEG_NT) {
+      const int l = l0 + i;
+      part[offa + (l - m)] = cscale(sacc[i], a.s[offc + (l - m)]);
+    }
+  }
+}
+
+// y_lm = dl_out[l] * sum_blk partial[blk][lm] + dadd[l] * xadd_lm; zero at
+// inactive l (dl_out = dadd = 0 there) and Im(a_l0) = 0.
+template <typename T>
+__global__ void leg_finalize_kernel(FinalizeArgs<T> a) {
+  using C = typename Tr<T>::C;
+  const int64_t nlm = n_lm(a.L);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlm; i += (int64_t)gridDim.x * blockDim.x) {
+    C s = a.partial[i];
+    for (int b = 1; b < a.nblk; ++b) s = cadd(s, a.partial[(int64_t)b * nlm + i]);
+    // recover l, m from the flat index (m-major layout)
+    int m = (int)((2.0 * (a.L + 1) + 1.0 - sqrt((2.0 * (a.L + 1) + 1.0) * (2.0 * (a.L + 1) + 1.0) - 8.0 * (double)i)) * 0.5);
+    while (m > 0 && lm_off(a.L, m) > i) --m;
+    while (m < a.L && lm_off(a.L, m + 1) <= i) ++m;
+    const int l = m + (int)(i - lm_off(a.L, m));
+    T f = a.dl_out ? a.dl_out[l] : (T)1;
+    C y = cscale(s, f);
+    if (a.dadd) {
+      C x = a.xadd[i];
+      y.x = fma(a.dadd[l], x.x, y.x);
+      y.y = fma(a.dadd[l], x.y, y.y);
+    }
+    if (m == 0) y.y = 0;
+    if (a.accumulate) y = cadd(y, a.out[i]);
+    a.out[i] = y;
+  }
+}
+
+template <typename T>
+int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st) {
+  if (a.L < 0) return CR_OK;
+  dim3 grid(a.L + 1, (a.npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP));
+  leg_synth_kernel<T><<<grid, LEG_NT, 0, st>>>(a);
+  CR_CHECK_LAUNCH("leg_synth_kernel");
+  return CR_OK;
+}
+
+template <typename T>
+int leg_adjoint_nblk(int npairs) {
+  return (npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP);
+}
+
+template <typename T>
+int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream_t st) {
+  if (a.L < 0) return CR_OK;
+  dim3 grid(a.L + 1, leg_adjoint_nblk<T>(a.npairs));
+  leg_adjoint_kernel<T><<<grid, LEG_NT, 0, st>>>(a);
+  CR_CHECK_LAUNCH("leg_adjoint_kernel");
+  FinalizeArgs<T> ff = f;
+  ff.partial = a.partial;
+  ff.nblk = grid.y;
+  ff.L = a.L;
+  const int64_t nlm = n_lm(a.L);
+  int blocks = (int)std::min<int64_t>((nlm + 255) / 256, 152 * 16);
+  leg_finalize_kernel<T><<<blocks, 256, 0, st>>>(ff);
+  CR_CHECK_LAUNCH("leg_finalize_kernel");
+  return CR_OK;
+}
+
+int leg_partial_blocks(int npairs) { return (npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP); }
+
+template int launch_leg_synth<double>(const LegArgs<double>&, cudaStream_t);
+template int launch_leg_synth<float>(const LegArgs<float>&, cudaStream_t);
+template int launch_leg_adjoint<double>(const LegArgs<double>&, const FinalizeArgs<double>&, cudaStream_t);
+template int launch_leg_adjoint<float>(const LegArgs<float>&, const FinalizeArgs<float>&, cudaStream_t);
+
+}  // namespace cr

@@ -1,0 +1,623 @@
+// Plan construction and the C ABI entry points for transforms and A.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cr {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return CR_ECUDA;
+}
+
+cudaEvent_t Timing::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Timing::flush() {
+  for (auto& r : pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      auto& v = acc[r.name];
+      v.first += ms;
+      v.second += 1;
+    }
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  pending.clear();
+}
+
+Timing::~Timing() {
+  for (auto& r : pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+TimerScope::TimerScope(Timing& t, cudaStream_t st, const char* name) : t_(&t), st_(st), idx_(-1) {
+  if (!t.enabled) return;
+  Timing::Rec r{name, t.get(), t.get()};
+  cudaEventRecord(r.a, st);
+  t.pending.push_back(r);
+  idx_ = (int)t.pending.size() - 1;
+}
+
+TimerScope::~TimerScope() {
+  if (idx_ >= 0) cudaEventRecord(t_->pending[idx_].b, st_);
+}
+
+// HEALPix RING-scheme rings (Gorski et al. 2005): polar ring i < N has 4i
+// pixels at z = 1 - i^2/(3N^2), phi = pi (2j + 1) / (4i); equatorial ring
+// N <= i <= 3N has 4N pixels at z = 4/3 - 2i/(3N), phi = pi (2j + s) / (4N),
+// s = (i - N + 1) mod 2; the south cap mirrors the north.
+static void healpix_rings(Grid& g, int N) {
+  g.kind = CR_GRID_HEALPIX;
+  g.nside = N;
+  g.nring = 4 * N - 1;
+  g.z.resize(g.nring);
+  g.sth.resize(g.nring);
+  g.fft.resize(g.nring);
+  int64_t off = 0;
+  for (int i = 1; i <= 4 * N - 1; ++i) {
+    const int k = i - 1;
+    double z, sth;
+    int n, s;
+    if (i < N || i > 3 * N) {
+      const int ii = (i < N) ? i : 4 * N - i;
+      const double omz = (double)ii * ii / (3.0 * N * N);
+      z = 1.0 - omz;
+      sth = std::sqrt(omz * (2.0 - omz));
+      if (i > 3 * N) z = -z;
+      n = 4 * ii;
+      s = 1;
+    } else {
+      z = 4.0 / 3.0 - 2.0 * i / (3.0 * N);
+      sth = std::sqrt((1.0 - z) * (1.0 + z));
+      n = 4 * N;
+      s = (i - N + 1) % 2;
+    }
+    g.z[k] = z;
+    g.sth[k] = sth;
+    RingFFT f{};
+    f.n = n;
+    f.shift = s;
+    f.off = off;
+    g.fft[k] = f;
+    off += n;
+  }
+  g.npix = off;
+  g.npairs = (g.nring + 1) / 2;
+}
+
+// Gauss-Legendre rings: nodes of P_ntheta by Newton iteration in theta
+// (accurate near the poles), nphi pixels per ring at phi = 2 pi j / nphi.
+static void gl_rings(Grid& g, int ntheta, int nphi, std::vector<double>* weights) {
+  g.kind = CR_GRID_GL;
+  g.nside = 0;
+  g.nring = ntheta;
+  g.z.resize(ntheta);
+  g.sth.resize(ntheta);
+  g.fft.resize(ntheta);
+  if (weights) weights->resize(ntheta);
+  const int n = ntheta;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double th = M_PI * (i + 0.75) / (n + 0.5);
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      const double x = std::cos(th);
+      double p0 = 1.0, p1 = x;
+      for (int l = 2; l <= n; ++l) {
+        const double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
+        p0 = p1;
+        p1 = p2;
+      }
+      // dP_n/dtheta = -sin(theta) dP_n/dx = n (x P_n - P_{n-1}) / sin(theta)... use the
+      // identity (1 - x^2) P_n' = n (P_{n-1} - x P_n)
+      const double s = std::sin(th);
+      const double dPdx = n * (p0 - x * p1) / (s * s);
+      const double dPdth = -s * dPdx;
+      const double step = p1 / dPdth;
+      th -= step;
+      dp = dPdx;
+      if (std::fabs(step) < 1e-16 * std::max(1.0, th)) {
+        // one more derivative evaluation at the converged node
+        const double xx = std::cos(th);
+        double q0 = 1.0, q1 = xx;
+        for (int l = 2; l <= n; ++l) {
+          const double q2 = ((2.0 * l - 1.0) * xx * q1 - (l - 1.0) * q0) / l;
+          q0 = q1;
+          q1 = q2;
+        }
+        const double ss = std::sin(th);
+        dp = n * (q0 - xx * q1) / (ss * ss);
+        break;
+      }
+    }
+    const double x = std::cos(th), s = std::sin(th);
+    const double w = 2.0 / (s * s * dp * dp);
+    g.z[i] = x;
+    g.sth[i] = s;
+    g.z[n - 1 - i] = -x;
+    g.sth[n - 1 - i] = s;
+    if (weights) {
+      (*weights)[i] = w;
+      (*weights)[n - 1 - i] = w;
+    }
+  }
+  int64_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    RingFFT f{};
+    f.n = nphi;
+    f.shift = 0;
+    f.off = off;
+    g.fft[k] = f;
+    off += nphi;
+  }
+  g.npix = off;
+  g.npairs = (g.nring + 1) / 2;
+}
+
+static int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
+  std::vector<float> z32(g.z.begin(), g.z.end());
+  // pair tables use the north ring of each pair
+  CR_CUDA(cudaMalloc(&g.d_z, g.nring * sizeof(double)));
+  CR_CUDA(cudaMalloc(&g.d_z32, g.nring * sizeof(float)));
+  CR_CUDA(cudaMalloc(&g.d_sth, g.nring * sizeof(double)));
+  CR_CUDA(cudaMemcpyAsync(g.d_z, g.z.data(), g.nring * sizeof(double), cudaMemcpyHostToDevice, st));
+  CR_CUDA(cudaMemcpyAsync(g.d_z32, z32.data(), g.nring * sizeof(float), cudaMemcpyHostToDevice, st));
+  CR_CUDA(cudaMemcpyAsync(g.d_sth, g.sth.data(), g.nring * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = build_fft_tables(g, st);
+  if (rc) return rc;
+  return build_seeds(g, Lseed, st);
+}
+
+static void grid_free(Grid& g) {
+  void* ptrs[] = {g.d_z, g.d_z32, g.d_sth, g.d_fft, g.d_tab, g.d_tab32, g.d_vhat, g.d_vhat32,
+                  g.d_tw, g.d_tw32, g.d_seed, g.d_lev, g.d_seed32, g.d_lev32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// Recurrence tables for the rescaled recurrence Q_l = c_lm z Q_{l-1} - Q_{l-2},
+// P~_lm = s_lm Q_l, derived from the normalised three-term recurrence
+// P~_lm = a_lm (z P~_{l-1,m} - P~_{l-2,m} / a_{l-1,m}),
+// a_lm = sqrt((4 l^2 - 1) / (l^2 - m^2)).
+static int build_coef(cr_plan* P, int Lc) {
+  const int64_t nlm = n_lm(Lc);
+  std::vector<double> c(nlm), s(nlm);
+  for (int m = 0; m <= Lc; ++m) {
+    const int64_t o = lm_off(Lc, m);
+    c[o] = 0.0;
+    s[o] = 1.0;
+    if (m + 1 > Lc) continue;
+    double a_prev = std::sqrt(2.0 * m + 3.0);
+    c[o + 1] = a_prev;
+    s[o + 1] = 1.0;
+    double s_m2 = 1.0, s_m1 = 1.0;
+    for (int l = m + 2; l <= Lc; ++l) {
+      const double a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+      const double sl = (a / a_prev) * s_m2;
+      c[o + (l - m)] = a * s_m1 / sl;
+      s[o + (l - m)] = sl;
+      s_m2 = s_m1;
+      s_m1 = sl;
+      a_prev = a;
+    }
+  }
+  std::vector<float> c32(c.begin(), c.end()), s32(s.begin(), s.end());
+  CR_CUDA(cudaMalloc(&P->d_c, nlm * sizeof(double)));
+  CR_CUDA(cudaMalloc(&P->d_s, nlm * sizeof(double)));
+  CR_CUDA(cudaMalloc(&P->d_c32, nlm * sizeof(float)));
+  CR_CUDA(cudaMalloc(&P->d_s32, nlm * sizeof(float)));
+  CR_CUDA(cudaMemcpy(P->d_c, c.data(), nlm * sizeof(double), cudaMemcpyHostToDevice));
+  CR_CUDA(cudaMemcpy(P->d_s, s.data(), nlm * sizeof(double), cudaMemcpyHostToDevice));
+  CR_CUDA(cudaMemcpy(P->d_c32, c32.data(), nlm * sizeof(float), cudaMemcpyHostToDevice));
+  CR_CUDA(cudaMemcpy(P->d_s32, s32.data(), nlm * sizeof(float), cudaMemcpyHostToDevice));
+  P->Lcoef = Lc;
+  return CR_OK;
+}
+
+static int ensure_workspace(cr_plan* P, const Grid& g, int L) {
+  const int64_t phase = (int64_t)g.nring * (L + 1) * (int64_t)sizeof(double2);
+  const int64_t partial = (int64_t)leg_partial_blocks(g.npairs) * n_lm(L) * (int64_t)sizeof(double2);
+  if (phase > P->ws.phase_bytes) {
+    if (P->ws.phase) cudaFree(P->ws.phase);
+    P->ws.phase = nullptr;
+    CR_CUDA(cudaMalloc(&P->ws.phase, phase));
+    P->ws.phase_bytes = phase;
+  }
+  if (partial > P->ws.partial_bytes) {
+    if (P->ws.partial) cudaFree(P->ws.partial);
+    P->ws.partial = nullptr;
+    CR_CUDA(cudaMalloc(&P->ws.partial, partial));
+    P->ws.partial_bytes = partial;
+  }
+  return CR_OK;
+}
+
+static void plan_free(cr_plan* P) {
+  grid_free(P->obs);
+  for (Grid* g : P->level_grids) {
+    grid_free(*g);
+    delete g;
+  }
+  void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
+                  P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+__global__ void ninv32_kernel(const double* in, float* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// ---- transform drivers ------------------------------------------------------
+
+template <typename T>
+static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
+  LegArgs<T> a;
+  a.ldp = L + 1;
+  a.L = L;
+  a.Lc = P->Lcoef;
+  if constexpr (sizeof(T) == 8) {
+    a.c = P->d_c;
+    a.s = P->d_s;
+    a.z = g.d_z;
+    a.seed = g.d_seed;
+    a.lev = g.d_lev;
+  } else {
+    a.c = P->d_c32;
+    a.s = P->d_s32;
+    a.z = g.d_z32;
+    a.seed = g.d_seed32;
+    a.lev = g.d_lev32;
+  }
+  a.ld_seed = g.npairs;
+  a.npairs = g.npairs;
+  a.nring = g.nring;
+  a.phase = reinterpret_cast<typename Tr<T>::C*>(P->ws.phase);
+  a.partial = reinterpret_cast<typename Tr<T>::C*>(P->ws.partial);
+  return a;
+}
+
+template <typename T>
+static RingArgs<T> ring_args(cr_plan* P, const Grid& g, int L) {
+  RingArgs<T> r;
+  r.fft = g.d_fft;
+  if constexpr (sizeof(T) == 8) {
+    r.tab = g.d_tab;
+    r.vhat = g.d_vhat;
+    r.tw = g.d_tw;
+  } else {
+    r.tab = g.d_tab32;
+    r.vhat = g.d_vhat32;
+    r.tw = g.d_tw32;
+  }
+  r.Mmax = g.Mmax;
+  r.phase = reinterpret_cast<typename Tr<T>::C*>(P->ws.phase);
+  r.ldp = L + 1;
+  r.L = L;
+  r.nring = g.nring;
+  return r;
+}
+
+template <typename T>
+int do_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, const T* dl) {
+  LegArgs<T> a = leg_args<T>(P, g, L);
+  a.alm = reinterpret_cast<const typename Tr<T>::C*>(alm);
+  a.dl = dl;
+  int rc;
+  {
+    TimerScope ts(P->timing, P->stream, "legendre_synth");
+    rc = launch_leg_synth<T>(a, P->stream);
+  }
+  if (rc) return rc;
+  RingArgs<T> r = ring_args<T>(P, g, L);
+  r.map_out = reinterpret_cast<T*>(map);
+  TimerScope ts(P->timing, P->stream, "ring_fft_synth");
+  return launch_ring_fft<T>(r, 0, P->stream);
+}
+
+template <typename T>
+int do_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, const T* dl_out, const T* dadd,
+               const void* xadd, int accumulate) {
+  RingArgs<T> r = ring_args<T>(P, g, L);
+  r.map_in = reinterpret_cast<const T*>(map);
+  int rc;
+  {
+    TimerScope ts(P->timing, P->stream, "ring_fft_adjoint");
+    rc = launch_ring_fft<T>(r, 1, P->stream);
+  }
+  if (rc) return rc;
+  LegArgs<T> a = leg_args<T>(P, g, L);
+  FinalizeArgs<T> f;
+  f.dl_out = dl_out;
+  f.dadd = dadd;
+  f.xadd = reinterpret_cast<const typename Tr<T>::C*>(xadd);
+  f.accumulate = accumulate;
+  f.out = reinterpret_cast<typename Tr<T>::C*>(alm);
+  TimerScope ts(P->timing, P->stream, "legendre_adjoint");
+  return launch_leg_adjoint<T>(a, f, P->stream);
+}
+
+// y = dl_out Y^T diag(pix) Y (dl_in x) + dadd x  on grid g at band limit L.
+template <typename T>
+int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const T* dl_in, const T* pix,
+                const T* dl_out, const T* dadd, T* map_copy) {
+  LegArgs<T> a = leg_args<T>(P, g, L);
+  a.alm = reinterpret_cast<const typename Tr<T>::C*>(x);
+  a.dl = dl_in;
+  int rc;
+  {
+    TimerScope ts(P->timing, P->stream, "legendre_synth");
+    rc = launch_leg_synth<T>(a, P->stream);
+  }
+  if (rc) return rc;
+  RingArgs<T> r = ring_args<T>(P, g, L);
+  r.pixdiag = pix;
+  r.map_out = map_copy;
+  {
+    TimerScope ts(P->timing, P->stream, "ring_fft_apply");
+    rc = launch_ring_fft<T>(r, 2, P->stream);
+  }
+  if (rc) return rc;
+  FinalizeArgs<T> f;
+  f.dl_out = dl_out;
+  f.dadd = dadd;
+  f.xadd = reinterpret_cast<const typename Tr<T>::C*>(x);
+  f.out = reinterpret_cast<typename Tr<T>::C*>(y);
+  TimerScope ts(P->timing, P->stream, "legendre_adjoint");
+  return launch_leg_adjoint<T>(a, f, P->stream);
+}
+
+static const Grid* grid_of(cr_plan* P, int grid, int* L) {
+  if (grid == CR_OBS) {
+    *L = P->lmax;
+    return &P->obs;
+  }
+  const int h = grid - CR_OBS;
+  if (h >= 1 && h <= (int)P->level_grids.size()) {
+    *L = P->levels[h].lmax_h;
+    return P->level_grids[h - 1];
+  }
+  return nullptr;
+}
+
+}  // namespace cr
+
+using namespace cr;
+
+extern "C" {
+
+const char* cr_last_error(void) { return g_last_error.c_str(); }
+
+int cr_plan_create(cr_plan** out, const cr_params* p) {
+  if (!out || !p) return fail(CR_EINVAL, "cr_plan_create: null argument");
+  if (p->struct_size != (int)sizeof(cr_params)) return fail(CR_EINVAL, "cr_plan_create: struct_size mismatch");
+  if (p->lmax < 0 || p->lmax > 16384) return fail(CR_EINVAL, "cr_plan_create: lmax out of range");
+  if (p->grid_kind == CR_GRID_HEALPIX) {
+    if (p->nside < 1 || (p->nside & (p->nside - 1)) || p->nside > 16384)
+      return fail(CR_EINVAL, "cr_plan_create: nside must be a power of two in [1, 16384]");
+  } else if (p->grid_kind == CR_GRID_GL) {
+    if (p->gl_ntheta < 1 || p->gl_nphi < 2 || (p->gl_nphi & 1))
+      return fail(CR_EINVAL, "cr_plan_create: GL grid needs ntheta >= 1 and even nphi >= 2");
+  } else {
+    return fail(CR_EINVAL, "cr_plan_create: unknown grid kind");
+  }
+  cr_plan* P = nullptr;
+  try {
+    P = new cr_plan();
+  } catch (std::bad_alloc&) {
+    return fail(CR_ENOMEM, "cr_plan_create: host allocation");
+  }
+  P->p = *p;
+  P->stream = reinterpret_cast<cudaStream_t>(p->stream);
+  P->lmax = p->lmax;
+  P->levels.resize(1);
+  P->levels[0].lmax_h = p->lmax;
+  int rc = CR_OK;
+  try {
+    if (p->grid_kind == CR_GRID_HEALPIX) healpix_rings(P->obs, p->nside);
+    else gl_rings(P->obs, p->gl_ntheta, p->gl_nphi, nullptr);
+  } catch (std::bad_alloc&) {
+    delete P;
+    return fail(CR_ENOMEM, "cr_plan_create: host allocation");
+  }
+  rc = grid_upload(P->obs, P->lmax, P->stream);
+  if (!rc) rc = build_coef(P, P->lmax);
+  if (!rc) rc = ensure_workspace(P, P->obs, P->lmax);
+  if (!rc && p->cl) {
+    const int L = P->lmax;
+    P->h_cl.assign(p->cl, p->cl + L + 1);
+    P->h_bl.assign(L + 1, 1.0);
+    if (p->bl) P->h_bl.assign(p->bl, p->bl + L + 1);
+    std::vector<double> bl(L + 1), sinv(L + 1);
+    for (int l = 0; l <= L; ++l) {
+      if (!(P->h_cl[l] >= 0.0) || !std::isfinite(P->h_cl[l])) {
+        rc = fail(CR_EINVAL, "cr_plan_create: C_l must be finite and >= 0");
+        break;
+      }
+      const bool act = P->h_cl[l] > 0.0;
+      bl[l] = act ? P->h_bl[l] : 0.0;
+      sinv[l] = act ? 1.0 / P->h_cl[l] : 0.0;
+    }
+    if (!rc) {
+      std::vector<float> bl32(bl.begin(), bl.end()), sinv32(sinv.begin(), sinv.end());
+      auto up = [&](double** d, const std::vector<double>& h) -> int {
+        CR_CUDA(cudaMalloc(d, h.size() * sizeof(double)));
+        CR_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+        return CR_OK;
+      };
+      auto up32 = [&](float** d, const std::vector<float>& h) -> int {
+        CR_CUDA(cudaMalloc(d, h.size() * sizeof(float)));
+        CR_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+        return CR_OK;
+      };
+      rc = up(&P->d_bl, bl);
+      if (!rc) rc = up(&P->d_sinv, sinv);
+      if (!rc) rc = up32(&P->d_bl32, bl32);
+      if (!rc) rc = up32(&P->d_sinv32, sinv32);
+      const int64_t npix = P->obs.npix;
+      if (!rc) {
+        cudaError_t e = cudaMalloc(&P->d_ninv, npix * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&P->d_ninv32, npix * sizeof(float));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(ninv)");
+      }
+      if (!rc) {
+        cudaError_t e = p->ninv ? cudaMemcpyAsync(P->d_ninv, p->ninv, npix * sizeof(double),
+                                                  cudaMemcpyDeviceToDevice, P->stream)
+                                : cudaMemsetAsync(P->d_ninv, 0, npix * sizeof(double), P->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy ninv");
+      }
+      if (!rc) {
+        ninv32_kernel<<<1024, 256, 0, P->stream>>>(P->d_ninv, P->d_ninv32, npix);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ninv32");
+      }
+      if (!rc) P->has_op = true;
+    }
+  }
+  if (rc) {
+    plan_free(P);
+    delete P;
+    return rc;
+  }
+  *out = P;
+  return CR_OK;
+}
+
+int cr_plan_destroy(cr_plan* plan) {
+  if (!plan) return CR_OK;
+  cudaStreamSynchronize(plan->stream);
+  plan_free(plan);
+  delete plan;
+  return CR_OK;
+}
+
+int cr_plan_sizes(const cr_plan* plan, int grid, int64_t* npix, int* nring, int* lmax, int64_t* nlm) {
+  if (!plan) return fail(CR_EINVAL, "cr_plan_sizes: null plan");
+  int L = 0;
+  const Grid* g = grid_of(const_cast<cr_plan*>(plan), grid, &L);
+  if (!g) return fail(CR_EINVAL, "cr_plan_sizes: unknown grid");
+  if (npix) *npix = g->npix;
+  if (nring) *nring = g->nring;
+  if (lmax) *lmax = L;
+  if (nlm) *nlm = n_lm(L);
+  return CR_OK;
+}
+
+static int check_ptr(const void* p, int dtype) {
+  const uintptr_t a = (uintptr_t)p;
+  const uintptr_t al = dtype == CR_F64 ? 16 : 8;
+  if (!p || (a % al)) return fail(CR_EINVAL, "buffer pointer null or not aligned to a complex element");
+  return CR_OK;
+}
+
+int cr_sht_synth(cr_plan* plan, int grid, const void* alm, void* map, int nrhs, int dtype) {
+  if (!plan) return fail(CR_EINVAL, "cr_sht_synth: null plan");
+  int L = 0;
+  const Grid* g = grid_of(plan, grid, &L);
+  if (!g) return fail(CR_EINVAL, "cr_sht_synth: unknown grid");
+  if (nrhs < 0 || (dtype != CR_F64 && dtype != CR_F32)) return fail(CR_EINVAL, "cr_sht_synth: nrhs/dtype");
+  if (nrhs == 0) return CR_OK;
+  if (check_ptr(alm, dtype) || check_ptr(map, dtype)) return CR_EINVAL;
+  const size_t es = dtype == CR_F64 ? 8 : 4;
+  for (int r = 0; r < nrhs; ++r) {
+    const char* a = (const char*)alm + (size_t)r * n_lm(L) * 2 * es;
+    char* m = (char*)map + (size_t)r * g->npix * es;
+    int rc = dtype == CR_F64 ? do_synth<double>(plan, *g, L, a, m, nullptr) : do_synth<float>(plan, *g, L, a, m, nullptr);
+    if (rc) return rc;
+  }
+  return CR_OK;
+}
+
+int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs, int dtype) {
+  if (!plan) return fail(CR_EINVAL, "cr_sht_adjoint: null plan");
+  int L = 0;
+  const Grid* g = grid_of(plan, grid, &L);
+  if (!g) return fail(CR_EINVAL, "cr_sht_adjoint: unknown grid");
+  if (nrhs < 0 || (dtype != CR_F64 && dtype != CR_F32)) return fail(CR_EINVAL, "cr_sht_adjoint: nrhs/dtype");
+  if (nrhs == 0) return CR_OK;
+  if (check_ptr(alm, dtype) || check_ptr(map, dtype)) return CR_EINVAL;
+  const size_t es = dtype == CR_F64 ? 8 : 4;
+  for (int r = 0; r < nrhs; ++r) {
+    const char* m = (const char*)map + (size_t)r * g->npix * es;
+    char* a = (char*)alm + (size_t)r * n_lm(L) * 2 * es;
+    int rc = dtype == CR_F64 ? do_adjoint<double>(plan, *g, L, m, a, nullptr, nullptr, nullptr, 0)
+                             : do_adjoint<float>(plan, *g, L, m, a, nullptr, nullptr, nullptr, 0);
+    if (rc) return rc;
+  }
+  return CR_OK;
+}
+
+int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int dtype) {
+  if (!plan) return fail(CR_EINVAL, "cr_apply_A: null plan");
+  if (!plan->has_op) return fail(CR_ESTATE, "cr_apply_A: plan was created without C_l");
+  if (level != 0) return fail(CR_EINVAL, "cr_apply_A: level out of range");
+  if (nrhs < 0 || (dtype != CR_F64 && dtype != CR_F32)) return fail(CR_EINVAL, "cr_apply_A: nrhs/dtype");
+  if (nrhs == 0) return CR_OK;
+  if (check_ptr(x, dtype) || check_ptr(y, dtype)) return CR_EINVAL;
+  if (x == y) return fail(CR_EINVAL, "cr_apply_A: x and y must not overlap");
+  const int L = plan->lmax;
+  const size_t es = dtype == CR_F64 ? 8 : 4;
+  for (int r = 0; r < nrhs; ++r) {
+    const char* xr = (const char*)x + (size_t)r * n_lm(L) * 2 * es;
+    char* yr = (char*)y + (size_t)r * n_lm(L) * 2 * es;
+    int rc = dtype == CR_F64
+                 ? do_sandwich<double>(plan, plan->obs, L, xr, yr, plan->d_bl, plan->d_ninv, plan->d_bl, plan->d_sinv, nullptr)
+                 : do_sandwich<float>(plan, plan->obs, L, xr, yr, plan->d_bl32, plan->d_ninv32, plan->d_bl32,
+                                      plan->d_sinv32, nullptr);
+    if (rc) return rc;
+  }
+  return CR_OK;
+}
+
+int cr_plan_set_timing(cr_plan* plan, int enable) {
+  if (!plan) return fail(CR_EINVAL, "cr_plan_set_timing: null plan");
+  plan->timing.flush();
+  plan->timing.acc.clear();
+  plan->timing.enabled = enable != 0;
+  return CR_OK;
+}
+
+int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, int* count) {
+  if (!plan) return fail(CR_EINVAL, "cr_plan_timing: null plan");
+  plan->timing.flush();
+  if (count) *count = (int)plan->timing.acc.size();
+  if (i < 0) return CR_OK;
+  if (i >= (int)plan->timing.acc.size()) return fail(CR_EINVAL, "cr_plan_timing: index out of range");
+  auto it = plan->timing.acc.begin();
+  std::advance(it, i);
+  if (name && name_cap > 0) {
+    std::strncpy(name, it->first.c_str(), name_cap - 1);
+    name[name_cap - 1] = 0;
+  }
+  if (ms) *ms = it->second.first;
+  if (launches) *launches = it->second.second;
+  return CR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Internal plan and grid structures of the CR solver library.
+#pragma once
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cr {
+
+// Per-ring FFT description.  A ring of n pixels (n even) is transformed as a
+// complex sequence of nh = n/2 values (real-data packing).  If nh is a power
+// of two the FFT has size M = nh; otherwise Bluestein's chirp-z algorithm is
+// used with a power-of-two convolution of size M >= 2 nh - 1.
+struct RingFFT {
+  int n;         // pixels on the ring
+  int nh;        // n / 2
+  int M;         // power-of-two FFT size
+  int logM;      // log2(M)
+  int bluestein; // 1 if nh is not a power of two
+  int shift;     // azimuth of pixel j is pi (2 j + shift) / n, shift in {0, 1}
+  int64_t off;   // first pixel of the ring in the map
+  int64_t tab;   // offset of this ring length's e^{i pi u / n}, u < 2n, table
+  int64_t vhat;  // offset of the Bluestein kernel spectrum (bit-reversed, /M)
+};
+
+// A ring grid with its transform tables.
+struct Grid {
+  int kind = CR_GRID_HEALPIX;
+  int nside = 0;
+  int nring = 0;
+  int npairs = 0;  // north/south ring pairs (the middle ring pairs with itself)
+  int64_t npix = 0;
+  int Lseed = -1;  // seeds exist for m <= Lseed
+  int Mmax = 1;    // largest FFT size
+  std::vector<double> z, sth;
+  std::vector<RingFFT> fft;
+  // device tables
+  double* d_z = nullptr;      // [nring]
+  float* d_z32 = nullptr;     // [nring]
+  double* d_sth = nullptr;    // [nring]
+  RingFFT* d_fft = nullptr;   // [nring]
+  double2* d_tab = nullptr;   // concatenated e^{i pi u/n}
+  float2* d_tab32 = nullptr;
+  double2* d_vhat = nullptr;  // concatenated Bluestein spectra
+  float2* d_vhat32 = nullptr;
+  double2* d_tw = nullptr;    // e^{-2 pi i j / Mmax}, j < Mmax/2
+  float2* d_tw32 = nullptr;
+  int64_t tab_len = 0, vhat_len = 0;
+  // Legendre seeds P~_mm(z_pair) in scaled form, [m][pair]
+  double* d_seed = nullptr;
+  int* d_lev = nullptr;
+  float* d_seed32 = nullptr;
+  int* d_lev32 = nullptr;
+};
+
+// Scratch sizes for transforms at band limit L on a grid.
+struct Workspace {
+  void* phase = nullptr;   // [nring][ldp] complex (sized for double2)
+  void* partial = nullptr; // [nblk][n_lm] complex (sized for double2)
+  int64_t phase_bytes = 0, partial_bytes = 0;
+};
+
+// Optional per-stage CUDA-event timing (enabled with cr_plan_set_timing).
+struct Timing {
+  bool enabled = false;
+  struct Rec {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<double, long>> acc;  // name -> (ms, launches)
+  cudaEvent_t get();
+  void flush();
+  ~Timing();
+};
+
+class TimerScope {
+ public:
+  TimerScope(Timing& t, cudaStream_t st, const char* name);
+  ~TimerScope();
+
+ private:
+  Timing* t_;
+  cudaStream_t st_;
+  int idx_;
+};
+
+struct Level {
+  int nside_h = 0;
+  int lmax_h = 0;
+};
+
+}  // namespace cr
+
+struct cr_plan {
+  cr_params p{};
+  cudaStream_t stream = nullptr;
+  int lmax = 0;
+  int Lcoef = -1;
+  cr::Grid obs;
+  std::vector<cr::Grid*> level_grids;  // pixel grids of levels 1..H
+  std::vector<cr::Level> levels;       // levels[0] = top
+  // Legendre recurrence tables, layout off_m(Lcoef) + l - m
+  double* d_c = nullptr;
+  double* d_s = nullptr;
+  float* d_c32 = nullptr;
+  float* d_s32 = nullptr;
+  // operator diagonals (l-indexed, [lmax+1])
+  bool has_op = false;
+  double* d_bl = nullptr;    // b_l p_l, 0 where C_l = 0
+  double* d_sinv = nullptr;  // 1/C_l, 0 where C_l = 0
+  float* d_bl32 = nullptr;
+  float* d_sinv32 = nullptr;
+  double* d_ninv = nullptr;  // [npix] obs grid
+  float* d_ninv32 = nullptr;
+  cr::Workspace ws;
+  cr::Timing timing;
+  std::vector<double> h_cl, h_bl;
+};

@@ -13,8 +13,8 @@ same shapes are used:
   * Gaussian beams b_l = exp(-l(l+1) sigma^2 / 2), sigma = FWHM / sqrt(8 ln 2);
     the pixel window is 1;
   * white noise with per-pixel RMS log-uniform in [lo, hi] uK, optionally
-    modulated by exp(0.3 g), g a smooth unit-variance random field built from
-    randomly placed Gaussian bumps of the requested angular scale;
+    modulated by exp(0.3 g), g a smooth unit-variance random field with a
+    5-degree-FWHM Gaussian correlation (random-phase plane waves);
   * masks: a galactic cut |b| < b_cut (grid pole = galactic pole) plus random
     circular holes of a given radius with centres uniform on the sphere;
     masked pixels have N^-1 = 0;
@@ -115,27 +115,27 @@ def _pixels_near(nside, vec, radius, table):
     return np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
 
 
-def smooth_field(nside, scale_deg, seed, table, nbumps=None):
-    """Smooth unit-variance random field: sum of randomly placed Gaussian
-    bumps of width ``scale_deg`` with random signs, standardized."""
+def smooth_field(nside, fwhm_deg, seed, table, nwaves=256):
+    """Smooth, approximately Gaussian random field with unit variance and a
+    Gaussian correlation of the given FWHM: a random-phase sum of 3-D plane
+    waves cos(k . n + phi) restricted to the sphere, with wave vectors
+    k ~ N(0, I / s^2), s = FWHM / sqrt(8 ln 2), so that
+    E[f(n1) f(n2)] = exp(-|n1 - n2|^2 / (2 s^2)) ~ exp(-theta^2 / (2 s^2))."""
     z, nphi, phi0, off = table
     npix = 12 * nside * nside
     g = rng(seed, 5)
-    s = math.radians(scale_deg) / math.sqrt(8.0 * math.log(2.0))
-    nb = nbumps or int(min(4000, 8.0 * 4.0 * math.pi / (s * s)))
-    c = g.normal(size=(nb, 3))
-    c /= np.linalg.norm(c, axis=1, keepdims=True)
-    w = g.normal(size=nb)
+    s = math.radians(fwhm_deg) / math.sqrt(8.0 * math.log(2.0))
+    k = g.normal(size=(nwaves, 3)) / s
+    ph = g.uniform(0.0, 2.0 * np.pi, size=nwaves)
     th = np.repeat(np.arccos(z), nphi)
     ring = np.repeat(np.arange(len(z)), nphi)
     phi = phi0[ring] + 2.0 * np.pi * (np.arange(npix) - off[ring]) / nphi[ring]
     v = np.stack([np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi), np.cos(th)], axis=1)
     f = np.zeros(npix)
-    for b0 in range(0, nb, 64):
-        d = v @ c[b0:b0 + 64].T
-        f += (np.exp((d - 1.0) / (s * s)) * w[b0:b0 + 64]).sum(axis=1)
-    f -= f.mean()
-    return f / f.std()
+    for b0 in range(0, nwaves, 32):
+        f += np.cos(v @ k[b0:b0 + 32].T + ph[b0:b0 + 32]).sum(axis=1)
+    f *= math.sqrt(2.0 / nwaves)
+    return f
 
 
 def noise_rms(nside, lo, hi, seed=BASE_SEED, modulation=False, table=None):

@@ -1,0 +1,143 @@
+"""Parity of the CUDA transforms with the FP64 oracle (Section 2.1):
+synthesis Y, adjoint synthesis Y^T, and A (Eq. system-explicit), element by
+element at sizes the oracle finishes in seconds (several CTA tiles and ragged
+ring blocks, aliasing band limits, Bluestein and power-of-two rings), and on
+sampled rings at the full Nside 2048 / lmax 3000 size."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import cuda_device, rel_l2
+from oracle import geometry, operators, sht
+from paper_1308_5299_gb300 import binding, synthetic
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10   # FP64 transforms vs the oracle, relative L2
+TOL32 = 2e-5    # FP32 transforms vs the oracle, relative L2
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return cuda_device()
+
+
+HP_CASES = [(1, 3), (2, 7), (4, 20), (8, 23), (8, 40), (16, 47), (32, 95), (64, 191), (128, 383), (256, 767)]
+
+
+@pytest.mark.parametrize("nside,lmax", HP_CASES)
+def test_synth_adjoint_healpix_f64(dev, nside, lmax):
+    g = geometry.healpix_grid(nside)
+    plan = binding.Plan(lmax, nside=nside)
+    a = synthetic.random_alm(lmax, seed=100 + nside)
+    y = synthetic.random_map(g["npix"], seed=200 + nside)
+    m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(dev), m)
+    assert rel_l2(m.cpu().numpy(), sht.synth(a, lmax, g)) < TOL64
+    b = torch.empty(sht.n_lm(lmax), dtype=torch.complex128, device=dev)
+    plan.sht_adjoint(torch.from_numpy(y).to(dev), b)
+    assert rel_l2(b.cpu().numpy(), sht.adjoint(y, lmax, g)) < TOL64
+
+
+@pytest.mark.parametrize("nside,lmax", [(8, 23), (32, 95), (256, 767)])
+def test_synth_adjoint_healpix_f32(dev, nside, lmax):
+    g = geometry.healpix_grid(nside)
+    plan = binding.Plan(lmax, nside=nside)
+    a = synthetic.random_alm(lmax, seed=300 + nside)
+    y = synthetic.random_map(g["npix"], seed=400 + nside)
+    m = torch.empty(g["npix"], dtype=torch.float32, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(torch.complex64).to(dev), m)
+    assert rel_l2(m.cpu().numpy(), sht.synth(a, lmax, g)) < TOL32
+    b = torch.empty(sht.n_lm(lmax), dtype=torch.complex64, device=dev)
+    plan.sht_adjoint(torch.from_numpy(y).to(torch.float32).to(dev), b)
+    assert rel_l2(b.cpu().numpy(), sht.adjoint(y, lmax, g)) < TOL32
+
+
+@pytest.mark.parametrize("ntheta,nphi,lmax", [(24, 48, 23), (33, 66, 40), (20, 42, 30), (64, 128, 63)])
+def test_synth_adjoint_gl_f64(dev, ntheta, nphi, lmax):
+    g = geometry.gl_grid(ntheta, nphi)
+    plan = binding.Plan(lmax, gl=(ntheta, nphi))
+    a = synthetic.random_alm(lmax, seed=5)
+    y = synthetic.random_map(g["npix"], seed=6)
+    m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(dev), m)
+    assert rel_l2(m.cpu().numpy(), sht.synth(a, lmax, g)) < TOL64
+    b = torch.empty(sht.n_lm(lmax), dtype=torch.complex128, device=dev)
+    plan.sht_adjoint(torch.from_numpy(y).to(dev), b)
+    assert rel_l2(b.cpu().numpy(), sht.adjoint(y, lmax, g)) < TOL64
+
+
+def test_batched_rhs_and_edge_sizes(dev):
+    """nrhs > 1 handles each vector independently; lmax = 0 and nrhs = 0 work."""
+    nside, lmax = 4, 11
+    g = geometry.healpix_grid(nside)
+    plan = binding.Plan(lmax, nside=nside)
+    a = np.stack([synthetic.random_alm(lmax, seed=s) for s in range(3)])
+    m = torch.empty((3, g["npix"]), dtype=torch.float64, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(dev), m)
+    for i in range(3):
+        assert rel_l2(m[i].cpu().numpy(), sht.synth(a[i], lmax, g)) < TOL64
+    p0 = binding.Plan(0, nside=2)
+    a0 = torch.tensor([2.5 + 0j], dtype=torch.complex128, device=dev)
+    m0 = torch.empty(48, dtype=torch.float64, device=dev)
+    p0.sht_synth(a0, m0)
+    assert np.allclose(m0.cpu().numpy(), 2.5 / np.sqrt(4 * np.pi), rtol=1e-14)
+    empty = torch.empty((0,), dtype=torch.complex128, device=dev)
+    p0.sht_synth(empty, torch.empty((0,), dtype=torch.float64, device=dev))
+
+
+@pytest.mark.parametrize("name", ["nside8_lmax23", "nside32_lmax95", "nside256_lmax767"])
+def test_apply_A_f64(dev, name):
+    cfg, cl, bl, ninv = synthetic.problem_inputs(name)
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev))
+    x = synthetic.draw_prior(cl, index=3)
+    y = torch.empty(sht.n_lm(cfg["lmax"]), dtype=torch.complex128, device=dev)
+    plan.apply_A(torch.from_numpy(x).to(dev), y)
+    assert rel_l2(y.cpu().numpy(), operators.apply_A(prob, x)) < TOL64
+
+
+def test_apply_A_f32(dev):
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside32_lmax95")
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev))
+    x = synthetic.draw_prior(cl, index=4)
+    y = torch.empty(sht.n_lm(cfg["lmax"]), dtype=torch.complex64, device=dev)
+    plan.apply_A(torch.from_numpy(x).to(torch.complex64).to(dev), y)
+    assert rel_l2(y.cpu().numpy(), operators.apply_A(prob, x)) < 1e-4
+
+
+@pytest.mark.parametrize("nside,lmax", [(2048, 3000), (1024, 2047), (512, 1023)])
+def test_full_size_sampled_rings(dev, nside, lmax):
+    """Full-size transforms in the benchmark's configuration, checked on a
+    sample of rings the oracle computes one by one: polar rings (Bluestein,
+    heavy aliasing), the cap/belt boundary, equatorial rings (power of two)."""
+    g = geometry.healpix_grid(nside)
+    plan = binding.Plan(lmax, nside=nside)
+    a = synthetic.random_alm(lmax, seed=77)
+    m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(dev), m)
+    R = g["nring"]
+    rings = np.array([0, 1, 7, nside // 3, nside - 2, nside - 1, nside, 2 * nside - 1, R - 1 - nside // 2, R - 1])
+    ref = sht.synth(a, lmax, g, rings=rings)
+    mh = m.cpu().numpy()
+    for k in rings:
+        sl = slice(g["off"][k], g["off"][k] + g["nphi"][k])
+        assert rel_l2(mh[sl], ref[sl]) < TOL64, k
+    # adjoint of a map supported on the sampled rings only
+    y = np.zeros(g["npix"])
+    rs = np.random.default_rng(9)
+    for k in rings:
+        y[g["off"][k]: g["off"][k] + g["nphi"][k]] = rs.normal(size=g["nphi"][k])
+    b = torch.empty(sht.n_lm(lmax), dtype=torch.complex128, device=dev)
+    plan.sht_adjoint(torch.from_numpy(y).to(dev), b)
+    assert rel_l2(b.cpu().numpy(), sht.adjoint(y, lmax, g, rings=rings)) < TOL64
+    # adjoint identity over the whole grid
+    yy = synthetic.random_map(g["npix"], seed=3)
+    bb = torch.empty(sht.n_lm(lmax), dtype=torch.complex128, device=dev)
+    plan.sht_adjoint(torch.from_numpy(yy).to(dev), bb)
+    lhs = float(mh @ yy)
+    rhs = sht.alm_dot(a, bb.cpu().numpy(), lmax)
+    assert abs(lhs - rhs) < 1e-11 * np.linalg.norm(mh) * np.linalg.norm(yy)
