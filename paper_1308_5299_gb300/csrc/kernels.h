@@ -16,9 +16,12 @@ struct LegArgs {
   int L = 0;       // band limit of the coefficient vector
   int Lc = 0;      // band limit of the recurrence-table layout
   const T* c = nullptr;
+  const T* c2 = nullptr;   // c - 2 (polar difference form)
   const T* s = nullptr;
   const T* dl = nullptr;   // synthesis: per-l multiplier of a_lm (may be null)
   const T* z = nullptr;    // cos(colatitude) per ring (north ring of each pair)
+  const T* w = nullptr;    // 1 - z per ring (used by the polar form)
+  int npolar = 0;          // pairs [0, npolar) use the polar form z Q = Q - w Q
   const T* seed = nullptr; // [m][pair]
   const int* lev = nullptr;
   int ld_seed = 0;

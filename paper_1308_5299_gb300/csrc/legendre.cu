@@ -38,32 +38,64 @@ constexpr int LEG_RP = 4;
 constexpr int LEG_CH = 256;
 constexpr int LEG_NW = LEG_NT / 32;
 
-template <typename T>
-__device__ __forceinline__ T dev_ldexp_up(int S) {
-  return (T)1.0;
+// One recurrence step Q_l = c z Q_{l-1} - Q_{l-2}; returns Q_l and advances
+// the state (s1, s2).
+//  - standard form: state (Q_{l-1}, Q_{l-2});
+//  - polar form (FP32 pairs with z > 1/2): state (Q_{l-1}, D_{l-1}) with the
+//    difference D_l = Q_l - Q_{l-1} = ((c - 2) - c w) Q_{l-1} + D_{l-1},
+//    w = 1 - z.  Near the poles Q changes slowly in l and the standard form
+//    loses the small second difference to cancellation (in FP32 1 - z itself
+//    rounds away); carrying D with c - 2 and w at full relative precision
+//    keeps it.
+template <typename T, bool POLAR>
+__device__ __forceinline__ T rstep(T c, T c2, T zw, T& s1, T& s2) {
+  if (POLAR) {
+    const T e = fma(-c, zw, c2);
+    const T d = fma(e, s1, s2);
+    const T q = s1 + d;
+    s1 = q;
+    s2 = d;
+    return q;
+  }
+  const T q = fma(c * zw, s1, -s2);
+  s2 = s1;
+  s1 = q;
+  return q;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a) {
+// Ring pairs are split into a polar range [0, npolar) and an equatorial
+// range [npolar, npairs); each CTA covers LEG_NT*LEG_RP pairs of one range.
+// Block row yb (= blockIdx.y + the launch's row offset) < nbp is polar.
+__device__ __forceinline__ int pair_base(int npolar, int nbp, int yb, int tid) {
+  return yb < nbp ? yb * (LEG_NT * LEG_RP) + tid : npolar + (yb - nbp) * (LEG_NT * LEG_RP) + tid;
+}
+
+template <typename T, bool POLAR>
+__global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
   const int m = blockIdx.x;
   const int L = a.L;
   const int tid = threadIdx.x;
   __shared__ C sa[LEG_CH];
   __shared__ T sc[LEG_CH];
+  __shared__ T sc2[LEG_CH];
   const T thr = (T)exp2((double)Tr<T>::THR);
   const T down = (T)exp2(-(double)Tr<T>::S);
 
   T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
   int lev[LEG_RP];
   C accE[LEG_RP], accO[LEG_RP];
-  const int pbase = blockIdx.y * (LEG_NT * LEG_RP) + tid;
+  const int yb = (int)blockIdx.y + yoff;
+  const int pbase = pair_base(a.npolar, nbp, yb, tid);
+  const int pend = POLAR ? a.npolar : a.npairs;
 #pragma unroll
   for (int j = 0; j < LEG_RP; ++j) {
     const int p = pbase + j * LEG_NT;
-    if (p < a.npairs) {
-      zz[j] = a.z[p];
-      P2[j] = -a.seed[(int64_t)m * a.ld_seed + p];
+    if (p < pend) {
+      zz[j] = POLAR ? a.w[p] : a.z[p];
+      // (Q_{m-1}, Q_{m-2}) = (0, -seed), i.e. D_{m-1} = +seed in the polar form
+      const T sd = a.seed[(int64_t)m * a.ld_seed + p];
+      P2[j] = POLAR ? sd : -sd;
       lev[j] = a.lev[(int64_t)m * a.ld_seed + p];
     } else {
       zz[j] = 0;
@@ -88,6 +120,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a) {
       if (a.dl) f *= a.dl[l];
       sa[i] = cscale(v, f);
       sc[i] = a.c[offc + (l - m)];
+      if (POLAR) sc2[i] = a.c2[offc + (l - m)];
     }
     __syncthreads();
     bool all0 = true;
@@ -98,13 +131,12 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a) {
       int i = 0;
       for (; i + 1 < nl; i += 2) {
         const T c0 = sc[i], c1 = sc[i + 1];
+        const T d0 = POLAR ? sc2[i] : (T)0, d1 = POLAR ? sc2[i + 1] : (T)0;
         const C a0 = sa[i], a1 = sa[i + 1];
 #pragma unroll
         for (int j = 0; j < LEG_RP; ++j) {
-          T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
-          T q1 = fma(c1 * zz[j], q0, -P1[j]);
-          P2[j] = q0;
-          P1[j] = q1;
+          T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+          T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
           accE[j].x = fma(q0, a0.x, accE[j].x);
           accE[j].y = fma(q0, a0.y, accE[j].y);
           accO[j].x = fma(q1, a1.x, accO[j].x);
@@ -113,12 +145,11 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a) {
       }
       if (i < nl) {
         const T c0 = sc[i];
+        const T d0 = POLAR ? sc2[i] : (T)0;
         const C a0 = sa[i];
 #pragma unroll
         for (int j = 0; j < LEG_RP; ++j) {
-          T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
-          P2[j] = P1[j];
-          P1[j] = q0;
+          T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
           accE[j].x = fma(q0, a0.x, accE[j].x);
           accE[j].y = fma(q0, a0.y, accE[j].y);
         }
@@ -126,13 +157,12 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a) {
     } else {
       for (int i = 0; i < nl; ++i) {
         const T c0 = sc[i];
+        const T d0 = POLAR ? sc2[i] : (T)0;
         const C a0 = sa[i];
         const bool odd = i & 1;  // l0 - m is a multiple of LEG_CH (even)
 #pragma unroll
         for (int j = 0; j < LEG_RP; ++j) {
-          T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
-          P2[j] = P1[j];
-          P1[j] = q0;
+          T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
           if (lev[j] == 0) {
             if (odd) {
               accO[j].x = fma(q0, a0.x, accO[j].x);
@@ -153,7 +183,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a) {
 #pragma unroll
   for (int j = 0; j < LEG_RP; ++j) {
     const int p = pbase + j * LEG_NT;
-    if (p < a.npairs) {
+    if (p < pend) {
       const int rn = p, rs = a.nring - 1 - p;
       a.phase[(int64_t)rn * a.ldp + m] = cadd(accE[j], accO[j]);
       if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = csub(accE[j], accO[j]);
@@ -207,14 +237,15 @@ __device__ __forceinline__ void warp_reduce8(C v[8]) {
   v[0].y += shfl_x(v[0].y, 1);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a) {
+template <typename T, bool POLAR>
+__global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
   const int m = blockIdx.x;
   const int L = a.L;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   __shared__ T sc[LEG_CH];
+  __shared__ T sc2[LEG_CH];
   __shared__ C sacc[LEG_CH];
   __shared__ C red[2][LEG_NW][8];
   const T thr = (T)exp2((double)Tr<T>::THR);
@@ -223,14 +254,17 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a) {
   T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
   int lev[LEG_RP];
   C GE[LEG_RP], GO[LEG_RP];
-  const int pbase = blockIdx.y * (LEG_NT * LEG_RP) + tid;
+  const int yb = (int)blockIdx.y + yoff;
+  const int pbase = pair_base(a.npolar, nbp, yb, tid);
+  const int pend = POLAR ? a.npolar : a.npairs;
 #pragma unroll
   for (int j = 0; j < LEG_RP; ++j) {
     const int p = pbase + j * LEG_NT;
     P1[j] = 0;
-    if (p < a.npairs) {
-      zz[j] = a.z[p];
-      P2[j] = -a.seed[(int64_t)m * a.ld_seed + p];
+    if (p < pend) {
+      zz[j] = POLAR ? a.w[p] : a.z[p];
+      const T sd = a.seed[(int64_t)m * a.ld_seed + p];
+      P2[j] = POLAR ? sd : -sd;
       lev[j] = a.lev[(int64_t)m * a.ld_seed + p];
       const int rn = p, rs = a.nring - 1 - p;
       const C gn = a.phase[(int64_t)rn * a.ldp + m];
@@ -247,13 +281,16 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a) {
   }
   const int64_t offa = lm_off(L, m);
   const int64_t offc = lm_off(a.Lc, m);
-  C* part = a.partial + (int64_t)blockIdx.y * n_lm(L);
+  C* part = a.partial + (int64_t)yb * n_lm(L);
   int rb = 0;
 
   for (int l0 = m; l0 <= L; l0 += LEG_CH) {
     const int nl = min(LEG_CH, L - l0 + 1);
     __syncthreads();
-    for (int i = tid; i < nl; i += LEG_NT) sc[i] = a.c[offc + (l0 - m) + i];
+    for (int i = tid; i < nl; i += LEG_NT) {
+      sc[i] = a.c[offc + (l0 - m) + i];
+      if (POLAR) sc2[i] = a.c2[offc + (l0 - m) + i];
+    }
     __syncthreads();
     bool all0 = true;
 #pragma unroll
@@ -269,12 +306,12 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a) {
           if (i8 + u < nl) {
             const T c0 = sc[i8 + u];
             const T c1 = (i8 + u + 1 < nl) ? sc[i8 + u + 1] : (T)0;
+            const T d0 = POLAR ? sc2[i8 + u] : (T)0;
+            const T d1 = (POLAR && i8 + u + 1 < nl) ? sc2[i8 + u + 1] : (T)0;
 #pragma unroll
             for (int j = 0; j < LEG_RP; ++j) {
-              T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
-              T q1 = fma(c1 * zz[j], q0, -P1[j]);
-              P2[j] = q0;
-              P1[j] = q1;
+              T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+              T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
               acc[u].x = fma(q0, GE[j].x, acc[u].x);
               acc[u].y = fma(q0, GE[j].y, acc[u].y);
               acc[u + 1].x = fma(q1, GO[j].x, acc[u + 1].x);
@@ -287,11 +324,10 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a) {
         for (int u = 0; u < 8; ++u) {
           if (i8 + u < nl) {
             const T c0 = sc[i8 + u];
+            const T d0 = POLAR ? sc2[i8 + u] : (T)0;
 #pragma unroll
             for (int j = 0; j < LEG_RP; ++j) {
-              T q0 = fma(c0 * zz[j], P1[j], -P2[j]);
-              P2[j] = P1[j];
-              P1[j] = q0;
+              T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
               if (lev[j] == 0) {
                 const C g = (u & 1) ? GO[j] : GE[j];
                 acc[u].x = fma(q0, g.x, acc[u].x);
@@ -351,29 +387,33 @@ __global__ void leg_finalize_kernel(FinalizeArgs<T> a) {
   }
 }
 
+static inline void pair_blocks(int npolar, int npairs, int* nbp, int* nbe) {
+  *nbp = (npolar + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP);
+  *nbe = (npairs - npolar + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP);
+}
+
 template <typename T>
 int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st) {
   if (a.L < 0) return CR_OK;
-  dim3 grid(a.L + 1, (a.npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP));
-  leg_synth_kernel<T><<<grid, LEG_NT, 0, st>>>(a);
+  int nbp, nbe;
+  pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
+  if (nbp) leg_synth_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0);
+  if (nbe) leg_synth_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp);
   CR_CHECK_LAUNCH("leg_synth_kernel");
   return CR_OK;
 }
 
 template <typename T>
-int leg_adjoint_nblk(int npairs) {
-  return (npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP);
-}
-
-template <typename T>
 int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream_t st) {
   if (a.L < 0) return CR_OK;
-  dim3 grid(a.L + 1, leg_adjoint_nblk<T>(a.npairs));
-  leg_adjoint_kernel<T><<<grid, LEG_NT, 0, st>>>(a);
+  int nbp, nbe;
+  pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
+  if (nbp) leg_adjoint_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0);
+  if (nbe) leg_adjoint_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp);
   CR_CHECK_LAUNCH("leg_adjoint_kernel");
   FinalizeArgs<T> ff = f;
   ff.partial = a.partial;
-  ff.nblk = grid.y;
+  ff.nblk = nbp + nbe;
   ff.L = a.L;
   const int64_t nlm = n_lm(a.L);
   int blocks = (int)std::min<int64_t>((nlm + 255) / 256, 152 * 16);
@@ -382,7 +422,8 @@ int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream
   return CR_OK;
 }
 
-int leg_partial_blocks(int npairs) { return (npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP); }
+// upper bound on the partial rows of the adjoint (polar and equatorial ranges)
+int leg_partial_blocks(int npairs) { return (npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP) + 1; }
 
 template int launch_leg_synth<double>(const LegArgs<double>&, cudaStream_t);
 template int launch_leg_synth<float>(const LegArgs<float>&, cudaStream_t);

@@ -1,0 +1,389 @@
+// Level table, HEALPix nested-scheme tile geometry and the small vector
+// kernels of the multi-level cycle (Sections 3.2-3.5).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <tuple>
+#include <unordered_map>
+
+#include "common.cuh"
+#include "hier.h"
+#include "kernels.h"
+#include "levels.h"
+
+namespace cr {
+
+int LArr::upload(const std::vector<double>& h) {
+  release();
+  n = (int)h.size();
+  std::vector<float> hf(h.begin(), h.end());
+  CR_CUDA(cudaMalloc(&d, std::max<size_t>(1, h.size()) * sizeof(double)));
+  CR_CUDA(cudaMalloc(&f, std::max<size_t>(1, h.size()) * sizeof(float)));
+  if (!h.empty()) {
+    CR_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CR_CUDA(cudaMemcpy(f, hf.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  return CR_OK;
+}
+
+void LArr::release() {
+  if (d) cudaFree(d);
+  if (f) cudaFree(f);
+  d = nullptr;
+  f = nullptr;
+  n = 0;
+}
+
+// ---------------------------------------------------------------------------
+// filters (Section 3.3, Eq. fourth-power-beam) and the level table
+
+std::vector<double> q_filter(int lmax, double ell_star, double value) {
+  std::vector<double> q(lmax + 1);
+  const double lam = -std::log(value) / (ell_star * ell_star * (ell_star + 1.0) * (ell_star + 1.0));
+  for (int l = 0; l <= lmax; ++l) q[l] = std::exp(-(double)l * l * (l + 1.0) * (l + 1.0) * lam);
+  return q;
+}
+
+std::vector<double> gauss_filter(int lmax, int nside_h) {
+  const double fwhm = 2.0 * std::sqrt(4.0 * M_PI / (12.0 * (double)nside_h * nside_h));
+  const double s = fwhm / std::sqrt(8.0 * std::log(2.0));
+  std::vector<double> g(lmax + 1);
+  for (int l = 0; l <= lmax; ++l) g[l] = std::exp(-0.5 * l * (l + 1.0) * s * s);
+  return g;
+}
+
+// Default levels: the paper's Planck table for Nside 2048 / lmax 3000
+// (Table cycle-cost); otherwise pixel levels Nside/2, Nside/4, ... >= k with
+// lmax_1 = lmax, lmax_2 = min(lmax, 4 Nside_2), lmax_h = min(lmax_{h-1},
+// 6 Nside_h); filters: q with q_{2.51 Nside_1} = 0.1, times q with
+// q_{3 Nside_2} = 0.1, then Gaussians of FWHM 2 pixels clipped to the level
+// above; filter values below 1e-8 are cut and the band limit follows.
+void default_levels(int nside, int lmax, int k, std::vector<LevelSpec>& out, int* lmax_dense) {
+  out.clear();
+  std::vector<std::pair<int, int>> spec;
+  const bool planck = (nside == 2048 && lmax == 3000);
+  if (planck) {
+    spec = {{1024, 3000}, {512, 2048}, {256, 1280}, {128, 768}, {64, 384}, {32, 224}};
+  } else {
+    for (int nh = nside / 2; nh >= k; nh /= 2) {
+      int lh;
+      if (spec.empty()) lh = lmax;
+      else if (spec.size() == 1) lh = std::min(lmax, 4 * nh);
+      else lh = std::min(spec.back().second, 6 * nh);
+      spec.push_back({nh, lh});
+    }
+  }
+  std::vector<double> prev(lmax + 1, 1.0);
+  for (size_t i = 0; i < spec.size(); ++i) {
+    const int nh = spec[i].first;
+    int lh = spec[i].second;
+    std::vector<double> f;
+    if (i == 0) {
+      f = q_filter(lmax, planck ? 2570.0 : 2.51 * nh, 0.1);
+    } else if (i == 1) {
+      f = q_filter(lmax, planck ? 1536.0 : 3.0 * nh, 0.1);
+      for (int l = 0; l <= lmax; ++l) f[l] *= prev[l];
+    } else {
+      f = gauss_filter(lmax, nh);
+      for (int l = 0; l <= lmax; ++l) f[l] = std::min(f[l], prev[l]);
+    }
+    for (int l = lh + 1; l <= lmax; ++l) f[l] = 0.0;
+    for (int l = 0; l <= lmax; ++l)
+      if (f[l] < 1e-8) f[l] = 0.0;
+    int last = -1;
+    for (int l = 0; l <= lmax; ++l)
+      if (f[l] > 0.0) last = l;
+    lh = std::max(0, std::min(lh, last));
+    for (int l = lh + 1; l <= lmax; ++l) f[l] = 0.0;
+    LevelSpec s;
+    s.nside_h = nh;
+    s.lmax_h = lh;
+    s.n_rec = 2;
+    s.fl = f;
+    out.push_back(s);
+    prev = f;
+  }
+  if (!out.empty()) {
+    out.back().n_rec = 1;
+    *lmax_dense = std::min(40, out.back().lmax_h / 2);
+  } else {
+    *lmax_dense = std::min(40, lmax);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// HEALPix nested scheme (Gorski et al. 2005)
+
+static const int JRLL[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+static const int JPLL[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+
+__host__ __device__ static inline int64_t compress_bits(int64_t v) {
+  int64_t out = 0;
+  for (int b = 0; b < 31; ++b) out |= ((v >> (2 * b)) & 1) << b;
+  return out;
+}
+
+__host__ __device__ void nest_xyf(int64_t nside, int64_t ipix, int* ix, int* iy, int* f) {
+  const int64_t npf = nside * nside;
+  *f = (int)(ipix / npf);
+  const int64_t w = ipix % npf;
+  *ix = (int)compress_bits(w);
+  *iy = (int)compress_bits(w >> 1);
+}
+
+__host__ __device__ int64_t xyf_ring(int64_t N, int ix, int iy, int f) {
+  const int jrll[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+  const int jpll[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+  const int64_t jr = jrll[f] * N - ix - iy - 1;
+  int64_t nr, s, start;
+  if (jr < N) {
+    nr = jr;
+    s = 1;
+    start = 2 * jr * (jr - 1);
+  } else if (jr > 3 * N) {
+    nr = 4 * N - jr;
+    s = 1;
+    start = 12 * N * N - 2 * nr * (nr + 1);
+  } else {
+    nr = N;
+    s = (jr - N + 1) & 1;
+    start = 2 * N * (N - 1) + (jr - N) * 4 * N;
+  }
+  int64_t j = (nr * jpll[f] + ix - iy - s) / 2;
+  const int64_t M = 4 * nr;
+  j = ((j % M) + M) % M;
+  return start + j;
+}
+
+__host__ __device__ int64_t nest2ring(int64_t nside, int64_t ipix) {
+  int ix, iy, f;
+  nest_xyf(nside, ipix, &ix, &iy, &f);
+  return xyf_ring(nside, ix, iy, f);
+}
+
+// Unit vector of continuous face coordinates (x, y) in [0, N]^2 of face f.
+__host__ __device__ void face_vec(double N, int f, double x, double y, double* v) {
+  const int jrll[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+  const int jpll[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+  const double jr = jrll[f] * N - x - y;
+  double z, nr;
+  if (jr < N) {
+    z = 1.0 - jr * jr / (3.0 * N * N);
+    nr = jr;
+  } else if (jr > 3.0 * N) {
+    const double t = 4.0 * N - jr;
+    z = -(1.0 - t * t / (3.0 * N * N));
+    nr = t;
+  } else {
+    z = 4.0 / 3.0 - 2.0 * jr / (3.0 * N);
+    nr = N;
+  }
+  const double phi = nr > 0 ? 0.25 * M_PI * (jpll[f] + (x - y) / nr) : 0.0;
+  double omz;  // 1 - |z| exactly in the polar caps
+  if (jr < N) omz = jr * jr / (3.0 * N * N);
+  else if (jr > 3.0 * N) omz = (4.0 * N - jr) * (4.0 * N - jr) / (3.0 * N * N);
+  else omz = 1.0 - fabs(z);
+  const double st = sqrt(omz * (2.0 - omz));
+  v[0] = st * cos(phi);
+  v[1] = st * sin(phi);
+  v[2] = z;
+}
+
+// Exact integer key of a lattice point (x, y) of face f: its ring coordinate
+// jr = jrll N - x - y and azimuth numerator (jpll nr + x - y) mod 8 nr, which
+// identify the same sphere point seen from every face that contains it.
+static inline std::pair<int64_t, int64_t> vertex_key(int64_t N, int f, int64_t x, int64_t y) {
+  const int64_t jr = JRLL[f] * N - x - y;
+  int64_t nr;
+  if (jr < N) nr = jr;
+  else if (jr > 3 * N) nr = 4 * N - jr;
+  else nr = N;
+  if (nr == 0) return {jr, 0};
+  const int64_t M = 8 * nr;
+  int64_t num = (JPLL[f] * nr + x - y) % M;
+  if (num < 0) num += M;
+  return {jr, num};
+}
+
+// Tiles = pixels of the Nside_t grid; neighbours share at least one vertex.
+void tile_pattern(int nside_t, BlockPattern& P) {
+  const int nt = 12 * nside_t * nside_t;
+  P.ntile = nt;
+  std::map<std::pair<int64_t, int64_t>, std::vector<int>> keys;
+  for (int t = 0; t < nt; ++t) {
+    int ix, iy, f;
+    nest_xyf(nside_t, t, &ix, &iy, &f);
+    for (int dx = 0; dx <= 1; ++dx)
+      for (int dy = 0; dy <= 1; ++dy) keys[vertex_key(nside_t, f, ix + dx, iy + dy)].push_back(t);
+  }
+  P.nb.assign(nt, {});
+  for (auto& kv : keys)
+    for (int t : kv.second)
+      for (int u : kv.second) P.nb[t].push_back(u);
+  for (auto& v : P.nb) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  // greedy colouring in nested order; order colour-major, then tile index
+  std::vector<int> col(nt, -1);
+  int ncol = 0;
+  for (int t = 0; t < nt; ++t) {
+    std::vector<char> used(32, 0);
+    for (int u : P.nb[t])
+      if (col[u] >= 0 && col[u] < 32) used[col[u]] = 1;
+    int c = 0;
+    while (used[c]) ++c;
+    col[t] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  P.order.resize(nt);
+  std::iota(P.order.begin(), P.order.end(), 0);
+  std::stable_sort(P.order.begin(), P.order.end(), [&](int a, int b) { return col[a] < col[b]; });
+  P.pos.assign(nt, 0);
+  for (int p = 0; p < nt; ++p) P.pos[P.order[p]] = p;
+  P.colour_start.assign(ncol + 1, nt);
+  for (int p = nt - 1; p >= 0; --p) P.colour_start[col[P.order[p]]] = p;
+  P.colour_start[ncol] = nt;
+  for (int c = ncol - 1; c >= 0; --c)
+    if (P.colour_start[c] > P.colour_start[c + 1]) P.colour_start[c] = P.colour_start[c + 1];
+  // rows: blocks (p, q) for neighbouring q < p ascending, then the diagonal
+  P.row_ptr.assign(nt + 1, 0);
+  P.row_col.clear();
+  for (int p = 0; p < nt; ++p) {
+    std::vector<int> qs;
+    for (int u : P.nb[P.order[p]])
+      if (P.pos[u] < p) qs.push_back(P.pos[u]);
+    std::sort(qs.begin(), qs.end());
+    for (int q : qs) P.row_col.push_back(q);
+    P.row_col.push_back(p);
+    P.row_ptr[p + 1] = (int64_t)P.row_col.size();
+  }
+  P.nblocks = (int64_t)P.row_col.size();
+}
+
+int64_t BlockPattern::block_of(int p, int q) const {
+  const int* b = row_col.data() + row_ptr[p];
+  const int* e = row_col.data() + row_ptr[p + 1];
+  const int* it = std::lower_bound(b, e, q);
+  if (it == e || *it != q) return -1;
+  return row_ptr[p] + (it - b);
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels (one CTA per m; threads over l)
+
+template <typename T>
+__global__ void restrict_kernel(const typename Tr<T>::C* in, int Lh, typename Tr<T>::C* out, int LH, const T* ratio) {
+  const int m = blockIdx.x;
+  const int64_t oh = lm_off(Lh, m), oH = lm_off(LH, m);
+  for (int l = m + threadIdx.x; l <= LH; l += blockDim.x) out[oH + l - m] = cscale(in[oh + l - m], ratio[l]);
+}
+
+template <typename T>
+__global__ void prolong_add_kernel(typename Tr<T>::C* x, int Lh, const typename Tr<T>::C* c, int LH, const T* ratio) {
+  const int m = blockIdx.x;
+  const int64_t oh = lm_off(Lh, m), oH = lm_off(LH, m);
+  for (int l = m + threadIdx.x; l <= LH; l += blockDim.x) {
+    typename Tr<T>::C v = x[oh + l - m];
+    const typename Tr<T>::C a = c[oH + l - m];
+    v.x = fma(ratio[l], a.x, v.x);
+    v.y = fma(ratio[l], a.y, v.y);
+    x[oh + l - m] = v;
+  }
+}
+
+// x += d .* r with d indexed like the coefficients (complex storage index)
+template <typename T>
+__global__ void diag_axpy_kernel(typename Tr<T>::C* x, const typename Tr<T>::C* r, const T* d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    typename Tr<T>::C v = x[i];
+    const typename Tr<T>::C a = r[i];
+    v.x = fma(d[i], a.x, v.x);
+    v.y = fma(d[i], a.y, v.y);
+    x[i] = v;
+  }
+}
+
+// sum over (l, m) of w_m wl[l] Re(a conj b), w_0 = 1, w_m = 2, accumulated in FP64
+template <typename T>
+__global__ void dot_kernel(const typename Tr<T>::C* a, const typename Tr<T>::C* b, const double* wl, int L, double* out) {
+  const int m = blockIdx.x;
+  const int64_t o = lm_off(L, m);
+  double s = 0.0;
+  for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+    const typename Tr<T>::C u = a[o + l - m], v = b[o + l - m];
+    const double w = wl ? wl[l] : 1.0;
+    s += w * ((double)u.x * (double)v.x + (double)u.y * (double)v.y);
+  }
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    atomicAdd(out, (m == 0 ? 1.0 : 2.0) * t);
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* in, TO* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+// x += y (element type TY converted to TX)
+template <typename TX, typename TY>
+__global__ void add_convert_kernel(TX* x, const TY* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (TX)y[i];
+}
+
+template <typename T>
+int launch_restrict(const void* in, int Lh, void* out, int LH, const T* ratio, cudaStream_t st) {
+  restrict_kernel<T><<<LH + 1, 128, 0, st>>>((const typename Tr<T>::C*)in, Lh, (typename Tr<T>::C*)out, LH, ratio);
+  CR_CHECK_LAUNCH("restrict_kernel");
+  return CR_OK;
+}
+template <typename T>
+int launch_prolong_add(void* x, int Lh, const void* c, int LH, const T* ratio, cudaStream_t st) {
+  prolong_add_kernel<T><<<LH + 1, 128, 0, st>>>((typename Tr<T>::C*)x, Lh, (const typename Tr<T>::C*)c, LH, ratio);
+  CR_CHECK_LAUNCH("prolong_add_kernel");
+  return CR_OK;
+}
+template <typename T>
+int launch_diag_axpy(void* x, const void* r, const T* d, int64_t n, cudaStream_t st) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  diag_axpy_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>((typename Tr<T>::C*)x, (const typename Tr<T>::C*)r, d, n);
+  CR_CHECK_LAUNCH("diag_axpy_kernel");
+  return CR_OK;
+}
+template <typename T>
+int launch_dot(const void* a, const void* b, const double* wl, int L, double* out, cudaStream_t st) {
+  CR_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  dot_kernel<T><<<L + 1, 256, 0, st>>>((const typename Tr<T>::C*)a, (const typename Tr<T>::C*)b, wl, L, out);
+  CR_CHECK_LAUNCH("dot_kernel");
+  return CR_OK;
+}
+int launch_convert_d2f(const double* in, float* out, int64_t n, cudaStream_t st) {
+  convert_kernel<double, float><<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>(in, out, n);
+  CR_CHECK_LAUNCH("convert_kernel");
+  return CR_OK;
+}
+int launch_add_f2d(double* x, const float* y, int64_t n, cudaStream_t st) {
+  add_convert_kernel<double, float><<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>(x, y, n);
+  CR_CHECK_LAUNCH("add_convert_kernel");
+  return CR_OK;
+}
+
+template int launch_restrict<double>(const void*, int, void*, int, const double*, cudaStream_t);
+template int launch_restrict<float>(const void*, int, void*, int, const float*, cudaStream_t);
+template int launch_prolong_add<double>(void*, int, const void*, int, const double*, cudaStream_t);
+template int launch_prolong_add<float>(void*, int, const void*, int, const float*, cudaStream_t);
+template int launch_diag_axpy<double>(void*, const void*, const double*, int64_t, cudaStream_t);
+template int launch_diag_axpy<float>(void*, const void*, const float*, int64_t, cudaStream_t);
+template int launch_dot<double>(const void*, const void*, const double*, int, double*, cudaStream_t);
+template int launch_dot<float>(const void*, const void*, const double*, int, double*, cudaStream_t);
+
+}  // namespace cr

@@ -180,6 +180,16 @@ static void gl_rings(Grid& g, int ntheta, int nphi, std::vector<double>* weights
 
 static int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
   std::vector<float> z32(g.z.begin(), g.z.end());
+  // FP32 polar form for north rings with z > 1/2 (rings are ordered north to
+  // south, so these are the first pairs); 1 - z is exact in FP64 there.
+  std::vector<float> w32(g.nring);
+  g.npolar32 = 0;
+  for (int k = 0; k < g.nring; ++k) {
+    w32[k] = (float)(1.0 - g.z[k]);
+    if (k < g.npairs && g.z[k] > 0.5) g.npolar32 = k + 1;
+  }
+  CR_CUDA(cudaMalloc(&g.d_w32, g.nring * sizeof(float)));
+  CR_CUDA(cudaMemcpyAsync(g.d_w32, w32.data(), g.nring * sizeof(float), cudaMemcpyHostToDevice, st));
   // pair tables use the north ring of each pair
   CR_CUDA(cudaMalloc(&g.d_z, g.nring * sizeof(double)));
   CR_CUDA(cudaMalloc(&g.d_z32, g.nring * sizeof(float)));
@@ -193,7 +203,7 @@ static int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
 }
 
 static void grid_free(Grid& g) {
-  void* ptrs[] = {g.d_z, g.d_z32, g.d_sth, g.d_fft, g.d_tab, g.d_tab32, g.d_vhat, g.d_vhat32,
+  void* ptrs[] = {g.d_z, g.d_z32, g.d_w32, g.d_sth, g.d_fft, g.d_tab, g.d_tab32, g.d_vhat, g.d_vhat32,
                   g.d_tw, g.d_tw32, g.d_seed, g.d_lev, g.d_seed32, g.d_lev32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -202,34 +212,38 @@ static void grid_free(Grid& g) {
 // Recurrence tables for the rescaled recurrence Q_l = c_lm z Q_{l-1} - Q_{l-2},
 // P~_lm = s_lm Q_l, derived from the normalised three-term recurrence
 // P~_lm = a_lm (z P~_{l-1,m} - P~_{l-2,m} / a_{l-1,m}),
-// a_lm = sqrt((4 l^2 - 1) / (l^2 - m^2)).
+// a_lm = sqrt((4 l^2 - 1) / (l^2 - m^2)):
+//   s_l = (a_l / a_{l-1}) s_{l-2},  c_l = a_l s_{l-1} / s_l.
+// The even (l - m even) and odd chains of s are independent; s_m = 1 and the
+// odd chain is scaled so both chains end at the same value at l = Lc.  Then
+// c_l -> 2 for l >> m, so near the poles Q varies slowly in l and c - 2 is
+// small, which the FP32 difference form of the recurrence relies on.
 static int build_coef(cr_plan* P, int Lc) {
   const int64_t nlm = n_lm(Lc);
-  std::vector<double> c(nlm), s(nlm);
+  std::vector<double> c(nlm), s(nlm), a(Lc + 1);
   for (int m = 0; m <= Lc; ++m) {
     const int64_t o = lm_off(Lc, m);
-    c[o] = 0.0;
+    const int K = Lc - m;
+    for (int l = m + 1; l <= Lc; ++l) a[l - m] = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
     s[o] = 1.0;
-    if (m + 1 > Lc) continue;
-    double a_prev = std::sqrt(2.0 * m + 3.0);
-    c[o + 1] = a_prev;
-    s[o + 1] = 1.0;
-    double s_m2 = 1.0, s_m1 = 1.0;
-    for (int l = m + 2; l <= Lc; ++l) {
-      const double a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
-      const double sl = (a / a_prev) * s_m2;
-      c[o + (l - m)] = a * s_m1 / sl;
-      s[o + (l - m)] = sl;
-      s_m2 = s_m1;
-      s_m1 = sl;
-      a_prev = a;
+    if (K >= 1) s[o + 1] = 1.0;
+    for (int k = 2; k <= K; ++k) s[o + k] = (a[k] / a[k - 1]) * s[o + k - 2];
+    if (K >= 2) {
+      const int ke = (K % 2 == 0) ? K : K - 1, ko = (K % 2 == 1) ? K : K - 1;
+      const double r = s[o + ke] / s[o + ko];
+      for (int k = 1; k <= K; k += 2) s[o + k] *= r;
     }
+    c[o] = 0.0;
+    for (int k = 1; k <= K; ++k) c[o + k] = a[k] * s[o + k - 1] / s[o + k];
   }
-  std::vector<float> c32(c.begin(), c.end()), s32(s.begin(), s.end());
+  std::vector<float> c32(c.begin(), c.end()), s32(s.begin(), s.end()), c2_32(nlm);
+  for (int64_t i = 0; i < nlm; ++i) c2_32[i] = (float)(c[i] - 2.0);
   CR_CUDA(cudaMalloc(&P->d_c, nlm * sizeof(double)));
   CR_CUDA(cudaMalloc(&P->d_s, nlm * sizeof(double)));
   CR_CUDA(cudaMalloc(&P->d_c32, nlm * sizeof(float)));
   CR_CUDA(cudaMalloc(&P->d_s32, nlm * sizeof(float)));
+  CR_CUDA(cudaMalloc(&P->d_c2_32, nlm * sizeof(float)));
+  CR_CUDA(cudaMemcpy(P->d_c2_32, c2_32.data(), nlm * sizeof(float), cudaMemcpyHostToDevice));
   CR_CUDA(cudaMemcpy(P->d_c, c.data(), nlm * sizeof(double), cudaMemcpyHostToDevice));
   CR_CUDA(cudaMemcpy(P->d_s, s.data(), nlm * sizeof(double), cudaMemcpyHostToDevice));
   CR_CUDA(cudaMemcpy(P->d_c32, c32.data(), nlm * sizeof(float), cudaMemcpyHostToDevice));
@@ -262,7 +276,7 @@ static void plan_free(cr_plan* P) {
     grid_free(*g);
     delete g;
   }
-  void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
+  void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_c2_32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
                   P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -287,10 +301,14 @@ static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
     a.z = g.d_z;
     a.seed = g.d_seed;
     a.lev = g.d_lev;
+    a.npolar = 0;
   } else {
     a.c = P->d_c32;
+    a.c2 = P->d_c2_32;
     a.s = P->d_s32;
     a.z = g.d_z32;
+    a.w = g.d_w32;
+    a.npolar = g.npolar32;
     a.seed = g.d_seed32;
     a.lev = g.d_lev32;
   }

@@ -38,6 +38,8 @@ struct Grid {
   // device tables
   double* d_z = nullptr;      // [nring]
   float* d_z32 = nullptr;     // [nring]
+  float* d_w32 = nullptr;     // [nring] 1 - z (FP32 polar recurrence form)
+  int npolar32 = 0;           // FP32: pairs [0, npolar32) use the polar form
   double* d_sth = nullptr;    // [nring]
   RingFFT* d_fft = nullptr;   // [nring]
   double2* d_tab = nullptr;   // concatenated e^{i pi u/n}
@@ -106,6 +108,7 @@ struct cr_plan {
   double* d_c = nullptr;
   double* d_s = nullptr;
   float* d_c32 = nullptr;
+  float* d_c2_32 = nullptr;  // c - 2, FP32 (polar difference form)
   float* d_s32 = nullptr;
   // operator diagonals (l-indexed, [lmax+1])
   bool has_op = false;

@@ -14,7 +14,7 @@ from paper_1308_5299_gb300 import binding, synthetic
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10   # FP64 transforms vs the oracle, relative L2
-TOL32 = 2e-5    # FP32 transforms vs the oracle, relative L2
+TOL32 = 1e-5    # FP32 transforms vs the oracle, relative L2
 
 
 @pytest.fixture(scope="module")
@@ -134,6 +134,17 @@ def test_full_size_sampled_rings(dev, nside, lmax):
     b = torch.empty(sht.n_lm(lmax), dtype=torch.complex128, device=dev)
     plan.sht_adjoint(torch.from_numpy(y).to(dev), b)
     assert rel_l2(b.cpu().numpy(), sht.adjoint(y, lmax, g, rings=rings)) < TOL64
+    # FP32 transforms on the same sampled rings (polar rings use the
+    # difference form of the recurrence)
+    m32 = torch.empty(g["npix"], dtype=torch.float32, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(torch.complex64).to(dev), m32)
+    m32h = m32.cpu().numpy()
+    for k in rings:
+        sl = slice(g["off"][k], g["off"][k] + g["nphi"][k])
+        assert rel_l2(m32h[sl], ref[sl]) < 2e-4, k
+    b32 = torch.empty(sht.n_lm(lmax), dtype=torch.complex64, device=dev)
+    plan.sht_adjoint(torch.from_numpy(y).to(torch.float32).to(dev), b32)
+    assert rel_l2(b32.cpu().numpy(), sht.adjoint(y, lmax, g, rings=rings)) < 1e-4
     # adjoint identity over the whole grid
     yy = synthetic.random_map(g["npix"], seed=3)
     bb = torch.empty(sht.n_lm(lmax), dtype=torch.complex128, device=dev)
