@@ -150,6 +150,31 @@ int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int d
 int cr_plan_set_timing(cr_plan* plan, int enable);
 int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, int* count);
 
+/*
+ * Allocation-free synthesis (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc at all -- code running while a CUDA
+ * graph is captured, allocator callbacks, real-time loops, or code working
+ * inside a device-memory budget owned by another framework -- and therefore
+ * cannot create a plan: map = Y alm in FP64 on the HEALPix grid of `nside`
+ * (RING order) at band limit `lmax`, the same operation and layouts as
+ * cr_sht_synth with dtype CR_F64, but with no plan and no allocation.
+ *   alm   DEVICE [N_lm(lmax)] double2 (16-byte aligned), input.
+ *   map   DEVICE [12 nside^2] double, output.
+ *   stream  cudaStream_t (NULL = default stream).
+ * The library's only scratch for this call is a fixed 16 MiB device array in
+ * the library itself, so (4 nside - 1)(lmax + 1) * 16 bytes must not exceed
+ * 16 MiB (e.g. nside 256 with lmax <= 1023); larger sizes return CR_EINVAL.
+ * The array exists on every GPU that loads the library until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (different streams, or different host threads on the same device) race, so
+ * serialise them.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Errors: CR_EINVAL, CR_ECUDA.
+ */
+int cr_sht_synth_noalloc(int nside, int lmax, const void* alm, void* map, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,8 @@ _SIGS = {
                        ctypes.c_int),
     "cr_apply_A": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
                    ctypes.c_int),
+    "cr_sht_synth_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                             ctypes.c_int),
     "cr_plan_set_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_plan_timing": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long),
@@ -106,6 +108,19 @@ def _dev(t):
 
 def n_lm(lmax):
     return (lmax + 1) * (lmax + 2) // 2
+
+
+def sht_synth_noalloc(nside, lmax, alm, out, stream=None):
+    """FP64 synthesis with no plan and no allocation (``cr_sht_synth_noalloc``):
+    for callers that cannot allocate device memory.  ``alm`` complex128 and
+    ``out`` float64 CUDA tensors."""
+    if alm.dtype != torch.complex128 or out.dtype != torch.float64:
+        raise TypeError("sht_synth_noalloc is FP64 only")
+    if alm.numel() != n_lm(lmax) or out.numel() != 12 * nside * nside:
+        raise ValueError("sht_synth_noalloc: sizes")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().cr_sht_synth_noalloc(int(nside), int(lmax), _dev(alm), _dev(out), ctypes.c_void_p(st.cuda_stream)))
+    return out
 
 
 class Plan:
