@@ -58,6 +58,11 @@ extern "C" {
 /* arithmetic of a call */
 #define CR_F64 0
 #define CR_F32 1
+/* solve mode: FP32 W-cycles inside an FP64 iterative-refinement loop */
+#define CR_MIXED 2
+/* solve flag (or-ed with CR_F64 / CR_MIXED): flexible preconditioned CG with
+ * one CR-Cycle as the preconditioner instead of repeated cycles */
+#define CR_PCG 4
 
 /* grid kinds */
 #define CR_GRID_HEALPIX 0
@@ -67,6 +72,20 @@ extern "C" {
 #define CR_OBS 0 /* the observation grid at the plan's lmax; level grids are CR_OBS + h, h >= 1 */
 
 typedef struct cr_plan cr_plan;
+
+/*
+ * One spherical-harmonic level with its sibling pixel grid (Section 3.2):
+ * HEALPix Nside_h (power of two, >= 8, <= the observation Nside), band limit
+ * lmax_h (non-increasing from level to level), n_rec recursions into the
+ * next coarser level, and the cumulative filter f^h_l (HOST [lmax + 1];
+ * entries above lmax_h are ignored).
+ */
+typedef struct cr_level_spec {
+  int nside_h;
+  int lmax_h;
+  int n_rec;
+  const double* fl;
+} cr_level_spec;
 
 /*
  * Plan parameters.  struct_size must be sizeof(cr_params).
@@ -91,6 +110,27 @@ typedef struct cr_params {
   const double* bl;
   const double* ninv;
   void* stream;
+  /* multi-level solver (needs cl).  nlevels: -1 = the default level table
+   * (the paper's Planck table for Nside 2048 / lmax 3000, otherwise levels
+   * at Nside/2, Nside/4, ... >= 8 with fourth-power and Gaussian filters),
+   * 0 = no levels (transforms and A only), > 0 = the `levels` array (fine to
+   * coarse).  lmax_dense: band limit of the bottom dense level (-1: default
+   * min(40, lmax_H / 2)).  ridge_factor (0: 1.5) and ridge_bisections
+   * (0: 30) set the incomplete-Cholesky ridge search (Section 3.5);
+   * ridge_alpha (HOST [nlevels], or NULL) fixes the ridges instead.
+   * ridge_lambda_target (0: 1.5; < 0: off): after the ridge search the
+   * ridge is raised further until a power-iteration estimate of the largest
+   * eigenvalue of S_h A_h (smoother times level operator) is at most this
+   * value, so that no error-smoothing step over-corrects (not applied when
+   * ridge_alpha is given); the top-level diagonal smoother is scaled down to
+   * the same bound when its estimate exceeds it. */
+  int nlevels;
+  const cr_level_spec* levels;
+  int lmax_dense;
+  double ridge_factor;
+  int ridge_bisections;
+  const double* ridge_alpha;
+  double ridge_lambda_target;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */
@@ -138,17 +178,81 @@ int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs
 int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int dtype);
 
 /*
+ * Multi-level solver (Section 3.2, Fig. code:mg).  Levels are numbered
+ * h = 0 (top, lmax, diagonal smoother), 1..H (pixel levels), H + 1 (bottom
+ * dense level).  Vectors of level h use that level's band limit lmax_h.
+ * All entry points below need a plan created with levels.
+ */
+/* Number of pixel levels H. */
+int cr_plan_nlevels(cr_plan* plan, int* H);
+/* Level h: pixel grid Nside_h (0 for the top and bottom), lmax_h, n_rec,
+ * the cumulative filter (HOST out [lmax + 1]), the ridge alpha used by its
+ * incomplete Cholesky (for h = 0: the damping factor applied to the
+ * diagonal smoother) and the estimate of lambda_max(S_h A_h) (for h >= 1
+ * after the ridge adjustment; for h = 0 before damping; 0 when not
+ * estimated).  Any output pointer may be NULL. */
+int cr_plan_level(cr_plan* plan, int h, int* nside_h, int* lmax_h, int* n_rec, double* fl, double* ridge,
+                  double* lambda_max);
+/* y = A_h x, A_h = D_h + B_h Y^T N^-1 Y B_h (Eq. A_h); h = 0 is A. */
+int cr_level_apply(cr_plan* plan, int h, const void* x, void* y, int dtype);
+/* r_H = I_h^H r_h: diagonal f^{h+1}/f^h, truncated at lmax_{h+1} (Eq. f_l). */
+int cr_restrict(cr_plan* plan, int h, const void* r_h, void* r_H, int dtype);
+/* x_h += (I_h^H)^T c_H (interpolation = transposed restriction). */
+int cr_prolong_add(cr_plan* plan, int h, const void* c_H, void* x_h, int dtype);
+/* c = S_h(r), the error-smoothing correction of level h for residual r:
+ * h = 0: (1 - f^1) diag(A)^-1 r (Section 3.2);  h >= 1: Y_h^T M_h Y_h r with
+ * M_h the block incomplete-Cholesky smoother (Section 3.5, Eqs.
+ * pixel-correction-1..3).  c is overwritten. */
+int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype);
+/* x = A_bottom^-1 b on the bottom level (l <= lmax_dense), dense (FP64). */
+int cr_bottom_solve(cr_plan* plan, const void* b, void* x, int dtype);
+/* The assembled real-basis matrix of the bottom level (before factorising):
+ * A_bottom = D + B (Y^T N^-1 Y) B over the active real dofs with l <= lmax_dense,
+ * from the ring formula (Section 3.3, Eq. Ni-dense).  Dof order: a_l0 for
+ * l = 0..lmax_dense, then (sqrt2 Re a_lm, sqrt2 Im a_lm) for m >= 1 in storage
+ * order, inactive (C_l = 0) dofs removed.  *nd receives the dimension; host
+ * (may be NULL) receives nd x nd doubles, row-major. */
+int cr_bottom_matrix(cr_plan* plan, double* host, int* nd);
+/* One CR-Cycle from the top level, improving x in place for right-hand
+ * side b (Fig. code:mg).  x, b: [nrhs][N_lm(lmax)]. */
+int cr_wcycle(cr_plan* plan, void* x, const void* b, int nrhs, int dtype);
+/*
+ * CR-Solve (Fig. code:mg): x = 0, repeat CR-Cycle and r = b - A x until
+ * r^T S^-1 r < eps b^T S^-1 b (eps = 1e-12 is a 1e-6 relative residual).
+ * x, b: FP64 [nrhs][N_lm(lmax)].  mode CR_F64: every cycle in FP64;
+ * CR_MIXED: each cycle in FP32 applied to the FP64 residual (iterative
+ * refinement; the residual r = b - A x is always FP64).  Or-ed with CR_PCG:
+ * flexible preconditioned CG (Polak-Ribiere beta) whose preconditioner is
+ * one CR-Cycle from zero, in the chosen precision, with A and the residual in
+ * FP64; one cycle and one FP64 A per iteration.  Outputs (may be
+ * NULL): cycles_out[nrhs], relres_out[nrhs] (final sqrt of the ratio),
+ * history[nrhs][max_cycles] (relative residual after each cycle).
+ * Errors: CR_EDIVERGED (residual grew over two consecutive cycles),
+ * CR_EMAXITER, CR_ENONFINITE; x holds the last iterate in each case.
+ */
+int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int max_cycles, int mode, int* cycles_out,
+             double* relres_out, double* history);
+
+/*
  * Per-stage timing (the per-level, per-action cost breakdown of the paper's
  * Table "cycle-cost"): while enabled, every kernel stage launched by the plan
  * is bracketed by CUDA events on the plan's stream and accumulated by stage
  * name.  cr_plan_set_timing(plan, 1) clears and enables, 0 disables.
  * cr_plan_timing synchronises the recorded events and reports stage i
  * (0 <= i < *count) in name order: its name (NUL-terminated, truncated to
- * name_cap), total milliseconds and number of launches; i < 0 only sets
- * *count.  Any output pointer may be NULL.
+ * name_cap; transform stages carry a _f64 / _f32 suffix), total
+ * milliseconds, number of recorded scopes, and the algorithmic work of those
+ * scopes (flops for the Legendre stages: 8 per ring pair and (l, m); bytes
+ * for the pixel smoother: the factor blocks read twice; 0 where not
+ * defined); i < 0 only sets *count.  Any output pointer may be NULL.
  */
 int cr_plan_set_timing(cr_plan* plan, int enable);
-int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, int* count);
+/* Number of kernels the library has launched in this process on the
+ * transform, operator, smoother and solver paths (plan-time table builders
+ * excluded); the difference across a region counts its launches. */
+long cr_launch_count(void);
+int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, double* work,
+                   int* count);
 
 /*
  * Allocation-free synthesis (no counterpart in the paper).

@@ -52,7 +52,7 @@ def gauss_filter(lmax, nside_h):
     return np.exp(-0.5 * l * (l + 1.0) * s * s)
 
 
-def level_table(nside, lmax, k=8, planck=None):
+def level_table(nside, lmax, k=8, planck=None, first=None):
     """Levels for an observation grid of Nside ``nside`` and band limit
     ``lmax``.  Returns dict(top, levels[list], bottom).  Each pixel level:
     nside_h, lmax_h, fl (cumulative filter, length lmax+1, zero above
@@ -64,7 +64,7 @@ def level_table(nside, lmax, k=8, planck=None):
         spec = [(1024, 3000), (512, 2048), (256, 1280), (128, 768), (64, 384), (32, 224)]
     else:
         spec = []
-        nh = nside // 2
+        nh = nside // 2 if first is None else first
         while nh >= k:
             if not spec:
                 lh = lmax
@@ -379,7 +379,10 @@ class PixelLevel:
 
 
 class Hierarchy:
-    def __init__(self, prob, table=None, k=8, ridge_factor=1.5, alphas=None):
+    def __init__(self, prob, table=None, k=8, ridge_factor=1.5, alphas=None, lambda_target=None):
+        """lambda_target: if given (and alphas is None), each level's ridge is
+        raised after the search until the power-iteration estimate of
+        lambda_max(S_h A_h) is at most this value."""
         self.prob = prob
         self.table = table or level_table(prob.grid["nside"], prob.lmax, k=k)
         self.levels = self.table["levels"]
@@ -402,6 +405,33 @@ class Hierarchy:
         self.act_d = act_d
         self.Abottom = 0.5 * (Ad + Ad.T)
         self.chol_bottom = scipy.linalg.cho_factor(self.Abottom, lower=True)
+        self.lambda_max = [None] * len(self.pix)
+        if lambda_target is not None and alphas is None:
+            for h in range(1, len(self.pix) + 1):
+                pl = self.pix[h - 1]
+                for _ in range(24):
+                    lam = self.smoother_lambda_max(h)
+                    self.lambda_max[h - 1] = lam
+                    if lam <= lambda_target:
+                        break
+                    a = pl.alpha if pl.alpha > 0 else 1e-6 * np.max(np.abs(pl.Ahat))
+                    a *= max(2.0, lam / lambda_target)
+                    pl.alpha = a
+                    pl.L = icc0_blocks(pl.Ahat + a * np.eye(len(pl.perm)), 64, pl.nbmat_ord)
+
+    def smoother_lambda_max(self, h, iters=12, seed=0):
+        """Rayleigh-quotient power iteration for lambda_max(S_h A_h) in the
+        A_h inner product."""
+        L = self.lmax_h(h)
+        rs = np.random.default_rng(seed)
+        v = rs.uniform(-1, 1, size=sht.n_lm(L)) + 1j * rs.uniform(-1, 1, size=sht.n_lm(L))
+        lam = 0.0
+        for _ in range(iters):
+            av = self.apply_A(h, v)
+            w = self.smooth(h, av)
+            lam = sht.alm_dot(w, av, L) / sht.alm_dot(v, av, L)
+            v = w / np.sqrt(sht.alm_dot(w, w, L))
+        return lam
 
     # level h: 0 = top, 1..H = pixel levels, H+1 = bottom
     def fl(self, h):

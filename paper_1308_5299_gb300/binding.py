@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcrgb300.so")
 
 CR_OK = 0
-CR_F64, CR_F32 = 0, 1
+CR_F64, CR_F32, CR_MIXED, CR_PCG = 0, 1, 2, 4
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0
 
@@ -31,6 +31,11 @@ class CRError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
         self.code = code
+
+
+class cr_level_spec(ctypes.Structure):
+    _fields_ = [("nside_h", ctypes.c_int), ("lmax_h", ctypes.c_int), ("n_rec", ctypes.c_int),
+                ("fl", ctypes.POINTER(ctypes.c_double))]
 
 
 class cr_params(ctypes.Structure):
@@ -45,6 +50,13 @@ class cr_params(ctypes.Structure):
         ("bl", ctypes.POINTER(ctypes.c_double)),
         ("ninv", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
+        ("nlevels", ctypes.c_int),
+        ("levels", ctypes.POINTER(cr_level_spec)),
+        ("lmax_dense", ctypes.c_int),
+        ("ridge_factor", ctypes.c_double),
+        ("ridge_bisections", ctypes.c_int),
+        ("ridge_alpha", ctypes.POINTER(ctypes.c_double)),
+        ("ridge_lambda_target", ctypes.c_double),
     ]
 
 
@@ -66,9 +78,25 @@ _SIGS = {
     "cr_sht_synth_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                              ctypes.c_int),
     "cr_plan_set_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "cr_launch_count": ([], ctypes.c_long),
+    "cr_plan_nlevels": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cr_plan_level": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cr_level_apply": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "cr_restrict": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "cr_prolong_add": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "cr_smooth": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "cr_bottom_solve": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "cr_bottom_matrix": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
+                         ctypes.c_int),
+    "cr_wcycle": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "cr_solve": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_plan_timing": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long),
-                        ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
 }
 
 
@@ -110,6 +138,11 @@ def n_lm(lmax):
     return (lmax + 1) * (lmax + 2) // 2
 
 
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().cr_launch_count())
+
+
 def sht_synth_noalloc(nside, lmax, alm, out, stream=None):
     """FP64 synthesis with no plan and no allocation (``cr_sht_synth_noalloc``):
     for callers that cannot allocate device memory.  ``alm`` complex128 and
@@ -126,7 +159,11 @@ def sht_synth_noalloc(nside, lmax, alm, out, stream=None):
 class Plan:
     """One CR system / transform plan (``cr_plan_create``)."""
 
-    def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None):
+    def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
+                 lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0):
+        """levels: None (transforms and A only), "default" (the library's level
+        table), or a list of dicts with nside_h, lmax_h, n_rec and fl
+        (cumulative filter, length lmax+1)."""
         p = cr_params()
         p.struct_size = ctypes.sizeof(cr_params)
         if gl is not None:
@@ -153,6 +190,30 @@ class Plan:
             p.ninv = ninv.data_ptr()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         p.stream = self.stream.cuda_stream
+        if levels is None:
+            p.nlevels = 0
+        elif isinstance(levels, str) and levels == "default":
+            p.nlevels = -1
+        else:
+            arr = (cr_level_spec * len(levels))()
+            for i, lv in enumerate(levels):
+                f = np.ascontiguousarray(lv["fl"], dtype=np.float64)
+                self._keep.append(f)
+                arr[i].nside_h = int(lv["nside_h"])
+                arr[i].lmax_h = int(lv["lmax_h"])
+                arr[i].n_rec = int(lv["n_rec"])
+                arr[i].fl = f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            self._keep.append(arr)
+            p.nlevels = len(levels)
+            p.levels = arr
+        p.lmax_dense = int(lmax_dense)
+        p.ridge_factor = float(ridge_factor)
+        p.ridge_bisections = int(ridge_bisections)
+        p.ridge_lambda_target = float(ridge_lambda_target)
+        if ridge_alpha is not None:
+            ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
+            self._keep.append(ra)
+            p.ridge_alpha = ra.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         h = ctypes.c_void_p()
         _check(lib().cr_plan_create(ctypes.byref(h), ctypes.byref(p)))
         self._h = h
@@ -202,16 +263,82 @@ class Plan:
         _check(lib().cr_plan_set_timing(self._h, 1 if enable else 0))
 
     def timing(self):
-        """{stage name: (total ms, launches)} since timing was enabled."""
+        """{stage name: (total ms, scopes, algorithmic work)} since timing was
+        enabled."""
         cnt = ctypes.c_int()
-        _check(lib().cr_plan_timing(self._h, -1, None, 0, None, None, ctypes.byref(cnt)))
+        _check(lib().cr_plan_timing(self._h, -1, None, 0, None, None, None, ctypes.byref(cnt)))
         out = {}
         for i in range(cnt.value):
             buf = ctypes.create_string_buffer(64)
-            ms, n = ctypes.c_double(), ctypes.c_long()
-            _check(lib().cr_plan_timing(self._h, i, buf, 64, ctypes.byref(ms), ctypes.byref(n), None))
-            out[buf.value.decode()] = (ms.value, n.value)
+            ms, n, w = ctypes.c_double(), ctypes.c_long(), ctypes.c_double()
+            _check(lib().cr_plan_timing(self._h, i, buf, 64, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w),
+                                        None))
+            out[buf.value.decode()] = (ms.value, n.value, w.value)
         return out
+
+    # ---- multi-level solver -------------------------------------------------
+    def nlevels(self):
+        h = ctypes.c_int()
+        _check(lib().cr_plan_nlevels(self._h, ctypes.byref(h)))
+        return h.value
+
+    def level(self, h):
+        """dict(nside_h, lmax_h, n_rec, fl, ridge) of level h (0 = top,
+        1..H pixel levels, H+1 bottom)."""
+        ns, lm, nr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        fl = np.zeros(self.lmax + 1)
+        ridge, lam = ctypes.c_double(), ctypes.c_double()
+        _check(lib().cr_plan_level(self._h, h, ctypes.byref(ns), ctypes.byref(lm), ctypes.byref(nr),
+                                   fl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(ridge),
+                                   ctypes.byref(lam)))
+        return dict(nside_h=ns.value, lmax_h=lm.value, n_rec=nr.value, fl=fl, ridge=ridge.value, lambda_max=lam.value)
+
+    def level_apply(self, h, x, out):
+        _check(lib().cr_level_apply(self._h, h, _dev(x), _dev(out), _dtype_code(x)))
+        return out
+
+    def restrict(self, h, r, out):
+        _check(lib().cr_restrict(self._h, h, _dev(r), _dev(out), _dtype_code(r)))
+        return out
+
+    def prolong_add(self, h, c, x):
+        _check(lib().cr_prolong_add(self._h, h, _dev(c), _dev(x), _dtype_code(c)))
+        return x
+
+    def smooth(self, h, r, out):
+        _check(lib().cr_smooth(self._h, h, _dev(r), _dev(out), _dtype_code(r)))
+        return out
+
+    def bottom_solve(self, b, out):
+        _check(lib().cr_bottom_solve(self._h, _dev(b), _dev(out), _dtype_code(b)))
+        return out
+
+    def bottom_matrix(self):
+        nd = ctypes.c_int()
+        _check(lib().cr_bottom_matrix(self._h, None, ctypes.byref(nd)))
+        out = np.zeros((nd.value, nd.value))
+        _check(lib().cr_bottom_matrix(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(nd)))
+        return out
+
+    def wcycle(self, x, b):
+        nrhs = self._nrhs(b, n_lm(self.lmax))
+        _check(lib().cr_wcycle(self._h, _dev(x), _dev(b), nrhs, _dtype_code(b)))
+        return x
+
+    def solve(self, b, x, eps=1e-12, max_cycles=30, mode=CR_F64, check=True):
+        """CR-Solve.  Returns (cycles, relres, history) per right-hand side;
+        with check=False a CR_EDIVERGED / CR_EMAXITER status is returned as
+        the 4th element instead of raising."""
+        nrhs = self._nrhs(b, n_lm(self.lmax))
+        cyc = (ctypes.c_int * nrhs)()
+        rel = (ctypes.c_double * nrhs)()
+        hist = np.zeros((nrhs, max_cycles))
+        rc = lib().cr_solve(self._h, _dev(x), _dev(b), nrhs, float(eps), int(max_cycles), int(mode), cyc, rel,
+                            hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if check:
+            _check(rc)
+        out = (list(cyc), list(rel), hist)
+        return out if check else out + (rc,)
 
     def apply_A(self, x, out, level=0):
         nrhs = self._nrhs(x, n_lm(self.lmax)) if level == 0 else x.numel() // max(1, out.numel())

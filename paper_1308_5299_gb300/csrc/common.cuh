@@ -51,6 +51,10 @@ __host__ __device__ inline int64_t lm_off(int L, int m) {
 }
 __host__ __device__ inline int64_t n_lm(int L) { return (int64_t)(L + 1) * (L + 2) / 2; }
 
+// ---- launch accounting (kernels launched by the library, process-wide) ----
+void count_launch(long n = 1);
+long launch_count();
+
 // ---- error plumbing ----------------------------------------------------------
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);

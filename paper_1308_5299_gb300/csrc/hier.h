@@ -47,6 +47,7 @@ struct PixLevel {
   BlockPattern pat;
   double alpha = 0.0;      // ridge used for the factorisation
   double amax = 0.0;       // max |A_hat| entry
+  double lambda_max = 0.0; // power-iteration estimate of lambda_max(S_h A_h) after the ridge
   // device
   float* d_A = nullptr;    // A_hat blocks
   float* d_L = nullptr;    // factor blocks (diagonal blocks hold inv(L_pp))
@@ -75,11 +76,14 @@ struct Hierarchy {
   int n_rec_top = 1;
   // top-level diagonal smoother: x += H_l r / diag(A)
   LArr inv_diag_hp;           // [n_lm(lmax)] (highpass / diag(A)), complex-storage index
+  double top_lambda = 0.0;    // lambda_max estimate of the top smoother (before scaling)
+  double top_scale = 1.0;     // damping applied to the top smoother
   // bottom dense level
   int ld = 0;
   std::vector<double> fb;     // bottom filter [lmax + 1]
   int nd = 0;                 // active real dofs of the bottom block
   double* d_Ainv = nullptr;   // [nd][nd] inverse of the bottom A (FP64)
+  double* d_Abottom = nullptr; // [nd][nd] the assembled bottom A (FP64)
   int* d_dof_lm = nullptr;    // real dof -> (lm index * 2 + part)
   LArr bd;                    // B at the bottom, used by the ring formula
   // per-level work vectors (complex, sized for double2)
@@ -91,7 +95,8 @@ struct Hierarchy {
   void* map_work2 = nullptr;
   double* d_dot = nullptr;    // dot-product scratch
   double* d_dot_host = nullptr;
-  std::vector<double> restrict_ratio_h;
+  void* ops_store = nullptr;  // per-level operator arrays (solver.cu)
+  void* krylov[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // PCG vectors (FP64, top level)
 };
 
 }  // namespace cr

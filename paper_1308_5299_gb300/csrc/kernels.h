@@ -27,6 +27,7 @@ struct LegArgs {
   int ld_seed = 0;
   int npairs = 0, nring = 0;
   typename Tr<T>::C* partial = nullptr;    // adjoint: [nblk][n_lm(L)]
+  const T* ringval = nullptr;              // SQ variant: per-ring value
 };
 
 template <typename T>
@@ -38,6 +39,7 @@ struct FinalizeArgs {
   const T* dadd = nullptr;                 // per-l multiplier of xadd (may be null)
   const typename Tr<T>::C* xadd = nullptr;
   int accumulate = 0;                      // out += result instead of out = result
+  const typename Tr<T>::C* bsub = nullptr; // if set: out = bsub - result (residual)
   typename Tr<T>::C* out = nullptr;
 };
 
@@ -62,7 +64,23 @@ struct RingArgs {
 template <typename T> int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st);
 template <typename T> int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream_t st);
 int leg_partial_blocks(int npairs);
+int launch_leg_diag(cr_plan* P, const double* ringval, double2* out);
 template <typename T> int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st);
+
+// transform drivers (plan.cu)
+template <typename T> int do_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, const T* dl);
+template <typename T>
+int do_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, const T* dl_out, const T* dadd,
+               const void* xadd, int accumulate);
+template <typename T>
+int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const T* dl_in, const T* pix,
+                const T* dl_out, const T* dadd, T* map_copy, const void* bsub);
+
+// grids and workspace (plan.cu)
+void healpix_rings(Grid& g, int N);
+int grid_upload(Grid& g, int Lseed, cudaStream_t st);
+void grid_free(Grid& g);
+int ensure_workspace(cr_plan* P, const Grid& g, int L);
 
 // plan-time table builders (ringfft.cu)
 int build_fft_tables(Grid& g, cudaStream_t st);

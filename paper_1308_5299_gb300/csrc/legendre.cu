@@ -237,7 +237,10 @@ __device__ __forceinline__ void warp_reduce8(C v[8]) {
   v[0].y += shfl_x(v[0].y, 1);
 }
 
-template <typename T, bool POLAR>
+// SQ: accumulate P~^2 times a per-ring value (ringval) instead of P~ times
+// the ring's phase G_m: sum_k P~_lm(z_k)^2 v_k, used for the diagonal of
+// Y^T N^-1 Y (the Delta m = 0 term of the ring formula).
+template <typename T, bool POLAR, bool SQ = false>
 __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
   const int m = blockIdx.x;
@@ -267,10 +270,16 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
       P2[j] = POLAR ? sd : -sd;
       lev[j] = a.lev[(int64_t)m * a.ld_seed + p];
       const int rn = p, rs = a.nring - 1 - p;
-      const C gn = a.phase[(int64_t)rn * a.ldp + m];
-      const C gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : mk((T)0, (T)0);
-      GE[j] = cadd(gn, gs);
-      GO[j] = csub(gn, gs);
+      if (SQ) {
+        const T v = a.ringval[rn] + ((rs != rn) ? a.ringval[rs] : (T)0);
+        GE[j] = mk(v, (T)0);
+        GO[j] = GE[j];
+      } else {
+        const C gn = a.phase[(int64_t)rn * a.ldp + m];
+        const C gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : mk((T)0, (T)0);
+        GE[j] = cadd(gn, gs);
+        GO[j] = csub(gn, gs);
+      }
     } else {
       zz[j] = 0;
       P2[j] = 0;
@@ -312,6 +321,10 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
             for (int j = 0; j < LEG_RP; ++j) {
               T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
               T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
+              if (SQ) {
+                q0 *= q0;
+                q1 *= q1;
+              }
               acc[u].x = fma(q0, GE[j].x, acc[u].x);
               acc[u].y = fma(q0, GE[j].y, acc[u].y);
               acc[u + 1].x = fma(q1, GO[j].x, acc[u + 1].x);
@@ -329,6 +342,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
             for (int j = 0; j < LEG_RP; ++j) {
               T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
               if (lev[j] == 0) {
+                if (SQ) q0 *= q0;
                 const C g = (u & 1) ? GO[j] : GE[j];
                 acc[u].x = fma(q0, g.x, acc[u].x);
                 acc[u].y = fma(q0, g.y, acc[u].y);
@@ -355,7 +369,8 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
     __syncthreads();
     for (int i = tid; i < nl; i += LEG_NT) {
       const int l = l0 + i;
-      part[offa + (l - m)] = cscale(sacc[i], a.s[offc + (l - m)]);
+      const T sc_ = a.s[offc + (l - m)];
+      part[offa + (l - m)] = cscale(sacc[i], SQ ? sc_ * sc_ : sc_);
     }
   }
 }
@@ -381,6 +396,10 @@ __global__ void leg_finalize_kernel(FinalizeArgs<T> a) {
       y.x = fma(a.dadd[l], x.x, y.x);
       y.y = fma(a.dadd[l], x.y, y.y);
     }
+    if (a.bsub) {
+      const C bb = a.bsub[i];
+      y = mk(bb.x - y.x, (m == 0) ? (T)0 : bb.y - y.y);
+    }
     if (m == 0) y.y = 0;
     if (a.accumulate) y = cadd(y, a.out[i]);
     a.out[i] = y;
@@ -397,8 +416,8 @@ int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st) {
   if (a.L < 0) return CR_OK;
   int nbp, nbe;
   pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
-  if (nbp) leg_synth_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0);
-  if (nbe) leg_synth_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp);
+  if (nbp) { leg_synth_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { leg_synth_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   CR_CHECK_LAUNCH("leg_synth_kernel");
   return CR_OK;
 }
@@ -408,8 +427,8 @@ int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream
   if (a.L < 0) return CR_OK;
   int nbp, nbe;
   pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
-  if (nbp) leg_adjoint_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0);
-  if (nbe) leg_adjoint_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp);
+  if (nbp) { leg_adjoint_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { leg_adjoint_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   CR_CHECK_LAUNCH("leg_adjoint_kernel");
   FinalizeArgs<T> ff = f;
   ff.partial = a.partial;
@@ -417,7 +436,40 @@ int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream
   ff.L = a.L;
   const int64_t nlm = n_lm(a.L);
   int blocks = (int)std::min<int64_t>((nlm + 255) / 256, 152 * 16);
-  leg_finalize_kernel<T><<<blocks, 256, 0, st>>>(ff);
+  { leg_finalize_kernel<T><<<blocks, 256, 0, st>>>(ff); count_launch(); }
+  CR_CHECK_LAUNCH("leg_finalize_kernel");
+  return CR_OK;
+}
+
+// out_lm = sum_k P~_lm(z_k)^2 ringval_k on the observation grid (FP64)
+int launch_leg_diag(cr_plan* P, const double* ringval, double2* out) {
+  const Grid& g = P->obs;
+  LegArgs<double> a;
+  a.ldp = P->lmax + 1;
+  a.L = P->lmax;
+  a.Lc = P->Lcoef;
+  a.c = P->d_c;
+  a.s = P->d_s;
+  a.z = g.d_z;
+  a.seed = g.d_seed;
+  a.lev = g.d_lev;
+  a.ld_seed = g.npairs;
+  a.npairs = g.npairs;
+  a.nring = g.nring;
+  a.npolar = 0;
+  a.ringval = ringval;
+  a.partial = reinterpret_cast<double2*>(P->ws.partial);
+  int nbp, nbe;
+  pair_blocks(0, a.npairs, &nbp, &nbe);
+  { leg_adjoint_kernel<double, false, true><<<dim3(a.L + 1, nbe), LEG_NT, 0, P->stream>>>(a, 0, 0); count_launch(); }
+  CR_CHECK_LAUNCH("leg_adjoint_kernel<SQ>");
+  FinalizeArgs<double> ff;
+  ff.partial = a.partial;
+  ff.nblk = nbe;
+  ff.L = a.L;
+  ff.out = out;
+  const int64_t nlm = n_lm(a.L);
+  { leg_finalize_kernel<double><<<(int)std::min<int64_t>((nlm + 255) / 256, 152 * 16), 256, 0, P->stream>>>(ff); count_launch(); }
   CR_CHECK_LAUNCH("leg_finalize_kernel");
   return CR_OK;
 }

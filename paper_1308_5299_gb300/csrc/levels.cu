@@ -118,78 +118,6 @@ void default_levels(int nside, int lmax, int k, std::vector<LevelSpec>& out, int
 static const int JRLL[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
 static const int JPLL[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
 
-__host__ __device__ static inline int64_t compress_bits(int64_t v) {
-  int64_t out = 0;
-  for (int b = 0; b < 31; ++b) out |= ((v >> (2 * b)) & 1) << b;
-  return out;
-}
-
-__host__ __device__ void nest_xyf(int64_t nside, int64_t ipix, int* ix, int* iy, int* f) {
-  const int64_t npf = nside * nside;
-  *f = (int)(ipix / npf);
-  const int64_t w = ipix % npf;
-  *ix = (int)compress_bits(w);
-  *iy = (int)compress_bits(w >> 1);
-}
-
-__host__ __device__ int64_t xyf_ring(int64_t N, int ix, int iy, int f) {
-  const int jrll[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
-  const int jpll[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
-  const int64_t jr = jrll[f] * N - ix - iy - 1;
-  int64_t nr, s, start;
-  if (jr < N) {
-    nr = jr;
-    s = 1;
-    start = 2 * jr * (jr - 1);
-  } else if (jr > 3 * N) {
-    nr = 4 * N - jr;
-    s = 1;
-    start = 12 * N * N - 2 * nr * (nr + 1);
-  } else {
-    nr = N;
-    s = (jr - N + 1) & 1;
-    start = 2 * N * (N - 1) + (jr - N) * 4 * N;
-  }
-  int64_t j = (nr * jpll[f] + ix - iy - s) / 2;
-  const int64_t M = 4 * nr;
-  j = ((j % M) + M) % M;
-  return start + j;
-}
-
-__host__ __device__ int64_t nest2ring(int64_t nside, int64_t ipix) {
-  int ix, iy, f;
-  nest_xyf(nside, ipix, &ix, &iy, &f);
-  return xyf_ring(nside, ix, iy, f);
-}
-
-// Unit vector of continuous face coordinates (x, y) in [0, N]^2 of face f.
-__host__ __device__ void face_vec(double N, int f, double x, double y, double* v) {
-  const int jrll[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
-  const int jpll[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
-  const double jr = jrll[f] * N - x - y;
-  double z, nr;
-  if (jr < N) {
-    z = 1.0 - jr * jr / (3.0 * N * N);
-    nr = jr;
-  } else if (jr > 3.0 * N) {
-    const double t = 4.0 * N - jr;
-    z = -(1.0 - t * t / (3.0 * N * N));
-    nr = t;
-  } else {
-    z = 4.0 / 3.0 - 2.0 * jr / (3.0 * N);
-    nr = N;
-  }
-  const double phi = nr > 0 ? 0.25 * M_PI * (jpll[f] + (x - y) / nr) : 0.0;
-  double omz;  // 1 - |z| exactly in the polar caps
-  if (jr < N) omz = jr * jr / (3.0 * N * N);
-  else if (jr > 3.0 * N) omz = (4.0 * N - jr) * (4.0 * N - jr) / (3.0 * N * N);
-  else omz = 1.0 - fabs(z);
-  const double st = sqrt(omz * (2.0 - omz));
-  v[0] = st * cos(phi);
-  v[1] = st * sin(phi);
-  v[2] = z;
-}
-
 // Exact integer key of a lattice point (x, y) of face f: its ring coordinate
 // jr = jrll N - x - y and azimuth numerator (jpll nr + x - y) mod 8 nr, which
 // identify the same sphere point seen from every face that contains it.
@@ -327,6 +255,24 @@ __global__ void dot_kernel(const typename Tr<T>::C* a, const typename Tr<T>::C* 
   }
 }
 
+// deterministic pseudo-random FP32 coefficients in [-1, 1) (integer hash of
+// the index), Im(a_l0) = 0: start vectors of the plan-time power iterations
+__global__ void fill_random_kernel(float2* v, int L, uint32_t seed) {
+  const int m = blockIdx.x;
+  const int64_t o = lm_off(L, m);
+  for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+    uint32_t h = (uint32_t)(o + l - m) * 2654435761u ^ seed;
+    h ^= h >> 16;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    h *= 3266489917u;
+    h ^= h >> 16;
+    const float a = (float)(h & 0xffff) / 32768.f - 1.f;
+    const float b = (float)(h >> 16) / 32768.f - 1.f;
+    v[o + l - m] = make_float2(a, m == 0 ? 0.f : b);
+  }
+}
+
 template <typename TI, typename TO>
 __global__ void convert_kernel(const TI* in, TO* out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -342,37 +288,69 @@ __global__ void add_convert_kernel(TX* x, const TY* y, int64_t n) {
 
 template <typename T>
 int launch_restrict(const void* in, int Lh, void* out, int LH, const T* ratio, cudaStream_t st) {
-  restrict_kernel<T><<<LH + 1, 128, 0, st>>>((const typename Tr<T>::C*)in, Lh, (typename Tr<T>::C*)out, LH, ratio);
+  { restrict_kernel<T><<<LH + 1, 128, 0, st>>>((const typename Tr<T>::C*)in, Lh, (typename Tr<T>::C*)out, LH, ratio); count_launch(); }
   CR_CHECK_LAUNCH("restrict_kernel");
   return CR_OK;
 }
 template <typename T>
 int launch_prolong_add(void* x, int Lh, const void* c, int LH, const T* ratio, cudaStream_t st) {
-  prolong_add_kernel<T><<<LH + 1, 128, 0, st>>>((typename Tr<T>::C*)x, Lh, (const typename Tr<T>::C*)c, LH, ratio);
+  { prolong_add_kernel<T><<<LH + 1, 128, 0, st>>>((typename Tr<T>::C*)x, Lh, (const typename Tr<T>::C*)c, LH, ratio); count_launch(); }
   CR_CHECK_LAUNCH("prolong_add_kernel");
   return CR_OK;
 }
 template <typename T>
 int launch_diag_axpy(void* x, const void* r, const T* d, int64_t n, cudaStream_t st) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-  diag_axpy_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>((typename Tr<T>::C*)x, (const typename Tr<T>::C*)r, d, n);
+  { diag_axpy_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>((typename Tr<T>::C*)x, (const typename Tr<T>::C*)r, d, n); count_launch(); }
   CR_CHECK_LAUNCH("diag_axpy_kernel");
   return CR_OK;
 }
 template <typename T>
 int launch_dot(const void* a, const void* b, const double* wl, int L, double* out, cudaStream_t st) {
   CR_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
-  dot_kernel<T><<<L + 1, 256, 0, st>>>((const typename Tr<T>::C*)a, (const typename Tr<T>::C*)b, wl, L, out);
+  { dot_kernel<T><<<L + 1, 256, 0, st>>>((const typename Tr<T>::C*)a, (const typename Tr<T>::C*)b, wl, L, out); count_launch(); }
   CR_CHECK_LAUNCH("dot_kernel");
   return CR_OK;
 }
+__global__ void scale_copy_kernel(const float2* in, float2* out, float s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_float2(in[i].x * s, in[i].y * s);
+}
+
+int launch_scale_copy(const void* in, void* out, float s, int64_t n, cudaStream_t st) {
+  scale_copy_kernel<<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>((const float2*)in,
+                                                                                          (float2*)out, s, n);
+  CR_CHECK_LAUNCH("scale_copy_kernel");
+  return CR_OK;
+}
+
+// y = a x + b y on interleaved complex FP64 vectors of n complex elements
+__global__ void axpby_kernel(double2* y, double a, const double2* x, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 u = x[i], v = y[i];
+    y[i] = make_double2(fma(a, u.x, b * v.x), fma(a, u.y, b * v.y));
+  }
+}
+
+int launch_axpby(void* y, double a, const void* x, double b, int64_t n, cudaStream_t st) {
+  { axpby_kernel<<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>((double2*)y, a, (const double2*)x, b, n); count_launch(); }
+  CR_CHECK_LAUNCH("axpby_kernel");
+  return CR_OK;
+}
+
+int launch_fill_random(void* v, int L, uint32_t seed, cudaStream_t st) {
+  fill_random_kernel<<<L + 1, 128, 0, st>>>((float2*)v, L, seed);
+  CR_CHECK_LAUNCH("fill_random_kernel");
+  return CR_OK;
+}
+
 int launch_convert_d2f(const double* in, float* out, int64_t n, cudaStream_t st) {
-  convert_kernel<double, float><<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>(in, out, n);
+  { convert_kernel<double, float><<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>(in, out, n); count_launch(); }
   CR_CHECK_LAUNCH("convert_kernel");
   return CR_OK;
 }
 int launch_add_f2d(double* x, const float* y, int64_t n, cudaStream_t st) {
-  add_convert_kernel<double, float><<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>(x, y, n);
+  { add_convert_kernel<double, float><<<(int)std::min<int64_t>((n + 255) / 256 + 1, 152 * 8), 256, 0, st>>>(x, y, n); count_launch(); }
   CR_CHECK_LAUNCH("add_convert_kernel");
   return CR_OK;
 }

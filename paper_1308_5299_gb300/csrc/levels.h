@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "healpix.cuh"
 #include "hier.h"
 
 namespace cr {
@@ -17,26 +18,31 @@ std::vector<double> gauss_filter(int lmax, int nside_h);
 void default_levels(int nside, int lmax, int k, std::vector<LevelSpec>& out, int* lmax_dense);
 void tile_pattern(int nside_t, BlockPattern& P);
 
-__host__ __device__ void nest_xyf(int64_t nside, int64_t ipix, int* ix, int* iy, int* f);
-__host__ __device__ int64_t xyf_ring(int64_t N, int ix, int iy, int f);
-__host__ __device__ int64_t nest2ring(int64_t nside, int64_t ipix);
-__host__ __device__ void face_vec(double N, int f, double x, double y, double* v);
 
 template <typename T> int launch_restrict(const void* in, int Lh, void* out, int LH, const T* ratio, cudaStream_t st);
 template <typename T> int launch_prolong_add(void* x, int Lh, const void* c, int LH, const T* ratio, cudaStream_t st);
 template <typename T> int launch_diag_axpy(void* x, const void* r, const T* d, int64_t n, cudaStream_t st);
+int launch_fill_random(void* v, int L, uint32_t seed, cudaStream_t st);
+int launch_axpby(void* y, double a, const void* x, double b, int64_t n, cudaStream_t st);
+int launch_scale_copy(const void* in, void* out, float s, int64_t n, cudaStream_t st);
 template <typename T> int launch_dot(const void* a, const void* b, const double* wl, int L, double* out, cudaStream_t st);
 int launch_convert_d2f(const double* in, float* out, int64_t n, cudaStream_t st);
 int launch_add_f2d(double* x, const float* y, int64_t n, cudaStream_t st);
 
 // smoother.cu
 int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisections, double fixed_alpha);
+int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok);
 template <typename T> int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out);
 void free_smoother(PixLevel& lev);
 
 // dense.cu
 int build_bottom(cr_plan* P, Hierarchy& Hh);
 template <typename T> int bottom_solve(cr_plan* P, Hierarchy& Hh, const void* b, void* x);
+int bottom_matrix(cr_plan* P, double* host, int* nd);
 int build_top_diag(cr_plan* P, Hierarchy& Hh, const std::vector<double>& f1);
+
+// solver.cu
+int build_hierarchy(cr_plan* P, const cr_params* p);
+void free_hierarchy(cr_plan* P);
 
 }  // namespace cr

@@ -173,9 +173,9 @@ extern "C" int cr_sht_synth_noalloc(int nside, int lmax, const void* alm, void* 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int npairs = 2 * nside;
   dim3 g1(lmax + 1, (npairs + 127) / 128);
-  noalloc_legendre_kernel<<<g1, 128, 0, st>>>((const double2*)alm, nside, lmax, scratch);
+  { noalloc_legendre_kernel<<<g1, 128, 0, st>>>((const double2*)alm, nside, lmax, scratch); count_launch(); }
   CR_CHECK_LAUNCH("noalloc_legendre_kernel");
-  noalloc_ring_kernel<<<nring, 256, 0, st>>>(scratch, nside, lmax, (double*)map);
+  { noalloc_ring_kernel<<<nring, 256, 0, st>>>(scratch, nside, lmax, (double*)map); count_launch(); }
   CR_CHECK_LAUNCH("noalloc_ring_kernel");
   return CR_OK;
 }

@@ -1,4 +1,5 @@
 // Plan construction and the C ABI entry points for transforms and A.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -6,11 +7,16 @@
 #include <vector>
 
 #include "common.cuh"
+#include "hier.h"
 #include "kernels.h"
+#include "levels.h"
 
 namespace cr {
 
 static thread_local std::string g_last_error;
+static std::atomic<long> g_launches{0};
+void count_launch(long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int code, const std::string& msg) {
@@ -38,8 +44,9 @@ void Timing::flush() {
     float ms = 0.f;
     if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       auto& v = acc[r.name];
-      v.first += ms;
-      v.second += 1;
+      v.ms += ms;
+      v.n += 1;
+      v.work += r.work;
     }
     pool.push_back(r.a);
     pool.push_back(r.b);
@@ -55,9 +62,13 @@ Timing::~Timing() {
   for (auto e : pool) cudaEventDestroy(e);
 }
 
-TimerScope::TimerScope(Timing& t, cudaStream_t st, const char* name) : t_(&t), st_(st), idx_(-1) {
+TimerScope::TimerScope(Timing& t, cudaStream_t st, const char* name, double work)
+    : TimerScope(t, st, std::string(name), work) {}
+
+TimerScope::TimerScope(Timing& t, cudaStream_t st, const std::string& name, double work)
+    : t_(&t), st_(st), idx_(-1) {
   if (!t.enabled) return;
-  Timing::Rec r{name, t.get(), t.get()};
+  Timing::Rec r{name, t.get(), t.get(), work};
   cudaEventRecord(r.a, st);
   t.pending.push_back(r);
   idx_ = (int)t.pending.size() - 1;
@@ -71,7 +82,7 @@ TimerScope::~TimerScope() {
 // pixels at z = 1 - i^2/(3N^2), phi = pi (2j + 1) / (4i); equatorial ring
 // N <= i <= 3N has 4N pixels at z = 4/3 - 2i/(3N), phi = pi (2j + s) / (4N),
 // s = (i - N + 1) mod 2; the south cap mirrors the north.
-static void healpix_rings(Grid& g, int N) {
+void healpix_rings(Grid& g, int N) {
   g.kind = CR_GRID_HEALPIX;
   g.nside = N;
   g.nring = 4 * N - 1;
@@ -178,7 +189,7 @@ static void gl_rings(Grid& g, int ntheta, int nphi, std::vector<double>* weights
   g.npairs = (g.nring + 1) / 2;
 }
 
-static int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
+int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
   std::vector<float> z32(g.z.begin(), g.z.end());
   // FP32 polar form for north rings with z > 1/2 (rings are ordered north to
   // south, so these are the first pairs); 1 - z is exact in FP64 there.
@@ -202,7 +213,7 @@ static int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
   return build_seeds(g, Lseed, st);
 }
 
-static void grid_free(Grid& g) {
+void grid_free(Grid& g) {
   void* ptrs[] = {g.d_z, g.d_z32, g.d_w32, g.d_sth, g.d_fft, g.d_tab, g.d_tab32, g.d_vhat, g.d_vhat32,
                   g.d_tw, g.d_tw32, g.d_seed, g.d_lev, g.d_seed32, g.d_lev32};
   for (void* p : ptrs)
@@ -252,7 +263,7 @@ static int build_coef(cr_plan* P, int Lc) {
   return CR_OK;
 }
 
-static int ensure_workspace(cr_plan* P, const Grid& g, int L) {
+int ensure_workspace(cr_plan* P, const Grid& g, int L) {
   const int64_t phase = (int64_t)g.nring * (L + 1) * (int64_t)sizeof(double2);
   const int64_t partial = (int64_t)leg_partial_blocks(g.npairs) * n_lm(L) * (int64_t)sizeof(double2);
   if (phase > P->ws.phase_bytes) {
@@ -271,6 +282,7 @@ static int ensure_workspace(cr_plan* P, const Grid& g, int L) {
 }
 
 static void plan_free(cr_plan* P) {
+  free_hierarchy(P);
   grid_free(P->obs);
   for (Grid* g : P->level_grids) {
     grid_free(*g);
@@ -342,19 +354,26 @@ static RingArgs<T> ring_args(cr_plan* P, const Grid& g, int L) {
 }
 
 template <typename T>
+static const char* ptag() {
+  return sizeof(T) == 8 ? "_f64" : "_f32";
+}
+// algorithmic flops of one Legendre stage on grid g at band limit L
+static double leg_work(const Grid& g, int L) { return 8.0 * g.npairs * (double)n_lm(L); }
+
+template <typename T>
 int do_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, const T* dl) {
   LegArgs<T> a = leg_args<T>(P, g, L);
   a.alm = reinterpret_cast<const typename Tr<T>::C*>(alm);
   a.dl = dl;
   int rc;
   {
-    TimerScope ts(P->timing, P->stream, "legendre_synth");
+    TimerScope ts(P->timing, P->stream, std::string("legendre_synth") + ptag<T>(), leg_work(g, L));
     rc = launch_leg_synth<T>(a, P->stream);
   }
   if (rc) return rc;
   RingArgs<T> r = ring_args<T>(P, g, L);
   r.map_out = reinterpret_cast<T*>(map);
-  TimerScope ts(P->timing, P->stream, "ring_fft_synth");
+  TimerScope ts(P->timing, P->stream, std::string("ring_fft_synth") + ptag<T>());
   return launch_ring_fft<T>(r, 0, P->stream);
 }
 
@@ -365,7 +384,7 @@ int do_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, con
   r.map_in = reinterpret_cast<const T*>(map);
   int rc;
   {
-    TimerScope ts(P->timing, P->stream, "ring_fft_adjoint");
+    TimerScope ts(P->timing, P->stream, std::string("ring_fft_adjoint") + ptag<T>());
     rc = launch_ring_fft<T>(r, 1, P->stream);
   }
   if (rc) return rc;
@@ -376,20 +395,21 @@ int do_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, con
   f.xadd = reinterpret_cast<const typename Tr<T>::C*>(xadd);
   f.accumulate = accumulate;
   f.out = reinterpret_cast<typename Tr<T>::C*>(alm);
-  TimerScope ts(P->timing, P->stream, "legendre_adjoint");
+  TimerScope ts(P->timing, P->stream, std::string("legendre_adjoint") + ptag<T>(), leg_work(g, L));
   return launch_leg_adjoint<T>(a, f, P->stream);
 }
 
-// y = dl_out Y^T diag(pix) Y (dl_in x) + dadd x  on grid g at band limit L.
+// y = dl_out Y^T diag(pix) Y (dl_in x) + dadd x  on grid g at band limit L
+// (or y = bsub - that, when bsub is given).
 template <typename T>
 int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const T* dl_in, const T* pix,
-                const T* dl_out, const T* dadd, T* map_copy) {
+                const T* dl_out, const T* dadd, T* map_copy, const void* bsub) {
   LegArgs<T> a = leg_args<T>(P, g, L);
   a.alm = reinterpret_cast<const typename Tr<T>::C*>(x);
   a.dl = dl_in;
   int rc;
   {
-    TimerScope ts(P->timing, P->stream, "legendre_synth");
+    TimerScope ts(P->timing, P->stream, std::string("legendre_synth") + ptag<T>(), leg_work(g, L));
     rc = launch_leg_synth<T>(a, P->stream);
   }
   if (rc) return rc;
@@ -397,7 +417,7 @@ int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const 
   r.pixdiag = pix;
   r.map_out = map_copy;
   {
-    TimerScope ts(P->timing, P->stream, "ring_fft_apply");
+    TimerScope ts(P->timing, P->stream, std::string("ring_fft_apply") + ptag<T>());
     rc = launch_ring_fft<T>(r, 2, P->stream);
   }
   if (rc) return rc;
@@ -405,10 +425,22 @@ int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const 
   f.dl_out = dl_out;
   f.dadd = dadd;
   f.xadd = reinterpret_cast<const typename Tr<T>::C*>(x);
+  f.bsub = reinterpret_cast<const typename Tr<T>::C*>(bsub);
   f.out = reinterpret_cast<typename Tr<T>::C*>(y);
-  TimerScope ts(P->timing, P->stream, "legendre_adjoint");
+  TimerScope ts(P->timing, P->stream, std::string("legendre_adjoint") + ptag<T>(), leg_work(g, L));
   return launch_leg_adjoint<T>(a, f, P->stream);
 }
+
+template int do_synth<double>(cr_plan*, const Grid&, int, const void*, void*, const double*);
+template int do_synth<float>(cr_plan*, const Grid&, int, const void*, void*, const float*);
+template int do_adjoint<double>(cr_plan*, const Grid&, int, const void*, void*, const double*, const double*,
+                                const void*, int);
+template int do_adjoint<float>(cr_plan*, const Grid&, int, const void*, void*, const float*, const float*,
+                               const void*, int);
+template int do_sandwich<double>(cr_plan*, const Grid&, int, const void*, void*, const double*, const double*,
+                                 const double*, const double*, double*, const void*);
+template int do_sandwich<float>(cr_plan*, const Grid&, int, const void*, void*, const float*, const float*,
+                                const float*, const float*, float*, const void*);
 
 static const Grid* grid_of(cr_plan* P, int grid, int* L) {
   if (grid == CR_OBS) {
@@ -511,11 +543,16 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
       }
       if (!rc) {
         ninv32_kernel<<<1024, 256, 0, P->stream>>>(P->d_ninv, P->d_ninv32, npix);
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "ninv32");
       }
       if (!rc) P->has_op = true;
+    }
+    if (!rc && p->nlevels != 0) {
+      if (p->grid_kind != CR_GRID_HEALPIX) rc = fail(CR_EINVAL, "cr_plan_create: levels need a HEALPix grid");
+      else rc = build_hierarchy(P, p);
     }
   }
   if (rc) {
@@ -594,7 +631,7 @@ int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs
 int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int dtype) {
   if (!plan) return fail(CR_EINVAL, "cr_apply_A: null plan");
   if (!plan->has_op) return fail(CR_ESTATE, "cr_apply_A: plan was created without C_l");
-  if (level != 0) return fail(CR_EINVAL, "cr_apply_A: level out of range");
+  if (level != 0) return cr_level_apply(plan, level, x, y, dtype);
   if (nrhs < 0 || (dtype != CR_F64 && dtype != CR_F32)) return fail(CR_EINVAL, "cr_apply_A: nrhs/dtype");
   if (nrhs == 0) return CR_OK;
   if (check_ptr(x, dtype) || check_ptr(y, dtype)) return CR_EINVAL;
@@ -605,9 +642,10 @@ int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int d
     const char* xr = (const char*)x + (size_t)r * n_lm(L) * 2 * es;
     char* yr = (char*)y + (size_t)r * n_lm(L) * 2 * es;
     int rc = dtype == CR_F64
-                 ? do_sandwich<double>(plan, plan->obs, L, xr, yr, plan->d_bl, plan->d_ninv, plan->d_bl, plan->d_sinv, nullptr)
+                 ? do_sandwich<double>(plan, plan->obs, L, xr, yr, plan->d_bl, plan->d_ninv, plan->d_bl, plan->d_sinv,
+                                       nullptr, nullptr)
                  : do_sandwich<float>(plan, plan->obs, L, xr, yr, plan->d_bl32, plan->d_ninv32, plan->d_bl32,
-                                      plan->d_sinv32, nullptr);
+                                      plan->d_sinv32, nullptr, nullptr);
     if (rc) return rc;
   }
   return CR_OK;
@@ -621,7 +659,8 @@ int cr_plan_set_timing(cr_plan* plan, int enable) {
   return CR_OK;
 }
 
-int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, int* count) {
+int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, double* work,
+                   int* count) {
   if (!plan) return fail(CR_EINVAL, "cr_plan_timing: null plan");
   plan->timing.flush();
   if (count) *count = (int)plan->timing.acc.size();
@@ -633,9 +672,12 @@ int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, l
     std::strncpy(name, it->first.c_str(), name_cap - 1);
     name[name_cap - 1] = 0;
   }
-  if (ms) *ms = it->second.first;
-  if (launches) *launches = it->second.second;
+  if (ms) *ms = it->second.ms;
+  if (launches) *launches = it->second.n;
+  if (work) *work = it->second.work;
   return CR_OK;
 }
+
+long cr_launch_count(void) { return launch_count(); }
 
 }  // extern "C"

@@ -69,10 +69,16 @@ struct Timing {
   struct Rec {
     std::string name;
     cudaEvent_t a, b;
+    double work;
+  };
+  struct Acc {
+    double ms = 0.0;
+    long n = 0;
+    double work = 0.0;  // algorithmic flops (or bytes) of the recorded launches
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
-  std::map<std::string, std::pair<double, long>> acc;  // name -> (ms, launches)
+  std::map<std::string, Acc> acc;
   cudaEvent_t get();
   void flush();
   ~Timing();
@@ -80,7 +86,8 @@ struct Timing {
 
 class TimerScope {
  public:
-  TimerScope(Timing& t, cudaStream_t st, const char* name);
+  TimerScope(Timing& t, cudaStream_t st, const char* name, double work = 0.0);
+  TimerScope(Timing& t, cudaStream_t st, const std::string& name, double work = 0.0);
   ~TimerScope();
 
  private:
@@ -95,6 +102,10 @@ struct Level {
 };
 
 }  // namespace cr
+
+namespace cr {
+struct Hierarchy;
+}
 
 struct cr_plan {
   cr_params p{};
@@ -120,5 +131,7 @@ struct cr_plan {
   float* d_ninv32 = nullptr;
   cr::Workspace ws;
   cr::Timing timing;
+  cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)
+  void* hier_tile_work = nullptr;     // FP32 tile-ordered smoother work vector
   std::vector<double> h_cl, h_bl;
 };

@@ -208,15 +208,15 @@ int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st) {
   switch (mode) {
     case 0:
       CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      ring_fft_kernel<T, 0><<<a.nring, RF_NT, smem, st>>>(a);
+      { ring_fft_kernel<T, 0><<<a.nring, RF_NT, smem, st>>>(a); count_launch(); }
       break;
     case 1:
       CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      ring_fft_kernel<T, 1><<<a.nring, RF_NT, smem, st>>>(a);
+      { ring_fft_kernel<T, 1><<<a.nring, RF_NT, smem, st>>>(a); count_launch(); }
       break;
     default:
       CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      ring_fft_kernel<T, 2><<<a.nring, RF_NT, smem, st>>>(a);
+      { ring_fft_kernel<T, 2><<<a.nring, RF_NT, smem, st>>>(a); count_launch(); }
       break;
   }
   CR_CHECK_LAUNCH("ring_fft_kernel");

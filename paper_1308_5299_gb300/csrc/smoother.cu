@@ -1,0 +1,694 @@
+// Pixel-domain error smoother of one level (Section 3.5): explicit
+// A_hat_h = D_hat_h + B_hat_h^T N^-1 B_hat_h inside the tile pattern, its
+// zero-fill-in incomplete Cholesky factor with the ridge search, and the
+// triangular solves that apply M_hat_h = (L L^T)^-1.  All in FP32 (the paper
+// runs its smoothers in single precision).
+//
+// Tiles are the pixels of the HEALPix grid at Nside_h / k (k = 8, so a tile
+// holds 64 NESTED level pixels); a tile couples to the tiles it shares a
+// vertex with.  Tiles are eliminated colour by colour (a greedy colouring of
+// that neighbour graph), so every colour is a batch of independent tiles:
+// one CTA per tile, one launch per colour.
+//
+// D_hat and B_hat entries come from the addition theorem (Eq.
+// addition-theorem) g(theta) = sum_l (2l+1)/(4 pi) g_l P_l(cos theta),
+// tabulated once per level in FP64 against the chord d = 2 sin(theta/2) and
+// interpolated with 4-point Lagrange polynomials (g is even in d).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <iterator>
+#include <vector>
+
+#include "common.cuh"
+#include "hier.h"
+#include "kernels.h"
+#include "levels.h"
+
+namespace cr {
+
+constexpr int TK = 64;        // pixels per tile (k = 8)
+constexpr int SM_NT = 256;    // threads of the assembly / factorisation kernels
+
+// ---------------------------------------------------------------------------
+// coupling tables
+
+__global__ void coupling_table_kernel(const double* gl, int L, double h, int n, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = i * h;
+  const double x = 1.0 - 0.5 * d * d;
+  double p0 = 1.0, p1 = x;
+  double s = gl[0] * p0;
+  if (L >= 1) s += 3.0 * gl[1] * p1;
+  for (int l = 2; l <= L; ++l) {
+    const double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
+    p0 = p1;
+    p1 = p2;
+    s += (2.0 * l + 1.0) * gl[l] * p1;
+  }
+  out[i] = (float)(s / (4.0 * M_PI));
+}
+
+struct Table {
+  const float* g;
+  int n;
+  float inv_h;
+};
+
+__device__ __forceinline__ float table_eval(const Table& t, float d, int* overflow) {
+  const float u = d * t.inv_h;
+  int i = (int)u;
+  const float f = u - (float)i;
+  if (i + 2 >= t.n) {
+    *overflow = 1;
+    i = t.n - 3;
+  }
+  const float gm = t.g[i == 0 ? 1 : i - 1];  // g(-h) = g(h)
+  const float g0 = t.g[i], g1 = t.g[i + 1], g2 = t.g[i + 2];
+  const float wm = -f * (f - 1.f) * (f - 2.f) * (1.f / 6.f);
+  const float w0 = (f + 1.f) * (f - 1.f) * (f - 2.f) * 0.5f;
+  const float w1 = -(f + 1.f) * f * (f - 2.f) * 0.5f;
+  const float w2 = (f + 1.f) * f * (f - 1.f) * (1.f / 6.f);
+  return wm * gm + w0 * g0 + w1 * g1 + w2 * g2;
+}
+
+// ---------------------------------------------------------------------------
+// A_hat assembly: one CTA per stored block (p, q), q <= p.
+
+struct AssembleArgs {
+  int nside_h, nside_obs, ratio2;     // ratio2 = obs pixels per tile
+  const int* order;                   // position -> nested tile
+  const int* blk_p;
+  const int* blk_q;
+  const int64_t* cobs_ptr;            // per block: common obs tiles (nested)
+  const int* cobs;
+  const double* ninv;                 // obs grid, RING order
+  Table gD, gB;
+  float* A;
+  int* overflow;
+};
+
+__device__ __forceinline__ void tile_pixel_vec(int64_t nside, int64_t nest, double* v) {
+  int ix, iy, f;
+  nest_xyf(nside, nest, &ix, &iy, &f);
+  face_vec((double)nside, f, ix + 0.5, iy + 0.5, v);
+}
+
+__global__ void __launch_bounds__(SM_NT) assemble_kernel(AssembleArgs a) {
+  const int b = blockIdx.x;
+  const int p = a.blk_p[b], q = a.blk_q[b];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  __shared__ double ref[3];
+  __shared__ float3 vp[TK], vq[TK], vo[TK];
+  __shared__ float No[TK];
+  __shared__ __align__(16) float Bi[TK][TK + 4];
+  __shared__ __align__(16) float Bj[TK][TK + 4];
+  __shared__ int ovf;
+  if (tid == 0) {
+    double v[3];
+    tile_pixel_vec(a.nside_h, (int64_t)a.order[p] * TK, v);
+    ref[0] = v[0];
+    ref[1] = v[1];
+    ref[2] = v[2];
+    ovf = 0;
+  }
+  __syncthreads();
+  if (tid < 2 * TK) {
+    const int t = tid & (TK - 1);
+    const int tile = (tid < TK) ? a.order[p] : a.order[q];
+    double v[3];
+    tile_pixel_vec(a.nside_h, (int64_t)tile * TK + t, v);
+    const float3 o = make_float3((float)(v[0] - ref[0]), (float)(v[1] - ref[1]), (float)(v[2] - ref[2]));
+    if (tid < TK) vp[t] = o;
+    else vq[t] = o;
+  }
+  __syncthreads();
+  int myovf = 0;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float3 u = vp[4 * ty + i], w = vq[4 * tx + j];
+      const float dx = u.x - w.x, dy = u.y - w.y, dz = u.z - w.z;
+      acc[i][j] = table_eval(a.gD, sqrtf(dx * dx + dy * dy + dz * dz), &myovf);
+    }
+  for (int64_t c = a.cobs_ptr[b]; c < a.cobs_ptr[b + 1]; ++c) {
+    const int64_t base = (int64_t)a.cobs[c] * a.ratio2;
+    for (int c0 = 0; c0 < a.ratio2; c0 += TK) {
+      __syncthreads();
+      if (tid < TK) {
+        const int64_t nest = base + c0 + tid;
+        double v[3];
+        tile_pixel_vec(a.nside_obs, nest, v);
+        vo[tid] = make_float3((float)(v[0] - ref[0]), (float)(v[1] - ref[1]), (float)(v[2] - ref[2]));
+        No[tid] = (float)a.ninv[nest2ring(a.nside_obs, nest)];
+      }
+      __syncthreads();
+      if (!__syncthreads_or(tid < TK && No[tid] != 0.f)) continue;
+      for (int e = tid; e < TK * 2 * TK; e += SM_NT) {
+        const int o = e >> 7, cc = e & 127;
+        const float3 u = vo[o];
+        const float3 w = (cc < TK) ? vp[cc] : vq[cc - TK];
+        const float dx = u.x - w.x, dy = u.y - w.y, dz = u.z - w.z;
+        const float g = table_eval(a.gB, sqrtf(dx * dx + dy * dy + dz * dz), &myovf);
+        if (cc < TK) Bi[o][cc] = No[o] * g;
+        else Bj[o][cc - TK] = g;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int o = 0; o < TK; ++o) {
+        const float4 x = *reinterpret_cast<const float4*>(&Bi[o][4 * ty]);
+        const float4 y = *reinterpret_cast<const float4*>(&Bj[o][4 * tx]);
+        const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], ya[j], acc[i][j]);
+      }
+    }
+  }
+  float* out = a.A + (int64_t)b * TK * TK;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[(4 * tx + j) * TK + 4 * ty + i] = acc[i][j];  // column-major
+  if (myovf) atomicOr(a.overflow, 1);
+}
+
+// symmetrise the diagonal blocks (A_pp = (A_pp + A_pp^T) / 2)
+__global__ void symmetrise_diag_kernel(float* A, const int64_t* diag_blk) {
+  float* B = A + diag_blk[blockIdx.x] * TK * TK;
+  for (int e = threadIdx.x; e < TK * TK; e += blockDim.x) {
+    const int i = e % TK, j = e / TK;
+    if (i > j) {
+      const float s = 0.5f * (B[j * TK + i] + B[i * TK + j]);
+      B[j * TK + i] = s;
+      B[i * TK + j] = s;
+    }
+  }
+}
+
+__global__ void absmax_kernel(const float* A, int64_t n, unsigned int* out) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(A[i]));
+  for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// ---------------------------------------------------------------------------
+// block ICC(0), one colour per launch, one CTA per tile
+
+struct IccArgs {
+  const float* A;
+  float* L;
+  const int64_t* upd_ptr;
+  const int64_t* tgt_blk;
+  const int* tgt_u;
+  const int64_t* tgt_ptr;
+  const int64_t* pair_a;
+  const int64_t* pair_b;
+  float alpha;
+  int* fail;
+};
+
+// S -= X Y^T for column-major 64x64 blocks X, Y in global memory, staged
+// through shared memory.
+__device__ void sub_xyT(float (*S)[TK + 1], const float* X, const float* Y, float (*sx)[TK + 1], float (*sy)[TK + 1]) {
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int e = tid; e < TK * TK; e += SM_NT) {
+    const int i = e % TK, k = e / TK;
+    sx[i][k] = X[e];
+    sy[i][k] = Y[e];
+  }
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;
+  float acc[4][4] = {};
+  for (int k = 0; k < TK; ++k) {
+    float xa[4], ya[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      xa[i] = sx[4 * ty + i][k];
+      ya[i] = sy[4 * tx + i][k];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], ya[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) S[4 * ty + i][4 * tx + j] -= acc[i][j];
+}
+
+__global__ void __launch_bounds__(SM_NT) icc_colour_kernel(IccArgs a, int p0) {
+  const int p = p0 + blockIdx.x;
+  extern __shared__ __align__(16) float sm[];
+  float(*S)[TK + 1] = reinterpret_cast<float(*)[TK + 1]>(sm);
+  float(*Li)[TK + 1] = reinterpret_cast<float(*)[TK + 1]>(sm + TK * (TK + 1));
+  float(*sx)[TK + 1] = reinterpret_cast<float(*)[TK + 1]>(sm + 2 * TK * (TK + 1));
+  float(*sy)[TK + 1] = reinterpret_cast<float(*)[TK + 1]>(sm + 3 * TK * (TK + 1));
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int64_t t = a.upd_ptr[p]; t < a.upd_ptr[p + 1]; ++t) {
+    const int u = a.tgt_u[t];
+    const float* Ab = a.A + a.tgt_blk[t] * TK * TK;
+    __syncthreads();
+    for (int e = tid; e < TK * TK; e += SM_NT) {
+      const int i = e % TK, j = e / TK;
+      S[i][j] = Ab[e] + ((u == p && i == j) ? a.alpha : 0.f);
+    }
+    for (int64_t c = a.tgt_ptr[t]; c < a.tgt_ptr[t + 1]; ++c)
+      sub_xyT(S, a.L + a.pair_a[c] * TK * TK, a.L + a.pair_b[c] * TK * TK, sx, sy);
+    __syncthreads();
+    float* Lb = a.L + a.tgt_blk[t] * TK * TK;
+    if (u == p) {
+      // Cholesky of S (lower), right-looking
+      for (int j = 0; j < TK; ++j) {
+        if (tid == 0) {
+          const float d = S[j][j];
+          if (!(d > 0.f) || !isfinite(d)) bad = 1;
+          S[j][j] = sqrtf(fmaxf(d, 1e-30f));
+        }
+        __syncthreads();
+        const float djj = S[j][j];
+        for (int i = j + 1 + tid; i < TK; i += SM_NT) S[i][j] /= djj;
+        __syncthreads();
+        const int m = TK - j - 1;
+        for (int e = tid; e < m * m; e += SM_NT) {
+          const int i = j + 1 + e % m, k = j + 1 + e / m;
+          if (k <= i) S[i][k] -= S[i][j] * S[k][j];
+        }
+        __syncthreads();
+      }
+      // inverse of the lower factor, one column per thread
+      if (tid < TK) {
+        const int c = tid;
+        for (int i = 0; i < TK; ++i) {
+          float s = (i == c) ? 1.f : 0.f;
+          if (i > c)
+            for (int k = c; k < i; ++k) s -= S[i][k] * Li[k][c];
+          Li[i][c] = (i >= c) ? s / S[i][i] : 0.f;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < TK * TK; e += SM_NT) {
+        const int i = e % TK, j = e / TK;
+        Lb[e] = Li[i][j];  // diagonal block stores inv(L_pp)
+      }
+    } else {
+      // L_up = S L_pp^-T = S Li^T
+      __syncthreads();
+      const int ty = tid >> 4, tx = tid & 15;
+      float acc[4][4] = {};
+      for (int k = 0; k < TK; ++k) {
+        float xa[4], ya[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          xa[i] = S[4 * ty + i][k];
+          ya[i] = Li[4 * tx + i][k];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], ya[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Lb[(4 * tx + j) * TK + 4 * ty + i] = acc[i][j];
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && bad) atomicOr(a.fail, 1);
+}
+
+// ---------------------------------------------------------------------------
+// triangular solves.  y is the tile-ordered work vector (FP32).
+
+template <typename T>
+__global__ void __launch_bounds__(TK) fwd_colour_kernel(const float* L, const int64_t* row_ptr, const int* row_col,
+                                                        const int* perm, const T* map_in, float* y, int p0) {
+  const int p = p0 + blockIdx.x;
+  const int i = threadIdx.x;
+  __shared__ float ys[TK], ts[TK];
+  float t = (float)map_in[perm[(int64_t)p * TK + i]];
+  const int64_t b0 = row_ptr[p], b1 = row_ptr[p + 1] - 1;  // last block is the diagonal
+  for (int64_t b = b0; b < b1; ++b) {
+    const int q = row_col[b];
+    __syncthreads();
+    ys[i] = y[(int64_t)q * TK + i];
+    __syncthreads();
+    const float* B = L + b * TK * TK;
+    float s = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < TK; ++j) s = fmaf(B[j * TK + i], ys[j], s);
+    t -= s;
+  }
+  ts[i] = t;
+  __syncthreads();
+  const float* D = L + b1 * TK * TK;
+  float s = 0.f;
+#pragma unroll 8
+  for (int j = 0; j < TK; ++j) s = fmaf(D[j * TK + i], ts[j], s);
+  y[(int64_t)p * TK + i] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TK) bwd_colour_kernel(const float* L, const int64_t* row_ptr, const int64_t* col_ptr,
+                                                        const int* col_row, const int64_t* col_blk, const int* perm,
+                                                        float* y, T* map_out, int p0) {
+  const int p = p0 + blockIdx.x;
+  const int i = threadIdx.x;
+  __shared__ float xs[TK], ts[TK];
+  __shared__ float Bs[TK][TK + 1];
+  float t = y[(int64_t)p * TK + i];
+  for (int64_t c = col_ptr[p]; c < col_ptr[p + 1]; ++c) {
+    const int u = col_row[c];
+    const float* B = L + col_blk[c] * TK * TK;
+    __syncthreads();
+    xs[i] = y[(int64_t)u * TK + i];
+    for (int j = 0; j < TK; ++j) Bs[j][i] = B[j * TK + i];  // Bs[col][row]
+    __syncthreads();
+    float s = 0.f;
+#pragma unroll 8
+    for (int r = 0; r < TK; ++r) s = fmaf(Bs[i][r], xs[r], s);  // (B^T x)_i = sum_r B[r][i] x_r
+    t -= s;
+  }
+  const int64_t bd = row_ptr[p + 1] - 1;
+  const float* D = L + bd * TK * TK;
+  __syncthreads();
+  ts[i] = t;
+  for (int j = 0; j < TK; ++j) Bs[j][i] = D[j * TK + i];
+  __syncthreads();
+  float s = 0.f;
+#pragma unroll 8
+  for (int r = 0; r < TK; ++r) s = fmaf(Bs[i][r], ts[r], s);
+  y[(int64_t)p * TK + i] = s;
+  map_out[perm[(int64_t)p * TK + i]] = (T)s;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+template <typename X>
+static int upload_vec(X** d, const std::vector<X>& h) {
+  CR_CUDA(cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(X)));
+  if (!h.empty()) CR_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(X), cudaMemcpyHostToDevice));
+  return CR_OK;
+}
+
+struct SmootherBuild {
+  int* d_order = nullptr;
+  int* d_blk_p = nullptr;
+  int* d_blk_q = nullptr;
+  int64_t* d_cobs_ptr = nullptr;
+  int* d_cobs = nullptr;
+  int64_t* d_diag = nullptr;
+  float* d_gD = nullptr;
+  float* d_gB = nullptr;
+  double* d_gl = nullptr;
+  int* d_ovf = nullptr;
+  unsigned* d_amax = nullptr;
+  ~SmootherBuild() {
+    void* ptrs[] = {d_order, d_blk_p, d_blk_q, d_cobs_ptr, d_cobs, d_diag, d_gD, d_gB, d_gl, d_ovf, d_amax};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+};
+
+int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
+  const BlockPattern& pat = lev.pat;
+  IccArgs a;
+  a.A = lev.d_A;
+  a.L = lev.d_L;
+  a.upd_ptr = lev.d_upd_ptr;
+  a.tgt_blk = lev.d_tgt_blk;
+  a.tgt_u = lev.d_tgt_u;
+  a.tgt_ptr = lev.d_tgt_ptr;
+  a.pair_a = lev.d_pair_a;
+  a.pair_b = lev.d_pair_b;
+  a.alpha = alpha;
+  a.fail = lev.d_fail;
+  const size_t smem = 4 * TK * (TK + 1) * sizeof(float);
+  CR_CUDA(cudaFuncSetAttribute(icc_colour_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CR_CUDA(cudaMemsetAsync(lev.d_fail, 0, sizeof(int), P->stream));
+  for (size_t c = 0; c + 1 < pat.colour_start.size(); ++c) {
+    const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
+    if (p1 > p0) { icc_colour_kernel<<<p1 - p0, SM_NT, smem, P->stream>>>(a, p0); count_launch(); }
+  }
+  CR_CHECK_LAUNCH("icc_colour_kernel");
+  int fail = 0;
+  CR_CUDA(cudaMemcpyAsync(&fail, lev.d_fail, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CR_CUDA(cudaStreamSynchronize(P->stream));
+  *ok = (fail == 0);
+  return CR_OK;
+}
+
+int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisections, double fixed_alpha) {
+  if (lev.k != 8) return fail(CR_EINVAL, "smoother: only k = 8 tiles are supported");
+  lev.nside_t = lev.nside_h / lev.k;
+  const int nobs = P->obs.nside;
+  if (lev.nside_t < 1 || nobs % lev.nside_t) return fail(CR_EINVAL, "smoother: Nside_h / k must divide the obs Nside");
+  BlockPattern& pat = lev.pat;
+  tile_pattern(lev.nside_t, pat);
+  pat.kk = TK;
+  const int nt = pat.ntile;
+  // per-block (p, q) and common observation tiles
+  std::vector<int> blk_p(pat.nblocks), blk_q(pat.nblocks);
+  std::vector<int64_t> cobs_ptr(pat.nblocks + 1, 0), diag(nt);
+  std::vector<int> cobs;
+  for (int p = 0; p < nt; ++p) {
+    for (int64_t b = pat.row_ptr[p]; b < pat.row_ptr[p + 1]; ++b) {
+      const int q = pat.row_col[b];
+      blk_p[b] = p;
+      blk_q[b] = q;
+      const auto& A = pat.nb[pat.order[p]];
+      const auto& B = pat.nb[pat.order[q]];
+      std::vector<int> common;
+      std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(common));
+      for (int t : common) cobs.push_back(t);
+      cobs_ptr[b + 1] = (int64_t)cobs.size();
+    }
+    diag[p] = pat.row_ptr[p + 1] - 1;
+  }
+  // ICC update lists (targets: the diagonal first, then later neighbours u)
+  std::vector<int64_t> upd_ptr(nt + 1, 0), tgt_blk, tgt_ptr(1, 0), pair_a, pair_b;
+  std::vector<int> tgt_u;
+  std::vector<std::vector<int>> later(nt);  // positions u > p coupled to p
+  std::vector<std::vector<int>> nbpos(nt);
+  for (int p = 0; p < nt; ++p) {
+    for (int u : pat.nb[pat.order[p]]) nbpos[p].push_back(pat.pos[u]);
+    std::sort(nbpos[p].begin(), nbpos[p].end());
+    for (int u : nbpos[p])
+      if (u > p) later[p].push_back(u);
+  }
+  for (int p = 0; p < nt; ++p) {
+    std::vector<int> targets(1, p);
+    targets.insert(targets.end(), later[p].begin(), later[p].end());
+    for (int u : targets) {
+      tgt_blk.push_back(pat.block_of(u, p));
+      tgt_u.push_back(u);
+      // k < p coupled to both u and p
+      for (int k : nbpos[p]) {
+        if (k >= p) break;
+        if (!std::binary_search(nbpos[u].begin(), nbpos[u].end(), k)) continue;
+        pair_a.push_back(pat.block_of(u, k));
+        pair_b.push_back(pat.block_of(p, k));
+      }
+      tgt_ptr.push_back((int64_t)pair_a.size());
+    }
+    upd_ptr[p + 1] = (int64_t)tgt_blk.size();
+  }
+  // backward-solve column lists: blocks (u, p), u > p
+  std::vector<int64_t> col_ptr(nt + 1, 0), col_blk;
+  std::vector<int> col_row;
+  for (int p = 0; p < nt; ++p) {
+    for (int u : later[p]) {
+      col_row.push_back(u);
+      col_blk.push_back(pat.block_of(u, p));
+    }
+    col_ptr[p + 1] = (int64_t)col_row.size();
+  }
+  // tile-ordered level pixel -> RING index
+  const int64_t npix_h = 12LL * lev.nside_h * lev.nside_h;
+  std::vector<int> perm(npix_h);
+  for (int p = 0; p < nt; ++p)
+    for (int j = 0; j < TK; ++j) perm[(int64_t)p * TK + j] = (int)nest2ring(lev.nside_h, (int64_t)pat.order[p] * TK + j);
+
+  SmootherBuild sb;
+  int rc = CR_OK;
+  if ((rc = upload_vec(&lev.d_perm, perm))) return rc;
+  if ((rc = upload_vec(&lev.d_row_ptr, pat.row_ptr))) return rc;
+  if ((rc = upload_vec(&lev.d_row_col, pat.row_col))) return rc;
+  if ((rc = upload_vec(&lev.d_col_ptr, col_ptr))) return rc;
+  if ((rc = upload_vec(&lev.d_col_row, col_row))) return rc;
+  if ((rc = upload_vec(&lev.d_col_blk, col_blk))) return rc;
+  if ((rc = upload_vec(&lev.d_upd_ptr, upd_ptr))) return rc;
+  if ((rc = upload_vec(&lev.d_tgt_blk, tgt_blk))) return rc;
+  if ((rc = upload_vec(&lev.d_tgt_u, tgt_u))) return rc;
+  if ((rc = upload_vec(&lev.d_tgt_ptr, tgt_ptr))) return rc;
+  if ((rc = upload_vec(&lev.d_pair_a, pair_a))) return rc;
+  if ((rc = upload_vec(&lev.d_pair_b, pair_b))) return rc;
+  if ((rc = upload_vec(&sb.d_order, pat.order))) return rc;
+  if ((rc = upload_vec(&sb.d_blk_p, blk_p))) return rc;
+  if ((rc = upload_vec(&sb.d_blk_q, blk_q))) return rc;
+  if ((rc = upload_vec(&sb.d_cobs_ptr, cobs_ptr))) return rc;
+  if ((rc = upload_vec(&sb.d_cobs, cobs))) return rc;
+  if ((rc = upload_vec(&sb.d_diag, diag))) return rc;
+  CR_CUDA(cudaMalloc(&lev.d_fail, sizeof(int)));
+  CR_CUDA(cudaMalloc(&sb.d_ovf, sizeof(int)));
+  CR_CUDA(cudaMalloc(&sb.d_amax, sizeof(unsigned)));
+  CR_CUDA(cudaMemset(sb.d_ovf, 0, sizeof(int)));
+  CR_CUDA(cudaMemset(sb.d_amax, 0, sizeof(unsigned)));
+  const int64_t nel = pat.nblocks * TK * TK;
+  CR_CUDA(cudaMalloc(&lev.d_A, nel * sizeof(float)));
+  CR_CUDA(cudaMalloc(&lev.d_L, nel * sizeof(float)));
+
+  // coupling tables in the chord d; d_max covers any pixel pair of two
+  // vertex-sharing tiles (4 tile radii, measured) with a margin
+  double rmax = 0.0;
+  for (int t = 0; t < nt; ++t) {
+    int ix, iy, f;
+    nest_xyf(lev.nside_t, t, &ix, &iy, &f);
+    double c[3];
+    face_vec(lev.nside_t, f, ix + 0.5, iy + 0.5, c);
+    for (int dx = 0; dx <= 1; ++dx)
+      for (int dy = 0; dy <= 1; ++dy) {
+        double v[3];
+        face_vec(lev.nside_t, f, ix + dx, iy + dy, v);
+        const double d = std::sqrt((v[0] - c[0]) * (v[0] - c[0]) + (v[1] - c[1]) * (v[1] - c[1]) +
+                                   (v[2] - c[2]) * (v[2] - c[2]));
+        rmax = std::max(rmax, d);
+      }
+  }
+  const double dmax = std::min(2.0, 4.5 * rmax + 4.0 * std::sqrt(4.0 * M_PI / (12.0 * nobs * nobs)));
+  const int Lh = lev.lmax_h;
+  const double h = 2.0 * M_PI / (128.0 * (Lh + 1));
+  const int nd = (int)std::ceil(dmax / h) + 4;
+  std::vector<double> gD(Lh + 1, 0.0), gB(Lh + 1, 0.0);
+  for (int l = 0; l <= Lh; ++l) {
+    const double cl = P->h_cl[l];
+    if (cl > 0) {
+      gD[l] = lev.fl[l] * lev.fl[l] / cl;
+      gB[l] = lev.fl[l] * P->h_bl[l];
+    }
+  }
+  CR_CUDA(cudaMalloc(&sb.d_gl, (Lh + 1) * sizeof(double)));
+  CR_CUDA(cudaMalloc(&sb.d_gD, nd * sizeof(float)));
+  CR_CUDA(cudaMalloc(&sb.d_gB, nd * sizeof(float)));
+  CR_CUDA(cudaMemcpy(sb.d_gl, gD.data(), (Lh + 1) * sizeof(double), cudaMemcpyHostToDevice));
+  coupling_table_kernel<<<(nd + 127) / 128, 128, 0, P->stream>>>(sb.d_gl, Lh, h, nd, sb.d_gD);
+  CR_CUDA(cudaStreamSynchronize(P->stream));
+  CR_CUDA(cudaMemcpy(sb.d_gl, gB.data(), (Lh + 1) * sizeof(double), cudaMemcpyHostToDevice));
+  coupling_table_kernel<<<(nd + 127) / 128, 128, 0, P->stream>>>(sb.d_gl, Lh, h, nd, sb.d_gB);
+  CR_CHECK_LAUNCH("coupling_table_kernel");
+
+  AssembleArgs aa;
+  aa.nside_h = lev.nside_h;
+  aa.nside_obs = nobs;
+  aa.ratio2 = (nobs / lev.nside_t) * (nobs / lev.nside_t);
+  aa.order = sb.d_order;
+  aa.blk_p = sb.d_blk_p;
+  aa.blk_q = sb.d_blk_q;
+  aa.cobs_ptr = sb.d_cobs_ptr;
+  aa.cobs = sb.d_cobs;
+  aa.ninv = P->d_ninv;
+  aa.gD = Table{sb.d_gD, nd, (float)(1.0 / h)};
+  aa.gB = Table{sb.d_gB, nd, (float)(1.0 / h)};
+  aa.A = lev.d_A;
+  aa.overflow = sb.d_ovf;
+  {
+    TimerScope ts(P->timing, P->stream, "smoother_assemble");
+    for (int64_t b0 = 0; b0 < pat.nblocks; b0 += (1 << 20)) {
+      const int nb = (int)std::min<int64_t>(1 << 20, pat.nblocks - b0);
+      AssembleArgs ab = aa;
+      ab.blk_p = sb.d_blk_p + b0;
+      ab.blk_q = sb.d_blk_q + b0;
+      ab.cobs_ptr = sb.d_cobs_ptr + b0;
+      ab.A = lev.d_A + b0 * TK * TK;
+      { assemble_kernel<<<nb, SM_NT, 0, P->stream>>>(ab); count_launch(); }
+    }
+    CR_CHECK_LAUNCH("assemble_kernel");
+    symmetrise_diag_kernel<<<nt, 256, 0, P->stream>>>(lev.d_A, sb.d_diag);
+    CR_CHECK_LAUNCH("symmetrise_diag_kernel");
+  }
+  int ovf = 0;
+  CR_CUDA(cudaMemcpyAsync(&ovf, sb.d_ovf, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  absmax_kernel<<<1024, 256, 0, P->stream>>>(lev.d_A, nel, sb.d_amax);
+  unsigned amax_bits = 0;
+  CR_CUDA(cudaMemcpyAsync(&amax_bits, sb.d_amax, sizeof(unsigned), cudaMemcpyDeviceToHost, P->stream));
+  CR_CUDA(cudaStreamSynchronize(P->stream));
+  if (ovf) return fail(CR_EINVAL, "smoother: pixel pair beyond the coupling table (tile geometry bound)");
+  float amaxf;
+  std::memcpy(&amaxf, &amax_bits, sizeof(float));
+  lev.amax = amaxf;
+
+  // ridge search (Section 3.5): smallest alpha letting ICC(0) succeed, used x ridge_factor
+  TimerScope ts(P->timing, P->stream, "smoother_icc");
+  bool ok = false;
+  if (fixed_alpha >= 0.0) {
+    lev.alpha = fixed_alpha;
+    if ((rc = factorise(P, lev, (float)fixed_alpha, &ok))) return rc;
+    if (!ok) return fail(CR_EICC, "smoother: ICC(0) failed with the given ridge");
+    return CR_OK;
+  }
+  if ((rc = factorise(P, lev, 0.f, &ok))) return rc;
+  double alpha = 0.0;
+  if (!ok) {
+    if ((rc = factorise(P, lev, (float)lev.amax, &ok))) return rc;
+    if (!ok) return fail(CR_EICC, "smoother: ICC(0) fails even with a ridge of max|A_hat|");
+    double lo = std::log(1e-12), hi = 0.0;
+    for (int it = 0; it < bisections; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if ((rc = factorise(P, lev, (float)(lev.amax * std::exp(mid)), &ok))) return rc;
+      if (ok) hi = mid;
+      else lo = mid;
+    }
+    alpha = lev.amax * std::exp(hi);
+  }
+  lev.alpha = ridge_factor * alpha;
+  if ((rc = factorise(P, lev, (float)lev.alpha, &ok))) return rc;
+  if (!ok) return fail(CR_EICC, "smoother: final ICC(0) factorisation failed");
+  return CR_OK;
+}
+
+template <typename T>
+int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
+  const BlockPattern& pat = lev.pat;
+  float* y = reinterpret_cast<float*>(P->hier_tile_work);
+  const int nc = (int)pat.colour_start.size() - 1;
+  for (int c = 0; c < nc; ++c) {
+    const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
+    if (p1 > p0)
+      { fwd_colour_kernel<T><<<p1 - p0, TK, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_row_col, lev.d_perm, map_in, y,
+                                                          p0); count_launch(); }
+  }
+  CR_CHECK_LAUNCH("fwd_colour_kernel");
+  for (int c = nc - 1; c >= 0; --c) {
+    const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
+    if (p1 > p0)
+      { bwd_colour_kernel<T><<<p1 - p0, TK, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_col_ptr, lev.d_col_row,
+                                                          lev.d_col_blk, lev.d_perm, y, map_out, p0); count_launch(); }
+  }
+  CR_CHECK_LAUNCH("bwd_colour_kernel");
+  return CR_OK;
+}
+template int apply_smoother<double>(cr_plan*, PixLevel&, double*, double*);
+template int apply_smoother<float>(cr_plan*, PixLevel&, float*, float*);
+
+void free_smoother(PixLevel& lev) {
+  void* ptrs[] = {lev.d_A, lev.d_L, lev.d_perm, lev.d_row_ptr, lev.d_row_col, lev.d_col_ptr, lev.d_col_row,
+                  lev.d_col_blk, lev.d_upd_ptr, lev.d_tgt_blk, lev.d_tgt_u, lev.d_tgt_ptr, lev.d_pair_a, lev.d_pair_b,
+                  lev.d_fail};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace cr

@@ -1,0 +1,208 @@
+"""Parity of the CUDA multi-level solver with the oracle (Sections 3.2-3.5,
+Fig. code:mg): the level table and filters, the level operators A_h,
+restriction and interpolation, the top-level diagonal smoother, the pixel
+block-ICC smoothers (same ridge), the bottom dense solve, one CR-Cycle, and
+CR-Solve in FP64 and mixed precision against the exact answer x_true of
+b = A x_true."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import cuda_device, rel_l2
+from oracle import geometry, multilevel, operators, sht
+from paper_1308_5299_gb300 import binding, synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return cuda_device()
+
+
+@pytest.fixture(scope="module")
+def case32(dev):
+    """Nside 32 / lmax 95: two pixel levels (Nside_h 16, 8) and a dense
+    bottom, built by the oracle; the GPU plan takes the same level table and
+    ridges."""
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside32_lmax95")
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    H = multilevel.Hierarchy(prob)
+    levels = [dict(nside_h=l["nside_h"], lmax_h=l["lmax_h"], n_rec=l["n_rec"], fl=l["fl"]) for l in H.levels]
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        levels=levels, lmax_dense=H.ld, ridge_alpha=[p.alpha for p in H.pix])
+    return dict(cfg=cfg, cl=cl, bl=bl, ninv=ninv, prob=prob, H=H, plan=plan)
+
+
+def rand_alm(L, seed, cl=None):
+    a = synthetic.random_alm(L, seed=seed)
+    if cl is not None:
+        l, m = sht.lm_arrays(L)
+        a[cl[l] <= 0] = 0.0
+    return a
+
+
+@pytest.mark.parametrize("nside,lmax", [(32, 95), (64, 191), (128, 383)])
+def test_default_level_table(dev, nside, lmax):
+    cl = synthetic.cl_spectrum(lmax, True)
+    bl = synthetic.gaussian_beam(lmax, 60.0)
+    ninv = torch.ones(12 * nside * nside, dtype=torch.float64, device=dev)
+    plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=ninv, levels="default", ridge_bisections=8)
+    t = multilevel.level_table(nside, lmax)
+    assert plan.nlevels() == len(t["levels"])
+    for h, ref in enumerate(t["levels"], start=1):
+        lv = plan.level(h)
+        assert (lv["nside_h"], lv["lmax_h"], lv["n_rec"]) == (ref["nside_h"], ref["lmax_h"], ref["n_rec"])
+        np.testing.assert_allclose(lv["fl"], ref["fl"], rtol=1e-12, atol=1e-300)
+    bt = plan.level(plan.nlevels() + 1)
+    assert bt["lmax_h"] == t["bottom"]["lmax_h"]
+
+
+def test_level_operators(case32, dev):
+    H, plan, prob = case32["H"], case32["plan"], case32["prob"]
+    for h in range(0, len(H.levels) + 2):
+        L = H.lmax_h(h)
+        x = rand_alm(L, 10 + h, prob.cl)
+        y = torch.empty(sht.n_lm(L), dtype=torch.complex128, device=dev)
+        plan.level_apply(h, torch.from_numpy(x).to(dev), y)
+        assert rel_l2(y.cpu().numpy(), H.apply_A(h, x)) < 1e-10, h
+
+
+def test_restrict_prolong(case32, dev):
+    H, plan, prob = case32["H"], case32["plan"], case32["prob"]
+    for h in range(0, len(H.levels) + 1):
+        Lh, LH = H.lmax_h(h), H.lmax_h(h + 1)
+        r = rand_alm(Lh, 20 + h)
+        out = torch.empty(sht.n_lm(LH), dtype=torch.complex128, device=dev)
+        plan.restrict(h, torch.from_numpy(r).to(dev), out)
+        assert rel_l2(out.cpu().numpy(), H.restrict(h, r)) < 1e-14
+        c = rand_alm(LH, 30 + h)
+        x0 = rand_alm(Lh, 40 + h)
+        x = torch.from_numpy(x0.copy()).to(dev)
+        plan.prolong_add(h, torch.from_numpy(c).to(dev), x)
+        assert rel_l2(x.cpu().numpy(), x0 + H.prolong(h, c)) < 1e-14
+
+
+def test_top_smoother(case32, dev):
+    H, plan, prob = case32["H"], case32["plan"], case32["prob"]
+    r = rand_alm(prob.lmax, 50, prob.cl)
+    c = torch.empty(sht.n_lm(prob.lmax), dtype=torch.complex128, device=dev)
+    plan.smooth(0, torch.from_numpy(r).to(dev), c)
+    assert rel_l2(c.cpu().numpy(), H.smooth(0, r)) < 1e-10
+
+
+def test_bottom_solve(case32, dev):
+    H, plan, prob = case32["H"], case32["plan"], case32["prob"]
+    b = rand_alm(H.ld, 60, prob.cl)
+    x = torch.empty(sht.n_lm(H.ld), dtype=torch.complex128, device=dev)
+    plan.bottom_solve(torch.from_numpy(b).to(dev), x)
+    assert rel_l2(x.cpu().numpy(), H.bottom_solve(b)) < 1e-8
+
+
+def test_bottom_matrix_ring_formula_nside256(dev):
+    """The bottom level's explicit matrix (Eq. Ni-dense, l <= 40) at Nside 256,
+    where polar seeds P~_mm fall below 2^-300 and the scaled recurrence has to
+    renormalise, against the oracle's independent ring formula."""
+    nside, lmax, ld = 256, 767, 40
+    cl = synthetic.cl_spectrum(lmax, True)
+    bl = synthetic.gaussian_beam(lmax, 20.0)
+    ninv = synthetic.mask(nside, 15.0, 20, 120.0) / synthetic.noise_rms(nside, 2.0, 30.0) ** 2
+    fl = multilevel.gauss_filter(lmax, 32)
+    fl[190:] = 0.0
+    plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        levels=[dict(nside_h=32, lmax_h=189, n_rec=1, fl=fl)], lmax_dense=ld, ridge_bisections=4)
+    A = plan.bottom_matrix()
+    g = geometry.healpix_grid(nside)
+    prob = operators.Problem(ld, cl[:ld + 1], bl[:ld + 1] * fl[:ld + 1], ninv, g)
+    act = operators.real_active_mask(prob, ld)
+    M = operators.ring_formula_inv_noise(prob, ld)[np.ix_(act, act)]
+    lv = np.concatenate([np.arange(ld + 1)] + [np.repeat(np.arange(m, ld + 1), 2) for m in range(1, ld + 1)])[act]
+    bv = (bl * fl)[lv]
+    ref = bv[:, None] * M * bv[None, :] + np.diag(fl[lv] ** 2 / cl[lv])
+    assert np.max(np.abs(A - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("h", [1, 2])
+def test_pixel_smoother(case32, dev, h):
+    """Y_h^T M_h Y_h r with the same ridge: FP32 assembly (interpolated
+    addition theorem) and FP32 ICC(0) against the FP64 oracle."""
+    H, plan, prob = case32["H"], case32["plan"], case32["prob"]
+    L = H.lmax_h(h)
+    r = rand_alm(L, 70 + h, prob.cl)
+    c = torch.empty(sht.n_lm(L), dtype=torch.complex128, device=dev)
+    plan.smooth(h, torch.from_numpy(r).to(dev), c)
+    assert rel_l2(c.cpu().numpy(), H.smooth(h, r)) < 2e-4
+    assert abs(plan.level(h)["ridge"] - H.pix[h - 1].alpha) <= 1e-12 * abs(H.pix[h - 1].alpha) + 1e-300
+
+
+def test_gpu_ridge_search(case32, dev):
+    """The GPU's own ridge search (FP32 factorisations) lands near the
+    oracle's FP64 bracket."""
+    c = case32
+    levels = [dict(nside_h=l["nside_h"], lmax_h=l["lmax_h"], n_rec=l["n_rec"], fl=l["fl"]) for l in c["H"].levels]
+    plan = binding.Plan(c["cfg"]["lmax"], nside=c["cfg"]["nside"], cl=c["cl"], bl=c["bl"],
+                        ninv=torch.from_numpy(c["ninv"]).to(dev), levels=levels, lmax_dense=c["H"].ld,
+                        ridge_lambda_target=-1.0)
+    for h in range(1, len(levels) + 1):
+        a_gpu, a_ref = plan.level(h)["ridge"], c["H"].pix[h - 1].alpha
+        assert 0.3 * a_ref <= a_gpu <= 3.0 * a_ref, (h, a_gpu, a_ref)
+
+
+def test_one_cycle(case32, dev):
+    H, plan, prob = case32["H"], case32["plan"], case32["prob"]
+    b = operators.apply_A(prob, synthetic.draw_prior(case32["cl"], index=5))
+    x = torch.zeros(sht.n_lm(prob.lmax), dtype=torch.complex128, device=dev)
+    plan.wcycle(x, torch.from_numpy(b).to(dev))
+    ref = H.cycle(0, np.zeros_like(b), b)
+    assert rel_l2(x.cpu().numpy(), ref) < 2e-4
+
+
+@pytest.fixture(scope="module")
+def plan32_default(case32, dev):
+    """The library's own level table and ridges (search plus the
+    lambda_max(S_h A_h) <= 1.5 bound) on the Nside 32 problem."""
+    c = case32
+    plan = binding.Plan(c["cfg"]["lmax"], nside=c["cfg"]["nside"], cl=c["cl"], bl=c["bl"],
+                        ninv=torch.from_numpy(c["ninv"]).to(dev), levels="default")
+    for h in range(0, plan.nlevels() + 1):
+        lv = plan.level(h)
+        assert lv["lambda_max"] <= 1.5 or (h == 0 and lv["ridge"] < 1.0)
+    return plan
+
+
+@pytest.mark.parametrize("mode", [binding.CR_F64, binding.CR_MIXED])
+def test_solve_to_exact_answer(case32, plan32_default, dev, mode):
+    """CR-Solve converges to x_true of b = A x_true (the exact answer)."""
+    prob, plan, cl = case32["prob"], plan32_default, case32["cl"]
+    x_true = prob.clean(synthetic.draw_prior(cl, index=6))
+    b = operators.apply_A(prob, x_true)
+    x = torch.empty_like(torch.from_numpy(b)).to(dev)
+    cyc, rel, hist = plan.solve(torch.from_numpy(b).to(dev), x, eps=1e-18, max_cycles=120, mode=mode, check=False)[:3]
+    xh = x.cpu().numpy()
+    assert rel[0] < 1e-9, (rel, hist)
+    g = prob.grid
+    err_map = sht.synth(xh - x_true, prob.lmax, g)
+    assert np.max(np.abs(err_map)) < 1e-3  # uK, max-pixel
+
+
+def test_solve_nside256(dev):
+    """The medium configuration (Nside 256, lmax 767, modulated noise,
+    galactic cut plus 200 holes): default levels, GPU ridge search, FP64
+    and mixed CR-Solve to a 1e-6 relative residual; max-pixel error against
+    x_true below 1e-3 uK after tightening to 1e-10."""
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside256_lmax767")
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    x_true = prob.clean(synthetic.draw_prior(cl, index=7))
+    b = operators.apply_A(prob, x_true)
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        levels="default")
+    tb = torch.from_numpy(b).to(dev)
+    for mode in (binding.CR_F64, binding.CR_MIXED):
+        x = torch.empty_like(tb)
+        cyc, rel, hist = plan.solve(tb, x, eps=1e-20, max_cycles=100, mode=mode, check=False)[:3]
+        assert rel[0] < 1e-10, (mode, hist[0][:cyc[0]])
+        m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
+        plan.sht_synth(x - torch.from_numpy(x_true).to(dev), m)
+        assert float(m.abs().max()) < 1e-3, mode
