@@ -52,6 +52,16 @@ def gauss_filter(lmax, nside_h):
     return np.exp(-0.5 * l * (l + 1.0) * s * s)
 
 
+def first_level_nside(nside, lmax, k=8):
+    """Nside of the first pixel level outside the paper's Planck table: the
+    power of two nearest lmax / 2.93 (the table's 3000 / 1024), so that the
+    top level's high-pass 1 - f^1 covers the same share of the band, clipped
+    to [k, nside]."""
+    e = math.log2(max(1.0, lmax / 2.93))
+    nh = 1 << max(0, int(math.floor(e + 0.5)))
+    return max(min(nh, nside), k)
+
+
 def level_table(nside, lmax, k=8, planck=None, first=None):
     """Levels for an observation grid of Nside ``nside`` and band limit
     ``lmax``.  Returns dict(top, levels[list], bottom).  Each pixel level:
@@ -64,7 +74,7 @@ def level_table(nside, lmax, k=8, planck=None, first=None):
         spec = [(1024, 3000), (512, 2048), (256, 1280), (128, 768), (64, 384), (32, 224)]
     else:
         spec = []
-        nh = nside // 2 if first is None else first
+        nh = first_level_nside(nside, lmax, k) if first is None else first
         while nh >= k:
             if not spec:
                 lh = lmax

@@ -54,11 +54,21 @@ std::vector<double> gauss_filter(int lmax, int nside_h) {
 }
 
 // Default levels: the paper's Planck table for Nside 2048 / lmax 3000
-// (Table cycle-cost); otherwise pixel levels Nside/2, Nside/4, ... >= k with
+// (Table cycle-cost); otherwise pixel levels N_1, N_1/2, ... >= k, where N_1
+// is the power of two nearest lmax / 2.93 (the paper's 3000 / 1024, so that
+// the top level's high-pass 1 - f^1 only acts on the same noise-dominated
+// share of the band) clipped to [k, Nside], with
 // lmax_1 = lmax, lmax_2 = min(lmax, 4 Nside_2), lmax_h = min(lmax_{h-1},
 // 6 Nside_h); filters: q with q_{2.51 Nside_1} = 0.1, times q with
 // q_{3 Nside_2} = 0.1, then Gaussians of FWHM 2 pixels clipped to the level
 // above; filter values below 1e-8 are cut and the band limit follows.
+int first_level_nside(int nside, int lmax, int k) {
+  const double e = std::log2(std::max(1.0, lmax / 2.93));
+  int nh = 1 << std::max(0, (int)std::lround(e));
+  nh = std::min(nh, nside);
+  return std::max(nh, k);
+}
+
 void default_levels(int nside, int lmax, int k, std::vector<LevelSpec>& out, int* lmax_dense) {
   out.clear();
   std::vector<std::pair<int, int>> spec;
@@ -66,7 +76,7 @@ void default_levels(int nside, int lmax, int k, std::vector<LevelSpec>& out, int
   if (planck) {
     spec = {{1024, 3000}, {512, 2048}, {256, 1280}, {128, 768}, {64, 384}, {32, 224}};
   } else {
-    for (int nh = nside / 2; nh >= k; nh /= 2) {
+    for (int nh = first_level_nside(nside, lmax, k); nh >= k; nh /= 2) {
       int lh;
       if (spec.empty()) lh = lmax;
       else if (spec.size() == 1) lh = std::min(lmax, 4 * nh);

@@ -15,6 +15,7 @@ struct LevelSpec {
 
 std::vector<double> q_filter(int lmax, double ell_star, double value);
 std::vector<double> gauss_filter(int lmax, int nside_h);
+int first_level_nside(int nside, int lmax, int k);
 void default_levels(int nside, int lmax, int k, std::vector<LevelSpec>& out, int* lmax_dense);
 void tile_pattern(int nside_t, BlockPattern& P);
 

@@ -8,8 +8,10 @@ harmonic transform, no operator, no solver.
 The paper's inputs (the Planck 2013 143 GHz RMS map, beam, masks and the
 LCDM spectrum, Section 4.1) are not available, so seeded stand-ins with the
 same shapes are used:
-  * C_l: 1e3 / (l(l+1)) uK^2 for l >= 2 (C_0 = C_1 = 0), optionally damped by
-    exp(-l^2 / 2000^2);
+  * C_l: 1e3 / (l(l+1)) uK^2 for l >= 2, optionally damped by
+    exp(-l^2 / 2000^2), and C_0 = C_1 = C_2, the wide monopole/dipole prior of
+    Section 4.1 (``low="zero"`` gives C_0 = C_1 = 0 instead, for tests of the
+    inactive-multipole handling);
   * Gaussian beams b_l = exp(-l(l+1) sigma^2 / 2), sigma = FWHM / sqrt(8 ln 2);
     the pixel window is 1;
   * white noise with per-pixel RMS log-uniform in [lo, hi] uK, optionally
@@ -33,26 +35,28 @@ BASE_SEED = 1308
 
 # Workload presets (sizes, spectra, beams, noise and masks of the five
 # configurations the solver is exercised on; see the paper's Section 4.1 for
-# the Planck setup these imitate).
+# the Planck setup these imitate).  cl_low: "c2" is the paper's wide
+# monopole/dipole prior C_0 = C_1 = C_2; "zero" conditions on l = 0, 1
+# (C_0 = C_1 = 0), which the small FP64 cases use.
 CONFIGS = {
     # plain FP64 method, small: Nside 32, lmax 95, no spectral damping
-    "nside32_lmax95": dict(nside=32, lmax=95, damp=False, fwhm_arcmin=180.0, rms=(5.0, 50.0),
+    "nside32_lmax95": dict(nside=32, lmax=95, damp=False, cl_low="zero", fwhm_arcmin=180.0, rms=(5.0, 50.0),
                            modulation=False, gal_cut_deg=20.0, holes=0, hole_radius_arcmin=0.0),
     # plain FP64 method, medium: Nside 256, lmax 767, modulated noise, 200 holes
-    "nside256_lmax767": dict(nside=256, lmax=767, damp=True, fwhm_arcmin=20.0, rms=(2.0, 30.0),
+    "nside256_lmax767": dict(nside=256, lmax=767, damp=True, cl_low="zero", fwhm_arcmin=20.0, rms=(2.0, 30.0),
                              modulation=True, gal_cut_deg=15.0, holes=200, hole_radius_arcmin=60.0),
     # Planck-143-shaped: Nside 2048, lmax 3000, 7.3' beam, 3000 holes of 5'
-    "nside2048_lmax3000": dict(nside=2048, lmax=3000, damp=True, fwhm_arcmin=7.3, rms=(10.0, 60.0),
+    "nside2048_lmax3000": dict(nside=2048, lmax=3000, damp=True, cl_low="c2", fwhm_arcmin=7.3, rms=(10.0, 60.0),
                                modulation=False, gal_cut_deg=10.0, holes=3000, hole_radius_arcmin=5.0),
     # batched mixed resolutions
-    "nside1024_lmax2047": dict(nside=1024, lmax=2047, damp=True, fwhm_arcmin=7.3, rms=(10.0, 60.0),
+    "nside1024_lmax2047": dict(nside=1024, lmax=2047, damp=True, cl_low="c2", fwhm_arcmin=7.3, rms=(10.0, 60.0),
                                modulation=False, gal_cut_deg=10.0, holes=3000, hole_radius_arcmin=5.0),
-    "nside512_lmax1023": dict(nside=512, lmax=1023, damp=True, fwhm_arcmin=7.3, rms=(10.0, 60.0),
+    "nside512_lmax1023": dict(nside=512, lmax=1023, damp=True, cl_low="c2", fwhm_arcmin=7.3, rms=(10.0, 60.0),
                               modulation=False, gal_cut_deg=10.0, holes=3000, hole_radius_arcmin=5.0),
     # tiny cases the dense oracle solves exactly
-    "nside8_lmax23": dict(nside=8, lmax=23, damp=True, fwhm_arcmin=180.0, rms=(10.0, 60.0),
+    "nside8_lmax23": dict(nside=8, lmax=23, damp=True, cl_low="c2", fwhm_arcmin=180.0, rms=(10.0, 60.0),
                           modulation=False, gal_cut_deg=10.0, holes=3, hole_radius_arcmin=300.0),
-    "nside16_lmax47": dict(nside=16, lmax=47, damp=True, fwhm_arcmin=120.0, rms=(10.0, 60.0),
+    "nside16_lmax47": dict(nside=16, lmax=47, damp=True, cl_low="zero", fwhm_arcmin=120.0, rms=(10.0, 60.0),
                            modulation=False, gal_cut_deg=10.0, holes=4, hole_radius_arcmin=300.0),
 }
 
@@ -61,12 +65,20 @@ def rng(seed, stream):
     return np.random.Generator(np.random.Philox(key=[int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream)]))
 
 
-def cl_spectrum(lmax, damp):
+def cl_spectrum(lmax, damp, low="c2"):
+    """Prior spectrum.  With C_0 = C_1 = 0 every level's beam kernel
+    sum_l (2l+1)/(4 pi) f_l b_l P_l loses its monopole and dipole and gets a
+    negative floor over the whole sphere, so the pixel smoothers' block
+    pattern misses a large part of A_hat; Section 4.1 sets C_0 = C_1 = C_2."""
     l = np.arange(lmax + 1, dtype=np.float64)
     cl = np.zeros(lmax + 1)
     cl[2:] = 1e3 / (l[2:] * (l[2:] + 1.0))
     if damp:
         cl *= np.exp(-(l * l) / (2000.0 ** 2))
+    if low == "c2" and lmax >= 2:
+        cl[0] = cl[1] = cl[2]
+    elif low != "zero":
+        raise ValueError("low must be 'c2' or 'zero'")
     return cl
 
 
@@ -199,7 +211,7 @@ def problem_inputs(name, seed=BASE_SEED):
     cfg = CONFIGS[name]
     nside, lmax = cfg["nside"], cfg["lmax"]
     table = healpix_ring_table(nside)
-    cl = cl_spectrum(lmax, cfg["damp"])
+    cl = cl_spectrum(lmax, cfg["damp"], cfg["cl_low"])
     bl = gaussian_beam(lmax, cfg["fwhm_arcmin"])
     rms = noise_rms(nside, *cfg["rms"], seed=seed, modulation=cfg["modulation"], table=table)
     msk = mask(nside, cfg["gal_cut_deg"], cfg["holes"], cfg["hole_radius_arcmin"], seed=seed, table=table)

@@ -186,11 +186,12 @@ def test_solve_to_exact_answer(case32, plan32_default, dev, mode):
     assert np.max(np.abs(err_map)) < 1e-3  # uK, max-pixel
 
 
-def test_solve_nside256(dev):
+@pytest.mark.parametrize("mode", [binding.CR_F64, binding.CR_MIXED | binding.CR_PCG])
+def test_solve_nside256(dev, mode):
     """The medium configuration (Nside 256, lmax 767, modulated noise,
-    galactic cut plus 200 holes): default levels, GPU ridge search, FP64
-    and mixed CR-Solve to a 1e-6 relative residual; max-pixel error against
-    x_true below 1e-3 uK after tightening to 1e-10."""
+    galactic cut plus 200 holes, C_0 = C_1 = 0): default levels, GPU ridge
+    search, stationary FP64 and mixed flexible-PCG CR-Solve to a 1e-10
+    relative residual; max-pixel error against x_true below 1e-3 uK."""
     cfg, cl, bl, ninv = synthetic.problem_inputs("nside256_lmax767")
     g = geometry.healpix_grid(cfg["nside"])
     prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
@@ -199,10 +200,33 @@ def test_solve_nside256(dev):
     plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
                         levels="default")
     tb = torch.from_numpy(b).to(dev)
-    for mode in (binding.CR_F64, binding.CR_MIXED):
-        x = torch.empty_like(tb)
-        cyc, rel, hist = plan.solve(tb, x, eps=1e-20, max_cycles=100, mode=mode, check=False)[:3]
-        assert rel[0] < 1e-10, (mode, hist[0][:cyc[0]])
-        m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
-        plan.sht_synth(x - torch.from_numpy(x_true).to(dev), m)
-        assert float(m.abs().max()) < 1e-3, mode
+    x = torch.empty_like(tb)
+    cyc, rel, hist = plan.solve(tb, x, eps=1e-20, max_cycles=100, mode=mode, check=False)[:3]
+    assert rel[0] < 1e-10, (mode, hist[0][:cyc[0]])
+    m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
+    plan.sht_synth(x - torch.from_numpy(x_true).to(dev), m)
+    assert float(m.abs().max()) < 1e-3, mode
+
+
+def test_solve_planck_shaped_nside2048(dev):
+    """The Planck-143-shaped workload at full size (Nside 2048, lmax 3000,
+    7.3' beam, |b| < 10 deg cut plus 3000 holes of 5', C_0 = C_1 = C_2): the
+    default level table of Table cycle-cost, the mixed-precision flexible-PCG
+    CR-Solve, and the property that holds at any size -- the max-pixel error
+    against x_true of b = A x_true falls below 1e-3 uK within 8 cycles and
+    the relative residual history decreases."""
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside2048_lmax3000")
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        levels="default")
+    assert [plan.level(h)["nside_h"] for h in range(1, plan.nlevels() + 1)] == [1024, 512, 256, 128, 64, 32]
+    x_true = torch.from_numpy(synthetic.draw_prior(cl, index=0)).to(dev)
+    b = torch.empty_like(x_true)
+    plan.apply_A(x_true, b)
+    x = torch.empty_like(b)
+    cyc, rel, hist = plan.solve(b, x, eps=1e-24, max_cycles=8, mode=binding.CR_MIXED | binding.CR_PCG,
+                                check=False)[:3]
+    h = hist[0][:cyc[0]]
+    assert np.all(np.diff(h) < 0), h
+    m = torch.empty(12 * cfg["nside"] ** 2, dtype=torch.float64, device=dev)
+    plan.sht_synth(x - x_true, m)
+    assert float(m.abs().max()) < 1e-3, h

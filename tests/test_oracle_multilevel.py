@@ -139,10 +139,22 @@ def test_multilevel_fixed_point_equals_dense_solve():
     prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
     x_true = synthetic.draw_prior(cl, index=1)
     b = operators.apply_A(prob, x_true)
-    H = multilevel.Hierarchy(prob)
+    H = multilevel.Hierarchy(prob, table=multilevel.level_table(cfg["nside"], cfg["lmax"], first=8))
     assert len(H.pix) == 1
     x, hist = H.solve(b, eps=1e-20, max_cycles=45, x_true=prob.clean(x_true))
     errs = [h[1] for h in hist]
     assert all(b2 < b1 for b1, b2 in zip(errs[:-1], errs[1:]))
     assert errs[-1] < 1e-8 * errs[0]
     assert np.max(np.abs(x - prob.clean(x_true))) < 1e-7 * np.max(np.abs(x_true))
+
+
+def test_first_level_rule_matches_planck_table():
+    """The default first pixel level reproduces the paper's Planck choice
+    (lmax 3000 -> Nside_h 1024, Section 3.2) and scales with lmax elsewhere."""
+    assert multilevel.first_level_nside(2048, 3000) == 1024
+    assert multilevel.first_level_nside(32, 95) == 32
+    assert multilevel.first_level_nside(256, 767) == 256
+    assert multilevel.first_level_nside(1024, 2047) == 512
+    assert multilevel.first_level_nside(8, 23) == 8
+    t = multilevel.level_table(256, 767)
+    assert [lv["nside_h"] for lv in t["levels"]] == [256, 128, 64, 32, 16, 8]
