@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-cycles", type=int, default=2,
+                    help="cycles per realization priced by the reference arm (the GPU arm's measured count)")
     return ap.parse_args()
 
 
@@ -99,53 +101,115 @@ def measured_peaks():
         return {}
 
 
-# FMA-pipe peaks of this GB300 pool, measured with an FMA-loop probe (152 SMs,
-# 8 independent FMA chains per thread, CUDA events): FP64 1.19 TFLOP/s,
-# FP32 74.5 TFLOP/s.
-FP64_FMA_PEAK_TFLOPS = 1.19
-FP32_FMA_PEAK_TFLOPS = 74.5
+def gl_noise_grid(nside, lmax_h):
+    """Gauss-Legendre grid the library uses for a level's inverse-noise term
+    (auto rule): 2 lmax_h + 1 rings, nphi the power of two >= 4 lmax_h + 1,
+    when that is at most half the observation grid's rings; else None."""
+    if 2 * lmax_h + 1 > (4 * nside - 1) // 2:
+        return None
+    nphi = 2
+    while nphi < 4 * lmax_h + 1:
+        nphi *= 2
+    return (2 * lmax_h + 1, nphi)
 
 
-def algorithmic_sht_flops(nside, lmax):
-    """Algorithmic flops of one synthesis or adjoint synthesis: ring pairs x
-    coefficients x 8 (recurrence ~4, accumulation ~4), no polar skipping."""
-    npairs = 2 * nside
-    nlm = (lmax + 1) * (lmax + 2) // 2
-    return npairs * nlm * 8.0
+def realization_pairs(nside, lmax, levels, cycles):
+    """SHT pairs (one synthesis + one adjoint) of one realization: `cycles`
+    CR-Cycles from zero (Fig. code:mg; n_rec 1 at the top, the table's n_rec
+    below; the top smoother is diagonal, the bottom dense) and the FP64
+    residual before every cycle but the first.  levels: list of (nside_h,
+    lmax_h, n_rec, noise) with noise None (observation grid) or (ntheta,
+    nphi).  Returns {grid key: pairs}, keys ("healpix", nside, L) or
+    ("gl", ntheta, nphi, L)."""
+    from collections import Counter
+
+    def a_key(h):
+        if h == 0:
+            return ("healpix", nside, lmax)
+        nh, lh, _, noise = levels[h - 1]
+        return ("healpix", nside, lh) if noise is None else ("gl", noise[0], noise[1], lh)
+
+    def cycle(h, start):
+        if h == len(levels) + 1:
+            return Counter()
+        c = Counter()
+        sm = None if h == 0 else ("healpix", levels[h - 1][0], levels[h - 1][1])
+        if start != "zero":
+            c[a_key(h)] += 1
+        if sm:
+            c[sm] += 1
+        c[a_key(h)] += 1
+        nrec = 1 if h == 0 else levels[h - 1][2]
+        for i in range(nrec):
+            c += cycle(h + 1, "zero" if i == 0 else "gen")
+        c[a_key(h)] += 1
+        if sm:
+            c[sm] += 1
+        return c
+
+    tot = Counter()
+    for _ in range(cycles):
+        tot += cycle(0, "zero")
+    tot[("healpix", nside, lmax)] += cycles - 1
+    return dict(tot)
 
 
-def cpu_baseline(cfg, seconds_budget=15.0):
-    """The oracle (plain FP64 direct SHT, as it stands) timed on this host's
-    cores on a bounded sample of rings of the same grid; scaled to SHT pairs/s
-    of the full grid."""
+def oracle_pair_seconds(key, nring_sample=32):
+    """The oracle's time for one synthesis + adjoint on the full grid of
+    `key`, from its time on evenly spaced sample rings (scaled by rings)."""
     import numpy as np
 
     from oracle import geometry, sht
 
-    nside, lmax = cfg["nside"], cfg["lmax"]
-    g = geometry.healpix_grid(nside)
+    if key[0] == "healpix":
+        g = geometry.healpix_grid(key[1])
+    else:
+        g = geometry.gl_grid(key[1], key[2])
+    L = key[-1]
+    nr = min(nring_sample, g["nring"])
+    idx = np.unique(np.linspace(0, g["nring"] - 1, nr).astype(np.int64))
+    nphi = g["nphi"][idx]
+    sub = dict(kind=g["kind"], z=g["z"][idx], sth=g["sth"][idx], nphi=nphi,
+               off=np.concatenate([[0], np.cumsum(nphi)[:-1]]).astype(np.int64), phi0=g["phi0"][idx],
+               wgt=g["wgt"][idx], npix=int(nphi.sum()), nring=len(idx))
     rng = np.random.default_rng(0)
-    a = rng.normal(size=sht.n_lm(lmax)) + 1j * rng.normal(size=sht.n_lm(lmax))
-    a[: lmax + 1] = a[: lmax + 1].real
-    y = rng.normal(size=g["npix"])
-    nr = 16
-    spent = 0.0
-    done_rings = 0
-    t_total = 0.0
-    while spent < seconds_budget and done_rings < g["nring"]:
-        rings = np.linspace(0, g["nring"] - 1, nr).astype(np.int64)
-        t0 = time.perf_counter()
-        sht.synth(a, lmax, g, rings=rings)
-        sht.adjoint(y, lmax, g, rings=rings)
-        dt = time.perf_counter() - t0
-        spent += dt
-        t_total += dt
-        done_rings += nr
-        nr *= 2
-    per_pair = t_total / done_rings * g["nring"]
-    return {"value": 1.0 / per_pair, "unit": "SHT pairs/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d rings (synthesis + adjoint, direct Legendre + direct DFT) of the Nside %d / lmax %d "
-                      "grid, scaled to all %d rings" % (done_rings, nside, lmax, g["nring"])}
+    a = rng.normal(size=sht.n_lm(L)) + 1j * rng.normal(size=sht.n_lm(L))
+    a[: L + 1] = a[: L + 1].real
+    y = rng.normal(size=sub["npix"])
+    t0 = time.perf_counter()
+    sht.synth(a, L, sub)
+    sht.adjoint(y, L, sub)
+    dt = time.perf_counter() - t0
+    return dt * g["nring"] / len(idx), len(idx)
+
+
+def oracle_levels(nside, lmax):
+    """The level table (with the noise grid of each level) the library builds
+    by default, from the oracle's level-table rule."""
+    from oracle import multilevel
+
+    t = multilevel.level_table(nside, lmax)
+    return [(lv["nside_h"], lv["lmax_h"], lv["n_rec"], gl_noise_grid(nside, lv["lmax_h"])) for lv in t["levels"]]
+
+
+def cpu_baseline(nside, lmax, levels, cycles):
+    """The oracle (plain FP64 direct SHT, C + OpenMP, as it stands) priced on
+    one realization: per (grid, band limit), its time for one SHT pair on a
+    sample of rings scaled to the full grid, times the pairs the realization
+    needs.  The pixel smoothers' triangular solves and the dense bottom
+    solves are not counted, so this is a lower bound."""
+    pairs = realization_pairs(nside, lmax, levels, cycles)
+    total, rings = 0.0, 0
+    for key, n in pairs.items():
+        t, nr = oracle_pair_seconds(key)
+        total += n * t
+        rings += nr
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": total, "unit": "s/realization", "cores": cores, "kind": "oracle",
+            "sample": "oracle SHT pair timed on %d sample rings over %d (grid, lmax) combinations, scaled to "
+                      "full grids and to the %d SHT pairs of one %d-cycle realization at Nside %d / lmax %d "
+                      "(smoother and bottom solves excluded: lower bound)"
+                      % (rings, len(pairs), sum(pairs.values()), cycles, nside, lmax)}
 
 
 def run_reference(args, rank, world):
@@ -154,21 +218,28 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     cfg = synthetic.CONFIGS[args.workload]
-    steps = []
+    nside, lmax = cfg["nside"], cfg["lmax"]
+    levels = oracle_levels(nside, lmax)
+    cycles = args.ref_cycles
+    steps, walls = [], []
     base = None
     for i in range(args.warmup + args.steps):
-        b = cpu_baseline(cfg, seconds_budget=8.0)
+        t0 = time.perf_counter()
+        b = cpu_baseline(nside, lmax, levels, cycles)
         if i >= args.warmup:
-            steps.append(1.0 / b["value"])
+            steps.append(b["value"])
+            walls.append(time.perf_counter() - t0)
             base = b
-    sec = statistics.median(steps)
-    v = 1.0 / sec
-    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "SHT pairs/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+    v = statistics.median(steps)
+    # a step is one bounded sample (timed rings); value is the realization
+    # time it prices
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/realization", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(walls) * 1e3,
+           "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "nside": cfg["nside"], "lmax": cfg["lmax"]},
+           "config": {"workload": args.workload, "nside": nside, "lmax": lmax, "cycles": cycles},
            "cpu_baseline": dict(base, value=v),
-           "e2e": {"value": v, "unit": "SHT pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": v, "unit": "s/realization", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
@@ -180,28 +251,39 @@ def max_pixel_error(plan, x, x_true, npix, dev):
     return float(m.abs().max())
 
 
+# ALU peaks derived from unit counts and clocks (152 SMs at 2070 MHz): FP32
+# 128 FMA lanes per SM -> 152 * 128 * 2 * 2.07e9 = 80.5 TFLOP/s; FP64 the
+# part's nominal 1.25 TFLOP/s (about 2 FMA per SM per clock).  An FMA-loop
+# probe on this pool measured 74.5 (FP32) and 1.19 (FP64) TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+# stages that time a sequence of kernels rather than one kernel
+COMPOSITE = {"outer_residual"}
+
+
 def roofline_of(stages, steps):
-    """Roofline of the stage with the largest share of the timed region:
-    Legendre stages against the FP64 / FP32 FMA-pipe peak (algorithmic flops),
-    the pixel smoother against HBM (algorithmic bytes)."""
+    """Roofline of the kernel stage with the largest share of the timed
+    region: Legendre stages against the FP64 / FP32 FMA peak (algorithmic
+    flops 8 per ring pair and (l, m)), ring-FFT stages and the pixel smoother
+    against the measured HBM copy bandwidth (algorithmic bytes)."""
     peaks = measured_peaks()
-    dom = max(stages, key=lambda k: stages[k][0])
-    ms, n, work = stages[dom]
+    kern = {k: v for k, v in stages.items() if k not in COMPOSITE}
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms, n, work = kern[dom]
+    base = {"kernel": dom, "ms_per_step": ms / steps, "launches_per_step": n / steps,
+            "algorithmic_work_per_launch": work / max(n, 1), "traffic": None}
     if dom.startswith("legendre") and work > 0:
-        f64 = dom.endswith("_f64")
-        peak = FP64_FMA_PEAK_TFLOPS if f64 else FP32_FMA_PEAK_TFLOPS
+        peak = FP64_PEAK_TFLOPS if dom.endswith("_f64") else FP32_PEAK_TFLOPS
         ach = work / (ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "peak_source": "measured FMA-loop probe (FP64 1.19 / FP32 74.5 TFLOP/s)",
-                "ms_per_step": ms / steps, "launch_scopes_per_step": n / steps,
-                "algorithmic_work_per_step": work / steps}
-    if dom == "pixel_smoother" and work > 0:
+        return dict(base, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    peak_source="derived: 152 SMs x 2070 MHz x (FP32 128 / FP64 2) FMA per SM per clock x 2")
+    if work > 0:
         peak = peaks.get("hbm_gbs", 6778.0)
         ach = work / (ms * 1e-3) / 1e9
-        return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "ms_per_step": ms / steps}
-    return {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None, "ms_per_step": ms / steps}
+        return dict(base, bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak,
+                    peak_source="MEASURED_PEAKS.json hbm_gbs (measured)")
+    return dict(base, bound="alu", achieved=None, peak=None, unit=None, frac=None)
 
 
 def main():
@@ -247,7 +329,7 @@ def main():
     # calibration (outside the timed region): fewest cycles reaching < 1 uK
     def cycles_to(mode, cap=12):
         for c in range(1, cap + 1):
-            plan.solve(b, x, eps=0.0, max_cycles=c, mode=mode, check=False)
+            plan.solve(b, x, eps=0.0, max_cycles=c, mode=mode | binding.CR_FIXED, check=False)
             err = max_pixel_error(plan, x, x_true, npix, dev)
             if err < 1.0:
                 return c, err
@@ -264,7 +346,7 @@ def main():
     mode_f64, cyc_f64, err_f64 = best_mode(binding.CR_F64)
 
     def solve_mixed():
-        plan.solve(b, x, eps=0.0, max_cycles=cyc_mixed, mode=mode_mixed, check=False)
+        plan.solve(b, x, eps=0.0, max_cycles=cyc_mixed, mode=mode_mixed | binding.CR_FIXED, check=False)
 
     for _ in range(args.warmup):
         solve_mixed()
@@ -276,11 +358,13 @@ def main():
     l0 = binding.launch_count()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
             solve_mixed()
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = binding.launch_count() - l0
     ms = e0.elapsed_time(e1) / args.steps
     stages = plan.timing()
@@ -294,7 +378,7 @@ def main():
     # plain FP64 solve (same protocol), one timed run
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    plan.solve(b, x, eps=0.0, max_cycles=cyc_f64, mode=mode_f64, check=False)
+    plan.solve(b, x, eps=0.0, max_cycles=cyc_f64, mode=mode_f64 | binding.CR_FIXED, check=False)
     f1.record(stream)
     torch.cuda.synchronize()
     f64_s = f0.elapsed_time(f1) * 1e-3
@@ -323,7 +407,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps // 2)):
         bd = bh.to(dev, non_blocking=True)
-        plan.solve(bd, x, eps=0.0, max_cycles=cyc_mixed, mode=mode_mixed, check=False)
+        plan.solve(bd, x, eps=0.0, max_cycles=cyc_mixed, mode=mode_mixed | binding.CR_FIXED, check=False)
         xh.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
@@ -335,10 +419,10 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "s/realization", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "nside": nside, "lmax": lmax,
                    "step": "one realization: CR-Solve of b = A x_true, FP32 W-cycles under FP64 refinement, "
-                           "fixed cycle count reaching < 1 uK max-pixel error",
+                           "fixed cycle count reaching < 1 uK max-pixel error (found before the timed region)",
                    "cycles": cyc_mixed, "levels": [plan.level(h)["nside_h"] for h in range(1, plan.nlevels() + 1)],
                    "l2": "inputs larger than L2 (N^-1 403 MB, phase 393 MB, smoother factors ~20 GB)",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -355,11 +439,12 @@ def main():
         "gpu_launches": int(launches),
     }
     if not args.no_cpu_baseline:
-        base = cpu_baseline(cfg)
-        # oracle s/realization estimate: the GPU mixed cycle count times the
-        # oracle's time for the SHT pairs of one cycle is not defined by the
-        # oracle; report its measured SHT-pair rate and per-pair time.
-        out["cpu_baseline"] = base
+        levels = []
+        for h in range(1, plan.nlevels() + 1):
+            lv = plan.level(h)
+            kind, nring, npx = plan.level_grid(h)
+            levels.append((lv["nside_h"], lv["lmax_h"], lv["n_rec"], (nring, npx // nring) if kind == "gl" else None))
+        out["cpu_baseline"] = cpu_baseline(nside, lmax, levels, cyc_mixed)
     print(json.dumps(out))
 
 

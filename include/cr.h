@@ -63,6 +63,12 @@ extern "C" {
 /* solve flag (or-ed with CR_F64 / CR_MIXED): flexible preconditioned CG with
  * one CR-Cycle as the preconditioner instead of repeated cycles */
 #define CR_PCG 4
+/* solve flag: run exactly max_cycles cycles with no stop test; in the
+ * stationary form the residual after the last cycle (needed only by the
+ * stop test) is not formed, so relres_out reports the residual before the
+ * last cycle and the last history entry is NaN.  For timing a cycle count
+ * found beforehand. */
+#define CR_FIXED 8
 
 /* grid kinds */
 #define CR_GRID_HEALPIX 0
@@ -112,7 +118,8 @@ typedef struct cr_params {
   void* stream;
   /* multi-level solver (needs cl).  nlevels: -1 = the default level table
    * (the paper's Planck table for Nside 2048 / lmax 3000, otherwise levels
-   * at Nside/2, Nside/4, ... >= 8 with fourth-power and Gaussian filters),
+   * from the power of two nearest lmax / 2.93 down to 8, with fourth-power
+   * and Gaussian filters),
    * 0 = no levels (transforms and A only), > 0 = the `levels` array (fine to
    * coarse).  lmax_dense: band limit of the bottom dense level (-1: default
    * min(40, lmax_H / 2)).  ridge_factor (0: 1.5) and ridge_bisections
@@ -131,6 +138,16 @@ typedef struct cr_params {
   int ridge_bisections;
   const double* ridge_alpha;
   double ridge_lambda_target;
+  /* gl_downgrade (Section 3.4, Eqs. Ni-rewrite and Xi): a pixel level's
+   * Y_obs^T N^-1 Y_obs at band limit lmax_h only sees the inverse-noise map
+   * up to multipole 2 lmax_h, so it is applied on a Gauss-Legendre grid of
+   * 2 lmax_h + 1 rings and a power-of-two nphi >= 4 lmax_h + 1 with the
+   * quadrature-weighted map w_j (sum_{L<=2 lmax_h} xi_LM Y_LM)(n_j),
+   * xi = Y_obs^T n: the same operator (exact by the Gaunt expansion, up to
+   * rounding) at O(lmax_h^3) cost.  0 = on for levels whose GL grid has at
+   * most half the observation grid's rings, 1 = on for every pixel level,
+   * -1 = off. */
+  int gl_downgrade;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */
@@ -143,6 +160,13 @@ const char* cr_last_error(void);
  * only on success.  Errors: CR_EINVAL, CR_ENOMEM, CR_ECUDA.
  */
 int cr_plan_create(cr_plan** out, const cr_params* p);
+
+/* Grid on which pixel level h (1..nlevels) applies its inverse-noise term:
+ * *kind = CR_GRID_HEALPIX (the observation grid) or CR_GRID_GL (the
+ * downgraded grid of gl_downgrade), with its ring and pixel counts.  Any
+ * output pointer may be NULL.  Errors: CR_EINVAL (no levels, h out of
+ * range). */
+int cr_plan_level_grid(const cr_plan* plan, int h, int* kind, int* nring, int64_t* npix);
 
 /* Release every resource of the plan (NULL is accepted). */
 int cr_plan_destroy(cr_plan* plan);

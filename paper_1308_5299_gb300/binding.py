@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcrgb300.so")
 
 CR_OK = 0
-CR_F64, CR_F32, CR_MIXED, CR_PCG = 0, 1, 2, 4
+CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED = 0, 1, 2, 4, 8
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0
 
@@ -57,6 +57,7 @@ class cr_params(ctypes.Structure):
         ("ridge_bisections", ctypes.c_int),
         ("ridge_alpha", ctypes.POINTER(ctypes.c_double)),
         ("ridge_lambda_target", ctypes.c_double),
+        ("gl_downgrade", ctypes.c_int),
     ]
 
 
@@ -80,6 +81,8 @@ _SIGS = {
     "cr_plan_set_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_launch_count": ([], ctypes.c_long),
     "cr_plan_nlevels": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cr_plan_level_grid": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cr_plan_level": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -160,10 +163,13 @@ class Plan:
     """One CR system / transform plan (``cr_plan_create``)."""
 
     def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
-                 lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0):
+                 lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0,
+                 gl_downgrade=0):
         """levels: None (transforms and A only), "default" (the library's level
         table), or a list of dicts with nside_h, lmax_h, n_rec and fl
-        (cumulative filter, length lmax+1)."""
+        (cumulative filter, length lmax+1).  gl_downgrade: 0 auto, 1 every
+        pixel level, -1 off (Gauss-Legendre grids for the levels'
+        inverse-noise term)."""
         p = cr_params()
         p.struct_size = ctypes.sizeof(cr_params)
         if gl is not None:
@@ -210,6 +216,7 @@ class Plan:
         p.ridge_factor = float(ridge_factor)
         p.ridge_bisections = int(ridge_bisections)
         p.ridge_lambda_target = float(ridge_lambda_target)
+        p.gl_downgrade = int(gl_downgrade)
         if ridge_alpha is not None:
             ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
             self._keep.append(ra)
@@ -292,6 +299,13 @@ class Plan:
                                    fl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(ridge),
                                    ctypes.byref(lam)))
         return dict(nside_h=ns.value, lmax_h=lm.value, n_rec=nr.value, fl=fl, ridge=ridge.value, lambda_max=lam.value)
+
+    def level_grid(self, h):
+        """(kind, nring, npix) of the grid on which pixel level h applies its
+        inverse-noise term: kind "healpix" (observation grid) or "gl"."""
+        k, nr, npx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib().cr_plan_level_grid(self._h, h, ctypes.byref(k), ctypes.byref(nr), ctypes.byref(npx)))
+        return ("gl" if k.value == CR_GRID_GL else "healpix", nr.value, npx.value)
 
     def level_apply(self, h, x, out):
         _check(lib().cr_level_apply(self._h, h, _dev(x), _dev(out), _dtype_code(x)))

@@ -43,6 +43,12 @@ struct PixLevel {
   int nside_h = 0, lmax_h = 0, n_rec = 1, k = 8, nside_t = 0;
   std::vector<double> fl;  // cumulative filter, [lmax + 1], 0 above lmax_h
   Grid* grid = nullptr;    // pixel grid (RING order) at lmax_h
+  // Gauss-Legendre grid of the level's inverse-noise term (Section 3.4), or
+  // null (the observation grid); d_nt = quadrature-weighted band-limited
+  // inverse-noise map on it
+  Grid* gl = nullptr;
+  double* d_nt = nullptr;
+  float* d_nt32 = nullptr;
   LArr bh, dh;             // B_h = f b p, D_h = f^2 / C  (0 where C_l = 0), [lmax_h + 1]
   BlockPattern pat;
   double alpha = 0.0;      // ridge used for the factorisation

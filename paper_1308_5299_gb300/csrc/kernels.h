@@ -78,6 +78,9 @@ int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const 
 
 // grids and workspace (plan.cu)
 void healpix_rings(Grid& g, int N);
+void gl_rings(Grid& g, int ntheta, int nphi, std::vector<double>* weights);
+int grid_reseed(Grid& g, int Lseed, cudaStream_t st);
+int rebuild_coef(cr_plan* P, int Lc);
 int grid_upload(Grid& g, int Lseed, cudaStream_t st);
 void grid_free(Grid& g);
 int ensure_workspace(cr_plan* P, const Grid& g, int L);

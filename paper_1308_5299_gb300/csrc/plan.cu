@@ -123,7 +123,7 @@ void healpix_rings(Grid& g, int N) {
 
 // Gauss-Legendre rings: nodes of P_ntheta by Newton iteration in theta
 // (accurate near the poles), nphi pixels per ring at phi = 2 pi j / nphi.
-static void gl_rings(Grid& g, int ntheta, int nphi, std::vector<double>* weights) {
+void gl_rings(Grid& g, int ntheta, int nphi, std::vector<double>* weights) {
   g.kind = CR_GRID_GL;
   g.nside = 0;
   g.nring = ntheta;
@@ -263,6 +263,33 @@ static int build_coef(cr_plan* P, int Lc) {
   return CR_OK;
 }
 
+// Recurrence tables for a larger band limit (the plan's transforms at any
+// L <= Lc keep working: the layout is off_m(Lc) + l - m).
+int rebuild_coef(cr_plan* P, int Lc) {
+  float** f[] = {&P->d_c32, &P->d_c2_32, &P->d_s32};
+  for (float** q : f) {
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+  }
+  if (P->d_c) cudaFree(P->d_c);
+  if (P->d_s) cudaFree(P->d_s);
+  P->d_c = P->d_s = nullptr;
+  return build_coef(P, Lc);
+}
+
+// Legendre seeds of a grid for a larger band limit.
+int grid_reseed(Grid& g, int Lseed, cudaStream_t st) {
+  CR_CUDA(cudaStreamSynchronize(st));
+  void* ptrs[] = {g.d_seed, g.d_lev, g.d_seed32, g.d_lev32};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  g.d_seed = nullptr;
+  g.d_lev = nullptr;
+  g.d_seed32 = nullptr;
+  g.d_lev32 = nullptr;
+  return build_seeds(g, Lseed, st);
+}
+
 int ensure_workspace(cr_plan* P, const Grid& g, int L) {
   const int64_t phase = (int64_t)g.nring * (L + 1) * (int64_t)sizeof(double2);
   const int64_t partial = (int64_t)leg_partial_blocks(g.npairs) * n_lm(L) * (int64_t)sizeof(double2);
@@ -359,6 +386,12 @@ static const char* ptag() {
 }
 // algorithmic flops of one Legendre stage on grid g at band limit L
 static double leg_work(const Grid& g, int L) { return 8.0 * g.npairs * (double)n_lm(L); }
+// algorithmic HBM bytes of one ring-FFT stage: the phase array [nring][L+1]
+// once, plus `maps` pixel arrays of T (map in or out, pixel diagonal, copy)
+template <typename T>
+static double fft_bytes(const Grid& g, int L, int maps) {
+  return (double)g.nring * (L + 1) * sizeof(typename Tr<T>::C) + (double)maps * g.npix * sizeof(T);
+}
 
 template <typename T>
 int do_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, const T* dl) {
@@ -373,7 +406,7 @@ int do_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, const
   if (rc) return rc;
   RingArgs<T> r = ring_args<T>(P, g, L);
   r.map_out = reinterpret_cast<T*>(map);
-  TimerScope ts(P->timing, P->stream, std::string("ring_fft_synth") + ptag<T>());
+  TimerScope ts(P->timing, P->stream, std::string("ring_fft_synth") + ptag<T>(), fft_bytes<T>(g, L, 1));
   return launch_ring_fft<T>(r, 0, P->stream);
 }
 
@@ -384,7 +417,7 @@ int do_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, con
   r.map_in = reinterpret_cast<const T*>(map);
   int rc;
   {
-    TimerScope ts(P->timing, P->stream, std::string("ring_fft_adjoint") + ptag<T>());
+    TimerScope ts(P->timing, P->stream, std::string("ring_fft_adjoint") + ptag<T>(), fft_bytes<T>(g, L, 1));
     rc = launch_ring_fft<T>(r, 1, P->stream);
   }
   if (rc) return rc;
@@ -417,7 +450,9 @@ int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const 
   r.pixdiag = pix;
   r.map_out = map_copy;
   {
-    TimerScope ts(P->timing, P->stream, std::string("ring_fft_apply") + ptag<T>());
+    // phase read and written back, pixel diagonal read (+ the map copy)
+    TimerScope ts(P->timing, P->stream, std::string("ring_fft_apply") + ptag<T>(),
+                  fft_bytes<T>(g, L, map_copy ? 2 : 1) + (double)g.nring * (L + 1) * sizeof(typename Tr<T>::C));
     rc = launch_ring_fft<T>(r, 2, P->stream);
   }
   if (rc) return rc;

@@ -48,16 +48,29 @@ static HierOps& ops_of(cr_plan* P) {
   return *reinterpret_cast<HierOps*>(P->hier->ops_store);
 }
 
+// Grid and pixel weights of level h's inverse-noise term: the level's
+// Gauss-Legendre grid when it has one, else the observation grid.
+template <typename T>
+static const Grid& noise_grid(cr_plan* P, int h, const T** pix) {
+  const Hierarchy& H = *P->hier;
+  if (h >= 1 && h <= H.H && H.pix[h - 1].gl) {
+    const PixLevel& lev = H.pix[h - 1];
+    if constexpr (sizeof(T) == 8) *pix = lev.d_nt;
+    else *pix = lev.d_nt32;
+    return *lev.gl;
+  }
+  if constexpr (sizeof(T) == 8) *pix = P->d_ninv;
+  else *pix = P->d_ninv32;
+  return P->obs;
+}
+
 template <typename T>
 static int residual(cr_plan* P, int h, const void* x, const void* b, void* r) {
-  Hierarchy& H = *P->hier;
   LevelOps& o = ops_of(P).ops[h];
   const int L = lmax_of(P, h);
-  const T* pix;
-  if constexpr (sizeof(T) == 8) pix = P->d_ninv;
-  else pix = P->d_ninv32;
-  (void)H;
-  return do_sandwich<T>(P, P->obs, L, x, r, o.b.get<T>(), pix, o.b.get<T>(), o.d.get<T>(), nullptr, b);
+  const T* pix = nullptr;
+  const Grid& g = noise_grid<T>(P, h, &pix);
+  return do_sandwich<T>(P, g, L, x, r, o.b.get<T>(), pix, o.b.get<T>(), o.d.get<T>(), nullptr, b);
 }
 
 template <typename T>
@@ -158,6 +171,54 @@ static int alloc_work(Hierarchy& H, int h, int L) {
   return CR_OK;
 }
 
+__global__ void gl_weight_kernel(double* nt, float* nt32, const double* wr, int nphi, int64_t npix) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = nt[i] * wr[i / nphi];
+    nt[i] = v;
+    nt32[i] = (float)v;
+  }
+}
+
+// Section 3.4 (Eqs. Ni-rewrite, Xi): for band limit Lh the operator
+// Y_obs^T N^-1 Y_obs sees the inverse-noise map n only through
+// xi_LM = (Y_obs^T n)_LM, L <= 2 Lh (the product Y*_lm Y_l'm' expands into
+// Y_LM with L <= l + l').  On a Gauss-Legendre grid exact for degree 4 Lh
+// (2 Lh + 1 rings, nphi >= 4 Lh + 1) the same operator is
+// Y_gl^T diag(w_j nt(n_j)) Y_gl with nt = sum_{L<=2Lh} xi_LM Y_LM.
+static int build_gl_level(cr_plan* P, PixLevel& lev) {
+  const int Lh = lev.lmax_h, L2 = 2 * Lh;
+  int nphi = 2;
+  while (nphi < 2 * L2 + 1) nphi <<= 1;
+  lev.gl = new Grid();
+  std::vector<double> w;
+  gl_rings(*lev.gl, L2 + 1, nphi, &w);
+  int rc = grid_upload(*lev.gl, L2, P->stream);
+  if (!rc) rc = ensure_workspace(P, *lev.gl, L2);
+  if (!rc) rc = ensure_workspace(P, P->obs, L2);
+  if (rc) return rc;
+  const int64_t npix = lev.gl->npix;
+  void* xi = nullptr;
+  double* d_wr = nullptr;
+  CR_CUDA(cudaMalloc(&xi, n_lm(L2) * sizeof(double2)));
+  CR_CUDA(cudaMalloc(&lev.d_nt, npix * sizeof(double)));
+  CR_CUDA(cudaMalloc(&lev.d_nt32, npix * sizeof(float)));
+  CR_CUDA(cudaMalloc(&d_wr, w.size() * sizeof(double)));
+  for (auto& v : w) v *= 2.0 * M_PI / nphi;
+  CR_CUDA(cudaMemcpy(d_wr, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  rc = do_adjoint<double>(P, P->obs, L2, P->d_ninv, xi, nullptr, nullptr, nullptr, 0);
+  if (!rc) rc = do_synth<double>(P, *lev.gl, L2, xi, lev.d_nt, nullptr);
+  if (!rc) {
+    gl_weight_kernel<<<1024, 256, 0, P->stream>>>(lev.d_nt, lev.d_nt32, d_wr, nphi, npix);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "gl_weight_kernel");
+  }
+  cudaFree(xi);
+  cudaFree(d_wr);
+  return rc;
+}
+
 int build_hierarchy(cr_plan* P, const cr_params* p) {
   Hierarchy* Hp = new Hierarchy();
   P->hier = Hp;
@@ -240,6 +301,20 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
     for (int l = 0; l <= LH; ++l) ratio[l] = (fh[l] != 0.0) ? fH[l] / fh[l] : 0.0;
     if ((rc = hops->ops[h].ratio.upload(ratio))) return rc;
   }
+  // Gauss-Legendre grids for the levels' inverse-noise term (gl_downgrade)
+  {
+    std::vector<int> use(H.H, 0);
+    int Lneed = P->Lcoef;
+    for (int i = 0; i < H.H; ++i) {
+      const int Lh = H.pix[i].lmax_h;
+      use[i] = p->gl_downgrade > 0 || (p->gl_downgrade == 0 && 2 * Lh + 1 <= P->obs.nring / 2);
+      if (use[i]) Lneed = std::max(Lneed, 2 * Lh);
+    }
+    if (Lneed > P->Lcoef && (rc = rebuild_coef(P, Lneed))) return rc;
+    if (Lneed > P->obs.Lseed && (rc = grid_reseed(P->obs, Lneed, P->stream))) return rc;
+    for (int i = 0; i < H.H; ++i)
+      if (use[i] && (rc = build_gl_level(P, H.pix[i]))) return rc;
+  }
   // work vectors
   if ((rc = alloc_work(H, 0, L))) return rc;
   for (int h = 1; h <= H.H; ++h)
@@ -307,6 +382,12 @@ void free_hierarchy(cr_plan* P) {
       grid_free(*lev.grid);
       delete lev.grid;
     }
+    if (lev.gl) {
+      grid_free(*lev.gl);
+      delete lev.gl;
+    }
+    if (lev.d_nt) cudaFree(lev.d_nt);
+    if (lev.d_nt32) cudaFree(lev.d_nt32);
   }
   if (H.ops_store) {
     HierOps* hops = reinterpret_cast<HierOps*>(H.ops_store);
@@ -353,8 +434,8 @@ __global__ void nonfinite_kernel(const double* v, int64_t n, int* flag) {
 // z = C(r), beta = <z, r - r_old> / <z_old, r_old> (Polak-Ribiere form, so
 // that an FP32 cycle -- a slightly nonlinear preconditioner -- stays safe),
 // p = z + beta p, alpha = <z, r> / <p, A p>.  Residual and A in FP64.
-static int pcg_solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, bool mixed, double bsb,
-                     int* cycles_out, double* relres_out, double* history) {
+static int pcg_solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, bool mixed, bool fixed,
+                     double bsb, int* cycles_out, double* relres_out, double* history) {
   Hierarchy& H = *P->hier;
   const int L = P->lmax;
   const int64_t nlm = n_lm(L);
@@ -413,11 +494,11 @@ static int pcg_solve(cr_plan* P, void* x, const void* b, double eps, int max_cyc
       if (relres_out) *relres_out = rel;
       return fail(CR_ENONFINITE, "pcg: non-finite residual");
     }
-    if (rel * rel < eps) break;
+    if (!fixed && rel * rel < eps) break;
   }
   if (cycles_out) *cycles_out = std::min(k, max_cycles);
   if (relres_out) *relres_out = rel;
-  if (k > max_cycles) return fail(CR_EMAXITER, "pcg: cycle cap reached before the tolerance");
+  if (k > max_cycles && !fixed) return fail(CR_EMAXITER, "pcg: cycle cap reached before the tolerance");
   return CR_OK;
 }
 
@@ -436,7 +517,8 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
     return CR_OK;
   }
   if (mode & CR_PCG)
-    return pcg_solve(P, x, b, eps, max_cycles, (mode & 3) == CR_MIXED, bsb, cycles_out, relres_out, history);
+    return pcg_solve(P, x, b, eps, max_cycles, (mode & 3) == CR_MIXED, (mode & CR_FIXED) != 0, bsb, cycles_out,
+                     relres_out, history);
   void* r = H.work[0].r;   // FP64 residual
   void* c32 = H.work[0].x; // FP32 correction (mixed mode)
   void* r32 = H.work[0].b; // FP32 residual (mixed mode)
@@ -454,6 +536,13 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
       if ((rc = cycle<float>(P, 0, c32, r32, true, nullptr))) return rc;
       if ((rc = launch_add_f2d((double*)x, (const float*)c32, 2 * nlm, P->stream))) return rc;
     }
+    if ((mode & CR_FIXED) && k == max_cycles) {
+      // fixed cycle count: the last residual would only feed the stop test
+      if (history) history[k - 1] = std::nan("");
+      if (cycles_out) *cycles_out = k;
+      if (relres_out) *relres_out = rel;
+      return CR_OK;
+    }
     // r = b - A x in FP64
     {
       TimerScope ts(P->timing, P->stream, "outer_residual");
@@ -467,6 +556,7 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
       if (relres_out) *relres_out = rel;
       return fail(CR_ENONFINITE, "solve: non-finite residual");
     }
+    if (mode & CR_FIXED) continue;
     if (rel * rel < eps) break;
     grow = (rel > prev) ? grow + 1 : 0;
     if (grow >= 2) {
@@ -480,7 +570,7 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
   (void)prev2;
   if (cycles_out) *cycles_out = std::min(k, max_cycles);
   if (relres_out) *relres_out = rel;
-  if (k > max_cycles) return fail(CR_EMAXITER, "solve: cycle cap reached before the tolerance");
+  if (k > max_cycles && !(mode & CR_FIXED)) return fail(CR_EMAXITER, "solve: cycle cap reached before the tolerance");
   return CR_OK;
 }
 
@@ -494,10 +584,9 @@ template int wcycle<float>(cr_plan*, void*, const void*);
 template <typename T>
 int level_apply(cr_plan* P, int h, const void* x, void* y) {
   LevelOps& o = ops_of(P).ops[h];
-  const T* pix;
-  if constexpr (sizeof(T) == 8) pix = P->d_ninv;
-  else pix = P->d_ninv32;
-  return do_sandwich<T>(P, P->obs, lmax_of(P, h), x, y, o.b.get<T>(), pix, o.b.get<T>(), o.d.get<T>(), nullptr,
+  const T* pix = nullptr;
+  const Grid& g = noise_grid<T>(P, h, &pix);
+  return do_sandwich<T>(P, g, lmax_of(P, h), x, y, o.b.get<T>(), pix, o.b.get<T>(), o.d.get<T>(), nullptr,
                         nullptr);
 }
 template <typename T>
@@ -563,6 +652,19 @@ int cr_plan_nlevels(cr_plan* plan, int* H) {
   int rc = check_hier(plan, "cr_plan_nlevels");
   if (rc) return rc;
   if (H) *H = plan->hier->H;
+  return CR_OK;
+}
+
+int cr_plan_level_grid(const cr_plan* cplan, int h, int* kind, int* nring, int64_t* npix) {
+  cr_plan* plan = const_cast<cr_plan*>(cplan);
+  int rc = check_hier(plan, "cr_plan_level_grid");
+  if (rc) return rc;
+  if (h < 1 || h > plan->hier->H) return fail(CR_EINVAL, "cr_plan_level_grid: h must be a pixel level");
+  const PixLevel& lev = plan->hier->pix[h - 1];
+  const Grid& g = lev.gl ? *lev.gl : plan->obs;
+  if (kind) *kind = g.kind;
+  if (nring) *nring = g.nring;
+  if (npix) *npix = g.npix;
   return CR_OK;
 }
 

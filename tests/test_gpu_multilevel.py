@@ -69,6 +69,55 @@ def test_level_operators(case32, dev):
         assert rel_l2(y.cpu().numpy(), H.apply_A(h, x)) < 1e-10, h
 
 
+def test_gl_downgrade_level_operators(case32, dev):
+    """Section 3.4: every pixel level's A_h applied through its
+    Gauss-Legendre grid (2 lmax_h + 1 rings, band-limited quadrature-weighted
+    inverse-noise map) equals the oracle's A_h on the observation grid."""
+    c, H = case32, case32["H"]
+    levels = [dict(nside_h=l["nside_h"], lmax_h=l["lmax_h"], n_rec=l["n_rec"], fl=l["fl"]) for l in H.levels]
+    plan = binding.Plan(c["cfg"]["lmax"], nside=c["cfg"]["nside"], cl=c["cl"], bl=c["bl"],
+                        ninv=torch.from_numpy(c["ninv"]).to(dev), levels=levels, lmax_dense=H.ld,
+                        ridge_alpha=[p.alpha for p in H.pix], gl_downgrade=1)
+    for h in range(1, len(H.levels) + 1):
+        L = H.lmax_h(h)
+        kind, nring, npix = plan.level_grid(h)
+        assert kind == "gl" and nring == 2 * L + 1, (h, kind, nring)
+        x = rand_alm(L, 70 + h, c["prob"].cl)
+        ref = H.apply_A(h, x)
+        y = torch.empty(sht.n_lm(L), dtype=torch.complex128, device=dev)
+        plan.level_apply(h, torch.from_numpy(x).to(dev), y)
+        assert rel_l2(y.cpu().numpy(), ref) < 1e-10, h
+        y32 = torch.empty(sht.n_lm(L), dtype=torch.complex64, device=dev)
+        plan.level_apply(h, torch.from_numpy(x).to(dev).to(torch.complex64), y32)
+        assert rel_l2(y32.cpu().numpy().astype(np.complex128), ref) < 2e-5, h
+    assert c["plan"].level_grid(1)[0] == "healpix"
+
+
+def test_gl_downgrade_nside256_matches_obs_grid(dev):
+    """At Nside 256 / lmax 767 the default rule moves the coarse levels to
+    Gauss-Legendre grids; their A_h agree with the observation-grid A_h of a
+    plan with the downgrade off."""
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside256_lmax767")
+    kw = dict(nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev), levels="default",
+              ridge_lambda_target=-1.0, ridge_bisections=6)
+    pa = binding.Plan(cfg["lmax"], gl_downgrade=0, **kw)
+    pb = binding.Plan(cfg["lmax"], gl_downgrade=-1, **kw)
+    ngl = 0
+    for h in range(1, pa.nlevels() + 1):
+        L = pa.level(h)["lmax_h"]
+        assert pb.level_grid(h)[0] == "healpix"
+        if pa.level_grid(h)[0] != "gl":
+            continue
+        ngl += 1
+        x = torch.from_numpy(rand_alm(L, 80 + h, cl)).to(dev)
+        ya = torch.empty_like(x)
+        yb = torch.empty_like(x)
+        pa.level_apply(h, x, ya)
+        pb.level_apply(h, x, yb)
+        assert rel_l2(ya.cpu().numpy(), yb.cpu().numpy()) < 1e-11, h
+    assert ngl >= 3
+
+
 def test_restrict_prolong(case32, dev):
     H, plan, prob = case32["H"], case32["plan"], case32["prob"]
     for h in range(0, len(H.levels) + 1):
