@@ -22,8 +22,8 @@ struct LegArgs {
   const T* z = nullptr;    // cos(colatitude) per ring (north ring of each pair)
   const T* w = nullptr;    // 1 - z per ring (used by the polar form)
   int npolar = 0;          // pairs [0, npolar) use the polar form z Q = Q - w Q
-  const T* seed = nullptr; // [m][pair]
-  const int* lev = nullptr;
+  const int* ls = nullptr;                 // [m][pair] start l (start tables)
+  const typename Tr<T>::C* st = nullptr;   // [m][pair] recurrence state at the start
   int ld_seed = 0;
   int npairs = 0, nring = 0;
   typename Tr<T>::C* partial = nullptr;    // adjoint: [nblk][n_lm(L)]
@@ -88,5 +88,6 @@ int ensure_workspace(cr_plan* P, const Grid& g, int L);
 // plan-time table builders (ringfft.cu)
 int build_fft_tables(Grid& g, cudaStream_t st);
 int build_seeds(Grid& g, int Lseed, cudaStream_t st);
+int build_start_tables(cr_plan* P, Grid& g);
 
 }  // namespace cr

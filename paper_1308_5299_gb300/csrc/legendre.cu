@@ -15,19 +15,26 @@
 // so the loop is uniform from l = m.  a_lm is multiplied by s_lm when staged
 // (synthesis) and the adjoint result by s_lm when written.
 //
-// Seeds P~_mm(z) arrive in underflow-safe scaled form (value v, level lev<=0;
-// true value v * 2^(S lev)).  While lev < 0 a pair only advances its
-// recurrence (its terms are below 2^(THR-S), negligible) and is renormalised
-// when it grows past 2^THR; warps whose pairs are all at lev 0 run a loop
-// without these checks.
+// Each (m, ring pair) starts where |P~_lm| first reaches a precision-dependent
+// threshold tau (FP64 2^-100, FP32 2^-60): the plan-time start tables hold
+// that l and the recurrence state there, computed once from the seed
+// P~_mm in scaled FP64 (build_start_tables).  Terms with |P~_lm| < tau are
+// dropped; they are below the rounding of either precision by more than
+// twenty orders of magnitude.  Before its start a pair neither steps nor
+// accumulates; pairs that never reach tau within the band limit hold a zero
+// state.  Each warp classifies every group of 8 l as idle (no pair started
+// yet), full (every live pair started: the unchecked loop) or ramp (per-pair
+// start test), so the region below the turning point where the functions are
+// negligible costs nothing.
 //
 // Work decomposition: one CTA per (m, block of LEG_NT*LEG_RP ring pairs);
-// each thread owns LEG_RP ring pairs.  The a_lm of the CTA's m (synthesis) and
-// the recurrence coefficients are staged through shared memory in chunks of
-// LEG_CH l-values.  The adjoint reduces over ring pairs with a warp-shuffle
-// transpose reduction over 8 consecutive l (each lane ends with one l), a
-// fixed-order cross-warp sum, and one partial row per ring block summed in a
-// second, deterministic kernel.
+// each warp owns 32*LEG_RP consecutive pairs (lane + 32 j), so its pairs'
+// start points are close.  The a_lm of the CTA's m (synthesis) and the
+// recurrence coefficients are staged through shared memory in chunks of
+// LEG_CH l-values from the CTA's earliest start.  The adjoint reduces over
+// ring pairs with a warp-shuffle transpose reduction over 8 consecutive l
+// (each lane ends with one l), a fixed-order cross-warp sum, and one partial
+// row per ring block summed in a second, deterministic kernel.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -66,8 +73,45 @@ __device__ __forceinline__ T rstep(T c, T c2, T zw, T& s1, T& s2) {
 // Ring pairs are split into a polar range [0, npolar) and an equatorial
 // range [npolar, npairs); each CTA covers LEG_NT*LEG_RP pairs of one range.
 // Block row yb (= blockIdx.y + the launch's row offset) < nbp is polar.
-__device__ __forceinline__ int pair_base(int npolar, int nbp, int yb, int tid) {
-  return yb < nbp ? yb * (LEG_NT * LEG_RP) + tid : npolar + (yb - nbp) * (LEG_NT * LEG_RP) + tid;
+__device__ __forceinline__ int pair_of(int npolar, int nbp, int yb, int warp, int lane, int j) {
+  const int base = yb < nbp ? yb * (LEG_NT * LEG_RP) : npolar + (yb - nbp) * (LEG_NT * LEG_RP);
+  return base + warp * (32 * LEG_RP) + j * 32 + lane;
+}
+
+// Per-thread pair setup shared by both kernels: start point, state, and the
+// warp's earliest / latest start over its live pairs (a pair is live when it
+// starts at or below L).  Returns false when the warp has no live pair.
+template <typename T, bool POLAR>
+__device__ __forceinline__ bool load_pairs(const LegArgs<T>& a, int m, int yb, int nbp, int warp, int lane,
+                                           int p[LEG_RP], int ls[LEG_RP], T P1[LEG_RP], T P2[LEG_RP],
+                                           T zz[LEG_RP], int* wmin, int* wmax) {
+  using C = typename Tr<T>::C;
+  const int pend = POLAR ? a.npolar : a.npairs;
+  int lo = a.L + 1, hi = m;
+#pragma unroll
+  for (int j = 0; j < LEG_RP; ++j) {
+    p[j] = pair_of(a.npolar, nbp, yb, warp, lane, j);
+    ls[j] = a.L + 1;
+    P1[j] = 0;
+    P2[j] = 0;
+    zz[j] = 0;
+    if (p[j] < pend) {
+      const int64_t o = (int64_t)m * a.ld_seed + p[j];
+      const int l = a.ls[o];
+      zz[j] = POLAR ? a.w[p[j]] : a.z[p[j]];
+      if (l <= a.L) {
+        const C st = a.st[o];
+        ls[j] = l;
+        P1[j] = st.x;
+        P2[j] = st.y;
+        lo = min(lo, l);
+        hi = max(hi, l);
+      }
+    }
+  }
+  *wmin = __reduce_min_sync(0xffffffffu, lo);
+  *wmax = __reduce_max_sync(0xffffffffu, hi);
+  return *wmin <= a.L;
 }
 
 template <typename T, bool POLAR>
@@ -76,40 +120,35 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
   const int m = blockIdx.x;
   const int L = a.L;
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   __shared__ C sa[LEG_CH];
   __shared__ T sc[LEG_CH];
   __shared__ T sc2[LEG_CH];
-  const T thr = (T)exp2((double)Tr<T>::THR);
-  const T down = (T)exp2(-(double)Tr<T>::S);
+  __shared__ int s_min;
 
   T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
-  int lev[LEG_RP];
+  int ls[LEG_RP], p[LEG_RP];
   C accE[LEG_RP], accO[LEG_RP];
-  const int yb = (int)blockIdx.y + yoff;
-  const int pbase = pair_base(a.npolar, nbp, yb, tid);
-  const int pend = POLAR ? a.npolar : a.npairs;
 #pragma unroll
   for (int j = 0; j < LEG_RP; ++j) {
-    const int p = pbase + j * LEG_NT;
-    if (p < pend) {
-      zz[j] = POLAR ? a.w[p] : a.z[p];
-      // (Q_{m-1}, Q_{m-2}) = (0, -seed), i.e. D_{m-1} = +seed in the polar form
-      const T sd = a.seed[(int64_t)m * a.ld_seed + p];
-      P2[j] = POLAR ? sd : -sd;
-      lev[j] = a.lev[(int64_t)m * a.ld_seed + p];
-    } else {
-      zz[j] = 0;
-      P2[j] = 0;
-      lev[j] = 0;
-    }
-    P1[j] = 0;
     accE[j] = mk((T)0, (T)0);
     accO[j] = mk((T)0, (T)0);
   }
+  const int yb = (int)blockIdx.y + yoff;
+  int wmin, wmax;
+  const bool live = load_pairs<T, POLAR>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  if (tid == 0) s_min = L + 1;
+  __syncthreads();
+  if (lane == 0 && live) atomicMin(&s_min, wmin);
+  __syncthreads();
+  const int cmin = s_min;
   const int64_t offa = lm_off(L, m);
   const int64_t offc = lm_off(a.Lc, m);
 
-  for (int l0 = m; l0 <= L; l0 += LEG_CH) {
+  // chunks start at an offset from m that is a multiple of 8, so l - m and
+  // the group index agree in parity
+  const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~7) : L + 1;
+  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
     const int nl = min(LEG_CH, L - l0 + 1);
     __syncthreads();
     for (int i = tid; i < nl; i += LEG_NT) {
@@ -123,68 +162,55 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
       if (POLAR) sc2[i] = a.c2[offc + (l - m)];
     }
     __syncthreads();
-    bool all0 = true;
+    if (!live || wmin >= l0 + nl) continue;
+    for (int i8 = 0; i8 < nl; i8 += 8) {
+      const int lg = l0 + i8;
+      const int ng = min(8, nl - i8);
+      if (wmin >= lg + ng) continue;  // no pair of the warp has started
+      if (wmax <= lg && ng == 8) {
 #pragma unroll
-    for (int j = 0; j < LEG_RP; ++j) all0 = all0 && (lev[j] == 0);
-    all0 = __all_sync(0xffffffffu, all0);
-    if (all0) {
-      int i = 0;
-      for (; i + 1 < nl; i += 2) {
-        const T c0 = sc[i], c1 = sc[i + 1];
-        const T d0 = POLAR ? sc2[i] : (T)0, d1 = POLAR ? sc2[i + 1] : (T)0;
-        const C a0 = sa[i], a1 = sa[i + 1];
+        for (int u = 0; u < 8; u += 2) {
+          const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
+          const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
+          const C a0 = sa[i8 + u], a1 = sa[i8 + u + 1];
 #pragma unroll
-        for (int j = 0; j < LEG_RP; ++j) {
-          T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-          T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
-          accE[j].x = fma(q0, a0.x, accE[j].x);
-          accE[j].y = fma(q0, a0.y, accE[j].y);
-          accO[j].x = fma(q1, a1.x, accO[j].x);
-          accO[j].y = fma(q1, a1.y, accO[j].y);
+          for (int j = 0; j < LEG_RP; ++j) {
+            const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+            const T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
+            accE[j].x = fma(q0, a0.x, accE[j].x);
+            accE[j].y = fma(q0, a0.y, accE[j].y);
+            accO[j].x = fma(q1, a1.x, accO[j].x);
+            accO[j].y = fma(q1, a1.y, accO[j].y);
+          }
         }
-      }
-      if (i < nl) {
-        const T c0 = sc[i];
-        const T d0 = POLAR ? sc2[i] : (T)0;
-        const C a0 = sa[i];
+      } else {
+        for (int u = 0; u < ng; ++u) {
+          const int l = lg + u;
+          const T c0 = sc[i8 + u];
+          const T d0 = POLAR ? sc2[i8 + u] : (T)0;
+          const C a0 = sa[i8 + u];
 #pragma unroll
-        for (int j = 0; j < LEG_RP; ++j) {
-          T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-          accE[j].x = fma(q0, a0.x, accE[j].x);
-          accE[j].y = fma(q0, a0.y, accE[j].y);
-        }
-      }
-    } else {
-      for (int i = 0; i < nl; ++i) {
-        const T c0 = sc[i];
-        const T d0 = POLAR ? sc2[i] : (T)0;
-        const C a0 = sa[i];
-        const bool odd = i & 1;  // l0 - m is a multiple of LEG_CH (even)
-#pragma unroll
-        for (int j = 0; j < LEG_RP; ++j) {
-          T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-          if (lev[j] == 0) {
-            if (odd) {
-              accO[j].x = fma(q0, a0.x, accO[j].x);
-              accO[j].y = fma(q0, a0.y, accO[j].y);
-            } else {
-              accE[j].x = fma(q0, a0.x, accE[j].x);
-              accE[j].y = fma(q0, a0.y, accE[j].y);
+          for (int j = 0; j < LEG_RP; ++j) {
+            if (l >= ls[j]) {
+              const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+              if (u & 1) {
+                accO[j].x = fma(q0, a0.x, accO[j].x);
+                accO[j].y = fma(q0, a0.y, accO[j].y);
+              } else {
+                accE[j].x = fma(q0, a0.x, accE[j].x);
+                accE[j].y = fma(q0, a0.y, accE[j].y);
+              }
             }
-          } else if (fabs(P1[j]) > thr) {
-            P1[j] *= down;
-            P2[j] *= down;
-            lev[j] += 1;
           }
         }
       }
     }
   }
+  const int pend = POLAR ? a.npolar : a.npairs;
 #pragma unroll
   for (int j = 0; j < LEG_RP; ++j) {
-    const int p = pbase + j * LEG_NT;
-    if (p < pend) {
-      const int rn = p, rs = a.nring - 1 - p;
+    if (p[j] < pend) {
+      const int rn = p[j], rs = a.nring - 1 - p[j];
       a.phase[(int64_t)rn * a.ldp + m] = cadd(accE[j], accO[j]);
       if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = csub(accE[j], accO[j]);
     }
@@ -251,25 +277,21 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   __shared__ T sc2[LEG_CH];
   __shared__ C sacc[LEG_CH];
   __shared__ C red[2][LEG_NW][8];
-  const T thr = (T)exp2((double)Tr<T>::THR);
-  const T down = (T)exp2(-(double)Tr<T>::S);
+  __shared__ int s_min;
 
   T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
-  int lev[LEG_RP];
+  int ls[LEG_RP], p[LEG_RP];
   C GE[LEG_RP], GO[LEG_RP];
   const int yb = (int)blockIdx.y + yoff;
-  const int pbase = pair_base(a.npolar, nbp, yb, tid);
+  int wmin, wmax;
+  const bool live = load_pairs<T, POLAR>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   const int pend = POLAR ? a.npolar : a.npairs;
 #pragma unroll
   for (int j = 0; j < LEG_RP; ++j) {
-    const int p = pbase + j * LEG_NT;
-    P1[j] = 0;
-    if (p < pend) {
-      zz[j] = POLAR ? a.w[p] : a.z[p];
-      const T sd = a.seed[(int64_t)m * a.ld_seed + p];
-      P2[j] = POLAR ? sd : -sd;
-      lev[j] = a.lev[(int64_t)m * a.ld_seed + p];
-      const int rn = p, rs = a.nring - 1 - p;
+    GE[j] = mk((T)0, (T)0);
+    GO[j] = mk((T)0, (T)0);
+    if (p[j] < pend && ls[j] <= L) {
+      const int rn = p[j], rs = a.nring - 1 - p[j];
       if (SQ) {
         const T v = a.ringval[rn] + ((rs != rn) ? a.ringval[rs] : (T)0);
         GE[j] = mk(v, (T)0);
@@ -280,20 +302,22 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
         GE[j] = cadd(gn, gs);
         GO[j] = csub(gn, gs);
       }
-    } else {
-      zz[j] = 0;
-      P2[j] = 0;
-      lev[j] = 0;
-      GE[j] = mk((T)0, (T)0);
-      GO[j] = mk((T)0, (T)0);
     }
   }
+  if (tid == 0) s_min = L + 1;
+  __syncthreads();
+  if (lane == 0 && live) atomicMin(&s_min, wmin);
+  __syncthreads();
+  const int cmin = s_min;
   const int64_t offa = lm_off(L, m);
   const int64_t offc = lm_off(a.Lc, m);
   C* part = a.partial + (int64_t)yb * n_lm(L);
+  const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~7) : L + 1;
+  // rows before the block's earliest start are zero
+  for (int l = m + tid; l < lbeg; l += LEG_NT) part[offa + (l - m)] = mk((T)0, (T)0);
   int rb = 0;
 
-  for (int l0 = m; l0 <= L; l0 += LEG_CH) {
+  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
     const int nl = min(LEG_CH, L - l0 + 1);
     __syncthreads();
     for (int i = tid; i < nl; i += LEG_NT) {
@@ -301,22 +325,21 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
       if (POLAR) sc2[i] = a.c2[offc + (l0 - m) + i];
     }
     __syncthreads();
-    bool all0 = true;
-#pragma unroll
-    for (int j = 0; j < LEG_RP; ++j) all0 = all0 && (lev[j] == 0);
-    all0 = __all_sync(0xffffffffu, all0);
     for (int i8 = 0; i8 < nl; i8 += 8) {
-      C acc[8];
+      const int lg = l0 + i8;
+      const int ng = min(8, nl - i8);
+      if (!live || wmin >= lg + ng) {
+        // no pair of this warp has started: its share of the sums is zero
+        if (lane < 8) red[rb][warp][lane] = mk((T)0, (T)0);
+      } else {
+        C acc[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] = mk((T)0, (T)0);
-      if (all0) {
+        for (int u = 0; u < 8; ++u) acc[u] = mk((T)0, (T)0);
+        if (wmax <= lg && ng == 8) {
 #pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          if (i8 + u < nl) {
-            const T c0 = sc[i8 + u];
-            const T c1 = (i8 + u + 1 < nl) ? sc[i8 + u + 1] : (T)0;
-            const T d0 = POLAR ? sc2[i8 + u] : (T)0;
-            const T d1 = (POLAR && i8 + u + 1 < nl) ? sc2[i8 + u + 1] : (T)0;
+          for (int u = 0; u < 8; u += 2) {
+            const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
+            const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
 #pragma unroll
             for (int j = 0; j < LEG_RP; ++j) {
               T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
@@ -331,32 +354,29 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
               acc[u + 1].y = fma(q1, GO[j].y, acc[u + 1].y);
             }
           }
-        }
-      } else {
+        } else {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (i8 + u < nl) {
-            const T c0 = sc[i8 + u];
-            const T d0 = POLAR ? sc2[i8 + u] : (T)0;
+          for (int u = 0; u < 8; ++u) {
+            if (u < ng) {
+              const int l = lg + u;
+              const T c0 = sc[i8 + u];
+              const T d0 = POLAR ? sc2[i8 + u] : (T)0;
 #pragma unroll
-            for (int j = 0; j < LEG_RP; ++j) {
-              T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-              if (lev[j] == 0) {
-                if (SQ) q0 *= q0;
-                const C g = (u & 1) ? GO[j] : GE[j];
-                acc[u].x = fma(q0, g.x, acc[u].x);
-                acc[u].y = fma(q0, g.y, acc[u].y);
-              } else if (fabs(P1[j]) > thr) {
-                P1[j] *= down;
-                P2[j] *= down;
-                lev[j] += 1;
+              for (int j = 0; j < LEG_RP; ++j) {
+                if (l >= ls[j]) {
+                  T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+                  if (SQ) q0 *= q0;
+                  const C g = (u & 1) ? GO[j] : GE[j];
+                  acc[u].x = fma(q0, g.x, acc[u].x);
+                  acc[u].y = fma(q0, g.y, acc[u].y);
+                }
               }
             }
           }
         }
+        warp_reduce8(acc);
+        if ((lane & 3) == 0) red[rb][warp][lane >> 2] = acc[0];
       }
-      warp_reduce8(acc);
-      if ((lane & 3) == 0) red[rb][warp][lane >> 2] = acc[0];
       __syncthreads();
       if (tid < 8) {
         C s = red[rb][0][tid];
@@ -451,8 +471,8 @@ int launch_leg_diag(cr_plan* P, const double* ringval, double2* out) {
   a.c = P->d_c;
   a.s = P->d_s;
   a.z = g.d_z;
-  a.seed = g.d_seed;
-  a.lev = g.d_lev;
+  a.ls = g.d_ls64;
+  a.st = g.d_st64;
   a.ld_seed = g.npairs;
   a.npairs = g.npairs;
   a.nring = g.nring;
@@ -471,6 +491,74 @@ int launch_leg_diag(cr_plan* P, const double* ringval, double2* out) {
   const int64_t nlm = n_lm(a.L);
   { leg_finalize_kernel<double><<<(int)std::min<int64_t>((nlm + 255) / 256, 152 * 16), 256, 0, P->stream>>>(ff); count_launch(); }
   CR_CHECK_LAUNCH("leg_finalize_kernel");
+  return CR_OK;
+}
+
+// Start tables (see Grid): for each m <= Lseed and ring pair, the scaled FP64
+// recurrence from the seed P~_mm up to the first l with |P~_lm| >= tau.
+__global__ void start_kernel(const double* z, const double* seed, const int* lev, int ld, const double* c,
+                             const double* s, int Lc, int Lseed, int npairs, int npolar32, int* ls64,
+                             double2* st64, int* ls32, float2* st32) {
+  const int m = blockIdx.y;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const int64_t o = (int64_t)m * ld + p;
+  const double zz = z[p];
+  const int64_t offc = lm_off(Lc, m);
+  const double thr = exp2((double)Tr<double>::THR);
+  const double down = exp2(-(double)Tr<double>::S);
+  const double tau64 = exp2(-100.0), tau32 = exp2(-60.0);
+  double q1 = 0.0, q2 = -seed[o];
+  int e = lev[o];
+  int f64 = Lseed + 1, f32 = Lseed + 1;
+  double2 s64 = make_double2(0.0, 0.0);
+  float2 s32 = make_float2(0.f, 0.f);
+  for (int l = m; l <= Lseed; ++l) {
+    const double q = c[offc + (l - m)] * zz * q1 - q2;
+    if (e == 0) {
+      const double pv = fabs(s[offc + (l - m)] * q);
+      if (f64 > Lseed && pv >= tau64) {
+        f64 = l;
+        s64 = make_double2(q1, q2);
+      }
+      if (pv >= tau32) {  // tau32 > tau64: the FP32 start comes last
+        f32 = l;
+        s32 = (p < npolar32) ? make_float2((float)q1, (float)(q1 - q2)) : make_float2((float)q1, (float)q2);
+        break;
+      }
+    }
+    q2 = q1;
+    q1 = q;
+    if (e < 0 && fabs(q1) > thr) {
+      q1 *= down;
+      q2 *= down;
+      ++e;
+    }
+  }
+  ls64[o] = f64;
+  st64[o] = s64;
+  ls32[o] = f32;
+  st32[o] = s32;
+}
+
+int build_start_tables(cr_plan* P, Grid& g) {
+  const int Ls = g.Lseed;
+  if (Ls < 0) return CR_OK;
+  if (Ls > P->Lcoef) return fail(CR_EINVAL, "start tables: grid band limit above the recurrence tables");
+  void* ptrs[] = {g.d_ls64, g.d_st64, g.d_ls32, g.d_st32};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  const int64_t n = (int64_t)(Ls + 1) * g.npairs;
+  CR_CUDA(cudaMalloc(&g.d_ls64, n * sizeof(int)));
+  CR_CUDA(cudaMalloc(&g.d_st64, n * sizeof(double2)));
+  CR_CUDA(cudaMalloc(&g.d_ls32, n * sizeof(int)));
+  CR_CUDA(cudaMalloc(&g.d_st32, n * sizeof(float2)));
+  dim3 grid((g.npairs + 127) / 128, Ls + 1);
+  { start_kernel<<<grid, 128, 0, P->stream>>>(g.d_z, g.d_seed, g.d_lev, g.npairs, P->d_c, P->d_s, P->Lcoef, Ls,
+                                               g.npairs, g.npolar32, g.d_ls64, g.d_st64, g.d_ls32, g.d_st32);
+    count_launch(); }
+  CR_CHECK_LAUNCH("start_kernel");
+  CR_CUDA(cudaStreamSynchronize(P->stream));
   return CR_OK;
 }
 

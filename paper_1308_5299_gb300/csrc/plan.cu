@@ -215,7 +215,8 @@ int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
 
 void grid_free(Grid& g) {
   void* ptrs[] = {g.d_z, g.d_z32, g.d_w32, g.d_sth, g.d_fft, g.d_tab, g.d_tab32, g.d_vhat, g.d_vhat32,
-                  g.d_tw, g.d_tw32, g.d_seed, g.d_lev, g.d_seed32, g.d_lev32};
+                  g.d_tw, g.d_tw32, g.d_seed, g.d_lev, g.d_seed32, g.d_lev32, g.d_ls64, g.d_st64, g.d_ls32,
+                  g.d_st32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -280,13 +281,17 @@ int rebuild_coef(cr_plan* P, int Lc) {
 // Legendre seeds of a grid for a larger band limit.
 int grid_reseed(Grid& g, int Lseed, cudaStream_t st) {
   CR_CUDA(cudaStreamSynchronize(st));
-  void* ptrs[] = {g.d_seed, g.d_lev, g.d_seed32, g.d_lev32};
+  void* ptrs[] = {g.d_seed, g.d_lev, g.d_seed32, g.d_lev32, g.d_ls64, g.d_st64, g.d_ls32, g.d_st32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   g.d_seed = nullptr;
   g.d_lev = nullptr;
   g.d_seed32 = nullptr;
   g.d_lev32 = nullptr;
+  g.d_ls64 = nullptr;
+  g.d_st64 = nullptr;
+  g.d_ls32 = nullptr;
+  g.d_st32 = nullptr;
   return build_seeds(g, Lseed, st);
 }
 
@@ -338,8 +343,8 @@ static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
     a.c = P->d_c;
     a.s = P->d_s;
     a.z = g.d_z;
-    a.seed = g.d_seed;
-    a.lev = g.d_lev;
+    a.ls = g.d_ls64;
+    a.st = g.d_st64;
     a.npolar = 0;
   } else {
     a.c = P->d_c32;
@@ -348,8 +353,8 @@ static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
     a.z = g.d_z32;
     a.w = g.d_w32;
     a.npolar = g.npolar32;
-    a.seed = g.d_seed32;
-    a.lev = g.d_lev32;
+    a.ls = g.d_ls32;
+    a.st = g.d_st32;
   }
   a.ld_seed = g.npairs;
   a.npairs = g.npairs;
@@ -532,6 +537,7 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   }
   rc = grid_upload(P->obs, P->lmax, P->stream);
   if (!rc) rc = build_coef(P, P->lmax);
+  if (!rc) rc = build_start_tables(P, P->obs);
   if (!rc) rc = ensure_workspace(P, P->obs, P->lmax);
   if (!rc && p->cl) {
     const int L = P->lmax;

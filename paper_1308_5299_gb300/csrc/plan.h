@@ -54,6 +54,14 @@ struct Grid {
   int* d_lev = nullptr;
   float* d_seed32 = nullptr;
   int* d_lev32 = nullptr;
+  // Legendre start tables, [m][pair] for m <= Lseed: the first l with
+  // |P~_lm| >= tau (FP64 2^-100, FP32 2^-60; Lseed + 1 if none) and the
+  // recurrence state there: (Q_{l-1}, Q_{l-2}), or (Q_{l-1}, D_{l-1}) on the
+  // FP32 polar pairs; built from the plan's recurrence tables
+  int* d_ls64 = nullptr;
+  double2* d_st64 = nullptr;
+  int* d_ls32 = nullptr;
+  float2* d_st32 = nullptr;
 };
 
 // Scratch sizes for transforms at band limit L on a grid.

@@ -193,6 +193,7 @@ static int build_gl_level(cr_plan* P, PixLevel& lev) {
   std::vector<double> w;
   gl_rings(*lev.gl, L2 + 1, nphi, &w);
   int rc = grid_upload(*lev.gl, L2, P->stream);
+  if (!rc) rc = build_start_tables(P, *lev.gl);
   if (!rc) rc = ensure_workspace(P, *lev.gl, L2);
   if (!rc) rc = ensure_workspace(P, P->obs, L2);
   if (rc) return rc;
@@ -273,6 +274,22 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
     if (!r2) r2 = hops->ops[h].act.upload(act);
     return r2;
   };
+  // Gauss-Legendre grids for the levels' inverse-noise term (gl_downgrade):
+  // decided first, since they may need recurrence tables and observation-grid
+  // seeds beyond lmax (up to 2 lmax_h)
+  std::vector<int> use_gl(H.H, 0);
+  {
+    int Lneed = P->Lcoef;
+    for (int i = 0; i < H.H; ++i) {
+      const int Lh = specs[i].lmax_h;
+      use_gl[i] = p->gl_downgrade > 0 || (p->gl_downgrade == 0 && 2 * Lh + 1 <= P->obs.nring / 2);
+      if (use_gl[i]) Lneed = std::max(Lneed, 2 * Lh);
+    }
+    const bool recoef = Lneed > P->Lcoef, reseed = Lneed > P->obs.Lseed;
+    if (recoef && (rc = rebuild_coef(P, Lneed))) return rc;
+    if (reseed && (rc = grid_reseed(P->obs, Lneed, P->stream))) return rc;
+    if ((recoef || reseed) && (rc = build_start_tables(P, P->obs))) return rc;
+  }
   std::vector<double> ftop(L + 1, 1.0);
   if ((rc = level_arrays(0, ftop, L))) return rc;
   for (int i = 0; i < H.H; ++i) {
@@ -285,6 +302,7 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
     lev.grid = new Grid();
     healpix_rings(*lev.grid, lev.nside_h);
     if ((rc = grid_upload(*lev.grid, lev.lmax_h, P->stream))) return rc;
+    if ((rc = build_start_tables(P, *lev.grid))) return rc;
     if ((rc = ensure_workspace(P, *lev.grid, lev.lmax_h))) return rc;
     max_npix_h = std::max(max_npix_h, lev.grid->npix);
     if ((rc = level_arrays(i + 1, lev.fl, lev.lmax_h))) return rc;
@@ -301,20 +319,8 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
     for (int l = 0; l <= LH; ++l) ratio[l] = (fh[l] != 0.0) ? fH[l] / fh[l] : 0.0;
     if ((rc = hops->ops[h].ratio.upload(ratio))) return rc;
   }
-  // Gauss-Legendre grids for the levels' inverse-noise term (gl_downgrade)
-  {
-    std::vector<int> use(H.H, 0);
-    int Lneed = P->Lcoef;
-    for (int i = 0; i < H.H; ++i) {
-      const int Lh = H.pix[i].lmax_h;
-      use[i] = p->gl_downgrade > 0 || (p->gl_downgrade == 0 && 2 * Lh + 1 <= P->obs.nring / 2);
-      if (use[i]) Lneed = std::max(Lneed, 2 * Lh);
-    }
-    if (Lneed > P->Lcoef && (rc = rebuild_coef(P, Lneed))) return rc;
-    if (Lneed > P->obs.Lseed && (rc = grid_reseed(P->obs, Lneed, P->stream))) return rc;
-    for (int i = 0; i < H.H; ++i)
-      if (use[i] && (rc = build_gl_level(P, H.pix[i]))) return rc;
-  }
+  for (int i = 0; i < H.H; ++i)
+    if (use_gl[i] && (rc = build_gl_level(P, H.pix[i]))) return rc;
   // work vectors
   if ((rc = alloc_work(H, 0, L))) return rc;
   for (int h = 1; h <= H.H; ++h)
