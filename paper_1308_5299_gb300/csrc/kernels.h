@@ -59,6 +59,11 @@ struct RingArgs {
   const T* map_in = nullptr;   // mode 1 input
   const T* pixdiag = nullptr;  // mode 2 diagonal
   int nring = 0;
+  const int* rings = nullptr;  // ring indices ordered by FFT size (device)
+  int rbase = 0;               // first entry of this launch's class
+  int nclass = 0;              // host: FFT-size classes
+  const int* cls_M = nullptr;
+  const int* cls_start = nullptr;
 };
 
 template <typename T> int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st);

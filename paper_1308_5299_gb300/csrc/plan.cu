@@ -216,7 +216,7 @@ int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
 void grid_free(Grid& g) {
   void* ptrs[] = {g.d_z, g.d_z32, g.d_w32, g.d_sth, g.d_fft, g.d_tab, g.d_tab32, g.d_vhat, g.d_vhat32,
                   g.d_tw, g.d_tw32, g.d_seed, g.d_lev, g.d_seed32, g.d_lev32, g.d_ls64, g.d_st64, g.d_ls32,
-                  g.d_st32};
+                  g.d_st32, g.d_rings};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -378,6 +378,10 @@ static RingArgs<T> ring_args(cr_plan* P, const Grid& g, int L) {
     r.tw = g.d_tw32;
   }
   r.Mmax = g.Mmax;
+  r.rings = g.d_rings;
+  r.nclass = (int)g.cls_M.size();
+  r.cls_M = g.cls_M.data();
+  r.cls_start = g.cls_start.data();
   r.phase = reinterpret_cast<typename Tr<T>::C*>(P->ws.phase);
   r.ldp = L + 1;
   r.L = L;

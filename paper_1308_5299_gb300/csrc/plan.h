@@ -35,6 +35,8 @@ struct Grid {
   int Mmax = 1;    // largest FFT size
   std::vector<double> z, sth;
   std::vector<RingFFT> fft;
+  std::vector<int> cls_M, cls_start;  // FFT-size classes over d_rings
+  int* d_rings = nullptr;             // ring indices ordered by FFT size
   // device tables
   double* d_z = nullptr;      // [nring]
   float* d_z32 = nullptr;     // [nring]

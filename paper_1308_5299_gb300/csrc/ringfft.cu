@@ -28,6 +28,7 @@
 //
 // One CTA per ring; mode 2 keeps the ring's map in shared memory between the
 // synthesis and the adjoint (map * N^-1 never touches HBM).
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <vector>
@@ -43,44 +44,136 @@ __device__ __forceinline__ int bitrev(int k, int logM) {
   return logM ? (int)(__brev((unsigned)k) >> (32 - logM)) : 0;
 }
 
-// In-place radix-2 decimation-in-time FFT: bit-reversed input, natural output.
-// sign = -1 forward (e^{-2 pi i jk/M}), +1 inverse (unnormalised).
 template <typename C>
-__device__ void fft_dit(C* buf, int M, int sign, const C* __restrict__ tw, int Mmax) {
-  for (int h = 1; h < M; h <<= 1) {
-    const int ts = Mmax / (2 * h);
-    for (int i = threadIdx.x; i < (M >> 1); i += blockDim.x) {
-      const int k = i & (h - 1);
-      const int j0 = ((i - k) << 1) + k;
-      const int j1 = j0 + h;
-      C w = tw[k * ts];
-      if (sign > 0) w = cconj(w);
-      const C u = buf[j0];
-      const C v = cmul(buf[j1], w);
-      buf[j0] = cadd(u, v);
-      buf[j1] = csub(u, v);
+__device__ __forceinline__ C twid(const C* __restrict__ tw, int idx, int sign) {
+  const C w = tw[idx];
+  return sign > 0 ? cconj(w) : w;
+}
+// radix-2 butterflies: decimation in time a' = a + w b, b' = a - w b;
+// decimation in frequency a' = a + b, b' = (a - b) w
+template <typename C>
+__device__ __forceinline__ void bf_dit(C& a, C& b, C w) {
+  const C v = cmul(b, w);
+  b = csub(a, v);
+  a = cadd(a, v);
+}
+template <typename C>
+__device__ __forceinline__ void bf_dif(C& a, C& b, C w) {
+  const C u = a;
+  a = cadd(u, b);
+  b = cmul(csub(u, b), w);
+}
+
+// In-place radix-2 decimation-in-time FFT: bit-reversed input, natural output.
+// sign = -1 forward (e^{-2 pi i jk/M}), +1 inverse (unnormalised).  Up to
+// three consecutive stages (spans h, 2h, 4h) run per pass on 8 elements
+// j0 + t h held in registers, one barrier per pass.
+template <typename C>
+__device__ void fft_dit(C* buf, int M, int logM, int sign, const C* __restrict__ tw, int Mmax) {
+  int lh = 0;
+  while (lh < logM) {
+    const int h = 1 << lh;
+    const int ns = min(3, logM - lh);
+    const int ng = M >> ns;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+      const int k = g & (h - 1);
+      const int j0 = ((g - k) << ns) + k;
+      if (ns == 3) {
+        C e[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) e[t] = buf[j0 + t * h];
+        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2), s3 = Mmax >> (lh + 3);
+        const C w1 = twid(tw, k * s1, sign);
+        bf_dit(e[0], e[1], w1);
+        bf_dit(e[2], e[3], w1);
+        bf_dit(e[4], e[5], w1);
+        bf_dit(e[6], e[7], w1);
+        const C w2a = twid(tw, k * s2, sign), w2b = twid(tw, (k + h) * s2, sign);
+        bf_dit(e[0], e[2], w2a);
+        bf_dit(e[1], e[3], w2b);
+        bf_dit(e[4], e[6], w2a);
+        bf_dit(e[5], e[7], w2b);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) bf_dit(e[t], e[t + 4], twid(tw, (k + t * h) * s3, sign));
+#pragma unroll
+        for (int t = 0; t < 8; ++t) buf[j0 + t * h] = e[t];
+      } else if (ns == 2) {
+        C e[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) e[t] = buf[j0 + t * h];
+        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2);
+        const C w1 = twid(tw, k * s1, sign);
+        bf_dit(e[0], e[1], w1);
+        bf_dit(e[2], e[3], w1);
+        bf_dit(e[0], e[2], twid(tw, k * s2, sign));
+        bf_dit(e[1], e[3], twid(tw, (k + h) * s2, sign));
+#pragma unroll
+        for (int t = 0; t < 4; ++t) buf[j0 + t * h] = e[t];
+      } else {
+        C a = buf[j0], b = buf[j0 + h];
+        bf_dit(a, b, twid(tw, k * (Mmax >> (lh + 1)), sign));
+        buf[j0] = a;
+        buf[j0 + h] = b;
+      }
     }
     __syncthreads();
+    lh += ns;
   }
 }
 
-// In-place radix-2 decimation-in-frequency FFT: natural input, bit-reversed output.
+// In-place radix-2 decimation-in-frequency FFT: natural input, bit-reversed
+// output; passes of up to three stages (spans 4h, 2h, h).
 template <typename C>
-__device__ void fft_dif(C* buf, int M, int sign, const C* __restrict__ tw, int Mmax) {
-  for (int h = M >> 1; h >= 1; h >>= 1) {
-    const int ts = Mmax / (2 * h);
-    for (int i = threadIdx.x; i < (M >> 1); i += blockDim.x) {
-      const int k = i & (h - 1);
-      const int j0 = ((i - k) << 1) + k;
-      const int j1 = j0 + h;
-      C w = tw[k * ts];
-      if (sign > 0) w = cconj(w);
-      const C u = buf[j0];
-      const C v = buf[j1];
-      buf[j0] = cadd(u, v);
-      buf[j1] = cmul(csub(u, v), w);
+__device__ void fft_dif(C* buf, int M, int logM, int sign, const C* __restrict__ tw, int Mmax) {
+  int lt = logM;  // stages with span >= 2^lt are done
+  while (lt > 0) {
+    const int ns = min(3, lt);
+    const int lh = lt - ns;  // smallest span of this pass
+    const int h = 1 << lh;
+    const int ng = M >> ns;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+      const int k = g & (h - 1);
+      const int j0 = ((g - k) << ns) + k;
+      if (ns == 3) {
+        C e[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) e[t] = buf[j0 + t * h];
+        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2), s3 = Mmax >> (lh + 3);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) bf_dif(e[t], e[t + 4], twid(tw, (k + t * h) * s3, sign));
+        const C w2a = twid(tw, k * s2, sign), w2b = twid(tw, (k + h) * s2, sign);
+        bf_dif(e[0], e[2], w2a);
+        bf_dif(e[1], e[3], w2b);
+        bf_dif(e[4], e[6], w2a);
+        bf_dif(e[5], e[7], w2b);
+        const C w1 = twid(tw, k * s1, sign);
+        bf_dif(e[0], e[1], w1);
+        bf_dif(e[2], e[3], w1);
+        bf_dif(e[4], e[5], w1);
+        bf_dif(e[6], e[7], w1);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) buf[j0 + t * h] = e[t];
+      } else if (ns == 2) {
+        C e[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) e[t] = buf[j0 + t * h];
+        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2);
+        bf_dif(e[0], e[2], twid(tw, k * s2, sign));
+        bf_dif(e[1], e[3], twid(tw, (k + h) * s2, sign));
+        const C w1 = twid(tw, k * s1, sign);
+        bf_dif(e[0], e[1], w1);
+        bf_dif(e[2], e[3], w1);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) buf[j0 + t * h] = e[t];
+      } else {
+        C a = buf[j0], b = buf[j0 + h];
+        bf_dif(a, b, twid(tw, k * (Mmax >> (lh + 1)), sign));
+        buf[j0] = a;
+        buf[j0 + h] = b;
+      }
     }
     __syncthreads();
+    lt = lh;
   }
 }
 
@@ -89,28 +182,32 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
   using C = typename Tr<T>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int r = blockIdx.x;
+  const int r = a.rings[a.rbase + blockIdx.x];
   const RingFFT f = a.fft[r];
   const C* __restrict__ tab = a.tab + f.tab;
   const C* __restrict__ vh = a.vhat + f.vhat;
   const int n = f.n, nh = f.nh, M = f.M, lg = f.logM;
-  const int64_t twon = 2 * (int64_t)n;
+  const int twon = 2 * n;
   C* row = a.phase + (int64_t)r * a.ldp;
   const int L = a.L;
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
-  auto chirp = [&](int k) -> C { return tab[(int)((2 * (int64_t)k * k) % twon)]; };
+  // e^{i pi (2 k^2 mod 2n) / n}; 2 k^2 < 2^31 for k < 2^15
+  auto chirp = [&](int k) -> C { return tab[(int)((2u * (unsigned)k * (unsigned)k) % (unsigned)twon)]; };
 
   if (MODE != 1) {
     auto fold = [&](int b) -> C {
+      // m = b + q n: e^{i pi s m / n} = tab[s (b + (q mod 2) n)]
       C h = mk((T)0, (T)0);
+      int u = f.shift ? b : 0;
+      const int du = f.shift ? n : 0;
       for (int m = b; m <= L; m += n) {
         const C F = row[m];
-        const C t = tab[(int)(((int64_t)f.shift * m) % twon)];
-        const C v = cmul(F, t);
+        const C v = cmul(F, tab[u]);
         const T w = (m == 0) ? (T)1 : (T)2;
         h.x = fma(w, v.x, h.x);
         h.y = fma(w, v.y, h.y);
+        u = (u + du < twon) ? u + du : u + du - twon;
       }
       return h;
     };
@@ -131,12 +228,12 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
       for (int k = nh + tid; k < M; k += NT) buf[k] = mk((T)0, (T)0);
     __syncthreads();
     if (!f.bluestein) {
-      fft_dit(buf, M, +1, a.tw, a.Mmax);
+      fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
     } else {
-      fft_dif(buf, M, -1, a.tw, a.Mmax);
+      fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
       for (int i = tid; i < M; i += NT) buf[i] = cmul(buf[i], vh[i]);
       __syncthreads();
-      fft_dit(buf, M, +1, a.tw, a.Mmax);
+      fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
       for (int t = tid; t < nh; t += NT) buf[t] = cmul(buf[t], chirp(t));
       __syncthreads();
     }
@@ -173,12 +270,12 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
 
   // forward length-nh DFT of z_t = y_{2t} + i y_{2t+1}
   if (!f.bluestein) {
-    fft_dif(buf, M, -1, a.tw, a.Mmax);  // Z'_k at buf[bitrev(k)]
+    fft_dif(buf, M, lg, -1, a.tw, a.Mmax);  // Z'_k at buf[bitrev(k)]
   } else {
-    fft_dif(buf, M, -1, a.tw, a.Mmax);
+    fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
     for (int i = tid; i < M; i += NT) buf[i] = cmul(buf[i], vh[i]);
     __syncthreads();
-    fft_dit(buf, M, +1, a.tw, a.Mmax);  // Z'_k = conj(buf[k] chirp(k))
+    fft_dit(buf, M, lg, +1, a.tw, a.Mmax);  // Z'_k = conj(buf[k] chirp(k))
   }
   auto getZ = [&](int k) -> C {
     return f.bluestein ? cconj(cmul(buf[k], chirp(k))) : buf[bitrev(k, lg)];
@@ -195,31 +292,41 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
   for (int m = tid; m <= L; m += NT) {
     const int b = m % n;
     const C Y = (b <= nh) ? Yhat(b) : cconj(Yhat(n - b));
-    const C t = tab[(int)(((int64_t)f.shift * m) % twon)];
+    const C t = tab[f.shift ? m % twon : 0];
     row[m] = cmul(Y, cconj(t));
   }
 }
 
+// One launch per FFT-size class (rings ordered by their FFT size M), each
+// with the shared memory and block size its rings need.
 template <typename T>
 int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st) {
   using C = typename Tr<T>::C;
-  const size_t smem = (size_t)a.Mmax * sizeof(C);
-  if (smem > 227 * 1024) return fail(CR_EINVAL, "ring FFT buffer exceeds shared memory");
-  switch (mode) {
-    case 0:
-      CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      { ring_fft_kernel<T, 0><<<a.nring, RF_NT, smem, st>>>(a); count_launch(); }
-      break;
-    case 1:
-      CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      { ring_fft_kernel<T, 1><<<a.nring, RF_NT, smem, st>>>(a); count_launch(); }
-      break;
-    default:
-      CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      { ring_fft_kernel<T, 2><<<a.nring, RF_NT, smem, st>>>(a); count_launch(); }
-      break;
+  for (int c = 0; c < a.nclass; ++c) {
+    const int M = a.cls_M[c];
+    const int cnt = a.cls_start[c + 1] - a.cls_start[c];
+    if (cnt <= 0) continue;
+    const size_t smem = (size_t)M * sizeof(C);
+    if (smem > 227 * 1024) return fail(CR_EINVAL, "ring FFT buffer exceeds shared memory");
+    const int nt = std::max(64, std::min(RF_NT, M / 8));
+    RingArgs<T> b = a;
+    b.rbase = a.cls_start[c];
+    switch (mode) {
+      case 0:
+        CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        { ring_fft_kernel<T, 0><<<cnt, nt, smem, st>>>(b); count_launch(); }
+        break;
+      case 1:
+        CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        { ring_fft_kernel<T, 1><<<cnt, nt, smem, st>>>(b); count_launch(); }
+        break;
+      default:
+        CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        { ring_fft_kernel<T, 2><<<cnt, nt, smem, st>>>(b); count_launch(); }
+        break;
+    }
+    CR_CHECK_LAUNCH("ring_fft_kernel");
   }
-  CR_CHECK_LAUNCH("ring_fft_kernel");
   return CR_OK;
 }
 template int launch_ring_fft<double>(const RingArgs<double>&, int, cudaStream_t);
@@ -265,7 +372,7 @@ __global__ void vhat_kernel(const LenDesc* lens, const double2* tab, const doubl
     buf[k] = (dd >= 0) ? cconj(tab[d.tab + (int)((2 * (int64_t)dd * dd) % twon)]) : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  fft_dif(buf, d.M, -1, tw, Mmax);
+  fft_dif(buf, d.M, d.logM, -1, tw, Mmax);
   for (int k = threadIdx.x; k < d.M; k += blockDim.x) vhat[d.vhat + k] = cscale(buf[k], 1.0 / d.M);
 }
 
@@ -345,6 +452,25 @@ int build_fft_tables(Grid& g, cudaStream_t st) {
   if (vhat_len > 0) to_f32_kernel<<<256, 256, 0, st>>>(g.d_vhat, g.d_vhat32, vhat_len);
   to_f32_kernel<<<64, 256, 0, st>>>(g.d_tw, g.d_tw32, Mmax / 2);
   CR_CHECK_LAUNCH("to_f32_kernel");
+  // rings ordered by FFT size; one launch class per distinct size
+  {
+    std::vector<int> order(g.fft.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return g.fft[x].M < g.fft[y].M; });
+    g.cls_M.clear();
+    g.cls_start.clear();
+    // sizes up to 1024 share one class (their shared memory is small anyway)
+    auto key = [&](int r) { return std::max(g.fft[r].M, std::min(1024, Mmax)); };
+    for (size_t i = 0; i < order.size(); ++i) {
+      if (g.cls_M.empty() || key(order[i]) != g.cls_M.back()) {
+        g.cls_M.push_back(key(order[i]));
+        g.cls_start.push_back((int)i);
+      }
+    }
+    g.cls_start.push_back((int)order.size());
+    CR_CUDA(cudaMalloc(&g.d_rings, order.size() * sizeof(int)));
+    CR_CUDA(cudaMemcpyAsync(g.d_rings, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   CR_CUDA(cudaMalloc(&g.d_fft, g.fft.size() * sizeof(RingFFT)));
   CR_CUDA(cudaMemcpyAsync(g.d_fft, g.fft.data(), g.fft.size() * sizeof(RingFFT), cudaMemcpyHostToDevice, st));
   CR_CUDA(cudaStreamSynchronize(st));
