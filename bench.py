@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG comparison on the Nside 256 workload")
     ap.add_argument("--ref-cycles", type=int, default=2,
                     help="cycles per realization priced by the reference arm (the GPU arm's measured count)")
     return ap.parse_args()
@@ -286,6 +287,35 @@ def roofline_of(stages, steps):
     return dict(base, bound="alu", achieved=None, peak=None, unit=None, frac=None)
 
 
+def cg_comparison(binding, synthetic, dev, stream, workload="nside256_lmax767"):
+    """The multi-level solver against diagonal-preconditioned CG (the method
+    the paper compares against) on the Nside 256 workload: iterations and
+    GPU time to a 1e-6 relative residual r^T S^-1 r / b^T S^-1 b < 1e-12."""
+    import torch
+
+    cfg, cl, bl, ninv = synthetic.problem_inputs(workload)
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        stream=stream, levels="default")
+    x_true = torch.from_numpy(synthetic.draw_prior(cl, index=7)).to(dev)
+    b = torch.empty_like(x_true)
+    plan.apply_A(x_true, b)
+    x = torch.empty_like(b)
+    out = {"workload": workload, "stop": "relative residual 1e-6 (r^T S^-1 r < 1e-12 b^T S^-1 b)"}
+    for name, mode, cap in [("multilevel_f64", binding.CR_F64 | binding.CR_PCG, 400),
+                            ("multilevel_mixed", binding.CR_MIXED | binding.CR_PCG, 400),
+                            ("cg_diag_f64", binding.CR_F64 | binding.CR_CG, 20000)]:
+        plan.solve(b, x, eps=1e-12, max_cycles=cap, mode=mode, check=False)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cyc, rel, hist, rc = plan.solve(b, x, eps=1e-12, max_cycles=cap, mode=mode, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"iterations": int(cyc[0]), "relres": float(rel[0]), "s": e0.elapsed_time(e1) * 1e-3,
+                     "converged": rc == 0}
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -412,6 +442,8 @@ def main():
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
 
+    cg_cmp = None if args.no_cg else cg_comparison(binding, synthetic, dev, stream)
+
     if rank != 0:
         return
     clocks = clk.summary()
@@ -438,6 +470,8 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
+    if cg_cmp is not None:
+        out["cg_comparison"] = cg_cmp
     if not args.no_cpu_baseline:
         levels = []
         for h in range(1, plan.nlevels() + 1):

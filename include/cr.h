@@ -69,6 +69,11 @@ extern "C" {
  * last cycle and the last history entry is NaN.  For timing a cycle count
  * found beforehand. */
 #define CR_FIXED 8
+/* solve flag: diagonal-preconditioned conjugate gradients on A instead of the
+ * multi-level cycle (the comparison method of Sections 1 and 2.4), FP64 only,
+ * needs no levels; max_cycles caps the CG iterations and cycles_out counts
+ * them (one FP64 A per iteration). */
+#define CR_CG 16
 
 /* grid kinds */
 #define CR_GRID_HEALPIX 0

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcrgb300.so")
 
 CR_OK = 0
-CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED = 0, 1, 2, 4, 8
+CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED, CR_CG = 0, 1, 2, 4, 8, 16
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0
 

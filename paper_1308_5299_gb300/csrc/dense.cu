@@ -263,33 +263,47 @@ __global__ void top_inv_from_complex_kernel(const double2* diag, const double* s
   }
 }
 
+// out_lm = hp_l / diag(A)_lm (0 where C_l = 0), diag(A) = 1/C_l + b_l^2 times
+// the Delta m = 0 ring-formula diagonal of Y^T N^-1 Y; out is device [n_lm].
+int inv_diag_A(cr_plan* P, const std::vector<double>& hpl, double* out) {
+  const int L = P->lmax;
+  const int64_t nlm = n_lm(L);
+  double *rs = nullptr, *hp = nullptr;
+  double2* diag = nullptr;
+  CR_CUDA(cudaMalloc(&rs, P->obs.nring * sizeof(double)));
+  { ring_sum_kernel<<<P->obs.nring, 256, 0, P->stream>>>(P->obs.d_fft, P->d_ninv, rs); count_launch(); }
+  CR_CHECK_LAUNCH("ring_sum_kernel");
+  CR_CUDA(cudaMalloc(&diag, nlm * sizeof(double2)));
+  int rc = launch_leg_diag(P, rs, diag);
+  if (!rc) {
+    CR_CUDA(cudaMalloc(&hp, (L + 1) * sizeof(double)));
+    CR_CUDA(cudaMemcpy(hp, hpl.data(), (L + 1) * sizeof(double), cudaMemcpyHostToDevice));
+    { top_inv_from_complex_kernel<<<L + 1, 128, 0, P->stream>>>(diag, P->d_sinv, P->d_bl, hp, L, out); count_launch(); }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "top_inv_kernel");
+  }
+  void* ptrs[] = {rs, hp, diag};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  return rc;
+}
+
 int build_top_diag(cr_plan* P, Hierarchy& Hh, const std::vector<double>& f1) {
   const int L = P->lmax;
   const int64_t nlm = n_lm(L);
-  double *rs = nullptr, *hp = nullptr, *out = nullptr;
-  double2* diag = nullptr;
-  int rc = CR_OK;
-  CR_CUDA(cudaMalloc(&rs, P->obs.nring * sizeof(double)));
-  ring_sum_kernel<<<P->obs.nring, 256, 0, P->stream>>>(P->obs.d_fft, P->d_ninv, rs);
-  CR_CHECK_LAUNCH("ring_sum_kernel");
-  CR_CUDA(cudaMalloc(&diag, nlm * sizeof(double2)));
-  rc = launch_leg_diag(P, rs, diag);
+  std::vector<double> h(L + 1);
+  for (int l = 0; l <= L; ++l) h[l] = 1.0 - (l < (int)f1.size() ? f1[l] : 0.0);
+  double* out = nullptr;
+  CR_CUDA(cudaMalloc(&out, nlm * sizeof(double)));
+  int rc = inv_diag_A(P, h, out);
   if (!rc) {
-    std::vector<double> h(L + 1);
-    for (int l = 0; l <= L; ++l) h[l] = 1.0 - (l < (int)f1.size() ? f1[l] : 0.0);
-    CR_CUDA(cudaMalloc(&hp, (L + 1) * sizeof(double)));
-    CR_CUDA(cudaMemcpy(hp, h.data(), (L + 1) * sizeof(double), cudaMemcpyHostToDevice));
-    CR_CUDA(cudaMalloc(&out, nlm * sizeof(double)));
-    top_inv_from_complex_kernel<<<L + 1, 128, 0, P->stream>>>(diag, P->d_sinv, P->d_bl, hp, L, out);
-    CR_CHECK_LAUNCH("top_inv_kernel");
     std::vector<double> hv(nlm);
-    CR_CUDA(cudaMemcpyAsync(hv.data(), out, nlm * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
-    CR_CUDA(cudaStreamSynchronize(P->stream));
-    rc = Hh.inv_diag_hp.upload(hv);
+    cudaError_t e = cudaMemcpy(hv.data(), out, nlm * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_fail(e, "top diag copy");
+    else rc = Hh.inv_diag_hp.upload(hv);
   }
-  void* ptrs[] = {rs, hp, out, diag};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  cudaFree(out);
   return rc;
 }
 

@@ -41,6 +41,9 @@ int build_bottom(cr_plan* P, Hierarchy& Hh);
 template <typename T> int bottom_solve(cr_plan* P, Hierarchy& Hh, const void* b, void* x);
 int bottom_matrix(cr_plan* P, double* host, int* nd);
 int build_top_diag(cr_plan* P, Hierarchy& Hh, const std::vector<double>& f1);
+int inv_diag_A(cr_plan* P, const std::vector<double>& hpl, double* out);
+int cg_solve(cr_plan* P, void* x, const void* b, double eps, int maxit, int* it_out, double* relres_out,
+             double* history);
 
 // solver.cu
 int build_hierarchy(cr_plan* P, const cr_params* p);

@@ -321,7 +321,8 @@ static void plan_free(cr_plan* P) {
     delete g;
   }
   void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_c2_32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
-                  P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial};
+                  P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial, P->d_pcinv, P->cgv[0], P->cgv[1],
+                  P->cgv[2], P->cgv[3], P->d_cgdot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

@@ -143,5 +143,9 @@ struct cr_plan {
   cr::Timing timing;
   cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)
   void* hier_tile_work = nullptr;     // FP32 tile-ordered smoother work vector
+  // diagonal-preconditioned CG (created on first use)
+  double* d_pcinv = nullptr;          // [n_lm] 1 / diag(A), 0 where C_l = 0
+  void* cgv[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* d_cgdot = nullptr;
   std::vector<double> h_cl, h_bl;
 };

@@ -730,6 +730,19 @@ int cr_wcycle(cr_plan* plan, void* x, const void* b, int nrhs, int dtype) {
 
 int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int max_cycles, int mode, int* cycles_out,
              double* relres_out, double* history) {
+  if (plan && (mode & CR_CG)) {
+    if (!plan->has_op) return fail(CR_EINVAL, "cr_solve: CG needs a plan created with C_l");
+    if ((mode & 3) != CR_F64) return fail(CR_EINVAL, "cr_solve: CG runs in FP64 (CR_F64)");
+    if (max_cycles < 1 || !(eps >= 0.0)) return fail(CR_EINVAL, "cr_solve: eps / max_cycles");
+    const int64_t nlm = n_lm(plan->lmax);
+    for (int i = 0; i < nrhs; ++i) {
+      int rc = cg_solve(plan, (char*)x + i * nlm * sizeof(double2), (const char*)b + i * nlm * sizeof(double2), eps,
+                        max_cycles, cycles_out ? cycles_out + i : nullptr, relres_out ? relres_out + i : nullptr,
+                        history ? history + (int64_t)i * max_cycles : nullptr);
+      if (rc) return rc;
+    }
+    return CR_OK;
+  }
   int rc = check_hier(plan, "cr_solve");
   if (rc) return rc;
   if ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) return fail(CR_EINVAL, "cr_solve: mode precision must be CR_F64 or CR_MIXED");
