@@ -173,6 +173,24 @@ int cr_plan_create(cr_plan** out, const cr_params* p);
  * range). */
 int cr_plan_level_grid(const cr_plan* plan, int h, int* kind, int* nring, int64_t* npix);
 
+/*
+ * Right-hand side of the CR system (Section 2.3, Eq. system-explicit and the
+ * constrained-realization construction it cites):
+ *   b = B Y^T N^-1 d + S^-1/2 omega_1 + B Y^T N^-1/2 omega_2
+ * with omega_1 ~ N(0, I) in the real orthonormal coefficient basis and
+ * omega_2 ~ N(0, I) per pixel (N^-1/2 = 0 under the mask); without
+ * CR_DRAW_FLUCT only the Wiener-filter term is formed.  d: device FP64
+ * [nrhs][npix] RING map, or NULL for d = 0.  b: device FP64 complex
+ * [nrhs][N_lm(lmax)], overwritten (0 at C_l = 0, Im a_l0 = 0).  Normals come
+ * from Philox4x32-10 (Salmon et al. 2011) keyed by `seed`: element k of
+ * stream s (3 = omega_1 at k = 2 i + part of coefficient i, 4 = omega_2 at
+ * pixel k) for right-hand side j uses counter (k >> 2, k >> 34, s, j) and
+ * Box-Muller slot k & 3.  Allocates one FP64 map for the call; synchronous.
+ * Errors: CR_EINVAL (no C_l in the plan, bad flag), CR_ECUDA.
+ */
+#define CR_DRAW_FLUCT 1
+int cr_draw(cr_plan* plan, uint64_t seed, const void* d, void* b, int nrhs, int flags);
+
 /* Release every resource of the plan (NULL is accepted). */
 int cr_plan_destroy(cr_plan* plan);
 

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libcrgb300.so")
 
 CR_OK = 0
 CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED, CR_CG = 0, 1, 2, 4, 8, 16
+CR_DRAW_FLUCT = 1
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0
 
@@ -81,6 +82,8 @@ _SIGS = {
     "cr_plan_set_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_launch_count": ([], ctypes.c_long),
     "cr_plan_nlevels": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cr_draw": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+                ctypes.c_int),
     "cr_plan_level_grid": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cr_plan_level": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -299,6 +302,17 @@ class Plan:
                                    fl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(ridge),
                                    ctypes.byref(lam)))
         return dict(nside_h=ns.value, lmax_h=lm.value, n_rec=nr.value, fl=fl, ridge=ridge.value, lambda_max=lam.value)
+
+    def draw(self, seed, b, d=None, fluct=True):
+        """Right-hand side b = B Y^T N^-1 d (+ S^-1/2 w1 + B Y^T N^-1/2 w2 with
+        fluct) for every right-hand side j of b ([nrhs, N_lm] complex128);
+        d: float64 CUDA map(s) [nrhs, npix] or None."""
+        nrhs = self._nrhs(b, n_lm(self.lmax))
+        if d is not None and not (d.is_cuda and d.dtype == torch.float64):
+            raise ValueError("d must be a float64 CUDA tensor")
+        _check(lib().cr_draw(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, None if d is None else _dev(d), _dev(b), nrhs,
+                             CR_DRAW_FLUCT if fluct else 0))
+        return b
 
     def level_grid(self, h):
         """(kind, nring, npix) of the grid on which pixel level h applies its
