@@ -191,6 +191,36 @@ int cr_plan_level_grid(const cr_plan* plan, int h, int* kind, int* nring, int64_
 #define CR_DRAW_FLUCT 1
 int cr_draw(cr_plan* plan, uint64_t seed, const void* d, void* b, int nrhs, int flags);
 
+/*
+ * Gradient contractions for differentiating the solve of Section 2.3 (A is
+ * symmetric, so the adjoint lambda = A^-1 g is another CR-Solve).
+ * cr_grad_cl: out[l] = alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l for
+ *   l = 0..lmax (0 where C_l = 0), <.,.>_l the real inner product restricted
+ *   to multipole l and w1 the constrained-realization normals of cr_draw
+ *   (seed, right-hand side rhs) in complex storage.  u, v: device FP64
+ *   complex [N_lm] (v may be NULL: its term is 0); out: device FP64 [lmax+1].
+ *   A realization x = A^-1 b with loss gradient g uses (u, v) = (A^-1 g, x),
+ *   alpha = 1, beta = -1/2; the Wiener-filter data term uses u = v = A^-1 b,
+ *   alpha = 1/2, beta = 0.
+ * cr_grad_ninv: out_i = alpha p_i q_i + p_i (gamma d_i + delta w2_i / sqrt n_i)
+ *   + eps d_i^2 with p = Y B u, q = Y B v synthesised in FP64, w2 the pixel
+ *   normals of cr_draw, n the plan's N^-1 (the w2 term only where n_i > 0);
+ *   d: device FP64 [npix] or NULL; out: device FP64 [npix].  Realization:
+ *   alpha = -1, gamma = 1, delta = 1/2, eps = 0; Wiener-filter data term:
+ *   u = v = A^-1 b, alpha = -1/2, gamma = 1, delta = 0, eps = -1/2.
+ *   Allocates two FP64 maps for the call.
+ * cr_map_wdot: *out = sum_i n_i a_i b_i (host result; a, b device FP64 maps).
+ * cr_alm_dot: *out = <u, v> (real inner product, S^-1-weighted if weighted).
+ * All synchronous.  Errors: CR_EINVAL (null pointers, plan without C_l),
+ * CR_ECUDA.
+ */
+int cr_grad_cl(cr_plan* plan, const void* u, const void* v, double alpha, double beta, uint64_t seed, int rhs,
+               double* out);
+int cr_grad_ninv(cr_plan* plan, const void* u, const void* v, const double* d, double alpha, double gamma,
+                 double delta, double eps, uint64_t seed, int rhs, double* out);
+int cr_map_wdot(cr_plan* plan, const double* a, const double* b, double* out);
+int cr_alm_dot(cr_plan* plan, const void* u, const void* v, int weighted, double* out);
+
 /* Release every resource of the plan (NULL is accepted). */
 int cr_plan_destroy(cr_plan* plan);
 

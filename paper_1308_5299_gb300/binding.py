@@ -82,6 +82,15 @@ _SIGS = {
     "cr_plan_set_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_launch_count": ([], ctypes.c_long),
     "cr_plan_nlevels": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cr_grad_cl": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                    ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "cr_grad_ninv": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
+                      ctypes.c_void_p], ctypes.c_int),
+    "cr_map_wdot": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
+                    ctypes.c_int),
+    "cr_alm_dot": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_draw": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
                 ctypes.c_int),
     "cr_plan_level_grid": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -229,6 +238,7 @@ class Plan:
         self._h = h
         self.lmax = int(lmax)
         self._keep = []
+        self.npix = self.sizes()["npix"]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -313,6 +323,34 @@ class Plan:
         _check(lib().cr_draw(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, None if d is None else _dev(d), _dev(b), nrhs,
                              CR_DRAW_FLUCT if fluct else 0))
         return b
+
+    def grad_cl(self, u, v, alpha, beta, seed=0, rhs=0, out=None):
+        """out[l] = alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l (cr_grad_cl)."""
+        if out is None:
+            out = torch.empty(self.lmax + 1, dtype=torch.float64, device=u.device)
+        _check(lib().cr_grad_cl(self._h, _dev(u), None if v is None else _dev(v), float(alpha), float(beta),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF, int(rhs), _dev(out)))
+        return out
+
+    def grad_ninv(self, u, v, d, alpha, gamma, delta, eps, seed=0, rhs=0, out=None):
+        """out_i = alpha p_i q_i + p_i (gamma d_i + delta w2_i / sqrt n_i) + eps d_i^2,
+        p = Y B u, q = Y B v (cr_grad_ninv)."""
+        if out is None:
+            out = torch.empty(self.npix, dtype=torch.float64, device=u.device)
+        _check(lib().cr_grad_ninv(self._h, _dev(u), _dev(v), None if d is None else _dev(d), float(alpha),
+                                  float(gamma), float(delta), float(eps), int(seed) & 0xFFFFFFFFFFFFFFFF, int(rhs),
+                                  _dev(out)))
+        return out
+
+    def map_wdot(self, a, b):
+        out = ctypes.c_double()
+        _check(lib().cr_map_wdot(self._h, _dev(a), _dev(b), ctypes.byref(out)))
+        return out.value
+
+    def alm_dot(self, u, v, weighted=False):
+        out = ctypes.c_double()
+        _check(lib().cr_alm_dot(self._h, _dev(u), _dev(v), int(bool(weighted)), ctypes.byref(out)))
+        return out.value
 
     def level_grid(self, h):
         """(kind, nring, npix) of the grid on which pixel level h applies its
