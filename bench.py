@@ -269,7 +269,7 @@ def roofline_of(stages, steps):
     flops 8 per ring pair and (l, m)), ring-FFT stages and the pixel smoother
     against the measured HBM copy bandwidth (algorithmic bytes)."""
     peaks = measured_peaks()
-    kern = {k: v for k, v in stages.items() if k not in COMPOSITE}
+    kern = {k: v for k, v in stages.items() if k not in COMPOSITE and "." not in k}
     dom = max(kern, key=lambda k: kern[k][0])
     ms, n, work = kern[dom]
     base = {"kernel": dom, "ms_per_step": ms / steps, "launches_per_step": n / steps,
@@ -466,6 +466,7 @@ def main():
         "e2e": {"value": e2e_s, "unit": "s/realization", "h2d_bytes_per_step": int(bh.numel() * 16),
                 "d2h_bytes_per_step": int(xh.numel() * 16)},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "stages_work_per_step": {k: v[2] / args.steps for k, v in stages.items() if v[2] > 0},
         "roofline": roofline_of(stages, args.steps),
         "clocks": clocks,
         "gpu_launches": int(launches),

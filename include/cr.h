@@ -153,6 +153,12 @@ typedef struct cr_params {
    * most half the observation grid's rings, 1 = on for every pixel level,
    * -1 = off. */
   int gl_downgrade;
+  /* fp64_df: 1 = evaluate the FP64 Legendre stages (FP64 transforms, FP64
+   * A, the outer residual of CR_MIXED) in double-float arithmetic on the
+   * FP32 pipes -- pairs of floats with error-free sums and products, about
+   * 2^-44 relative per operation -- which GB300 runs several times faster
+   * than native FP64; 0 = native FP64. */
+  int fp64_df;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */

@@ -59,6 +59,7 @@ class cr_params(ctypes.Structure):
         ("ridge_alpha", ctypes.POINTER(ctypes.c_double)),
         ("ridge_lambda_target", ctypes.c_double),
         ("gl_downgrade", ctypes.c_int),
+        ("fp64_df", ctypes.c_int),
     ]
 
 
@@ -176,7 +177,7 @@ class Plan:
 
     def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
                  lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0,
-                 gl_downgrade=0):
+                 gl_downgrade=0, fp64_df=False):
         """levels: None (transforms and A only), "default" (the library's level
         table), or a list of dicts with nside_h, lmax_h, n_rec and fl
         (cumulative filter, length lmax+1).  gl_downgrade: 0 auto, 1 every
@@ -229,6 +230,7 @@ class Plan:
         p.ridge_bisections = int(ridge_bisections)
         p.ridge_lambda_target = float(ridge_lambda_target)
         p.gl_downgrade = int(gl_downgrade)
+        p.fp64_df = int(bool(fp64_df))
         if ridge_alpha is not None:
             ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
             self._keep.append(ra)

@@ -57,6 +57,8 @@ struct PixLevel {
   // device
   float* d_A = nullptr;    // A_hat blocks
   float* d_L = nullptr;    // factor blocks (diagonal blocks hold inv(L_pp))
+  float* d_LT = nullptr;   // backward-sweep copy: per position p, column p's blocks transposed, then inv(L_pp)^T
+  bool lt_valid = false;
   int* d_perm = nullptr;   // tile-ordered level pixel -> RING index
   int64_t* d_row_ptr = nullptr;
   int* d_row_col = nullptr;

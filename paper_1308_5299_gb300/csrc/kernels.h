@@ -24,6 +24,9 @@ struct LegArgs {
   int npolar = 0;          // pairs [0, npolar) use the polar form z Q = Q - w Q
   const int* ls = nullptr;                 // [m][pair] start l (start tables)
   const typename Tr<T>::C* st = nullptr;   // [m][pair] recurrence state at the start
+  int df = 0;                              // FP64 stages in double-float arithmetic (legendre_df.cu)
+  const int* ls_df = nullptr;              // double-float start l (FP32 threshold) and FP64 state there
+  const double2* st_df = nullptr;
   int ld_seed = 0;
   int npairs = 0, nring = 0;
   typename Tr<T>::C* partial = nullptr;    // adjoint: [nblk][n_lm(L)]
@@ -69,6 +72,9 @@ struct RingArgs {
 template <typename T> int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st);
 template <typename T> int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream_t st);
 int leg_partial_blocks(int npairs);
+int df_pair_blocks(int npairs);
+int launch_leg_synth_df(const LegArgs<double>& a, cudaStream_t st);
+int launch_leg_adjoint_df(const LegArgs<double>& a, int* nblk, cudaStream_t st);
 int launch_leg_diag(cr_plan* P, const double* ringval, double2* out);
 template <typename T> int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st);
 

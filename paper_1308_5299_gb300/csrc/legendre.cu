@@ -434,6 +434,8 @@ static inline void pair_blocks(int npolar, int npairs, int* nbp, int* nbe) {
 template <typename T>
 int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st) {
   if (a.L < 0) return CR_OK;
+  if constexpr (sizeof(T) == 8)
+    if (a.df) return launch_leg_synth_df(a, st);
   int nbp, nbe;
   pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
   if (nbp) { leg_synth_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
@@ -445,11 +447,21 @@ int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st) {
 template <typename T>
 int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream_t st) {
   if (a.L < 0) return CR_OK;
-  int nbp, nbe;
-  pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
-  if (nbp) { leg_adjoint_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { leg_adjoint_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
-  CR_CHECK_LAUNCH("leg_adjoint_kernel");
+  int nbp = 0, nbe = 0;
+  bool done = false;
+  if constexpr (sizeof(T) == 8) {
+    if (a.df) {
+      int rc = launch_leg_adjoint_df(a, &nbe, st);
+      if (rc) return rc;
+      done = true;
+    }
+  }
+  if (!done) {
+    pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
+    if (nbp) { leg_adjoint_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_adjoint_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    CR_CHECK_LAUNCH("leg_adjoint_kernel");
+  }
   FinalizeArgs<T> ff = f;
   ff.partial = a.partial;
   ff.nblk = nbp + nbe;
@@ -498,7 +510,7 @@ int launch_leg_diag(cr_plan* P, const double* ringval, double2* out) {
 // recurrence from the seed P~_mm up to the first l with |P~_lm| >= tau.
 __global__ void start_kernel(const double* z, const double* seed, const int* lev, int ld, const double* c,
                              const double* s, int Lc, int Lseed, int npairs, int npolar32, int* ls64,
-                             double2* st64, int* ls32, float2* st32) {
+                             double2* st64, int* ls32, float2* st32, double2* st64b) {
   const int m = blockIdx.y;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npairs) return;
@@ -511,7 +523,7 @@ __global__ void start_kernel(const double* z, const double* seed, const int* lev
   double q1 = 0.0, q2 = -seed[o];
   int e = lev[o];
   int f64 = Lseed + 1, f32 = Lseed + 1;
-  double2 s64 = make_double2(0.0, 0.0);
+  double2 s64 = make_double2(0.0, 0.0), s64b = make_double2(0.0, 0.0);
   float2 s32 = make_float2(0.f, 0.f);
   for (int l = m; l <= Lseed; ++l) {
     const double q = c[offc + (l - m)] * zz * q1 - q2;
@@ -524,6 +536,7 @@ __global__ void start_kernel(const double* z, const double* seed, const int* lev
       if (pv >= tau32) {  // tau32 > tau64: the FP32 start comes last
         f32 = l;
         s32 = (p < npolar32) ? make_float2((float)q1, (float)(q1 - q2)) : make_float2((float)q1, (float)q2);
+        s64b = make_double2(q1, q2);
         break;
       }
     }
@@ -539,13 +552,14 @@ __global__ void start_kernel(const double* z, const double* seed, const int* lev
   st64[o] = s64;
   ls32[o] = f32;
   st32[o] = s32;
+  st64b[o] = s64b;
 }
 
 int build_start_tables(cr_plan* P, Grid& g) {
   const int Ls = g.Lseed;
   if (Ls < 0) return CR_OK;
   if (Ls > P->Lcoef) return fail(CR_EINVAL, "start tables: grid band limit above the recurrence tables");
-  void* ptrs[] = {g.d_ls64, g.d_st64, g.d_ls32, g.d_st32};
+  void* ptrs[] = {g.d_ls64, g.d_st64, g.d_ls32, g.d_st32, g.d_st64b};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   const int64_t n = (int64_t)(Ls + 1) * g.npairs;
@@ -553,17 +567,22 @@ int build_start_tables(cr_plan* P, Grid& g) {
   CR_CUDA(cudaMalloc(&g.d_st64, n * sizeof(double2)));
   CR_CUDA(cudaMalloc(&g.d_ls32, n * sizeof(int)));
   CR_CUDA(cudaMalloc(&g.d_st32, n * sizeof(float2)));
+  CR_CUDA(cudaMalloc(&g.d_st64b, n * sizeof(double2)));
   dim3 grid((g.npairs + 127) / 128, Ls + 1);
   { start_kernel<<<grid, 128, 0, P->stream>>>(g.d_z, g.d_seed, g.d_lev, g.npairs, P->d_c, P->d_s, P->Lcoef, Ls,
-                                               g.npairs, g.npolar32, g.d_ls64, g.d_st64, g.d_ls32, g.d_st32);
+                                               g.npairs, g.npolar32, g.d_ls64, g.d_st64, g.d_ls32, g.d_st32,
+                                               g.d_st64b);
     count_launch(); }
   CR_CHECK_LAUNCH("start_kernel");
   CR_CUDA(cudaStreamSynchronize(P->stream));
   return CR_OK;
 }
 
-// upper bound on the partial rows of the adjoint (polar and equatorial ranges)
-int leg_partial_blocks(int npairs) { return (npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP) + 1; }
+// upper bound on the partial rows of the adjoint: the polar and equatorial
+// ranges of LEG_NT * LEG_RP pairs, or the double-float kernels' blocks
+int leg_partial_blocks(int npairs) {
+  return std::max((npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP) + 1, df_pair_blocks(npairs));
+}
 
 template int launch_leg_synth<double>(const LegArgs<double>&, cudaStream_t);
 template int launch_leg_synth<float>(const LegArgs<float>&, cudaStream_t);

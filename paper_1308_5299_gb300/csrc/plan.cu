@@ -216,7 +216,7 @@ int grid_upload(Grid& g, int Lseed, cudaStream_t st) {
 void grid_free(Grid& g) {
   void* ptrs[] = {g.d_z, g.d_z32, g.d_w32, g.d_sth, g.d_fft, g.d_tab, g.d_tab32, g.d_vhat, g.d_vhat32,
                   g.d_tw, g.d_tw32, g.d_seed, g.d_lev, g.d_seed32, g.d_lev32, g.d_ls64, g.d_st64, g.d_ls32,
-                  g.d_st32, g.d_rings};
+                  g.d_st32, g.d_st64b, g.d_rings};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -281,7 +281,7 @@ int rebuild_coef(cr_plan* P, int Lc) {
 // Legendre seeds of a grid for a larger band limit.
 int grid_reseed(Grid& g, int Lseed, cudaStream_t st) {
   CR_CUDA(cudaStreamSynchronize(st));
-  void* ptrs[] = {g.d_seed, g.d_lev, g.d_seed32, g.d_lev32, g.d_ls64, g.d_st64, g.d_ls32, g.d_st32};
+  void* ptrs[] = {g.d_seed, g.d_lev, g.d_seed32, g.d_lev32, g.d_ls64, g.d_st64, g.d_ls32, g.d_st32, g.d_st64b};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   g.d_seed = nullptr;
@@ -292,6 +292,7 @@ int grid_reseed(Grid& g, int Lseed, cudaStream_t st) {
   g.d_st64 = nullptr;
   g.d_ls32 = nullptr;
   g.d_st32 = nullptr;
+  g.d_st64b = nullptr;
   return build_seeds(g, Lseed, st);
 }
 
@@ -347,6 +348,9 @@ static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
     a.ls = g.d_ls64;
     a.st = g.d_st64;
     a.npolar = 0;
+    a.df = P->fp64_df;
+    a.ls_df = g.d_ls32;
+    a.st_df = g.d_st64b;
   } else {
     a.c = P->d_c32;
     a.c2 = P->d_c2_32;
@@ -529,6 +533,7 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   }
   P->p = *p;
   P->stream = reinterpret_cast<cudaStream_t>(p->stream);
+  P->fp64_df = p->fp64_df ? 1 : 0;
   P->lmax = p->lmax;
   P->levels.resize(1);
   P->levels[0].lmax_h = p->lmax;

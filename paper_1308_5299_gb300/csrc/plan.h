@@ -64,6 +64,7 @@ struct Grid {
   double2* d_st64 = nullptr;
   int* d_ls32 = nullptr;
   float2* d_st32 = nullptr;
+  double2* d_st64b = nullptr;  // FP64 state at the FP32 start (double-float kernels)
 };
 
 // Scratch sizes for transforms at band limit L on a grid.
@@ -141,6 +142,7 @@ struct cr_plan {
   float* d_ninv32 = nullptr;
   cr::Workspace ws;
   cr::Timing timing;
+  int fp64_df = 0;  // FP64 Legendre stages in double-float arithmetic
   cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)
   void* hier_tile_work = nullptr;     // FP32 tile-ordered smoother work vector
   // diagonal-preconditioned CG (created on first use)

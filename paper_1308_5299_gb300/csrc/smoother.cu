@@ -20,6 +20,7 @@
 #include <iterator>
 #include <vector>
 
+
 #include "common.cuh"
 #include "hier.h"
 #include "kernels.h"
@@ -332,66 +333,204 @@ __global__ void __launch_bounds__(SM_NT) icc_colour_kernel(IccArgs a, int p0) {
 // ---------------------------------------------------------------------------
 // triangular solves.  y is the tile-ordered work vector (FP32).
 
-template <typename T>
-__global__ void __launch_bounds__(TK) fwd_colour_kernel(const float* L, const int64_t* row_ptr, const int* row_col,
-                                                        const int* perm, const T* map_in, float* y, int p0) {
-  const int p = p0 + blockIdx.x;
-  const int i = threadIdx.x;
-  __shared__ float ys[TK], ts[TK];
-  float t = (float)map_in[perm[(int64_t)p * TK + i]];
-  const int64_t b0 = row_ptr[p], b1 = row_ptr[p + 1] - 1;  // last block is the diagonal
-  for (int64_t b = b0; b < b1; ++b) {
-    const int q = row_col[b];
-    __syncthreads();
-    ys[i] = y[(int64_t)q * TK + i];
-    __syncthreads();
-    const float* B = L + b * TK * TK;
-    float s = 0.f;
+// Triangular solves of one colour (tiles of a colour are independent).  One
+// CTA of 64 threads per tile: thread (rq, jg) = (tid & 15, tid >> 4) owns rows
+// 4 rq .. 4 rq + 3 and the column group j = 16 jg .. 16 jg + 15 of every
+// 64 x 64 block, read as float4 rows of the column-major block (coalesced);
+// the neighbours' vectors are staged once, the four column groups are summed
+// through shared memory.  The diagonal block holds inv(L_pp).
+// Forward: y_p = inv(L_pp) (r_p - sum_{q<p} L_pq y_q), blocks of row p.
+// Backward: x_p = inv(L_pp)^T (y_p - sum_{u>p} L_up^T x_u), using the
+// transposed copies of column p's blocks (LT, built after factorisation).
+__device__ __forceinline__ float4 f4fma(float4 a, float s, float4 c) {
+  c.x = fmaf(a.x, s, c.x);
+  c.y = fmaf(a.y, s, c.y);
+  c.z = fmaf(a.z, s, c.z);
+  c.w = fmaf(a.w, s, c.w);
+  return c;
+}
+
+// acc(rows 4 rq..) = sum_k sum_{j in group} B_k(:, j) v_k[j]
+__device__ __forceinline__ float4 block_gemv(const float* __restrict__ B, const float* __restrict__ v, int rq,
+                                             int jg, float4 acc) {
+  const float4* B4 = reinterpret_cast<const float4*>(B);
 #pragma unroll 8
-    for (int j = 0; j < TK; ++j) s = fmaf(B[j * TK + i], ys[j], s);
-    t -= s;
+  for (int jj = 0; jj < 16; ++jj) {
+    const int j = jg * 16 + jj;
+    acc = f4fma(__ldg(B4 + j * (TK / 4) + rq), v[j], acc);
   }
-  ts[i] = t;
+  return acc;
+}
+
+// sum the four column groups' partials: row i of the result
+__device__ __forceinline__ float reduce_groups(float4 acc, float4 (*part)[16], int rq, int jg, int tid) {
+  part[jg][rq] = acc;
   __syncthreads();
-  const float* D = L + b1 * TK * TK;
+  const int r = tid >> 2, e = tid & 3;  // thread tid returns row tid: quad tid >> 2, lane tid & 3
   float s = 0.f;
-#pragma unroll 8
-  for (int j = 0; j < TK; ++j) s = fmaf(D[j * TK + i], ts[j], s);
-  y[(int64_t)p * TK + i] = s;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const float4 v = part[g][r];
+    s += (e == 0) ? v.x : (e == 1) ? v.y : (e == 2) ? v.z : v.w;
+  }
+  __syncthreads();
+  return s;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TK) bwd_colour_kernel(const float* L, const int64_t* row_ptr, const int64_t* col_ptr,
-                                                        const int* col_row, const int64_t* col_blk, const int* perm,
-                                                        float* y, T* map_out, int p0) {
-  const int p = p0 + blockIdx.x;
-  const int i = threadIdx.x;
-  __shared__ float xs[TK], ts[TK];
-  __shared__ float Bs[TK][TK + 1];
-  float t = y[(int64_t)p * TK + i];
-  for (int64_t c = col_ptr[p]; c < col_ptr[p + 1]; ++c) {
-    const int u = col_row[c];
-    const float* B = L + col_blk[c] * TK * TK;
-    __syncthreads();
-    xs[i] = y[(int64_t)u * TK + i];
-    for (int j = 0; j < TK; ++j) Bs[j][i] = B[j * TK + i];  // Bs[col][row]
-    __syncthreads();
-    float s = 0.f;
-#pragma unroll 8
-    for (int r = 0; r < TK; ++r) s = fmaf(Bs[i][r], xs[r], s);  // (B^T x)_i = sum_r B[r][i] x_r
-    t -= s;
-  }
-  const int64_t bd = row_ptr[p + 1] - 1;
-  const float* D = L + bd * TK * TK;
+__device__ __forceinline__ void fwd_tile(const float* L, const int64_t* row_ptr, const int* row_col, const int* perm,
+                                         const T* map_in, float* y, int p) {
+  const int tid = threadIdx.x, rq = tid & 15, jg = tid >> 4;
+  __shared__ float vs[8][TK];
+  __shared__ float ts[TK];
+  __shared__ float4 part[4][16];
+  const int64_t b0 = row_ptr[p];
+  const int nb = (int)(row_ptr[p + 1] - 1 - b0);  // lower blocks; the last one is the diagonal
+  const float r = (float)map_in[perm[(int64_t)p * TK + tid]];
+  for (int k = 0; k < nb; ++k) vs[k][tid] = y[(int64_t)row_col[b0 + k] * TK + tid];
   __syncthreads();
-  ts[i] = t;
-  for (int j = 0; j < TK; ++j) Bs[j][i] = D[j * TK + i];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < nb; ++k) acc = block_gemv(L + (b0 + k) * TK * TK, vs[k], rq, jg, acc);
+  ts[tid] = r - reduce_groups(acc, part, rq, jg, tid);
+  __syncthreads();
+  acc = block_gemv(L + (b0 + nb) * TK * TK, ts, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
+  y[(int64_t)p * TK + tid] = reduce_groups(acc, part, rq, jg, tid);
+}
+
+template <typename T>
+__device__ __forceinline__ void bwd_tile(const float* LT, const int64_t* col_ptr, const int* col_row, const int* perm,
+                                         float* y, T* map_out, int p) {
+  const int tid = threadIdx.x, rq = tid & 15, jg = tid >> 4;
+  __shared__ float vs[8][TK];
+  __shared__ float ts[TK];
+  __shared__ float4 part[4][16];
+  const int64_t c0 = col_ptr[p];
+  const int nc = (int)(col_ptr[p + 1] - c0);
+  const float t = y[(int64_t)p * TK + tid];
+  for (int k = 0; k < nc; ++k) vs[k][tid] = y[(int64_t)col_row[c0 + k] * TK + tid];
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* Lp = LT + (c0 + p) * TK * TK;  // column p's transposed blocks, then inv(L_pp)^T
+  for (int k = 0; k < nc; ++k) acc = block_gemv(Lp + (int64_t)k * TK * TK, vs[k], rq, jg, acc);
+  ts[tid] = t - reduce_groups(acc, part, rq, jg, tid);
+  __syncthreads();
+  acc = block_gemv(Lp + (int64_t)nc * TK * TK, ts, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
+  const float s = reduce_groups(acc, part, rq, jg, tid);
+  y[(int64_t)p * TK + tid] = s;
+  map_out[perm[(int64_t)p * TK + tid]] = (T)s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TK) fwd_colour_kernel(const float* L, const int64_t* row_ptr, const int* row_col,
+                                                        const int* perm, const T* map_in, float* y, int p0) {
+  fwd_tile<T>(L, row_ptr, row_col, perm, map_in, y, p0 + blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TK) bwd_colour_kernel(const float* LT, const int64_t* col_ptr, const int* col_row,
+                                                        const int* perm, float* y, T* map_out, int p0) {
+  bwd_tile<T>(LT, col_ptr, col_row, perm, y, map_out, p0 + blockIdx.x);
+}
+
+// Coarse levels have few tiles per colour, so a colour's latency, not HBM,
+// bounds the sweep: there each tile gets 256 threads (16 column groups of 4
+// columns), which cuts every thread's chain of dependent loads by four.
+constexpr int TKW = 256;
+
+__device__ __forceinline__ float4 block_gemv_w(const float* __restrict__ B, const float* __restrict__ v, int rq,
+                                               int jg, float4 acc) {
+  const float4* B4 = reinterpret_cast<const float4*>(B);
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int j = jg * 4 + jj;
+    acc = f4fma(__ldg(B4 + j * (TK / 4) + rq), v[j], acc);
+  }
+  return acc;
+}
+
+// rows of the result for threads tid < 64 (sum of the 16 column groups)
+__device__ __forceinline__ float reduce_groups_w(float4 acc, float4 (*part)[16], int rq, int jg, int tid) {
+  part[jg][rq] = acc;
   __syncthreads();
   float s = 0.f;
-#pragma unroll 8
-  for (int r = 0; r < TK; ++r) s = fmaf(Bs[i][r], ts[r], s);
-  y[(int64_t)p * TK + i] = s;
-  map_out[perm[(int64_t)p * TK + i]] = (T)s;
+  if (tid < TK) {
+    const int r = tid >> 2, e = tid & 3;
+#pragma unroll
+    for (int g = 0; g < 16; ++g) {
+      const float4 v = part[g][r];
+      s += (e == 0) ? v.x : (e == 1) ? v.y : (e == 2) ? v.z : v.w;
+    }
+  }
+  __syncthreads();
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TKW) fwd_colour_w_kernel(const float* L, const int64_t* row_ptr, const int* row_col,
+                                                           const int* perm, const T* map_in, float* y, int p0) {
+  const int p = p0 + blockIdx.x;
+  const int tid = threadIdx.x, rq = tid & 15, jg = tid >> 4;
+  __shared__ float vs[8][TK];
+  __shared__ float ts[TK];
+  __shared__ float4 part[16][16];
+  const int64_t b0 = row_ptr[p];
+  const int nb = (int)(row_ptr[p + 1] - 1 - b0);
+  for (int e = tid; e < nb * TK; e += TKW) vs[e / TK][e % TK] = y[(int64_t)row_col[b0 + e / TK] * TK + (e % TK)];
+  const float r = (tid < TK) ? (float)map_in[perm[(int64_t)p * TK + tid]] : 0.f;
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < nb; ++k) acc = block_gemv_w(L + (b0 + k) * TK * TK, vs[k], rq, jg, acc);
+  const float s1 = reduce_groups_w(acc, part, rq, jg, tid);
+  if (tid < TK) ts[tid] = r - s1;
+  __syncthreads();
+  acc = block_gemv_w(L + (b0 + nb) * TK * TK, ts, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
+  const float s2 = reduce_groups_w(acc, part, rq, jg, tid);
+  if (tid < TK) y[(int64_t)p * TK + tid] = s2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TKW) bwd_colour_w_kernel(const float* LT, const int64_t* col_ptr, const int* col_row,
+                                                           const int* perm, float* y, T* map_out, int p0) {
+  const int p = p0 + blockIdx.x;
+  const int tid = threadIdx.x, rq = tid & 15, jg = tid >> 4;
+  __shared__ float vs[8][TK];
+  __shared__ float ts[TK];
+  __shared__ float4 part[16][16];
+  const int64_t c0 = col_ptr[p];
+  const int nc = (int)(col_ptr[p + 1] - c0);
+  for (int e = tid; e < nc * TK; e += TKW) vs[e / TK][e % TK] = y[(int64_t)col_row[c0 + e / TK] * TK + (e % TK)];
+  const float t = (tid < TK) ? y[(int64_t)p * TK + tid] : 0.f;
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* Lp = LT + (c0 + p) * TK * TK;
+  for (int k = 0; k < nc; ++k) acc = block_gemv_w(Lp + (int64_t)k * TK * TK, vs[k], rq, jg, acc);
+  const float s1 = reduce_groups_w(acc, part, rq, jg, tid);
+  if (tid < TK) ts[tid] = t - s1;
+  __syncthreads();
+  acc = block_gemv_w(Lp + (int64_t)nc * TK * TK, ts, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
+  const float s = reduce_groups_w(acc, part, rq, jg, tid);
+  if (tid < TK) {
+    y[(int64_t)p * TK + tid] = s;
+    map_out[perm[(int64_t)p * TK + tid]] = (T)s;
+  }
+}
+
+// LT[col_ptr[p] + p + k] = (block (col_row[..], p))^T for column p's entries,
+// then LT[col_ptr[p + 1] + p] = (inv(L_pp))^T; one CTA per position p.
+__global__ void transpose_blocks_kernel(const float* L, const int64_t* row_ptr, const int64_t* col_ptr,
+                                        const int64_t* col_blk, float* LT) {
+  const int p = blockIdx.x;
+  __shared__ float tile[TK][TK + 1];
+  const int64_t c0 = col_ptr[p], c1 = col_ptr[p + 1];
+  for (int64_t c = c0; c <= c1; ++c) {
+    const int64_t src = (c < c1) ? col_blk[c] : row_ptr[p + 1] - 1;
+    const float* S = L + src * TK * TK;
+    float* D = LT + (c + p) * TK * TK;
+    __syncthreads();
+    for (int e = threadIdx.x; e < TK * TK; e += blockDim.x) tile[e / TK][e % TK] = S[e];  // tile[col][row]
+    __syncthreads();
+    for (int e = threadIdx.x; e < TK * TK; e += blockDim.x) D[e] = tile[e % TK][e / TK];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -439,6 +578,7 @@ int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
   const size_t smem = 4 * TK * (TK + 1) * sizeof(float);
   CR_CUDA(cudaFuncSetAttribute(icc_colour_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CR_CUDA(cudaMemsetAsync(lev.d_fail, 0, sizeof(int), P->stream));
+  lev.lt_valid = false;
   for (size_t c = 0; c + 1 < pat.colour_start.size(); ++c) {
     const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
     if (p1 > p0) { icc_colour_kernel<<<p1 - p0, SM_NT, smem, P->stream>>>(a, p0); count_launch(); }
@@ -662,8 +802,33 @@ int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisection
 template <typename T>
 int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
   const BlockPattern& pat = lev.pat;
+  if (!lev.lt_valid) {
+    if (!lev.d_LT) CR_CUDA(cudaMalloc(&lev.d_LT, (size_t)pat.nblocks * TK * TK * sizeof(float)));
+    { transpose_blocks_kernel<<<pat.ntile, 256, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_col_ptr, lev.d_col_blk,
+                                                                  lev.d_LT); count_launch(); }
+    CR_CHECK_LAUNCH("transpose_blocks_kernel");
+    lev.lt_valid = true;
+  }
   float* y = reinterpret_cast<float*>(P->hier_tile_work);
   const int nc = (int)pat.colour_start.size() - 1;
+  // levels with few tiles per colour: the 256-thread tiles (latency-bound)
+  if (pat.ntile <= 16384) {
+    for (int c = 0; c < nc; ++c) {
+      const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
+      if (p1 > p0)
+        { fwd_colour_w_kernel<T><<<p1 - p0, TKW, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_row_col, lev.d_perm,
+                                                               map_in, y, p0); count_launch(); }
+    }
+    CR_CHECK_LAUNCH("fwd_colour_w_kernel");
+    for (int c = nc - 1; c >= 0; --c) {
+      const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
+      if (p1 > p0)
+        { bwd_colour_w_kernel<T><<<p1 - p0, TKW, 0, P->stream>>>(lev.d_LT, lev.d_col_ptr, lev.d_col_row, lev.d_perm, y,
+                                                               map_out, p0); count_launch(); }
+    }
+    CR_CHECK_LAUNCH("bwd_colour_w_kernel");
+    return CR_OK;
+  }
   for (int c = 0; c < nc; ++c) {
     const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
     if (p1 > p0)
@@ -674,8 +839,8 @@ int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
   for (int c = nc - 1; c >= 0; --c) {
     const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
     if (p1 > p0)
-      { bwd_colour_kernel<T><<<p1 - p0, TK, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_col_ptr, lev.d_col_row,
-                                                          lev.d_col_blk, lev.d_perm, y, map_out, p0); count_launch(); }
+      { bwd_colour_kernel<T><<<p1 - p0, TK, 0, P->stream>>>(lev.d_LT, lev.d_col_ptr, lev.d_col_row, lev.d_perm, y,
+                                                          map_out, p0); count_launch(); }
   }
   CR_CHECK_LAUNCH("bwd_colour_kernel");
   return CR_OK;
@@ -684,7 +849,7 @@ template int apply_smoother<double>(cr_plan*, PixLevel&, double*, double*);
 template int apply_smoother<float>(cr_plan*, PixLevel&, float*, float*);
 
 void free_smoother(PixLevel& lev) {
-  void* ptrs[] = {lev.d_A, lev.d_L, lev.d_perm, lev.d_row_ptr, lev.d_row_col, lev.d_col_ptr, lev.d_col_row,
+  void* ptrs[] = {lev.d_A, lev.d_L, lev.d_LT, lev.d_perm, lev.d_row_ptr, lev.d_row_col, lev.d_col_ptr, lev.d_col_row,
                   lev.d_col_blk, lev.d_upd_ptr, lev.d_tgt_blk, lev.d_tgt_u, lev.d_tgt_ptr, lev.d_pair_a, lev.d_pair_b,
                   lev.d_fail};
   for (void* p : ptrs)

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -88,7 +89,9 @@ static int smooth_add(cr_plan* P, int h, void* x, const void* r) {
   if (rc) return rc;
   {
     // algorithmic bytes: every factor block read once forward, once backward
-    TimerScope ts(P->timing, P->stream, "pixel_smoother", 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float));
+    const double bytes = 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float);
+    TimerScope ts(P->timing, P->stream, "pixel_smoother", bytes);
+    TimerScope tl(P->timing, P->stream, "pixel_smoother.n" + std::to_string(lev.nside_h), bytes);
     rc = apply_smoother<T>(P, lev, m1, m2);
   }
   if (rc) return rc;

@@ -152,3 +152,47 @@ def test_full_size_sampled_rings(dev, nside, lmax):
     lhs = float(mh @ yy)
     rhs = sht.alm_dot(a, bb.cpu().numpy(), lmax)
     assert abs(lhs - rhs) < 1e-11 * np.linalg.norm(mh) * np.linalg.norm(yy)
+
+
+@pytest.mark.parametrize("nside,lmax", [(4, 20), (16, 47), (128, 383), (256, 767)])
+def test_double_float_fp64_transforms(dev, nside, lmax):
+    """FP64 transforms with the Legendre stages in double-float arithmetic
+    on the FP32 pipes (plan option fp64_df) keep FP64 parity."""
+    g = geometry.healpix_grid(nside)
+    plan = binding.Plan(lmax, nside=nside, fp64_df=True)
+    a = synthetic.random_alm(lmax, seed=500 + nside)
+    y = synthetic.random_map(g["npix"], seed=600 + nside)
+    m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(dev), m)
+    assert rel_l2(m.cpu().numpy(), sht.synth(a, lmax, g)) < TOL64
+    b = torch.empty(sht.n_lm(lmax), dtype=torch.complex128, device=dev)
+    plan.sht_adjoint(torch.from_numpy(y).to(dev), b)
+    assert rel_l2(b.cpu().numpy(), sht.adjoint(y, lmax, g)) < TOL64
+
+
+def test_double_float_full_size_sampled_rings(dev):
+    nside, lmax = 2048, 3000
+    g = geometry.healpix_grid(nside)
+    plan = binding.Plan(lmax, nside=nside, fp64_df=True)
+    a = synthetic.random_alm(lmax, seed=78)
+    m = torch.empty(g["npix"], dtype=torch.float64, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(dev), m)
+    R = g["nring"]
+    rings = np.array([0, 3, nside // 2, nside - 1, nside, 2 * nside - 1, R - 1])
+    ref = sht.synth(a, lmax, g, rings=rings)
+    mh = m.cpu().numpy()
+    for k in rings:
+        sl = slice(g["off"][k], g["off"][k] + g["nphi"][k])
+        assert rel_l2(mh[sl], ref[sl]) < TOL64, k
+
+
+def test_double_float_apply_A(dev):
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside256_lmax767")
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        fp64_df=True)
+    x = synthetic.draw_prior(cl, index=3)
+    y = torch.empty(sht.n_lm(cfg["lmax"]), dtype=torch.complex128, device=dev)
+    plan.apply_A(torch.from_numpy(x).to(dev), y)
+    assert rel_l2(y.cpu().numpy(), operators.apply_A(prob, x)) < TOL64
