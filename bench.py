@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG comparison on the Nside 256 workload")
+    ap.add_argument("--no-df", action="store_true", help="skip the double-float outer-residual variant")
     ap.add_argument("--ref-cycles", type=int, default=2,
                     help="cycles per realization priced by the reference arm (the GPU arm's measured count)")
     return ap.parse_args()
@@ -287,6 +288,47 @@ def roofline_of(stages, steps):
     return dict(base, bound="alu", achieved=None, peak=None, unit=None, frac=None)
 
 
+def df_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv, x_true, npix):
+    """Mixed-precision realization with the outer residual's FP64 Legendre
+    stages in double-float arithmetic: cycles to < 1 uK, time per
+    realization (CUDA events, same protocol as the headline), error."""
+    import torch
+
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        stream=stream, levels="default", fp64_df=True)
+    b = torch.empty_like(x_true)
+    plan.apply_A(x_true, b)
+    x = torch.empty_like(b)
+    mode = binding.CR_MIXED | binding.CR_FIXED
+    cyc = 1
+    for cyc in range(1, 13):
+        plan.solve(b, x, eps=0.0, max_cycles=cyc, mode=mode, check=False)
+        if max_pixel_error(plan, x, x_true, npix, dev) < 1.0:
+            break
+    for _ in range(args.warmup):
+        plan.solve(b, x, eps=0.0, max_cycles=cyc, mode=mode, check=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.solve(b, x, eps=0.0, max_cycles=cyc, mode=mode, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) * 1e-3 / args.steps
+    err = max_pixel_error(plan, x, x_true, npix, dev)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    y = torch.empty_like(b)
+    a0.record(stream)
+    plan.apply_A(x_true, y)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    del plan
+    torch.cuda.synchronize()
+    return {"s_per_realization": s, "cycles": cyc, "max_pixel_error_uK": err,
+            "apply_A_f64_df_s": a0.elapsed_time(a1) * 1e-3,
+            "note": "outer residual with FP64 Legendre stages in double-float (FP32-pair, error-free transforms)"}
+
+
 def cg_comparison(binding, synthetic, dev, stream, workload="nside256_lmax767"):
     """The multi-level solver against diagonal-preconditioned CG (the method
     the paper compares against) on the Nside 256 workload: iterations and
@@ -442,6 +484,14 @@ def main():
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
 
+    # the same realization with the FP64 Legendre stages (outer residual) in
+    # double-float arithmetic on the FP32 pipes (plan option fp64_df)
+    mixed_df = None
+    if not args.no_df:
+        del plan
+        torch.cuda.synchronize()
+        mixed_df = df_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv, x_true, npix)
+
     cg_cmp = None if args.no_cg else cg_comparison(binding, synthetic, dev, stream)
 
     if rank != 0:
@@ -471,6 +521,8 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
+    if mixed_df is not None:
+        out["mixed_df_residual"] = mixed_df
     if cg_cmp is not None:
         out["cg_comparison"] = cg_cmp
     if not args.no_cpu_baseline:

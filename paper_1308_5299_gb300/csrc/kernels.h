@@ -25,6 +25,7 @@ struct LegArgs {
   const int* ls = nullptr;                 // [m][pair] start l (start tables)
   const typename Tr<T>::C* st = nullptr;   // [m][pair] recurrence state at the start
   int df = 0;                              // FP64 stages in double-float arithmetic (legendre_df.cu)
+  int npolar_df = 0;                       // double-float: pairs [0, npolar_df) use the polar form
   const int* ls_df = nullptr;              // double-float start l (FP32 threshold) and FP64 state there
   const double2* st_df = nullptr;
   int ld_seed = 0;

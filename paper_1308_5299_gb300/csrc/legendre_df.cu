@@ -9,8 +9,12 @@
 // (a_lm, the phase array, the adjoint's partial rows); only the arithmetic of
 // the recurrence and the accumulation changes.  Each (m, ring pair) starts at
 // the FP32 start point (|P~_lm| >= 2^-60) from its FP64 recurrence state, so
-// both halves of every value stay normal floats.  The same work
-// decomposition and reductions as the FP64 kernels (legendre.cu).
+// both halves of every value stay normal floats.  Pairs with z > 1/2 use the
+// difference form of the recurrence (as the FP32 kernels do): near the poles
+// Q changes slowly in l and the standard form would lose the second
+// difference to cancellation; c - 2 and w = 1 - z are exact in FP64 there.
+// The same work decomposition and reductions as the FP64 kernels
+// (legendre.cu), over a polar and an equatorial range of ring pairs.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -60,34 +64,50 @@ constexpr int DF_RP = 2;  // ring pairs per thread
 constexpr int DF_CH = 128;
 constexpr int DF_NW = DF_NT / 32;
 
-// Q_l = c z Q_{l-1} - Q_{l-2}
-__device__ __forceinline__ df dstep(df c, df z, df& s1, df& s2) {
-  const df q = dsub(dmul(dmul(c, z), s1), s2);
+// standard form Q_l = c z Q_{l-1} - Q_{l-2} on state (Q_{l-1}, Q_{l-2});
+// polar form on state (Q_{l-1}, D_{l-1}): D_l = ((c - 2) - c w) Q_{l-1} + D_{l-1},
+// Q_l = Q_{l-1} + D_l, with zw = w = 1 - z
+template <bool POLAR>
+__device__ __forceinline__ df dstep(df c, df c2, df zw, df& s1, df& s2) {
+  if (POLAR) {
+    const df e = dsub(c2, dmul(c, zw));
+    const df d = dadd(dmul(e, s1), s2);
+    const df q = dadd(s1, d);
+    s1 = q;
+    s2 = d;
+    return q;
+  }
+  const df q = dsub(dmul(dmul(c, zw), s1), s2);
   s2 = s1;
   s1 = q;
   return q;
 }
 
-__device__ __forceinline__ bool df_load_pairs(const LegArgs<double>& a, int m, int yb, int warp, int lane,
+// block row yb < nbp covers polar pairs [0, npolar), the rest equatorial pairs
+template <bool POLAR>
+__device__ __forceinline__ bool df_load_pairs(const LegArgs<double>& a, int m, int yb, int nbp, int warp, int lane,
                                               int p[DF_RP], int ls[DF_RP], df P1[DF_RP], df P2[DF_RP],
                                               df zz[DF_RP], int* wmin, int* wmax) {
   int lo = a.L + 1, hi = m;
+  const int base = POLAR ? yb * (DF_NT * DF_RP) : a.npolar_df + (yb - nbp) * (DF_NT * DF_RP);
+  const int pend = POLAR ? a.npolar_df : a.npairs;
 #pragma unroll
   for (int j = 0; j < DF_RP; ++j) {
-    p[j] = yb * (DF_NT * DF_RP) + warp * (32 * DF_RP) + j * 32 + lane;
+    p[j] = base + warp * (32 * DF_RP) + j * 32 + lane;
     ls[j] = a.L + 1;
     P1[j] = {0.f, 0.f};
     P2[j] = {0.f, 0.f};
     zz[j] = {0.f, 0.f};
-    if (p[j] < a.npairs) {
+    if (p[j] < pend) {
       const int64_t o = (int64_t)m * a.ld_seed + p[j];
       const int l = a.ls_df[o];
-      zz[j] = mkdf(a.z[p[j]]);
+      const double z = a.z[p[j]];
+      zz[j] = POLAR ? mkdf(1.0 - z) : mkdf(z);  // 1 - z is exact for z >= 1/2
       if (l <= a.L) {
         const double2 st = a.st_df[o];
         ls[j] = l;
         P1[j] = mkdf(st.x);
-        P2[j] = mkdf(st.y);
+        P2[j] = POLAR ? mkdf(st.x - st.y) : mkdf(st.y);
         lo = min(lo, l);
         hi = max(hi, l);
       }
@@ -98,23 +118,26 @@ __device__ __forceinline__ bool df_load_pairs(const LegArgs<double>& a, int m, i
   return *wmin <= a.L;
 }
 
-__global__ void __launch_bounds__(DF_NT) leg_synth_df_kernel(LegArgs<double> a) {
+template <bool POLAR>
+__global__ void __launch_bounds__(DF_NT) leg_synth_df_kernel(LegArgs<double> a, int nbp, int yoff) {
   const int m = blockIdx.x;
   const int L = a.L;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ dfc sa[DF_CH];
   __shared__ df sc[DF_CH];
+  __shared__ df sc2[DF_CH];
   __shared__ int s_min;
   df P1[DF_RP], P2[DF_RP], zz[DF_RP];
   int ls[DF_RP], p[DF_RP];
   dfc accE[DF_RP], accO[DF_RP];
+  const int yb = (int)blockIdx.y + yoff;
 #pragma unroll
   for (int j = 0; j < DF_RP; ++j) {
     accE[j] = {{0.f, 0.f}, {0.f, 0.f}};
     accO[j] = accE[j];
   }
   int wmin, wmax;
-  const bool live = df_load_pairs(a, m, blockIdx.y, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  const bool live = df_load_pairs<POLAR>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   if (tid == 0) s_min = L + 1;
   __syncthreads();
   if (lane == 0 && live) atomicMin(&s_min, wmin);
@@ -133,7 +156,9 @@ __global__ void __launch_bounds__(DF_NT) leg_synth_df_kernel(LegArgs<double> a) 
       double f = a.s[offc + (l - m)];
       if (a.dl) f *= a.dl[l];
       sa[i] = {mkdf(v.x * f), mkdf(v.y * f)};
-      sc[i] = mkdf(a.c[offc + (l - m)]);
+      const double cc = a.c[offc + (l - m)];
+      sc[i] = mkdf(cc);
+      if (POLAR) sc2[i] = mkdf(cc - 2.0);  // exact for c in [1, 4]
     }
     __syncthreads();
     if (!live || wmin >= l0 + nl) continue;
@@ -145,11 +170,12 @@ __global__ void __launch_bounds__(DF_NT) leg_synth_df_kernel(LegArgs<double> a) 
       for (int u = 0; u < ng; ++u) {
         const int l = lg + u;
         const df c0 = sc[i8 + u];
+        const df d0 = POLAR ? sc2[i8 + u] : df{0.f, 0.f};
         const dfc a0 = sa[i8 + u];
 #pragma unroll
         for (int j = 0; j < DF_RP; ++j) {
           if (full || l >= ls[j]) {
-            const df q = dstep(c0, zz[j], P1[j], P2[j]);
+            const df q = dstep<POLAR>(c0, d0, zz[j], P1[j], P2[j]);
             if (u & 1) accO[j] = cfma(q, a0, accO[j]);
             else accE[j] = cfma(q, a0, accE[j]);
           }
@@ -157,9 +183,10 @@ __global__ void __launch_bounds__(DF_NT) leg_synth_df_kernel(LegArgs<double> a) 
       }
     }
   }
+  const int pend = POLAR ? a.npolar_df : a.npairs;
 #pragma unroll
   for (int j = 0; j < DF_RP; ++j) {
-    if (p[j] < a.npairs) {
+    if (p[j] < pend) {
       const int rn = p[j], rs = a.nring - 1 - p[j];
       const dfc sN = cadd(accE[j], accO[j]);
       a.phase[(int64_t)rn * a.ldp + m] = make_double2(todbl(sN.x), todbl(sN.y));
@@ -208,25 +235,28 @@ __device__ __forceinline__ void warp_reduce8_df(dfc v[8]) {
   v[0] = cadd(v[0], shfl_dfc(v[0], 1));
 }
 
-__global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a) {
+template <bool POLAR>
+__global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a, int nbp, int yoff) {
   const int m = blockIdx.x;
   const int L = a.L;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ df sc[DF_CH];
+  __shared__ df sc2[DF_CH];
   __shared__ dfc sacc[DF_CH];
   __shared__ dfc red[2][DF_NW][8];
   __shared__ int s_min;
   df P1[DF_RP], P2[DF_RP], zz[DF_RP];
   int ls[DF_RP], p[DF_RP];
   dfc GE[DF_RP], GO[DF_RP];
-  const int yb = blockIdx.y;
+  const int yb = (int)blockIdx.y + yoff;
   int wmin, wmax;
-  const bool live = df_load_pairs(a, m, yb, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  const bool live = df_load_pairs<POLAR>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  const int pend = POLAR ? a.npolar_df : a.npairs;
 #pragma unroll
   for (int j = 0; j < DF_RP; ++j) {
     GE[j] = {{0.f, 0.f}, {0.f, 0.f}};
     GO[j] = GE[j];
-    if (p[j] < a.npairs && ls[j] <= L) {
+    if (p[j] < pend && ls[j] <= L) {
       const int rn = p[j], rs = a.nring - 1 - p[j];
       const double2 gn = a.phase[(int64_t)rn * a.ldp + m];
       const double2 gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : make_double2(0.0, 0.0);
@@ -248,7 +278,11 @@ __global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a
   for (int l0 = lbeg; l0 <= L; l0 += DF_CH) {
     const int nl = min(DF_CH, L - l0 + 1);
     __syncthreads();
-    for (int i = tid; i < nl; i += DF_NT) sc[i] = mkdf(a.c[offc + (l0 - m) + i]);
+    for (int i = tid; i < nl; i += DF_NT) {
+      const double cc = a.c[offc + (l0 - m) + i];
+      sc[i] = mkdf(cc);
+      if (POLAR) sc2[i] = mkdf(cc - 2.0);
+    }
     __syncthreads();
     for (int i8 = 0; i8 < nl; i8 += 8) {
       const int lg = l0 + i8;
@@ -265,10 +299,11 @@ __global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a
           if (u < ng) {
             const int l = lg + u;
             const df c0 = sc[i8 + u];
+            const df d0 = POLAR ? sc2[i8 + u] : df{0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < DF_RP; ++j) {
               if (full || l >= ls[j]) {
-                const df q = dstep(c0, zz[j], P1[j], P2[j]);
+                const df q = dstep<POLAR>(c0, d0, zz[j], P1[j], P2[j]);
                 acc[u] = cfma(q, (u & 1) ? GO[j] : GE[j], acc[u]);
               }
             }
@@ -295,22 +330,32 @@ __global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a
   }
 }
 
-int df_pair_blocks(int npairs) { return (npairs + DF_NT * DF_RP - 1) / (DF_NT * DF_RP); }
+static void df_blocks(int npolar, int npairs, int* nbp, int* nbe) {
+  *nbp = (npolar + DF_NT * DF_RP - 1) / (DF_NT * DF_RP);
+  *nbe = (npairs - npolar + DF_NT * DF_RP - 1) / (DF_NT * DF_RP);
+}
+
+// upper bound on the adjoint's partial rows over both ranges
+int df_pair_blocks(int npairs) { return (npairs + DF_NT * DF_RP - 1) / (DF_NT * DF_RP) + 1; }
 
 int launch_leg_synth_df(const LegArgs<double>& a, cudaStream_t st) {
   if (a.L < 0) return CR_OK;
-  const int nb = df_pair_blocks(a.npairs);
-  { leg_synth_df_kernel<<<dim3(a.L + 1, nb), DF_NT, 0, st>>>(a); count_launch(); }
+  int nbp, nbe;
+  df_blocks(a.npolar_df, a.npairs, &nbp, &nbe);
+  if (nbp) { leg_synth_df_kernel<true><<<dim3(a.L + 1, nbp), DF_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { leg_synth_df_kernel<false><<<dim3(a.L + 1, nbe), DF_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   CR_CHECK_LAUNCH("leg_synth_df_kernel");
   return CR_OK;
 }
 
 int launch_leg_adjoint_df(const LegArgs<double>& a, int* nblk, cudaStream_t st) {
   if (a.L < 0) return CR_OK;
-  const int nb = df_pair_blocks(a.npairs);
-  { leg_adjoint_df_kernel<<<dim3(a.L + 1, nb), DF_NT, 0, st>>>(a); count_launch(); }
+  int nbp, nbe;
+  df_blocks(a.npolar_df, a.npairs, &nbp, &nbe);
+  if (nbp) { leg_adjoint_df_kernel<true><<<dim3(a.L + 1, nbp), DF_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { leg_adjoint_df_kernel<false><<<dim3(a.L + 1, nbe), DF_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   CR_CHECK_LAUNCH("leg_adjoint_df_kernel");
-  *nblk = nb;
+  *nblk = nbp + nbe;
   return CR_OK;
 }
 

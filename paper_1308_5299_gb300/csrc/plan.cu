@@ -351,6 +351,7 @@ static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
     a.df = P->fp64_df;
     a.ls_df = g.d_ls32;
     a.st_df = g.d_st64b;
+    a.npolar_df = g.npolar32;
   } else {
     a.c = P->d_c32;
     a.c2 = P->d_c2_32;
