@@ -486,6 +486,12 @@ def main():
 
     # the same realization with the FP64 Legendre stages (outer residual) in
     # double-float arithmetic on the FP32 pipes (plan option fp64_df)
+    level_nsides = [plan.level(h)["nside_h"] for h in range(1, plan.nlevels() + 1)]
+    level_rows = []
+    for h in range(1, plan.nlevels() + 1):
+        lv = plan.level(h)
+        kind, nring, npx = plan.level_grid(h)
+        level_rows.append((lv["nside_h"], lv["lmax_h"], lv["n_rec"], (nring, npx // nring) if kind == "gl" else None))
     mixed_df = None
     if not args.no_df:
         del plan
@@ -505,7 +511,7 @@ def main():
         "config": {"workload": args.workload, "nside": nside, "lmax": lmax,
                    "step": "one realization: CR-Solve of b = A x_true, FP32 W-cycles under FP64 refinement, "
                            "fixed cycle count reaching < 1 uK max-pixel error (found before the timed region)",
-                   "cycles": cyc_mixed, "levels": [plan.level(h)["nside_h"] for h in range(1, plan.nlevels() + 1)],
+                   "cycles": cyc_mixed, "levels": level_nsides,
                    "l2": "inputs larger than L2 (N^-1 403 MB, phase 393 MB, smoother factors ~20 GB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "max_pixel_error_uK": {"mixed": err_timed, "mixed_calibration": err_mixed, "fp64": err_f64},
@@ -526,12 +532,7 @@ def main():
     if cg_cmp is not None:
         out["cg_comparison"] = cg_cmp
     if not args.no_cpu_baseline:
-        levels = []
-        for h in range(1, plan.nlevels() + 1):
-            lv = plan.level(h)
-            kind, nring, npx = plan.level_grid(h)
-            levels.append((lv["nside_h"], lv["lmax_h"], lv["n_rec"], (nring, npx // nring) if kind == "gl" else None))
-        out["cpu_baseline"] = cpu_baseline(nside, lmax, levels, cyc_mixed)
+        out["cpu_baseline"] = cpu_baseline(nside, lmax, level_rows, cyc_mixed)
     print(json.dumps(out))
 
 
