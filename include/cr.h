@@ -227,6 +227,28 @@ int cr_grad_ninv(cr_plan* plan, const void* u, const void* v, const double* d, d
 int cr_map_wdot(cr_plan* plan, const double* a, const double* b, double* out);
 int cr_alm_dot(cr_plan* plan, const void* u, const void* v, int weighted, double* out);
 
+/*
+ * Batched realizations in one CUDA graph.  cr_batch_create captures, on the
+ * plans' common stream, the fixed-count CR-Solve (max_cycles = cycles, no
+ * stop test) of nrhs[i] right-hand sides for every plan i -- plans may have
+ * different resolutions -- after one uncaptured solve per plan (which builds
+ * tables created on first use), and instantiates the graph.  x[i], b[i]:
+ * device FP64 complex [nrhs[i]][N_lm(lmax_i)]; the buffers are bound into
+ * the graph, so later runs read b and write x at the same addresses.  mode:
+ * CR_F64 or CR_MIXED (stationary).  cr_batch_run launches the graph on that
+ * stream (asynchronous); replays give results identical to the uncaptured
+ * solves.  cr_batch_nodes: number of graph nodes (kernels and copies).
+ * Errors: CR_EINVAL (plans without levels, on different streams or on the
+ * legacy default stream, which cannot be captured; bad mode), CR_ECUDA.  The
+ * plans must outlive the batch.
+ */
+typedef struct cr_batch cr_batch;
+int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* const* x, const void* const* b,
+                    const int* nrhs, int cycles, int mode);
+int cr_batch_run(cr_batch* batch);
+int cr_batch_nodes(const cr_batch* batch, int64_t* nodes);
+int cr_batch_destroy(cr_batch* batch);
+
 /* Release every resource of the plan (NULL is accepted). */
 int cr_plan_destroy(cr_plan* plan);
 

@@ -83,6 +83,12 @@ _SIGS = {
     "cr_plan_set_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_launch_count": ([], ctypes.c_long),
     "cr_plan_nlevels": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cr_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "cr_batch_run": ([ctypes.c_void_p], ctypes.c_int),
+    "cr_batch_nodes": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cr_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "cr_grad_cl": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                     ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "cr_grad_ninv": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
@@ -412,3 +418,39 @@ class Plan:
         nrhs = self._nrhs(x, n_lm(self.lmax)) if level == 0 else x.numel() // max(1, out.numel())
         _check(lib().cr_apply_A(self._h, level, _dev(x), _dev(out), nrhs, _dtype_code(x)))
         return out
+
+
+class Batch:
+    """Fixed-count CR-Solves of many right-hand sides over one or more plans
+    (mixed resolutions) captured into one CUDA graph (cr_batch_create);
+    run() replays it with a single launch."""
+
+    def __init__(self, plans, xs, bs, cycles, mode=CR_MIXED):
+        n = len(plans)
+        hp = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+        xp = (ctypes.c_void_p * n)(*[_dev(x).value for x in xs])
+        bp = (ctypes.c_void_p * n)(*[_dev(b).value for b in bs])
+        nr = (ctypes.c_int * n)(*[p._nrhs(b, n_lm(p.lmax)) for p, b in zip(plans, bs)])
+        h = ctypes.c_void_p()
+        _check(lib().cr_batch_create(ctypes.byref(h), n, hp, xp, bp, nr, int(cycles), int(mode)))
+        self._h = h
+        self._keep = (plans, xs, bs)
+
+    def run(self):
+        _check(lib().cr_batch_run(self._h))
+
+    def nodes(self):
+        n = ctypes.c_int64()
+        _check(lib().cr_batch_nodes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,110 @@
+// Batched realizations: the fixed-count CR-Solves (Fig. code:mg) of many
+// right-hand sides, over one or several plans (mixed resolutions), captured
+// once into a CUDA graph and replayed with a single graph launch.  Replays
+// run the same kernels with the same arguments as the uncaptured solves, so
+// their results are identical; the host issues one launch per batch instead
+// of one per kernel.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "hier.h"
+#include "kernels.h"
+#include "levels.h"
+
+namespace cr {
+int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mode, int* cycles_out,
+          double* relres_out, double* history);
+}  // namespace cr
+
+struct cr_batch {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  size_t nodes = 0;
+};
+
+using namespace cr;
+
+extern "C" {
+
+int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* const* x, const void* const* b,
+                    const int* nrhs, int cycles, int mode) {
+  if (!out || nplans < 1 || !plans || !x || !b || !nrhs || cycles < 1)
+    return fail(CR_EINVAL, "cr_batch_create: bad arguments");
+  if ((mode & ~3) != 0 || ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED))
+    return fail(CR_EINVAL, "cr_batch_create: mode must be CR_F64 or CR_MIXED (stationary, fixed count)");
+  cudaStream_t st = plans[0] ? plans[0]->stream : nullptr;
+  if (!st) return fail(CR_EINVAL, "cr_batch_create: graph capture needs a created stream, not the default stream");
+  for (int i = 0; i < nplans; ++i) {
+    if (!plans[i] || !plans[i]->hier) return fail(CR_EINVAL, "cr_batch_create: every plan needs levels");
+    if (plans[i]->stream != st) return fail(CR_EINVAL, "cr_batch_create: plans must share one stream");
+    if (nrhs[i] < 0) return fail(CR_EINVAL, "cr_batch_create: nrhs < 0");
+  }
+  const int fmode = mode | CR_FIXED;
+  // one uncaptured solve per plan first: it builds the tables created lazily
+  // on first use, which must not be allocated inside the capture
+  for (int i = 0; i < nplans; ++i) {
+    if (nrhs[i] == 0) continue;
+    int rc = solve(plans[i], x[i], b[i], 0.0, 1, fmode, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  CR_CUDA(cudaStreamSynchronize(st));
+  cr_batch* bt = new cr_batch();
+  bt->stream = st;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    delete bt;
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  int rc = CR_OK;
+  for (int i = 0; i < nplans && !rc; ++i) {
+    const int64_t nlm = n_lm(plans[i]->lmax);
+    plans[i]->capturing = true;
+    for (int j = 0; j < nrhs[i] && !rc; ++j)
+      rc = solve(plans[i], (char*)x[i] + j * nlm * sizeof(double2), (const char*)b[i] + j * nlm * sizeof(double2), 0.0,
+                 cycles, fmode, nullptr, nullptr, nullptr);
+    plans[i]->capturing = false;
+  }
+  e = cudaStreamEndCapture(st, &bt->graph);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
+  if (!rc) {
+    e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+  }
+  if (!rc) {
+    e = cudaGraphGetNodes(bt->graph, nullptr, &bt->nodes);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphGetNodes");
+  }
+  if (rc) {
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    delete bt;
+    return rc;
+  }
+  *out = bt;
+  return CR_OK;
+}
+
+int cr_batch_run(cr_batch* bt) {
+  if (!bt || !bt->exec) return fail(CR_EINVAL, "cr_batch_run: no batch");
+  CR_CUDA(cudaGraphLaunch(bt->exec, bt->stream));
+  return CR_OK;
+}
+
+int cr_batch_nodes(const cr_batch* bt, int64_t* nodes) {
+  if (!bt || !nodes) return fail(CR_EINVAL, "cr_batch_nodes: null argument");
+  *nodes = (int64_t)bt->nodes;
+  return CR_OK;
+}
+
+int cr_batch_destroy(cr_batch* bt) {
+  if (!bt) return CR_OK;
+  if (bt->stream) cudaStreamSynchronize(bt->stream);
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  delete bt;
+  return CR_OK;
+}
+
+}  // extern "C"

@@ -143,6 +143,7 @@ struct cr_plan {
   cr::Workspace ws;
   cr::Timing timing;
   int fp64_df = 0;  // FP64 Legendre stages in double-float arithmetic
+  bool capturing = false;  // inside a CUDA-graph capture: no host synchronisation
   cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)
   void* hier_tile_work = nullptr;     // FP32 tile-ordered smoother work vector
   // diagonal-preconditioned CG (created on first use)

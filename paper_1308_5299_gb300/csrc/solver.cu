@@ -516,9 +516,13 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
   Hierarchy& H = *P->hier;
   const int L = P->lmax;
   const int64_t nlm = n_lm(L);
-  double bsb = 0.0, rsr = 0.0;
-  int rc = weighted_norm2(P, b, &bsb);
-  if (rc) return rc;
+  double bsb = 1.0, rsr = 0.0;
+  int rc = CR_OK;
+  // under graph capture (fixed-count stationary solves only) no norm is read
+  // back: the stop test and the residual history are skipped
+  if (P->capturing && (!(mode & CR_FIXED) || (mode & CR_PCG)))
+    return fail(CR_EINVAL, "solve: graph capture needs a fixed-count stationary solve");
+  if (!P->capturing && (rc = weighted_norm2(P, b, &bsb))) return rc;
   if (!(bsb > 0.0)) {
     CR_CUDA(cudaMemsetAsync(x, 0, nlm * sizeof(double2), P->stream));
     if (cycles_out) *cycles_out = 0;
@@ -556,6 +560,10 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
     {
       TimerScope ts(P->timing, P->stream, "outer_residual");
       if ((rc = residual<double>(P, 0, x, b, r))) return rc;
+    }
+    if (P->capturing) {
+      rel = std::nan("");
+      continue;
     }
     if ((rc = weighted_norm2(P, r, &rsr))) return rc;
     rel = std::sqrt(std::max(rsr, 0.0) / bsb);
