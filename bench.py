@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG comparison on the Nside 256 workload")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float outer-residual variant")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched mixed-resolution measurement")
     ap.add_argument("--ref-cycles", type=int, default=2,
                     help="cycles per realization priced by the reference arm (the GPU arm's measured count)")
     return ap.parse_args()
@@ -329,6 +330,80 @@ def df_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv, x_true,
             "note": "outer residual with FP64 Legendre stages in double-float (FP32-pair, error-free transforms)"}
 
 
+def batch_measurement(binding, synthetic, dev, args, nrhs=16):
+    """Batched mixed-resolution realizations: nrhs right-hand sides at
+    Nside 1024 / lmax 2047 and nrhs at Nside 512 / lmax 1023, mixed-precision
+    fixed-count CR-Solves captured into one CUDA graph and replayed with one
+    launch; the cycle count is the fewest reaching < 1 uK max-pixel error on
+    every right-hand side.  Reports realizations/s for the graph and for the
+    same solves launched directly, and every realization's error."""
+    import numpy as np
+    import torch
+
+    st = torch.cuda.Stream(dev)
+    with torch.cuda.stream(st):
+        plans, xs, bs, xts, npx = [], [], [], [], []
+        for k, name in enumerate(["nside1024_lmax2047", "nside512_lmax1023"]):
+            cfg, cl, bl, ninv = synthetic.problem_inputs(name)
+            plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                                stream=st, levels="default")
+            xt = torch.from_numpy(np.stack([synthetic.draw_prior(cl, index=100 * (k + 1) + j)
+                                            for j in range(nrhs)])).to(dev)
+            b = torch.empty_like(xt)
+            plan.apply_A(xt, b)
+            plans.append(plan)
+            xs.append(torch.zeros_like(b))
+            bs.append(b)
+            xts.append(xt)
+            npx.append(12 * cfg["nside"] ** 2)
+
+        def errors():
+            out = []
+            for plan, x, xt, n in zip(plans, xs, xts, npx):
+                for j in range(x.shape[0]):
+                    out.append(max_pixel_error(plan, x[j], xt[j], n, dev))
+            return out
+
+        mode = binding.CR_MIXED
+        cycles = 1
+        for cycles in range(1, 13):
+            for plan, x, b in zip(plans, xs, bs):
+                plan.solve(b, x, eps=0.0, max_cycles=cycles, mode=mode | binding.CR_FIXED, check=False)
+            if max(errors()) < 1.0:
+                break
+        total = sum(x.shape[0] for x in xs)
+
+        def direct():
+            for plan, x, b in zip(plans, xs, bs):
+                plan.solve(b, x, eps=0.0, max_cycles=cycles, mode=mode | binding.CR_FIXED, check=False)
+
+        direct()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        direct()
+        torch.cuda.synchronize()
+        t_direct = time.perf_counter() - t0
+        graph = binding.Batch(plans, xs, bs, cycles, mode)
+        graph.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(st)
+        for _ in range(reps):
+            graph.run()
+        e1.record(st)
+        torch.cuda.synchronize()
+        t_graph = e0.elapsed_time(e1) * 1e-3 / reps
+        errs = errors()
+        nodes = graph.nodes()
+        graph.close()
+    return {"workload": "%d x (Nside 1024, lmax 2047) + %d x (Nside 512, lmax 1023)" % (nrhs, nrhs),
+            "cycles": cycles, "realizations": total, "graph_nodes": nodes,
+            "graph_realizations_per_s": total / t_graph, "graph_s": t_graph,
+            "direct_realizations_per_s": total / t_direct, "direct_s": t_direct,
+            "max_pixel_error_uK": {"max": max(errs), "median": float(np.median(errs))}}
+
+
 def cg_comparison(binding, synthetic, dev, stream, workload="nside256_lmax767"):
     """The multi-level solver against diagonal-preconditioned CG (the method
     the paper compares against) on the Nside 256 workload: iterations and
@@ -499,6 +574,7 @@ def main():
         mixed_df = df_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv, x_true, npix)
 
     cg_cmp = None if args.no_cg else cg_comparison(binding, synthetic, dev, stream)
+    batch = None if args.no_batch else batch_measurement(binding, synthetic, dev, args)
 
     if rank != 0:
         return
@@ -531,6 +607,8 @@ def main():
         out["mixed_df_residual"] = mixed_df
     if cg_cmp is not None:
         out["cg_comparison"] = cg_cmp
+    if batch is not None:
+        out["batch"] = batch
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nside, lmax, level_rows, cyc_mixed)
     print(json.dumps(out))
