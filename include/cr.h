@@ -195,35 +195,53 @@ int cr_plan_level_grid(const cr_plan* plan, int h, int* kind, int* nring, int64_
  * Errors: CR_EINVAL (no C_l in the plan, bad flag), CR_ECUDA.
  */
 #define CR_DRAW_FLUCT 1
+/* CR_DRAW_PLAIN: the data term is B Y^T d (no N^-1), e.g. for trace probes */
+#define CR_DRAW_PLAIN 2
 int cr_draw(cr_plan* plan, uint64_t seed, const void* d, void* b, int nrhs, int flags);
 
 /*
  * Gradient contractions for differentiating the solve of Section 2.3 (A is
  * symmetric, so the adjoint lambda = A^-1 g is another CR-Solve).
- * cr_grad_cl: out[l] = alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l for
- *   l = 0..lmax (0 where C_l = 0), <.,.>_l the real inner product restricted
- *   to multipole l and w1 the constrained-realization normals of cr_draw
- *   (seed, right-hand side rhs) in complex storage.  u, v: device FP64
- *   complex [N_lm] (v may be NULL: its term is 0); out: device FP64 [lmax+1].
+ * cr_grad_cl: out[l] = alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l
+ *   + kappa (2l+1) / C_l for l = 0..lmax (0 where C_l = 0), <.,.>_l the real
+ *   inner product restricted to multipole l and w1 the constrained-realization
+ *   normals of cr_draw (seed, right-hand side rhs) in complex storage.  u, v:
+ *   device FP64 complex [N_lm] (v may be NULL: its term is 0); out: device
+ *   FP64 [lmax+1], overwritten, or added to when accumulate != 0.
  *   A realization x = A^-1 b with loss gradient g uses (u, v) = (A^-1 g, x),
  *   alpha = 1, beta = -1/2; the Wiener-filter data term uses u = v = A^-1 b,
  *   alpha = 1/2, beta = 0.
  * cr_grad_ninv: out_i = alpha p_i q_i + p_i (gamma d_i + delta w2_i / sqrt n_i)
- *   + eps d_i^2 with p = Y B u, q = Y B v synthesised in FP64, w2 the pixel
- *   normals of cr_draw, n the plan's N^-1 (the w2 term only where n_i > 0);
- *   d: device FP64 [npix] or NULL; out: device FP64 [npix].  Realization:
+ *   + eps d_i^2 + kappa / n_i with p = Y B u, q = Y B v synthesised in FP64
+ *   (v may be NULL: q = 0), w2 the pixel normals of cr_draw, n the plan's
+ *   N^-1 (the w2 and 1/n terms only where n_i > 0); d: device FP64 [npix] or
+ *   NULL; out: device FP64 [npix], overwritten or accumulated.  Realization:
  *   alpha = -1, gamma = 1, delta = 1/2, eps = 0; Wiener-filter data term:
  *   u = v = A^-1 b, alpha = -1/2, gamma = 1, delta = 0, eps = -1/2.
  *   Allocates two FP64 maps for the call.
+ * Log-determinant part of the Wiener-filter log-likelihood,
+ *   -1/2 ln det M = -1/2 (ln det N + ln det S + ln det A) (determinant lemma):
+ *   d/dC_l = -1/2 ((2l+1)/C_l - C_l^-2 tr_l A^-1), d/dn_i = -1/2 (-1/n_i +
+ *   (Y B A^-1 B Y^T)_ii), the traces by Hutchinson estimates over Rademacher
+ *   probes z (cr_probe CR_PROBE_ALM: <z, A^-1 z>_l) and w (CR_PROBE_MAP:
+ *   (Y B A^-1 B Y^T w)_i w_i, with B Y^T w from cr_draw CR_DRAW_PLAIN).
+ * cr_probe: Rademacher probe j: CR_PROBE_ALM a complex [N_lm] vector in the
+ *   real orthonormal basis (0 at C_l = 0), CR_PROBE_MAP an FP64 [npix] map
+ *   (0 where n_i = 0); element k of stream 5 (coefficients, k = 2 i + part)
+ *   or 6 (pixels) takes word k & 3 of Philox4x32-10 at counter
+ *   (k >> 2, k >> 34, stream, j), sign + for an even word.
  * cr_map_wdot: *out = sum_i n_i a_i b_i (host result; a, b device FP64 maps).
  * cr_alm_dot: *out = <u, v> (real inner product, S^-1-weighted if weighted).
  * All synchronous.  Errors: CR_EINVAL (null pointers, plan without C_l),
  * CR_ECUDA.
  */
-int cr_grad_cl(cr_plan* plan, const void* u, const void* v, double alpha, double beta, uint64_t seed, int rhs,
-               double* out);
+int cr_grad_cl(cr_plan* plan, const void* u, const void* v, double alpha, double beta, double kappa, uint64_t seed,
+               int rhs, int accumulate, double* out);
 int cr_grad_ninv(cr_plan* plan, const void* u, const void* v, const double* d, double alpha, double gamma,
-                 double delta, double eps, uint64_t seed, int rhs, double* out);
+                 double delta, double eps, double kappa, uint64_t seed, int rhs, int accumulate, double* out);
+#define CR_PROBE_ALM 0
+#define CR_PROBE_MAP 1
+int cr_probe(cr_plan* plan, uint64_t seed, int kind, int j, void* out);
 int cr_map_wdot(cr_plan* plan, const double* a, const double* b, double* out);
 int cr_alm_dot(cr_plan* plan, const void* u, const void* v, int weighted, double* out);
 

@@ -84,3 +84,16 @@ def draw_rhs(prob, seed, d=None, fluct=True, rhs=0):
         act = prob.active
         b[act] += a[act] / np.sqrt(prob.cl[prob.l[act]])
     return prob.clean(b)
+
+
+def rademacher(seed, stream, n, j=0):
+    """n Rademacher signs of one stream for probe j: element k takes word
+    k & 3 of Philox4x32-10 at counter (k >> 2, k >> 34, stream, j); + for an
+    even word.  Streams: 5 = coefficient probes, 6 = pixel probes."""
+    k = np.arange(n, dtype=np.uint64)
+    ctr = k >> np.uint64(2)
+    x = philox4x32_10(ctr & np.uint64(MASK), ctr >> np.uint64(32), np.full_like(ctr, stream), np.full_like(ctr, j),
+                      seed & MASK, (seed >> 32) & MASK)
+    slot = (k & np.uint64(3)).astype(np.int64)
+    word = np.choose(slot, x)
+    return np.where(word & np.uint64(1), -1.0, 1.0)

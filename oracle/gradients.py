@@ -12,6 +12,13 @@ adjoint vector is lambda = A^-1 w and, differentiating A x = b,
 with a1 the complex-storage w1 and <.,.>_l the inner product restricted to
 multipole l.
 
+Log-determinant term: -1/2 ln det M with ln det M = ln det N + ln det S +
+ln det A (over the observed pixels, N = diag(1/n)), so
+  d/dC_l = -1/2 ((2l+1)/C_l - C_l^-2 tr(P_l A^-1 P_l)),
+  d/dn_i = -1/2 (-1/n_i + (Y B A^-1 B Y^T)_ii)     (n_i > 0),
+exactly from the dense A^-1, or by Hutchinson's estimator with the
+Rademacher probes of ``draw.rademacher`` (the estimator the GPU runs).
+
 Wiener-filter data term: with M = N + Y B S B Y^T (pixel covariance of the
 data over observed pixels), d^T M^-1 d = d^T N^-1 d - b^T A^-1 b,
 b = B Y^T N^-1 d (Woodbury), so
@@ -124,3 +131,77 @@ def wf_data_term_pixel(prob, d):
     K = cols[obs] @ cols[obs].T
     M = np.diag(1.0 / prob.ninv[obs]) + K
     return -0.5 * d[obs] @ np.linalg.solve(M, d[obs])
+
+
+def _ainv_dense(prob):
+    A, act = _dense(prob)
+    return np.linalg.inv(A), act
+
+
+def logdet_grad_exact(prob):
+    """(d/dC_l, d/dn) of -1/2 ln det M, traces from the dense inverse."""
+    L = prob.lmax
+    Ainv, act = _ainv_dense(prob)
+    l_real = np.concatenate([np.arange(L + 1)] + [np.repeat(np.arange(m, L + 1), 2) for m in range(1, L + 1)])
+    la = l_real[act]
+    tr = np.bincount(la, weights=np.diag(Ainv), minlength=L + 1)
+    nu = np.bincount(la, minlength=L + 1).astype(np.float64)
+    cl = prob.cl
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gcl = np.where(cl > 0, -0.5 * (nu / np.where(cl > 0, cl, 1.0) - tr / np.where(cl > 0, cl, 1.0) ** 2), 0.0)
+    # (Y B A^-1 B Y^T)_ii: columns of Y B in the real basis
+    npix = prob.grid["npix"]
+    idx = np.nonzero(act)[0]
+    YB = np.zeros((npix, idx.size))
+    for j, k in enumerate(idx):
+        u = np.zeros((L + 1) ** 2)
+        u[k] = 1.0
+        YB[:, j] = sht.synth(prob.bl[prob.l] * sht.real_to_alm(u, L), L, prob.grid)
+    diag = np.einsum("ij,jk,ik->i", YB, Ainv, YB)
+    n = prob.ninv
+    with np.errstate(divide="ignore"):
+        gn = np.where(n > 0, -0.5 * (-1.0 / np.where(n > 0, n, 1.0) + diag), 0.0)
+    return gcl, gn
+
+
+def logdet_grad_hutchinson(prob, seed, nprobe):
+    """The same gradient with both traces by Hutchinson over nprobe probes."""
+    L = prob.lmax
+    cl, n = prob.cl, prob.ninv
+    nlm = sht.n_lm(L)
+    A, act = _dense(prob)
+    trs = np.zeros(L + 1)
+    dg = np.zeros(prob.grid["npix"])
+    bl = prob.bl[prob.l]
+    for j in range(nprobe):
+        zr = draw.rademacher(seed, 5, 2 * nlm, j)
+        z = np.where(prob.m == 0, zr[0::2] + 0j, (zr[0::2] + 1j * zr[1::2]) / math.sqrt(2.0))
+        z = prob.clean(z)
+        trs += per_l_dot(z, solve_dense(prob, z, A, act), L)
+        w = np.where(n > 0, draw.rademacher(seed, 6, prob.grid["npix"], j), 0.0)
+        bw = prob.clean(bl * sht.adjoint(w, L, prob.grid))
+        dg += sht.synth(bl * solve_dense(prob, bw, A, act), L, prob.grid) * w
+    trs /= nprobe
+    dg /= nprobe
+    l = np.arange(L + 1)
+    nu = np.where(cl > 0, 2 * l + 1.0, 0.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gcl = np.where(cl > 0, -0.5 * (nu / np.where(cl > 0, cl, 1.0) - trs / np.where(cl > 0, cl, 1.0) ** 2), 0.0)
+        gn = np.where(n > 0, -0.5 * (-1.0 / np.where(n > 0, n, 1.0) + dg), 0.0)
+    return gcl, gn
+
+
+def logdet_M(prob):
+    """ln det M over the observed pixels, M = N + Y B S B Y^T, formed densely."""
+    L = prob.lmax
+    obs = np.nonzero(prob.ninv > 0)[0]
+    act = operators.real_active_mask(prob)
+    l_real = np.concatenate([np.arange(L + 1)] + [np.repeat(np.arange(m, L + 1), 2) for m in range(1, L + 1)])
+    cols = []
+    for k in np.nonzero(act)[0]:
+        u = np.zeros((L + 1) ** 2)
+        u[k] = 1.0
+        cols.append(sht.synth(prob.bl[prob.l] * sht.real_to_alm(u, L), L, prob.grid)[obs] * math.sqrt(prob.cl[l_real[k]]))
+    K = np.stack(cols, axis=1)
+    M = np.diag(1.0 / prob.ninv[obs]) + K @ K.T
+    return np.linalg.slogdet(M)[1]

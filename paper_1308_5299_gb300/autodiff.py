@@ -14,6 +14,15 @@ wf_data_term(cl, ninv, d): D = -1/2 (d^T N^-1 d - b^T A^-1 b), b = B Y^T N^-1 d
 identity), with dD/dC_l = 1/2 C_l^-2 <xh, xh>_l and dD/dn_i =
 -1/2 (d_i - (Y B xh)_i)^2, xh = A^-1 b.
 
+wf_loglike_grad(cl, ninv, d, nprobe): the gradient of the whole Wiener-filter
+log-likelihood -1/2 d^T M^-1 d - 1/2 ln det M, M = N + Y B S B Y^T: the data
+term above plus the log-determinant term (determinant lemma ln det M =
+ln det N + ln det S + ln det A)
+  d/dC_l = -1/2 ((2l+1)/C_l - C_l^-2 tr_l A^-1),
+  d/dn_i = -1/2 (-1/n_i + (Y B A^-1 B Y^T)_ii),
+with both traces estimated by Hutchinson over nprobe Rademacher probes
+(cr_probe), each needing one more solve.
+
 Complex gradients follow torch's convention G = dL/dRe x + i dL/dIm x; the
 library's adjoint right-hand side g satisfies dL = <g, dx> in its real inner
 product, so g = G at m = 0 and G / 2 at m > 0 (a convention conversion).
@@ -61,8 +70,9 @@ class _Realization(torch.autograd.Function):
         gn = torch.zeros(plan.npix, dtype=torch.float64, device=x.device)
         for j in range(ctx.nrhs):
             dj = None if ctx.d is None else ctx.d[j].contiguous()
-            gcl += plan.grad_cl(lam[j].contiguous(), x[j].contiguous(), 1.0, -0.5, ctx.seed, j)
-            gn += plan.grad_ninv(lam[j].contiguous(), x[j].contiguous(), dj, -1.0, 1.0, 0.5, 0.0, ctx.seed, j)
+            plan.grad_cl(lam[j].contiguous(), x[j].contiguous(), 1.0, -0.5, ctx.seed, j, out=gcl, accumulate=True)
+            plan.grad_ninv(lam[j].contiguous(), x[j].contiguous(), dj, -1.0, 1.0, 0.5, 0.0, ctx.seed, j, out=gn,
+                           accumulate=True)
         return gcl.to(ctx.cl_dev), gn, None, None, None, None, None, None
 
 
@@ -104,3 +114,34 @@ def realization(cl, ninv, bl, nside, d=None, seed=0, nrhs=1, solve_kw=None):
 def wf_data_term(cl, ninv, bl, nside, d, solve_kw=None):
     """Wiener-filter data term D (scalar), differentiable in cl and ninv."""
     return _WFData.apply(cl, ninv, bl, nside, d, dict(DEFAULT_SOLVE, **(solve_kw or {})))
+
+
+def wf_loglike_grad(cl, ninv, bl, nside, d, nprobe=8, seed=0, solve_kw=None):
+    """(D, dL/dC_l, dL/dn): the Wiener-filter data term D and the gradient of
+    the whole log-likelihood (data term exact, log-determinant term by
+    Hutchinson over nprobe probes).  cl float64 [lmax+1], ninv and d float64
+    CUDA [npix]; returns CUDA tensors."""
+    kw = dict(DEFAULT_SOLVE, **(solve_kw or {}))
+    plan = _plan(cl, ninv, bl, nside, "default", None)
+    nlm = binding.n_lm(plan.lmax)
+    dev = ninv.device
+    b = torch.empty(nlm, dtype=torch.complex128, device=dev)
+    plan.draw(0, b, d=d, fluct=False)
+    xh = torch.empty_like(b)
+    plan.solve(b, xh, **kw)
+    D = -0.5 * (plan.map_wdot(d, d) - plan.alm_dot(b, xh))
+    gcl = plan.grad_cl(xh, xh, 0.5, 0.0, kappa=-0.5)
+    gn = plan.grad_ninv(xh, xh, d, -0.5, 1.0, 0.0, -0.5, kappa=0.5)
+    z = torch.empty(nlm, dtype=torch.complex128, device=dev)
+    lam = torch.empty_like(z)
+    w = torch.empty(plan.npix, dtype=torch.float64, device=dev)
+    bw = torch.empty_like(z)
+    for j in range(nprobe):
+        plan.probe(seed, binding.CR_PROBE_ALM, j, z)
+        plan.solve(z, lam, **kw)
+        plan.grad_cl(z, lam, 0.5 / nprobe, 0.0, out=gcl, accumulate=True)
+        plan.probe(seed, binding.CR_PROBE_MAP, j, w)
+        plan.draw(0, bw, d=w, fluct=False, plain=True)
+        plan.solve(bw, lam, **kw)
+        plan.grad_ninv(lam, None, w, 0.0, -0.5 / nprobe, 0.0, 0.0, out=gn, accumulate=True)
+    return D, gcl, gn

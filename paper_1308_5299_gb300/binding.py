@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libcrgb300.so")
 
 CR_OK = 0
 CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED, CR_CG = 0, 1, 2, 4, 8, 16
-CR_DRAW_FLUCT = 1
+CR_DRAW_FLUCT, CR_DRAW_PLAIN = 1, 2
+CR_PROBE_ALM, CR_PROBE_MAP = 0, 1
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0
 
@@ -90,10 +91,11 @@ _SIGS = {
     "cr_batch_nodes": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cr_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "cr_grad_cl": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
-                    ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+                    ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "cr_grad_ninv": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
-                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
-                      ctypes.c_void_p], ctypes.c_int),
+                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                      ctypes.c_int, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "cr_probe": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "cr_map_wdot": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
                     ctypes.c_int),
     "cr_alm_dot": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -321,7 +323,7 @@ class Plan:
                                    ctypes.byref(lam)))
         return dict(nside_h=ns.value, lmax_h=lm.value, n_rec=nr.value, fl=fl, ridge=ridge.value, lambda_max=lam.value)
 
-    def draw(self, seed, b, d=None, fluct=True):
+    def draw(self, seed, b, d=None, fluct=True, plain=False):
         """Right-hand side b = B Y^T N^-1 d (+ S^-1/2 w1 + B Y^T N^-1/2 w2 with
         fluct) for every right-hand side j of b ([nrhs, N_lm] complex128);
         d: float64 CUDA map(s) [nrhs, npix] or None."""
@@ -329,25 +331,31 @@ class Plan:
         if d is not None and not (d.is_cuda and d.dtype == torch.float64):
             raise ValueError("d must be a float64 CUDA tensor")
         _check(lib().cr_draw(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, None if d is None else _dev(d), _dev(b), nrhs,
-                             CR_DRAW_FLUCT if fluct else 0))
+                             (CR_DRAW_FLUCT if fluct else 0) | (CR_DRAW_PLAIN if plain else 0)))
         return b
 
-    def grad_cl(self, u, v, alpha, beta, seed=0, rhs=0, out=None):
-        """out[l] = alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l (cr_grad_cl)."""
+    def grad_cl(self, u, v, alpha, beta, seed=0, rhs=0, out=None, kappa=0.0, accumulate=False):
+        """out[l] (+)= alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l + kappa (2l+1)/C_l (cr_grad_cl)."""
         if out is None:
             out = torch.empty(self.lmax + 1, dtype=torch.float64, device=u.device)
         _check(lib().cr_grad_cl(self._h, _dev(u), None if v is None else _dev(v), float(alpha), float(beta),
-                                int(seed) & 0xFFFFFFFFFFFFFFFF, int(rhs), _dev(out)))
+                                float(kappa), int(seed) & 0xFFFFFFFFFFFFFFFF, int(rhs), int(bool(accumulate)),
+                                _dev(out)))
         return out
 
-    def grad_ninv(self, u, v, d, alpha, gamma, delta, eps, seed=0, rhs=0, out=None):
-        """out_i = alpha p_i q_i + p_i (gamma d_i + delta w2_i / sqrt n_i) + eps d_i^2,
+    def grad_ninv(self, u, v, d, alpha, gamma, delta, eps, seed=0, rhs=0, out=None, kappa=0.0, accumulate=False):
+        """out_i (+)= alpha p_i q_i + p_i (gamma d_i + delta w2_i / sqrt n_i) + eps d_i^2 + kappa / n_i,
         p = Y B u, q = Y B v (cr_grad_ninv)."""
         if out is None:
             out = torch.empty(self.npix, dtype=torch.float64, device=u.device)
-        _check(lib().cr_grad_ninv(self._h, _dev(u), _dev(v), None if d is None else _dev(d), float(alpha),
-                                  float(gamma), float(delta), float(eps), int(seed) & 0xFFFFFFFFFFFFFFFF, int(rhs),
-                                  _dev(out)))
+        _check(lib().cr_grad_ninv(self._h, _dev(u), None if v is None else _dev(v), None if d is None else _dev(d),
+                                  float(alpha), float(gamma), float(delta), float(eps), float(kappa),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(rhs), int(bool(accumulate)), _dev(out)))
+        return out
+
+    def probe(self, seed, kind, j, out):
+        """Rademacher probe j (cr_probe): kind CR_PROBE_ALM -> complex [N_lm], CR_PROBE_MAP -> map [npix]."""
+        _check(lib().cr_probe(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, int(kind), int(j), _dev(out)))
         return out
 
     def map_wdot(self, a, b):

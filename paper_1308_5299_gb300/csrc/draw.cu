@@ -20,11 +20,11 @@
 namespace cr {
 
 // map_i = N^-1_i d_i + sqrt(N^-1_i) omega_2,i
-__global__ void draw_map_kernel(const double* ninv, const double* d, int fluct, uint64_t seed, uint32_t rhs,
+__global__ void draw_map_kernel(const double* ninv, const double* d, int fluct, int plain, uint64_t seed, uint32_t rhs,
                                 int64_t npix, double* map) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
     const double n = ninv[i];
-    double v = d ? n * d[i] : 0.0;
+    double v = d ? (plain ? d[i] : n * d[i]) : 0.0;
     if (fluct) v += sqrt(fmax(n, 0.0)) * draw_normal(seed, 4u, rhs, (uint64_t)i);
     map[i] = v;
   }
@@ -59,8 +59,9 @@ using namespace cr;
 extern "C" int cr_draw(cr_plan* plan, uint64_t seed, const void* d, void* b, int nrhs, int flags) {
   if (!plan || !b || nrhs < 1) return fail(CR_EINVAL, "cr_draw: null plan / output or nrhs < 1");
   if (!plan->has_op) return fail(CR_EINVAL, "cr_draw: the plan needs C_l, b_l and N^-1");
-  if (flags & ~CR_DRAW_FLUCT) return fail(CR_EINVAL, "cr_draw: unknown flag");
+  if (flags & ~(CR_DRAW_FLUCT | CR_DRAW_PLAIN)) return fail(CR_EINVAL, "cr_draw: unknown flag");
   const int fluct = (flags & CR_DRAW_FLUCT) ? 1 : 0;
+  const int plain = (flags & CR_DRAW_PLAIN) ? 1 : 0;
   const Grid& g = plan->obs;
   const int L = plan->lmax;
   const int64_t nlm = n_lm(L);
@@ -70,7 +71,7 @@ extern "C" int cr_draw(cr_plan* plan, uint64_t seed, const void* d, void* b, int
   for (int j = 0; j < nrhs && !rc; ++j) {
     double2* bj = reinterpret_cast<double2*>(b) + (int64_t)j * nlm;
     const double* dj = d ? reinterpret_cast<const double*>(d) + (int64_t)j * g.npix : nullptr;
-    { draw_map_kernel<<<1024, 256, 0, plan->stream>>>(plan->d_ninv, dj, fluct, seed, (uint32_t)j, g.npix, map);
+    { draw_map_kernel<<<1024, 256, 0, plan->stream>>>(plan->d_ninv, dj, fluct, plain, seed, (uint32_t)j, g.npix, map);
       count_launch(); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -22,9 +22,10 @@
 
 namespace cr {
 
-// out_l = alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l  (0 where C_l = 0)
+// out_l (+)= alpha C_l^-2 <u, v>_l + beta C_l^-3/2 <u, w1>_l + kappa (2l+1) / C_l
+// (0 where C_l = 0)
 __global__ void grad_cl_kernel(const double2* u, const double2* v, const double* sinv, int L, double alpha,
-                               double beta, uint64_t seed, uint32_t rhs, double* out) {
+                               double beta, double kappa, uint64_t seed, uint32_t rhs, int acc, double* out) {
   const int l = blockIdx.x;
   __shared__ double red[256];
   double s1 = 0.0, s2 = 0.0;
@@ -63,26 +64,62 @@ __global__ void grad_cl_kernel(const double2* u, const double2* v, const double*
   }
   if (threadIdx.x == 0) {
     const double si = sinv[l];
-    out[l] = (si > 0.0) ? alpha * si * si * t1 + beta * si * sqrt(si) * red[0] : 0.0;
+    const double g = (si > 0.0) ? alpha * si * si * t1 + beta * si * sqrt(si) * red[0] + kappa * (2.0 * l + 1.0) * si
+                                : 0.0;
+    out[l] = acc ? out[l] + g : g;
   }
 }
 
-// out_i = alpha p_i q_i + p_i (gamma d_i + delta w2_i / sqrt n_i) + eps d_i^2
-// (the w2 term only where n_i > 0)
+// out_i (+)= alpha p_i q_i + p_i (gamma d_i + delta w2_i / sqrt n_i) + eps d_i^2 + kappa / n_i
+// (the w2 and 1/n terms only where n_i > 0; q may be null: its term is 0)
 __global__ void grad_ninv_kernel(const double* p, const double* q, const double* d, const double* ninv, double alpha,
-                                 double gamma, double delta, double eps, uint64_t seed, uint32_t rhs, int64_t npix,
-                                 double* out) {
+                                 double gamma, double delta, double eps, double kappa, uint64_t seed, uint32_t rhs,
+                                 int acc, int64_t npix, double* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
     const double pi = p[i];
-    double r = alpha * pi * q[i];
+    double r = q ? alpha * pi * q[i] : 0.0;
     if (d) {
       const double di = d[i];
       r += gamma * pi * di + eps * di * di;
     }
     const double n = ninv[i];
     if (delta != 0.0 && n > 0.0) r += delta * pi * draw_normal(seed, 4u, rhs, (uint64_t)i) / sqrt(n);
-    out[i] = r;
+    if (kappa != 0.0 && n > 0.0) r += kappa / n;
+    out[i] = acc ? out[i] + r : r;
   }
+}
+
+// Rademacher probes: element k of stream s for probe j takes word k & 3 of
+// Philox4x32-10 at counter (k >> 2, k >> 34, s, j); sign + for an even word.
+__device__ __forceinline__ double rademacher(uint64_t seed, uint32_t stream, uint32_t j, uint64_t k) {
+  const U4 x = philox4x32_10((uint32_t)(k >> 2), (uint32_t)(k >> 34), stream, j, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return (x.x[k & 3] & 1u) ? -1.0 : 1.0;
+}
+
+// coefficient probe in the real orthonormal basis: a_l0 = z, a_lm = (z_re + i z_im) / sqrt2
+__global__ void probe_alm_kernel(const double* sinv, int L, uint64_t seed, uint32_t j, double2* out) {
+  const int m = blockIdx.x;
+  const int64_t o = lm_off(L, m);
+  for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+    const int64_t i = o + (l - m);
+    double2 v = make_double2(0.0, 0.0);
+    if (sinv[l] > 0.0) {
+      const double zr = rademacher(seed, 5u, j, 2 * (uint64_t)i);
+      if (m == 0) {
+        v.x = zr;
+      } else {
+        v.x = zr * M_SQRT1_2;
+        v.y = rademacher(seed, 5u, j, 2 * (uint64_t)i + 1) * M_SQRT1_2;
+      }
+    }
+    out[i] = v;
+  }
+}
+
+// pixel probe on observed pixels (n_i > 0)
+__global__ void probe_map_kernel(const double* ninv, int64_t npix, uint64_t seed, uint32_t j, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = ninv[i] > 0.0 ? rademacher(seed, 6u, j, (uint64_t)i) : 0.0;
 }
 
 // sum_i n_i a_i b_i, fixed-order two-pass reduction
@@ -104,22 +141,24 @@ __global__ void wdot_partial_kernel(const double* a, const double* b, const doub
 
 using namespace cr;
 
-extern "C" int cr_grad_cl(cr_plan* plan, const void* u, const void* v, double alpha, double beta, uint64_t seed,
-                          int rhs, double* out) {
+extern "C" int cr_grad_cl(cr_plan* plan, const void* u, const void* v, double alpha, double beta, double kappa,
+                          uint64_t seed, int rhs, int accumulate, double* out) {
   if (!plan || !u || !out) return fail(CR_EINVAL, "cr_grad_cl: null argument");
   if (!plan->has_op) return fail(CR_EINVAL, "cr_grad_cl: the plan needs C_l");
   if (rhs < 0) return fail(CR_EINVAL, "cr_grad_cl: rhs < 0");
   const int L = plan->lmax;
   { grad_cl_kernel<<<L + 1, 256, 0, plan->stream>>>((const double2*)u, (const double2*)v, plan->d_sinv, L, alpha,
-                                                     beta, seed, (uint32_t)rhs, out); count_launch(); }
+                                                     beta, kappa, seed, (uint32_t)rhs, accumulate ? 1 : 0, out);
+    count_launch(); }
   CR_CHECK_LAUNCH("grad_cl_kernel");
   CR_CUDA(cudaStreamSynchronize(plan->stream));
   return CR_OK;
 }
 
 extern "C" int cr_grad_ninv(cr_plan* plan, const void* u, const void* v, const double* d, double alpha, double gamma,
-                            double delta, double eps, uint64_t seed, int rhs, double* out) {
-  if (!plan || !u || !v || !out) return fail(CR_EINVAL, "cr_grad_ninv: null argument");
+                            double delta, double eps, double kappa, uint64_t seed, int rhs, int accumulate,
+                            double* out) {
+  if (!plan || !u || !out) return fail(CR_EINVAL, "cr_grad_ninv: null argument");
   if (!plan->has_op) return fail(CR_EINVAL, "cr_grad_ninv: the plan needs C_l, b_l and N^-1");
   if (rhs < 0) return fail(CR_EINVAL, "cr_grad_ninv: rhs < 0");
   const Grid& g = plan->obs;
@@ -131,10 +170,11 @@ extern "C" int cr_grad_ninv(cr_plan* plan, const void* u, const void* v, const d
     return cuda_fail(e, "cudaMalloc(grad maps)");
   }
   int rc = do_synth<double>(plan, g, plan->lmax, u, p, plan->d_bl);
-  if (!rc) rc = do_synth<double>(plan, g, plan->lmax, v, q, plan->d_bl);
+  if (!rc && v) rc = do_synth<double>(plan, g, plan->lmax, v, q, plan->d_bl);
   if (!rc) {
-    { grad_ninv_kernel<<<1024, 256, 0, plan->stream>>>(p, q, d, plan->d_ninv, alpha, gamma, delta, eps, seed,
-                                                        (uint32_t)rhs, g.npix, out); count_launch(); }
+    { grad_ninv_kernel<<<1024, 256, 0, plan->stream>>>(p, v ? q : nullptr, d, plan->d_ninv, alpha, gamma, delta, eps,
+                                                        kappa, seed, (uint32_t)rhs, accumulate ? 1 : 0, g.npix, out);
+      count_launch(); }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "grad_ninv_kernel");
@@ -175,4 +215,21 @@ extern "C" int cr_alm_dot(cr_plan* plan, const void* u, const void* v, int weigh
   cudaFree(d);
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cr_alm_dot");
   return rc;
+}
+
+extern "C" int cr_probe(cr_plan* plan, uint64_t seed, int kind, int j, void* out) {
+  if (!plan || !out || j < 0) return fail(CR_EINVAL, "cr_probe: null argument or j < 0");
+  if (!plan->has_op) return fail(CR_EINVAL, "cr_probe: the plan needs C_l and N^-1");
+  if (kind == CR_PROBE_ALM) {
+    { probe_alm_kernel<<<plan->lmax + 1, 128, 0, plan->stream>>>(plan->d_sinv, plan->lmax, seed, (uint32_t)j,
+                                                                  (double2*)out); count_launch(); }
+  } else if (kind == CR_PROBE_MAP) {
+    { probe_map_kernel<<<1024, 256, 0, plan->stream>>>(plan->d_ninv, plan->obs.npix, seed, (uint32_t)j, (double*)out);
+      count_launch(); }
+  } else {
+    return fail(CR_EINVAL, "cr_probe: kind must be CR_PROBE_ALM or CR_PROBE_MAP");
+  }
+  CR_CHECK_LAUNCH("probe kernel");
+  CR_CUDA(cudaStreamSynchronize(plan->stream));
+  return CR_OK;
 }

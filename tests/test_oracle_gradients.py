@@ -79,3 +79,33 @@ def test_wf_data_term_woodbury_and_gradient():
         fd = (gradients.wf_data_term(rebuild(prob, ninv=npl), d)[0]
               - gradients.wf_data_term(rebuild(prob, ninv=nmi), d)[0]) / (2 * h)
         assert abs(fd - gn[i]) < 1e-6 * max(1.0, abs(fd)), (i, fd, gn[i])
+
+
+def test_logdet_gradient_matches_finite_differences_of_dense_logdet():
+    prob, rng = small_problem(0.3)
+    gcl, gn = gradients.logdet_grad_exact(prob)
+    f = lambda p: -0.5 * gradients.logdet_M(p)
+    for l in [0, 1, 3, 8]:
+        h = 1e-5 * prob.cl[l]
+        cp, cm = prob.cl.copy(), prob.cl.copy()
+        cp[l] += h
+        cm[l] -= h
+        fd = (f(rebuild(prob, cl=cp)) - f(rebuild(prob, cl=cm))) / (2 * h)
+        assert abs(fd - gcl[l]) < 1e-6 * max(1.0, abs(fd)), (l, fd, gcl[l])
+    for i in np.nonzero(prob.ninv > 0)[0][:4]:
+        h = 1e-5 * prob.ninv[i]
+        npl, nmi = prob.ninv.copy(), prob.ninv.copy()
+        npl[i] += h
+        nmi[i] -= h
+        fd = (f(rebuild(prob, ninv=npl)) - f(rebuild(prob, ninv=nmi))) / (2 * h)
+        assert abs(fd - gn[i]) < 1e-6 * max(1.0, abs(fd)), (i, fd, gn[i])
+
+
+def test_hutchinson_estimate_converges_to_exact_trace():
+    prob, rng = small_problem(0.3)
+    gcl, gn = gradients.logdet_grad_exact(prob)
+    hcl, hn = gradients.logdet_grad_hutchinson(prob, 31, 400)
+    act = prob.cl > 0
+    assert np.max(np.abs(hcl - gcl)[act] / np.abs(gcl[act])) < 0.1
+    obs = prob.ninv > 0
+    assert np.linalg.norm((hn - gn)[obs]) < 0.1 * np.linalg.norm(gn[obs])
