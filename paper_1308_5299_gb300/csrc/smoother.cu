@@ -811,34 +811,28 @@ int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
   }
   float* y = reinterpret_cast<float*>(P->hier_tile_work);
   const int nc = (int)pat.colour_start.size() - 1;
-  // levels with few tiles per colour: the 256-thread tiles (latency-bound)
-  if (pat.ntile <= 16384) {
-    for (int c = 0; c < nc; ++c) {
-      const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
-      if (p1 > p0)
-        { fwd_colour_w_kernel<T><<<p1 - p0, TKW, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_row_col, lev.d_perm,
-                                                               map_in, y, p0); count_launch(); }
-    }
-    CR_CHECK_LAUNCH("fwd_colour_w_kernel");
-    for (int c = nc - 1; c >= 0; --c) {
-      const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
-      if (p1 > p0)
-        { bwd_colour_w_kernel<T><<<p1 - p0, TKW, 0, P->stream>>>(lev.d_LT, lev.d_col_ptr, lev.d_col_row, lev.d_perm, y,
-                                                               map_out, p0); count_launch(); }
-    }
-    CR_CHECK_LAUNCH("bwd_colour_w_kernel");
-    return CR_OK;
-  }
+  // colours with few tiles are latency-bound: they get the 256-thread tiles
+  // (coarse levels throughout, and the small leftover colours of the fine
+  // levels); wide colours stream the factor with the 64-thread tiles
+  auto wide = [&](int c) { return pat.ntile <= 16384 || pat.colour_start[c + 1] - pat.colour_start[c] < 2048; };
   for (int c = 0; c < nc; ++c) {
     const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
-    if (p1 > p0)
-      { fwd_colour_kernel<T><<<p1 - p0, TK, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_row_col, lev.d_perm, map_in, y,
-                                                          p0); count_launch(); }
+    if (p1 <= p0) continue;
+    if (wide(c))
+      { fwd_colour_w_kernel<T><<<p1 - p0, TKW, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_row_col, lev.d_perm,
+                                                             map_in, y, p0); count_launch(); }
+    else
+      { fwd_colour_kernel<T><<<p1 - p0, TK, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_row_col, lev.d_perm, map_in,
+                                                          y, p0); count_launch(); }
   }
   CR_CHECK_LAUNCH("fwd_colour_kernel");
   for (int c = nc - 1; c >= 0; --c) {
     const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
-    if (p1 > p0)
+    if (p1 <= p0) continue;
+    if (wide(c))
+      { bwd_colour_w_kernel<T><<<p1 - p0, TKW, 0, P->stream>>>(lev.d_LT, lev.d_col_ptr, lev.d_col_row, lev.d_perm, y,
+                                                             map_out, p0); count_launch(); }
+    else
       { bwd_colour_kernel<T><<<p1 - p0, TK, 0, P->stream>>>(lev.d_LT, lev.d_col_ptr, lev.d_col_row, lev.d_perm, y,
                                                           map_out, p0); count_launch(); }
   }
