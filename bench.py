@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cg", action="store_true", help="skip the CG comparison on the Nside 256 workload")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float outer-residual variant")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched mixed-resolution measurement")
+    ap.add_argument("--no-graph", action="store_true", help="time the solves launched directly, not as a CUDA graph")
     ap.add_argument("--ref-cycles", type=int, default=2,
                     help="cycles per realization priced by the reference arm (the GPU arm's measured count)")
     return ap.parse_args()
@@ -306,17 +307,27 @@ def df_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv, x_true,
         plan.solve(b, x, eps=0.0, max_cycles=cyc, mode=mode, check=False)
         if max_pixel_error(plan, x, x_true, npix, dev) < 1.0:
             break
+    graph = None if args.no_graph else binding.Batch([plan], [x], [b], cyc, binding.CR_MIXED)
+
+    def step():
+        if graph is not None:
+            graph.run()
+        else:
+            plan.solve(b, x, eps=0.0, max_cycles=cyc, mode=mode, check=False)
+
     for _ in range(args.warmup):
-        plan.solve(b, x, eps=0.0, max_cycles=cyc, mode=mode, check=False)
+        step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.solve(b, x, eps=0.0, max_cycles=cyc, mode=mode, check=False)
+        step()
     e1.record(stream)
     torch.cuda.synchronize()
     s = e0.elapsed_time(e1) * 1e-3 / args.steps
     err = max_pixel_error(plan, x, x_true, npix, dev)
+    if graph is not None:
+        graph.close()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     y = torch.empty_like(b)
     a0.record(stream)
@@ -461,7 +472,9 @@ def main():
     cfg, cl, bl, ninv = synthetic.problem_inputs(args.workload)
     nside, lmax = cfg["nside"], cfg["lmax"]
     npix = 12 * nside * nside
-    stream = torch.cuda.current_stream(dev)
+    # a created stream (the legacy default stream cannot be captured into a graph)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev), stream=stream,
@@ -495,25 +508,47 @@ def main():
     def solve_mixed():
         plan.solve(b, x, eps=0.0, max_cycles=cyc_mixed, mode=mode_mixed | binding.CR_FIXED, check=False)
 
+    # the fixed-count solve captured once into a CUDA graph (stationary form):
+    # one launch per realization; the direct launches are timed beside it
+    graph = None
+    if not (mode_mixed & binding.CR_PCG) and not args.no_graph:
+        graph = binding.Batch([plan], [x], [b], cyc_mixed, mode_mixed)
+
+    def step():
+        if graph is not None:
+            graph.run()
+        else:
+            solve_mixed()
+
     for _ in range(args.warmup):
-        solve_mixed()
+        step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plan.set_timing(True)  # per-stage CUDA events on the plan's stream
     l0 = binding.launch_count()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
-            solve_mixed()
+            step()
         e1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-    launches = binding.launch_count() - l0
+    launches = (graph.kernel_nodes() * args.steps) if graph is not None else binding.launch_count() - l0
     ms = e0.elapsed_time(e1) / args.steps
+    # the same solves launched directly, with per-stage CUDA events (the
+    # kernel-level breakdown and the roofline come from this region)
+    plan.set_timing(True)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    d0.record(stream)
+    for _ in range(args.steps):
+        solve_mixed()
+    d1.record(stream)
+    torch.cuda.synchronize()
+    ms_direct = d0.elapsed_time(d1) / args.steps
     stages = plan.timing()
     plan.set_timing(False)
     if world > 1:
@@ -553,8 +588,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps // 2)):
-        bd = bh.to(dev, non_blocking=True)
-        plan.solve(bd, x, eps=0.0, max_cycles=cyc_mixed, mode=mode_mixed | binding.CR_FIXED, check=False)
+        b.copy_(bh, non_blocking=True)  # the graph reads b and writes x at their bound addresses
+        step()
         xh.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
@@ -568,6 +603,8 @@ def main():
         kind, nring, npx = plan.level_grid(h)
         level_rows.append((lv["nside_h"], lv["lmax_h"], lv["n_rec"], (nring, npx // nring) if kind == "gl" else None))
     mixed_df = None
+    if graph is not None:
+        graph.close()
     if not args.no_df:
         del plan
         torch.cuda.synchronize()
@@ -591,6 +628,8 @@ def main():
                    "l2": "inputs larger than L2 (N^-1 403 MB, phase 393 MB, smoother factors ~20 GB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "max_pixel_error_uK": {"mixed": err_timed, "mixed_calibration": err_mixed, "fp64": err_f64},
+        "launch": "cuda_graph" if graph is not None else "direct",
+        "direct_launch_s_per_realization": ms_direct * 1e-3,
         "fp64": {"s_per_realization": f64_s, "cycles": cyc_f64, "pcg": bool(mode_f64 & binding.CR_PCG)},
         "mixed_pcg": bool(mode_mixed & binding.CR_PCG),
         "sht_pairs_per_s": {"f64": pairs_f64, "f32": pairs_f32},

@@ -255,7 +255,8 @@ int cr_alm_dot(cr_plan* plan, const void* u, const void* v, int weighted, double
  * the graph, so later runs read b and write x at the same addresses.  mode:
  * CR_F64 or CR_MIXED (stationary).  cr_batch_run launches the graph on that
  * stream (asynchronous); replays give results identical to the uncaptured
- * solves.  cr_batch_nodes: number of graph nodes (kernels and copies).
+ * solves.  cr_batch_nodes: number of graph nodes (kernels and copies) and of
+ * kernel nodes (either pointer may be NULL).
  * Errors: CR_EINVAL (plans without levels, on different streams or on the
  * legacy default stream, which cannot be captured; bad mode), CR_ECUDA.  The
  * plans must outlive the batch.
@@ -264,7 +265,7 @@ typedef struct cr_batch cr_batch;
 int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* const* x, const void* const* b,
                     const int* nrhs, int cycles, int mode);
 int cr_batch_run(cr_batch* batch);
-int cr_batch_nodes(const cr_batch* batch, int64_t* nodes);
+int cr_batch_nodes(const cr_batch* batch, int64_t* nodes, int64_t* kernels);
 int cr_batch_destroy(cr_batch* batch);
 
 /* Release every resource of the plan (NULL is accepted). */

@@ -88,7 +88,8 @@ _SIGS = {
                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                          ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "cr_batch_run": ([ctypes.c_void_p], ctypes.c_int),
-    "cr_batch_nodes": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cr_batch_nodes": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+                       ctypes.c_int),
     "cr_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "cr_grad_cl": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                     ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
@@ -449,8 +450,13 @@ class Batch:
 
     def nodes(self):
         n = ctypes.c_int64()
-        _check(lib().cr_batch_nodes(self._h, ctypes.byref(n)))
+        _check(lib().cr_batch_nodes(self._h, ctypes.byref(n), None))
         return n.value
+
+    def kernel_nodes(self):
+        k = ctypes.c_int64()
+        _check(lib().cr_batch_nodes(self._h, None, ctypes.byref(k)))
+        return k.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -22,6 +22,7 @@ struct cr_batch {
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
   size_t nodes = 0;
+  int64_t kernels = 0;  // kernel nodes
 };
 
 using namespace cr;
@@ -76,6 +77,17 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
     e = cudaGraphGetNodes(bt->graph, nullptr, &bt->nodes);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphGetNodes");
   }
+  if (!rc && bt->nodes) {
+    std::vector<cudaGraphNode_t> nodes(bt->nodes);
+    size_t n = bt->nodes;
+    e = cudaGraphGetNodes(bt->graph, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[i], &t);
+      if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++bt->kernels;
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "graph node types");
+  }
   if (rc) {
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->graph) cudaGraphDestroy(bt->graph);
@@ -92,9 +104,10 @@ int cr_batch_run(cr_batch* bt) {
   return CR_OK;
 }
 
-int cr_batch_nodes(const cr_batch* bt, int64_t* nodes) {
-  if (!bt || !nodes) return fail(CR_EINVAL, "cr_batch_nodes: null argument");
-  *nodes = (int64_t)bt->nodes;
+int cr_batch_nodes(const cr_batch* bt, int64_t* nodes, int64_t* kernels) {
+  if (!bt) return fail(CR_EINVAL, "cr_batch_nodes: null argument");
+  if (nodes) *nodes = (int64_t)bt->nodes;
+  if (kernels) *kernels = bt->kernels;
   return CR_OK;
 }
 
