@@ -268,6 +268,15 @@ int cr_batch_run(cr_batch* batch);
 int cr_batch_nodes(const cr_batch* batch, int64_t* nodes, int64_t* kernels);
 int cr_batch_destroy(cr_batch* batch);
 
+/*
+ * Tensor-core self-test: one 128 x 32 x K tile (K in {16, 32, 48, 64}) of
+ * BF16 products accumulated in FP32 tensor memory by tcgen05.mma, against the
+ * same product on the CUDA cores; *max_abs_err receives the largest
+ * difference (0 for a correct tile: the inputs are small integers).  Errors:
+ * CR_EINVAL (bad K), CR_ECUDA (including a completion wait that gave up).
+ */
+int cr_tc_selftest(int K, float* max_abs_err);
+
 /* Release every resource of the plan (NULL is accepted). */
 int cr_plan_destroy(cr_plan* plan);
 

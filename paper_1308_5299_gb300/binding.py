@@ -83,6 +83,7 @@ _SIGS = {
                              ctypes.c_int),
     "cr_plan_set_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_launch_count": ([], ctypes.c_long),
+    "cr_tc_selftest": ([ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "cr_plan_nlevels": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "cr_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -161,6 +162,13 @@ def _dev(t):
 
 def n_lm(lmax):
     return (lmax + 1) * (lmax + 2) // 2
+
+
+def tc_selftest(K=64):
+    """Largest |difference| of a 128 x 32 x K tcgen05 BF16 tile against the CUDA cores (cr_tc_selftest)."""
+    e = ctypes.c_float()
+    _check(lib().cr_tc_selftest(int(K), ctypes.byref(e)))
+    return e.value
 
 
 def launch_count():
