@@ -58,6 +58,11 @@ extern "C" {
 /* arithmetic of a call */
 #define CR_F64 0
 #define CR_F32 1
+/* dtype of cr_sht_synth only: FP32 data (complex64 alm, float32 maps), many
+ * right-hand sides, the Legendre contraction on the tensor cores (tcgen05,
+ * BF16 operands, FP32 accumulation; 16 right-hand sides per launch): about
+ * BF16 accuracy (1e-2 relative) for batched throughput. */
+#define CR_TC 3
 /* solve mode: FP32 W-cycles inside an FP64 iterative-refinement loop */
 #define CR_MIXED 2
 /* solve flag (or-ed with CR_F64 / CR_MIXED): flexible preconditioned CG with

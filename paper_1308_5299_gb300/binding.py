@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libcrgb300.so")
 CR_OK = 0
 CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED, CR_CG = 0, 1, 2, 4, 8, 16
 CR_DRAW_FLUCT, CR_DRAW_PLAIN = 1, 2
+CR_TC = 3
 CR_PROBE_ALM, CR_PROBE_MAP = 0, 1
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0
@@ -282,12 +283,20 @@ class Plan:
             raise ValueError("tensor size %d is not a multiple of %d" % (t.numel(), per))
         return t.numel() // per
 
-    def sht_synth(self, alm, out, grid=CR_OBS):
+    def sht_synth(self, alm, out, grid=CR_OBS, tensor_cores=False):
+        """map = Y alm for every right-hand side; tensor_cores=True (complex64
+        / float32 data): batched Legendre contraction on the tensor cores
+        (CR_TC, BF16 operands, FP32 accumulation)."""
         s = self.sizes(grid)
         nrhs = self._nrhs(alm, s["nlm"])
         if out.numel() != nrhs * s["npix"] or _dtype_code(alm) != _dtype_code(out):
             raise ValueError("sht_synth: output shape/dtype")
-        _check(lib().cr_sht_synth(self._h, grid, _dev(alm), _dev(out), nrhs, _dtype_code(alm)))
+        code = _dtype_code(alm)
+        if tensor_cores:
+            if code != CR_F32:
+                raise TypeError("tensor-core synthesis takes complex64 / float32 data")
+            code = CR_TC
+        _check(lib().cr_sht_synth(self._h, grid, _dev(alm), _dev(out), nrhs, code))
         return out
 
     def sht_adjoint(self, map_, out, grid=CR_OBS):

@@ -323,7 +323,7 @@ static void plan_free(cr_plan* P) {
   }
   void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_c2_32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
                   P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial, P->d_pcinv, P->cgv[0], P->cgv[1],
-                  P->cgv[2], P->cgv[3], P->d_cgdot};
+                  P->cgv[2], P->cgv[3], P->d_cgdot, P->tc_phase, P->d_tc_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -643,11 +643,55 @@ static int check_ptr(const void* p, int dtype) {
   return CR_OK;
 }
 
+// batched synthesis with the Legendre contraction on the tensor cores (BF16
+// operands, FP32 accumulation; legendre_tc.cu), FP32 data, 16 right-hand
+// sides per Legendre launch, then the FP32 ring FFTs per right-hand side
+static int tc_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, int nrhs) {
+  const int64_t need = (int64_t)16 * g.nring * (L + 1) * (int64_t)sizeof(float2);
+  if (need > P->tc_phase_bytes) {
+    if (P->tc_phase) cudaFree(P->tc_phase);
+    P->tc_phase = nullptr;
+    CR_CUDA(cudaMalloc(&P->tc_phase, need));
+    P->tc_phase_bytes = need;
+  }
+  if (!P->d_tc_status) CR_CUDA(cudaMalloc(&P->d_tc_status, sizeof(int)));
+  CR_CUDA(cudaMemsetAsync(P->d_tc_status, 0, sizeof(int), P->stream));
+  LegArgs<float> la = leg_args<float>(P, g, L);
+  const int64_t nlm = n_lm(L);
+  for (int r0 = 0; r0 < nrhs; r0 += 16) {
+    const int nr = std::min(16, nrhs - r0);
+    const float2* a = reinterpret_cast<const float2*>(alm) + (int64_t)r0 * nlm;
+    int rc;
+    {
+      TimerScope ts(P->timing, P->stream, "legendre_synth_tc", 8.0 * g.npairs * (double)nlm * nr);
+      rc = launch_tc_synth(la, a, nlm, nr, reinterpret_cast<float2*>(P->tc_phase), P->d_tc_status, P->stream);
+    }
+    if (rc) return rc;
+    for (int r = 0; r < nr; ++r) {
+      RingArgs<float> ra = ring_args<float>(P, g, L);
+      ra.phase = reinterpret_cast<float2*>(P->tc_phase) + (int64_t)r * g.nring * (L + 1);
+      ra.map_out = reinterpret_cast<float*>(map) + (int64_t)(r0 + r) * g.npix;
+      TimerScope ts(P->timing, P->stream, "ring_fft_synth_f32", fft_bytes<float>(g, L, 1));
+      if ((rc = launch_ring_fft<float>(ra, 0, P->stream))) return rc;
+    }
+  }
+  int st = 0;
+  CR_CUDA(cudaMemcpyAsync(&st, P->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CR_CUDA(cudaStreamSynchronize(P->stream));
+  if (st) return fail(CR_ECUDA, "tensor-core synthesis: a completion wait gave up");
+  return CR_OK;
+}
+
 int cr_sht_synth(cr_plan* plan, int grid, const void* alm, void* map, int nrhs, int dtype) {
   if (!plan) return fail(CR_EINVAL, "cr_sht_synth: null plan");
   int L = 0;
   const Grid* g = grid_of(plan, grid, &L);
   if (!g) return fail(CR_EINVAL, "cr_sht_synth: unknown grid");
+  if (nrhs >= 0 && dtype == CR_TC) {
+    if (nrhs == 0) return CR_OK;
+    if (check_ptr(alm, CR_F32) || check_ptr(map, CR_F32)) return CR_EINVAL;
+    return tc_synth(plan, *g, L, alm, map, nrhs);
+  }
   if (nrhs < 0 || (dtype != CR_F64 && dtype != CR_F32)) return fail(CR_EINVAL, "cr_sht_synth: nrhs/dtype");
   if (nrhs == 0) return CR_OK;
   if (check_ptr(alm, dtype) || check_ptr(map, dtype)) return CR_EINVAL;

@@ -144,6 +144,9 @@ struct cr_plan {
   cr::Timing timing;
   int fp64_df = 0;  // FP64 Legendre stages in double-float arithmetic
   bool capturing = false;  // inside a CUDA-graph capture: no host synchronisation
+  void* tc_phase = nullptr;  // batched tensor-core synthesis: [16][nring][L+1] complex64
+  int64_t tc_phase_bytes = 0;
+  int* d_tc_status = nullptr;
   cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)
   void* hier_tile_work = nullptr;     // FP32 tile-ordered smoother work vector
   // diagonal-preconditioned CG (created on first use)
