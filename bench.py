@@ -408,11 +408,30 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
         errs = errors()
         nodes = graph.nodes()
         graph.close()
+        # batched synthesis of the 16 Nside 1024 solutions: Legendre
+        # contraction on the tensor cores vs 16 FP32 syntheses
+        p0, x0 = plans[0], xs[0]
+        x32 = x0.to(torch.complex64)
+        maps = torch.empty((x32.shape[0], npx[0]), dtype=torch.float32, device=dev)
+        p0.sht_synth(x32, maps, tensor_cores=True)
+        torch.cuda.synchronize()
+        t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        t0.record(st)
+        p0.sht_synth(x32, maps, tensor_cores=True)
+        t1.record(st)
+        for j in range(x32.shape[0]):
+            p0.sht_synth(x32[j], maps[j])
+        t2.record(st)
+        torch.cuda.synchronize()
+        tc_ms, f32_ms = t0.elapsed_time(t1), t1.elapsed_time(t2)
     return {"workload": "%d x (Nside 1024, lmax 2047) + %d x (Nside 512, lmax 1023)" % (nrhs, nrhs),
             "cycles": cycles, "realizations": total, "graph_nodes": nodes,
             "graph_realizations_per_s": total / t_graph, "graph_s": t_graph,
             "direct_realizations_per_s": total / t_direct, "direct_s": t_direct,
-            "max_pixel_error_uK": {"max": max(errs), "median": float(np.median(errs))}}
+            "max_pixel_error_uK": {"max": max(errs), "median": float(np.median(errs))},
+            "synthesis_16rhs_nside1024": {"tensor_core_ms": tc_ms, "fp32_ms": f32_ms,
+                                          "note": "Legendre contraction on tcgen05 (BF16 in, FP32 accumulation) "
+                                                  "vs the FP32 CUDA-core kernels; ring FFTs included in both"}}
 
 
 def cg_comparison(binding, synthetic, dev, stream, workload="nside256_lmax767"):

@@ -72,10 +72,12 @@ __global__ void __launch_bounds__(TS_M) tc_synth_kernel(TsArgs a, int nbp, int y
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t taddr_s;
   __shared__ int s_min;
-  const int m = blockIdx.x;
+  // blockIdx.x runs over ring-pair blocks and blockIdx.y over m, so the
+  // blocks sharing an m's coefficients run together and share them in L2
+  const int m = blockIdx.y;
   const int L = a.L;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int yb = (int)blockIdx.y + yoff;
+  const int yb = (int)blockIdx.x + yoff;
   const int base = POLAR ? yb * TS_M : a.npolar + (yb - nbp) * TS_M;
   const int pend = POLAR ? a.npolar : a.npairs;
   const int p = base + tid;
@@ -140,20 +142,30 @@ __global__ void __launch_bounds__(TS_M) tc_synth_kernel(TsArgs a, int nbp, int y
       sfac[tid] = in ? a.s[offc + (l - m)] * (a.dl ? a.dl[l] : 1.f) : 0.f;
     }
     __syncthreads();
-    // B operands: rows 2 r (re) and 2 r + 1 (im), K index k: l = l0 + 2 k (+1 for odd)
-    for (int e = tid; e < TS_RHS * 2 * TS_KC; e += TS_M) {
-      const int r = e / (2 * TS_KC), j = e % (2 * TS_KC);  // j = l - l0
-      const int k = j >> 1;
-      float vr = 0.f, vi = 0.f;
-      const int l = l0 + j;
-      if (r < a.nrhs && l <= L) {
-        const float2 av = a.alm[r * a.ld_alm + offa + (l - m)];
-        vr = av.x * sfac[j];
-        vi = (m == 0) ? 0.f : av.y * sfac[j];
+    // B operands: rows 2 r (re) and 2 r + 1 (im), K index k: l = l0 + 2 k
+    // (+1 for odd); each task packs 8 K values of both rows of one
+    // right-hand side and parity into two 16-byte stores
+    for (int e = tid; e < TS_RHS * 2 * (TS_KC / 8); e += TS_M) {
+      const int r = e / (2 * (TS_KC / 8)), rem = e % (2 * (TS_KC / 8));
+      const int par = rem & 1, k8 = rem >> 1;
+      float vr[8], vi[8];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int j = 2 * (k8 * 8 + kk) + par;  // l - l0
+        const int l = l0 + j;
+        vr[kk] = 0.f;
+        vi[kk] = 0.f;
+        if (r < a.nrhs && l <= L) {
+          const float2 av = a.alm[r * a.ld_alm + offa + (l - m)];
+          vr[kk] = av.x * sfac[j];
+          vi[kk] = (m == 0) ? 0.f : av.y * sfac[j];
+        }
       }
-      uint8_t* B = (j & 1) ? BO : BE;
-      *reinterpret_cast<__nv_bfloat16*>(B + tc::kmajor_offset(2 * r, k, TS_KC)) = __float2bfloat16(vr);
-      *reinterpret_cast<__nv_bfloat16*>(B + tc::kmajor_offset(2 * r + 1, k, TS_KC)) = __float2bfloat16(vi);
+      uint8_t* B = par ? BO : BE;
+      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * r, k8 * 8, TS_KC)) =
+          make_uint4(pack_bf16(vr[0], vr[1]), pack_bf16(vr[2], vr[3]), pack_bf16(vr[4], vr[5]), pack_bf16(vr[6], vr[7]));
+      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * r + 1, k8 * 8, TS_KC)) =
+          make_uint4(pack_bf16(vi[0], vi[1]), pack_bf16(vi[2], vi[3]), pack_bf16(vi[4], vi[5]), pack_bf16(vi[6], vi[7]));
     }
     // A operands: this thread's row, 8 K values (16 l) per 16-byte store;
     // chunks the pair covers entirely run without per-step checks
@@ -267,8 +279,9 @@ int launch_tc_synth(const LegArgs<float>& la, const float2* alm, int64_t ld_alm,
   const size_t smem = 2 * (size_t)TS_STAGE;
   CR_CUDA(cudaFuncSetAttribute(tc_synth_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CR_CUDA(cudaFuncSetAttribute(tc_synth_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (nbp) { tc_synth_kernel<true><<<dim3(la.L + 1, nbp), TS_M, smem, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { tc_synth_kernel<false><<<dim3(la.L + 1, nbe), TS_M, smem, st>>>(a, nbp, nbp); count_launch(); }
+  if (la.L + 1 > 65535) return fail(CR_EINVAL, "tensor-core synthesis: lmax too large for the grid");
+  if (nbp) { tc_synth_kernel<true><<<dim3(nbp, la.L + 1), TS_M, smem, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { tc_synth_kernel<false><<<dim3(nbe, la.L + 1), TS_M, smem, st>>>(a, nbp, nbp); count_launch(); }
   CR_CHECK_LAUNCH("tc_synth_kernel");
   return CR_OK;
 }
