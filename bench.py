@@ -424,6 +424,26 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
         t2.record(st)
         torch.cuda.synchronize()
         tc_ms, f32_ms = t0.elapsed_time(t1), t1.elapsed_time(t2)
+        # the system matrix on the same 16 vectors: both Legendre stages on
+        # the tensor cores vs 16 FP32 applications; accuracy against FP64
+        y32 = torch.empty_like(x32)
+        p0.apply_A(x32, y32, tensor_cores=True)
+        torch.cuda.synchronize()
+        t0.record(st)
+        p0.apply_A(x32, y32, tensor_cores=True)
+        t1.record(st)
+        yf = torch.empty_like(x32)
+        for j in range(x32.shape[0]):
+            p0.apply_A(x32[j], yf[j])
+        t2.record(st)
+        torch.cuda.synchronize()
+        atc_ms, af32_ms = t0.elapsed_time(t1), t1.elapsed_time(t2)
+        y64 = torch.empty_like(x0)
+        p0.apply_A(x0, y64)
+        torch.cuda.synchronize()
+        rel_tc = float(torch.linalg.vector_norm(y32.to(torch.complex128) - y64) / torch.linalg.vector_norm(y64))
+        rel_f32 = float(torch.linalg.vector_norm(yf.to(torch.complex128) - y64) / torch.linalg.vector_norm(y64))
+        del y32, yf, y64
     return {"workload": "%d x (Nside 1024, lmax 2047) + %d x (Nside 512, lmax 1023)" % (nrhs, nrhs),
             "cycles": cycles, "realizations": total, "graph_nodes": nodes,
             "graph_realizations_per_s": total / t_graph, "graph_s": t_graph,
@@ -431,7 +451,11 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
             "max_pixel_error_uK": {"max": max(errs), "median": float(np.median(errs))},
             "synthesis_16rhs_nside1024": {"tensor_core_ms": tc_ms, "fp32_ms": f32_ms,
                                           "note": "Legendre contraction on tcgen05 (BF16 in, FP32 accumulation) "
-                                                  "vs the FP32 CUDA-core kernels; ring FFTs included in both"}}
+                                                  "vs the FP32 CUDA-core kernels; ring FFTs included in both"},
+            "apply_A_16rhs_nside1024": {"tensor_core_ms": atc_ms, "fp32_ms": af32_ms,
+                                        "rel_l2_vs_f64": {"tensor_core": rel_tc, "fp32": rel_f32},
+                                        "note": "A = S^-1 + B Y^T N^-1 Y B, both Legendre stages on tcgen05 "
+                                                "vs the FP32 CUDA-core kernels"}}
 
 
 def cg_comparison(binding, synthetic, dev, stream, workload="nside256_lmax767"):

@@ -58,10 +58,12 @@ extern "C" {
 /* arithmetic of a call */
 #define CR_F64 0
 #define CR_F32 1
-/* dtype of cr_sht_synth only: FP32 data (complex64 alm, float32 maps), many
- * right-hand sides, the Legendre contraction on the tensor cores (tcgen05,
- * BF16 operands, FP32 accumulation; 16 right-hand sides per launch): about
- * BF16 accuracy (1e-2 relative) for batched throughput. */
+/* dtype of cr_sht_synth, cr_sht_adjoint and cr_apply_A (level 0): FP32 data
+ * (complex64 alm, float32 maps), many right-hand sides, the Legendre
+ * contractions on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation; 16 right-hand sides per launch): about BF16 accuracy (1e-2
+ * relative) for batched throughput.  The call synchronises the plan's
+ * stream to read the kernels' completion status (CR_ECUDA if a wait gave up). */
 #define CR_TC 3
 /* solve mode: FP32 W-cycles inside an FP64 iterative-refinement loop */
 #define CR_MIXED 2
@@ -292,7 +294,8 @@ int cr_plan_sizes(const cr_plan* plan, int grid, int64_t* npix, int* nring, int*
 /*
  * Spherical-harmonic synthesis, map = Y alm (Section 2.1, Eq. sh-synthesis):
  *   map(n_i) = sum_{l<=L, |m|<=l} a_lm Y_lm(n_i),  real field.
- * alm: [nrhs][N_lm] complex; map: [nrhs][npix] real; dtype CR_F64/CR_F32.
+ * alm: [nrhs][N_lm] complex; map: [nrhs][npix] real; dtype CR_F64, CR_F32
+ * or CR_TC.
  * Band limits above what a ring resolves alias by folding m mod n_ring, so
  * Y^T below stays its exact transpose.
  */
@@ -301,7 +304,8 @@ int cr_sht_synth(cr_plan* plan, int grid, const void* alm, void* map, int nrhs, 
 /*
  * Adjoint synthesis, alm = Y^T map (Section 2.1: the transpose of Y, with no
  * quadrature weights):  a_lm = sum_i conj(Y_lm(n_i)) map_i.
- * map: [nrhs][npix]; alm: [nrhs][N_lm] (overwritten).
+ * map: [nrhs][npix]; alm: [nrhs][N_lm] (overwritten); dtype CR_F64, CR_F32
+ * or CR_TC.
  */
 int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs, int dtype);
 
@@ -311,6 +315,7 @@ int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs
  * diagonals.  level 0 is the full system; level h >= 1 applies the level
  * operator A_h = D_h + B_h Y^T N^-1 Y B_h (Section 3.2, Eq. A_h) at that
  * level's band limit.  x, y: [nrhs][N_lm]; x and y must not overlap.
+ * dtype CR_F64, CR_F32, or at level 0 CR_TC (batched, tensor cores).
  * Requires a plan created with cl.  Errors: CR_EINVAL, CR_ESTATE, CR_ECUDA.
  */
 int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int dtype);

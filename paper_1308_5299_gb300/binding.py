@@ -177,6 +177,14 @@ def launch_count():
     return int(lib().cr_launch_count())
 
 
+def _tc_code(code, tensor_cores, what):
+    if not tensor_cores:
+        return code
+    if code != CR_F32:
+        raise TypeError("tensor-core %s takes complex64 / float32 data" % what)
+    return CR_TC
+
+
 def sht_synth_noalloc(nside, lmax, alm, out, stream=None):
     """FP64 synthesis with no plan and no allocation (``cr_sht_synth_noalloc``):
     for callers that cannot allocate device memory.  ``alm`` complex128 and
@@ -292,19 +300,20 @@ class Plan:
         if out.numel() != nrhs * s["npix"] or _dtype_code(alm) != _dtype_code(out):
             raise ValueError("sht_synth: output shape/dtype")
         code = _dtype_code(alm)
-        if tensor_cores:
-            if code != CR_F32:
-                raise TypeError("tensor-core synthesis takes complex64 / float32 data")
-            code = CR_TC
+        code = _tc_code(code, tensor_cores, "synthesis")
         _check(lib().cr_sht_synth(self._h, grid, _dev(alm), _dev(out), nrhs, code))
         return out
 
-    def sht_adjoint(self, map_, out, grid=CR_OBS):
+    def sht_adjoint(self, map_, out, grid=CR_OBS, tensor_cores=False):
+        """alm = Y^T map for every right-hand side; tensor_cores=True (float32
+        / complex64 data): batched Legendre contraction on the tensor cores
+        (CR_TC)."""
         s = self.sizes(grid)
         nrhs = self._nrhs(map_, s["npix"])
         if out.numel() != nrhs * s["nlm"] or _dtype_code(map_) != _dtype_code(out):
             raise ValueError("sht_adjoint: output shape/dtype")
-        _check(lib().cr_sht_adjoint(self._h, grid, _dev(map_), _dev(out), nrhs, _dtype_code(map_)))
+        code = _tc_code(_dtype_code(map_), tensor_cores, "adjoint")
+        _check(lib().cr_sht_adjoint(self._h, grid, _dev(map_), _dev(out), nrhs, code))
         return out
 
     def set_timing(self, enable=True):
@@ -440,9 +449,14 @@ class Plan:
         out = (list(cyc), list(rel), hist)
         return out if check else out + (rc,)
 
-    def apply_A(self, x, out, level=0):
+    def apply_A(self, x, out, level=0, tensor_cores=False):
+        """out = A x; tensor_cores=True (level 0, complex64): both Legendre
+        stages of every 16 right-hand sides on the tensor cores (CR_TC)."""
         nrhs = self._nrhs(x, n_lm(self.lmax)) if level == 0 else x.numel() // max(1, out.numel())
-        _check(lib().cr_apply_A(self._h, level, _dev(x), _dev(out), nrhs, _dtype_code(x)))
+        if tensor_cores and level != 0:
+            raise ValueError("apply_A: tensor cores at level 0 only")
+        code = _tc_code(_dtype_code(x), tensor_cores, "apply_A")
+        _check(lib().cr_apply_A(self._h, level, _dev(x), _dev(out), nrhs, code))
         return out
 
 

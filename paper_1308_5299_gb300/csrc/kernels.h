@@ -76,6 +76,10 @@ int leg_partial_blocks(int npairs);
 int df_pair_blocks(int npairs);
 int launch_tc_synth(const LegArgs<float>& la, const float2* alm, int64_t ld_alm, int nrhs, float2* phase,
                     int* status, cudaStream_t st);
+int launch_tc_adjoint(const LegArgs<float>& la, const float2* phase, int nrhs, float2* partial, int* nblk,
+                      int* status, cudaStream_t st);
+int tc_adjoint_blocks(int npolar, int npairs);
+template <typename T> int launch_leg_finalize(const FinalizeArgs<T>& f, cudaStream_t st);
 int launch_leg_synth_df(const LegArgs<double>& a, cudaStream_t st);
 int launch_leg_adjoint_df(const LegArgs<double>& a, int* nblk, cudaStream_t st);
 int launch_leg_diag(cr_plan* P, const double* ringval, double2* out);

@@ -466,9 +466,14 @@ int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream
   ff.partial = a.partial;
   ff.nblk = nbp + nbe;
   ff.L = a.L;
-  const int64_t nlm = n_lm(a.L);
+  return launch_leg_finalize<T>(ff, st);
+}
+
+template <typename T>
+int launch_leg_finalize(const FinalizeArgs<T>& f, cudaStream_t st) {
+  const int64_t nlm = n_lm(f.L);
   int blocks = (int)std::min<int64_t>((nlm + 255) / 256, 152 * 16);
-  { leg_finalize_kernel<T><<<blocks, 256, 0, st>>>(ff); count_launch(); }
+  { leg_finalize_kernel<T><<<blocks, 256, 0, st>>>(f); count_launch(); }
   CR_CHECK_LAUNCH("leg_finalize_kernel");
   return CR_OK;
 }
@@ -586,6 +591,8 @@ int leg_partial_blocks(int npairs) {
 
 template int launch_leg_synth<double>(const LegArgs<double>&, cudaStream_t);
 template int launch_leg_synth<float>(const LegArgs<float>&, cudaStream_t);
+template int launch_leg_finalize<double>(const FinalizeArgs<double>&, cudaStream_t);
+template int launch_leg_finalize<float>(const FinalizeArgs<float>&, cudaStream_t);
 template int launch_leg_adjoint<double>(const LegArgs<double>&, const FinalizeArgs<double>&, cudaStream_t);
 template int launch_leg_adjoint<float>(const LegArgs<float>&, const FinalizeArgs<float>&, cudaStream_t);
 

@@ -286,4 +286,270 @@ int launch_tc_synth(const LegArgs<float>& la, const float2* alm, int64_t ld_alm,
   return CR_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched adjoint Legendre stage on the tensor cores.
+//
+// For many right-hand sides the adjoint Legendre stage is, per m, the
+// contraction a_lm[rhs] = s_lm sum_pairs Q_l(z_pair) G[pair, rhs] over ring
+// pairs, with G = G_m(z) + G_m(-z) for even l - m and G_m(z) - G_m(-z) for
+// odd (Section 2.1, Eq. sh-synthesis transposed).  One CTA per (m, 128 ring
+// pairs); K runs over the CTA's pairs, so each chunk of 128 l is one
+// complete product D[l, 64] = Q[l, pairs] G[pairs, 64] whose 64 columns hold
+// the even-parity combination (16 right-hand sides x re, im) and the odd one:
+// a row keeps the half of its own parity (the other half costs MMA work only,
+// which is far from the bound).  Each thread runs its pair's FP32 recurrence
+// (start tables, polar difference form as in legendre.cu); 8 consecutive l of
+// 8 neighbouring pairs are transposed with warp shuffles so that every lane
+// writes one 16-byte K-major row segment.  G is staged once per CTA the same
+// way.  The product is read back from tensor memory after each chunk, scaled
+// by s_lm and written as one partial row per ring-pair block; a second
+// kernel sums the partial rows in a fixed order per right-hand side.
+
+constexpr int TA_M = 128;    // l per chunk (rows of D)
+constexpr int TA_K = 128;    // ring pairs per CTA
+constexpr int TA_N = 64;     // 16 right-hand sides x (re, im) x parity
+constexpr int TA_A_BYTES = TA_M * TA_K * 2;   // 32 KB
+constexpr int TA_B_BYTES = TA_N * TA_K * 2;   // 16 KB
+
+struct TaArgs {
+  const float2* phase;   // [nrhs][nring][ldp]
+  int64_t ld_phase, ldp;
+  float2* partial;       // [nrhs][nblk][nlm]
+  int64_t nlm;
+  int nblk;
+  int L, Lc, nrhs;
+  const float *c, *c2, *s;
+  const float *z, *w;
+  int npolar;
+  const int* ls;
+  const float2* st;
+  int ld_seed, npairs, nring;
+  int* status;
+};
+
+// 8x8 transpose within each group of 8 lanes: on return lane 8 G + i holds,
+// in v[j], the value that lane 8 G + j held in v[i] (three butterfly stages
+// that exchange the off-diagonal blocks of halves, quarters and eighths)
+__device__ __forceinline__ void transpose8(float v[8], int lane) {
+#pragma unroll
+  for (int b = 4; b >= 1; b >>= 1) {
+    const bool hi = (lane & b) != 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j & b) continue;
+      const float send = hi ? v[j] : v[j | b];
+      const float recv = __shfl_xor_sync(0xffffffffu, send, b);
+      if (hi) v[j] = recv;
+      else v[j | b] = recv;
+    }
+  }
+}
+
+// after transpose8: lane 8 G + i holds row (row0 + i) for the 8 pairs
+// kbase + 8 G .. + 7; one 16-byte store of the K-major segment
+__device__ __forceinline__ void store_rows8(uint8_t* buf, const float v[8], int row0, int kbase, int lane, int K) {
+  *reinterpret_cast<uint4*>(buf + tc::kmajor_offset(row0 + (lane & 7), kbase + 8 * (lane >> 3), K)) =
+      make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+
+template <bool POLAR>
+__global__ void __launch_bounds__(TA_K) tc_adjoint_kernel(TaArgs a, int nbp, int yoff) {
+  extern __shared__ __align__(1024) uint8_t tasmem[];
+  uint8_t* A = tasmem;
+  uint8_t* B = tasmem + TA_A_BYTES;
+  __shared__ float sc[TA_M], sc2[TA_M];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_min;
+  const int m = blockIdx.y;
+  const int L = a.L;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int yb = (int)blockIdx.x + yoff;
+  const int base = POLAR ? yb * TA_K : a.npolar + (yb - nbp) * TA_K;
+  const int pend = POLAR ? a.npolar : a.npairs;
+  const int p = base + tid;
+  int ls = L + 1;
+  float P1 = 0.f, P2 = 0.f, zz = 0.f;
+  if (p < pend) {
+    const int64_t o = (int64_t)m * a.ld_seed + p;
+    zz = POLAR ? a.w[p] : a.z[p];
+    const int l = a.ls[o];
+    if (l <= L) {
+      const float2 s = a.st[o];
+      ls = l;
+      P1 = s.x;
+      P2 = s.y;
+    }
+  }
+  if (tid == 0) s_min = L + 1;
+  __syncthreads();
+  if (ls <= L) atomicMin(&s_min, ls);
+  __syncthreads();
+  const int cmin = s_min;
+  const int64_t offa = lm_off(L, m), offc = lm_off(a.Lc, m);
+  const int64_t rstride = (int64_t)a.nblk * a.nlm;
+  float2* part = a.partial + (int64_t)yb * a.nlm + offa;
+  const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~1) : L + 1;
+  // rows before the block's earliest start are zero
+  for (int r = 0; r < a.nrhs; ++r)
+    for (int l = m + tid; l < lbeg; l += TA_K) part[r * rstride + (l - m)] = make_float2(0.f, 0.f);
+  if (cmin > L) return;
+
+  // B operand: row 2 r / 2 r + 1 = Re / Im of the even combination of
+  // right-hand side r, rows 32 + 2 r / + 1 the odd one; K = this thread's pair
+  {
+    const bool live = p < pend && ls <= L;
+    const int rn = p, rs = a.nring - 1 - p;
+#pragma unroll 1
+    for (int q = 0; q < TS_RHS / 4; ++q) {
+      float ve[8], vo[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = 4 * q + i;
+        float2 gn = make_float2(0.f, 0.f), gs = make_float2(0.f, 0.f);
+        if (live && r < a.nrhs) {
+          gn = a.phase[r * a.ld_phase + (int64_t)rn * a.ldp + m];
+          if (rs != rn) gs = a.phase[r * a.ld_phase + (int64_t)rs * a.ldp + m];
+        }
+        ve[2 * i] = gn.x + gs.x;
+        ve[2 * i + 1] = gn.y + gs.y;
+        vo[2 * i] = gn.x - gs.x;
+        vo[2 * i + 1] = gn.y - gs.y;
+      }
+      transpose8(ve, lane);
+      transpose8(vo, lane);
+      store_rows8(B, ve, 8 * q, warp * 32, lane, TA_K);
+      store_rows8(B, vo, 32 + 8 * q, warp * 32, lane, TA_K);
+    }
+  }
+
+  if (warp == 0) tc::tmem_alloc(&taddr_s, TA_N);
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = taddr_s;
+  const uint32_t idesc = tc::idesc_bf16_f32(TA_M, TA_N);
+  const int nch = (L + 1 - lbeg + TA_M - 1) / TA_M;
+  bool ok = true;
+  for (int ch = 0; ch < nch && ok; ++ch) {
+    const int l0 = lbeg + ch * TA_M;
+    {
+      const int l = l0 + tid;
+      const bool in = l <= L;
+      sc[tid] = in ? a.c[offc + (l - m)] : 0.f;
+      if (POLAR) sc2[tid] = in ? a.c2[offc + (l - m)] : 0.f;
+    }
+    __syncthreads();
+    // A operand: row t = l - l0, K = this thread's pair; 8 l at a time,
+    // transposed so that each lane stores 8 pairs of one row
+    const bool full = (ls <= l0) && (l0 + TA_M - 1 <= L);
+#pragma unroll 1
+    for (int g = 0; g < TA_M / 8; ++g) {
+      float v[8];
+      if (full) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = tstep<POLAR>(sc[8 * g + j], POLAR ? sc2[8 * g + j] : 0.f, zz, P1, P2);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int l = l0 + 8 * g + j;
+          v[j] = 0.f;
+          if (l >= ls && l <= L) v[j] = tstep<POLAR>(sc[8 * g + j], POLAR ? sc2[8 * g + j] : 0.f, zz, P1, P2);
+        }
+      }
+      transpose8(v, lane);
+      store_rows8(A, v, 8 * g, warp * 32, lane, TA_K);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t aa = tc::smem_addr(A), bb = tc::smem_addr(B);
+      const uint32_t sbo = (TA_K / 8) * 128;
+#pragma unroll
+      for (int kk = 0; kk < TA_K / 16; ++kk)
+        tc::mma_bf16(taddr, tc::smem_desc(aa + kk * 256, 128, sbo), tc::smem_desc(bb + kk * 256, 128, sbo), idesc,
+                     kk > 0 ? 1u : 0u);
+      tc::mma_commit(&mbar);
+    }
+    ok = tc::mbar_wait(&mbar, ch & 1, TS_WAIT);
+    tc::fence_after_sync();
+    if (ok) {
+      float ve[32], vo[32];
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), ve);
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + 32, vo);
+      const int l = l0 + tid;
+      if (l <= L) {
+        const float sl = a.s[offc + (l - m)];
+        const bool odd = (tid & 1) != 0;  // l0 - m is even
+#pragma unroll
+        for (int r = 0; r < TS_RHS; ++r)
+          if (r < a.nrhs)
+            part[r * rstride + (l - m)] =
+                make_float2((odd ? vo[2 * r] : ve[2 * r]) * sl, (odd ? vo[2 * r + 1] : ve[2 * r + 1]) * sl);
+      }
+    } else if (tid == 0) {
+      atomicExch(a.status, 1);
+    }
+    // every thread's tensor-memory reads are done before the next MMA
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  if (warp == 0) tc::tmem_dealloc(taddr, TA_N);
+}
+
+// G of nrhs <= 16 right-hand sides (phase [nrhs][nring][L+1], complex64) ->
+// partial rows [nrhs][nblk][n_lm(L)] (s_lm applied); *nblk receives the
+// number of ring-pair blocks.  status: device int set to 1 if a completion
+// wait gave up.
+int tc_adjoint_blocks(int npolar, int npairs) {
+  return (npolar + TA_K - 1) / TA_K + (npairs - npolar + TA_K - 1) / TA_K;
+}
+
+int launch_tc_adjoint(const LegArgs<float>& la, const float2* phase, int nrhs, float2* partial, int* nblk,
+                      int* status, cudaStream_t st) {
+  const int nbp = (la.npolar + TA_K - 1) / TA_K;
+  const int nbe = (la.npairs - la.npolar + TA_K - 1) / TA_K;
+  *nblk = nbp + nbe;
+  if (la.L < 0 || nrhs <= 0) return CR_OK;
+  if (nrhs > TS_RHS) return fail(CR_EINVAL, "tensor-core adjoint: at most 16 right-hand sides per launch");
+  if (la.L + 1 > 65535) return fail(CR_EINVAL, "tensor-core adjoint: lmax too large for the grid");
+  TaArgs a;
+  a.phase = phase;
+  a.ldp = la.L + 1;
+  a.ld_phase = (int64_t)la.nring * a.ldp;
+  a.partial = partial;
+  a.nlm = n_lm(la.L);
+  a.nblk = nbp + nbe;
+  a.L = la.L;
+  a.Lc = la.Lc;
+  a.nrhs = nrhs;
+  a.c = la.c;
+  a.c2 = la.c2;
+  a.s = la.s;
+  a.z = la.z;
+  a.w = la.w;
+  a.npolar = la.npolar;
+  a.ls = la.ls;
+  a.st = la.st;
+  a.ld_seed = la.ld_seed;
+  a.npairs = la.npairs;
+  a.nring = la.nring;
+  a.status = status;
+  const size_t smem = (size_t)TA_A_BYTES + TA_B_BYTES;
+  CR_CUDA(cudaFuncSetAttribute(tc_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CR_CUDA(cudaFuncSetAttribute(tc_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (nbp) { tc_adjoint_kernel<true><<<dim3(nbp, la.L + 1), TA_K, smem, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { tc_adjoint_kernel<false><<<dim3(nbe, la.L + 1), TA_K, smem, st>>>(a, nbp, nbp); count_launch(); }
+  CR_CHECK_LAUNCH("tc_adjoint_kernel");
+  return CR_OK;
+}
+
 }  // namespace cr

@@ -323,7 +323,7 @@ static void plan_free(cr_plan* P) {
   }
   void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_c2_32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
                   P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial, P->d_pcinv, P->cgv[0], P->cgv[1],
-                  P->cgv[2], P->cgv[3], P->d_cgdot, P->tc_phase, P->d_tc_status};
+                  P->cgv[2], P->cgv[3], P->d_cgdot, P->tc_phase, P->d_tc_status, P->tc_partial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -643,43 +643,144 @@ static int check_ptr(const void* p, int dtype) {
   return CR_OK;
 }
 
-// batched synthesis with the Legendre contraction on the tensor cores (BF16
-// operands, FP32 accumulation; legendre_tc.cu), FP32 data, 16 right-hand
-// sides per Legendre launch, then the FP32 ring FFTs per right-hand side
-static int tc_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, int nrhs) {
-  const int64_t need = (int64_t)16 * g.nring * (L + 1) * (int64_t)sizeof(float2);
-  if (need > P->tc_phase_bytes) {
-    if (P->tc_phase) cudaFree(P->tc_phase);
-    P->tc_phase = nullptr;
-    CR_CUDA(cudaMalloc(&P->tc_phase, need));
-    P->tc_phase_bytes = need;
+// Batched transforms with the Legendre contractions on the tensor cores
+// (BF16 operands, FP32 accumulation; legendre_tc.cu) on FP32 data, 16
+// right-hand sides per Legendre launch; the ring FFTs run per right-hand side.
+static int grow(void** buf, int64_t* have, int64_t need) {
+  if (need <= *have) return CR_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  CR_CUDA(cudaMalloc(buf, need));
+  *have = need;
+  return CR_OK;
+}
+
+static int tc_begin(cr_plan* P, const Grid& g, int L, bool adjoint) {
+  int rc = grow(&P->tc_phase, &P->tc_phase_bytes, (int64_t)16 * g.nring * (L + 1) * (int64_t)sizeof(float2));
+  if (!rc && adjoint) {
+    const int64_t nblk = tc_adjoint_blocks(g.npolar32, g.npairs);
+    rc = grow(&P->tc_partial, &P->tc_partial_bytes, 16 * nblk * n_lm(L) * (int64_t)sizeof(float2));
   }
+  if (rc) return rc;
   if (!P->d_tc_status) CR_CUDA(cudaMalloc(&P->d_tc_status, sizeof(int)));
   CR_CUDA(cudaMemsetAsync(P->d_tc_status, 0, sizeof(int), P->stream));
+  return CR_OK;
+}
+
+static int tc_end(cr_plan* P, const char* what) {
+  int st = 0;
+  CR_CUDA(cudaMemcpyAsync(&st, P->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CR_CUDA(cudaStreamSynchronize(P->stream));
+  if (st) return fail(CR_ECUDA, what);
+  return CR_OK;
+}
+
+static float2* tc_slot(cr_plan* P, const Grid& g, int L, int r) {
+  return reinterpret_cast<float2*>(P->tc_phase) + (int64_t)r * g.nring * (L + 1);
+}
+
+// the adjoint Legendre stage of nr right-hand sides from the phase slots,
+// then out_r = dl_out sum_blk partial + dadd xadd_r per right-hand side
+static int tc_adjoint_tail(cr_plan* P, const Grid& g, int L, int nr, const float* dl_out, const float* dadd,
+                           const float2* xadd, float2* out) {
+  LegArgs<float> la = leg_args<float>(P, g, L);
+  const int64_t nlm = n_lm(L);
+  int nblk = 0, rc;
+  {
+    TimerScope ts(P->timing, P->stream, "legendre_adjoint_tc", leg_work(g, L) * nr);
+    rc = launch_tc_adjoint(la, tc_slot(P, g, L, 0), nr, reinterpret_cast<float2*>(P->tc_partial), &nblk,
+                           P->d_tc_status, P->stream);
+  }
+  if (rc) return rc;
+  for (int r = 0; r < nr; ++r) {
+    FinalizeArgs<float> f;
+    f.partial = reinterpret_cast<const float2*>(P->tc_partial) + (int64_t)r * nblk * nlm;
+    f.nblk = nblk;
+    f.L = L;
+    f.dl_out = dl_out;
+    f.dadd = dadd;
+    f.xadd = xadd ? xadd + r * nlm : nullptr;
+    f.out = out + r * nlm;
+    TimerScope ts(P->timing, P->stream, "legendre_finalize_tc", (double)(nblk + 1) * nlm * sizeof(float2));
+    if ((rc = launch_leg_finalize<float>(f, P->stream))) return rc;
+  }
+  return CR_OK;
+}
+
+static int tc_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, int nrhs) {
+  int rc = tc_begin(P, g, L, false);
+  if (rc) return rc;
   LegArgs<float> la = leg_args<float>(P, g, L);
   const int64_t nlm = n_lm(L);
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int nr = std::min(16, nrhs - r0);
     const float2* a = reinterpret_cast<const float2*>(alm) + (int64_t)r0 * nlm;
-    int rc;
     {
-      TimerScope ts(P->timing, P->stream, "legendre_synth_tc", 8.0 * g.npairs * (double)nlm * nr);
-      rc = launch_tc_synth(la, a, nlm, nr, reinterpret_cast<float2*>(P->tc_phase), P->d_tc_status, P->stream);
+      TimerScope ts(P->timing, P->stream, "legendre_synth_tc", leg_work(g, L) * nr);
+      rc = launch_tc_synth(la, a, nlm, nr, tc_slot(P, g, L, 0), P->d_tc_status, P->stream);
     }
     if (rc) return rc;
     for (int r = 0; r < nr; ++r) {
       RingArgs<float> ra = ring_args<float>(P, g, L);
-      ra.phase = reinterpret_cast<float2*>(P->tc_phase) + (int64_t)r * g.nring * (L + 1);
+      ra.phase = tc_slot(P, g, L, r);
       ra.map_out = reinterpret_cast<float*>(map) + (int64_t)(r0 + r) * g.npix;
       TimerScope ts(P->timing, P->stream, "ring_fft_synth_f32", fft_bytes<float>(g, L, 1));
       if ((rc = launch_ring_fft<float>(ra, 0, P->stream))) return rc;
     }
   }
-  int st = 0;
-  CR_CUDA(cudaMemcpyAsync(&st, P->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-  CR_CUDA(cudaStreamSynchronize(P->stream));
-  if (st) return fail(CR_ECUDA, "tensor-core synthesis: a completion wait gave up");
-  return CR_OK;
+  return tc_end(P, "tensor-core synthesis: a completion wait gave up");
+}
+
+static int tc_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, int nrhs) {
+  int rc = tc_begin(P, g, L, true);
+  if (rc) return rc;
+  const int64_t nlm = n_lm(L);
+  for (int r0 = 0; r0 < nrhs; r0 += 16) {
+    const int nr = std::min(16, nrhs - r0);
+    for (int r = 0; r < nr; ++r) {
+      RingArgs<float> ra = ring_args<float>(P, g, L);
+      ra.phase = tc_slot(P, g, L, r);
+      ra.map_in = reinterpret_cast<const float*>(map) + (int64_t)(r0 + r) * g.npix;
+      TimerScope ts(P->timing, P->stream, "ring_fft_adjoint_f32", fft_bytes<float>(g, L, 1));
+      if ((rc = launch_ring_fft<float>(ra, 1, P->stream))) return rc;
+    }
+    rc = tc_adjoint_tail(P, g, L, nr, nullptr, nullptr, nullptr, reinterpret_cast<float2*>(alm) + r0 * nlm);
+    if (rc) return rc;
+  }
+  return tc_end(P, "tensor-core adjoint: a completion wait gave up");
+}
+
+// y = (S^-1 + B Y^T N^-1 Y B) x for nrhs right-hand sides on the observation
+// grid (Eq. 3 system matrix), both Legendre stages on the tensor cores
+static int tc_apply(cr_plan* P, const void* x, void* y, int nrhs) {
+  const Grid& g = P->obs;
+  const int L = P->lmax;
+  int rc = tc_begin(P, g, L, true);
+  if (rc) return rc;
+  LegArgs<float> la = leg_args<float>(P, g, L);
+  la.dl = P->d_bl32;
+  const int64_t nlm = n_lm(L);
+  for (int r0 = 0; r0 < nrhs; r0 += 16) {
+    const int nr = std::min(16, nrhs - r0);
+    const float2* xr = reinterpret_cast<const float2*>(x) + (int64_t)r0 * nlm;
+    {
+      TimerScope ts(P->timing, P->stream, "legendre_synth_tc", leg_work(g, L) * nr);
+      rc = launch_tc_synth(la, xr, nlm, nr, tc_slot(P, g, L, 0), P->d_tc_status, P->stream);
+    }
+    if (rc) return rc;
+    for (int r = 0; r < nr; ++r) {
+      RingArgs<float> ra = ring_args<float>(P, g, L);
+      ra.phase = tc_slot(P, g, L, r);
+      ra.pixdiag = P->d_ninv32;
+      TimerScope ts(P->timing, P->stream, "ring_fft_apply_f32",
+                    fft_bytes<float>(g, L, 1) + (double)g.nring * (L + 1) * sizeof(float2));
+      if ((rc = launch_ring_fft<float>(ra, 2, P->stream))) return rc;
+    }
+    rc = tc_adjoint_tail(P, g, L, nr, P->d_bl32, P->d_sinv32, xr, reinterpret_cast<float2*>(y) + r0 * nlm);
+    if (rc) return rc;
+  }
+  return tc_end(P, "tensor-core apply: a completion wait gave up");
 }
 
 int cr_sht_synth(cr_plan* plan, int grid, const void* alm, void* map, int nrhs, int dtype) {
@@ -710,6 +811,11 @@ int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs
   int L = 0;
   const Grid* g = grid_of(plan, grid, &L);
   if (!g) return fail(CR_EINVAL, "cr_sht_adjoint: unknown grid");
+  if (nrhs >= 0 && dtype == CR_TC) {
+    if (nrhs == 0) return CR_OK;
+    if (check_ptr(alm, CR_F32) || check_ptr(map, CR_F32)) return CR_EINVAL;
+    return tc_adjoint(plan, *g, L, map, alm, nrhs);
+  }
   if (nrhs < 0 || (dtype != CR_F64 && dtype != CR_F32)) return fail(CR_EINVAL, "cr_sht_adjoint: nrhs/dtype");
   if (nrhs == 0) return CR_OK;
   if (check_ptr(alm, dtype) || check_ptr(map, dtype)) return CR_EINVAL;
@@ -728,6 +834,12 @@ int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int d
   if (!plan) return fail(CR_EINVAL, "cr_apply_A: null plan");
   if (!plan->has_op) return fail(CR_ESTATE, "cr_apply_A: plan was created without C_l");
   if (level != 0) return cr_level_apply(plan, level, x, y, dtype);
+  if (nrhs >= 0 && dtype == CR_TC) {
+    if (nrhs == 0) return CR_OK;
+    if (check_ptr(x, CR_F32) || check_ptr(y, CR_F32)) return CR_EINVAL;
+    if (x == y) return fail(CR_EINVAL, "cr_apply_A: x and y must not overlap");
+    return tc_apply(plan, x, y, nrhs);
+  }
   if (nrhs < 0 || (dtype != CR_F64 && dtype != CR_F32)) return fail(CR_EINVAL, "cr_apply_A: nrhs/dtype");
   if (nrhs == 0) return CR_OK;
   if (check_ptr(x, dtype) || check_ptr(y, dtype)) return CR_EINVAL;

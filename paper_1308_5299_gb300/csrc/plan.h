@@ -147,6 +147,8 @@ struct cr_plan {
   void* tc_phase = nullptr;  // batched tensor-core synthesis: [16][nring][L+1] complex64
   int64_t tc_phase_bytes = 0;
   int* d_tc_status = nullptr;
+  void* tc_partial = nullptr;  // batched tensor-core adjoint: [16][nblk][n_lm] complex64
+  int64_t tc_partial_bytes = 0;
   cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)
   void* hier_tile_work = nullptr;     // FP32 tile-ordered smoother work vector
   // diagonal-preconditioned CG (created on first use)
