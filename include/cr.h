@@ -166,6 +166,13 @@ typedef struct cr_params {
    * 2^-44 relative per operation -- which GB300 runs several times faster
    * than native FP64; 0 = native FP64. */
   int fp64_df;
+  /* defer_precompute: 1 = build the level structure (grids, tile patterns,
+   * the observation-dependent inverse-noise terms) but not the
+   * C_l-dependent numerical precompute (smoother factorisations with the
+   * ridge search, top-level diagonal smoother, bottom dense inverse); fill
+   * it in later with cr_load or cr_plan_update_cl.  Until then the solver
+   * entry points return CR_ESTATE.  0 = run everything at creation. */
+  int defer_precompute;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */
@@ -178,6 +185,40 @@ const char* cr_last_error(void);
  * only on success.  Errors: CR_EINVAL, CR_ENOMEM, CR_ECUDA.
  */
 int cr_plan_create(cr_plan** out, const cr_params* p);
+
+/*
+ * Replace the prior C_l of a plan (HOST [lmax + 1], finite, >= 0) and redo
+ * only the precompute that depends on it (Section 5): the diagonals S^-1 and
+ * B, the level operators' D_h, each pixel level's prior term of the
+ * assembled block matrix (its inverse-noise term is kept unless the set of
+ * l with C_l > 0 changes), the ridge search and incomplete-Cholesky
+ * factorisation, the top-level diagonal smoother and the bottom dense
+ * inverse.  Device arrays are rewritten in place, so CUDA graphs of
+ * cr_batch_create stay valid unless the set of l with C_l > 0 changes.
+ * Synchronous.  Errors: CR_EINVAL (null, bad C_l; the plan is unchanged),
+ * CR_ESTATE (plan created without C_l), CR_EICC, CR_ECUDA (after which the
+ * solver entry points return CR_ESTATE until a successful update or load).
+ */
+int cr_plan_update_cl(cr_plan* plan, const double* cl);
+
+/*
+ * Checkpoint of the C_l-dependent numerical precompute (Section 5: the
+ * precomputed smoothers are normally read from disk).  cr_save writes, to
+ * the file `path`, each pixel level's ridge and block incomplete-Cholesky
+ * factor, the top-level diagonal smoother, and the bottom dense matrix and
+ * its inverse, after a header identifying the plan (grid, band limits,
+ * level table, tile-pattern sizes) and 64-bit FNV-1a hashes of C_l, b_l and
+ * the N^-1 map, and followed by a hash of the whole file.  cr_load reads
+ * such a file into a plan built from the same inputs, normally created with
+ * defer_precompute = 1, and makes it ready to solve; solutions then equal
+ * those of the plan that was saved.  Both synchronous.  Errors: CR_EINVAL
+ * (null argument, plan without levels, a checkpoint made for other inputs),
+ * CR_ESTATE (cr_save before the precompute), CR_EIO (cannot open, read or
+ * write; not a checkpoint; truncated; checksum mismatch -- the plan is then
+ * unchanged), CR_ECUDA.
+ */
+int cr_save(cr_plan* plan, const char* path);
+int cr_load(cr_plan* plan, const char* path);
 
 /* Grid on which pixel level h (1..nlevels) applies its inverse-noise term:
  * *kind = CR_GRID_HEALPIX (the observation grid) or CR_GRID_GL (the

@@ -28,6 +28,8 @@ CR_OBS = 0
 
 ERRORS = {-1: "CR_EINVAL", -2: "CR_ENOMEM", -3: "CR_ECUDA", -4: "CR_EICC", -5: "CR_EDIVERGED",
           -6: "CR_EMAXITER", -7: "CR_ENONFINITE", -8: "CR_ESTATE", -9: "CR_EIO"}
+(CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_EICC, CR_EDIVERGED, CR_EMAXITER, CR_ENONFINITE, CR_ESTATE,
+ CR_EIO) = range(-1, -10, -1)
 
 
 class CRError(RuntimeError):
@@ -62,6 +64,7 @@ class cr_params(ctypes.Structure):
         ("ridge_lambda_target", ctypes.c_double),
         ("gl_downgrade", ctypes.c_int),
         ("fp64_df", ctypes.c_int),
+        ("defer_precompute", ctypes.c_int),
     ]
 
 
@@ -72,6 +75,9 @@ _SIGS = {
     "cr_last_error": ([], ctypes.c_char_p),
     "cr_plan_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(cr_params)], ctypes.c_int),
     "cr_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "cr_plan_update_cl": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cr_save": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
+    "cr_load": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
     "cr_plan_sizes": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cr_sht_synth": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
@@ -203,12 +209,13 @@ class Plan:
 
     def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
                  lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0,
-                 gl_downgrade=0, fp64_df=False):
+                 gl_downgrade=0, fp64_df=False, defer_precompute=False):
         """levels: None (transforms and A only), "default" (the library's level
         table), or a list of dicts with nside_h, lmax_h, n_rec and fl
         (cumulative filter, length lmax+1).  gl_downgrade: 0 auto, 1 every
         pixel level, -1 off (Gauss-Legendre grids for the levels'
-        inverse-noise term)."""
+        inverse-noise term).  defer_precompute: skip the C_l-dependent
+        precompute (then ``load`` a checkpoint or ``update_cl``)."""
         p = cr_params()
         p.struct_size = ctypes.sizeof(cr_params)
         if gl is not None:
@@ -257,6 +264,7 @@ class Plan:
         p.ridge_lambda_target = float(ridge_lambda_target)
         p.gl_downgrade = int(gl_downgrade)
         p.fp64_df = int(bool(fp64_df))
+        p.defer_precompute = int(bool(defer_precompute))
         if ridge_alpha is not None:
             ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
             self._keep.append(ra)
@@ -267,6 +275,22 @@ class Plan:
         self.lmax = int(lmax)
         self._keep = []
         self.npix = self.sizes()["npix"]
+
+    def update_cl(self, cl):
+        """Replace the prior C_l and redo the C_l-dependent precompute
+        (``cr_plan_update_cl``)."""
+        cl = np.ascontiguousarray(cl, dtype=np.float64)
+        if cl.shape != (self.lmax + 1,):
+            raise ValueError("update_cl: C_l must have lmax + 1 entries")
+        _check(lib().cr_plan_update_cl(self._h, cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def save(self, path):
+        """Write the precompute checkpoint (``cr_save``)."""
+        _check(lib().cr_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Read a precompute checkpoint made for the same inputs (``cr_load``)."""
+        _check(lib().cr_load(self._h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -488,6 +512,22 @@ class Batch:
         k = ctypes.c_int64()
         _check(lib().cr_batch_nodes(self._h, None, ctypes.byref(k)))
         return k.value
+
+    def update_cl(self, cl):
+        """Replace the prior C_l and redo the C_l-dependent precompute
+        (``cr_plan_update_cl``)."""
+        cl = np.ascontiguousarray(cl, dtype=np.float64)
+        if cl.shape != (self.lmax + 1,):
+            raise ValueError("update_cl: C_l must have lmax + 1 entries")
+        _check(lib().cr_plan_update_cl(self._h, cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def save(self, path):
+        """Write the precompute checkpoint (``cr_save``)."""
+        _check(lib().cr_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Read a precompute checkpoint made for the same inputs (``cr_load``)."""
+        _check(lib().cr_load(self._h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "_h", None):

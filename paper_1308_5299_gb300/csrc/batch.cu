@@ -39,6 +39,8 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
   if (!st) return fail(CR_EINVAL, "cr_batch_create: graph capture needs a created stream, not the default stream");
   for (int i = 0; i < nplans; ++i) {
     if (!plans[i] || !plans[i]->hier) return fail(CR_EINVAL, "cr_batch_create: every plan needs levels");
+    if (!plans[i]->hier->numeric_ready)
+      return fail(CR_ESTATE, "cr_batch_create: a plan's C_l-dependent precompute was deferred");
     if (plans[i]->stream != st) return fail(CR_EINVAL, "cr_batch_create: plans must share one stream");
     if (nrhs[i] < 0) return fail(CR_EINVAL, "cr_batch_create: nrhs < 0");
   }

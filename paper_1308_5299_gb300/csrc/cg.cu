@@ -42,7 +42,7 @@ static int precond(cr_plan* P, const void* r, void* z) {
 static int dots(cr_plan* P, int n, const void* const* a, const void* const* b, const double* const* w,
                 double* out) {
   for (int i = 0; i < n; ++i) {
-    int rc = launch_dot<double>(a[i], b[i], w[i], P->lmax, P->d_cgdot + i, P->stream);
+    int rc = launch_dot<double>(a[i], b[i], w[i], P->lmax, P->d_cgdot + i, P->d_dotpart, P->stream);
     if (rc) return rc;
   }
   CR_CUDA(cudaMemcpyAsync(out, P->d_cgdot, n * sizeof(double), cudaMemcpyDeviceToHost, P->stream));

@@ -301,7 +301,7 @@ int build_top_diag(cr_plan* P, Hierarchy& Hh, const std::vector<double>& f1) {
     std::vector<double> hv(nlm);
     cudaError_t e = cudaMemcpy(hv.data(), out, nlm * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = cuda_fail(e, "top diag copy");
-    else rc = Hh.inv_diag_hp.upload(hv);
+    else rc = Hh.inv_diag_hp.assign(hv);
   }
   cudaFree(out);
   return rc;
@@ -351,7 +351,18 @@ int build_bottom(cr_plan* P, Hierarchy& Hh) {
     assemble_dense_kernel<<<(int)((ne + 127) / 128), 128, 0, P->stream>>>(pt, X, 2 * Ld, P->obs.npairs,
                                                                           P->obs.nring, Ld, d_dofs, nd, dbl, ddl, A);
     CR_CHECK_LAUNCH("assemble_dense_kernel");
-    CR_CUDA(cudaMalloc(&Hh.d_Abottom, (size_t)nd * nd * sizeof(double)));
+    if (Hh.nd_alloc != nd) {
+      // a changed set of active l: new bottom arrays
+      void* old[] = {Hh.d_Abottom, Hh.d_Ainv, Hh.d_dof_lm};
+      for (void* q : old)
+        if (q) cudaFree(q);
+      Hh.d_Abottom = Hh.d_Ainv = nullptr;
+      Hh.d_dof_lm = nullptr;
+      CR_CUDA(cudaMalloc(&Hh.d_Abottom, (size_t)nd * nd * sizeof(double)));
+      CR_CUDA(cudaMalloc(&Hh.d_Ainv, (size_t)nd * nd * sizeof(double)));
+      CR_CUDA(cudaMalloc(&Hh.d_dof_lm, nd * sizeof(DofMap)));
+      Hh.nd_alloc = nd;
+    }
     CR_CUDA(cudaMemcpyAsync(Hh.d_Abottom, A, (size_t)nd * nd * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
     for (int j = 0; j < nd; ++j) {
       chol_col_kernel<<<1, 256, 0, P->stream>>>(A, nd, j, d_fail, d_fail_val);
@@ -363,7 +374,6 @@ int build_bottom(cr_plan* P, Hierarchy& Hh) {
     CR_CHECK_LAUNCH("chol kernels");
     tri_inv_kernel<<<(nd + 63) / 64, 64, 0, P->stream>>>(A, nd, Li);
     CR_CHECK_LAUNCH("tri_inv_kernel");
-    CR_CUDA(cudaMalloc(&Hh.d_Ainv, (size_t)nd * nd * sizeof(double)));
     dim3 gg((nd + 15) / 16, (nd + 15) / 16), bb(16, 16);
     gram_kernel<<<gg, bb, 0, P->stream>>>(Li, nd, Hh.d_Ainv);
     CR_CHECK_LAUNCH("gram_kernel");
@@ -378,13 +388,33 @@ int build_bottom(cr_plan* P, Hierarchy& Hh) {
                              std::to_string(nd) + " (l=" + std::to_string(dm.l) + " m=" + std::to_string(dm.m) +
                              ") is " + std::to_string(fval));
     }
-    CR_CUDA(cudaMalloc(&Hh.d_dof_lm, nd * sizeof(DofMap)));
     CR_CUDA(cudaMemcpy(Hh.d_dof_lm, dofs.data(), nd * sizeof(DofMap), cudaMemcpyHostToDevice));
   }
   void* ptrs[] = {X, pt, A, Li, dbl, ddl, d_dofs, d_fail, d_fail_val};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   return rc;
+}
+
+// bottom-level arrays from host copies (checkpoint load)
+int bottom_upload(cr_plan* P, Hierarchy& Hh, int nd, const double* a, const double* ainv, const int32_t* dofs) {
+  static_assert(sizeof(DofMap) == 3 * sizeof(int32_t), "dof map layout");
+  CR_CUDA(cudaStreamSynchronize(P->stream));
+  if (Hh.nd_alloc != nd) {
+    void* old[] = {Hh.d_Abottom, Hh.d_Ainv, Hh.d_dof_lm};
+    for (void* q : old)
+      if (q) cudaFree(q);
+    Hh.d_Abottom = Hh.d_Ainv = nullptr;
+    Hh.d_dof_lm = nullptr;
+    CR_CUDA(cudaMalloc(&Hh.d_Abottom, (size_t)nd * nd * sizeof(double)));
+    CR_CUDA(cudaMalloc(&Hh.d_Ainv, (size_t)nd * nd * sizeof(double)));
+    CR_CUDA(cudaMalloc(&Hh.d_dof_lm, nd * sizeof(DofMap)));
+    Hh.nd_alloc = nd;
+  }
+  CR_CUDA(cudaMemcpy(Hh.d_Abottom, a, (size_t)nd * nd * sizeof(double), cudaMemcpyHostToDevice));
+  CR_CUDA(cudaMemcpy(Hh.d_Ainv, ainv, (size_t)nd * nd * sizeof(double), cudaMemcpyHostToDevice));
+  CR_CUDA(cudaMemcpy(Hh.d_dof_lm, dofs, nd * sizeof(DofMap), cudaMemcpyHostToDevice));
+  return CR_OK;
 }
 
 int bottom_matrix(cr_plan* P, double* host, int* nd) {

@@ -208,7 +208,7 @@ extern "C" int cr_alm_dot(cr_plan* plan, const void* u, const void* v, int weigh
   if (weighted && !plan->has_op) return fail(CR_EINVAL, "cr_alm_dot: S^-1 weighting needs C_l");
   double* d = nullptr;
   CR_CUDA(cudaMalloc(&d, sizeof(double)));
-  int rc = launch_dot<double>(u, v, weighted ? plan->d_sinv : nullptr, plan->lmax, d, plan->stream);
+  int rc = launch_dot<double>(u, v, weighted ? plan->d_sinv : nullptr, plan->lmax, d, plan->d_dotpart, plan->stream);
   cudaError_t e = cudaSuccess;
   if (!rc) e = cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
   if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);

@@ -17,6 +17,9 @@ struct LArr {
   float* f = nullptr;
   int n = 0;
   int upload(const std::vector<double>& h);
+  // copy into the existing arrays when the size is unchanged (device
+  // pointers stay valid, e.g. inside captured CUDA graphs), else upload
+  int assign(const std::vector<double>& h);
   void release();
   template <typename T> const T* get() const;
 };
@@ -38,6 +41,8 @@ struct BlockPattern {
   int64_t nblocks = 0;
   int64_t block_of(int p, int q) const;  // -1 if (p, q) is not stored
 };
+
+struct SmootherBuild;
 
 struct PixLevel {
   int nside_h = 0, lmax_h = 0, n_rec = 1, k = 8, nside_t = 0;
@@ -75,6 +80,7 @@ struct PixLevel {
   int64_t* d_pair_a = nullptr;      // block (u, k)
   int64_t* d_pair_b = nullptr;      // block (p, k)
   int* d_fail = nullptr;            // factorisation failure flag
+  SmootherBuild* sb = nullptr;      // assembly inputs (smoother.cu)
 };
 
 struct Hierarchy {
@@ -90,6 +96,7 @@ struct Hierarchy {
   int ld = 0;
   std::vector<double> fb;     // bottom filter [lmax + 1]
   int nd = 0;                 // active real dofs of the bottom block
+  int nd_alloc = 0;           // dofs the bottom arrays are allocated for
   double* d_Ainv = nullptr;   // [nd][nd] inverse of the bottom A (FP64)
   double* d_Abottom = nullptr; // [nd][nd] the assembled bottom A (FP64)
   int* d_dof_lm = nullptr;    // real dof -> (lm index * 2 + part)
@@ -105,6 +112,12 @@ struct Hierarchy {
   double* d_dot_host = nullptr;
   void* ops_store = nullptr;  // per-level operator arrays (solver.cu)
   void* krylov[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // PCG vectors (FP64, top level)
+  // settings of the C_l-dependent precompute, kept for cr_plan_update_cl
+  double ridge_factor = 1.5;
+  int bisections = 30;
+  double lam_target = 1.5;
+  std::vector<double> ridge_fixed;  // given ridges per pixel level, or empty
+  bool numeric_ready = false;       // smoothers, top diagonal and bottom built
 };
 
 }  // namespace cr

@@ -27,6 +27,14 @@ int LArr::upload(const std::vector<double>& h) {
   return CR_OK;
 }
 
+int LArr::assign(const std::vector<double>& h) {
+  if (!d || n != (int)h.size() || h.empty()) return upload(h);
+  std::vector<float> hf(h.begin(), h.end());
+  CR_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CR_CUDA(cudaMemcpy(f, hf.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return CR_OK;
+}
+
 void LArr::release() {
   if (d) cudaFree(d);
   if (f) cudaFree(f);
@@ -243,9 +251,12 @@ __global__ void diag_axpy_kernel(typename Tr<T>::C* x, const typename Tr<T>::C* 
   }
 }
 
-// sum over (l, m) of w_m wl[l] Re(a conj b), w_0 = 1, w_m = 2, accumulated in FP64
+// sum over (l, m) of w_m wl[l] Re(a conj b), w_0 = 1, w_m = 2, accumulated in
+// FP64: one partial sum per m, then a fixed-order sum of the partials, so the
+// result is bitwise reproducible
 template <typename T>
-__global__ void dot_kernel(const typename Tr<T>::C* a, const typename Tr<T>::C* b, const double* wl, int L, double* out) {
+__global__ void dot_kernel(const typename Tr<T>::C* a, const typename Tr<T>::C* b, const double* wl, int L,
+                           double* part) {
   const int m = blockIdx.x;
   const int64_t o = lm_off(L, m);
   double s = 0.0;
@@ -261,7 +272,21 @@ __global__ void dot_kernel(const typename Tr<T>::C* a, const typename Tr<T>::C* 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    atomicAdd(out, (m == 0 ? 1.0 : 2.0) * t);
+    part[m] = (m == 0 ? 1.0 : 2.0) * t;
+  }
+}
+
+__global__ void dot_sum_kernel(const double* part, int n, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    *out = t;
   }
 }
 
@@ -316,9 +341,9 @@ int launch_diag_axpy(void* x, const void* r, const T* d, int64_t n, cudaStream_t
   return CR_OK;
 }
 template <typename T>
-int launch_dot(const void* a, const void* b, const double* wl, int L, double* out, cudaStream_t st) {
-  CR_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
-  { dot_kernel<T><<<L + 1, 256, 0, st>>>((const typename Tr<T>::C*)a, (const typename Tr<T>::C*)b, wl, L, out); count_launch(); }
+int launch_dot(const void* a, const void* b, const double* wl, int L, double* out, double* part, cudaStream_t st) {
+  { dot_kernel<T><<<L + 1, 256, 0, st>>>((const typename Tr<T>::C*)a, (const typename Tr<T>::C*)b, wl, L, part); count_launch(); }
+  { dot_sum_kernel<<<1, 1024, 0, st>>>(part, L + 1, out); count_launch(); }
   CR_CHECK_LAUNCH("dot_kernel");
   return CR_OK;
 }
@@ -371,7 +396,7 @@ template int launch_prolong_add<double>(void*, int, const void*, int, const doub
 template int launch_prolong_add<float>(void*, int, const void*, int, const float*, cudaStream_t);
 template int launch_diag_axpy<double>(void*, const void*, const double*, int64_t, cudaStream_t);
 template int launch_diag_axpy<float>(void*, const void*, const float*, int64_t, cudaStream_t);
-template int launch_dot<double>(const void*, const void*, const double*, int, double*, cudaStream_t);
-template int launch_dot<float>(const void*, const void*, const double*, int, double*, cudaStream_t);
+template int launch_dot<double>(const void*, const void*, const double*, int, double*, double*, cudaStream_t);
+template int launch_dot<float>(const void*, const void*, const double*, int, double*, double*, cudaStream_t);
 
 }  // namespace cr

@@ -26,12 +26,15 @@ template <typename T> int launch_diag_axpy(void* x, const void* r, const T* d, i
 int launch_fill_random(void* v, int L, uint32_t seed, cudaStream_t st);
 int launch_axpby(void* y, double a, const void* x, double b, int64_t n, cudaStream_t st);
 int launch_scale_copy(const void* in, void* out, float s, int64_t n, cudaStream_t st);
-template <typename T> int launch_dot(const void* a, const void* b, const double* wl, int L, double* out, cudaStream_t st);
+// out = weighted real inner product (FP64); part: scratch of >= L + 1 doubles
+template <typename T>
+int launch_dot(const void* a, const void* b, const double* wl, int L, double* out, double* part, cudaStream_t st);
 int launch_convert_d2f(const double* in, float* out, int64_t n, cudaStream_t st);
 int launch_add_f2d(double* x, const float* y, int64_t n, cudaStream_t st);
 
 // smoother.cu
-int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisections, double fixed_alpha);
+int smoother_structure(cr_plan* P, PixLevel& lev);
+int smoother_numeric(cr_plan* P, PixLevel& lev, double ridge_factor, int bisections, double fixed_alpha);
 int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok);
 template <typename T> int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out);
 void free_smoother(PixLevel& lev);
@@ -40,6 +43,7 @@ void free_smoother(PixLevel& lev);
 int build_bottom(cr_plan* P, Hierarchy& Hh);
 template <typename T> int bottom_solve(cr_plan* P, Hierarchy& Hh, const void* b, void* x);
 int bottom_matrix(cr_plan* P, double* host, int* nd);
+int bottom_upload(cr_plan* P, Hierarchy& Hh, int nd, const double* a, const double* ainv, const int32_t* dofs);
 int build_top_diag(cr_plan* P, Hierarchy& Hh, const std::vector<double>& f1);
 int inv_diag_A(cr_plan* P, const std::vector<double>& hpl, double* out);
 int cg_solve(cr_plan* P, void* x, const void* b, double eps, int maxit, int* it_out, double* relres_out,
@@ -47,6 +51,7 @@ int cg_solve(cr_plan* P, void* x, const void* b, double eps, int maxit, int* it_
 
 // solver.cu
 int build_hierarchy(cr_plan* P, const cr_params* p);
+int build_numeric(cr_plan* P);
 void free_hierarchy(cr_plan* P);
 
 }  // namespace cr

@@ -323,7 +323,7 @@ static void plan_free(cr_plan* P) {
   }
   void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_c2_32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
                   P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial, P->d_pcinv, P->cgv[0], P->cgv[1],
-                  P->cgv[2], P->cgv[3], P->d_cgdot, P->tc_phase, P->d_tc_status, P->tc_partial};
+                  P->cgv[2], P->cgv[3], P->d_cgdot, P->tc_phase, P->d_tc_status, P->tc_partial, P->d_dotpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -513,6 +513,32 @@ extern "C" {
 
 const char* cr_last_error(void) { return g_last_error.c_str(); }
 
+// Prior-dependent operator diagonals from h_cl and h_bl: B (b_l p_l, 0
+// where C_l = 0) and S^-1 (1 / C_l, 0 where C_l = 0) in FP64 and FP32,
+// copied into the existing device arrays when the plan already has them.
+static int upload_prior(cr_plan* P) {
+  const int L = P->lmax;
+  std::vector<double> bl(L + 1), sinv(L + 1);
+  for (int l = 0; l <= L; ++l) {
+    if (!(P->h_cl[l] >= 0.0) || !std::isfinite(P->h_cl[l])) return fail(CR_EINVAL, "C_l must be finite and >= 0");
+    const bool act = P->h_cl[l] > 0.0;
+    bl[l] = act ? P->h_bl[l] : 0.0;
+    sinv[l] = act ? 1.0 / P->h_cl[l] : 0.0;
+  }
+  std::vector<float> bl32(bl.begin(), bl.end()), sinv32(sinv.begin(), sinv.end());
+  auto up = [&](auto** d, const auto& h) -> int {
+    const size_t bytes = h.size() * sizeof(h[0]);
+    if (!*d) CR_CUDA(cudaMalloc(d, bytes));
+    CR_CUDA(cudaMemcpy(*d, h.data(), bytes, cudaMemcpyHostToDevice));
+    return CR_OK;
+  };
+  int rc = up(&P->d_bl, bl);
+  if (!rc) rc = up(&P->d_sinv, sinv);
+  if (!rc) rc = up(&P->d_bl32, bl32);
+  if (!rc) rc = up(&P->d_sinv32, sinv32);
+  return rc;
+}
+
 int cr_plan_create(cr_plan** out, const cr_params* p) {
   if (!out || !p) return fail(CR_EINVAL, "cr_plan_create: null argument");
   if (p->struct_size != (int)sizeof(cr_params)) return fail(CR_EINVAL, "cr_plan_create: struct_size mismatch");
@@ -550,37 +576,17 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   if (!rc) rc = build_coef(P, P->lmax);
   if (!rc) rc = build_start_tables(P, P->obs);
   if (!rc) rc = ensure_workspace(P, P->obs, P->lmax);
+  if (!rc) {
+    cudaError_t e = cudaMalloc(&P->d_dotpart, (P->lmax + 1) * sizeof(double));
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(dot partials)");
+  }
   if (!rc && p->cl) {
     const int L = P->lmax;
     P->h_cl.assign(p->cl, p->cl + L + 1);
     P->h_bl.assign(L + 1, 1.0);
     if (p->bl) P->h_bl.assign(p->bl, p->bl + L + 1);
-    std::vector<double> bl(L + 1), sinv(L + 1);
-    for (int l = 0; l <= L; ++l) {
-      if (!(P->h_cl[l] >= 0.0) || !std::isfinite(P->h_cl[l])) {
-        rc = fail(CR_EINVAL, "cr_plan_create: C_l must be finite and >= 0");
-        break;
-      }
-      const bool act = P->h_cl[l] > 0.0;
-      bl[l] = act ? P->h_bl[l] : 0.0;
-      sinv[l] = act ? 1.0 / P->h_cl[l] : 0.0;
-    }
+    rc = upload_prior(P);
     if (!rc) {
-      std::vector<float> bl32(bl.begin(), bl.end()), sinv32(sinv.begin(), sinv.end());
-      auto up = [&](double** d, const std::vector<double>& h) -> int {
-        CR_CUDA(cudaMalloc(d, h.size() * sizeof(double)));
-        CR_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
-        return CR_OK;
-      };
-      auto up32 = [&](float** d, const std::vector<float>& h) -> int {
-        CR_CUDA(cudaMalloc(d, h.size() * sizeof(float)));
-        CR_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
-        return CR_OK;
-      };
-      rc = up(&P->d_bl, bl);
-      if (!rc) rc = up(&P->d_sinv, sinv);
-      if (!rc) rc = up32(&P->d_bl32, bl32);
-      if (!rc) rc = up32(&P->d_sinv32, sinv32);
       const int64_t npix = P->obs.npix;
       if (!rc) {
         cudaError_t e = cudaMalloc(&P->d_ninv, npix * sizeof(double));
@@ -614,6 +620,28 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   }
   *out = P;
   return CR_OK;
+}
+
+int cr_plan_update_cl(cr_plan* plan, const double* cl) {
+  if (!plan || !cl) return fail(CR_EINVAL, "cr_plan_update_cl: null argument");
+  if (!plan->has_op) return fail(CR_ESTATE, "cr_plan_update_cl: plan was created without C_l");
+  const int L = plan->lmax;
+  for (int l = 0; l <= L; ++l)
+    if (!(cl[l] >= 0.0) || !std::isfinite(cl[l])) return fail(CR_EINVAL, "cr_plan_update_cl: C_l must be finite and >= 0");
+  CR_CUDA(cudaStreamSynchronize(plan->stream));
+  if (plan->hier) plan->hier->numeric_ready = false;
+  plan->h_cl.assign(cl, cl + L + 1);
+  int rc = upload_prior(plan);
+  if (rc) return rc;
+  if (plan->d_pcinv) {
+    cudaFree(plan->d_pcinv);
+    plan->d_pcinv = nullptr;
+  }
+  if (plan->hier) {
+    TimerScope ts(plan->timing, plan->stream, "precompute_cl");
+    rc = build_numeric(plan);
+  }
+  return rc;
 }
 
 int cr_plan_destroy(cr_plan* plan) {

@@ -152,6 +152,7 @@ struct cr_plan {
   cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)
   void* hier_tile_work = nullptr;     // FP32 tile-ordered smoother work vector
   // diagonal-preconditioned CG (created on first use)
+  double* d_dotpart = nullptr;        // [lmax + 1] per-m partial sums of inner products
   double* d_pcinv = nullptr;          // [n_lm] 1 / diag(A), 0 where C_l = 0
   void* cgv[4] = {nullptr, nullptr, nullptr, nullptr};
   double* d_cgdot = nullptr;

@@ -86,6 +86,8 @@ struct AssembleArgs {
   const int* cobs;
   const double* ninv;                 // obs grid, RING order
   Table gD, gB;
+  int with_d, with_noise;             // which terms to assemble
+  const float* base;                  // added to the result (or null)
   float* A;
   int* overflow;
 };
@@ -134,9 +136,10 @@ __global__ void __launch_bounds__(SM_NT) assemble_kernel(AssembleArgs a) {
     for (int j = 0; j < 4; ++j) {
       const float3 u = vp[4 * ty + i], w = vq[4 * tx + j];
       const float dx = u.x - w.x, dy = u.y - w.y, dz = u.z - w.z;
-      acc[i][j] = table_eval(a.gD, sqrtf(dx * dx + dy * dy + dz * dz), &myovf);
+      acc[i][j] = a.with_d ? table_eval(a.gD, sqrtf(dx * dx + dy * dy + dz * dz), &myovf) : 0.f;
     }
-  for (int64_t c = a.cobs_ptr[b]; c < a.cobs_ptr[b + 1]; ++c) {
+  const int64_t c_end = a.with_noise ? a.cobs_ptr[b + 1] : a.cobs_ptr[b];
+  for (int64_t c = a.cobs_ptr[b]; c < c_end; ++c) {
     const int64_t base = (int64_t)a.cobs[c] * a.ratio2;
     for (int c0 = 0; c0 < a.ratio2; c0 += TK) {
       __syncthreads();
@@ -172,10 +175,14 @@ __global__ void __launch_bounds__(SM_NT) assemble_kernel(AssembleArgs a) {
     }
   }
   float* out = a.A + (int64_t)b * TK * TK;
+  const float* bas = a.base ? a.base + (int64_t)b * TK * TK : nullptr;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) out[(4 * tx + j) * TK + 4 * ty + i] = acc[i][j];  // column-major
+    for (int j = 0; j < 4; ++j) {
+      const int64_t e = (4 * tx + j) * TK + 4 * ty + i;  // column-major
+      out[e] = bas ? acc[i][j] + bas[e] : acc[i][j];
+    }
   if (myovf) atomicOr(a.overflow, 1);
 }
 
@@ -543,7 +550,15 @@ static int upload_vec(X** d, const std::vector<X>& h) {
   return CR_OK;
 }
 
+// Assembly inputs kept with the level so that the C_l-dependent numerical
+// part (coupling tables, assembly, ridge search) can be redone alone.
 struct SmootherBuild {
+  int nd = 0;        // coupling-table entries
+  double h = 0.0;    // coupling-table spacing in the chord
+  // the inverse-noise term of A_hat alone (observation-dependent; it sees
+  // the prior only through the set of l with C_l > 0, recorded in an_active)
+  float* d_AN = nullptr;
+  std::vector<char> an_active;
   int* d_order = nullptr;
   int* d_blk_p = nullptr;
   int* d_blk_q = nullptr;
@@ -556,7 +571,7 @@ struct SmootherBuild {
   int* d_ovf = nullptr;
   unsigned* d_amax = nullptr;
   ~SmootherBuild() {
-    void* ptrs[] = {d_order, d_blk_p, d_blk_q, d_cobs_ptr, d_cobs, d_diag, d_gD, d_gB, d_gl, d_ovf, d_amax};
+    void* ptrs[] = {d_order, d_blk_p, d_blk_q, d_cobs_ptr, d_cobs, d_diag, d_gD, d_gB, d_gl, d_ovf, d_amax, d_AN};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -591,7 +606,10 @@ int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
   return CR_OK;
 }
 
-int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisections, double fixed_alpha) {
+// Tile pattern, elimination order, ICC update lists, solve lists and the
+// assembly index lists of a level (geometry only); allocates A_hat and the
+// factor.
+int smoother_structure(cr_plan* P, PixLevel& lev) {
   if (lev.k != 8) return fail(CR_EINVAL, "smoother: only k = 8 tiles are supported");
   lev.nside_t = lev.nside_h / lev.k;
   const int nobs = P->obs.nside;
@@ -662,7 +680,8 @@ int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisection
   for (int p = 0; p < nt; ++p)
     for (int j = 0; j < TK; ++j) perm[(int64_t)p * TK + j] = (int)nest2ring(lev.nside_h, (int64_t)pat.order[p] * TK + j);
 
-  SmootherBuild sb;
+  if (!lev.sb) lev.sb = new SmootherBuild();
+  SmootherBuild& sb = *lev.sb;
   int rc = CR_OK;
   if ((rc = upload_vec(&lev.d_perm, perm))) return rc;
   if ((rc = upload_vec(&lev.d_row_ptr, pat.row_ptr))) return rc;
@@ -685,11 +704,10 @@ int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisection
   CR_CUDA(cudaMalloc(&lev.d_fail, sizeof(int)));
   CR_CUDA(cudaMalloc(&sb.d_ovf, sizeof(int)));
   CR_CUDA(cudaMalloc(&sb.d_amax, sizeof(unsigned)));
-  CR_CUDA(cudaMemset(sb.d_ovf, 0, sizeof(int)));
-  CR_CUDA(cudaMemset(sb.d_amax, 0, sizeof(unsigned)));
   const int64_t nel = pat.nblocks * TK * TK;
   CR_CUDA(cudaMalloc(&lev.d_A, nel * sizeof(float)));
   CR_CUDA(cudaMalloc(&lev.d_L, nel * sizeof(float)));
+  CR_CUDA(cudaMalloc(&sb.d_AN, nel * sizeof(float)));
 
   // coupling tables in the chord d; d_max covers any pixel pair of two
   // vertex-sharing tiles (4 tile radii, measured) with a margin
@@ -710,8 +728,29 @@ int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisection
   }
   const double dmax = std::min(2.0, 4.5 * rmax + 4.0 * std::sqrt(4.0 * M_PI / (12.0 * nobs * nobs)));
   const int Lh = lev.lmax_h;
-  const double h = 2.0 * M_PI / (128.0 * (Lh + 1));
-  const int nd = (int)std::ceil(dmax / h) + 4;
+  sb.h = 2.0 * M_PI / (128.0 * (Lh + 1));
+  sb.nd = (int)std::ceil(dmax / sb.h) + 4;
+  CR_CUDA(cudaMalloc(&sb.d_gl, (Lh + 1) * sizeof(double)));
+  CR_CUDA(cudaMalloc(&sb.d_gD, sb.nd * sizeof(float)));
+  CR_CUDA(cudaMalloc(&sb.d_gB, sb.nd * sizeof(float)));
+  return CR_OK;
+}
+
+// The C_l-dependent numerical part of a level's smoother: coupling tables of
+// D_h and B_h, assembly of A_hat, the ridge search and the factorisation.
+int smoother_numeric(cr_plan* P, PixLevel& lev, double ridge_factor, int bisections, double fixed_alpha) {
+  if (!lev.sb) return fail(CR_ESTATE, "smoother: structure not built");
+  SmootherBuild& sb = *lev.sb;
+  const BlockPattern& pat = lev.pat;
+  const int nt = pat.ntile;
+  const int nobs = P->obs.nside;
+  const int Lh = lev.lmax_h;
+  const double h = sb.h;
+  const int nd = sb.nd;
+  const int64_t nel = pat.nblocks * TK * TK;
+  int rc = CR_OK;
+  CR_CUDA(cudaMemsetAsync(sb.d_ovf, 0, sizeof(int), P->stream));
+  CR_CUDA(cudaMemsetAsync(sb.d_amax, 0, sizeof(unsigned), P->stream));
   std::vector<double> gD(Lh + 1, 0.0), gB(Lh + 1, 0.0);
   for (int l = 0; l <= Lh; ++l) {
     const double cl = P->h_cl[l];
@@ -720,9 +759,7 @@ int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisection
       gB[l] = lev.fl[l] * P->h_bl[l];
     }
   }
-  CR_CUDA(cudaMalloc(&sb.d_gl, (Lh + 1) * sizeof(double)));
-  CR_CUDA(cudaMalloc(&sb.d_gD, nd * sizeof(float)));
-  CR_CUDA(cudaMalloc(&sb.d_gB, nd * sizeof(float)));
+  CR_CUDA(cudaStreamSynchronize(P->stream));
   CR_CUDA(cudaMemcpy(sb.d_gl, gD.data(), (Lh + 1) * sizeof(double), cudaMemcpyHostToDevice));
   coupling_table_kernel<<<(nd + 127) / 128, 128, 0, P->stream>>>(sb.d_gl, Lh, h, nd, sb.d_gD);
   CR_CUDA(cudaStreamSynchronize(P->stream));
@@ -742,19 +779,34 @@ int build_smoother(cr_plan* P, PixLevel& lev, double ridge_factor, int bisection
   aa.ninv = P->d_ninv;
   aa.gD = Table{sb.d_gD, nd, (float)(1.0 / h)};
   aa.gB = Table{sb.d_gB, nd, (float)(1.0 / h)};
-  aa.A = lev.d_A;
   aa.overflow = sb.d_ovf;
-  {
-    TimerScope ts(P->timing, P->stream, "smoother_assemble");
+  auto assemble = [&](bool with_d, bool with_noise, const float* base, float* out) {
     for (int64_t b0 = 0; b0 < pat.nblocks; b0 += (1 << 20)) {
       const int nb = (int)std::min<int64_t>(1 << 20, pat.nblocks - b0);
       AssembleArgs ab = aa;
+      ab.with_d = with_d;
+      ab.with_noise = with_noise;
+      ab.base = base ? base + b0 * TK * TK : nullptr;
       ab.blk_p = sb.d_blk_p + b0;
       ab.blk_q = sb.d_blk_q + b0;
       ab.cobs_ptr = sb.d_cobs_ptr + b0;
-      ab.A = lev.d_A + b0 * TK * TK;
+      ab.A = out + b0 * TK * TK;
       { assemble_kernel<<<nb, SM_NT, 0, P->stream>>>(ab); count_launch(); }
     }
+  };
+  // the inverse-noise term B_h Y^T N^-1 Y B_h (observation-dependent) is
+  // assembled once and kept; the prior term D_h is added to it for every C_l
+  std::vector<char> active(Lh + 1);
+  for (int l = 0; l <= Lh; ++l) active[l] = P->h_cl[l] > 0;
+  if (sb.an_active != active) {
+    TimerScope ts(P->timing, P->stream, "smoother_assemble_noise");
+    assemble(false, true, nullptr, sb.d_AN);
+    CR_CHECK_LAUNCH("assemble_kernel");
+    sb.an_active = active;
+  }
+  {
+    TimerScope ts(P->timing, P->stream, "smoother_assemble_prior");
+    assemble(true, false, sb.d_AN, lev.d_A);
     CR_CHECK_LAUNCH("assemble_kernel");
     symmetrise_diag_kernel<<<nt, 256, 0, P->stream>>>(lev.d_A, sb.d_diag);
     CR_CHECK_LAUNCH("symmetrise_diag_kernel");
@@ -843,6 +895,8 @@ template int apply_smoother<double>(cr_plan*, PixLevel&, double*, double*);
 template int apply_smoother<float>(cr_plan*, PixLevel&, float*, float*);
 
 void free_smoother(PixLevel& lev) {
+  delete lev.sb;
+  lev.sb = nullptr;
   void* ptrs[] = {lev.d_A, lev.d_L, lev.d_LT, lev.d_perm, lev.d_row_ptr, lev.d_row_col, lev.d_col_ptr, lev.d_col_row,
                   lev.d_col_blk, lev.d_upd_ptr, lev.d_tgt_blk, lev.d_tgt_u, lev.d_tgt_ptr, lev.d_pair_a, lev.d_pair_b,
                   lev.d_fail};

@@ -148,9 +148,9 @@ static int smoother_lambda_max(cr_plan* P, int h, int iters, double* lam) {
     if ((rc = level_apply<float>(P, h, v, av))) return rc;
     CR_CUDA(cudaMemsetAsync(w, 0, n_lm(L) * sizeof(float2), P->stream));
     if ((rc = smooth_add<float>(P, h, w, av))) return rc;
-    if ((rc = launch_dot<float>(w, av, nullptr, L, H.d_dot, P->stream))) return rc;
-    if ((rc = launch_dot<float>(v, av, nullptr, L, H.d_dot + 1, P->stream))) return rc;
-    if ((rc = launch_dot<float>(w, w, nullptr, L, H.d_dot + 2, P->stream))) return rc;
+    if ((rc = launch_dot<float>(w, av, nullptr, L, H.d_dot, P->d_dotpart, P->stream))) return rc;
+    if ((rc = launch_dot<float>(v, av, nullptr, L, H.d_dot + 1, P->d_dotpart, P->stream))) return rc;
+    if ((rc = launch_dot<float>(w, w, nullptr, L, H.d_dot + 2, P->d_dotpart, P->stream))) return rc;
     double d3[3];
     CR_CUDA(cudaMemcpyAsync(d3, H.d_dot, 3 * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
     CR_CUDA(cudaStreamSynchronize(P->stream));
@@ -223,6 +223,31 @@ static int build_gl_level(cr_plan* P, PixLevel& lev) {
   return rc;
 }
 
+// per-level operator arrays B_h = f_h b_l, D_h = f_h^2 / C_l and the active
+// mask (0 where C_l = 0) of every level (Section 3.2, Eq. A_h)
+static int upload_level_arrays(cr_plan* P) {
+  Hierarchy& H = *P->hier;
+  HierOps& hops = ops_of(P);
+  auto one = [&](int h, const std::vector<double>& f, int Lh) -> int {
+    std::vector<double> b(Lh + 1), d(Lh + 1), act(Lh + 1);
+    for (int l = 0; l <= Lh; ++l) {
+      const bool a = P->h_cl[l] > 0;
+      b[l] = a ? f[l] * P->h_bl[l] : 0.0;
+      d[l] = a ? f[l] * f[l] / P->h_cl[l] : 0.0;
+      act[l] = a ? 1.0 : 0.0;
+    }
+    int r2 = hops.ops[h].b.assign(b);
+    if (!r2) r2 = hops.ops[h].d.assign(d);
+    if (!r2) r2 = hops.ops[h].act.assign(act);
+    return r2;
+  };
+  std::vector<double> ftop(P->lmax + 1, 1.0);
+  int rc = one(0, ftop, P->lmax);
+  for (int i = 0; !rc && i < H.H; ++i) rc = one(i + 1, H.pix[i].fl, H.pix[i].lmax_h);
+  if (!rc) rc = one(H.H + 1, H.fb, H.ld);
+  return rc;
+}
+
 int build_hierarchy(cr_plan* P, const cr_params* p) {
   Hierarchy* Hp = new Hierarchy();
   P->hier = Hp;
@@ -263,20 +288,6 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
   const int nbis = p->ridge_bisections > 0 ? p->ridge_bisections : 30;
   int rc = CR_OK;
   int64_t max_npix_h = 1;
-  // per-level operator arrays
-  auto level_arrays = [&](int h, const std::vector<double>& f, int Lh) -> int {
-    std::vector<double> b(Lh + 1), d(Lh + 1), act(Lh + 1);
-    for (int l = 0; l <= Lh; ++l) {
-      const bool a = P->h_cl[l] > 0;
-      b[l] = a ? f[l] * P->h_bl[l] : 0.0;
-      d[l] = a ? f[l] * f[l] / P->h_cl[l] : 0.0;
-      act[l] = a ? 1.0 : 0.0;
-    }
-    int r2 = hops->ops[h].b.upload(b);
-    if (!r2) r2 = hops->ops[h].d.upload(d);
-    if (!r2) r2 = hops->ops[h].act.upload(act);
-    return r2;
-  };
   // Gauss-Legendre grids for the levels' inverse-noise term (gl_downgrade):
   // decided first, since they may need recurrence tables and observation-grid
   // seeds beyond lmax (up to 2 lmax_h)
@@ -294,7 +305,6 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
     if ((recoef || reseed) && (rc = build_start_tables(P, P->obs))) return rc;
   }
   std::vector<double> ftop(L + 1, 1.0);
-  if ((rc = level_arrays(0, ftop, L))) return rc;
   for (int i = 0; i < H.H; ++i) {
     PixLevel& lev = H.pix[i];
     lev.nside_h = specs[i].nside_h;
@@ -308,11 +318,10 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
     if ((rc = build_start_tables(P, *lev.grid))) return rc;
     if ((rc = ensure_workspace(P, *lev.grid, lev.lmax_h))) return rc;
     max_npix_h = std::max(max_npix_h, lev.grid->npix);
-    if ((rc = level_arrays(i + 1, lev.fl, lev.lmax_h))) return rc;
   }
   H.fb = specs.empty() ? ftop : specs.back().fl;
   for (int l = H.ld + 1; l <= L; ++l) H.fb[l] = 0.0;
-  if ((rc = level_arrays(H.H + 1, H.fb, H.ld))) return rc;
+  if ((rc = upload_level_arrays(P))) return rc;
   // restriction ratios f^{h+1} / f^h for l <= lmax_{h+1}
   for (int h = 0; h <= H.H; ++h) {
     const std::vector<double>& fh = (h == 0) ? ftop : H.pix[h - 1].fl;
@@ -334,15 +343,40 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
   CR_CUDA(cudaMalloc(&P->hier_tile_work, max_npix_h * sizeof(float)));
   CR_CUDA(cudaMalloc(&H.d_dot, 4 * sizeof(double)));
   for (int i = 0; i < 5; ++i) CR_CUDA(cudaMalloc(&H.krylov[i], n_lm(L) * sizeof(double2)));
-  // pixel smoothers (precompute): the paper's ridge search, then (unless the
-  // ridges are given) the ridge is raised until the smoother cannot
-  // over-correct: lambda_max(S_h A_h) <= target (power-iteration estimate)
-  const double lam_target = p->ridge_lambda_target == 0.0 ? 1.5 : p->ridge_lambda_target;
+  // settings of the C_l-dependent precompute
+  H.ridge_factor = rf;
+  H.bisections = nbis;
+  H.lam_target = p->ridge_lambda_target == 0.0 ? 1.5 : p->ridge_lambda_target;
+  if (p->ridge_alpha && p->nlevels > 0) H.ridge_fixed.assign(p->ridge_alpha, p->ridge_alpha + H.H);
+  // smoother structure (geometry only)
+  for (int i = 0; i < H.H; ++i)
+    if ((rc = smoother_structure(P, H.pix[i]))) return rc;
+  if (p->defer_precompute) {
+    CR_CUDA(cudaStreamSynchronize(P->stream));
+    return CR_OK;
+  }
+  return build_numeric(P);
+}
+
+// The C_l-dependent part of the precompute (Section 5: recomputed whenever
+// the prior changes): level arrays, the pixel smoothers' assembly, ridge
+// search and factorisation, the top-level diagonal smoother and the bottom
+// dense inverse.  Device arrays are updated in place where their sizes allow.
+int build_numeric(cr_plan* P) {
+  Hierarchy& H = *P->hier;
+  const int L = P->lmax;
+  H.numeric_ready = false;
+  int rc = upload_level_arrays(P);
+  if (rc) return rc;
+  // pixel smoothers: the paper's ridge search, then (unless the ridges are
+  // given) the ridge is raised until the smoother cannot over-correct:
+  // lambda_max(S_h A_h) <= target (power-iteration estimate)
+  const bool fixed_given = !H.ridge_fixed.empty();
+  const double lam_target = H.lam_target;
   for (int i = 0; i < H.H; ++i) {
-    const bool fixed_given = (p->ridge_alpha && p->nlevels > 0);
-    const double fixed = fixed_given ? p->ridge_alpha[i] : -1.0;
     PixLevel& lev = H.pix[i];
-    if ((rc = build_smoother(P, lev, rf, nbis, fixed))) return rc;
+    if ((rc = smoother_numeric(P, lev, H.ridge_factor, H.bisections, fixed_given ? H.ridge_fixed[i] : -1.0)))
+      return rc;
     lev.lambda_max = 0.0;
     if (fixed_given || lam_target < 0.0) continue;
     for (int trial = 0; trial < 24; ++trial) {
@@ -364,7 +398,8 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
   // the same bound for the top-level diagonal smoother: scale the high-pass
   // by target / lambda_max when the estimate exceeds the target
   H.top_scale = 1.0;
-  if (lam_target > 0.0 && !(p->ridge_alpha && p->nlevels > 0)) {
+  H.top_lambda = 0.0;
+  if (lam_target > 0.0 && !fixed_given) {
     double lam = 0.0;
     if ((rc = smoother_lambda_max(P, 0, 12, &lam))) return rc;
     H.top_lambda = lam;
@@ -374,11 +409,12 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
       std::vector<double> hv(n);
       CR_CUDA(cudaMemcpy(hv.data(), H.inv_diag_hp.d, n * sizeof(double), cudaMemcpyDeviceToHost));
       for (auto& v : hv) v *= H.top_scale;
-      if ((rc = H.inv_diag_hp.upload(hv))) return rc;
+      if ((rc = H.inv_diag_hp.assign(hv))) return rc;
     }
   }
   if ((rc = build_bottom(P, H))) return rc;
   CR_CUDA(cudaStreamSynchronize(P->stream));
+  H.numeric_ready = true;
   return CR_OK;
 }
 
@@ -426,7 +462,7 @@ void free_hierarchy(cr_plan* P) {
 
 // relative S^-1-weighted residual sqrt(r^T S^-1 r / b^T S^-1 b) (FP64 vectors)
 static int weighted_norm2(cr_plan* P, const void* v, double* out) {
-  int rc = launch_dot<double>(v, v, P->d_sinv, P->lmax, P->hier->d_dot, P->stream);
+  int rc = launch_dot<double>(v, v, P->d_sinv, P->lmax, P->hier->d_dot, P->d_dotpart, P->stream);
   if (rc) return rc;
   CR_CUDA(cudaMemcpyAsync(out, P->hier->d_dot, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
   CR_CUDA(cudaStreamSynchronize(P->stream));
@@ -469,8 +505,8 @@ static int pcg_solve(cr_plan* P, void* x, const void* b, double eps, int max_cyc
       if ((rc = launch_add_f2d((double*)z, (const float*)c32, 2 * nlm, P->stream))) return rc;
     }
     double d[3];
-    if ((rc = launch_dot<double>(z, r, nullptr, L, H.d_dot, P->stream))) return rc;
-    if (k > 1 && (rc = launch_dot<double>(z, rold, nullptr, L, H.d_dot + 1, P->stream))) return rc;
+    if ((rc = launch_dot<double>(z, r, nullptr, L, H.d_dot, P->d_dotpart, P->stream))) return rc;
+    if (k > 1 && (rc = launch_dot<double>(z, rold, nullptr, L, H.d_dot + 1, P->d_dotpart, P->stream))) return rc;
     CR_CUDA(cudaMemcpyAsync(d, H.d_dot, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
     CR_CUDA(cudaStreamSynchronize(P->stream));
     const double zr = d[0];
@@ -486,7 +522,7 @@ static int pcg_solve(cr_plan* P, void* x, const void* b, double eps, int max_cyc
       TimerScope ts(P->timing, P->stream, "outer_residual");
       if ((rc = level_apply<double>(P, 0, pv, q))) return rc;
     }
-    if ((rc = launch_dot<double>(pv, q, nullptr, L, H.d_dot + 2, P->stream))) return rc;
+    if ((rc = launch_dot<double>(pv, q, nullptr, L, H.d_dot + 2, P->d_dotpart, P->stream))) return rc;
     CR_CUDA(cudaMemcpyAsync(d + 2, H.d_dot + 2, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
     CR_CUDA(cudaStreamSynchronize(P->stream));
     if (!(d[2] > 0.0)) return fail(CR_ENONFINITE, "pcg: non-positive curvature p^T A p");
@@ -626,9 +662,11 @@ using namespace cr;
 
 extern "C" {
 
-static int check_hier(cr_plan* plan, const char* who) {
+static int check_hier(cr_plan* plan, const char* who, bool numeric = false) {
   if (!plan) return fail(CR_EINVAL, std::string(who) + ": null plan");
   if (!plan->hier) return fail(CR_ESTATE, std::string(who) + ": plan was created without levels");
+  if (numeric && !plan->hier->numeric_ready)
+    return fail(CR_ESTATE, std::string(who) + ": the C_l-dependent precompute was deferred (cr_load or cr_plan_update_cl first)");
   return CR_OK;
 }
 
@@ -707,27 +745,27 @@ int cr_prolong_add(cr_plan* plan, int h, const void* c_H, void* x_h, int dtype) 
 }
 
 int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype) {
-  int rc = check_hier(plan, "cr_smooth");
+  int rc = check_hier(plan, "cr_smooth", true);
   if (rc) return rc;
   if (h < 0 || h > plan->hier->H) return fail(CR_EINVAL, "cr_smooth: level out of range");
   return dtype == CR_F64 ? level_smooth<double>(plan, h, r, c) : level_smooth<float>(plan, h, r, c);
 }
 
 int cr_bottom_solve(cr_plan* plan, const void* b, void* x, int dtype) {
-  int rc = check_hier(plan, "cr_bottom_solve");
+  int rc = check_hier(plan, "cr_bottom_solve", true);
   if (rc) return rc;
   return dtype == CR_F64 ? bottom_solve<double>(plan, *plan->hier, b, x)
                          : bottom_solve<float>(plan, *plan->hier, b, x);
 }
 
 int cr_bottom_matrix(cr_plan* plan, double* host, int* nd) {
-  int rc = check_hier(plan, "cr_bottom_matrix");
+  int rc = check_hier(plan, "cr_bottom_matrix", true);
   if (rc) return rc;
   return bottom_matrix(plan, host, nd);
 }
 
 int cr_wcycle(cr_plan* plan, void* x, const void* b, int nrhs, int dtype) {
-  int rc = check_hier(plan, "cr_wcycle");
+  int rc = check_hier(plan, "cr_wcycle", true);
   if (rc) return rc;
   const int64_t nlm = n_lm(plan->lmax);
   const size_t es = dtype == CR_F64 ? sizeof(double2) : sizeof(float2);
@@ -754,7 +792,7 @@ int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int ma
     }
     return CR_OK;
   }
-  int rc = check_hier(plan, "cr_solve");
+  int rc = check_hier(plan, "cr_solve", true);
   if (rc) return rc;
   if ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) return fail(CR_EINVAL, "cr_solve: mode precision must be CR_F64 or CR_MIXED");
   if (max_cycles < 1 || !(eps >= 0.0)) return fail(CR_EINVAL, "cr_solve: eps / max_cycles");
