@@ -81,6 +81,13 @@ extern "C" {
  * needs no levels; max_cycles caps the CG iterations and cycles_out counts
  * them (one FP64 A per iteration). */
 #define CR_CG 16
+/* solve flag (with CR_MIXED, stationary): the FP32 cycles of up to 16
+ * right-hand sides run together, every Legendre stage of the hierarchy (the
+ * level operators and the pixel levels' transforms around the smoothers) as
+ * one tensor-core contraction over the right-hand sides (BF16 operands, FP32
+ * accumulation); the outer residual b - A x stays FP64 per right-hand side.
+ * Also accepted by cr_batch_create. */
+#define CR_TC_CYCLES 32
 
 /* grid kinds */
 #define CR_GRID_HEALPIX 0
@@ -301,7 +308,10 @@ int cr_alm_dot(cr_plan* plan, const void* u, const void* v, int weighted, double
  * tables created on first use), and instantiates the graph.  x[i], b[i]:
  * device FP64 complex [nrhs[i]][N_lm(lmax_i)]; the buffers are bound into
  * the graph, so later runs read b and write x at the same addresses.  mode:
- * CR_F64 or CR_MIXED (stationary).  cr_batch_run launches the graph on that
+ * CR_F64 or CR_MIXED (stationary), or CR_MIXED | CR_TC_CYCLES (the cycles of
+ * each plan's right-hand sides batched 16 at a time on the tensor cores; a
+ * completion wait that gives up inside a replay is reported by the plan's
+ * next uncaptured tensor-core call).  cr_batch_run launches the graph on that
  * stream (asynchronous); replays give results identical to the uncaptured
  * solves.  cr_batch_nodes: number of graph nodes (kernels and copies) and of
  * kernel nodes (either pointer may be NULL).

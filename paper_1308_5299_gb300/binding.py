@@ -22,6 +22,7 @@ CR_OK = 0
 CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED, CR_CG = 0, 1, 2, 4, 8, 16
 CR_DRAW_FLUCT, CR_DRAW_PLAIN = 1, 2
 CR_TC = 3
+CR_TC_CYCLES = 32
 CR_PROBE_ALM, CR_PROBE_MAP = 0, 1
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0
@@ -512,22 +513,6 @@ class Batch:
         k = ctypes.c_int64()
         _check(lib().cr_batch_nodes(self._h, None, ctypes.byref(k)))
         return k.value
-
-    def update_cl(self, cl):
-        """Replace the prior C_l and redo the C_l-dependent precompute
-        (``cr_plan_update_cl``)."""
-        cl = np.ascontiguousarray(cl, dtype=np.float64)
-        if cl.shape != (self.lmax + 1,):
-            raise ValueError("update_cl: C_l must have lmax + 1 entries")
-        _check(lib().cr_plan_update_cl(self._h, cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-
-    def save(self, path):
-        """Write the precompute checkpoint (``cr_save``)."""
-        _check(lib().cr_save(self._h, os.fsencode(path)))
-
-    def load(self, path):
-        """Read a precompute checkpoint made for the same inputs (``cr_load``)."""
-        _check(lib().cr_load(self._h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "_h", None):

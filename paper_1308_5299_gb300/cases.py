@@ -1,0 +1,87 @@
+"""Timed runs of single library calls on synthetic inputs, one JSON line each.
+
+    python -m paper_1308_5299_gb300.cases tc --nside 512 --lmax 1023 --nrhs 16
+
+``tc``: batched synthesis, adjoint synthesis and system-matrix application
+with the Legendre contractions on the tensor cores (BF16 operands, FP32
+accumulation) for ``nrhs`` right-hand sides, against the same number of
+FP32 CUDA-core calls, timed with CUDA events on the plan's stream after
+``--warmup`` untimed repetitions.  Inputs: random coefficients and maps of
+the Planck-shaped problem of that size (prior, beam and noise of
+``synthetic.problem_inputs`` where the name exists, else a damped spectrum
+with a 60 arcmin beam and unit noise).
+"""
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import binding, synthetic
+
+
+def _problem(nside, lmax, dev):
+    name = "nside%d_lmax%d" % (nside, lmax)
+    if name in synthetic.CONFIGS:
+        _, cl, bl, ninv = synthetic.problem_inputs(name)
+        return cl, bl, torch.from_numpy(ninv).to(dev)
+    cl = synthetic.cl_spectrum(lmax, True)
+    bl = synthetic.gaussian_beam(lmax, 60.0)
+    return cl, bl, torch.ones(12 * nside * nside, dtype=torch.float64, device=dev)
+
+
+def _time(fn, stream, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tc_case(nside, lmax, nrhs, warmup, reps):
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    cl, bl, ninv = _problem(nside, lmax, dev)
+    plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=ninv, stream=stream)
+    nlm = binding.n_lm(lmax)
+    a = torch.from_numpy(np.stack([synthetic.random_alm(lmax, seed=300 + j) for j in range(nrhs)]))
+    a = a.to(torch.complex64).to(dev)
+    m = torch.randn((nrhs, plan.npix), dtype=torch.float32, device=dev)
+    maps = torch.empty_like(m)
+    out = torch.empty((nrhs, nlm), dtype=torch.complex64, device=dev)
+    runs = {
+        "synthesis": (lambda: plan.sht_synth(a, maps, tensor_cores=True),
+                      lambda: [plan.sht_synth(a[j], maps[j]) for j in range(nrhs)]),
+        "adjoint": (lambda: plan.sht_adjoint(m, out, tensor_cores=True),
+                    lambda: [plan.sht_adjoint(m[j], out[j]) for j in range(nrhs)]),
+        "apply_A": (lambda: plan.apply_A(a, out, tensor_cores=True),
+                    lambda: [plan.apply_A(a[j], out[j]) for j in range(nrhs)]),
+    }
+    res = {}
+    for name, (tc, f32) in runs.items():
+        for _ in range(warmup):
+            tc()
+            f32()
+        torch.cuda.synchronize()
+        res[name] = {"tensor_core_ms": _time(tc, stream, reps), "fp32_ms": _time(f32, stream, reps)}
+    return {"case": "tc", "nside": nside, "lmax": lmax, "nrhs": nrhs, "reps": reps, "ms": res}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("case", choices=["tc"])
+    ap.add_argument("--nside", type=int, default=512)
+    ap.add_argument("--lmax", type=int, default=1023)
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=2)
+    args = ap.parse_args(argv)
+    binding.lib()
+    print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps)))
+
+
+if __name__ == "__main__":
+    main()

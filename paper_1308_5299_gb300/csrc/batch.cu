@@ -15,6 +15,8 @@
 namespace cr {
 int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mode, int* cycles_out,
           double* relres_out, double* history);
+int solve_tc(cr_plan* P, void* x, const void* b, int nrhs, double eps, int max_cycles, bool fixed, int* cycles_out,
+             double* relres_out, double* history);
 }  // namespace cr
 
 struct cr_batch {
@@ -33,8 +35,11 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
                     const int* nrhs, int cycles, int mode) {
   if (!out || nplans < 1 || !plans || !x || !b || !nrhs || cycles < 1)
     return fail(CR_EINVAL, "cr_batch_create: bad arguments");
-  if ((mode & ~3) != 0 || ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED))
-    return fail(CR_EINVAL, "cr_batch_create: mode must be CR_F64 or CR_MIXED (stationary, fixed count)");
+  const bool tc = (mode & CR_TC_CYCLES) != 0;
+  if ((mode & ~(3 | CR_TC_CYCLES)) != 0 || ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) ||
+      (tc && (mode & 3) != CR_MIXED))
+    return fail(CR_EINVAL, "cr_batch_create: mode must be CR_F64 or CR_MIXED (stationary, fixed count), "
+                           "CR_TC_CYCLES only with CR_MIXED");
   cudaStream_t st = plans[0] ? plans[0]->stream : nullptr;
   if (!st) return fail(CR_EINVAL, "cr_batch_create: graph capture needs a created stream, not the default stream");
   for (int i = 0; i < nplans; ++i) {
@@ -44,12 +49,13 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
     if (plans[i]->stream != st) return fail(CR_EINVAL, "cr_batch_create: plans must share one stream");
     if (nrhs[i] < 0) return fail(CR_EINVAL, "cr_batch_create: nrhs < 0");
   }
-  const int fmode = mode | CR_FIXED;
+  const int fmode = (mode & 3) | CR_FIXED;
   // one uncaptured solve per plan first: it builds the tables created lazily
   // on first use, which must not be allocated inside the capture
   for (int i = 0; i < nplans; ++i) {
     if (nrhs[i] == 0) continue;
-    int rc = solve(plans[i], x[i], b[i], 0.0, 1, fmode, nullptr, nullptr, nullptr);
+    int rc = tc ? solve_tc(plans[i], x[i], b[i], nrhs[i], 0.0, 1, true, nullptr, nullptr, nullptr)
+                : solve(plans[i], x[i], b[i], 0.0, 1, fmode, nullptr, nullptr, nullptr);
     if (rc) return rc;
   }
   CR_CUDA(cudaStreamSynchronize(st));
@@ -64,7 +70,9 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
   for (int i = 0; i < nplans && !rc; ++i) {
     const int64_t nlm = n_lm(plans[i]->lmax);
     plans[i]->capturing = true;
-    for (int j = 0; j < nrhs[i] && !rc; ++j)
+    if (tc && nrhs[i] > 0)
+      rc = solve_tc(plans[i], x[i], b[i], nrhs[i], 0.0, cycles, true, nullptr, nullptr, nullptr);
+    for (int j = 0; !tc && j < nrhs[i] && !rc; ++j)
       rc = solve(plans[i], (char*)x[i] + j * nlm * sizeof(double2), (const char*)b[i] + j * nlm * sizeof(double2), 0.0,
                  cycles, fmode, nullptr, nullptr, nullptr);
     plans[i]->capturing = false;

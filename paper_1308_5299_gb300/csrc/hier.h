@@ -112,6 +112,12 @@ struct Hierarchy {
   double* d_dot_host = nullptr;
   void* ops_store = nullptr;  // per-level operator arrays (solver.cu)
   void* krylov[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // PCG vectors (FP64, top level)
+  // FP32 work vectors of the batched cycles (16 right-hand sides each,
+  // [16][n_lm(lmax_h)] complex64), allocated on first use
+  struct TcWork {
+    float2 *x = nullptr, *b = nullptr, *r = nullptr;
+  };
+  std::vector<TcWork> tcw;  // [H + 2]
   // settings of the C_l-dependent precompute, kept for cr_plan_update_cl
   double ridge_factor = 1.5;
   int bisections = 30;

@@ -79,6 +79,25 @@ int launch_tc_synth(const LegArgs<float>& la, const float2* alm, int64_t ld_alm,
 int launch_tc_adjoint(const LegArgs<float>& la, const float2* phase, int nrhs, float2* partial, int* nblk,
                       int* status, cudaStream_t st);
 int tc_adjoint_blocks(int npolar, int npairs);
+
+// batched tensor-core stages of a plan (plan.cu): phase slots and partial
+// rows for 16 right-hand sides, the Legendre stages and the finalisation
+struct TcTail {
+  const float* dl_out = nullptr;
+  const float* dadd = nullptr;
+  const float2* xadd = nullptr;
+  const float2* bsub = nullptr;
+  float2* out = nullptr;
+  int accumulate = 0;
+};
+int tc_begin(cr_plan* P, const Grid& g, int L, bool adjoint, bool reset_status);
+int tc_end(cr_plan* P, const char* what);
+float2* tc_slot(cr_plan* P, const Grid& g, int L, int r);
+int tc_synth_stage(cr_plan* P, const Grid& g, int L, const float2* x, int nr, const float* dl);
+int tc_adjoint_tail(cr_plan* P, const Grid& g, int L, int nr, const TcTail& t);
+int tc_ring(cr_plan* P, const Grid& g, int L, int r, int mode, const float* map_in, float* map_out);
+int tc_sandwich(cr_plan* P, const Grid& g, int L, int nr, const float2* x, const float* dl_in, const float* pix,
+                const TcTail& t);
 template <typename T> int launch_leg_finalize(const FinalizeArgs<T>& f, cudaStream_t st);
 int launch_leg_synth_df(const LegArgs<double>& a, cudaStream_t st);
 int launch_leg_adjoint_df(const LegArgs<double>& a, int* nblk, cudaStream_t st);

@@ -671,6 +671,10 @@ static int check_ptr(const void* p, int dtype) {
   return CR_OK;
 }
 
+}  // extern "C"
+
+namespace cr {
+
 // Batched transforms with the Legendre contractions on the tensor cores
 // (BF16 operands, FP32 accumulation; legendre_tc.cu) on FP32 data, 16
 // right-hand sides per Legendre launch; the ring FFTs run per right-hand side.
@@ -684,19 +688,22 @@ static int grow(void** buf, int64_t* have, int64_t need) {
   return CR_OK;
 }
 
-static int tc_begin(cr_plan* P, const Grid& g, int L, bool adjoint) {
+int tc_begin(cr_plan* P, const Grid& g, int L, bool adjoint, bool reset_status) {
   int rc = grow(&P->tc_phase, &P->tc_phase_bytes, (int64_t)16 * g.nring * (L + 1) * (int64_t)sizeof(float2));
   if (!rc && adjoint) {
     const int64_t nblk = tc_adjoint_blocks(g.npolar32, g.npairs);
     rc = grow(&P->tc_partial, &P->tc_partial_bytes, 16 * nblk * n_lm(L) * (int64_t)sizeof(float2));
   }
   if (rc) return rc;
-  if (!P->d_tc_status) CR_CUDA(cudaMalloc(&P->d_tc_status, sizeof(int)));
-  CR_CUDA(cudaMemsetAsync(P->d_tc_status, 0, sizeof(int), P->stream));
+  if (!P->d_tc_status) {
+    CR_CUDA(cudaMalloc(&P->d_tc_status, sizeof(int)));
+    reset_status = true;
+  }
+  if (reset_status) CR_CUDA(cudaMemsetAsync(P->d_tc_status, 0, sizeof(int), P->stream));
   return CR_OK;
 }
 
-static int tc_end(cr_plan* P, const char* what) {
+int tc_end(cr_plan* P, const char* what) {
   int st = 0;
   CR_CUDA(cudaMemcpyAsync(&st, P->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
   CR_CUDA(cudaStreamSynchronize(P->stream));
@@ -704,14 +711,23 @@ static int tc_end(cr_plan* P, const char* what) {
   return CR_OK;
 }
 
-static float2* tc_slot(cr_plan* P, const Grid& g, int L, int r) {
+float2* tc_slot(cr_plan* P, const Grid& g, int L, int r) {
   return reinterpret_cast<float2*>(P->tc_phase) + (int64_t)r * g.nring * (L + 1);
 }
 
+// the synthesis Legendre stage of nr <= 16 right-hand sides x [nr][n_lm(L)]
+// (times dl, may be null) into the phase slots
+int tc_synth_stage(cr_plan* P, const Grid& g, int L, const float2* x, int nr, const float* dl) {
+  LegArgs<float> la = leg_args<float>(P, g, L);
+  la.dl = dl;
+  TimerScope ts(P->timing, P->stream, "legendre_synth_tc", leg_work(g, L) * nr);
+  return launch_tc_synth(la, x, n_lm(L), nr, tc_slot(P, g, L, 0), P->d_tc_status, P->stream);
+}
+
 // the adjoint Legendre stage of nr right-hand sides from the phase slots,
-// then out_r = dl_out sum_blk partial + dadd xadd_r per right-hand side
-static int tc_adjoint_tail(cr_plan* P, const Grid& g, int L, int nr, const float* dl_out, const float* dadd,
-                           const float2* xadd, float2* out) {
+// then per right-hand side r (vectors at stride n_lm(L)):
+//   out_r (+)= dl_out sum_blk partial + dadd xadd_r   (or bsub_r - that)
+int tc_adjoint_tail(cr_plan* P, const Grid& g, int L, int nr, const TcTail& t) {
   LegArgs<float> la = leg_args<float>(P, g, L);
   const int64_t nlm = n_lm(L);
   int nblk = 0, rc;
@@ -726,29 +742,59 @@ static int tc_adjoint_tail(cr_plan* P, const Grid& g, int L, int nr, const float
     f.partial = reinterpret_cast<const float2*>(P->tc_partial) + (int64_t)r * nblk * nlm;
     f.nblk = nblk;
     f.L = L;
-    f.dl_out = dl_out;
-    f.dadd = dadd;
-    f.xadd = xadd ? xadd + r * nlm : nullptr;
-    f.out = out + r * nlm;
+    f.dl_out = t.dl_out;
+    f.dadd = t.dadd;
+    f.xadd = t.xadd ? t.xadd + r * nlm : nullptr;
+    f.bsub = t.bsub ? t.bsub + r * nlm : nullptr;
+    f.accumulate = t.accumulate;
+    f.out = t.out + r * nlm;
     TimerScope ts(P->timing, P->stream, "legendre_finalize_tc", (double)(nblk + 1) * nlm * sizeof(float2));
     if ((rc = launch_leg_finalize<float>(f, P->stream))) return rc;
   }
   return CR_OK;
 }
 
-static int tc_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, int nrhs) {
-  int rc = tc_begin(P, g, L, false);
+// ring FFT stage of phase slot r: mode 0 slot -> map_out, mode 1 map_in -> slot
+int tc_ring(cr_plan* P, const Grid& g, int L, int r, int mode, const float* map_in, float* map_out) {
+  RingArgs<float> ra = ring_args<float>(P, g, L);
+  ra.phase = tc_slot(P, g, L, r);
+  ra.map_in = map_in;
+  ra.map_out = map_out;
+  TimerScope ts(P->timing, P->stream, mode == 0 ? "ring_fft_synth_f32" : "ring_fft_adjoint_f32",
+                fft_bytes<float>(g, L, 1));
+  return launch_ring_fft<float>(ra, mode, P->stream);
+}
+
+// y_r = dl_out Y^T diag(pix) Y (dl_in x_r) + dadd x_r (or bsub_r - that) for
+// nr <= 16 right-hand sides at stride n_lm(L), both Legendre stages on the
+// tensor cores
+int tc_sandwich(cr_plan* P, const Grid& g, int L, int nr, const float2* x, const float* dl_in, const float* pix,
+                const TcTail& t) {
+  int rc = tc_synth_stage(P, g, L, x, nr, dl_in);
   if (rc) return rc;
-  LegArgs<float> la = leg_args<float>(P, g, L);
+  for (int r = 0; r < nr; ++r) {
+    RingArgs<float> ra = ring_args<float>(P, g, L);
+    ra.phase = tc_slot(P, g, L, r);
+    ra.pixdiag = pix;
+    TimerScope ts(P->timing, P->stream, "ring_fft_apply_f32",
+                  fft_bytes<float>(g, L, 1) + (double)g.nring * (L + 1) * sizeof(float2));
+    if ((rc = launch_ring_fft<float>(ra, 2, P->stream))) return rc;
+  }
+  return tc_adjoint_tail(P, g, L, nr, t);
+}
+
+}  // namespace cr
+
+extern "C" {
+
+static int tc_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, int nrhs) {
+  int rc = tc_begin(P, g, L, false, true);
+  if (rc) return rc;
   const int64_t nlm = n_lm(L);
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int nr = std::min(16, nrhs - r0);
-    const float2* a = reinterpret_cast<const float2*>(alm) + (int64_t)r0 * nlm;
-    {
-      TimerScope ts(P->timing, P->stream, "legendre_synth_tc", leg_work(g, L) * nr);
-      rc = launch_tc_synth(la, a, nlm, nr, tc_slot(P, g, L, 0), P->d_tc_status, P->stream);
-    }
-    if (rc) return rc;
+    if ((rc = tc_synth_stage(P, g, L, reinterpret_cast<const float2*>(alm) + (int64_t)r0 * nlm, nr, nullptr)))
+      return rc;
     for (int r = 0; r < nr; ++r) {
       RingArgs<float> ra = ring_args<float>(P, g, L);
       ra.phase = tc_slot(P, g, L, r);
@@ -761,7 +807,7 @@ static int tc_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map
 }
 
 static int tc_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, int nrhs) {
-  int rc = tc_begin(P, g, L, true);
+  int rc = tc_begin(P, g, L, true, true);
   if (rc) return rc;
   const int64_t nlm = n_lm(L);
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
@@ -773,8 +819,9 @@ static int tc_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* a
       TimerScope ts(P->timing, P->stream, "ring_fft_adjoint_f32", fft_bytes<float>(g, L, 1));
       if ((rc = launch_ring_fft<float>(ra, 1, P->stream))) return rc;
     }
-    rc = tc_adjoint_tail(P, g, L, nr, nullptr, nullptr, nullptr, reinterpret_cast<float2*>(alm) + r0 * nlm);
-    if (rc) return rc;
+    TcTail t;
+    t.out = reinterpret_cast<float2*>(alm) + r0 * nlm;
+    if ((rc = tc_adjoint_tail(P, g, L, nr, t))) return rc;
   }
   return tc_end(P, "tensor-core adjoint: a completion wait gave up");
 }
@@ -784,29 +831,18 @@ static int tc_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* a
 static int tc_apply(cr_plan* P, const void* x, void* y, int nrhs) {
   const Grid& g = P->obs;
   const int L = P->lmax;
-  int rc = tc_begin(P, g, L, true);
+  int rc = tc_begin(P, g, L, true, true);
   if (rc) return rc;
-  LegArgs<float> la = leg_args<float>(P, g, L);
-  la.dl = P->d_bl32;
   const int64_t nlm = n_lm(L);
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int nr = std::min(16, nrhs - r0);
     const float2* xr = reinterpret_cast<const float2*>(x) + (int64_t)r0 * nlm;
-    {
-      TimerScope ts(P->timing, P->stream, "legendre_synth_tc", leg_work(g, L) * nr);
-      rc = launch_tc_synth(la, xr, nlm, nr, tc_slot(P, g, L, 0), P->d_tc_status, P->stream);
-    }
-    if (rc) return rc;
-    for (int r = 0; r < nr; ++r) {
-      RingArgs<float> ra = ring_args<float>(P, g, L);
-      ra.phase = tc_slot(P, g, L, r);
-      ra.pixdiag = P->d_ninv32;
-      TimerScope ts(P->timing, P->stream, "ring_fft_apply_f32",
-                    fft_bytes<float>(g, L, 1) + (double)g.nring * (L + 1) * sizeof(float2));
-      if ((rc = launch_ring_fft<float>(ra, 2, P->stream))) return rc;
-    }
-    rc = tc_adjoint_tail(P, g, L, nr, P->d_bl32, P->d_sinv32, xr, reinterpret_cast<float2*>(y) + r0 * nlm);
-    if (rc) return rc;
+    TcTail t;
+    t.dl_out = P->d_bl32;
+    t.dadd = P->d_sinv32;
+    t.xadd = xr;
+    t.out = reinterpret_cast<float2*>(y) + r0 * nlm;
+    if ((rc = tc_sandwich(P, g, L, nr, xr, P->d_bl32, P->d_ninv32, t))) return rc;
   }
   return tc_end(P, "tensor-core apply: a completion wait gave up");
 }

@@ -129,6 +129,118 @@ static int cycle(cr_plan* P, int h, void* x, const void* b, bool x_zero, const v
   return smooth_add<T>(P, h, x, r);
 }
 
+// ---------------------------------------------------------------------------
+// Batched CR-Cycle: the FP32 cycle above for up to 16 right-hand sides at
+// once, every Legendre stage (level operators A_h on their noise grids, the
+// pixel levels' Y_h and Y_h^T around the smoother) as one tensor-core
+// contraction over the right-hand sides (BF16 operands, FP32 accumulation);
+// ring FFTs, pixel smoothers, restriction, prolongation and the bottom solve
+// run per right-hand side.  Level h keeps its vectors in tcw[h], contiguous
+// [16][n_lm(lmax_h)].
+
+static int ensure_tc_work(cr_plan* P) {
+  Hierarchy& H = *P->hier;
+  if ((int)H.tcw.size() == H.H + 2) return CR_OK;
+  H.tcw.assign(H.H + 2, Hierarchy::TcWork());
+  for (int h = 0; h <= H.H + 1; ++h) {
+    const size_t bytes = (size_t)16 * n_lm(lmax_of(P, h)) * sizeof(float2);
+    CR_CUDA(cudaMalloc(&H.tcw[h].x, bytes));
+    CR_CUDA(cudaMalloc(&H.tcw[h].b, bytes));
+    CR_CUDA(cudaMalloc(&H.tcw[h].r, bytes));
+  }
+  return CR_OK;
+}
+
+// R = B - A_h X for nr right-hand sides
+static int residual_tc(cr_plan* P, int h, int nr, const float2* X, const float2* B, float2* R) {
+  LevelOps& o = ops_of(P).ops[h];
+  const int L = lmax_of(P, h);
+  const float* pix = nullptr;
+  const Grid& g = noise_grid<float>(P, h, &pix);
+  int rc = tc_begin(P, g, L, true, false);
+  if (rc) return rc;
+  TcTail t;
+  t.dl_out = o.b.get<float>();
+  t.dadd = o.d.get<float>();
+  t.xadd = X;
+  t.bsub = B;
+  t.out = R;
+  return tc_sandwich(P, g, L, nr, X, o.b.get<float>(), pix, t);
+}
+
+// X += S_h R for nr right-hand sides
+static int smooth_add_tc(cr_plan* P, int h, int nr, float2* X, const float2* R) {
+  Hierarchy& H = *P->hier;
+  const int L = lmax_of(P, h);
+  const int64_t nlm = n_lm(L);
+  if (h == 0) {
+    TimerScope ts(P->timing, P->stream, "top_smoother");
+    for (int r = 0; r < nr; ++r) {
+      int rc = launch_diag_axpy<float>(X + r * nlm, R + r * nlm, H.inv_diag_hp.get<float>(), nlm, P->stream);
+      if (rc) return rc;
+    }
+    return CR_OK;
+  }
+  PixLevel& lev = H.pix[h - 1];
+  const Grid& g = *lev.grid;
+  float* m1 = reinterpret_cast<float*>(H.map_work);
+  float* m2 = reinterpret_cast<float*>(H.map_work2);
+  int rc = tc_begin(P, g, L, true, false);
+  if (!rc) rc = tc_synth_stage(P, g, L, R, nr, nullptr);
+  for (int r = 0; r < nr && !rc; ++r) {
+    if ((rc = tc_ring(P, g, L, r, 0, nullptr, m1))) break;
+    {
+      const double bytes = 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float);
+      TimerScope ts(P->timing, P->stream, "pixel_smoother", bytes);
+      if ((rc = apply_smoother<float>(P, lev, m1, m2))) break;
+    }
+    rc = tc_ring(P, g, L, r, 1, m2, nullptr);
+  }
+  if (rc) return rc;
+  TcTail t;
+  t.dl_out = ops_of(P).ops[h].act.get<float>();
+  t.accumulate = 1;
+  t.out = X;
+  return tc_adjoint_tail(P, g, L, nr, t);
+}
+
+static int cycle_tc(cr_plan* P, int h, int nr, bool x_zero) {
+  Hierarchy& H = *P->hier;
+  Hierarchy::TcWork& w = H.tcw[h];
+  const int L = lmax_of(P, h);
+  const int64_t nlm = n_lm(L);
+  int rc;
+  if (h == H.H + 1) {
+    TimerScope ts(P->timing, P->stream, "bottom_solve");
+    for (int r = 0; r < nr; ++r)
+      if ((rc = bottom_solve<float>(P, H, w.b + r * nlm, w.x + r * nlm))) return rc;
+    return CR_OK;
+  }
+  const int LH = lmax_of(P, h + 1);
+  const int64_t nlmH = n_lm(LH);
+  Hierarchy::TcWork& wH = H.tcw[h + 1];
+  if (x_zero) {
+    CR_CUDA(cudaMemsetAsync(w.x, 0, nr * nlm * sizeof(float2), P->stream));
+    if ((rc = smooth_add_tc(P, h, nr, w.x, w.b))) return rc;
+  } else {
+    if ((rc = residual_tc(P, h, nr, w.x, w.b, w.r))) return rc;
+    if ((rc = smooth_add_tc(P, h, nr, w.x, w.r))) return rc;
+  }
+  if ((rc = residual_tc(P, h, nr, w.x, w.b, w.r))) return rc;
+  LevelOps& o = ops_of(P).ops[h];
+  for (int r = 0; r < nr; ++r)
+    if ((rc = launch_restrict<float>(w.r + r * nlm, L, wH.b + r * nlmH, LH, o.ratio.get<float>(), P->stream)))
+      return rc;
+  const int nrec = (h == 0) ? H.n_rec_top : H.pix[h - 1].n_rec;
+  for (int i = 0; i < nrec; ++i)
+    if ((rc = cycle_tc(P, h + 1, nr, i == 0))) return rc;
+  for (int r = 0; r < nr; ++r)
+    if ((rc = launch_prolong_add<float>(w.x + r * nlm, L, wH.x + r * nlmH, LH, o.ratio.get<float>(), P->stream)))
+      return rc;
+  if ((rc = residual_tc(P, h, nr, w.x, w.b, w.r))) return rc;
+  return smooth_add_tc(P, h, nr, w.x, w.r);
+}
+
 template <typename T>
 int level_apply(cr_plan* P, int h, const void* x, void* y);
 
@@ -452,6 +564,11 @@ void free_hierarchy(cr_plan* P) {
   H.inv_diag_hp.release();
   for (int i = 0; i < 5; ++i)
     if (H.krylov[i]) cudaFree(H.krylov[i]);
+  for (auto& w : H.tcw) {
+    void* q[] = {w.x, w.b, w.r};
+    for (void* p : q)
+      if (p) cudaFree(p);
+  }
   void* ptrs[] = {H.d_Ainv, H.d_Abottom, H.d_dof_lm, H.map_work, H.map_work2, H.d_dot, P->hier_tile_work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -627,6 +744,93 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
   return CR_OK;
 }
 
+// tensor-core buffers sized for every grid the batched cycle visits, so
+// that nothing is allocated once a capture has begun
+static int tc_prepare_all(cr_plan* P) {
+  Hierarchy& H = *P->hier;
+  int rc = ensure_tc_work(P);
+  if (!rc) rc = tc_begin(P, P->obs, P->lmax, true, true);
+  for (int h = 1; h <= H.H && !rc; ++h) {
+    const float* pix = nullptr;
+    const Grid& g = noise_grid<float>(P, h, &pix);
+    rc = tc_begin(P, g, H.pix[h - 1].lmax_h, true, false);
+    if (!rc) rc = tc_begin(P, *H.pix[h - 1].grid, H.pix[h - 1].lmax_h, true, false);
+  }
+  return rc;
+}
+
+// Batched mixed-precision CR-Solve: the stationary refinement of solve() for
+// nrhs right-hand sides, 16 at a time -- FP64 residual r = b - A x per
+// right-hand side, then one batched FP32 cycle (cycle_tc) of the group on
+// the FP32 residuals, x += c.  Without `fixed` a group stops when every
+// right-hand side meets r^T S^-1 r < eps b^T S^-1 b.
+int solve_tc(cr_plan* P, void* x, const void* b, int nrhs, double eps, int max_cycles, bool fixed, int* cycles_out,
+             double* relres_out, double* history) {
+  Hierarchy& H = *P->hier;
+  const int L = P->lmax;
+  const int64_t nlm = n_lm(L);
+  int rc = CR_OK;
+  if (!P->capturing && (rc = tc_prepare_all(P))) return rc;
+  if ((int)H.tcw.size() != H.H + 2 || !P->d_tc_status)
+    return fail(CR_ESTATE, "solve: batched cycle buffers missing (run the solve once outside a capture)");
+  CR_CUDA(cudaMemsetAsync(P->d_tc_status, 0, sizeof(int), P->stream));
+  Hierarchy::TcWork& w0 = H.tcw[0];
+  void* r64 = H.work[0].r;
+  bool capped = false;
+  for (int r0 = 0; r0 < nrhs; r0 += 16) {
+    const int nr = std::min(16, nrhs - r0);
+    double2* X = reinterpret_cast<double2*>(x) + r0 * nlm;
+    const double2* B = reinterpret_cast<const double2*>(b) + r0 * nlm;
+    std::vector<double> bsb(nr, 1.0), rel(nr, 1.0);
+    if (!P->capturing)
+      for (int j = 0; j < nr; ++j)
+        if ((rc = weighted_norm2(P, B + j * nlm, &bsb[j]))) return rc;
+    CR_CUDA(cudaMemsetAsync(X, 0, nr * nlm * sizeof(double2), P->stream));
+    for (int j = 0; j < nr; ++j)
+      if ((rc = launch_convert_d2f((const double*)(B + j * nlm), (float*)(w0.b + j * nlm), 2 * nlm, P->stream)))
+        return rc;
+    int k;
+    bool done = false;
+    for (k = 1; k <= max_cycles && !done; ++k) {
+      if ((rc = cycle_tc(P, 0, nr, true))) return rc;
+      for (int j = 0; j < nr; ++j)
+        if ((rc = launch_add_f2d((double*)(X + j * nlm), (const float*)(w0.x + j * nlm), 2 * nlm, P->stream)))
+          return rc;
+      if (fixed && k == max_cycles) {
+        if (history)
+          for (int j = 0; j < nr; ++j) history[(int64_t)(r0 + j) * max_cycles + k - 1] = std::nan("");
+        break;
+      }
+      bool all = true;
+      for (int j = 0; j < nr; ++j) {
+        {
+          TimerScope ts(P->timing, P->stream, "outer_residual");
+          if ((rc = residual<double>(P, 0, X + j * nlm, B + j * nlm, r64))) return rc;
+        }
+        if (!P->capturing) {
+          double rsr = 0.0;
+          if ((rc = weighted_norm2(P, r64, &rsr))) return rc;
+          rel[j] = bsb[j] > 0.0 ? std::sqrt(std::max(rsr, 0.0) / bsb[j]) : 0.0;
+          if (history) history[(int64_t)(r0 + j) * max_cycles + k - 1] = rel[j];
+          if (!std::isfinite(rel[j])) return fail(CR_ENONFINITE, "solve: non-finite residual");
+          if (!(rel[j] * rel[j] < eps)) all = false;
+        }
+        if ((rc = launch_convert_d2f((const double*)r64, (float*)(w0.b + j * nlm), 2 * nlm, P->stream))) return rc;
+      }
+      if (!fixed && !P->capturing && all) done = true;
+    }
+    const int kk = std::min(done ? k - 1 : k, max_cycles);
+    for (int j = 0; j < nr; ++j) {
+      if (cycles_out) cycles_out[r0 + j] = kk;
+      if (relres_out) relres_out[r0 + j] = fixed ? std::nan("") : rel[j];
+    }
+    if (!fixed && !done) capped = true;
+  }
+  if (!P->capturing && (rc = tc_end(P, "batched cycle: a tensor-core completion wait gave up"))) return rc;
+  if (capped) return fail(CR_EMAXITER, "solve: cycle cap reached before the tolerance");
+  return CR_OK;
+}
+
 template <typename T>
 int wcycle(cr_plan* P, void* x, const void* b) {
   return cycle<T>(P, 0, x, b, false, nullptr);
@@ -794,6 +998,13 @@ int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int ma
   }
   int rc = check_hier(plan, "cr_solve", true);
   if (rc) return rc;
+  if (mode & CR_TC_CYCLES) {
+    if ((mode & 3) != CR_MIXED || (mode & CR_PCG))
+      return fail(CR_EINVAL, "cr_solve: CR_TC_CYCLES is a stationary CR_MIXED solve");
+    if (max_cycles < 1 || !(eps >= 0.0) || nrhs < 0) return fail(CR_EINVAL, "cr_solve: eps / max_cycles / nrhs");
+    if (nrhs == 0) return CR_OK;
+    return solve_tc(plan, x, b, nrhs, eps, max_cycles, (mode & CR_FIXED) != 0, cycles_out, relres_out, history);
+  }
   if ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) return fail(CR_EINVAL, "cr_solve: mode precision must be CR_F64 or CR_MIXED");
   if (max_cycles < 1 || !(eps >= 0.0)) return fail(CR_EINVAL, "cr_solve: eps / max_cycles");
   const int64_t nlm = n_lm(plan->lmax);

@@ -65,3 +65,61 @@ def _run(dev, stream):
     torch.cuda.synchronize()
     assert torch.allclose(xs[0], 2.0 * refs[0], rtol=1e-9, atol=0)
     batch.close()
+
+
+def test_tensor_core_cycles_converge_to_exact_answers():
+    """CR_MIXED | CR_TC_CYCLES: 18 right-hand sides (a group of 16 and one of
+    2) whose FP32 cycles run together with every Legendre stage on the
+    tensor cores; the FP64 outer residual drives each to its exact answer
+    x_true of b = A x_true, and the residual history shrinks at a rate close
+    to the per-right-hand-side FP32 cycles."""
+    dev = cuda_device()
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        plan, cl = make_plan(64, 191, 120.0, stream, dev)
+        nr = 18
+        xt = torch.from_numpy(np.stack([synthetic.draw_prior(cl, index=200 + j) for j in range(nr)])).to(dev)
+        b = torch.empty_like(xt)
+        plan.apply_A(xt, b)
+        x = torch.zeros_like(b)
+        cyc, rel, hist = plan.solve(b, x, eps=1e-20, max_cycles=40, mode=binding.CR_MIXED | binding.CR_TC_CYCLES)
+        assert all(c <= 40 for c in cyc) and max(rel) < 1e-10
+        for j in range(nr):
+            m = torch.empty(12 * 64 * 64, dtype=torch.float64, device=dev)
+            plan.sht_synth(x[j] - xt[j], m)
+            assert float(m.abs().max()) < 1e-4
+        # convergence per cycle against the per-right-hand-side FP32 cycles
+        xr = torch.zeros_like(b[0])
+        _, _, href = plan.solve(b[0], xr, eps=0.0, max_cycles=4, mode=binding.CR_MIXED | binding.CR_FIXED,
+                                check=False)[:3]
+        h_tc = hist[0][:3]
+        assert h_tc[2] < 3.0 * href[0][2] + 1e-12, (h_tc, href[0][:3])
+
+
+def test_tensor_core_cycles_in_a_graph_match_direct():
+    dev = cuda_device()
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        specs = [(64, 191, 120.0, 17), (32, 95, 240.0, 3)]
+        plans, xs, bs, refs = [], [], [], []
+        cycles, mode = 3, binding.CR_MIXED | binding.CR_TC_CYCLES
+        for k, (nside, lmax, fwhm, nr) in enumerate(specs):
+            plan, cl = make_plan(nside, lmax, fwhm, stream, dev)
+            xt = torch.from_numpy(np.stack([synthetic.draw_prior(cl, index=300 + 20 * k + j)
+                                            for j in range(nr)])).to(dev)
+            b = torch.empty_like(xt)
+            plan.apply_A(xt, b)
+            r = torch.zeros_like(b)
+            plan.solve(b, r, eps=0.0, max_cycles=cycles, mode=mode | binding.CR_FIXED, check=False)
+            plans.append(plan)
+            bs.append(b)
+            xs.append(torch.zeros_like(b))
+            refs.append(r)
+        batch = binding.Batch(plans, xs, bs, cycles, mode)
+        for x in xs:
+            x.zero_()
+        batch.run()
+        torch.cuda.synchronize()
+        for x, r in zip(xs, refs):
+            assert torch.equal(x, r)
+        batch.close()
