@@ -357,7 +357,7 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
         for k, name in enumerate(["nside1024_lmax2047", "nside512_lmax1023"]):
             cfg, cl, bl, ninv = synthetic.problem_inputs(name)
             plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
-                                stream=st, levels="default")
+                                stream=st, levels="default", autotune=True)
             xt = torch.from_numpy(np.stack([synthetic.draw_prior(cl, index=100 * (k + 1) + j)
                                             for j in range(nrhs)])).to(dev)
             b = torch.empty_like(xt)
@@ -551,6 +551,13 @@ def main():
     precompute_split = {"structure_s": t1 - t0, "first_numeric_s": t2 - t1,
                         "cl_update_s": time.perf_counter() - t2}
     del ninv_d
+    # Legendre autotuner: ring-block choice per grid, band limit, precision
+    t3 = time.perf_counter()
+    table = plan.autotune()
+    autotune = {"s": time.perf_counter() - t3,
+                "observation_grid": {"%s_%s" % (t["precision"], t["stage"]): t["pairs_per_thread"]
+                                     for t in table if t["nring"] == 4 * nside - 1 and t["lmax"] == lmax},
+                "entries": len(table)}
     x_true = torch.from_numpy(synthetic.draw_prior(cl, index=rank)).to(dev)
     b = torch.empty_like(x_true)
     plan.apply_A(x_true, b)  # b = A x_true (FP64), the paper's synthetic protocol
@@ -705,6 +712,7 @@ def main():
         "sht_pairs_per_s": {"f64": pairs_f64, "f32": pairs_f32},
         "precompute_s": precompute_s,
         "precompute_split": precompute_split,
+        "autotune": autotune,
         "e2e": {"value": e2e_s, "unit": "s/realization", "h2d_bytes_per_step": int(bh.numel() * 16),
                 "d2h_bytes_per_step": int(xh.numel() * 16)},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},

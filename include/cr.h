@@ -180,6 +180,8 @@ typedef struct cr_params {
    * it in later with cr_load or cr_plan_update_cl.  Until then the solver
    * entry points return CR_ESTATE.  0 = run everything at creation. */
   int defer_precompute;
+  /* autotune: 1 = run cr_plan_autotune at the end of creation. */
+  int autotune;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */
@@ -192,6 +194,28 @@ const char* cr_last_error(void);
  * only on success.  Errors: CR_EINVAL, CR_ENOMEM, CR_ECUDA.
  */
 int cr_plan_create(cr_plan** out, const cr_params* p);
+
+/*
+ * Autotuner of the Legendre kernels (Section 2.1 transforms): times the
+ * FP32 and FP64 synthesis and adjoint Legendre stages with 2, 4 and 8 ring
+ * pairs per thread (the ring block of one CTA: 256, 512 or 1024 pairs of one
+ * m) on every grid and band limit the plan transforms on, and keeps the
+ * fastest.  Choices are cached for the process per (grid shape, band limit,
+ * precision, stage) and used by every plan with those shapes; shapes already
+ * in the cache are not re-timed.  Untuned shapes use 4.  *nentries (may be
+ * NULL) receives the size of the cache.  Synchronous; a few seconds at
+ * Nside 2048.  cr_tune_entry reads cache entry i (0 <= i < size): grid ring
+ * and pixel counts, band limit, precision in bytes (4 or 8), stage (0
+ * synthesis, 1 adjoint), the chosen pairs per thread and the measured ms of
+ * the three choices (HOST [3]); any output may be NULL.  Errors: CR_EINVAL,
+ * CR_ECUDA.
+ */
+int cr_plan_autotune(cr_plan* plan, int* nentries);
+int cr_tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* precision_bytes, int* stage, int* rp,
+                  double* ms);
+/* Pin the choice for one (grid shape, band limit, precision, stage): rp 2,
+ * 4 or 8.  Errors: CR_EINVAL. */
+int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp);
 
 /*
  * Replace the prior C_l of a plan (HOST [lmax + 1], finite, >= 0) and redo

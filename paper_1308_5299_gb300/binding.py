@@ -66,6 +66,7 @@ class cr_params(ctypes.Structure):
         ("gl_downgrade", ctypes.c_int),
         ("fp64_df", ctypes.c_int),
         ("defer_precompute", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -78,6 +79,12 @@ _SIGS = {
     "cr_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "cr_plan_update_cl": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_save": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
+    "cr_plan_autotune": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cr_tune_set": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+                    ctypes.c_int),
+    "cr_tune_entry": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_load": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
     "cr_plan_sizes": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -184,6 +191,32 @@ def launch_count():
     return int(lib().cr_launch_count())
 
 
+def tune_table():
+    """The Legendre autotuner's cached choices: one dict per (grid, band
+    limit, precision, stage) with the chosen pairs per thread and the
+    measured ms of 2, 4 and 8 pairs per thread."""
+    out = []
+    i = 0
+    while True:
+        nring, lmax, nb, stage, rp = (ctypes.c_int() for _ in range(5))
+        npix = ctypes.c_int64()
+        ms = (ctypes.c_double * 3)()
+        if lib().cr_tune_entry(i, ctypes.byref(nring), ctypes.byref(npix), ctypes.byref(lmax), ctypes.byref(nb),
+                               ctypes.byref(stage), ctypes.byref(rp), ms) != 0:
+            return out
+        out.append(dict(nring=nring.value, npix=npix.value, lmax=lmax.value, precision="f64" if nb.value == 8 else "f32",
+                        stage="synthesis" if stage.value == 0 else "adjoint", pairs_per_thread=rp.value,
+                        ms={2: ms[0], 4: ms[1], 8: ms[2]}))
+        i += 1
+
+
+def tune_set(nring, npix, lmax, precision, stage, pairs_per_thread):
+    """Pin the Legendre ring-block choice for one shape (``cr_tune_set``):
+    precision "f32"/"f64", stage "synthesis"/"adjoint"."""
+    _check(lib().cr_tune_set(int(nring), int(npix), int(lmax), 8 if precision == "f64" else 4,
+                             0 if stage == "synthesis" else 1, int(pairs_per_thread)))
+
+
 def _tc_code(code, tensor_cores, what):
     if not tensor_cores:
         return code
@@ -210,7 +243,7 @@ class Plan:
 
     def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
                  lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0,
-                 gl_downgrade=0, fp64_df=False, defer_precompute=False):
+                 gl_downgrade=0, fp64_df=False, defer_precompute=False, autotune=False):
         """levels: None (transforms and A only), "default" (the library's level
         table), or a list of dicts with nside_h, lmax_h, n_rec and fl
         (cumulative filter, length lmax+1).  gl_downgrade: 0 auto, 1 every
@@ -266,6 +299,7 @@ class Plan:
         p.gl_downgrade = int(gl_downgrade)
         p.fp64_df = int(bool(fp64_df))
         p.defer_precompute = int(bool(defer_precompute))
+        p.autotune = int(bool(autotune))
         if ridge_alpha is not None:
             ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
             self._keep.append(ra)
@@ -276,6 +310,13 @@ class Plan:
         self.lmax = int(lmax)
         self._keep = []
         self.npix = self.sizes()["npix"]
+
+    def autotune(self):
+        """Time the Legendre kernels' ring-block choices on this plan's grids
+        and keep the fastest (``cr_plan_autotune``); returns tune_table()."""
+        n = ctypes.c_int()
+        _check(lib().cr_plan_autotune(self._h, ctypes.byref(n)))
+        return tune_table()
 
     def update_cl(self, cl):
         """Replace the prior C_l and redo the C_l-dependent precompute

@@ -32,6 +32,7 @@ struct LegArgs {
   int npairs = 0, nring = 0;
   typename Tr<T>::C* partial = nullptr;    // adjoint: [nblk][n_lm(L)]
   const T* ringval = nullptr;              // SQ variant: per-ring value
+  int rp_synth = 4, rp_adj = 4;            // ring pairs per thread (2, 4, 8) of the two stages
 };
 
 template <typename T>

@@ -27,8 +27,10 @@
 // start test), so the region below the turning point where the functions are
 // negligible costs nothing.
 //
-// Work decomposition: one CTA per (m, block of LEG_NT*LEG_RP ring pairs);
-// each warp owns 32*LEG_RP consecutive pairs (lane + 32 j), so its pairs'
+// Work decomposition: one CTA per (m, block of LEG_NT*RP ring pairs), RP
+// (2, 4 or 8 pairs per thread: the ring-block size) chosen per grid, band
+// limit and precision by the plan's autotuner (default 4);
+// each warp owns 32*RP consecutive pairs (lane + 32 j), so its pairs'
 // start points are close.  The a_lm of the CTA's m (synthesis) and the
 // recurrence coefficients are staged through shared memory in chunks of
 // LEG_CH l-values from the CTA's earliest start.  The adjoint reduces over
@@ -41,7 +43,8 @@
 namespace cr {
 
 constexpr int LEG_NT = 128;
-constexpr int LEG_RP = 4;
+constexpr int LEG_RP = 4;      // default ring pairs per thread
+constexpr int LEG_RP_MIN = 2;  // smallest choice of the autotuner
 constexpr int LEG_CH = 256;
 constexpr int LEG_NW = LEG_NT / 32;
 
@@ -71,26 +74,27 @@ __device__ __forceinline__ T rstep(T c, T c2, T zw, T& s1, T& s2) {
 }
 
 // Ring pairs are split into a polar range [0, npolar) and an equatorial
-// range [npolar, npairs); each CTA covers LEG_NT*LEG_RP pairs of one range.
+// range [npolar, npairs); each CTA covers LEG_NT*RP pairs of one range.
 // Block row yb (= blockIdx.y + the launch's row offset) < nbp is polar.
+template <int RP>
 __device__ __forceinline__ int pair_of(int npolar, int nbp, int yb, int warp, int lane, int j) {
-  const int base = yb < nbp ? yb * (LEG_NT * LEG_RP) : npolar + (yb - nbp) * (LEG_NT * LEG_RP);
-  return base + warp * (32 * LEG_RP) + j * 32 + lane;
+  const int base = yb < nbp ? yb * (LEG_NT * RP) : npolar + (yb - nbp) * (LEG_NT * RP);
+  return base + warp * (32 * RP) + j * 32 + lane;
 }
 
 // Per-thread pair setup shared by both kernels: start point, state, and the
 // warp's earliest / latest start over its live pairs (a pair is live when it
 // starts at or below L).  Returns false when the warp has no live pair.
-template <typename T, bool POLAR>
+template <typename T, bool POLAR, int RP>
 __device__ __forceinline__ bool load_pairs(const LegArgs<T>& a, int m, int yb, int nbp, int warp, int lane,
-                                           int p[LEG_RP], int ls[LEG_RP], T P1[LEG_RP], T P2[LEG_RP],
-                                           T zz[LEG_RP], int* wmin, int* wmax) {
+                                           int p[RP], int ls[RP], T P1[RP], T P2[RP], T zz[RP], int* wmin,
+                                           int* wmax) {
   using C = typename Tr<T>::C;
   const int pend = POLAR ? a.npolar : a.npairs;
   int lo = a.L + 1, hi = m;
 #pragma unroll
-  for (int j = 0; j < LEG_RP; ++j) {
-    p[j] = pair_of(a.npolar, nbp, yb, warp, lane, j);
+  for (int j = 0; j < RP; ++j) {
+    p[j] = pair_of<RP>(a.npolar, nbp, yb, warp, lane, j);
     ls[j] = a.L + 1;
     P1[j] = 0;
     P2[j] = 0;
@@ -114,7 +118,7 @@ __device__ __forceinline__ bool load_pairs(const LegArgs<T>& a, int m, int yb, i
   return *wmin <= a.L;
 }
 
-template <typename T, bool POLAR>
+template <typename T, bool POLAR, int RP>
 __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
   const int m = blockIdx.x;
@@ -126,17 +130,17 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
   __shared__ T sc2[LEG_CH];
   __shared__ int s_min;
 
-  T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
-  int ls[LEG_RP], p[LEG_RP];
-  C accE[LEG_RP], accO[LEG_RP];
+  T P1[RP], P2[RP], zz[RP];
+  int ls[RP], p[RP];
+  C accE[RP], accO[RP];
 #pragma unroll
-  for (int j = 0; j < LEG_RP; ++j) {
+  for (int j = 0; j < RP; ++j) {
     accE[j] = mk((T)0, (T)0);
     accO[j] = mk((T)0, (T)0);
   }
   const int yb = (int)blockIdx.y + yoff;
   int wmin, wmax;
-  const bool live = load_pairs<T, POLAR>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   if (tid == 0) s_min = L + 1;
   __syncthreads();
   if (lane == 0 && live) atomicMin(&s_min, wmin);
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
           const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
           const C a0 = sa[i8 + u], a1 = sa[i8 + u + 1];
 #pragma unroll
-          for (int j = 0; j < LEG_RP; ++j) {
+          for (int j = 0; j < RP; ++j) {
             const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
             const T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
             accE[j].x = fma(q0, a0.x, accE[j].x);
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
           const T d0 = POLAR ? sc2[i8 + u] : (T)0;
           const C a0 = sa[i8 + u];
 #pragma unroll
-          for (int j = 0; j < LEG_RP; ++j) {
+          for (int j = 0; j < RP; ++j) {
             if (l >= ls[j]) {
               const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
               if (u & 1) {
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
   }
   const int pend = POLAR ? a.npolar : a.npairs;
 #pragma unroll
-  for (int j = 0; j < LEG_RP; ++j) {
+  for (int j = 0; j < RP; ++j) {
     if (p[j] < pend) {
       const int rn = p[j], rs = a.nring - 1 - p[j];
       a.phase[(int64_t)rn * a.ldp + m] = cadd(accE[j], accO[j]);
@@ -266,7 +270,7 @@ __device__ __forceinline__ void warp_reduce8(C v[8]) {
 // SQ: accumulate P~^2 times a per-ring value (ringval) instead of P~ times
 // the ring's phase G_m: sum_k P~_lm(z_k)^2 v_k, used for the diagonal of
 // Y^T N^-1 Y (the Delta m = 0 term of the ring formula).
-template <typename T, bool POLAR, bool SQ = false>
+template <typename T, bool POLAR, int RP, bool SQ = false>
 __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
   const int m = blockIdx.x;
@@ -279,15 +283,15 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   __shared__ C red[2][LEG_NW][8];
   __shared__ int s_min;
 
-  T P1[LEG_RP], P2[LEG_RP], zz[LEG_RP];
-  int ls[LEG_RP], p[LEG_RP];
-  C GE[LEG_RP], GO[LEG_RP];
+  T P1[RP], P2[RP], zz[RP];
+  int ls[RP], p[RP];
+  C GE[RP], GO[RP];
   const int yb = (int)blockIdx.y + yoff;
   int wmin, wmax;
-  const bool live = load_pairs<T, POLAR>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   const int pend = POLAR ? a.npolar : a.npairs;
 #pragma unroll
-  for (int j = 0; j < LEG_RP; ++j) {
+  for (int j = 0; j < RP; ++j) {
     GE[j] = mk((T)0, (T)0);
     GO[j] = mk((T)0, (T)0);
     if (p[j] < pend && ls[j] <= L) {
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
             const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
             const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
 #pragma unroll
-            for (int j = 0; j < LEG_RP; ++j) {
+            for (int j = 0; j < RP; ++j) {
               T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
               T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
               if (SQ) {
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
               const T c0 = sc[i8 + u];
               const T d0 = POLAR ? sc2[i8 + u] : (T)0;
 #pragma unroll
-              for (int j = 0; j < LEG_RP; ++j) {
+              for (int j = 0; j < RP; ++j) {
                 if (l >= ls[j]) {
                   T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
                   if (SQ) q0 *= q0;
@@ -426,9 +430,24 @@ __global__ void leg_finalize_kernel(FinalizeArgs<T> a) {
   }
 }
 
-static inline void pair_blocks(int npolar, int npairs, int* nbp, int* nbe) {
-  *nbp = (npolar + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP);
-  *nbe = (npairs - npolar + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP);
+static inline void pair_blocks(int npolar, int npairs, int rp, int* nbp, int* nbe) {
+  *nbp = (npolar + LEG_NT * rp - 1) / (LEG_NT * rp);
+  *nbe = (npairs - npolar + LEG_NT * rp - 1) / (LEG_NT * rp);
+}
+
+// ring pairs per thread of a launch: 2, 4 or 8 (other values: the default)
+static inline int legal_rp(int rp) { return (rp == 2 || rp == 4 || rp == 8) ? rp : LEG_RP; }
+
+template <typename T, int RP>
+static void synth_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
+  if (nbp) { leg_synth_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { leg_synth_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+}
+
+template <typename T, int RP>
+static void adjoint_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
+  if (nbp) { leg_adjoint_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { leg_adjoint_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
 }
 
 template <typename T>
@@ -437,9 +456,11 @@ int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st) {
   if constexpr (sizeof(T) == 8)
     if (a.df) return launch_leg_synth_df(a, st);
   int nbp, nbe;
-  pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
-  if (nbp) { leg_synth_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { leg_synth_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  const int rp = legal_rp(a.rp_synth);
+  pair_blocks(a.npolar, a.npairs, rp, &nbp, &nbe);
+  if (rp == 2) synth_launch<T, 2>(a, nbp, nbe, st);
+  else if (rp == 8) synth_launch<T, 8>(a, nbp, nbe, st);
+  else synth_launch<T, 4>(a, nbp, nbe, st);
   CR_CHECK_LAUNCH("leg_synth_kernel");
   return CR_OK;
 }
@@ -457,9 +478,11 @@ int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream
     }
   }
   if (!done) {
-    pair_blocks(a.npolar, a.npairs, &nbp, &nbe);
-    if (nbp) { leg_adjoint_kernel<T, true><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_adjoint_kernel<T, false><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    const int rp = legal_rp(a.rp_adj);
+    pair_blocks(a.npolar, a.npairs, rp, &nbp, &nbe);
+    if (rp == 2) adjoint_launch<T, 2>(a, nbp, nbe, st);
+    else if (rp == 8) adjoint_launch<T, 8>(a, nbp, nbe, st);
+    else adjoint_launch<T, 4>(a, nbp, nbe, st);
     CR_CHECK_LAUNCH("leg_adjoint_kernel");
   }
   FinalizeArgs<T> ff = f;
@@ -497,8 +520,8 @@ int launch_leg_diag(cr_plan* P, const double* ringval, double2* out) {
   a.ringval = ringval;
   a.partial = reinterpret_cast<double2*>(P->ws.partial);
   int nbp, nbe;
-  pair_blocks(0, a.npairs, &nbp, &nbe);
-  { leg_adjoint_kernel<double, false, true><<<dim3(a.L + 1, nbe), LEG_NT, 0, P->stream>>>(a, 0, 0); count_launch(); }
+  pair_blocks(0, a.npairs, LEG_RP, &nbp, &nbe);
+  { leg_adjoint_kernel<double, false, LEG_RP, true><<<dim3(a.L + 1, nbe), LEG_NT, 0, P->stream>>>(a, 0, 0); count_launch(); }
   CR_CHECK_LAUNCH("leg_adjoint_kernel<SQ>");
   FinalizeArgs<double> ff;
   ff.partial = a.partial;
@@ -584,9 +607,10 @@ int build_start_tables(cr_plan* P, Grid& g) {
 }
 
 // upper bound on the partial rows of the adjoint: the polar and equatorial
-// ranges of LEG_NT * LEG_RP pairs, or the double-float kernels' blocks
+// ranges of LEG_NT * RP pairs for the smallest RP, or the double-float
+// kernels' blocks
 int leg_partial_blocks(int npairs) {
-  return std::max((npairs + LEG_NT * LEG_RP - 1) / (LEG_NT * LEG_RP) + 1, df_pair_blocks(npairs));
+  return std::max((npairs + LEG_NT * LEG_RP_MIN - 1) / (LEG_NT * LEG_RP_MIN) + 1, df_pair_blocks(npairs));
 }
 
 template int launch_leg_synth<double>(const LegArgs<double>&, cudaStream_t);

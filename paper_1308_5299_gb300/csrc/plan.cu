@@ -1,5 +1,7 @@
 // Plan construction and the C ABI entry points for transforms and A.
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -335,9 +337,40 @@ __global__ void ninv32_kernel(const double* in, float* out, int64_t n) {
 
 // ---- transform drivers ------------------------------------------------------
 
+// Choices of the Legendre autotuner: ring pairs per thread (2, 4 or 8, the
+// ring-block size of one CTA) per (grid shape, band limit, precision,
+// stage 0 synthesis / 1 adjoint), kept for the process and shared by every
+// plan with the same shapes; 4 where nothing was tuned.
+struct TuneKey {
+  int nring;
+  int64_t npix;
+  int L, bytes, stage;
+  bool operator<(const TuneKey& o) const {
+    if (nring != o.nring) return nring < o.nring;
+    if (npix != o.npix) return npix < o.npix;
+    if (L != o.L) return L < o.L;
+    if (bytes != o.bytes) return bytes < o.bytes;
+    return stage < o.stage;
+  }
+};
+struct TuneVal {
+  int rp;
+  double ms[3];  // measured ms for 2, 4, 8 pairs per thread
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune;
+
+static int tuned_rp(const Grid& g, int L, int bytes, int stage) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey{g.nring, g.npix, L, bytes, stage});
+  return it == g_tune.end() ? 4 : it->second.rp;
+}
+
 template <typename T>
 static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
   LegArgs<T> a;
+  a.rp_synth = tuned_rp(g, L, (int)sizeof(T), 0);
+  a.rp_adj = tuned_rp(g, L, (int)sizeof(T), 1);
   a.ldp = L + 1;
   a.L = L;
   a.Lc = P->Lcoef;
@@ -505,6 +538,109 @@ static const Grid* grid_of(cr_plan* P, int grid, int* L) {
   return nullptr;
 }
 
+// Time one Legendre stage of grid g at band limit L for 2, 4 and 8 ring
+// pairs per thread (one untimed launch, then `reps` timed with CUDA events on
+// the plan's stream; native kernels, zero coefficients -- the work does not
+// depend on the data) and record the fastest.
+template <typename T>
+static int tune_stage(cr_plan* P, const Grid& g, int L, int stage, int reps) {
+  using C = typename Tr<T>::C;
+  int rc = ensure_workspace(P, g, L);
+  if (rc) return rc;
+  C* alm = nullptr;
+  CR_CUDA(cudaMalloc(&alm, n_lm(L) * sizeof(C)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemsetAsync(alm, 0, n_lm(L) * sizeof(C), P->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) rc = cuda_fail(e, "autotune setup");
+  TuneVal v{4, {0.0, 0.0, 0.0}};
+  const int rps[3] = {2, 4, 8};
+  for (int i = 0; i < 3 && !rc; ++i) {
+    LegArgs<T> a = leg_args<T>(P, g, L);
+    a.df = 0;
+    a.alm = alm;
+    a.rp_synth = a.rp_adj = rps[i];
+    FinalizeArgs<T> f;
+    f.out = alm;
+    auto run = [&]() { return stage == 0 ? launch_leg_synth<T>(a, P->stream) : launch_leg_adjoint<T>(a, f, P->stream); };
+    if ((rc = run())) break;
+    if ((e = cudaEventRecord(e0, P->stream)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    for (int k = 0; k < reps && !rc; ++k) rc = run();
+    if (!rc && (e = cudaEventRecord(e1, P->stream)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    if (!rc && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    float ms = 0.f;
+    if (!rc && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    v.ms[i] = ms / reps;
+  }
+  if (!rc) {
+    int best = 1;
+    for (int i = 0; i < 3; ++i)
+      if (v.ms[i] < v.ms[best]) best = i;
+    v.rp = rps[best];
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(alm);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[TuneKey{g.nring, g.npix, L, (int)sizeof(T), stage}] = v;
+  return CR_OK;
+}
+
+// every (grid, band limit) the plan transforms on: the observation grid at
+// lmax and, with levels, each pixel level's grid and inverse-noise grid at
+// lmax_h; both precisions, both stages
+int autotune_plan(cr_plan* P, int reps) {
+  std::vector<std::pair<const Grid*, int>> todo{{&P->obs, P->lmax}};
+  if (P->hier)
+    for (const PixLevel& lev : P->hier->pix) {
+      todo.push_back({lev.grid, lev.lmax_h});
+      todo.push_back({lev.gl ? lev.gl : &P->obs, lev.lmax_h});
+    }
+  for (auto& t : todo) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      if (g_tune.count(TuneKey{t.first->nring, t.first->npix, t.second, 8, 1})) continue;
+    }
+    for (int stage = 0; stage < 2; ++stage) {
+      int rc = tune_stage<float>(P, *t.first, t.second, stage, reps);
+      if (!rc) rc = tune_stage<double>(P, *t.first, t.second, stage, reps);
+      if (rc) return rc;
+    }
+  }
+  return CR_OK;
+}
+
+int tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* bytes, int* stage, int* rp, double* ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (i < 0 || i >= (int)g_tune.size()) return fail(CR_EINVAL, "cr_tune_entry: index out of range");
+  auto it = g_tune.begin();
+  std::advance(it, i);
+  if (nring) *nring = it->first.nring;
+  if (npix) *npix = it->first.npix;
+  if (lmax) *lmax = it->first.L;
+  if (bytes) *bytes = it->first.bytes;
+  if (stage) *stage = it->first.stage;
+  if (rp) *rp = it->second.rp;
+  if (ms)
+    for (int k = 0; k < 3; ++k) ms[k] = it->second.ms[k];
+  return CR_OK;
+}
+
+int tune_set(int nring, int64_t npix, int lmax, int bytes, int stage, int rp) {
+  if ((rp != 2 && rp != 4 && rp != 8) || (bytes != 4 && bytes != 8) || (stage != 0 && stage != 1) || lmax < 0)
+    return fail(CR_EINVAL, "cr_tune_set: bad choice");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[TuneKey{nring, npix, lmax, bytes, stage}] = TuneVal{rp, {0.0, 0.0, 0.0}};
+  return CR_OK;
+}
+
+int tune_count() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
+}
+
 }  // namespace cr
 
 using namespace cr;
@@ -613,6 +749,7 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
       else rc = build_hierarchy(P, p);
     }
   }
+  if (!rc && p->autotune) rc = autotune_plan(P, 3);
   if (rc) {
     plan_free(P);
     delete P;
@@ -620,6 +757,23 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   }
   *out = P;
   return CR_OK;
+}
+
+int cr_plan_autotune(cr_plan* plan, int* nentries) {
+  if (!plan) return fail(CR_EINVAL, "cr_plan_autotune: null plan");
+  CR_CUDA(cudaStreamSynchronize(plan->stream));
+  int rc = autotune_plan(plan, 3);
+  if (nentries) *nentries = tune_count();
+  return rc;
+}
+
+int cr_tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* precision_bytes, int* stage, int* rp,
+                  double* ms) {
+  return tune_entry(i, nring, npix, lmax, precision_bytes, stage, rp, ms);
+}
+
+int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp) {
+  return tune_set(nring, npix, lmax, precision_bytes, stage, rp);
 }
 
 int cr_plan_update_cl(cr_plan* plan, const double* cl) {

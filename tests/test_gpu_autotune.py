@@ -1,0 +1,59 @@
+"""The Legendre autotuner (ring pairs per thread 2, 4, 8 per grid, band
+limit, precision and stage): every choice computes the same transforms (FP64
+within 1e-10 of the oracle, FP32 within 1e-5), and the tuner records a
+measured time for each choice and keeps the fastest."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import cuda_device, rel_l2
+from oracle import geometry, sht
+from paper_1308_5299_gb300 import binding, synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("rp", [2, 4, 8])
+@pytest.mark.parametrize("nside,lmax", [(32, 95), (64, 191)])
+def test_every_ring_block_choice_matches_oracle(nside, lmax, rp):
+    dev = cuda_device()
+    g = geometry.healpix_grid(nside)
+    for prec in ("f32", "f64"):
+        for stage in ("synthesis", "adjoint"):
+            binding.tune_set(g["nring"], g["npix"], lmax, prec, stage, rp)
+    plan = binding.Plan(lmax, nside=nside)
+    a = synthetic.random_alm(lmax, seed=31)
+    mp = synthetic.random_map(g["npix"], seed=32)
+    ref_s, ref_a = sht.synth(a, lmax, g), sht.adjoint(mp, lmax, g)
+    for cdt, rdt, tol in ((torch.complex128, torch.float64, 1e-10), (torch.complex64, torch.float32, 1e-5)):
+        m = torch.empty(g["npix"], dtype=rdt, device=dev)
+        plan.sht_synth(torch.from_numpy(a).to(cdt).to(dev), m)
+        assert rel_l2(m.cpu().numpy().astype(np.float64), ref_s) < tol
+        out = torch.empty(sht.n_lm(lmax), dtype=cdt, device=dev)
+        plan.sht_adjoint(torch.from_numpy(mp).to(rdt).to(dev), out)
+        assert rel_l2(out.cpu().numpy().astype(np.complex128), ref_a) < tol
+
+
+def test_autotune_records_and_keeps_fastest():
+    dev = cuda_device()
+    nside, lmax = 128, 383
+    cl = synthetic.cl_spectrum(lmax, True)
+    bl = synthetic.gaussian_beam(lmax, 60.0)
+    ninv = torch.ones(12 * nside * nside, dtype=torch.float64, device=dev)
+    plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=ninv, levels="default", ridge_bisections=8)
+    table = plan.autotune()
+    g = geometry.healpix_grid(nside)
+    obs = [t for t in table if t["nring"] == g["nring"] and t["lmax"] == lmax]
+    assert len(obs) == 4
+    for t in obs:
+        assert all(v > 0 for v in t["ms"].values())
+        assert t["pairs_per_thread"] == min(t["ms"], key=t["ms"].get)
+    # levels' grids are tuned too
+    assert len({(t["nring"], t["lmax"]) for t in table}) > 1
+    # the tuned plan still solves to the exact answer
+    xt = torch.from_numpy(synthetic.draw_prior(cl, index=4)).to(dev)
+    b = torch.empty_like(xt)
+    plan.apply_A(xt, b)
+    x = torch.zeros_like(b)
+    plan.solve(b, x, eps=1e-20, max_cycles=40, mode=binding.CR_MIXED | binding.CR_PCG, check=False)
+    assert rel_l2(x.cpu().numpy(), xt.cpu().numpy()) < 1e-6
