@@ -35,8 +35,10 @@
 // recurrence coefficients are staged through shared memory in chunks of
 // LEG_CH l-values from the CTA's earliest start.  The adjoint reduces over
 // ring pairs with a warp-shuffle transpose reduction over 8 consecutive l
-// (each lane ends with one l), a fixed-order cross-warp sum, and one partial
-// row per ring block summed in a second, deterministic kernel.
+// (each lane ends with one l) into per-warp rows of shared memory, one
+// fixed-order cross-warp sum per chunk of LEG_CH l (a single barrier per
+// chunk), and one partial row per ring block summed in a second,
+// deterministic kernel.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -279,8 +281,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   const int warp = tid >> 5, lane = tid & 31;
   __shared__ T sc[LEG_CH];
   __shared__ T sc2[LEG_CH];
-  __shared__ C sacc[LEG_CH];
-  __shared__ C red[2][LEG_NW][8];
+  __shared__ C red[LEG_NW][LEG_CH];  // per-warp sums of the chunk's l
   __shared__ int s_min;
 
   T P1[RP], P2[RP], zz[RP];
@@ -319,7 +320,6 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~7) : L + 1;
   // rows before the block's earliest start are zero
   for (int l = m + tid; l < lbeg; l += LEG_NT) part[offa + (l - m)] = mk((T)0, (T)0);
-  int rb = 0;
 
   for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
     const int nl = min(LEG_CH, L - l0 + 1);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
       const int ng = min(8, nl - i8);
       if (!live || wmin >= lg + ng) {
         // no pair of this warp has started: its share of the sums is zero
-        if (lane < 8) red[rb][warp][lane] = mk((T)0, (T)0);
+        if (lane < 8) red[warp][i8 + lane] = mk((T)0, (T)0);
       } else {
         C acc[8];
 #pragma unroll
@@ -379,22 +379,18 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
           }
         }
         warp_reduce8(acc);
-        if ((lane & 3) == 0) red[rb][warp][lane >> 2] = acc[0];
+        if ((lane & 3) == 0) red[warp][i8 + (lane >> 2)] = acc[0];
       }
-      __syncthreads();
-      if (tid < 8) {
-        C s = red[rb][0][tid];
-#pragma unroll
-        for (int w = 1; w < LEG_NW; ++w) s = cadd(s, red[rb][w][tid]);
-        sacc[i8 + tid] = s;
-      }
-      rb ^= 1;
     }
+    // one barrier per chunk: the warps' sums in a fixed order
     __syncthreads();
     for (int i = tid; i < nl; i += LEG_NT) {
       const int l = l0 + i;
+      C sum = red[0][i];
+#pragma unroll
+      for (int w = 1; w < LEG_NW; ++w) sum = cadd(sum, red[w][i]);
       const T sc_ = a.s[offc + (l - m)];
-      part[offa + (l - m)] = cscale(sacc[i], SQ ? sc_ * sc_ : sc_);
+      part[offa + (l - m)] = cscale(sum, SQ ? sc_ * sc_ : sc_);
     }
   }
 }

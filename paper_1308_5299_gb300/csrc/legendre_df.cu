@@ -242,8 +242,7 @@ __global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ df sc[DF_CH];
   __shared__ df sc2[DF_CH];
-  __shared__ dfc sacc[DF_CH];
-  __shared__ dfc red[2][DF_NW][8];
+  __shared__ dfc red[DF_NW][DF_CH];  // per-warp sums of the chunk's l
   __shared__ int s_min;
   df P1[DF_RP], P2[DF_RP], zz[DF_RP];
   int ls[DF_RP], p[DF_RP];
@@ -274,7 +273,6 @@ __global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a
   double2* part = a.partial + (int64_t)yb * n_lm(L);
   const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~7) : L + 1;
   for (int l = m + tid; l < lbeg; l += DF_NT) part[offa + (l - m)] = make_double2(0.0, 0.0);
-  int rb = 0;
   for (int l0 = lbeg; l0 <= L; l0 += DF_CH) {
     const int nl = min(DF_CH, L - l0 + 1);
     __syncthreads();
@@ -288,7 +286,7 @@ __global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a
       const int lg = l0 + i8;
       const int ng = min(8, nl - i8);
       if (!live || wmin >= lg + ng) {
-        if (lane < 8) red[rb][warp][lane] = {{0.f, 0.f}, {0.f, 0.f}};
+        if (lane < 8) red[warp][i8 + lane] = {{0.f, 0.f}, {0.f, 0.f}};
       } else {
         dfc acc[8];
 #pragma unroll
@@ -310,22 +308,18 @@ __global__ void __launch_bounds__(DF_NT) leg_adjoint_df_kernel(LegArgs<double> a
           }
         }
         warp_reduce8_df(acc);
-        if ((lane & 3) == 0) red[rb][warp][lane >> 2] = acc[0];
+        if ((lane & 3) == 0) red[warp][i8 + (lane >> 2)] = acc[0];
       }
-      __syncthreads();
-      if (tid < 8) {
-        dfc s = red[rb][0][tid];
-#pragma unroll
-        for (int w = 1; w < DF_NW; ++w) s = cadd(s, red[rb][w][tid]);
-        sacc[i8 + tid] = s;
-      }
-      rb ^= 1;
     }
+    // one barrier per chunk: the warps' sums in a fixed order
     __syncthreads();
     for (int i = tid; i < nl; i += DF_NT) {
       const int l = l0 + i;
+      dfc sum = red[0][i];
+#pragma unroll
+      for (int w = 1; w < DF_NW; ++w) sum = cadd(sum, red[w][i]);
       const double sc_ = a.s[offc + (l - m)];
-      part[offa + (l - m)] = make_double2(todbl(sacc[i].x) * sc_, todbl(sacc[i].y) * sc_);
+      part[offa + (l - m)] = make_double2(todbl(sum.x) * sc_, todbl(sum.y) * sc_);
     }
   }
 }
