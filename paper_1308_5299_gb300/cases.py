@@ -1,6 +1,7 @@
 """Timed runs of single library calls on synthetic inputs, one JSON line each.
 
     python -m paper_1308_5299_gb300.cases tc --nside 512 --lmax 1023 --nrhs 16
+    python -m paper_1308_5299_gb300.cases sht --nside 1024 --lmax 2047 --dtype f32
 
 ``tc``: batched synthesis, adjoint synthesis and system-matrix application
 with the Legendre contractions on the tensor cores (BF16 operands, FP32
@@ -10,6 +11,9 @@ FP32 CUDA-core calls, timed with CUDA events on the plan's stream after
 the Planck-shaped problem of that size (prior, beam and noise of
 ``synthetic.problem_inputs`` where the name exists, else a damped spectrum
 with a 60 arcmin beam and unit noise).
+
+``sht``: one synthesis and one adjoint synthesis of a single right-hand side
+in FP32 or FP64.
 """
 import argparse
 import json
@@ -70,9 +74,30 @@ def tc_case(nside, lmax, nrhs, warmup, reps):
     return {"case": "tc", "nside": nside, "lmax": lmax, "nrhs": nrhs, "reps": reps, "ms": res}
 
 
+def sht_case(nside, lmax, warmup, reps, dtype):
+    """One synthesis and one adjoint synthesis (single right-hand side) in
+    FP32 or FP64, default (untuned) ring blocks."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    plan = binding.Plan(lmax, nside=nside, stream=stream)
+    cdt, rdt = (torch.complex64, torch.float32) if dtype == "f32" else (torch.complex128, torch.float64)
+    a = torch.from_numpy(synthetic.random_alm(lmax, seed=301)).to(cdt).to(dev)
+    m = torch.empty(plan.npix, dtype=rdt, device=dev)
+    out = torch.empty_like(a)
+    res = {}
+    for name, fn in (("synthesis", lambda: plan.sht_synth(a, m)), ("adjoint", lambda: plan.sht_adjoint(m, out))):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        res[name] = _time(fn, stream, reps)
+    return {"case": "sht", "nside": nside, "lmax": lmax, "dtype": dtype, "reps": reps, "ms": res}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["tc"])
+    ap.add_argument("case", choices=["tc", "sht"])
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--nside", type=int, default=512)
     ap.add_argument("--lmax", type=int, default=1023)
     ap.add_argument("--nrhs", type=int, default=16)
@@ -80,7 +105,10 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
     binding.lib()
-    print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps)))
+    if args.case == "tc":
+        print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps)))
+    else:
+        print(json.dumps(sht_case(args.nside, args.lmax, args.warmup, args.reps, args.dtype)))
 
 
 if __name__ == "__main__":

@@ -40,6 +40,13 @@ namespace cr {
 
 constexpr int RF_NT = 256;
 
+// Shared-memory position of FFT buffer element i: bits 4..15 XOR-folded into
+// bits 0..3 (a bijection on [0, 2^16)).  With 8-byte elements a bank pair
+// holds positions equal mod 16; the fold spreads every access pattern of
+// the kernels below -- consecutive, the radix-8 passes' strides 8^p, and the
+// bit-reversed scatter and gather -- over all 16 bank pairs.
+__device__ __forceinline__ int swz(int i) { return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15); }
+
 __device__ __forceinline__ int bitrev(int k, int logM) {
   return logM ? (int)(__brev((unsigned)k) >> (32 - logM)) : 0;
 }
@@ -81,7 +88,7 @@ __device__ void fft_dit(C* buf, int M, int logM, int sign, const C* __restrict__
       if (ns == 3) {
         C e[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) e[t] = buf[j0 + t * h];
+        for (int t = 0; t < 8; ++t) e[t] = buf[swz(j0 + t * h)];
         const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2), s3 = Mmax >> (lh + 3);
         const C w1 = twid(tw, k * s1, sign);
         bf_dit(e[0], e[1], w1);
@@ -96,11 +103,11 @@ __device__ void fft_dit(C* buf, int M, int logM, int sign, const C* __restrict__
 #pragma unroll
         for (int t = 0; t < 4; ++t) bf_dit(e[t], e[t + 4], twid(tw, (k + t * h) * s3, sign));
 #pragma unroll
-        for (int t = 0; t < 8; ++t) buf[j0 + t * h] = e[t];
+        for (int t = 0; t < 8; ++t) buf[swz(j0 + t * h)] = e[t];
       } else if (ns == 2) {
         C e[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) e[t] = buf[j0 + t * h];
+        for (int t = 0; t < 4; ++t) e[t] = buf[swz(j0 + t * h)];
         const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2);
         const C w1 = twid(tw, k * s1, sign);
         bf_dit(e[0], e[1], w1);
@@ -108,12 +115,12 @@ __device__ void fft_dit(C* buf, int M, int logM, int sign, const C* __restrict__
         bf_dit(e[0], e[2], twid(tw, k * s2, sign));
         bf_dit(e[1], e[3], twid(tw, (k + h) * s2, sign));
 #pragma unroll
-        for (int t = 0; t < 4; ++t) buf[j0 + t * h] = e[t];
+        for (int t = 0; t < 4; ++t) buf[swz(j0 + t * h)] = e[t];
       } else {
-        C a = buf[j0], b = buf[j0 + h];
+        C a = buf[swz(j0)], b = buf[swz(j0 + h)];
         bf_dit(a, b, twid(tw, k * (Mmax >> (lh + 1)), sign));
-        buf[j0] = a;
-        buf[j0 + h] = b;
+        buf[swz(j0)] = a;
+        buf[swz(j0 + h)] = b;
       }
     }
     __syncthreads();
@@ -137,7 +144,7 @@ __device__ void fft_dif(C* buf, int M, int logM, int sign, const C* __restrict__
       if (ns == 3) {
         C e[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) e[t] = buf[j0 + t * h];
+        for (int t = 0; t < 8; ++t) e[t] = buf[swz(j0 + t * h)];
         const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2), s3 = Mmax >> (lh + 3);
 #pragma unroll
         for (int t = 0; t < 4; ++t) bf_dif(e[t], e[t + 4], twid(tw, (k + t * h) * s3, sign));
@@ -152,11 +159,11 @@ __device__ void fft_dif(C* buf, int M, int logM, int sign, const C* __restrict__
         bf_dif(e[4], e[5], w1);
         bf_dif(e[6], e[7], w1);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) buf[j0 + t * h] = e[t];
+        for (int t = 0; t < 8; ++t) buf[swz(j0 + t * h)] = e[t];
       } else if (ns == 2) {
         C e[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) e[t] = buf[j0 + t * h];
+        for (int t = 0; t < 4; ++t) e[t] = buf[swz(j0 + t * h)];
         const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2);
         bf_dif(e[0], e[2], twid(tw, k * s2, sign));
         bf_dif(e[1], e[3], twid(tw, (k + h) * s2, sign));
@@ -164,12 +171,12 @@ __device__ void fft_dif(C* buf, int M, int logM, int sign, const C* __restrict__
         bf_dif(e[0], e[1], w1);
         bf_dif(e[2], e[3], w1);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) buf[j0 + t * h] = e[t];
+        for (int t = 0; t < 4; ++t) buf[swz(j0 + t * h)] = e[t];
       } else {
-        C a = buf[j0], b = buf[j0 + h];
+        C a = buf[swz(j0)], b = buf[swz(j0 + h)];
         bf_dif(a, b, twid(tw, k * (Mmax >> (lh + 1)), sign));
-        buf[j0] = a;
-        buf[j0 + h] = b;
+        buf[swz(j0)] = a;
+        buf[swz(j0 + h)] = b;
       }
     }
     __syncthreads();
@@ -216,55 +223,96 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
       const C h2 = fold(b == 0 ? 0 : n - b);
       return cscale(cadd(h1, cconj(h2)), (T)0.5);
     };
-    for (int k = tid; k < nh; k += NT) {
-      const C A = Hp(k);
-      const C B = cconj(Hp(nh - k));
-      const C w = tab[2 * k];
-      const C Z = cadd(cadd(A, B), cmuli(cmul(w, csub(A, B))));
-      if (!f.bluestein) buf[bitrev(k, lg)] = Z;
-      else buf[k] = cmul(Z, chirp(k));
+    // Rings with fewer bins than threads split each bin's fold over g lanes
+    // (a power of two <= 32; lane j of a group takes m = b + q n with
+    // q = j mod g, whose phase e^{i pi s m / n} is then constant) and sum the
+    // g partial Z in a fixed shuffle order: the long serial folds of the
+    // small polar rings become g short ones.
+    int g = 1;
+    while (g < 32 && nh * g * 2 <= NT) g <<= 1;
+    if (g == 1) {
+      for (int k = tid; k < nh; k += NT) {
+        const C A = Hp(k);
+        const C B = cconj(Hp(nh - k));
+        const C w = tab[2 * k];
+        const C Z = cadd(cadd(A, B), cmuli(cmul(w, csub(A, B))));
+        if (!f.bluestein) buf[swz(bitrev(k, lg))] = Z;
+        else buf[swz(k)] = cmul(Z, chirp(k));
+      }
+    } else {
+      const int k = tid / g, j = tid & (g - 1);
+      auto fold_part = [&](int b) -> C {
+        C h = mk((T)0, (T)0);
+#pragma unroll 4
+        for (int m = b + j * n; m <= L; m += g * n) {
+          const C F = row[m];
+          const T w = (m == 0) ? (T)1 : (T)2;
+          h.x = fma(w, F.x, h.x);
+          h.y = fma(w, F.y, h.y);
+        }
+        return f.shift ? cmul(h, tab[b + ((j & 1) ? n : 0)]) : h;
+      };
+      auto Hpp = [&](int b) -> C {
+        const C h1 = fold_part(b);
+        const C h2 = fold_part(b == 0 ? 0 : n - b);
+        return cscale(cadd(h1, cconj(h2)), (T)0.5);
+      };
+      C Z = mk((T)0, (T)0);
+      if (k < nh) {
+        const C A = Hpp(k);
+        const C B = cconj(Hpp(nh - k));
+        Z = cadd(cadd(A, B), cmuli(cmul(tab[2 * k], csub(A, B))));
+      }
+      for (int o = g >> 1; o > 0; o >>= 1) {
+        Z.x += __shfl_xor_sync(0xffffffffu, Z.x, o);
+        Z.y += __shfl_xor_sync(0xffffffffu, Z.y, o);
+      }
+      if (k < nh && j == 0) {
+        if (!f.bluestein) buf[swz(bitrev(k, lg))] = Z;
+        else buf[swz(k)] = cmul(Z, chirp(k));
+      }
     }
     if (f.bluestein)
-      for (int k = nh + tid; k < M; k += NT) buf[k] = mk((T)0, (T)0);
+      for (int k = nh + tid; k < M; k += NT) buf[swz(k)] = mk((T)0, (T)0);
     __syncthreads();
     if (!f.bluestein) {
       fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
     } else {
       fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
-      for (int i = tid; i < M; i += NT) buf[i] = cmul(buf[i], vh[i]);
+      for (int i = tid; i < M; i += NT) buf[swz(i)] = cmul(buf[swz(i)], vh[i]);
       __syncthreads();
       fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
-      for (int t = tid; t < nh; t += NT) buf[t] = cmul(buf[t], chirp(t));
+      for (int t = tid; t < nh; t += NT) buf[swz(t)] = cmul(buf[swz(t)], chirp(t));
       __syncthreads();
     }
     // buf[t] = z_t = (map_{2t}, map_{2t+1})
     if (MODE == 0) {
       C* out = reinterpret_cast<C*>(a.map_out + f.off);
-      for (int t = tid; t < nh; t += NT) out[t] = buf[t];
+      for (int t = tid; t < nh; t += NT) out[t] = buf[swz(t)];
       return;
     }
     // MODE 2: multiply by the pixel diagonal and continue with the adjoint.
     const C* dg = reinterpret_cast<const C*>(a.pixdiag + f.off);
     C* mo = a.map_out ? reinterpret_cast<C*>(a.map_out + f.off) : nullptr;
     for (int t = tid; t < nh; t += NT) {
-      C z = buf[t];
+      C z = buf[swz(t)];
       if (mo) mo[t] = z;
       const C d = dg[t];
       z.x *= d.x;
       z.y *= d.y;
-      buf[t] = f.bluestein ? cmul(cconj(z), chirp(t)) : z;
+      buf[swz(t)] = f.bluestein ? cmul(cconj(z), chirp(t)) : z;
     }
     if (f.bluestein)
-      for (int k = nh + tid; k < M; k += NT) buf[k] = mk((T)0, (T)0);
+      for (int k = nh + tid; k < M; k += NT) buf[swz(k)] = mk((T)0, (T)0);
     __syncthreads();
   } else {
     const C* in = reinterpret_cast<const C*>(a.map_in + f.off);
     for (int t = tid; t < nh; t += NT) {
       const C z = in[t];
-      buf[t] = f.bluestein ? cmul(cconj(z), chirp(t)) : z;
+      buf[swz(t)] = f.bluestein ? cmul(cconj(z), chirp(t)) : z;
     }
     if (f.bluestein)
-      for (int k = nh + tid; k < M; k += NT) buf[k] = mk((T)0, (T)0);
+      for (int k = nh + tid; k < M; k += NT) buf[swz(k)] = mk((T)0, (T)0);
     __syncthreads();
   }
 
@@ -273,12 +321,12 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
     fft_dif(buf, M, lg, -1, a.tw, a.Mmax);  // Z'_k at buf[bitrev(k)]
   } else {
     fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
-    for (int i = tid; i < M; i += NT) buf[i] = cmul(buf[i], vh[i]);
+    for (int i = tid; i < M; i += NT) buf[swz(i)] = cmul(buf[swz(i)], vh[i]);
     __syncthreads();
     fft_dit(buf, M, lg, +1, a.tw, a.Mmax);  // Z'_k = conj(buf[k] chirp(k))
   }
   auto getZ = [&](int k) -> C {
-    return f.bluestein ? cconj(cmul(buf[k], chirp(k))) : buf[bitrev(k, lg)];
+    return f.bluestein ? cconj(cmul(buf[swz(k)], chirp(k))) : buf[swz(bitrev(k, lg))];
   };
   auto Yhat = [&](int b) -> C {  // b in [0, nh]
     const C Zb = getZ(b == nh ? 0 : b);
@@ -307,8 +355,9 @@ int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st) {
     const int cnt = a.cls_start[c + 1] - a.cls_start[c];
     if (cnt <= 0) continue;
     const size_t smem = (size_t)M * sizeof(C);
-    if (smem > 227 * 1024) return fail(CR_EINVAL, "ring FFT buffer exceeds shared memory");
-    const int nt = std::max(64, std::min(RF_NT, M / 8));
+    if (smem > 227 * 1024 || M > 65536) return fail(CR_EINVAL, "ring FFT buffer exceeds shared memory");
+    // at least 128 threads: small rings split their folds over the idle lanes
+    const int nt = std::max(128, std::min(RF_NT, M / 8));
     RingArgs<T> b = a;
     b.rbase = a.cls_start[c];
     switch (mode) {
@@ -369,11 +418,11 @@ __global__ void vhat_kernel(const LenDesc* lens, const double2* tab, const doubl
     int dd = -1;
     if (k < d.nh) dd = k;
     else if (k > d.M - d.nh) dd = d.M - k;
-    buf[k] = (dd >= 0) ? cconj(tab[d.tab + (int)((2 * (int64_t)dd * dd) % twon)]) : make_double2(0.0, 0.0);
+    buf[swz(k)] = (dd >= 0) ? cconj(tab[d.tab + (int)((2 * (int64_t)dd * dd) % twon)]) : make_double2(0.0, 0.0);
   }
   __syncthreads();
   fft_dif(buf, d.M, d.logM, -1, tw, Mmax);
-  for (int k = threadIdx.x; k < d.M; k += blockDim.x) vhat[d.vhat + k] = cscale(buf[k], 1.0 / d.M);
+  for (int k = threadIdx.x; k < d.M; k += blockDim.x) vhat[d.vhat + k] = cscale(buf[swz(k)], 1.0 / d.M);
 }
 
 __global__ void to_f32_kernel(const double2* in, float2* out, int64_t n) {
