@@ -127,10 +127,13 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
   const int L = a.L;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  __shared__ C sa[LEG_CH];
-  __shared__ T sc[LEG_CH];
-  __shared__ T sc2[LEG_CH];
-  __shared__ int s_min;
+  // each warp stages its own chunks (no block-wide barrier in the loop)
+  __shared__ C sa_all[LEG_NW][LEG_CH];
+  __shared__ T sc_all[LEG_NW][LEG_CH];
+  __shared__ T sc2_all[POLAR ? LEG_NW : 1][LEG_CH];
+  C* sa = sa_all[warp];
+  T* sc = sc_all[warp];
+  T* sc2 = sc2_all[POLAR ? warp : 0];
 
   T P1[RP], P2[RP], zz[RP];
   int ls[RP], p[RP];
@@ -143,21 +146,16 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
   const int yb = (int)blockIdx.y + yoff;
   int wmin, wmax;
   const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
-  if (tid == 0) s_min = L + 1;
-  __syncthreads();
-  if (lane == 0 && live) atomicMin(&s_min, wmin);
-  __syncthreads();
-  const int cmin = s_min;
   const int64_t offa = lm_off(L, m);
   const int64_t offc = lm_off(a.Lc, m);
 
   // chunks start at an offset from m that is a multiple of 8, so l - m and
-  // the group index agree in parity
-  const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~7) : L + 1;
+  // the group index agree in parity; a warp starts at its earliest pair
+  const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
   for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
     const int nl = min(LEG_CH, L - l0 + 1);
-    __syncthreads();
-    for (int i = tid; i < nl; i += LEG_NT) {
+    __syncwarp();
+    for (int i = lane; i < nl; i += 32) {
       const int l = l0 + i;
       C v = a.alm[offa + (l - m)];
       if (m == 0) v.y = 0;
@@ -167,8 +165,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
       sc[i] = a.c[offc + (l - m)];
       if (POLAR) sc2[i] = a.c2[offc + (l - m)];
     }
-    __syncthreads();
-    if (!live || wmin >= l0 + nl) continue;
+    __syncwarp();
     for (int i8 = 0; i8 < nl; i8 += 8) {
       const int lg = l0 + i8;
       const int ng = min(8, nl - i8);
@@ -269,6 +266,201 @@ __device__ __forceinline__ void warp_reduce8(C v[8]) {
   v[0].y += shfl_x(v[0].y, 1);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 synthesis with packed pairs of FP32 lanes (f32x2 instructions of the
+// sm_100 family: two FP32 operations per issued instruction).  Inside the
+// unrolled 8-l group two ring pairs step together: one packed multiply and
+// one packed FMA for the recurrence, two packed FMAs for the complex
+// accumulators.  The minus sign of the three-term recurrence is folded into
+// a fixed sign pattern: with V_l = sigma_l Q_l, sigma = (+, +, -, -) by
+// (l - m) mod 4, the recurrence becomes V_l = alpha_l z V_{l-1} + V_{l-2},
+// alpha_l = sigma_l sigma_{l-1} c_lm (-c, +c, -c, +c by (l - m) mod 4), and
+// the staged coefficient carries sigma_l, so sum_l V_l (sigma_l a_lm) =
+// sum_l Q_l a_lm.  The polar difference form needs no sign change.  Staged
+// values are stored as (v, v) pairs so a 64-bit shared load yields the
+// broadcast operand.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 lds2(const float2* p) { return *reinterpret_cast<const u64*>(p); }
+
+template <bool POLAR, int RP>
+__global__ void __launch_bounds__(LEG_NT) leg_synth_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
+  static_assert(RP % 2 == 0, "pairs per thread must be even");
+  constexpr int NP = RP / 2;
+  const int m = blockIdx.x;
+  const int L = a.L;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  __shared__ float2 sax_all[LEG_NW][LEG_CH], say_all[LEG_NW][LEG_CH], sk_all[LEG_NW][LEG_CH];
+  __shared__ float2 sk2_all[POLAR ? LEG_NW : 1][LEG_CH];
+  float2* sax = sax_all[warp];
+  float2* say = say_all[warp];
+  float2* sk = sk_all[warp];
+  float2* sk2 = sk2_all[POLAR ? warp : 0];
+
+  float P1[RP], P2[RP], zz[RP];
+  int ls[RP], p[RP];
+  float ex[RP], ey[RP], ox[RP], oy[RP];
+#pragma unroll
+  for (int j = 0; j < RP; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
+  const int yb = (int)blockIdx.y + yoff;
+  int wmin, wmax;
+  const bool live = load_pairs<float, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
+  if (!POLAR) {
+#pragma unroll
+    for (int j = 0; j < RP; ++j)
+      if (ls[j] <= L) {
+        P1[j] *= sgn(ls[j] - 1);
+        P2[j] *= sgn(ls[j] - 2);
+      }
+  }
+  const int64_t offa = lm_off(L, m);
+  const int64_t offc = lm_off(a.Lc, m);
+  const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
+  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
+    const int nl = min(LEG_CH, L - l0 + 1);
+    __syncwarp();
+    for (int i = lane; i < nl; i += 32) {
+      const int l = l0 + i;
+      float2 v = a.alm[offa + (l - m)];
+      if (m == 0) v.y = 0.f;
+      float f = a.s[offc + (l - m)];
+      if (a.dl) f *= a.dl[l];
+      const float c = a.c[offc + (l - m)];
+      if (POLAR) {
+        sax[i] = make_float2(v.x * f, v.x * f);
+        say[i] = make_float2(v.y * f, v.y * f);
+        sk[i] = make_float2(-c, -c);
+        const float c2 = a.c2[offc + (l - m)];
+        sk2[i] = make_float2(c2, c2);
+      } else {
+        const float g = f * sgn(l);
+        const float al = ((l - m) & 1) ? c : -c;
+        sax[i] = make_float2(v.x * g, v.x * g);
+        say[i] = make_float2(v.y * g, v.y * g);
+        sk[i] = make_float2(al, al);
+      }
+    }
+    __syncwarp();
+    for (int i8 = 0; i8 < nl; i8 += 8) {
+      const int lg = l0 + i8;
+      const int ng = min(8, nl - i8);
+      if (wmin >= lg + ng) continue;  // no pair of the warp has started
+      if (wmax <= lg && ng == 8) {
+        u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
+          S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
+          S2[q] = pk2(P2[2 * q], P2[2 * q + 1]);
+          EX[q] = pk2(ex[2 * q], ex[2 * q + 1]);
+          EY[q] = pk2(ey[2 * q], ey[2 * q + 1]);
+          OX[q] = pk2(ox[2 * q], ox[2 * q + 1]);
+          OY[q] = pk2(oy[2 * q], oy[2 * q + 1]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const u64 K = lds2(&sk[i8 + u]);
+          const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
+          const u64 AX = lds2(&sax[i8 + u]), AY = lds2(&say[i8 + u]);
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            u64 Q;
+            if (POLAR) {
+              const u64 E = fma2(K, Z[q], K2);
+              const u64 D = fma2(E, S1[q], S2[q]);
+              Q = add2(S1[q], D);
+              S2[q] = D;
+            } else {
+              Q = fma2(mul2(K, Z[q]), S1[q], S2[q]);
+              S2[q] = S1[q];
+            }
+            S1[q] = Q;
+            if (u & 1) {
+              OX[q] = fma2(Q, AX, OX[q]);
+              OY[q] = fma2(Q, AY, OY[q]);
+            } else {
+              EX[q] = fma2(Q, AX, EX[q]);
+              EY[q] = fma2(Q, AY, EY[q]);
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
+          upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
+          upk2(EX[q], ex[2 * q], ex[2 * q + 1]);
+          upk2(EY[q], ey[2 * q], ey[2 * q + 1]);
+          upk2(OX[q], ox[2 * q], ox[2 * q + 1]);
+          upk2(OY[q], oy[2 * q], oy[2 * q + 1]);
+        }
+      } else {
+        for (int u = 0; u < ng; ++u) {
+          const int l = lg + u;
+          const float K = sk[i8 + u].x;
+          const float K2 = POLAR ? sk2[i8 + u].x : 0.f;
+          const float ax = sax[i8 + u].x, ay = say[i8 + u].x;
+#pragma unroll
+          for (int j = 0; j < RP; ++j) {
+            if (l >= ls[j]) {
+              float q;
+              if (POLAR) {
+                const float e = fmaf(K, zz[j], K2);
+                const float d = fmaf(e, P1[j], P2[j]);
+                q = P1[j] + d;
+                P2[j] = d;
+              } else {
+                q = fmaf(K * zz[j], P1[j], P2[j]);
+                P2[j] = P1[j];
+              }
+              P1[j] = q;
+              if (u & 1) {
+                ox[j] = fmaf(q, ax, ox[j]);
+                oy[j] = fmaf(q, ay, oy[j]);
+              } else {
+                ex[j] = fmaf(q, ax, ex[j]);
+                ey[j] = fmaf(q, ay, ey[j]);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  const int pend = POLAR ? a.npolar : a.npairs;
+#pragma unroll
+  for (int j = 0; j < RP; ++j) {
+    if (p[j] < pend) {
+      const int rn = p[j], rs = a.nring - 1 - p[j];
+      a.phase[(int64_t)rn * a.ldp + m] = make_float2(ex[j] + ox[j], ey[j] + oy[j]);
+      if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = make_float2(ex[j] - ox[j], ey[j] - oy[j]);
+    }
+  }
+}
+
 // SQ: accumulate P~^2 times a per-ring value (ringval) instead of P~ times
 // the ring's phase G_m: sum_k P~_lm(z_k)^2 v_k, used for the diagonal of
 // Y^T N^-1 Y (the Delta m = 0 term of the ring formula).
@@ -279,10 +471,16 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   const int L = a.L;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  __shared__ T sc[LEG_CH];
-  __shared__ T sc2[LEG_CH];
-  __shared__ C red[LEG_NW][LEG_CH];  // per-warp sums of the chunk's l
+  // per-warp copies of the recurrence coefficients (staged by each warp),
+  // and per-warp sums of the chunk's l, double-buffered by chunk parity in
+  // FP32 so that one barrier per chunk suffices
+  constexpr int NRB = sizeof(T) == 4 ? 2 : 1;
+  __shared__ T sc_all[LEG_NW][LEG_CH];
+  __shared__ T sc2_all[POLAR ? LEG_NW : 1][LEG_CH];
+  __shared__ C red_all[NRB][LEG_NW][LEG_CH];
   __shared__ int s_min;
+  T* sc = sc_all[warp];
+  T* sc2 = sc2_all[POLAR ? warp : 0];
 
   T P1[RP], P2[RP], zz[RP];
   int ls[RP], p[RP];
@@ -321,14 +519,17 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   // rows before the block's earliest start are zero
   for (int l = m + tid; l < lbeg; l += LEG_NT) part[offa + (l - m)] = mk((T)0, (T)0);
 
+  int rb = 0;
   for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
     const int nl = min(LEG_CH, L - l0 + 1);
-    __syncthreads();
-    for (int i = tid; i < nl; i += LEG_NT) {
+    if (NRB == 1) __syncthreads();  // the previous chunk's sums are read
+    C(*red)[LEG_CH] = red_all[rb];
+    __syncwarp();
+    for (int i = lane; i < nl; i += 32) {
       sc[i] = a.c[offc + (l0 - m) + i];
       if (POLAR) sc2[i] = a.c2[offc + (l0 - m) + i];
     }
-    __syncthreads();
+    __syncwarp();
     for (int i8 = 0; i8 < nl; i8 += 8) {
       const int lg = l0 + i8;
       const int ng = min(8, nl - i8);
@@ -392,6 +593,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
       const T sc_ = a.s[offc + (l - m)];
       part[offa + (l - m)] = cscale(sum, SQ ? sc_ * sc_ : sc_);
     }
+    rb = (rb + 1) % NRB;
   }
 }
 
@@ -436,8 +638,13 @@ static inline int legal_rp(int rp) { return (rp == 2 || rp == 4 || rp == 8) ? rp
 
 template <typename T, int RP>
 static void synth_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
-  if (nbp) { leg_synth_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { leg_synth_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  if constexpr (sizeof(T) == 4) {
+    if (nbp) { leg_synth_f32x2_kernel<true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_synth_f32x2_kernel<false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  } else {
+    if (nbp) { leg_synth_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_synth_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  }
 }
 
 template <typename T, int RP>
