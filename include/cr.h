@@ -88,6 +88,12 @@ extern "C" {
  * accumulation); the outer residual b - A x stays FP64 per right-hand side.
  * Also accepted by cr_batch_create. */
 #define CR_TC_CYCLES 32
+/* solve flag (with CR_TC_CYCLES): the top level's residuals (full band
+ * limit, the most accuracy-sensitive step of the cycle) run per right-hand
+ * side on the FP32 CUDA-core kernels; the pixel levels stay batched on the
+ * tensor cores.  A replayed batch graph keeps the choice it was captured
+ * with. */
+#define CR_TC_TOP_F32 64
 
 /* grid kinds */
 #define CR_GRID_HEALPIX 0

@@ -23,6 +23,7 @@ CR_F64, CR_F32, CR_MIXED, CR_PCG, CR_FIXED, CR_CG = 0, 1, 2, 4, 8, 16
 CR_DRAW_FLUCT, CR_DRAW_PLAIN = 1, 2
 CR_TC = 3
 CR_TC_CYCLES = 32
+CR_TC_TOP_F32 = 64
 CR_PROBE_ALM, CR_PROBE_MAP = 0, 1
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0

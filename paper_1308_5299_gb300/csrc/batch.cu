@@ -36,8 +36,8 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
   if (!out || nplans < 1 || !plans || !x || !b || !nrhs || cycles < 1)
     return fail(CR_EINVAL, "cr_batch_create: bad arguments");
   const bool tc = (mode & CR_TC_CYCLES) != 0;
-  if ((mode & ~(3 | CR_TC_CYCLES)) != 0 || ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) ||
-      (tc && (mode & 3) != CR_MIXED))
+  if ((mode & ~(3 | CR_TC_CYCLES | CR_TC_TOP_F32)) != 0 || ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) ||
+      (tc && (mode & 3) != CR_MIXED) || ((mode & CR_TC_TOP_F32) && !tc))
     return fail(CR_EINVAL, "cr_batch_create: mode must be CR_F64 or CR_MIXED (stationary, fixed count), "
                            "CR_TC_CYCLES only with CR_MIXED");
   cudaStream_t st = plans[0] ? plans[0]->stream : nullptr;
@@ -52,6 +52,7 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
   const int fmode = (mode & 3) | CR_FIXED;
   // one uncaptured solve per plan first: it builds the tables created lazily
   // on first use, which must not be allocated inside the capture
+  for (int i = 0; i < nplans; ++i) plans[i]->tc_top_f32 = (mode & CR_TC_TOP_F32) != 0;
   for (int i = 0; i < nplans; ++i) {
     if (nrhs[i] == 0) continue;
     int rc = tc ? solve_tc(plans[i], x[i], b[i], nrhs[i], 0.0, 1, true, nullptr, nullptr, nullptr)

@@ -151,10 +151,19 @@ static int ensure_tc_work(cr_plan* P) {
   return CR_OK;
 }
 
-// R = B - A_h X for nr right-hand sides
+// R = B - A_h X for nr right-hand sides (with P->tc_top_f32 the top level's
+// residuals run per right-hand side on the FP32 CUDA-core kernels)
 static int residual_tc(cr_plan* P, int h, int nr, const float2* X, const float2* B, float2* R) {
   LevelOps& o = ops_of(P).ops[h];
   const int L = lmax_of(P, h);
+  if (h == 0 && P->tc_top_f32) {
+    const int64_t nlm = n_lm(L);
+    for (int r = 0; r < nr; ++r) {
+      int rc = residual<float>(P, 0, X + r * nlm, B + r * nlm, R + r * nlm);
+      if (rc) return rc;
+    }
+    return CR_OK;
+  }
   const float* pix = nullptr;
   const Grid& g = noise_grid<float>(P, h, &pix);
   int rc = tc_begin(P, g, L, true, false);
@@ -1003,6 +1012,7 @@ int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int ma
       return fail(CR_EINVAL, "cr_solve: CR_TC_CYCLES is a stationary CR_MIXED solve");
     if (max_cycles < 1 || !(eps >= 0.0) || nrhs < 0) return fail(CR_EINVAL, "cr_solve: eps / max_cycles / nrhs");
     if (nrhs == 0) return CR_OK;
+    plan->tc_top_f32 = (mode & CR_TC_TOP_F32) != 0;
     return solve_tc(plan, x, b, nrhs, eps, max_cycles, (mode & CR_FIXED) != 0, cycles_out, relres_out, history);
   }
   if ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) return fail(CR_EINVAL, "cr_solve: mode precision must be CR_F64 or CR_MIXED");

@@ -67,7 +67,8 @@ def _run(dev, stream):
     batch.close()
 
 
-def test_tensor_core_cycles_converge_to_exact_answers():
+@pytest.mark.parametrize("top_f32", [False, True])
+def test_tensor_core_cycles_converge_to_exact_answers(top_f32):
     """CR_MIXED | CR_TC_CYCLES: 18 right-hand sides (a group of 16 and one of
     2) whose FP32 cycles run together with every Legendre stage on the
     tensor cores; the FP64 outer residual drives each to its exact answer
@@ -82,7 +83,8 @@ def test_tensor_core_cycles_converge_to_exact_answers():
         b = torch.empty_like(xt)
         plan.apply_A(xt, b)
         x = torch.zeros_like(b)
-        cyc, rel, hist = plan.solve(b, x, eps=1e-20, max_cycles=40, mode=binding.CR_MIXED | binding.CR_TC_CYCLES)
+        mode = binding.CR_MIXED | binding.CR_TC_CYCLES | (binding.CR_TC_TOP_F32 if top_f32 else 0)
+        cyc, rel, hist = plan.solve(b, x, eps=1e-20, max_cycles=40, mode=mode)
         assert all(c <= 40 for c in cyc) and max(rel) < 1e-10
         for j in range(nr):
             m = torch.empty(12 * 64 * 64, dtype=torch.float64, device=dev)
@@ -96,13 +98,14 @@ def test_tensor_core_cycles_converge_to_exact_answers():
         assert h_tc[2] < 3.0 * href[0][2] + 1e-12, (h_tc, href[0][:3])
 
 
-def test_tensor_core_cycles_in_a_graph_match_direct():
+@pytest.mark.parametrize("top_f32", [False, True])
+def test_tensor_core_cycles_in_a_graph_match_direct(top_f32):
     dev = cuda_device()
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         specs = [(64, 191, 120.0, 17), (32, 95, 240.0, 3)]
         plans, xs, bs, refs = [], [], [], []
-        cycles, mode = 3, binding.CR_MIXED | binding.CR_TC_CYCLES
+        cycles, mode = 3, binding.CR_MIXED | binding.CR_TC_CYCLES | (binding.CR_TC_TOP_F32 if top_f32 else 0)
         for k, (nside, lmax, fwhm, nr) in enumerate(specs):
             plan, cl = make_plan(nside, lmax, fwhm, stream, dev)
             xt = torch.from_numpy(np.stack([synthetic.draw_prior(cl, index=300 + 20 * k + j)
