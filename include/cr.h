@@ -188,6 +188,14 @@ typedef struct cr_params {
   int defer_precompute;
   /* autotune: 1 = run cr_plan_autotune at the end of creation. */
   int autotune;
+  /* smoother of the pixel levels: 0 = multicolour block ICC(0) (Section
+   * 3.5); 1 = additive Schwarz without overlap (block Jacobi): every tile is
+   * a subdomain solved exactly, M = blockdiag(A_hat_pp + alpha I)^-1, applied
+   * in one fully parallel pass -- the domain-decomposition smoother Section
+   * 3.5 names as the parallel alternative.  The ridge alpha is found as for
+   * ICC(0) (smallest alpha for which every block factorises, times
+   * ridge_factor) and raised under ridge_lambda_target. */
+  int smoother;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */

@@ -68,6 +68,7 @@ class cr_params(ctypes.Structure):
         ("fp64_df", ctypes.c_int),
         ("defer_precompute", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("smoother", ctypes.c_int),
     ]
 
 
@@ -244,7 +245,7 @@ class Plan:
 
     def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
                  lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0,
-                 gl_downgrade=0, fp64_df=False, defer_precompute=False, autotune=False):
+                 gl_downgrade=0, fp64_df=False, defer_precompute=False, autotune=False, smoother="icc"):
         """levels: None (transforms and A only), "default" (the library's level
         table), or a list of dicts with nside_h, lmax_h, n_rec and fl
         (cumulative filter, length lmax+1).  gl_downgrade: 0 auto, 1 every
@@ -301,6 +302,9 @@ class Plan:
         p.fp64_df = int(bool(fp64_df))
         p.defer_precompute = int(bool(defer_precompute))
         p.autotune = int(bool(autotune))
+        if smoother not in ("icc", "schwarz"):
+            raise ValueError("smoother: 'icc' (multicolour block ICC(0)) or 'schwarz' (block Jacobi)")
+        p.smoother = 0 if smoother == "icc" else 1
         if ridge_alpha is not None:
             ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
             self._keep.append(ra)

@@ -3,10 +3,11 @@
 //
 // File layout (little-endian, fixed-size fields):
 //   magic "CRPRECMP", u32 version, u32 reserved
-//   identity: i32 nside, lmax, H, ld; per pixel level i32 nside_h, lmax_h,
+//   identity: i32 nside, lmax, H, ld, smoother kind; per pixel level i32 nside_h, lmax_h,
 //             ntile, i64 nblocks; u64 hashes of C_l, b_l and the N^-1 map
 //   per pixel level: f64 alpha, amax, lambda_max; f32 factor blocks
-//                    [nblocks][64][64]
+//                    [nblocks][64][64] (Schwarz: the first ntile blocks hold
+//                    the tiles' inverse blocks)
 //   top level:       f64 top_lambda, top_scale; f64 inv_diag_hp [n_lm(lmax)]
 //   bottom level:    i32 nd; f64 A_bottom [nd][nd], A_bottom^-1 [nd][nd];
 //                    dof map [nd] (i32 l, m, part)
@@ -27,7 +28,7 @@ namespace cr {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'R', 'P', 'R', 'E', 'C', 'M', 'P'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr int kBlock = 64 * 64;  // floats per factor block
 
 // 64-bit FNV-1a over bytes
@@ -86,7 +87,7 @@ int input_hashes(cr_plan* P, uint64_t out[3]) {
 }
 
 struct Identity {
-  int32_t nside = 0, lmax = 0, H = 0, ld = 0;
+  int32_t nside = 0, lmax = 0, H = 0, ld = 0, smoother = 0;
   std::vector<int32_t> nside_h, lmax_h, ntile;
   std::vector<int64_t> nblocks;
   uint64_t hash[3] = {0, 0, 0};
@@ -98,6 +99,7 @@ int plan_identity(cr_plan* P, Identity& id) {
   id.lmax = P->lmax;
   id.H = H.H;
   id.ld = H.ld;
+  id.smoother = H.smoother_kind;
   for (const PixLevel& lev : H.pix) {
     id.nside_h.push_back(lev.nside_h);
     id.lmax_h.push_back(lev.lmax_h);
@@ -133,6 +135,7 @@ int cr_save(cr_plan* plan, const char* path) {
   w.val(id.lmax);
   w.val(id.H);
   w.val(id.ld);
+  w.val(id.smoother);
   for (int i = 0; i < id.H; ++i) {
     w.val(id.nside_h[i]);
     w.val(id.lmax_h[i]);
@@ -218,9 +221,11 @@ int cr_load(cr_plan* plan, const char* path) {
   fid.lmax = r.val<int32_t>();
   fid.H = r.val<int32_t>();
   fid.ld = r.val<int32_t>();
+  fid.smoother = r.val<int32_t>();
   if (!r.ok) return bad(CR_EIO, "truncated header");
-  if (fid.nside != id.nside || fid.lmax != id.lmax || fid.H != id.H || fid.ld != id.ld)
-    return bad(CR_EINVAL, "checkpoint was made for another grid, band limit or level table");
+  if (fid.nside != id.nside || fid.lmax != id.lmax || fid.H != id.H || fid.ld != id.ld ||
+      fid.smoother != id.smoother)
+    return bad(CR_EINVAL, "checkpoint was made for another grid, band limit, level table or smoother");
   for (int i = 0; i < fid.H; ++i) {
     const int32_t ns = r.val<int32_t>(), lm = r.val<int32_t>(), nt = r.val<int32_t>();
     const int64_t nb = r.val<int64_t>();

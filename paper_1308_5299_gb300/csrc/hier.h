@@ -124,6 +124,7 @@ struct Hierarchy {
   double lam_target = 1.5;
   std::vector<double> ridge_fixed;  // given ridges per pixel level, or empty
   bool numeric_ready = false;       // smoothers, top diagonal and bottom built
+  int smoother_kind = 0;            // 0 multicolour block ICC(0), 1 additive Schwarz (block Jacobi)
 };
 
 }  // namespace cr

@@ -577,8 +577,89 @@ struct SmootherBuild {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Additive Schwarz smoother without overlap (block Jacobi over tiles): the
+// subdomain solve of tile p is (A_hat_pp + alpha I)^-1, formed once per ridge
+// (Cholesky in shared memory, inverse of the factor L^-1, then L^-T L^-1) and
+// stored as a full symmetric 64 x 64 block at block p of the factor array;
+// one launch applies all tiles in parallel.
+__global__ void __launch_bounds__(256) schwarz_factor_kernel(const float* A, const int64_t* diag, float alpha,
+                                                             float* S, int* fail) {
+  const int p = blockIdx.x, tid = threadIdx.x;
+  __shared__ float M[TK][TK + 1];
+  __shared__ float Li[TK][TK + 1];
+  __shared__ int bad;
+  const float* Ab = A + diag[p] * TK * TK;  // column-major
+  for (int e = tid; e < TK * TK; e += 256) {
+    const int i = e % TK, j = e / TK;
+    M[i][j] = Ab[e] + (i == j ? alpha : 0.f);
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < TK; ++j) {
+    if (tid == 0) {
+      const float d = M[j][j];
+      if (!(d > 0.f) || !isfinite(d)) bad = 1;
+      M[j][j] = sqrtf(fmaxf(d, 1e-30f));
+    }
+    __syncthreads();
+    const float djj = M[j][j];
+    for (int i = j + 1 + tid; i < TK; i += 256) M[i][j] /= djj;
+    __syncthreads();
+    const int m = TK - j - 1;
+    for (int e = tid; e < m * m; e += 256) {
+      const int i = j + 1 + e % m, k = j + 1 + e / m;
+      if (k <= i) M[i][k] -= M[i][j] * M[k][j];
+    }
+    __syncthreads();
+  }
+  if (tid < TK) {
+    const int c = tid;
+    for (int i = 0; i < TK; ++i) {
+      float s = (i == c) ? 1.f : 0.f;
+      if (i > c)
+        for (int k = c; k < i; ++k) s -= M[i][k] * Li[k][c];
+      Li[i][c] = (i >= c) ? s / M[i][i] : 0.f;
+    }
+  }
+  __syncthreads();
+  float* Sb = S + (int64_t)p * TK * TK;
+  for (int e = tid; e < TK * TK; e += 256) {
+    const int i = e % TK, j = e / TK;
+    float s = 0.f;
+    for (int k = max(i, j); k < TK; ++k) s = fmaf(Li[k][i], Li[k][j], s);
+    Sb[e] = s;
+  }
+  if (tid == 0 && bad) atomicOr(fail, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TK) schwarz_apply_kernel(const float* S, const int* perm, const T* map_in,
+                                                           T* map_out) {
+  const int p = blockIdx.x, tid = threadIdx.x, rq = tid & 15, jg = tid >> 4;
+  __shared__ float vs[TK];
+  __shared__ float4 part[4][16];
+  const int pix = perm[(int64_t)p * TK + tid];
+  vs[tid] = (float)map_in[pix];
+  __syncthreads();
+  const float4 acc = block_gemv(S + (int64_t)p * TK * TK, vs, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
+  map_out[pix] = (T)reduce_groups(acc, part, rq, jg, tid);
+}
+
 int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
   const BlockPattern& pat = lev.pat;
+  if (P->hier && P->hier->smoother_kind == 1) {
+    if (!lev.sb) return fail(CR_ESTATE, "smoother: structure not built");
+    CR_CUDA(cudaMemsetAsync(lev.d_fail, 0, sizeof(int), P->stream));
+    { schwarz_factor_kernel<<<pat.ntile, 256, 0, P->stream>>>(lev.d_A, lev.sb->d_diag, alpha, lev.d_L, lev.d_fail);
+      count_launch(); }
+    CR_CHECK_LAUNCH("schwarz_factor_kernel");
+    int fl = 0;
+    CR_CUDA(cudaMemcpyAsync(&fl, lev.d_fail, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    CR_CUDA(cudaStreamSynchronize(P->stream));
+    *ok = (fl == 0);
+    return CR_OK;
+  }
   IccArgs a;
   a.A = lev.d_A;
   a.L = lev.d_L;
@@ -854,6 +935,11 @@ int smoother_numeric(cr_plan* P, PixLevel& lev, double ridge_factor, int bisecti
 template <typename T>
 int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
   const BlockPattern& pat = lev.pat;
+  if (P->hier && P->hier->smoother_kind == 1) {
+    { schwarz_apply_kernel<T><<<pat.ntile, TK, 0, P->stream>>>(lev.d_L, lev.d_perm, map_in, map_out); count_launch(); }
+    CR_CHECK_LAUNCH("schwarz_apply_kernel");
+    return CR_OK;
+  }
   if (!lev.lt_valid) {
     if (!lev.d_LT) CR_CUDA(cudaMalloc(&lev.d_LT, (size_t)pat.nblocks * TK * TK * sizeof(float)));
     { transpose_blocks_kernel<<<pat.ntile, 256, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_col_ptr, lev.d_col_blk,

@@ -89,7 +89,9 @@ static int smooth_add(cr_plan* P, int h, void* x, const void* r) {
   if (rc) return rc;
   {
     // algorithmic bytes: every factor block read once forward, once backward
-    const double bytes = 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float);
+    // (Schwarz: every tile's inverse block once)
+    const double bytes = H.smoother_kind == 1 ? lev.pat.ntile * 64.0 * 64.0 * sizeof(float)
+                                              : 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float);
     TimerScope ts(P->timing, P->stream, "pixel_smoother", bytes);
     TimerScope tl(P->timing, P->stream, "pixel_smoother.n" + std::to_string(lev.nside_h), bytes);
     rc = apply_smoother<T>(P, lev, m1, m2);
@@ -199,7 +201,8 @@ static int smooth_add_tc(cr_plan* P, int h, int nr, float2* X, const float2* R) 
   for (int r = 0; r < nr && !rc; ++r) {
     if ((rc = tc_ring(P, g, L, r, 0, nullptr, m1))) break;
     {
-      const double bytes = 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float);
+      const double bytes = H.smoother_kind == 1 ? lev.pat.ntile * 64.0 * 64.0 * sizeof(float)
+                                                : 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float);
       TimerScope ts(P->timing, P->stream, "pixel_smoother", bytes);
       if ((rc = apply_smoother<float>(P, lev, m1, m2))) break;
     }
@@ -405,6 +408,8 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
   H.pix.resize(H.H);
   H.work.resize(H.H + 2);
   hops->ops.resize(H.H + 2);
+  if (p->smoother != 0 && p->smoother != 1) return fail(CR_EINVAL, "levels: smoother must be 0 (ICC) or 1 (Schwarz)");
+  H.smoother_kind = p->smoother;
   const double rf = p->ridge_factor > 0 ? p->ridge_factor : 1.5;
   const int nbis = p->ridge_bisections > 0 ? p->ridge_bisections : 30;
   int rc = CR_OK;

@@ -281,3 +281,49 @@ def test_solve_planck_shaped_nside2048(dev):
     m = torch.empty(12 * cfg["nside"] ** 2, dtype=torch.float64, device=dev)
     plan.sht_synth(x - x_true, m)
     assert float(m.abs().max()) < 1e-3, h
+
+
+@pytest.fixture(scope="module")
+def plan32_schwarz(case32, dev):
+    """The oracle's level table with the additive Schwarz (block Jacobi)
+    smoother and fixed ridges: 1e-3 max|A_hat| per level."""
+    c = case32
+    H = c["H"]
+    alphas = [1e-3 * float(np.max(np.abs(pl.Ahat))) for pl in H.pix]
+    levels = [dict(nside_h=l["nside_h"], lmax_h=l["lmax_h"], n_rec=l["n_rec"], fl=l["fl"]) for l in H.levels]
+    plan = binding.Plan(c["cfg"]["lmax"], nside=c["cfg"]["nside"], cl=c["cl"], bl=c["bl"],
+                        ninv=torch.from_numpy(c["ninv"]).to(dev), levels=levels, lmax_dense=H.ld,
+                        ridge_alpha=alphas, smoother="schwarz")
+    return plan, alphas
+
+
+@pytest.mark.parametrize("h", [1, 2])
+def test_schwarz_smoother_matches_oracle(case32, plan32_schwarz, dev, h):
+    """Y_h^T M Y_h r with M = blockdiag(A_hat_pp + alpha I)^-1 (tiles as
+    subdomains): FP32 assembly and tile inverses against the FP64 oracle."""
+    H, prob = case32["H"], case32["prob"]
+    plan, alphas = plan32_schwarz
+    L = H.lmax_h(h)
+    r = rand_alm(L, 170 + h, prob.cl)
+    c = torch.empty(sht.n_lm(L), dtype=torch.complex128, device=dev)
+    plan.smooth(h, torch.from_numpy(r).to(dev), c)
+    ref = H.pix[h - 1].smooth_schwarz(r, alphas[h - 1], prob)
+    assert rel_l2(c.cpu().numpy(), ref) < 2e-4
+
+
+def test_schwarz_solve_converges(case32, dev):
+    """The library's own ridges (search plus the lambda_max <= 1.5 bound)
+    with the Schwarz smoother: mixed-precision PCG reaches the exact
+    answer."""
+    c = case32
+    plan = binding.Plan(c["cfg"]["lmax"], nside=c["cfg"]["nside"], cl=c["cl"], bl=c["bl"],
+                        ninv=torch.from_numpy(c["ninv"]).to(dev), levels="default", smoother="schwarz")
+    prob = c["prob"]
+    x_true = prob.clean(synthetic.draw_prior(c["cl"], index=9))
+    b = torch.from_numpy(operators.apply_A(prob, x_true)).to(dev)
+    x = torch.zeros_like(b)
+    cyc, rel, _ = plan.solve(b, x, eps=1e-20, max_cycles=80, mode=binding.CR_MIXED | binding.CR_PCG, check=False)[:3]
+    assert rel[0] < 1e-9, (cyc, rel)
+    assert rel_l2(x.cpu().numpy(), x_true) < 1e-6
+    for h in range(1, plan.nlevels() + 1):
+        assert plan.level(h)["lambda_max"] <= 1.5 + 1e-9

@@ -129,6 +129,10 @@ def test_checkpoint_rejects_other_inputs_and_damaged_files(inputs, tmp_path):
     damaged = bytearray(raw)
     damaged[len(raw) // 2] ^= 0x40
     open(flip, "wb").write(bytes(damaged))
+    other_smoother = make(inputs, cl, defer_precompute=True, smoother="schwarz")
+    with pytest.raises(binding.CRError) as e:
+        other_smoother.load(path)
+    assert e.value.code == binding.CR_EINVAL
     lazy = make(inputs, cl, defer_precompute=True)
     for bad in (cut, flip, str(tmp_path / "missing.crck")):
         with pytest.raises(binding.CRError) as e:
