@@ -2,6 +2,7 @@
 
     python -m paper_1308_5299_gb300.cases tc --nside 512 --lmax 1023 --nrhs 16
     python -m paper_1308_5299_gb300.cases sht --nside 1024 --lmax 2047 --dtype f32
+    python -m paper_1308_5299_gb300.cases diag --workload nside256_lmax767
 
 ``tc``: batched synthesis, adjoint synthesis and system-matrix application
 with the Legendre contractions on the tensor cores (BF16 operands, FP32
@@ -14,6 +15,10 @@ with a 60 arcmin beam and unit noise).
 
 ``sht``: one synthesis and one adjoint synthesis of a single right-hand side
 in FP32 or FP64.
+
+``diag``: the convergence diagnostics of ``diagnostics`` on a synthetic
+workload (error by scale per W-cycle, smoother-only stagnation on the first
+pixel level, level filters).
 """
 import argparse
 import json
@@ -94,9 +99,43 @@ def sht_case(nside, lmax, warmup, reps, dtype):
     return {"case": "sht", "nside": nside, "lmax": lmax, "dtype": dtype, "reps": reps, "ms": res}
 
 
+def diag_case(name, cycles, iters):
+    """Convergence diagnostics (``diagnostics``) of one synthetic problem:
+    error by scale after each W-cycle, smoother-only error and residual on
+    the first pixel level, and the level filters, sampled at a few l."""
+    from . import diagnostics
+
+    dev = torch.device("cuda", 0)
+    cfg, cl, bl, ninv = synthetic.problem_inputs(name)
+    lmax = cfg["lmax"]
+    plan = binding.Plan(lmax, nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        levels="default")
+    xt = torch.from_numpy(synthetic.draw_prior(cl, index=31)).to(dev)
+    b = torch.empty_like(xt)
+    plan.apply_A(xt, b)
+    ls = sorted({2, 8, 32, 128, lmax // 4, lmax // 2, (3 * lmax) // 4, lmax})
+    cyc = diagnostics.error_by_scale(plan, b, xt, cycles)
+    L1 = plan.level(1)["lmax_h"]
+    x = xt.cpu().numpy()
+    off = lambda mm: mm * (2 * lmax + 3 - mm) // 2
+    xt1 = np.concatenate([x[off(mm):off(mm) + L1 + 1 - mm] for mm in range(L1 + 1)])
+    res, rows = diagnostics.smoother_only(plan, 1, torch.from_numpy(xt1).to(dev), iters)
+    l1 = [l for l in ls if l <= L1]
+    filt = diagnostics.filter_curves(plan)
+    return {"case": "diag", "workload": name, "l": ls,
+            "error_by_scale": [[float(r[l]) for l in ls] for r in cyc],
+            "smoother_only_level1": {"l": l1, "relres": [float(v) for v in res],
+                                     "error_last": [float(rows[-1][l]) for l in l1],
+                                     "error_first": [float(rows[0][l]) for l in l1]},
+            "filters": {str(h): [float(f[l]) for l in ls] for h, f in filt.items()}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["tc", "sht"])
+    ap.add_argument("case", choices=["tc", "sht", "diag"])
+    ap.add_argument("--workload", default="nside256_lmax767")
+    ap.add_argument("--cycles", type=int, default=4)
+    ap.add_argument("--iters", type=int, default=16)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--nside", type=int, default=512)
     ap.add_argument("--lmax", type=int, default=1023)
@@ -107,6 +146,8 @@ def main(argv=None):
     binding.lib()
     if args.case == "tc":
         print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps)))
+    elif args.case == "diag":
+        print(json.dumps(diag_case(args.workload, args.cycles, args.iters)))
     else:
         print(json.dumps(sht_case(args.nside, args.lmax, args.warmup, args.reps, args.dtype)))
 

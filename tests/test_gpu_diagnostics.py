@@ -1,0 +1,71 @@
+"""Convergence diagnostics through the library (Fig. smoother, Fig.
+errors-by-scale, level filters) on the Nside 32 problem."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import cuda_device
+from oracle import geometry, operators, sht
+from paper_1308_5299_gb300 import binding, diagnostics, synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    dev = cuda_device()
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside32_lmax95")
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                        levels="default")
+    return dev, prob, plan, cl
+
+
+def test_error_by_scale_falls_with_cycles(setup):
+    dev, prob, plan, cl = setup
+    xt = prob.clean(synthetic.draw_prior(cl, index=21))
+    b = torch.from_numpy(operators.apply_A(prob, xt)).to(dev)
+    rows = diagnostics.error_by_scale(plan, b, torch.from_numpy(xt).to(dev), 4)
+    assert rows.shape == (4, prob.lmax + 1)
+    assert np.all(np.isnan(rows[:, :2]))  # C_0 = C_1 = 0: not unknowns
+    worst = np.nanmax(rows, axis=1)
+    assert np.all(np.diff(worst) < 0), worst
+    assert worst[-1] < 1e-2 * worst[0]
+
+
+def test_smoother_only_stagnates_where_the_cycle_does_not(setup):
+    """Repeated smoothing on the first pixel level reduces the residual at
+    first, then stalls: its large-scale error stays, while three W-cycles of
+    the full hierarchy are far below it (the point of the multi-level
+    algorithm)."""
+    dev, prob, plan, cl = setup
+    L1 = plan.level(1)["lmax_h"]
+    xt = prob.clean(synthetic.draw_prior(cl, index=22))
+    l, m = sht.lm_arrays(prob.lmax)
+    xt1 = np.concatenate([xt[sht.lm_offset(prob.lmax, mm):sht.lm_offset(prob.lmax, mm) + L1 + 1 - mm]
+                          for mm in range(L1 + 1)])
+    res, rows = diagnostics.smoother_only(plan, 1, torch.from_numpy(xt1).to(dev), 16)
+    print("smoother-only residuals", np.array2string(res, precision=3))
+    assert res[2] < res[0]
+    # stalling: the per-iteration contraction over the second half is much
+    # weaker than over the first three iterations
+    early = (res[3] / res[0]) ** (1.0 / 3.0)
+    late = (res[-1] / res[7]) ** (1.0 / (len(res) - 8))
+    assert late > early, (early, late)
+    b = torch.from_numpy(operators.apply_A(prob, xt)).to(dev)
+    cyc = diagnostics.error_by_scale(plan, b, torch.from_numpy(xt).to(dev), 3)
+    assert np.nanmax(cyc[-1]) < 0.1 * np.nanmax(rows[-1])
+
+
+def test_filter_curves(setup):
+    dev, prob, plan, cl = setup
+    f = diagnostics.filter_curves(plan)
+    H = plan.nlevels()
+    assert sorted(f) == list(range(1, H + 2))
+    for h in range(1, H + 1):
+        Lh = plan.level(h)["lmax_h"]
+        assert np.all(f[h][Lh + 1:] == 0)
+        assert np.all(f[h] <= 1.0 + 1e-12) and np.all(f[h] >= 0)
+        if h > 1:
+            assert np.all(f[h] <= f[h - 1] + 1e-12)
