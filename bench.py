@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--no-cg", action="store_true", help="skip the CG comparison on the Nside 256 workload")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float outer-residual variant")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched mixed-resolution measurement")
-    ap.add_argument("--no-schwarz", action="store_true", help="skip the additive Schwarz smoother variant")
+    ap.add_argument("--schwarz", action="store_true",
+                    help="also time the realization with the additive Schwarz pixel smoother (about a minute)")
     ap.add_argument("--no-graph", action="store_true", help="time the solves launched directly, not as a CUDA graph")
     ap.add_argument("--ref-cycles", type=int, default=2,
                     help="cycles per realization priced by the reference arm (the GPU arm's measured count)")
@@ -754,7 +755,7 @@ def main():
         torch.cuda.synchronize()
         mixed_df = df_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv, x_true, npix)
 
-    schwarz = None if args.no_schwarz else schwarz_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv,
+    schwarz = None if not args.schwarz else schwarz_variant(binding, synthetic, dev, stream, args, cfg, cl, bl, ninv,
                                                              x_true, npix)
     cg_cmp = None if args.no_cg else cg_comparison(binding, synthetic, dev, stream)
     batch = None if args.no_batch else batch_measurement(binding, synthetic, dev, args)
