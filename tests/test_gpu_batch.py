@@ -126,3 +126,42 @@ def test_tensor_core_cycles_in_a_graph_match_direct(top_f32):
         for x, r in zip(xs, refs):
             assert torch.equal(x, r)
         batch.close()
+
+
+@pytest.mark.parametrize("mode,cycles", [(binding.CR_MIXED, 3), (binding.CR_MIXED | binding.CR_TC_CYCLES, 4)])
+def test_batch_graph_at_the_mixed_resolution_sizes(mode, cycles):
+    """The batch of the benchmark's mixed-resolution measurement at its sizes
+    (Nside 1024 / lmax 2047 and Nside 512 / lmax 1023, the first two of its
+    realizations each, the cycle counts it reports): the graph replay equals
+    the uncaptured solves and every realization is within 1 uK max-pixel of
+    its exact answer x_true of b = A x_true."""
+    dev = cuda_device()
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        plans, xs, bs, xts, refs, npx = [], [], [], [], [], []
+        for k, name in enumerate(["nside1024_lmax2047", "nside512_lmax1023"]):
+            cfg, cl, bl, ninv = synthetic.problem_inputs(name)
+            plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                                stream=stream, levels="default")
+            xt = torch.from_numpy(np.stack([synthetic.draw_prior(cl, index=100 * (k + 1) + j)
+                                            for j in range(2)])).to(dev)
+            b = torch.empty_like(xt)
+            plan.apply_A(xt, b)
+            r = torch.zeros_like(b)
+            plan.solve(b, r, eps=0.0, max_cycles=cycles, mode=mode | binding.CR_FIXED, check=False)
+            plans.append(plan)
+            xs.append(torch.zeros_like(b))
+            bs.append(b)
+            xts.append(xt)
+            refs.append(r)
+            npx.append(12 * cfg["nside"] ** 2)
+        batch = binding.Batch(plans, xs, bs, cycles, mode)
+        batch.run()
+        torch.cuda.synchronize()
+        for plan, x, r, xt, n in zip(plans, xs, refs, xts, npx):
+            assert torch.equal(x, r)
+            for j in range(x.shape[0]):
+                m = torch.empty(n, dtype=torch.float64, device=dev)
+                plan.sht_synth(x[j] - xt[j], m)
+                assert float(m.abs().max()) < 1.0
+        batch.close()
