@@ -15,8 +15,10 @@
 // so the loop is uniform from l = m.  a_lm is multiplied by s_lm when staged
 // (synthesis) and the adjoint result by s_lm when written.
 //
-// Each (m, ring pair) starts where |P~_lm| first reaches a precision-dependent
-// threshold tau (FP64 2^-100, FP32 2^-60): the plan-time start tables hold
+// Each (m, ring pair) starts where |P~_lm| first reaches a threshold tau
+// (2^-60 for the transforms of both precisions, with the FP64 state there
+// for the FP64 kernels; 2^-100 for the squared sums of the smoother's
+// diagonal): the plan-time start tables hold
 // that l and the recurrence state there, computed once from the seed
 // P~_mm in scaled FP64 (build_start_tables).  Terms with |P~_lm| < tau are
 // dropped; they are below the rounding of either precision by more than

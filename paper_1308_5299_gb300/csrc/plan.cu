@@ -378,8 +378,11 @@ static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
     a.c = P->d_c;
     a.s = P->d_s;
     a.z = g.d_z;
-    a.ls = g.d_ls64;
-    a.st = g.d_st64;
+    // FP64 starts where |P~_lm| first reaches 2^-60 (the FP32 start table,
+    // with the FP64 state there): the terms left out are below 1e-18 of the
+    // largest and decay geometrically away from the start
+    a.ls = g.d_ls32;
+    a.st = g.d_st64b;
     a.npolar = 0;
     a.df = P->fp64_df;
     a.ls_df = g.d_ls32;
