@@ -21,8 +21,9 @@
 // diagonal): the plan-time start tables hold
 // that l and the recurrence state there, computed once from the seed
 // P~_mm in scaled FP64 (build_start_tables).  Terms with |P~_lm| < tau are
-// dropped; they are below the rounding of either precision by more than
-// twenty orders of magnitude.  Before its start a pair neither steps nor
+// dropped: below FP32 rounding by ten orders of magnitude and below FP64
+// rounding by two, and decaying geometrically away from the start, so their
+// sum stays under the rounding of either sum.  Before its start a pair neither steps nor
 // accumulates; pairs that never reach tau within the band limit hold a zero
 // state.  Each warp classifies every group of 8 l as idle (no pair started
 // yet), full (every live pair started: the unchecked loop) or ramp (per-pair
