@@ -66,7 +66,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 template <bool POLAR>
-__global__ void __launch_bounds__(TS_M) tc_synth_kernel(TsArgs a, int nbp, int yoff) {
+__global__ void __launch_bounds__(TS_M, 4) tc_synth_kernel(TsArgs a, int nbp, int yoff) {
   extern __shared__ __align__(1024) uint8_t tsmem[];
   __shared__ float sc[128], sc2[128], sfac[128];
   __shared__ uint64_t mbar[2];
@@ -123,6 +123,29 @@ __global__ void __launch_bounds__(TS_M) tc_synth_kernel(TsArgs a, int nbp, int y
   tc::fence_after_sync();
   const uint32_t taddr = taddr_s;
   const uint32_t idesc = tc::idesc_bf16_f32(TS_M, TS_N);
+  // B operands: rows 2 r (re) and 2 r + 1 (im), K index k: l = l0 + 2 k
+  // (+1 for odd).  Each thread owns one task -- right-hand side br, parity
+  // bpar, K group bk8 (8 K values of both rows, two 16-byte stores) -- and
+  // loads the next chunk's coefficients into registers before running the
+  // current chunk's recurrence, so their latency hides behind it.
+  static_assert(TS_RHS * 2 * (TS_KC / 8) == TS_M, "one B task per thread");
+  const int br = tid / (2 * (TS_KC / 8)), brem = tid % (2 * (TS_KC / 8));
+  const int bpar = brem & 1, bk8 = brem >> 1;
+  float2 pa[8];
+  float pc = 0.f, pc2 = 0.f, pf = 0.f;
+  auto prefetch = [&](int l0n) {
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int l = l0n + 2 * (bk8 * 8 + kk) + bpar;
+      pa[kk] = (br < a.nrhs && l <= L) ? a.alm[br * a.ld_alm + offa + (l - m)] : make_float2(0.f, 0.f);
+    }
+    const int l = l0n + tid;
+    const bool in = l <= L;
+    pc = in ? a.c[offc + (l - m)] : 0.f;
+    if (POLAR) pc2 = in ? a.c2[offc + (l - m)] : 0.f;
+    pf = in ? a.s[offc + (l - m)] * (a.dl ? a.dl[l] : 1.f) : 0.f;
+  };
+  prefetch(lbeg);
   bool ok = true;
   for (int ch = 0; ch < nch && ok; ++ch) {
     const int stg = ch & 1;
@@ -134,39 +157,25 @@ __global__ void __launch_bounds__(TS_M) tc_synth_kernel(TsArgs a, int nbp, int y
     // the MMAs that read this stage two chunks ago must be done
     if (ch >= 2) ok = tc::mbar_wait(&mbar[stg], ((ch - 2) >> 1) & 1, TS_WAIT);
     if (!ok) break;
-    {
-      const int l = l0 + tid;
-      const bool in = l <= L;
-      sc[tid] = in ? a.c[offc + (l - m)] : 0.f;
-      if (POLAR) sc2[tid] = in ? a.c2[offc + (l - m)] : 0.f;
-      sfac[tid] = in ? a.s[offc + (l - m)] * (a.dl ? a.dl[l] : 1.f) : 0.f;
-    }
+    sc[tid] = pc;
+    if (POLAR) sc2[tid] = pc2;
+    sfac[tid] = pf;
     __syncthreads();
-    // B operands: rows 2 r (re) and 2 r + 1 (im), K index k: l = l0 + 2 k
-    // (+1 for odd); each task packs 8 K values of both rows of one
-    // right-hand side and parity into two 16-byte stores
-    for (int e = tid; e < TS_RHS * 2 * (TS_KC / 8); e += TS_M) {
-      const int r = e / (2 * (TS_KC / 8)), rem = e % (2 * (TS_KC / 8));
-      const int par = rem & 1, k8 = rem >> 1;
+    {
       float vr[8], vi[8];
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
-        const int j = 2 * (k8 * 8 + kk) + par;  // l - l0
-        const int l = l0 + j;
-        vr[kk] = 0.f;
-        vi[kk] = 0.f;
-        if (r < a.nrhs && l <= L) {
-          const float2 av = a.alm[r * a.ld_alm + offa + (l - m)];
-          vr[kk] = av.x * sfac[j];
-          vi[kk] = (m == 0) ? 0.f : av.y * sfac[j];
-        }
+        const int j = 2 * (bk8 * 8 + kk) + bpar;  // l - l0
+        vr[kk] = pa[kk].x * sfac[j];
+        vi[kk] = (m == 0) ? 0.f : pa[kk].y * sfac[j];
       }
-      uint8_t* B = par ? BO : BE;
-      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * r, k8 * 8, TS_KC)) =
+      uint8_t* B = bpar ? BO : BE;
+      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * br, bk8 * 8, TS_KC)) =
           make_uint4(pack_bf16(vr[0], vr[1]), pack_bf16(vr[2], vr[3]), pack_bf16(vr[4], vr[5]), pack_bf16(vr[6], vr[7]));
-      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * r + 1, k8 * 8, TS_KC)) =
+      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * br + 1, bk8 * 8, TS_KC)) =
           make_uint4(pack_bf16(vi[0], vi[1]), pack_bf16(vi[2], vi[3]), pack_bf16(vi[4], vi[5]), pack_bf16(vi[6], vi[7]));
     }
+    if (ch + 1 < nch) prefetch(l0 + 2 * TS_KC);
     // A operands: this thread's row, 8 K values (16 l) per 16-byte store;
     // chunks the pair covers entirely run without per-step checks
     const bool full = (ls <= l0) && (l0 + 2 * TS_KC - 1 <= L);
