@@ -434,7 +434,8 @@ int cr_prolong_add(cr_plan* plan, int h, const void* c_H, void* x_h, int dtype);
 /* c = S_h(r), the error-smoothing correction of level h for residual r:
  * h = 0: (1 - f^1) diag(A)^-1 r (Section 3.2);  h >= 1: Y_h^T M_h Y_h r with
  * M_h the block incomplete-Cholesky smoother (Section 3.5, Eqs.
- * pixel-correction-1..3).  c is overwritten. */
+ * pixel-correction-1..3), or the additive Schwarz smoother of the plan
+ * option `smoother`.  c is overwritten. */
 int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype);
 /* x = A_bottom^-1 b on the bottom level (l <= lmax_dense), dense (FP64). */
 int cr_bottom_solve(cr_plan* plan, const void* b, void* x, int dtype);
@@ -459,8 +460,15 @@ int cr_wcycle(cr_plan* plan, void* x, const void* b, int nrhs, int dtype);
  * FP64; one cycle and one FP64 A per iteration.  Outputs (may be
  * NULL): cycles_out[nrhs], relres_out[nrhs] (final sqrt of the ratio),
  * history[nrhs][max_cycles] (relative residual after each cycle).
+ * Further flags: CR_FIXED (exactly max_cycles cycles, no stop test),
+ * CR_CG (diagonal-preconditioned CG instead of the cycles; needs no levels),
+ * CR_TC_CYCLES with CR_MIXED (the FP32 cycles of up to 16 right-hand sides
+ * batched on the tensor cores; CR_TC_TOP_F32 keeps the top level's
+ * residuals on the CUDA cores).
  * Errors: CR_EDIVERGED (residual grew over two consecutive cycles),
  * CR_EMAXITER, CR_ENONFINITE; x holds the last iterate in each case.
+ * CR_ESTATE: the plan was created with defer_precompute and has not been
+ * loaded or updated since.
  */
 int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int max_cycles, int mode, int* cycles_out,
              double* relres_out, double* history);
