@@ -126,7 +126,8 @@ typedef struct cr_level_spec {
  *   lmax        band limit L of the unknowns (>= 0).
  *   cl, bl      HOST arrays [lmax+1]: prior C_l (>= 0) and b_l p_l.  NULL cl
  *               means "transforms only" (no operator).  NULL bl means 1.
- *   ninv        DEVICE array [npix] of doubles, N^-1 per pixel (0 = masked).
+ *   ninv        DEVICE array [npix] of doubles, N^-1 per pixel (0 = masked),
+ *               finite and >= 0 (else CR_EINVAL naming the first bad pixel).
  *               Copied into the plan at creation.  NULL means no noise term.
  *   stream      cudaStream_t for every call on this plan (NULL = default).
  */

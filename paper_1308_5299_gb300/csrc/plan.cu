@@ -1,4 +1,5 @@
 // Plan construction and the C ABI entry points for transforms and A.
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -737,6 +738,29 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
                                                   cudaMemcpyDeviceToDevice, P->stream)
                                 : cudaMemsetAsync(P->d_ninv, 0, npix * sizeof(double), P->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "copy ninv");
+      }
+      if (!rc && p->ninv) {
+        // N^-1 must be finite and >= 0 (0 = masked): checked on the host in
+        // bounded chunks, so a NaN or a negative weight is refused here
+        // instead of surfacing later as a failed factorisation or a
+        // non-finite residual
+        const int64_t chunk = (int64_t)1 << 22;
+        std::vector<double> h((size_t)std::min<int64_t>(chunk, npix));
+        for (int64_t o = 0; o < npix && !rc; o += chunk) {
+          const int64_t n = std::min(chunk, npix - o);
+          cudaError_t e = cudaMemcpyAsync(h.data(), P->d_ninv + o, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                          P->stream);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+          if (e != cudaSuccess) {
+            rc = cuda_fail(e, "check ninv");
+            break;
+          }
+          for (int64_t i = 0; i < n; ++i)
+            if (!(h[i] >= 0.0) || !std::isfinite(h[i])) {
+              rc = fail(CR_EINVAL, "cr_plan_create: N^-1 must be finite and >= 0 (pixel " + std::to_string(o + i) + ")");
+              break;
+            }
+        }
       }
       if (!rc) {
         ninv32_kernel<<<1024, 256, 0, P->stream>>>(P->d_ninv, P->d_ninv32, npix);
