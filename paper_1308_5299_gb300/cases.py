@@ -3,6 +3,7 @@
     python -m paper_1308_5299_gb300.cases tc --nside 512 --lmax 1023 --nrhs 16
     python -m paper_1308_5299_gb300.cases sht --nside 1024 --lmax 2047 --dtype f32
     python -m paper_1308_5299_gb300.cases diag --workload nside256_lmax767
+    python -m paper_1308_5299_gb300.cases grad --workload nside512_lmax1023 --nrhs 8
 
 ``tc``: batched synthesis, adjoint synthesis and system-matrix application
 with the Legendre contractions on the tensor cores (BF16 operands, FP32
@@ -19,6 +20,9 @@ in FP32 or FP64.
 ``diag``: the convergence diagnostics of ``diagnostics`` on a synthetic
 workload (error by scale per W-cycle, smoother-only stagnation on the first
 pixel level, level filters).
+
+``grad``: forward and backward time of the differentiable constrained
+realizations (``autodiff``) for nrhs right-hand sides.
 """
 import argparse
 import json
@@ -130,9 +134,42 @@ def diag_case(name, cycles, iters):
             "filters": {str(h): [float(f[l]) for l in ls] for h, f in filt.items()}}
 
 
+def grad_case(name, nrhs, warmup):
+    """Differentiation (configuration 5): constrained realizations of nrhs
+    right-hand sides and the gradient of L = sum Re(w* x) with respect to
+    C_l and N^-1 through the adjoint solve (``autodiff.realization``);
+    wall-clock seconds of the forward pass (plan precompute, draws, solves)
+    and of the backward pass (adjoint solves, gradient contractions)."""
+    import time
+
+    from . import autodiff
+
+    dev = torch.device("cuda", 0)
+    cfg, cl, bl, ninv = synthetic.problem_inputs(name)
+    rng = np.random.default_rng(23)
+    w = torch.from_numpy(rng.normal(size=(nrhs, binding.n_lm(cfg["lmax"]))) + 0j).to(dev)
+    res = {}
+    for it in range(warmup + 1):
+        tcl = torch.tensor(cl, dtype=torch.float64, requires_grad=True)
+        tn = torch.tensor(ninv, dtype=torch.float64, device=dev, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = autodiff.realization(tcl, tn, bl, cfg["nside"], seed=5, nrhs=nrhs)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        (torch.conj(w) * x).real.sum().backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res = {"forward_s": t1 - t0, "backward_s": t2 - t1,
+               "grad_cl_finite": bool(torch.isfinite(tcl.grad).all()),
+               "grad_ninv_finite": bool(torch.isfinite(tn.grad).all())}
+    return {"case": "grad", "workload": name, "nrhs": nrhs, **res,
+            "note": "forward includes the plan precompute; solves to a 1e-12 relative residual (mixed PCG)"}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["tc", "sht", "diag"])
+    ap.add_argument("case", choices=["tc", "sht", "diag", "grad"])
     ap.add_argument("--workload", default="nside256_lmax767")
     ap.add_argument("--cycles", type=int, default=4)
     ap.add_argument("--iters", type=int, default=16)
@@ -148,6 +185,8 @@ def main(argv=None):
         print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps)))
     elif args.case == "diag":
         print(json.dumps(diag_case(args.workload, args.cycles, args.iters)))
+    elif args.case == "grad":
+        print(json.dumps(grad_case(args.workload, args.nrhs, args.warmup)))
     else:
         print(json.dumps(sht_case(args.nside, args.lmax, args.warmup, args.reps, args.dtype)))
 
