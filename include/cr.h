@@ -513,7 +513,9 @@ int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, l
  * The array exists on every GPU that loads the library until the process
  * exits.  The first call on a device looks up the array's device address
  * (with that device current); make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
+ * capture.  The address is looked up again when the device's context has
+ * been rebuilt (after cudaDeviceReset), so the call after a reset is again
+ * a "first call".  lmax is at most 16384, as for a plan.  All calls share the one array: calls that overlap on the GPU
  * (different streams, or different host threads on the same device) race, so
  * serialise them.  It calls no cudaMalloc, cudaFree or allocating library
  * routine.  Errors: CR_EINVAL, CR_ECUDA.

@@ -270,11 +270,12 @@ int cr_load(cr_plan* plan, const char* path) {
   if (!r.ok || !got) return bad(CR_EIO, "truncated body");
   if (trailer != want) return bad(CR_EIO, "checksum mismatch");
   std::fclose(r.f);
-  // bottom dofs must be those of the plan's active set
-  int nd_plan = 0;
-  for (int l = 0; l <= H.ld; ++l)
-    if (plan->h_cl[l] > 0) nd_plan += (l == 0) ? 1 : 1 + 2 * l;
-  if (nd != nd_plan) return fail(CR_EINVAL, "cr_load: bottom level does not match the plan's C_l");
+  // the bottom dof map indexes device vectors in the dense solve: it must be
+  // exactly the map the plan builds from its own C_l and band limit, not
+  // merely one of the same length
+  const std::vector<int32_t> dofs_plan = bottom_dof_map(plan, H.ld);
+  if ((size_t)nd * 3 != dofs_plan.size() || dofs != dofs_plan)
+    return fail(CR_EINVAL, "cr_load: bottom level does not match the plan's C_l");
   // upload
   CR_CUDA(cudaStreamSynchronize(plan->stream));
   H.numeric_ready = false;

@@ -307,17 +307,24 @@ int build_top_diag(cr_plan* P, Hierarchy& Hh, const std::vector<double>& f1) {
   return rc;
 }
 
-int build_bottom(cr_plan* P, Hierarchy& Hh) {
-  const int Ld = Hh.ld;
-  std::vector<DofMap> dofs;
+// Real degrees of freedom of the bottom level, in the order of the dense
+// matrix: every active (C_l > 0) l with m = 0, then for m = 1..Ld and
+// l = m..Ld the real and imaginary parts.  Returned as (l, m, part) triples.
+std::vector<int32_t> bottom_dof_map(const cr_plan* P, int Ld) {
+  std::vector<int32_t> d;
   for (int l = 0; l <= Ld; ++l)
-    if (P->h_cl[l] > 0) dofs.push_back({l, 0, 0});
+    if (P->h_cl[l] > 0) d.insert(d.end(), {l, 0, 0});
   for (int m = 1; m <= Ld; ++m)
     for (int l = m; l <= Ld; ++l)
-      if (P->h_cl[l] > 0) {
-        dofs.push_back({l, m, 0});
-        dofs.push_back({l, m, 1});
-      }
+      if (P->h_cl[l] > 0) d.insert(d.end(), {l, m, 0, l, m, 1});
+  return d;
+}
+
+int build_bottom(cr_plan* P, Hierarchy& Hh) {
+  const int Ld = Hh.ld;
+  const std::vector<int32_t> flat = bottom_dof_map(P, Ld);
+  std::vector<DofMap> dofs(flat.size() / 3);
+  for (size_t i = 0; i < dofs.size(); ++i) dofs[i] = {flat[3 * i], flat[3 * i + 1], flat[3 * i + 2]};
   const int nd = (int)dofs.size();
   Hh.nd = nd;
   if (nd == 0) return CR_OK;

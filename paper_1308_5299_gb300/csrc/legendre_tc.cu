@@ -146,8 +146,9 @@ __global__ void __launch_bounds__(TS_M, 4) tc_synth_kernel(TsArgs a, int nbp, in
     pf = in ? a.s[offc + (l - m)] * (a.dl ? a.dl[l] : 1.f) : 0.f;
   };
   prefetch(lbeg);
-  bool ok = true;
-  for (int ch = 0; ch < nch && ok; ++ch) {
+  bool ok = true;  // block-uniform: every wait below is taken by the whole CTA
+  int ncommit = 0;  // chunks whose MMAs have been committed
+  for (int ch = 0; ch < nch; ++ch) {
     const int stg = ch & 1;
     uint8_t* AE = tsmem + stg * TS_STAGE;
     uint8_t* AO = AE + TS_A_BYTES;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(TS_M, 4) tc_synth_kernel(TsArgs a, int nbp, in
     uint8_t* BO = BE + TS_B_BYTES;
     const int l0 = lbeg + ch * 2 * TS_KC;
     // the MMAs that read this stage two chunks ago must be done
-    if (ch >= 2) ok = tc::mbar_wait(&mbar[stg], ((ch - 2) >> 1) & 1, TS_WAIT);
+    if (ch >= 2) ok = tc::mbar_wait_block(&mbar[stg], ((ch - 2) >> 1) & 1, TS_WAIT);
     if (!ok) break;
     sc[tid] = pc;
     if (POLAR) sc2[tid] = pc2;
@@ -223,11 +224,15 @@ __global__ void __launch_bounds__(TS_M, 4) tc_synth_kernel(TsArgs a, int nbp, in
       }
       tc::mma_commit(&mbar[stg]);
     }
+    ncommit = ch + 1;
     __syncthreads();  // the staged tables are rewritten next chunk
   }
-  if (ok) {
-    const int cl = nch - 1;
-    ok = tc::mbar_wait(&mbar[cl & 1], (cl >> 1) & 1, TS_WAIT);
+  // Commits are cumulative, so the last committed chunk's phase covers every
+  // MMA issued.  This wait also runs after a give-up, so that tensor memory
+  // is not freed while an MMA may still write it.
+  if (ncommit > 0) {
+    const int cl = ncommit - 1;
+    if (!tc::mbar_wait_block(&mbar[cl & 1], (cl >> 1) & 1, TS_WAIT)) ok = false;
   }
   tc::fence_after_sync();
   if (ok) {
@@ -445,7 +450,7 @@ __global__ void __launch_bounds__(TA_K) tc_adjoint_kernel(TaArgs a, int nbp, int
   const uint32_t idesc = tc::idesc_bf16_f32(TA_M, TA_N);
   const int nch = (L + 1 - lbeg + TA_M - 1) / TA_M;
   bool ok = true;
-  for (int ch = 0; ch < nch && ok; ++ch) {
+  for (int ch = 0; ch < nch; ++ch) {
     const int l0 = lbeg + ch * TA_M;
     {
       const int l = l0 + tid;
@@ -487,9 +492,16 @@ __global__ void __launch_bounds__(TA_K) tc_adjoint_kernel(TaArgs a, int nbp, int
                      kk > 0 ? 1u : 0u);
       tc::mma_commit(&mbar);
     }
-    ok = tc::mbar_wait(&mbar, ch & 1, TS_WAIT);
+    ok = tc::mbar_wait_block(&mbar, ch & 1, TS_WAIT);
     tc::fence_after_sync();
-    if (ok) {
+    if (!ok) {
+      // one more bounded wait for the MMAs in flight before tensor memory is
+      // freed; the result is reported either way
+      tc::mbar_wait_block(&mbar, ch & 1, TS_WAIT);
+      if (tid == 0) atomicExch(a.status, 1);
+      break;
+    }
+    {
       float ve[32], vo[32];
       tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), ve);
       tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + 32, vo);
@@ -503,8 +515,6 @@ __global__ void __launch_bounds__(TA_K) tc_adjoint_kernel(TaArgs a, int nbp, int
             part[r * rstride + (l - m)] =
                 make_float2((odd ? vo[2 * r] : ve[2 * r]) * sl, (odd ? vo[2 * r + 1] : ve[2 * r + 1]) * sl);
       }
-    } else if (tid == 0) {
-      atomicExch(a.status, 1);
     }
     // every thread's tensor-memory reads are done before the next MMA
     tc::fence_before_sync();

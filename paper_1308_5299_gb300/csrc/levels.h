@@ -41,6 +41,7 @@ void free_smoother(PixLevel& lev);
 
 // dense.cu
 int build_bottom(cr_plan* P, Hierarchy& Hh);
+std::vector<int32_t> bottom_dof_map(const cr_plan* P, int Ld);
 template <typename T> int bottom_solve(cr_plan* P, Hierarchy& Hh, const void* b, void* x);
 int bottom_matrix(cr_plan* P, double* host, int* nd);
 int bottom_upload(cr_plan* P, Hierarchy& Hh, int nd, const double* a, const double* ainv, const int32_t* dofs);

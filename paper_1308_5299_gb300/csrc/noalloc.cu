@@ -11,6 +11,8 @@
 // CR_NOALLOC_SCRATCH_BYTES.  The array belongs to every GPU that loads the
 // library until the process exits; all calls share it and it keeps the
 // contents of the last call.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -44,19 +46,35 @@ __device__ static void hp_ring(int N, int i, double* z, double* sth, int* n, int
 // Legendre stage: F_m(+-z) = sum_l a_lm P~_lm(+-z) per ring pair, with the
 // normalised recurrence P~_l = a_l (z P~_{l-1} - P~_{l-2} / a_{l-1}) evaluated
 // in FP64 with its coefficients computed in place, and a seed
-// log2 P~_mm = 1/2 log2((2m+1)/(4 pi) Gamma(m+1/2) / (sqrt(pi) m!)) + m log2 sin
-// carried as v 2^e to stay clear of underflow.
-__global__ void noalloc_legendre_kernel(const double2* __restrict__ alm, int N, int L, double2* phase) {
+// log2 |P~_mm| = 1/2 [log2((2m+1)/(4 pi)) + sum_{k=1..m} log2(1 - 1/(2k))]
+//               + m log2 sin(theta)
+// carried as v 2^e to stay clear of underflow.  The product of (2k-1)/(2k) is
+// summed term by term with log1p (each term at full relative precision, a
+// fixed-order block reduction) rather than as a difference of two lgamma
+// values, which would lose digits to cancellation at large m.
+constexpr int NOALLOC_NT = 128;
+__global__ void __launch_bounds__(NOALLOC_NT) noalloc_legendre_kernel(const double2* __restrict__ alm, int N, int L,
+                                                                      double2* phase) {
   const int m = blockIdx.x;
   const int nring = 4 * N - 1, npairs = 2 * N;
   const int p = blockIdx.y * blockDim.x + threadIdx.x;
+  __shared__ double s_part[NOALLOC_NT];
+  {
+    double t = 0.0;
+    for (int k = 1 + (int)threadIdx.x; k <= m; k += NOALLOC_NT) t += log1p(-0.5 / k);
+    s_part[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = NOALLOC_NT / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) s_part[threadIdx.x] += s_part[threadIdx.x + w];
+      __syncthreads();
+    }
+  }
   if (p >= npairs) return;
   double z, sth;
   int n, s;
   int64_t off;
   hp_ring(N, p + 1, &z, &sth, &n, &s, &off);
-  const double lgn = 0.5 * (log2((2.0 * m + 1.0) / (4.0 * M_PI)) +
-                            (lgamma(m + 0.5) - lgamma(m + 1.0) - 0.5 * log(M_PI)) / log(2.0)) +
+  const double lgn = 0.5 * (log2((2.0 * m + 1.0) / (4.0 * M_PI)) + s_part[0] / log(2.0)) +
                      (m > 0 ? m * log2(sth) : 0.0);
   int e = (int)floor(lgn);
   double v1 = exp2(lgn - e);
@@ -136,16 +154,49 @@ __global__ void noalloc_ring_kernel(const double2* __restrict__ phase, int N, in
   }
 }
 
+// Device address of the scratch array per device ordinal, with the unique id
+// of the context it was resolved in: after a device reset the primary
+// context (and the module holding the array) is rebuilt, the id changes, and
+// the address is looked up again.
 static std::mutex g_noalloc_mutex;
 static double2* g_noalloc_addr[64] = {nullptr};
+static unsigned long long g_noalloc_ctx[64] = {0};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if none or if the
+// driver cannot report it).  The driver functions are reached through the
+// runtime's entry-point query, so the library does not link libcuda.
+static unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_cur, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+      get_cur = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+  }
+  if (!get_cur || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&c) != CUDA_SUCCESS || !c) return 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace cr
 
 using namespace cr;
 
 extern "C" int cr_sht_synth_noalloc(int nside, int lmax, const void* alm, void* map, void* stream) {
-  if (nside < 1 || (nside & (nside - 1)) || nside > 8192 || lmax < 0)
-    return fail(CR_EINVAL, "cr_sht_synth_noalloc: nside must be a power of two <= 8192 and lmax >= 0");
+  if (nside < 1 || (nside & (nside - 1)) || nside > 8192 || lmax < 0 || lmax > 16384)
+    return fail(CR_EINVAL, "cr_sht_synth_noalloc: nside must be a power of two <= 8192 and 0 <= lmax <= 16384");
   const int nring = 4 * nside - 1;
   const double need = (double)nring * (lmax + 1) * sizeof(double2);
   if (need > (double)CR_NOALLOC_SCRATCH_BYTES)
@@ -159,21 +210,25 @@ extern "C" int cr_sht_synth_noalloc(int nside, int lmax, const void* alm, void* 
   double2* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-      // Host code must not pass the symbol itself to a kernel: resolve its
-      // device address once per device, with that device current.
+    // Host code must not pass the symbol itself to a kernel: resolve its
+    // device address once per device (and again if that device's context
+    // was rebuilt), with that device current.  With no current context yet
+    // the id reads 0, and the symbol lookup below creates the context.
+    const unsigned long long ctx = current_ctx_id();
+    if (!g_noalloc_addr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
       cudaError_t e = cudaGetSymbolAddress((void**)&g_noalloc_addr[dev], g_noalloc_phase);
       if (e != cudaSuccess) {
         g_noalloc_addr[dev] = nullptr;
         return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
       }
+      g_noalloc_ctx[dev] = current_ctx_id();
     }
     scratch = g_noalloc_addr[dev];
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int npairs = 2 * nside;
-  dim3 g1(lmax + 1, (npairs + 127) / 128);
-  { noalloc_legendre_kernel<<<g1, 128, 0, st>>>((const double2*)alm, nside, lmax, scratch); count_launch(); }
+  dim3 g1(lmax + 1, (npairs + NOALLOC_NT - 1) / NOALLOC_NT);
+  { noalloc_legendre_kernel<<<g1, NOALLOC_NT, 0, st>>>((const double2*)alm, nside, lmax, scratch); count_launch(); }
   CR_CHECK_LAUNCH("noalloc_legendre_kernel");
   { noalloc_ring_kernel<<<nring, 256, 0, st>>>(scratch, nside, lmax, (double*)map); count_launch(); }
   CR_CHECK_LAUNCH("noalloc_ring_kernel");

@@ -96,6 +96,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return false;
 }
 
+// The same wait for a whole CTA: every thread polls, and the result is the
+// AND over the block (one barrier), so every thread takes the same branch
+// afterwards -- a thread that gave up never leaves the others in a barrier or
+// in a warp-collective tensor-memory load.  All threads of the block must
+// call it.
+__device__ __forceinline__ bool mbar_wait_block(uint64_t* mbar, uint32_t parity, uint32_t max_iter) {
+  return __syncthreads_and(mbar_wait(mbar, parity, max_iter) ? 1 : 0) != 0;
+}
+
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes (lane = thread)
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   uint32_t r[32];

@@ -46,8 +46,12 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(int K, float* D, float
     }
     tc::mma_commit(&mbar);
   }
-  const bool ok = tc::mbar_wait(&mbar, 0, 1u << 24);
-  if (!ok && lane == 0) atomicExch(status, 2);
+  const bool ok = tc::mbar_wait_block(&mbar, 0, 1u << 24);
+  if (!ok) {
+    // a second bounded wait before tensor memory is freed below
+    tc::mbar_wait_block(&mbar, 0, 1u << 24);
+    if (tid == 0) atomicExch(status, 2);
+  }
   tc::fence_after_sync();
   if (ok) {
     float v[32];

@@ -25,7 +25,9 @@ def dev():
     return cuda_device()
 
 
-@pytest.mark.parametrize("nside,lmax", [(64, 191), (256, 767)])
+# (1, 16384): the largest accepted band limit, where the seed's log-product
+# runs over the most terms (the equator ring's P~_mm does not underflow there)
+@pytest.mark.parametrize("nside,lmax", [(64, 191), (256, 767), (1, 16384)])
 def test_noalloc_matches_plan_synthesis(dev, nside, lmax):
     plan = binding.Plan(lmax, nside=nside)
     npix = 12 * nside * nside
@@ -37,6 +39,15 @@ def test_noalloc_matches_plan_synthesis(dev, nside, lmax):
         binding.sht_synth_noalloc(nside, lmax, a, out)
         torch.cuda.synchronize()
         assert rel_l2(out.cpu().numpy(), ref.cpu().numpy()) < TOL64, (call, nside, lmax)
+
+
+def test_noalloc_rejects_lmax_beyond_plan_range(dev):
+    lib = binding.lib()
+    a = torch.zeros(16, dtype=torch.complex128, device=dev)
+    m = torch.zeros(12, dtype=torch.float64, device=dev)
+    rc = lib.cr_sht_synth_noalloc(1, 16385, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(m.data_ptr()), None)
+    assert rc == -1  # CR_EINVAL before any buffer is touched
+    assert b"16384" in lib.cr_last_error()
 
 
 def test_noalloc_rejects_sizes_beyond_scratch(dev):
