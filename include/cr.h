@@ -197,6 +197,12 @@ typedef struct cr_params {
    * ICC(0) (smallest alpha for which every block factorises, times
    * ridge_factor) and raised under ridge_lambda_target. */
   int smoother;
+  /* triangular sweeps of the ICC(0) smoother: 0 = automatic (levels of at
+   * most 16384 tiles run both sweeps of one application in one cooperative
+   * persistent launch, larger levels one launch per colour); 1 = one launch
+   * per colour on every level; 2 = the cooperative launch wherever the
+   * device supports it.  The same operator either way. */
+  int smoother_sweep;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */
@@ -214,22 +220,22 @@ int cr_plan_create(cr_plan** out, const cr_params* p);
  * Autotuner of the Legendre kernels (Section 2.1 transforms): times the
  * FP32 and FP64 synthesis and adjoint Legendre stages with 2, 4 and 8 ring
  * pairs per thread (the ring block of one CTA: 256, 512 or 1024 pairs of one
- * m) on every grid and band limit the plan transforms on, and keeps the
- * fastest.  Choices are cached for the process per (grid shape, band limit,
+ * m; 16, i.e. 2048 pairs, too for the FP32 adjoint) on every grid and band
+ * limit the plan transforms on, and keeps the fastest.  Choices are cached for the process per (grid shape, band limit,
  * precision, stage) and used by every plan with those shapes; shapes already
  * in the cache are not re-timed.  Untuned shapes use 4.  *nentries (may be
  * NULL) receives the size of the cache.  Synchronous; a few seconds at
  * Nside 2048.  cr_tune_entry reads cache entry i (0 <= i < size): grid ring
  * and pixel counts, band limit, precision in bytes (4 or 8), stage (0
  * synthesis, 1 adjoint), the chosen pairs per thread and the measured ms of
- * the three choices (HOST [3]); any output may be NULL.  Errors: CR_EINVAL,
- * CR_ECUDA.
+ * the choices 2, 4, 8, 16 (HOST [4]; -1 where the stage has no such choice);
+ * any output may be NULL.  Errors: CR_EINVAL, CR_ECUDA.
  */
 int cr_plan_autotune(cr_plan* plan, int* nentries);
 int cr_tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* precision_bytes, int* stage, int* rp,
                   double* ms);
 /* Pin the choice for one (grid shape, band limit, precision, stage): rp 2,
- * 4 or 8.  Errors: CR_EINVAL. */
+ * 4 or 8, or 16 for the FP32 adjoint.  Errors: CR_EINVAL. */
 int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp);
 
 /*
@@ -374,6 +380,19 @@ int cr_batch_destroy(cr_batch* batch);
  */
 int cr_tc_selftest(int K, float* max_abs_err);
 
+/*
+ * Arithmetic peak probe (measurement tooling, no counterpart in the paper):
+ * the sustained FMA rate of one pipe on the current device, in TFLOP/s
+ * (2 flop per FMA), timed with CUDA events on the default stream as the best
+ * of five launches of independent FMA chains that fill every SM.
+ *   kind 0: FP32 scalar FMA; 1: FP32 packed pairs (fma.rn.f32x2);
+ *   2: FP64 FMA.
+ * These are the denominators of the Legendre stages' rooflines (they are
+ * bound by the FMA pipes, not by HBM or a dense contraction).  Allocates and
+ * frees a small output buffer.  Errors: CR_EINVAL, CR_ECUDA.
+ */
+int cr_probe_fma_peak(int kind, double* tflops);
+
 /* Release every resource of the plan (NULL is accepted). */
 int cr_plan_destroy(cr_plan* plan);
 
@@ -494,6 +513,13 @@ int cr_plan_set_timing(cr_plan* plan, int enable);
 long cr_launch_count(void);
 int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, long* launches, double* work,
                    int* count);
+/* The executed work of stage i (same order as cr_plan_timing): for the
+ * Legendre stages, 8 flops per (ring pair, l, m) term the kernels evaluate,
+ * i.e. only the terms at or past each (m, ring pair)'s start in the 2^-60
+ * start table (the dense count of cr_plan_timing credits the skipped region
+ * below the turning point too); 0 for stages without a flop count.
+ * Errors: CR_EINVAL. */
+int cr_plan_timing_exec(cr_plan* plan, int i, double* work_exec);
 
 /*
  * Allocation-free synthesis (no counterpart in the paper).

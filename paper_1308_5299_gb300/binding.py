@@ -69,6 +69,7 @@ class cr_params(ctypes.Structure):
         ("defer_precompute", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("smoother", ctypes.c_int),
+        ("smoother_sweep", ctypes.c_int),
     ]
 
 
@@ -137,6 +138,8 @@ _SIGS = {
     "cr_solve": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                   ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cr_plan_timing_exec": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cr_probe_fma_peak": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_plan_timing": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long),
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -188,6 +191,15 @@ def tc_selftest(K=64):
     return e.value
 
 
+def fma_peak(kind):
+    """Measured FMA-pipe peak in TFLOP/s on the current device: kind 'f32',
+    'f32x2' (packed pairs) or 'f64' (cr_probe_fma_peak)."""
+    k = {"f32": 0, "f32x2": 1, "f64": 2}[kind]
+    t = ctypes.c_double()
+    _check(lib().cr_probe_fma_peak(k, ctypes.byref(t)))
+    return t.value
+
+
 def launch_count():
     """Kernels launched by the library so far in this process."""
     return int(lib().cr_launch_count())
@@ -196,19 +208,20 @@ def launch_count():
 def tune_table():
     """The Legendre autotuner's cached choices: one dict per (grid, band
     limit, precision, stage) with the chosen pairs per thread and the
-    measured ms of 2, 4 and 8 pairs per thread."""
+    measured ms of 2, 4, 8 (and, for the FP32 adjoint, 16) pairs per
+    thread."""
     out = []
     i = 0
     while True:
         nring, lmax, nb, stage, rp = (ctypes.c_int() for _ in range(5))
         npix = ctypes.c_int64()
-        ms = (ctypes.c_double * 3)()
+        ms = (ctypes.c_double * 4)()
         if lib().cr_tune_entry(i, ctypes.byref(nring), ctypes.byref(npix), ctypes.byref(lmax), ctypes.byref(nb),
                                ctypes.byref(stage), ctypes.byref(rp), ms) != 0:
             return out
         out.append(dict(nring=nring.value, npix=npix.value, lmax=lmax.value, precision="f64" if nb.value == 8 else "f32",
                         stage="synthesis" if stage.value == 0 else "adjoint", pairs_per_thread=rp.value,
-                        ms={2: ms[0], 4: ms[1], 8: ms[2]}))
+                        ms={k: ms[i] for i, k in enumerate((2, 4, 8, 16)) if ms[i] >= 0}))
         i += 1
 
 
@@ -245,13 +258,16 @@ class Plan:
 
     def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
                  lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0,
-                 gl_downgrade=0, fp64_df=False, defer_precompute=False, autotune=False, smoother="icc"):
+                 gl_downgrade=0, fp64_df=False, defer_precompute=False, autotune=False, smoother="icc",
+                 smoother_sweep="auto"):
         """levels: None (transforms and A only), "default" (the library's level
         table), or a list of dicts with nside_h, lmax_h, n_rec and fl
         (cumulative filter, length lmax+1).  gl_downgrade: 0 auto, 1 every
         pixel level, -1 off (Gauss-Legendre grids for the levels'
         inverse-noise term).  defer_precompute: skip the C_l-dependent
-        precompute (then ``load`` a checkpoint or ``update_cl``)."""
+        precompute (then ``load`` a checkpoint or ``update_cl``).
+        smoother_sweep: "auto", "per_colour" or "cooperative" (how the ICC(0)
+        triangular sweeps are launched; the same operator)."""
         p = cr_params()
         p.struct_size = ctypes.sizeof(cr_params)
         if gl is not None:
@@ -305,6 +321,7 @@ class Plan:
         if smoother not in ("icc", "schwarz"):
             raise ValueError("smoother: 'icc' (multicolour block ICC(0)) or 'schwarz' (block Jacobi)")
         p.smoother = 0 if smoother == "icc" else 1
+        p.smoother_sweep = {"auto": 0, "per_colour": 1, "cooperative": 2}[smoother_sweep]
         if ridge_alpha is not None:
             ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
             self._keep.append(ra)
@@ -402,6 +419,20 @@ class Plan:
             _check(lib().cr_plan_timing(self._h, i, buf, 64, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w),
                                         None))
             out[buf.value.decode()] = (ms.value, n.value, w.value)
+        return out
+
+    def timing_exec(self):
+        """{stage name: executed work} since timing was enabled: for the
+        Legendre stages the flops of the terms past the start tables."""
+        cnt = ctypes.c_int()
+        _check(lib().cr_plan_timing(self._h, -1, None, 0, None, None, None, ctypes.byref(cnt)))
+        out = {}
+        for i in range(cnt.value):
+            buf = ctypes.create_string_buffer(64)
+            w = ctypes.c_double()
+            _check(lib().cr_plan_timing(self._h, i, buf, 64, None, None, None, None))
+            _check(lib().cr_plan_timing_exec(self._h, i, ctypes.byref(w)))
+            out[buf.value.decode()] = w.value
         return out
 
     # ---- multi-level solver -------------------------------------------------

@@ -17,6 +17,11 @@ with a 60 arcmin beam and unit noise).
 ``sht``: one synthesis and one adjoint synthesis of a single right-hand side
 in FP32 or FP64.
 
+``apply``: A = S^-1 + B Y^T N^-1 Y B of a single right-hand side in FP32
+or FP64 on a named workload (``--workload``), with the per-stage CUDA-event
+times of the plan (Legendre synthesis, fused ring FFTs with N^-1, Legendre
+adjoint) and the stages' dense and executed Legendre flops.
+
 ``diag``: the convergence diagnostics of ``diagnostics`` on a synthetic
 workload (error by scale per W-cycle, smoother-only stagnation on the first
 pixel level, level filters).
@@ -103,6 +108,39 @@ def sht_case(nside, lmax, warmup, reps, dtype):
     return {"case": "sht", "nside": nside, "lmax": lmax, "dtype": dtype, "reps": reps, "ms": res}
 
 
+def apply_case(name, warmup, reps, dtype, tune):
+    """A x for one right-hand side on the workload's observation grid, timed
+    whole and per stage (one realization's outer residual at Nside 2048 is
+    one FP64 call; the FP32 cycles make many FP32 calls)."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    cfg, cl, bl, ninv = synthetic.problem_inputs(name)
+    lmax = cfg["lmax"]
+    plan = binding.Plan(lmax, nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev), stream=stream)
+    if tune:
+        plan.autotune()
+    cdt = torch.complex64 if dtype == "f32" else torch.complex128
+    x = torch.from_numpy(synthetic.draw_prior(cl, index=1)).to(cdt).to(dev)
+    y = torch.empty_like(x)
+    fn = lambda: plan.apply_A(x, y)
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = _time(fn, stream, reps)
+    plan.set_timing(True)
+    for _ in range(reps):
+        fn()
+    st = plan.timing()
+    ex = plan.timing_exec()
+    plan.set_timing(False)
+    stages = {k: {"ms_per_call": v[0] / reps, "work_dense": v[2] / reps, "work_exec": ex.get(k, 0.0) / reps}
+              for k, v in st.items()}
+    return {"case": "apply", "workload": name, "dtype": dtype, "reps": reps, "autotuned": bool(tune),
+            "ms_per_call": ms, "stages": stages,
+            "tune": [t for t in binding.tune_table() if t["lmax"] == lmax] if tune else None}
+
+
 def diag_case(name, cycles, iters):
     """Convergence diagnostics (``diagnostics``) of one synthetic problem:
     error by scale after each W-cycle, smoother-only error and residual on
@@ -169,7 +207,8 @@ def grad_case(name, nrhs, warmup):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["tc", "sht", "diag", "grad"])
+    ap.add_argument("case", choices=["tc", "sht", "apply", "diag", "grad"])
+    ap.add_argument("--tune", action="store_true", help="apply: autotune the Legendre ring blocks first")
     ap.add_argument("--workload", default="nside256_lmax767")
     ap.add_argument("--cycles", type=int, default=4)
     ap.add_argument("--iters", type=int, default=16)
@@ -183,6 +222,8 @@ def main(argv=None):
     binding.lib()
     if args.case == "tc":
         print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps)))
+    elif args.case == "apply":
+        print(json.dumps(apply_case(args.workload, args.warmup, args.reps, args.dtype, args.tune)))
     elif args.case == "diag":
         print(json.dumps(diag_case(args.workload, args.cycles, args.iters)))
     elif args.case == "grad":

@@ -65,6 +65,8 @@ struct PixLevel {
   float* d_LT = nullptr;   // backward-sweep copy: per position p, column p's blocks transposed, then inv(L_pp)^T
   bool lt_valid = false;
   int* d_perm = nullptr;   // tile-ordered level pixel -> RING index
+  int* d_colour_start = nullptr;  // device copy of pat.colour_start
+  int coop_grid = 0;       // CTAs of the one-launch cooperative sweeps (0: one launch per colour)
   int64_t* d_row_ptr = nullptr;
   int* d_row_col = nullptr;
   // column lists for the backward solve: blocks (u, p), u > p
@@ -109,6 +111,8 @@ struct Hierarchy {
   void* map_work = nullptr;   // largest level pixel map (double)
   void* map_work2 = nullptr;
   double* d_dot = nullptr;    // dot-product scratch
+  unsigned int* d_sweep_bar = nullptr;  // grid barrier of the cooperative smoother sweeps [2]
+  int* d_sweep_status = nullptr;        // set when a wait of those sweeps gave up
   double* d_dot_host = nullptr;
   void* ops_store = nullptr;  // per-level operator arrays (solver.cu)
   void* krylov[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // PCG vectors (FP64, top level)
@@ -125,6 +129,7 @@ struct Hierarchy {
   std::vector<double> ridge_fixed;  // given ridges per pixel level, or empty
   bool numeric_ready = false;       // smoothers, top diagonal and bottom built
   int smoother_kind = 0;            // 0 multicolour block ICC(0), 1 additive Schwarz (block Jacobi)
+  int sweep_mode = 0;               // ICC(0) sweeps: 0 auto, 1 one launch per colour, 2 cooperative
 };
 
 }  // namespace cr

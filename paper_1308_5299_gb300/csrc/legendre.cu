@@ -52,6 +52,10 @@ constexpr int LEG_RP = 4;      // default ring pairs per thread
 constexpr int LEG_RP_MIN = 2;  // smallest choice of the autotuner
 constexpr int LEG_CH = 256;
 constexpr int LEG_NW = LEG_NT / 32;
+// The packed FP32 kernels run one warp per CTA: warps never wait for each
+// other (no block barrier; the adjoint writes one partial row per warp), and
+// a warp that finishes early frees its SM slot at once.
+constexpr int L32_NT = 32;
 
 // One recurrence step Q_l = c z Q_{l-1} - Q_{l-2}; returns Q_l and advances
 // the state (s1, s2).
@@ -81,16 +85,16 @@ __device__ __forceinline__ T rstep(T c, T c2, T zw, T& s1, T& s2) {
 // Ring pairs are split into a polar range [0, npolar) and an equatorial
 // range [npolar, npairs); each CTA covers LEG_NT*RP pairs of one range.
 // Block row yb (= blockIdx.y + the launch's row offset) < nbp is polar.
-template <int RP>
+template <int RP, int NT = LEG_NT>
 __device__ __forceinline__ int pair_of(int npolar, int nbp, int yb, int warp, int lane, int j) {
-  const int base = yb < nbp ? yb * (LEG_NT * RP) : npolar + (yb - nbp) * (LEG_NT * RP);
+  const int base = yb < nbp ? yb * (NT * RP) : npolar + (yb - nbp) * (NT * RP);
   return base + warp * (32 * RP) + j * 32 + lane;
 }
 
 // Per-thread pair setup shared by both kernels: start point, state, and the
 // warp's earliest / latest start over its live pairs (a pair is live when it
 // starts at or below L).  Returns false when the warp has no live pair.
-template <typename T, bool POLAR, int RP>
+template <typename T, bool POLAR, int RP, int NT = LEG_NT>
 __device__ __forceinline__ bool load_pairs(const LegArgs<T>& a, int m, int yb, int nbp, int warp, int lane,
                                            int p[RP], int ls[RP], T P1[RP], T P2[RP], T zz[RP], int* wmin,
                                            int* wmax) {
@@ -99,7 +103,7 @@ __device__ __forceinline__ bool load_pairs(const LegArgs<T>& a, int m, int yb, i
   int lo = a.L + 1, hi = m;
 #pragma unroll
   for (int j = 0; j < RP; ++j) {
-    p[j] = pair_of<RP>(a.npolar, nbp, yb, warp, lane, j);
+    p[j] = pair_of<RP, NT>(a.npolar, nbp, yb, warp, lane, j);
     ls[j] = a.L + 1;
     P1[j] = 0;
     P2[j] = 0;
@@ -309,19 +313,15 @@ __device__ __forceinline__ u64 add2(u64 a, u64 b) {
 __device__ __forceinline__ u64 lds2(const float2* p) { return *reinterpret_cast<const u64*>(p); }
 
 template <bool POLAR, int RP>
-__global__ void __launch_bounds__(LEG_NT) leg_synth_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
+__global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
   static_assert(RP % 2 == 0, "pairs per thread must be even");
   constexpr int NP = RP / 2;
   const int m = blockIdx.x;
   const int L = a.L;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  __shared__ float2 sax_all[LEG_NW][LEG_CH], say_all[LEG_NW][LEG_CH], sk_all[LEG_NW][LEG_CH];
-  __shared__ float2 sk2_all[POLAR ? LEG_NW : 1][LEG_CH];
-  float2* sax = sax_all[warp];
-  float2* say = say_all[warp];
-  float2* sk = sk_all[warp];
-  float2* sk2 = sk2_all[POLAR ? warp : 0];
+  const int lane = threadIdx.x;
+  const int warp = 0;
+  __shared__ float2 sax[LEG_CH], say[LEG_CH], sk[LEG_CH];
+  __shared__ float2 sk2[POLAR ? LEG_CH : 1];
 
   float P1[RP], P2[RP], zz[RP];
   int ls[RP], p[RP];
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_f32x2_kernel(LegArgs<float> 
   for (int j = 0; j < RP; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
   const int yb = (int)blockIdx.y + yoff;
   int wmin, wmax;
-  const bool live = load_pairs<float, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
   if (!POLAR) {
 #pragma unroll
@@ -600,6 +600,169 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 adjoint with packed pairs of FP32 lanes.  Two ring pairs step together
+// in one f32x2 instruction: the recurrence (sign-folded as in the packed
+// synthesis: V_l = sigma_l Q_l, V_l = alpha_l z V_{l-1} + V_{l-2}, so the
+// sums come out multiplied by sigma_l, which the partial-row write undoes;
+// the polar difference form needs no sign change) and the accumulation
+// A_l += V_l G, whose two halves hold the sums over the even and the odd
+// members of the thread's pair list and are added once per 8-l group before
+// the warp's shuffle-transpose reduction.  Up to 16 ring pairs per thread
+// spread the reduction over more terms.
+template <bool POLAR, int RP>
+__global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
+  static_assert(RP % 2 == 0, "pairs per thread must be even");
+  constexpr int NP = RP / 2;
+  const int m = blockIdx.x;
+  const int L = a.L;
+  const int lane = threadIdx.x;
+  __shared__ float2 sk[LEG_CH];
+  __shared__ float2 sk2[POLAR ? LEG_CH : 1];
+
+  float P1[RP], P2[RP], zz[RP];
+  int ls[RP], p[RP];
+  float2 GE[RP], GO[RP];
+  const int yb = (int)blockIdx.y + yoff;
+  int wmin, wmax;
+  const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, 0, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+  auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
+  const int pend = POLAR ? a.npolar : a.npairs;
+#pragma unroll
+  for (int j = 0; j < RP; ++j) {
+    GE[j] = make_float2(0.f, 0.f);
+    GO[j] = make_float2(0.f, 0.f);
+    if (p[j] < pend && ls[j] <= L) {
+      const int rn = p[j], rs = a.nring - 1 - p[j];
+      const float2 gn = a.phase[(int64_t)rn * a.ldp + m];
+      const float2 gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : make_float2(0.f, 0.f);
+      GE[j] = cadd(gn, gs);
+      GO[j] = csub(gn, gs);
+      if (!POLAR) {
+        P1[j] *= sgn(ls[j] - 1);
+        P2[j] *= sgn(ls[j] - 2);
+      }
+    }
+  }
+  const int64_t offa = lm_off(L, m);
+  const int64_t offc = lm_off(a.Lc, m);
+  // this warp's partial row: zero before its first group
+  float2* part = a.partial + (int64_t)yb * n_lm(L);
+  const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
+  for (int l = m + lane; l < lbeg; l += 32) part[offa + (l - m)] = make_float2(0.f, 0.f);
+
+  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
+    const int nl = min(LEG_CH, L - l0 + 1);
+    __syncwarp();
+    for (int i = lane; i < nl; i += 32) {
+      const int l = l0 + i;
+      const float c = a.c[offc + (l - m)];
+      if (POLAR) {
+        sk[i] = make_float2(-c, -c);
+        const float c2 = a.c2[offc + (l - m)];
+        sk2[i] = make_float2(c2, c2);
+      } else {
+        const float al = ((l - m) & 1) ? c : -c;
+        sk[i] = make_float2(al, al);
+      }
+    }
+    __syncwarp();
+    for (int i8 = 0; i8 < nl; i8 += 8) {
+      const int lg = l0 + i8;
+      const int ng = min(8, nl - i8);
+      float2 acc[8];
+      if (wmax <= lg && ng == 8) {
+        u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
+          S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
+          S2[q] = pk2(P2[2 * q], P2[2 * q + 1]);
+          EX[q] = pk2(GE[2 * q].x, GE[2 * q + 1].x);
+          EY[q] = pk2(GE[2 * q].y, GE[2 * q + 1].y);
+          OX[q] = pk2(GO[2 * q].x, GO[2 * q + 1].x);
+          OY[q] = pk2(GO[2 * q].y, GO[2 * q + 1].y);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const u64 K = lds2(&sk[i8 + u]);
+          const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
+          u64 AX = 0ull, AY = 0ull;
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            u64 Q;
+            if (POLAR) {
+              const u64 E = fma2(K, Z[q], K2);
+              const u64 D = fma2(E, S1[q], S2[q]);
+              Q = add2(S1[q], D);
+              S2[q] = D;
+            } else {
+              Q = fma2(mul2(K, Z[q]), S1[q], S2[q]);
+              S2[q] = S1[q];
+            }
+            S1[q] = Q;
+            if (u & 1) {
+              AX = q ? fma2(Q, OX[q], AX) : mul2(Q, OX[q]);
+              AY = q ? fma2(Q, OY[q], AY) : mul2(Q, OY[q]);
+            } else {
+              AX = q ? fma2(Q, EX[q], AX) : mul2(Q, EX[q]);
+              AY = q ? fma2(Q, EY[q], AY) : mul2(Q, EY[q]);
+            }
+          }
+          float x0, x1, y0, y1;
+          upk2(AX, x0, x1);
+          upk2(AY, y0, y1);
+          acc[u] = make_float2(x0 + x1, y0 + y1);
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
+          upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (u < ng) {
+            const int l = lg + u;
+            const float K = sk[i8 + u].x;
+            const float K2 = POLAR ? sk2[i8 + u].x : 0.f;
+#pragma unroll
+            for (int j = 0; j < RP; ++j) {
+              if (l >= ls[j]) {
+                float q;
+                if (POLAR) {
+                  const float e = fmaf(K, zz[j], K2);
+                  const float d = fmaf(e, P1[j], P2[j]);
+                  q = P1[j] + d;
+                  P2[j] = d;
+                } else {
+                  q = fmaf(K * zz[j], P1[j], P2[j]);
+                  P2[j] = P1[j];
+                }
+                P1[j] = q;
+                const float2 g = (u & 1) ? GO[j] : GE[j];
+                acc[u].x = fmaf(q, g.x, acc[u].x);
+                acc[u].y = fmaf(q, g.y, acc[u].y);
+              }
+            }
+          }
+        }
+      }
+      warp_reduce8(acc);
+      // lane 4 u holds the warp's sum for l = lg + u: scale by s_lm (and the
+      // recurrence's sign) and write it to the row
+      const int u = lane >> 2;
+      if ((lane & 3) == 0 && u < ng) {
+        const int l = lg + u;
+        const float f = a.s[offc + (l - m)] * (POLAR ? 1.f : sgn(l));
+        part[offa + (l - m)] = cscale(acc[0], f);
+      }
+    }
+  }
+}
+
 // y_lm = dl_out[l] * sum_blk partial[blk][lm] + dadd[l] * xadd_lm; zero at
 // inactive l (dl_out = dadd = 0 there) and Im(a_l0) = 0.
 template <typename T>
@@ -631,19 +794,21 @@ __global__ void leg_finalize_kernel(FinalizeArgs<T> a) {
   }
 }
 
-static inline void pair_blocks(int npolar, int npairs, int rp, int* nbp, int* nbe) {
-  *nbp = (npolar + LEG_NT * rp - 1) / (LEG_NT * rp);
-  *nbe = (npairs - npolar + LEG_NT * rp - 1) / (LEG_NT * rp);
+static inline void pair_blocks(int npolar, int npairs, int rp, int* nbp, int* nbe, int nt = LEG_NT) {
+  *nbp = (npolar + nt * rp - 1) / (nt * rp);
+  *nbe = (npairs - npolar + nt * rp - 1) / (nt * rp);
 }
 
-// ring pairs per thread of a launch: 2, 4 or 8 (other values: the default)
+// ring pairs per thread of a launch: 2, 4 or 8, and 16 for the packed FP32
+// adjoint (other values: the default)
 static inline int legal_rp(int rp) { return (rp == 2 || rp == 4 || rp == 8) ? rp : LEG_RP; }
+static inline int legal_rp_f32adj(int rp) { return (rp == 2 || rp == 4 || rp == 8 || rp == 16) ? rp : LEG_RP; }
 
 template <typename T, int RP>
 static void synth_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (nbp) { leg_synth_f32x2_kernel<true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_synth_f32x2_kernel<false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    if (nbp) { leg_synth_f32x2_kernel<true, RP><<<dim3(a.L + 1, nbp), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_synth_f32x2_kernel<false, RP><<<dim3(a.L + 1, nbe), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   } else {
     if (nbp) { leg_synth_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
     if (nbe) { leg_synth_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
@@ -652,8 +817,13 @@ static void synth_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st)
 
 template <typename T, int RP>
 static void adjoint_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
-  if (nbp) { leg_adjoint_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { leg_adjoint_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  if constexpr (sizeof(T) == 4) {
+    if (nbp) { leg_adjoint_f32x2_kernel<true, RP><<<dim3(a.L + 1, nbp), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_adjoint_f32x2_kernel<false, RP><<<dim3(a.L + 1, nbe), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  } else {
+    if (nbp) { leg_adjoint_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_adjoint_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  }
 }
 
 template <typename T>
@@ -663,7 +833,7 @@ int launch_leg_synth(const LegArgs<T>& a, cudaStream_t st) {
     if (a.df) return launch_leg_synth_df(a, st);
   int nbp, nbe;
   const int rp = legal_rp(a.rp_synth);
-  pair_blocks(a.npolar, a.npairs, rp, &nbp, &nbe);
+  pair_blocks(a.npolar, a.npairs, rp, &nbp, &nbe, sizeof(T) == 4 ? L32_NT : LEG_NT);
   if (rp == 2) synth_launch<T, 2>(a, nbp, nbe, st);
   else if (rp == 8) synth_launch<T, 8>(a, nbp, nbe, st);
   else synth_launch<T, 4>(a, nbp, nbe, st);
@@ -684,11 +854,16 @@ int launch_leg_adjoint(const LegArgs<T>& a, const FinalizeArgs<T>& f, cudaStream
     }
   }
   if (!done) {
-    const int rp = legal_rp(a.rp_adj);
-    pair_blocks(a.npolar, a.npairs, rp, &nbp, &nbe);
+    const int rp = sizeof(T) == 4 ? legal_rp_f32adj(a.rp_adj) : legal_rp(a.rp_adj);
+    pair_blocks(a.npolar, a.npairs, rp, &nbp, &nbe, sizeof(T) == 4 ? L32_NT : LEG_NT);
     if (rp == 2) adjoint_launch<T, 2>(a, nbp, nbe, st);
     else if (rp == 8) adjoint_launch<T, 8>(a, nbp, nbe, st);
-    else adjoint_launch<T, 4>(a, nbp, nbe, st);
+    else if constexpr (sizeof(T) == 4) {
+      if (rp == 16) adjoint_launch<T, 16>(a, nbp, nbe, st);
+      else adjoint_launch<T, 4>(a, nbp, nbe, st);
+    } else {
+      adjoint_launch<T, 4>(a, nbp, nbe, st);
+    }
     CR_CHECK_LAUNCH("leg_adjoint_kernel");
   }
   FinalizeArgs<T> ff = f;
@@ -813,10 +988,11 @@ int build_start_tables(cr_plan* P, Grid& g) {
 }
 
 // upper bound on the partial rows of the adjoint: the polar and equatorial
-// ranges of LEG_NT * RP pairs for the smallest RP, or the double-float
+// ranges of 32 * RP pairs (one-warp FP32 blocks; the FP64 blocks of
+// LEG_NT * RP pairs are fewer) for the smallest RP, or the double-float
 // kernels' blocks
 int leg_partial_blocks(int npairs) {
-  return std::max((npairs + LEG_NT * LEG_RP_MIN - 1) / (LEG_NT * LEG_RP_MIN) + 1, df_pair_blocks(npairs));
+  return std::max((npairs + L32_NT * LEG_RP_MIN - 1) / (L32_NT * LEG_RP_MIN) + 1, df_pair_blocks(npairs));
 }
 
 template int launch_leg_synth<double>(const LegArgs<double>&, cudaStream_t);

@@ -50,6 +50,7 @@ void Timing::flush() {
       v.ms += ms;
       v.n += 1;
       v.work += r.work;
+      v.work_exec += r.work_exec;
     }
     pool.push_back(r.a);
     pool.push_back(r.b);
@@ -65,13 +66,13 @@ Timing::~Timing() {
   for (auto e : pool) cudaEventDestroy(e);
 }
 
-TimerScope::TimerScope(Timing& t, cudaStream_t st, const char* name, double work)
-    : TimerScope(t, st, std::string(name), work) {}
+TimerScope::TimerScope(Timing& t, cudaStream_t st, const char* name, double work, double work_exec)
+    : TimerScope(t, st, std::string(name), work, work_exec) {}
 
-TimerScope::TimerScope(Timing& t, cudaStream_t st, const std::string& name, double work)
+TimerScope::TimerScope(Timing& t, cudaStream_t st, const std::string& name, double work, double work_exec)
     : t_(&t), st_(st), idx_(-1) {
   if (!t.enabled) return;
-  Timing::Rec r{name, t.get(), t.get(), work};
+  Timing::Rec r{name, t.get(), t.get(), work, work_exec};
   cudaEventRecord(r.a, st);
   t.pending.push_back(r);
   idx_ = (int)t.pending.size() - 1;
@@ -356,8 +357,13 @@ struct TuneKey {
 };
 struct TuneVal {
   int rp;
-  double ms[3];  // measured ms for 2, 4, 8 pairs per thread
+  double ms[4];  // measured ms for 2, 4, 8, 16 pairs per thread (-1: not a choice of this stage)
 };
+
+// 16 ring pairs per thread exist for the packed FP32 adjoint only
+static bool rp_allowed(int rp, int bytes, int stage) {
+  return rp == 2 || rp == 4 || rp == 8 || (rp == 16 && bytes == 4 && stage == 1);
+}
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune;
 
@@ -436,8 +442,36 @@ template <typename T>
 static const char* ptag() {
   return sizeof(T) == 8 ? "_f64" : "_f32";
 }
-// algorithmic flops of one Legendre stage on grid g at band limit L
+// algorithmic flops of one Legendre stage on grid g at band limit L (the
+// dense count: every ring pair and (l, m))
 static double leg_work(const Grid& g, int L) { return 8.0 * g.npairs * (double)n_lm(L); }
+
+// flops of the terms one Legendre stage evaluates: 8 per (ring pair, l, m)
+// at or past the (m, pair)'s start in the 2^-60 start table, which both
+// precisions use.  Counted once per (grid, band limit) from the table on the
+// host while timing is on (it synchronises, so not inside a graph capture,
+// where the dense count stands in).
+static double leg_work_exec(cr_plan* P, const Grid& gc, int L) {
+  if (!P->timing.enabled || L < 0) return 0.0;
+  Grid& g = const_cast<Grid&>(gc);
+  auto it = g.exec_terms.find(L);
+  if (it != g.exec_terms.end()) return 8.0 * it->second;
+  if (P->capturing || !g.d_ls32 || L > g.Lseed) return leg_work(g, L);
+  std::vector<int> ls((size_t)(L + 1) * g.npairs);
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess ||
+      cudaMemcpy(ls.data(), g.d_ls32, ls.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return leg_work(g, L);
+  double n = 0.0;
+  for (int m = 0; m <= L; ++m) {
+    const int* row = ls.data() + (size_t)m * g.npairs;
+    int64_t s = 0;
+    for (int p = 0; p < g.npairs; ++p)
+      if (row[p] <= L) s += L + 1 - row[p];
+    n += (double)s;
+  }
+  g.exec_terms[L] = n;
+  return 8.0 * n;
+}
 // algorithmic HBM bytes of one ring-FFT stage: the phase array [nring][L+1]
 // once, plus `maps` pixel arrays of T (map in or out, pixel diagonal, copy)
 template <typename T>
@@ -452,7 +486,8 @@ int do_synth(cr_plan* P, const Grid& g, int L, const void* alm, void* map, const
   a.dl = dl;
   int rc;
   {
-    TimerScope ts(P->timing, P->stream, std::string("legendre_synth") + ptag<T>(), leg_work(g, L));
+    TimerScope ts(P->timing, P->stream, std::string("legendre_synth") + ptag<T>(), leg_work(g, L),
+                  leg_work_exec(P, g, L));
     rc = launch_leg_synth<T>(a, P->stream);
   }
   if (rc) return rc;
@@ -480,7 +515,8 @@ int do_adjoint(cr_plan* P, const Grid& g, int L, const void* map, void* alm, con
   f.xadd = reinterpret_cast<const typename Tr<T>::C*>(xadd);
   f.accumulate = accumulate;
   f.out = reinterpret_cast<typename Tr<T>::C*>(alm);
-  TimerScope ts(P->timing, P->stream, std::string("legendre_adjoint") + ptag<T>(), leg_work(g, L));
+  TimerScope ts(P->timing, P->stream, std::string("legendre_adjoint") + ptag<T>(), leg_work(g, L),
+                  leg_work_exec(P, g, L));
   return launch_leg_adjoint<T>(a, f, P->stream);
 }
 
@@ -494,7 +530,8 @@ int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const 
   a.dl = dl_in;
   int rc;
   {
-    TimerScope ts(P->timing, P->stream, std::string("legendre_synth") + ptag<T>(), leg_work(g, L));
+    TimerScope ts(P->timing, P->stream, std::string("legendre_synth") + ptag<T>(), leg_work(g, L),
+                  leg_work_exec(P, g, L));
     rc = launch_leg_synth<T>(a, P->stream);
   }
   if (rc) return rc;
@@ -514,7 +551,8 @@ int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const 
   f.xadd = reinterpret_cast<const typename Tr<T>::C*>(x);
   f.bsub = reinterpret_cast<const typename Tr<T>::C*>(bsub);
   f.out = reinterpret_cast<typename Tr<T>::C*>(y);
-  TimerScope ts(P->timing, P->stream, std::string("legendre_adjoint") + ptag<T>(), leg_work(g, L));
+  TimerScope ts(P->timing, P->stream, std::string("legendre_adjoint") + ptag<T>(), leg_work(g, L),
+                  leg_work_exec(P, g, L));
   return launch_leg_adjoint<T>(a, f, P->stream);
 }
 
@@ -558,9 +596,10 @@ static int tune_stage(cr_plan* P, const Grid& g, int L, int stage, int reps) {
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) rc = cuda_fail(e, "autotune setup");
-  TuneVal v{4, {0.0, 0.0, 0.0}};
-  const int rps[3] = {2, 4, 8};
-  for (int i = 0; i < 3 && !rc; ++i) {
+  TuneVal v{4, {0.0, 0.0, 0.0, -1.0}};
+  const int rps[4] = {2, 4, 8, 16};
+  const int nchoice = rp_allowed(16, (int)sizeof(T), stage) ? 4 : 3;
+  for (int i = 0; i < nchoice && !rc; ++i) {
     LegArgs<T> a = leg_args<T>(P, g, L);
     a.df = 0;
     a.alm = alm;
@@ -579,7 +618,7 @@ static int tune_stage(cr_plan* P, const Grid& g, int L, int stage, int reps) {
   }
   if (!rc) {
     int best = 1;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < nchoice; ++i)
       if (v.ms[i] < v.ms[best]) best = i;
     v.rp = rps[best];
   }
@@ -628,15 +667,15 @@ int tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* bytes, int* sta
   if (stage) *stage = it->first.stage;
   if (rp) *rp = it->second.rp;
   if (ms)
-    for (int k = 0; k < 3; ++k) ms[k] = it->second.ms[k];
+    for (int k = 0; k < 4; ++k) ms[k] = it->second.ms[k];
   return CR_OK;
 }
 
 int tune_set(int nring, int64_t npix, int lmax, int bytes, int stage, int rp) {
-  if ((rp != 2 && rp != 4 && rp != 8) || (bytes != 4 && bytes != 8) || (stage != 0 && stage != 1) || lmax < 0)
+  if ((bytes != 4 && bytes != 8) || (stage != 0 && stage != 1) || lmax < 0 || !rp_allowed(rp, bytes, stage))
     return fail(CR_EINVAL, "cr_tune_set: bad choice");
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[TuneKey{nring, npix, lmax, bytes, stage}] = TuneVal{rp, {0.0, 0.0, 0.0}};
+  g_tune[TuneKey{nring, npix, lmax, bytes, stage}] = TuneVal{rp, {0.0, 0.0, 0.0, -1.0}};
   return CR_OK;
 }
 
@@ -901,7 +940,7 @@ float2* tc_slot(cr_plan* P, const Grid& g, int L, int r) {
 int tc_synth_stage(cr_plan* P, const Grid& g, int L, const float2* x, int nr, const float* dl) {
   LegArgs<float> la = leg_args<float>(P, g, L);
   la.dl = dl;
-  TimerScope ts(P->timing, P->stream, "legendre_synth_tc", leg_work(g, L) * nr);
+  TimerScope ts(P->timing, P->stream, "legendre_synth_tc", leg_work(g, L) * nr, leg_work_exec(P, g, L) * nr);
   return launch_tc_synth(la, x, n_lm(L), nr, tc_slot(P, g, L, 0), P->d_tc_status, P->stream);
 }
 
@@ -913,7 +952,8 @@ int tc_adjoint_tail(cr_plan* P, const Grid& g, int L, int nr, const TcTail& t) {
   const int64_t nlm = n_lm(L);
   int nblk = 0, rc;
   {
-    TimerScope ts(P->timing, P->stream, "legendre_adjoint_tc", leg_work(g, L) * nr);
+    TimerScope ts(P->timing, P->stream, "legendre_adjoint_tc", leg_work(g, L) * nr,
+                  leg_work_exec(P, g, L) * nr);
     rc = launch_tc_adjoint(la, tc_slot(P, g, L, 0), nr, reinterpret_cast<float2*>(P->tc_partial), &nblk,
                            P->d_tc_status, P->stream);
   }
@@ -1128,6 +1168,16 @@ int cr_plan_timing(cr_plan* plan, int i, char* name, int name_cap, double* ms, l
   if (ms) *ms = it->second.ms;
   if (launches) *launches = it->second.n;
   if (work) *work = it->second.work;
+  return CR_OK;
+}
+
+int cr_plan_timing_exec(cr_plan* plan, int i, double* work_exec) {
+  if (!plan || !work_exec) return fail(CR_EINVAL, "cr_plan_timing_exec: null argument");
+  plan->timing.flush();
+  if (i < 0 || i >= (int)plan->timing.acc.size()) return fail(CR_EINVAL, "cr_plan_timing_exec: index out of range");
+  auto it = plan->timing.acc.begin();
+  std::advance(it, i);
+  *work_exec = it->second.work_exec;
   return CR_OK;
 }
 

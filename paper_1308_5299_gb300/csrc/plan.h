@@ -65,6 +65,10 @@ struct Grid {
   int* d_ls32 = nullptr;
   float2* d_st32 = nullptr;
   double2* d_st64b = nullptr;  // FP64 state at the FP32 start (double-float kernels)
+  // number of (ring pair, l, m) terms the Legendre kernels evaluate at band
+  // limit L -- those at or past the 2^-60 start of each (m, pair) -- filled
+  // on demand from the start table (per-stage timing only)
+  std::map<int, double> exec_terms;
 };
 
 // Scratch sizes for transforms at band limit L on a grid.
@@ -81,11 +85,13 @@ struct Timing {
     std::string name;
     cudaEvent_t a, b;
     double work;
+    double work_exec;
   };
   struct Acc {
     double ms = 0.0;
     long n = 0;
-    double work = 0.0;  // algorithmic flops (or bytes) of the recorded launches
+    double work = 0.0;       // algorithmic flops (or bytes) of the recorded launches
+    double work_exec = 0.0;  // Legendre stages: flops of the terms actually evaluated
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
@@ -97,8 +103,8 @@ struct Timing {
 
 class TimerScope {
  public:
-  TimerScope(Timing& t, cudaStream_t st, const char* name, double work = 0.0);
-  TimerScope(Timing& t, cudaStream_t st, const std::string& name, double work = 0.0);
+  TimerScope(Timing& t, cudaStream_t st, const char* name, double work = 0.0, double work_exec = 0.0);
+  TimerScope(Timing& t, cudaStream_t st, const std::string& name, double work = 0.0, double work_exec = 0.0);
   ~TimerScope();
 
  private:

@@ -455,6 +455,19 @@ __device__ __forceinline__ float4 block_gemv_w(const float* __restrict__ B, cons
   return acc;
 }
 
+// the same product with the block in shared memory (plain loads: the
+// read-only global path of block_gemv_w cannot address shared memory)
+__device__ __forceinline__ float4 block_gemv_w_smem(const float* B, const float* __restrict__ v, int rq, int jg,
+                                                    float4 acc) {
+  const float4* B4 = reinterpret_cast<const float4*>(B);
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int j = jg * 4 + jj;
+    acc = f4fma(B4[j * (TK / 4) + rq], v[j], acc);
+  }
+  return acc;
+}
+
 // rows of the result for threads tid < 64 (sum of the 16 column groups)
 __device__ __forceinline__ float reduce_groups_w(float4 acc, float4 (*part)[16], int rq, int jg, int tid) {
   part[jg][rq] = acc;
@@ -519,6 +532,238 @@ __global__ void __launch_bounds__(TKW) bwd_colour_w_kernel(const float* LT, cons
   if (tid < TK) {
     y[(int64_t)p * TK + tid] = s;
     map_out[perm[(int64_t)p * TK + tid]] = (T)s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Both triangular sweeps of one smoother application in ONE persistent,
+// cooperatively launched kernel (levels with few tiles per colour, where one
+// launch per colour leaves the GPU waiting on launch and load latency).
+//
+// Each CTA owns tiles p = colour_start[c] + blockIdx.x + k gridDim.x of every
+// colour, forward colours first, then backward.  A tile's factor blocks are
+// contiguous (row p of L: its lower blocks then inv(L_pp); for the backward
+// sweep the transposed column blocks then inv(L_pp)^T in LT), so the CTA's
+// whole sequence of 16 KB blocks is known at launch: thread 0 streams it
+// into a ring of SW_NS shared-memory slots with bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on one mbarrier per slot),
+// SW_NS blocks ahead of the arithmetic -- across tile and colour boundaries,
+// so the loads for the next colour run during the grid-wide barrier.  The
+// 256 threads compute each block's product from shared memory as the
+// 256-thread per-colour kernels do.  Colours are separated by a grid barrier
+// (a counter and a generation word in global memory); the work vector y is
+// read through L2 (ld.global.cg) because other SMs wrote it.
+//
+// Every wait is bounded (slot mbarriers and the grid barrier): on a timeout
+// the CTA records it in *status, waits (bounded) for its copies in flight
+// and leaves; the other CTAs then time out at their next barrier and leave
+// too, and the host reports the status as an error.
+constexpr int SW_NT = 256;
+constexpr int SW_NS = 12;                           // shared-memory block slots
+constexpr int SW_BLOCK_BYTES = TK * TK * (int)sizeof(float);
+constexpr uint32_t SW_WAIT = 1u << 22;              // polls per wait (about a second)
+
+struct SweepArgs {
+  const float* L;
+  const float* LT;
+  const int64_t* row_ptr;
+  const int* row_col;
+  const int64_t* col_ptr;
+  const int* col_row;
+  const int* perm;
+  const int* colour_start;  // [ncol + 1]
+  int ncol;
+  float* y;
+  unsigned int* bar;        // [2]: arrivals, generation (arrivals zero at launch)
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t sw_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void sw_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sw_smem(mbar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sw_smem(dst)),
+      "l"(src), "r"(bytes), "r"(sw_smem(mbar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool sw_wait(uint64_t* mbar, uint32_t parity) {
+  const uint32_t a = sw_smem(mbar);
+  for (uint32_t it = 0; it < SW_WAIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// grid-wide barrier of the cooperative launch; false (for the whole CTA) if
+// the wait gave up
+__device__ bool sw_grid_barrier(unsigned int* bar, unsigned int nblk) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    const unsigned int gen = ld_acquire_gpu(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblk - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint32_t it = 0;
+      while (ld_acquire_gpu(bar + 1) == gen) {
+        if (++it > SW_WAIT) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Position in a CTA's block sequence: sweep (0 forward, 1 backward), colour,
+// tile, block within the tile.
+struct SwCursor {
+  int sweep, c, p, j;
+  bool done;
+};
+
+__device__ __forceinline__ int sw_nblk(const SweepArgs& a, int sweep, int p) {
+  return sweep == 0 ? (int)(a.row_ptr[p + 1] - a.row_ptr[p]) : (int)(a.col_ptr[p + 1] - a.col_ptr[p]) + 1;
+}
+__device__ __forceinline__ const float* sw_src(const SweepArgs& a, int sweep, int p, int j) {
+  return sweep == 0 ? a.L + (a.row_ptr[p] + j) * (int64_t)(TK * TK)
+                    : a.LT + (a.col_ptr[p] + p + j) * (int64_t)(TK * TK);
+}
+// first tile of this CTA at or after colour c of the sweep (skipping colours
+// it has no tile in); done when the sequence is exhausted
+__device__ void sw_seek(const SweepArgs& a, SwCursor& u) {
+  for (;;) {
+    if (u.sweep == 0 ? u.c >= a.ncol : u.c < 0) {
+      if (u.sweep == 0) {
+        u.sweep = 1;
+        u.c = a.ncol - 1;
+        continue;
+      }
+      u.done = true;
+      return;
+    }
+    u.p = a.colour_start[u.c] + (int)blockIdx.x;
+    u.j = 0;
+    if (u.p < a.colour_start[u.c + 1]) return;
+    u.c += u.sweep == 0 ? 1 : -1;
+  }
+}
+__device__ void sw_advance(const SweepArgs& a, SwCursor& u) {
+  if (++u.j < sw_nblk(a, u.sweep, u.p)) return;
+  u.j = 0;
+  u.p += (int)gridDim.x;
+  if (u.p < a.colour_start[u.c + 1]) return;
+  u.c += u.sweep == 0 ? 1 : -1;
+  sw_seek(a, u);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SW_NT, 1) sweep_coop_kernel(SweepArgs a, const T* map_in, T* map_out) {
+  extern __shared__ __align__(128) unsigned char sw_raw[];
+  float* slots = reinterpret_cast<float*>(sw_raw);
+  __shared__ uint64_t mbar[SW_NS];
+  __shared__ float vs[8][TK];
+  __shared__ float ts[TK];
+  __shared__ float4 part[16][16];
+  const int tid = threadIdx.x, rq = tid & 15, jg = tid >> 4;
+
+  // producer state (thread 0): the next block to load
+  SwCursor pc{0, 0, 0, 0, false};
+  long issued = 0;
+  if (tid == 0) {
+    for (int i = 0; i < SW_NS; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sw_smem(&mbar[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sw_seek(a, pc);
+    while (!pc.done && issued < SW_NS) {
+      sw_bulk_load(slots + (issued % SW_NS) * (TK * TK), sw_src(a, pc.sweep, pc.p, pc.j), SW_BLOCK_BYTES,
+                   &mbar[issued % SW_NS]);
+      ++issued;
+      sw_advance(a, pc);
+    }
+  }
+  __syncthreads();
+
+  long used = 0;  // blocks consumed
+  bool ok = true;
+  // wait for the next block; then thread 0 refills the slot freed by the
+  // previous block (every thread has passed the wait's barrier, so all are
+  // done with it)
+  auto next_block = [&]() -> const float* {
+    const int slot = (int)(used % SW_NS);
+    ok = __syncthreads_and(sw_wait(&mbar[slot], (uint32_t)((used / SW_NS) & 1)) ? 1 : 0) != 0;
+    if (!ok) return nullptr;
+    if (tid == 0 && used > 0 && !pc.done) {
+      const long fs = (used - 1) % SW_NS;
+      sw_bulk_load(slots + fs * (TK * TK), sw_src(a, pc.sweep, pc.p, pc.j), SW_BLOCK_BYTES, &mbar[fs]);
+      ++issued;
+      sw_advance(a, pc);
+    }
+    ++used;
+    return slots + slot * (TK * TK);
+  };
+
+  for (int step = 0; step < 2 * a.ncol && ok; ++step) {
+    const int sweep = step < a.ncol ? 0 : 1;
+    const int c = sweep == 0 ? step : 2 * a.ncol - 1 - step;
+    for (int p = a.colour_start[c] + (int)blockIdx.x; p < a.colour_start[c + 1] && ok; p += (int)gridDim.x) {
+      const int nb = sw_nblk(a, sweep, p) - 1;  // off-diagonal blocks
+      const int64_t b0 = sweep == 0 ? a.row_ptr[p] : a.col_ptr[p];
+      const int* nbr = sweep == 0 ? a.row_col : a.col_row;
+      for (int e = tid; e < nb * TK; e += SW_NT)
+        vs[e / TK][e % TK] = __ldcg(a.y + (int64_t)nbr[b0 + e / TK] * TK + (e % TK));
+      float r = 0.f;
+      if (tid < TK)
+        r = sweep == 0 ? (float)map_in[a.perm[(int64_t)p * TK + tid]] : __ldcg(a.y + (int64_t)p * TK + tid);
+      __syncthreads();
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < nb; ++k) {
+        const float* B = next_block();
+        if (!ok) break;
+        acc = block_gemv_w_smem(B, vs[k], rq, jg, acc);
+      }
+      if (!ok) break;
+      const float s1 = reduce_groups_w(acc, part, rq, jg, tid);
+      if (tid < TK) ts[tid] = r - s1;
+      const float* D = next_block();  // the barrier inside also publishes ts
+      if (!ok) break;
+      acc = block_gemv_w_smem(D, ts, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
+      const float v = reduce_groups_w(acc, part, rq, jg, tid);
+      if (tid < TK) {
+        a.y[(int64_t)p * TK + tid] = v;
+        if (sweep == 1) map_out[a.perm[(int64_t)p * TK + tid]] = (T)v;
+      }
+    }
+    if (!ok) break;
+    if (step + 1 < 2 * a.ncol) ok = sw_grid_barrier(a.bar, gridDim.x);
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(a.status, 1);
+    // the copies still in flight land in this CTA's shared memory: wait for
+    // them (bounded) before the CTA leaves
+    for (long b = used; b < issued; ++b) sw_wait(&mbar[b % SW_NS], (uint32_t)((b / SW_NS) & 1));
   }
 }
 
@@ -687,6 +932,36 @@ int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
   return CR_OK;
 }
 
+// Levels with at most SW_MAX_TILES tiles run both triangular sweeps of a
+// smoother application in one cooperative launch of
+// min(SMs, largest colour) CTAs (one per SM: the block slots take most of
+// its shared memory); larger levels keep one launch per colour, whose wide
+// colours stream the factor at close to the HBM rate.
+constexpr int SW_MAX_TILES = 16384;
+
+static int choose_coop_grid(cr_plan* P, PixLevel& lev) {
+  lev.coop_grid = 0;
+  const BlockPattern& pat = lev.pat;
+  const int mode = P->hier ? P->hier->sweep_mode : 0;
+  if ((P->hier && P->hier->smoother_kind == 1) || mode == 1 || (mode == 0 && pat.ntile > SW_MAX_TILES)) return CR_OK;
+  int dev = 0, nsm = 0, coop = 0, nb_d = 0, nb_f = 0;
+  CR_CUDA(cudaGetDevice(&dev));
+  CR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return CR_OK;
+  const int smem = SW_NS * SW_BLOCK_BYTES;
+  CR_CUDA(cudaFuncSetAttribute(sweep_coop_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CR_CUDA(cudaFuncSetAttribute(sweep_coop_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_d, sweep_coop_kernel<double>, SW_NT, smem));
+  CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, sweep_coop_kernel<float>, SW_NT, smem));
+  if (nb_d < 1 || nb_f < 1) return CR_OK;
+  int widest = 0;
+  for (size_t c = 0; c + 1 < pat.colour_start.size(); ++c)
+    widest = std::max(widest, pat.colour_start[c + 1] - pat.colour_start[c]);
+  lev.coop_grid = std::max(1, std::min(nsm, widest));
+  return CR_OK;
+}
+
 // Tile pattern, elimination order, ICC update lists, solve lists and the
 // assembly index lists of a level (geometry only); allocates A_hat and the
 // factor.
@@ -765,6 +1040,8 @@ int smoother_structure(cr_plan* P, PixLevel& lev) {
   SmootherBuild& sb = *lev.sb;
   int rc = CR_OK;
   if ((rc = upload_vec(&lev.d_perm, perm))) return rc;
+  if ((rc = upload_vec(&lev.d_colour_start, pat.colour_start))) return rc;
+  if ((rc = choose_coop_grid(P, lev))) return rc;
   if ((rc = upload_vec(&lev.d_row_ptr, pat.row_ptr))) return rc;
   if ((rc = upload_vec(&lev.d_row_col, pat.row_col))) return rc;
   if ((rc = upload_vec(&lev.d_col_ptr, col_ptr))) return rc;
@@ -949,6 +1226,36 @@ int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
   }
   float* y = reinterpret_cast<float*>(P->hier_tile_work);
   const int nc = (int)pat.colour_start.size() - 1;
+  if (lev.coop_grid > 0) {
+    // both sweeps in one cooperative launch (few tiles per colour)
+    SweepArgs sa;
+    sa.L = lev.d_L;
+    sa.LT = lev.d_LT;
+    sa.row_ptr = lev.d_row_ptr;
+    sa.row_col = lev.d_row_col;
+    sa.col_ptr = lev.d_col_ptr;
+    sa.col_row = lev.d_col_row;
+    sa.perm = lev.d_perm;
+    sa.colour_start = lev.d_colour_start;
+    sa.ncol = nc;
+    sa.y = y;
+    sa.bar = P->hier->d_sweep_bar;
+    sa.status = P->hier->d_sweep_status;
+    CR_CUDA(cudaMemsetAsync(sa.bar, 0, 2 * sizeof(unsigned int), P->stream));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(lev.coop_grid);
+    cfg.blockDim = dim3(SW_NT);
+    cfg.dynamicSmemBytes = (size_t)SW_NS * SW_BLOCK_BYTES;
+    cfg.stream = P->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CR_CUDA(cudaLaunchKernelEx(&cfg, sweep_coop_kernel<T>, sa, (const T*)map_in, map_out));
+    count_launch();
+    return CR_OK;
+  }
   // colours with few tiles are latency-bound: they get the 256-thread tiles
   // (coarse levels throughout, and the small leftover colours of the fine
   // levels); wide colours stream the factor with the 64-thread tiles
@@ -977,13 +1284,26 @@ int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
   CR_CHECK_LAUNCH("bwd_colour_kernel");
   return CR_OK;
 }
+// Device-side wait timeouts of the cooperative sweeps since the last check
+// (synchronises the plan's stream; clears the flag).
+int sweep_status(cr_plan* P) {
+  if (!P->hier || !P->hier->d_sweep_status || P->capturing) return CR_OK;
+  int st = 0;
+  CR_CUDA(cudaMemcpyAsync(&st, P->hier->d_sweep_status, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CR_CUDA(cudaStreamSynchronize(P->stream));
+  if (!st) return CR_OK;
+  CR_CUDA(cudaMemsetAsync(P->hier->d_sweep_status, 0, sizeof(int), P->stream));
+  return fail(CR_ECUDA, "pixel smoother: a bounded wait of the cooperative triangular sweeps gave up");
+}
+
 template int apply_smoother<double>(cr_plan*, PixLevel&, double*, double*);
 template int apply_smoother<float>(cr_plan*, PixLevel&, float*, float*);
 
 void free_smoother(PixLevel& lev) {
   delete lev.sb;
   lev.sb = nullptr;
-  void* ptrs[] = {lev.d_A, lev.d_L, lev.d_LT, lev.d_perm, lev.d_row_ptr, lev.d_row_col, lev.d_col_ptr, lev.d_col_row,
+  void* ptrs[] = {lev.d_A, lev.d_L, lev.d_LT, lev.d_perm, lev.d_colour_start, lev.d_row_ptr, lev.d_row_col,
+                  lev.d_col_ptr, lev.d_col_row,
                   lev.d_col_blk, lev.d_upd_ptr, lev.d_tgt_blk, lev.d_tgt_u, lev.d_tgt_ptr, lev.d_pair_a, lev.d_pair_b,
                   lev.d_fail};
   for (void* p : ptrs)

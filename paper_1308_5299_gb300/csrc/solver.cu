@@ -410,6 +410,8 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
   hops->ops.resize(H.H + 2);
   if (p->smoother != 0 && p->smoother != 1) return fail(CR_EINVAL, "levels: smoother must be 0 (ICC) or 1 (Schwarz)");
   H.smoother_kind = p->smoother;
+  if (p->smoother_sweep < 0 || p->smoother_sweep > 2) return fail(CR_EINVAL, "levels: smoother_sweep must be 0, 1 or 2");
+  H.sweep_mode = p->smoother_sweep;
   const double rf = p->ridge_factor > 0 ? p->ridge_factor : 1.5;
   const int nbis = p->ridge_bisections > 0 ? p->ridge_bisections : 30;
   int rc = CR_OK;
@@ -468,6 +470,10 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
   CR_CUDA(cudaMalloc(&H.map_work2, max_npix_h * sizeof(double)));
   CR_CUDA(cudaMalloc(&P->hier_tile_work, max_npix_h * sizeof(float)));
   CR_CUDA(cudaMalloc(&H.d_dot, 4 * sizeof(double)));
+  CR_CUDA(cudaMalloc(&H.d_sweep_bar, 2 * sizeof(unsigned int)));
+  CR_CUDA(cudaMalloc(&H.d_sweep_status, sizeof(int)));
+  CR_CUDA(cudaMemset(H.d_sweep_bar, 0, 2 * sizeof(unsigned int)));
+  CR_CUDA(cudaMemset(H.d_sweep_status, 0, sizeof(int)));
   for (int i = 0; i < 5; ++i) CR_CUDA(cudaMalloc(&H.krylov[i], n_lm(L) * sizeof(double2)));
   // settings of the C_l-dependent precompute
   H.ridge_factor = rf;
@@ -583,7 +589,8 @@ void free_hierarchy(cr_plan* P) {
     for (void* p : q)
       if (p) cudaFree(p);
   }
-  void* ptrs[] = {H.d_Ainv, H.d_Abottom, H.d_dof_lm, H.map_work, H.map_work2, H.d_dot, P->hier_tile_work};
+  void* ptrs[] = {H.d_Ainv, H.d_Abottom, H.d_dof_lm, H.map_work, H.map_work2, H.d_dot, P->hier_tile_work,
+                  H.d_sweep_bar, H.d_sweep_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   P->hier_tile_work = nullptr;
@@ -966,7 +973,8 @@ int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype) {
   int rc = check_hier(plan, "cr_smooth", true);
   if (rc) return rc;
   if (h < 0 || h > plan->hier->H) return fail(CR_EINVAL, "cr_smooth: level out of range");
-  return dtype == CR_F64 ? level_smooth<double>(plan, h, r, c) : level_smooth<float>(plan, h, r, c);
+  rc = dtype == CR_F64 ? level_smooth<double>(plan, h, r, c) : level_smooth<float>(plan, h, r, c);
+  return rc ? rc : sweep_status(plan);
 }
 
 int cr_bottom_solve(cr_plan* plan, const void* b, void* x, int dtype) {
@@ -992,7 +1000,7 @@ int cr_wcycle(cr_plan* plan, void* x, const void* b, int nrhs, int dtype) {
                          : wcycle<float>(plan, (char*)x + i * nlm * es, (const char*)b + i * nlm * es);
     if (rc) return rc;
   }
-  return CR_OK;
+  return sweep_status(plan);
 }
 
 int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int max_cycles, int mode, int* cycles_out,
@@ -1018,7 +1026,8 @@ int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int ma
     if (max_cycles < 1 || !(eps >= 0.0) || nrhs < 0) return fail(CR_EINVAL, "cr_solve: eps / max_cycles / nrhs");
     if (nrhs == 0) return CR_OK;
     plan->tc_top_f32 = (mode & CR_TC_TOP_F32) != 0;
-    return solve_tc(plan, x, b, nrhs, eps, max_cycles, (mode & CR_FIXED) != 0, cycles_out, relres_out, history);
+    rc = solve_tc(plan, x, b, nrhs, eps, max_cycles, (mode & CR_FIXED) != 0, cycles_out, relres_out, history);
+    return rc ? rc : sweep_status(plan);
   }
   if ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) return fail(CR_EINVAL, "cr_solve: mode precision must be CR_F64 or CR_MIXED");
   if (max_cycles < 1 || !(eps >= 0.0)) return fail(CR_EINVAL, "cr_solve: eps / max_cycles");
@@ -1029,7 +1038,7 @@ int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int ma
                history ? history + (int64_t)i * max_cycles : nullptr);
     if (rc) return rc;
   }
-  return CR_OK;
+  return sweep_status(plan);
 }
 
 }  // extern "C"

@@ -139,9 +139,15 @@ def test_full_size_sampled_rings(dev, nside, lmax):
     m32 = torch.empty(g["npix"], dtype=torch.float32, device=dev)
     plan.sht_synth(torch.from_numpy(a).to(torch.complex64).to(dev), m32)
     m32h = m32.cpu().numpy()
+    e32 = []
     for k in rings:
         sl = slice(g["off"][k], g["off"][k] + g["nphi"][k])
-        assert rel_l2(m32h[sl], ref[sl]) < 2e-4, k
+        e32.append(rel_l2(m32h[sl], ref[sl]))
+    print("FP32 synthesis, nside %d lmax %d, per sampled ring:" % (nside, lmax), np.array2string(np.array(e32), precision=2))
+    # single rings: up to 2.2e-5 measured, on the rings next to the cap/belt
+    # boundary (z near 2/3, where the FP32 polar form runs)
+    for k, e in zip(rings, e32):
+        assert e < 5e-5, k
     b32 = torch.empty(sht.n_lm(lmax), dtype=torch.complex64, device=dev)
     plan.sht_adjoint(torch.from_numpy(y).to(torch.float32).to(dev), b32)
     assert rel_l2(b32.cpu().numpy(), sht.adjoint(y, lmax, g, rings=rings)) < 1e-4
@@ -152,6 +158,27 @@ def test_full_size_sampled_rings(dev, nside, lmax):
     lhs = float(mh @ yy)
     rhs = sht.alm_dot(a, bb.cpu().numpy(), lmax)
     assert abs(lhs - rhs) < 1e-11 * np.linalg.norm(mh) * np.linalg.norm(yy)
+
+
+@pytest.mark.slow
+def test_apply_A_full_size_nside2048(dev):
+    """A = S^-1 + B Y^T N^-1 Y B at the Planck-shaped size (Nside 2048,
+    lmax 3000, 7.3' beam, |b| < 10 deg cut plus 3000 holes of 5') on one
+    prior draw, element by element against the oracle's direct transforms:
+    the operator that forms the benchmark's right-hand side b = A x_true."""
+    cfg, cl, bl, ninv = synthetic.problem_inputs("nside2048_lmax3000")
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev))
+    x = synthetic.draw_prior(cl, index=0)
+    y = torch.empty(sht.n_lm(cfg["lmax"]), dtype=torch.complex128, device=dev)
+    plan.apply_A(torch.from_numpy(x).to(dev), y)
+    yh = y.cpu().numpy()
+    del plan
+    ref = operators.apply_A(prob, x)
+    err = rel_l2(yh, ref)
+    print("apply_A nside 2048 / lmax 3000: rel L2 vs oracle %.3e" % err)
+    assert err < TOL64
 
 
 @pytest.mark.parametrize("nside,lmax", [(4, 20), (16, 47), (128, 383), (256, 767)])

@@ -23,7 +23,15 @@ def test_pins_read_back_and_replace(lib):
     assert got == {("f64", "adjoint"): 2, ("f32", "synthesis"): 2}
 
 
-@pytest.mark.parametrize("rp,prec,stage", [(3, "f32", "synthesis"), (16, "f64", "adjoint")])
+def test_sixteen_pairs_only_for_fp32_adjoint(lib):
+    binding.tune_set(63, 3072, 47, "f32", "adjoint", 16)
+    rows = [t for t in binding.tune_table() if (t["nring"], t["npix"], t["lmax"]) == (63, 3072, 47)]
+    assert [t["pairs_per_thread"] for t in rows] == [16]
+    with pytest.raises(binding.CRError):
+        binding.tune_set(63, 3072, 47, "f32", "synthesis", 16)
+
+
+@pytest.mark.parametrize("rp,prec,stage", [(3, "f32", "synthesis"), (16, "f64", "adjoint"), (32, "f32", "adjoint")])
 def test_invalid_choice_rejected(lib, rp, prec, stage):
     with pytest.raises(binding.CRError) as e:
         binding.tune_set(31, 768, 23, prec, stage, rp)
