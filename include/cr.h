@@ -203,6 +203,12 @@ typedef struct cr_params {
    * per colour on every level; 2 = the cooperative launch wherever the
    * device supports it.  The same operator either way. */
   int smoother_sweep;
+  /* tensor-core contractions of batched right-hand sides (CR_TC, and the
+   * cycles of CR_TC_CYCLES): 0 = BF16 operands (about 2^-9 relative per
+   * product, FP32 accumulation); 1 = each operand carried as a BF16 pair
+   * hi + lo and the product as A_hi B_hi + A_hi B_lo + A_lo B_hi (three MMAs
+   * per step, about 2^-17 relative). */
+  int tc_split;
 } cr_params;
 
 /* One-line message describing the last error on the calling thread. */
@@ -225,17 +231,23 @@ int cr_plan_create(cr_plan** out, const cr_params* p);
  * precision, stage) and used by every plan with those shapes; shapes already
  * in the cache are not re-timed.  Untuned shapes use 4.  *nentries (may be
  * NULL) receives the size of the cache.  Synchronous; a few seconds at
- * Nside 2048.  cr_tune_entry reads cache entry i (0 <= i < size): grid ring
- * and pixel counts, band limit, precision in bytes (4 or 8), stage (0
- * synthesis, 1 adjoint), the chosen pairs per thread and the measured ms of
- * the choices 2, 4, 8, 16 (HOST [4]; -1 where the stage has no such choice);
- * any output may be NULL.  Errors: CR_EINVAL, CR_ECUDA.
+ * Nside 2048.  The batched tensor-core synthesis (16 right-hand sides) is
+ * tuned too: its stage shape (variant 0: K 32 per parity, 2 pipeline
+ * stages; 1: K 32, 3 stages; 2: K 16, 3 stages), cached with precision 2
+ * and stage 2.  cr_tune_entry reads cache entry i (0 <= i < size): grid
+ * ring and pixel counts, band limit, precision in bytes (4 or 8; 2 for the
+ * tensor-core entries), stage (0 synthesis, 1 adjoint, 2 tensor-core
+ * synthesis), the chosen pairs per thread (or variant) and the measured ms
+ * of the choices 2, 4, 8, 16 pairs per thread (or variants 0, 1, 2) (HOST
+ * [4]; -1 where there is no such choice); any output may be NULL.  Errors:
+ * CR_EINVAL, CR_ECUDA.
  */
 int cr_plan_autotune(cr_plan* plan, int* nentries);
 int cr_tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* precision_bytes, int* stage, int* rp,
                   double* ms);
 /* Pin the choice for one (grid shape, band limit, precision, stage): rp 2,
- * 4 or 8, or 16 for the FP32 adjoint.  Errors: CR_EINVAL. */
+ * 4 or 8, or 16 for the FP32 adjoint; precision 2 with stage 2: the
+ * tensor-core synthesis variant 0, 1 or 2.  Errors: CR_EINVAL. */
 int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp);
 
 /*
@@ -379,6 +391,14 @@ int cr_batch_destroy(cr_batch* batch);
  * CR_EINVAL (bad K), CR_ECUDA (including a completion wait that gave up).
  */
 int cr_tc_selftest(int K, float* max_abs_err);
+/* The same tile with both operands in the MN-major (transposed) layout
+ * without swizzle, the layout the batched adjoint writes: core matrices of
+ * 8 K rows x 8 MN elements, 128 bytes apart along MN and (MN / 8) * 128
+ * bytes apart along K.  swap = 0 passes the MN stride as the descriptor's
+ * leading byte offset and the K stride as its stride byte offset, swap = 1
+ * the other way round (the operand buffers are large enough for either).
+ * Errors: CR_EINVAL, CR_ECUDA. */
+int cr_tc_selftest_mn(int K, int swap, float* max_abs_err);
 
 /*
  * Arithmetic peak probe (measurement tooling, no counterpart in the paper):

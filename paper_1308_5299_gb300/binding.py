@@ -70,6 +70,7 @@ class cr_params(ctypes.Structure):
         ("autotune", ctypes.c_int),
         ("smoother", ctypes.c_int),
         ("smoother_sweep", ctypes.c_int),
+        ("tc_split", ctypes.c_int),
     ]
 
 
@@ -139,6 +140,7 @@ _SIGS = {
                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                   ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_plan_timing_exec": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cr_tc_selftest_mn": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "cr_probe_fma_peak": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_plan_timing": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long),
@@ -191,6 +193,14 @@ def tc_selftest(K=64):
     return e.value
 
 
+def tc_selftest_mn(K=64, swap=0):
+    """Largest |difference| of the MN-major tcgen05 tile against the CUDA
+    cores (cr_tc_selftest_mn)."""
+    e = ctypes.c_float()
+    _check(lib().cr_tc_selftest_mn(int(K), int(swap), ctypes.byref(e)))
+    return e.value
+
+
 def fma_peak(kind):
     """Measured FMA-pipe peak in TFLOP/s on the current device: kind 'f32',
     'f32x2' (packed pairs) or 'f64' (cr_probe_fma_peak)."""
@@ -206,10 +216,13 @@ def launch_count():
 
 
 def tune_table():
-    """The Legendre autotuner's cached choices: one dict per (grid, band
-    limit, precision, stage) with the chosen pairs per thread and the
-    measured ms of 2, 4, 8 (and, for the FP32 adjoint, 16) pairs per
-    thread."""
+    """The autotuner's cached choices: one dict per (grid, band limit,
+    precision, stage).  Legendre stages (precision "f32"/"f64", stage
+    "synthesis"/"adjoint"): the chosen pairs per thread and the measured ms
+    of 2, 4, 8 (and, for the FP32 adjoint, 16) pairs per thread.  The
+    batched tensor-core synthesis (precision "bf16", stage "tc_synthesis"):
+    the chosen stage-shape variant (0: K 32 per parity, 2 stages; 1: K 32,
+    3 stages; 2: K 16, 3 stages) and the measured ms of each."""
     out = []
     i = 0
     while True:
@@ -219,17 +232,25 @@ def tune_table():
         if lib().cr_tune_entry(i, ctypes.byref(nring), ctypes.byref(npix), ctypes.byref(lmax), ctypes.byref(nb),
                                ctypes.byref(stage), ctypes.byref(rp), ms) != 0:
             return out
-        out.append(dict(nring=nring.value, npix=npix.value, lmax=lmax.value, precision="f64" if nb.value == 8 else "f32",
-                        stage="synthesis" if stage.value == 0 else "adjoint", pairs_per_thread=rp.value,
-                        ms={k: ms[i] for i, k in enumerate((2, 4, 8, 16)) if ms[i] >= 0}))
+        if nb.value == 2:
+            out.append(dict(nring=nring.value, npix=npix.value, lmax=lmax.value, precision="bf16",
+                            stage="tc_synthesis", variant=rp.value,
+                            ms={k: ms[k] for k in range(3) if ms[k] >= 0}))
+        else:
+            out.append(dict(nring=nring.value, npix=npix.value, lmax=lmax.value,
+                            precision="f64" if nb.value == 8 else "f32",
+                            stage="synthesis" if stage.value == 0 else "adjoint", pairs_per_thread=rp.value,
+                            ms={k: ms[i2] for i2, k in enumerate((2, 4, 8, 16)) if ms[i2] >= 0}))
         i += 1
 
 
 def tune_set(nring, npix, lmax, precision, stage, pairs_per_thread):
-    """Pin the Legendre ring-block choice for one shape (``cr_tune_set``):
-    precision "f32"/"f64", stage "synthesis"/"adjoint"."""
-    _check(lib().cr_tune_set(int(nring), int(npix), int(lmax), 8 if precision == "f64" else 4,
-                             0 if stage == "synthesis" else 1, int(pairs_per_thread)))
+    """Pin one autotuner choice (``cr_tune_set``): precision "f32"/"f64" with
+    stage "synthesis"/"adjoint" and the pairs per thread, or precision
+    "bf16" with stage "tc_synthesis" and the shape variant (0, 1, 2)."""
+    nb = {"f64": 8, "f32": 4, "bf16": 2}[precision]
+    st = {"synthesis": 0, "adjoint": 1, "tc_synthesis": 2}[stage]
+    _check(lib().cr_tune_set(int(nring), int(npix), int(lmax), nb, st, int(pairs_per_thread)))
 
 
 def _tc_code(code, tensor_cores, what):
@@ -259,7 +280,7 @@ class Plan:
     def __init__(self, lmax, nside=None, gl=None, cl=None, bl=None, ninv=None, stream=None, levels=None,
                  lmax_dense=-1, ridge_factor=0.0, ridge_bisections=0, ridge_alpha=None, ridge_lambda_target=0.0,
                  gl_downgrade=0, fp64_df=False, defer_precompute=False, autotune=False, smoother="icc",
-                 smoother_sweep="auto"):
+                 smoother_sweep="auto", tc_split=False):
         """levels: None (transforms and A only), "default" (the library's level
         table), or a list of dicts with nside_h, lmax_h, n_rec and fl
         (cumulative filter, length lmax+1).  gl_downgrade: 0 auto, 1 every
@@ -267,7 +288,8 @@ class Plan:
         inverse-noise term).  defer_precompute: skip the C_l-dependent
         precompute (then ``load`` a checkpoint or ``update_cl``).
         smoother_sweep: "auto", "per_colour" or "cooperative" (how the ICC(0)
-        triangular sweeps are launched; the same operator)."""
+        triangular sweeps are launched; the same operator).  tc_split: the
+        tensor-core contractions with hi + lo BF16 operands (three MMAs)."""
         p = cr_params()
         p.struct_size = ctypes.sizeof(cr_params)
         if gl is not None:
@@ -322,6 +344,7 @@ class Plan:
             raise ValueError("smoother: 'icc' (multicolour block ICC(0)) or 'schwarz' (block Jacobi)")
         p.smoother = 0 if smoother == "icc" else 1
         p.smoother_sweep = {"auto": 0, "per_colour": 1, "cooperative": 2}[smoother_sweep]
+        p.tc_split = int(bool(tc_split))
         if ridge_alpha is not None:
             ra = np.ascontiguousarray(ridge_alpha, dtype=np.float64)
             self._keep.append(ra)

@@ -22,6 +22,11 @@ or FP64 on a named workload (``--workload``), with the per-stage CUDA-event
 times of the plan (Legendre synthesis, fused ring FFTs with N^-1, Legendre
 adjoint) and the stages' dense and executed Legendre flops.
 
+``smooth``: one pixel-smoother application (Y_h^T M_h Y_h r in FP32) per
+pixel level of a named workload's default hierarchy, with the ICC(0)
+triangular sweeps launched once per colour and as one cooperative launch:
+the plan's per-stage time of the sweeps alone, per application.
+
 ``diag``: the convergence diagnostics of ``diagnostics`` on a synthetic
 workload (error by scale per W-cycle, smoother-only stagnation on the first
 pixel level, level filters).
@@ -58,12 +63,14 @@ def _time(fn, stream, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def tc_case(nside, lmax, nrhs, warmup, reps):
+def tc_case(nside, lmax, nrhs, warmup, reps, tune=False, split=False):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     cl, bl, ninv = _problem(nside, lmax, dev)
-    plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=ninv, stream=stream)
+    plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=ninv, stream=stream, tc_split=split)
+    if tune:
+        plan.autotune()
     nlm = binding.n_lm(lmax)
     a = torch.from_numpy(np.stack([synthetic.random_alm(lmax, seed=300 + j) for j in range(nrhs)]))
     a = a.to(torch.complex64).to(dev)
@@ -85,7 +92,8 @@ def tc_case(nside, lmax, nrhs, warmup, reps):
             f32()
         torch.cuda.synchronize()
         res[name] = {"tensor_core_ms": _time(tc, stream, reps), "fp32_ms": _time(f32, stream, reps)}
-    return {"case": "tc", "nside": nside, "lmax": lmax, "nrhs": nrhs, "reps": reps, "ms": res}
+    return {"case": "tc", "nside": nside, "lmax": lmax, "nrhs": nrhs, "reps": reps, "split": bool(split),
+            "ms": res, "tune": [t for t in binding.tune_table() if t["lmax"] == lmax] if tune else None}
 
 
 def sht_case(nside, lmax, warmup, reps, dtype):
@@ -139,6 +147,34 @@ def apply_case(name, warmup, reps, dtype, tune):
     return {"case": "apply", "workload": name, "dtype": dtype, "reps": reps, "autotuned": bool(tune),
             "ms_per_call": ms, "stages": stages,
             "tune": [t for t in binding.tune_table() if t["lmax"] == lmax] if tune else None}
+
+
+def smooth_case(name, warmup, reps):
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    cfg, cl, bl, ninv = synthetic.problem_inputs(name)
+    res = {}
+    for mode in ("per_colour", "cooperative"):
+        plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                            levels="default", stream=stream, smoother_sweep=mode)
+        for h in range(1, plan.nlevels() + 1):
+            lv = plan.level(h)
+            r = torch.from_numpy(synthetic.random_alm(lv["lmax_h"], seed=7)).to(torch.complex64).to(dev)
+            c = torch.empty_like(r)
+            for _ in range(warmup):
+                plan.smooth(h, r, c)
+            torch.cuda.synchronize()
+            plan.set_timing(True)
+            for _ in range(reps):
+                plan.smooth(h, r, c)
+            st = plan.timing()
+            plan.set_timing(False)
+            ms = st.get("pixel_smoother", (0.0, 1, 0.0))
+            res.setdefault("n%d" % lv["nside_h"], {})[mode] = {"ms": ms[0] / reps, "GB_per_s": ms[2] / ms[0] / 1e6}
+        del plan
+        torch.cuda.synchronize()
+    return {"case": "smooth", "workload": name, "reps": reps, "levels": res}
 
 
 def diag_case(name, cycles, iters):
@@ -207,8 +243,9 @@ def grad_case(name, nrhs, warmup):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["tc", "sht", "apply", "diag", "grad"])
-    ap.add_argument("--tune", action="store_true", help="apply: autotune the Legendre ring blocks first")
+    ap.add_argument("case", choices=["tc", "sht", "apply", "smooth", "diag", "grad"])
+    ap.add_argument("--tune", action="store_true", help="apply, tc: autotune the kernel shapes first")
+    ap.add_argument("--split", action="store_true", help="tc: hi + lo BF16 operands")
     ap.add_argument("--workload", default="nside256_lmax767")
     ap.add_argument("--cycles", type=int, default=4)
     ap.add_argument("--iters", type=int, default=16)
@@ -221,9 +258,11 @@ def main(argv=None):
     args = ap.parse_args(argv)
     binding.lib()
     if args.case == "tc":
-        print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps)))
+        print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps, args.tune, args.split)))
     elif args.case == "apply":
         print(json.dumps(apply_case(args.workload, args.warmup, args.reps, args.dtype, args.tune)))
+    elif args.case == "smooth":
+        print(json.dumps(smooth_case(args.workload, args.warmup, args.reps)))
     elif args.case == "diag":
         print(json.dumps(diag_case(args.workload, args.cycles, args.iters)))
     elif args.case == "grad":

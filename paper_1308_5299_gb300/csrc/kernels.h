@@ -33,6 +33,8 @@ struct LegArgs {
   typename Tr<T>::C* partial = nullptr;    // adjoint: [nblk][n_lm(L)]
   const T* ringval = nullptr;              // SQ variant: per-ring value
   int rp_synth = 4, rp_adj = 4;            // ring pairs per thread (2, 4, 8) of the two stages
+  int tc_variant = 0;                      // tensor-core kernels: stage shape (legendre_tc.cu)
+  int tc_split = 0;                        // tensor-core kernels: hi + lo BF16 operands
 };
 
 template <typename T>

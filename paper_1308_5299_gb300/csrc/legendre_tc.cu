@@ -3,30 +3,22 @@
 // For many right-hand sides the synthesis Legendre stage is, per m, a dense
 // contraction F[pair, rhs] = sum_l P~_lm(z_pair) a_lm[rhs] (Section 2.1,
 // Eq. sh-synthesis), split by the parity of l - m into E (even) and O (odd)
-// sums so that F(z) = E + O and F(-z) = E - O.  One CTA per (m, 128 ring
-// pairs): each thread runs its pair's FP32 recurrence Q_l (start tables,
-// polar difference form near the poles as in legendre.cu) and writes Q of
-// 64 even and 64 odd l per chunk as BF16 into the A operands (128 x 64,
-// K-major); the B operands hold a_lm s_lm (times an optional per-l factor)
-// of up to 16 right-hand sides, real and imaginary parts as 32 columns.
-// One thread issues tcgen05.mma (M 128, N 32, K 16, FP32 accumulation in
-// tensor memory) for both parities; stages are double-buffered on mbarriers
-// so the recurrence of the next chunk overlaps the tensor cores.  The
-// accumulators are read back with tcgen05.ld at the end.
+// sums so that F(z) = E + O and F(-z) = E - O.  The CUDA cores generate the
+// A operand -- Q_l of every ring pair by the FP32 recurrence (start tables,
+// polar difference form near the poles as in legendre.cu), written as BF16
+// K-major rows -- and the B operand, a_lm s_lm (times an optional per-l
+// factor) of up to 16 right-hand sides, real and imaginary parts as 32
+// columns; tcgen05.mma (M 128, N 32, FP32 accumulation in tensor memory)
+// does the contraction, and the accumulators are read back with tcgen05.ld
+// at the end.
 #include "common.cuh"
 #include "kernels.h"
 #include "tc.cuh"
 
 namespace cr {
 
-constexpr int TS_M = 128;     // ring pairs per CTA
-constexpr int TS_KC = 32;     // K per chunk and parity (64 l per chunk)
-constexpr int TS_N = 32;      // 16 right-hand sides x (re, im)
-constexpr int TS_RHS = 16;
-constexpr int TS_A_BYTES = TS_M * TS_KC * 2;   // 8 KB
-constexpr int TS_B_BYTES = TS_N * TS_KC * 2;   // 2 KB
-constexpr int TS_STAGE = 2 * TS_A_BYTES + 2 * TS_B_BYTES;
-constexpr uint32_t TS_WAIT = 1u << 26;
+constexpr int TS_RHS = 16;               // right-hand sides per launch (N = 32: Re, Im)
+constexpr uint32_t TS_WAIT = 1u << 26;   // polls of a bounded mbarrier wait
 
 struct TsArgs {
   const float2* alm;     // [nrhs][ld_alm] complex64
@@ -65,207 +57,362 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <bool POLAR>
-__global__ void __launch_bounds__(TS_M, 4) tc_synth_kernel(TsArgs a, int nbp, int yoff) {
-  extern __shared__ __align__(1024) uint8_t tsmem[];
-  __shared__ float sc[128], sc2[128], sfac[128];
-  __shared__ uint64_t mbar[2];
+// ---------------------------------------------------------------------------
+// The work is split so that the CUDA cores never wait for each other:
+//  - four producer warps generate the operands; every thread runs the FP32
+//    recurrence of two ring pairs (one in each of two 128-row M tiles, two
+//    independent dependency chains) and writes their Q rows (BF16, K-major)
+//    and one task of the coefficient operand;
+//  - a fifth warp issues the MMAs: it waits until all 128 producers have
+//    arrived on the stage's "full" mbarrier, issues the stage's MMAs (two
+//    tiles x two parities x K/16, D in tensor memory) and commits them to the
+//    stage's "empty" mbarrier, which the producers wait on before they reuse
+//    the stage NSTG chunks later;
+//  - no block-wide barrier inside the chunk loop: the recurrence coefficients
+//    are staged per warp.
+// SPLIT: each operand value v is carried as hi = bf16(v) and lo = bf16(v - hi)
+// and the product as A_hi B_hi + A_hi B_lo + A_lo B_hi (three MMAs on the same
+// accumulator), which brings the contraction from the 2^-9 of one BF16
+// rounding to about 2^-17 relative.
+constexpr int T2_PW = 4;                   // producer warps
+constexpr int T2_NT = 32 * (T2_PW + 1);    // + the MMA warp
+constexpr int T2_TILES = 2;                // M tiles of 128 ring pairs
+
+template <int KC, bool SPLIT>
+struct T2Layout {
+  static constexpr int NPART = SPLIT ? 2 : 1;
+  static constexpr int A_BYTES = 128 * KC * 2;           // one tile, one parity, one part
+  static constexpr int B_BYTES = 32 * KC * 2;            // one parity, one part
+  static constexpr int STAGE = T2_TILES * 2 * NPART * A_BYTES + 2 * NPART * B_BYTES;
+  __device__ static uint32_t a_off(int t, int q, int part) { return ((t * 2 + q) * NPART + part) * A_BYTES; }
+  __device__ static uint32_t b_off(int q, int part) {
+    return T2_TILES * 2 * NPART * A_BYTES + (q * NPART + part) * B_BYTES;
+  }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(mbar)) : "memory");
+}
+
+// 8 values -> 16 bytes of BF16 (hi part), and the residuals' BF16 (lo part)
+__device__ __forceinline__ uint4 pack8_hi(const float v[8]) {
+  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ uint4 pack8_lo(const float v[8]) {
+  float r[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = v[i] - bf16_round(v[i]);
+  return pack8_hi(r);
+}
+
+template <bool POLAR, int KC, int NSTG, bool SPLIT>
+__global__ void __launch_bounds__(T2_NT) tc_synth2_kernel(TsArgs a, int nbp, int yoff) {
+  using Lay = T2Layout<KC, SPLIT>;
+  constexpr int CH = 2 * KC;  // l values per chunk
+  extern __shared__ __align__(1024) uint8_t t2smem[];
+  __shared__ float s_c[T2_PW][CH], s_c2[POLAR ? T2_PW : 1][CH], s_f[T2_PW][CH];
+  __shared__ uint64_t full[NSTG], empty[NSTG];
   __shared__ uint32_t taddr_s;
   __shared__ int s_min;
-  // blockIdx.x runs over ring-pair blocks and blockIdx.y over m, so the
-  // blocks sharing an m's coefficients run together and share them in L2
+  __shared__ volatile int s_abort;
   const int m = blockIdx.y;
   const int L = a.L;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp < T2_PW;
   const int yb = (int)blockIdx.x + yoff;
-  const int base = POLAR ? yb * TS_M : a.npolar + (yb - nbp) * TS_M;
+  const int base = POLAR ? yb * (128 * T2_TILES) : a.npolar + (yb - nbp) * (128 * T2_TILES);
   const int pend = POLAR ? a.npolar : a.npairs;
-  const int p = base + tid;
-  int ls = L + 1;
-  float P1 = 0.f, P2 = 0.f, zz = 0.f;
-  if (p < pend) {
-    const int64_t o = (int64_t)m * a.ld_seed + p;
-    zz = POLAR ? a.w[p] : a.z[p];
-    const int l = a.ls[o];
-    if (l <= L) {
-      const float2 s = a.st[o];
-      ls = l;
-      P1 = s.x;
-      P2 = s.y;
+  // this thread's two ring pairs (tile 0 row tid, tile 1 row tid)
+  int pp[T2_TILES], ls[T2_TILES];
+  float P1[T2_TILES], P2[T2_TILES], zz[T2_TILES];
+#pragma unroll
+  for (int t = 0; t < T2_TILES; ++t) {
+    pp[t] = base + t * 128 + tid;
+    ls[t] = L + 1;
+    P1[t] = P2[t] = zz[t] = 0.f;
+    if (producer && pp[t] < pend) {
+      const int64_t o = (int64_t)m * a.ld_seed + pp[t];
+      zz[t] = POLAR ? a.w[pp[t]] : a.z[pp[t]];
+      const int l = a.ls[o];
+      if (l <= L) {
+        const float2 st = a.st[o];
+        ls[t] = l;
+        P1[t] = st.x;
+        P2[t] = st.y;
+      }
     }
   }
-  if (tid == 0) s_min = L + 1;
+  if (tid == 0) {
+    s_min = L + 1;
+    s_abort = 0;
+  }
   __syncthreads();
-  if (ls <= L) atomicMin(&s_min, ls);
+  if (producer) atomicMin(&s_min, min(ls[0], ls[1]));
   __syncthreads();
   const int cmin = s_min;
   if (cmin > L) {
     // no pair of the block reaches the threshold: F = 0
-    if (p < pend)
-      for (int r = 0; r < a.nrhs; ++r) {
-        const int rn = p, rs = a.nring - 1 - p;
-        a.phase[r * a.ld_phase + (int64_t)rn * a.ldp + m] = make_float2(0.f, 0.f);
-        if (rs != rn) a.phase[r * a.ld_phase + (int64_t)rs * a.ldp + m] = make_float2(0.f, 0.f);
-      }
+    if (producer)
+      for (int t = 0; t < T2_TILES; ++t)
+        if (pp[t] < pend)
+          for (int r = 0; r < a.nrhs; ++r) {
+            const int rn = pp[t], rs = a.nring - 1 - pp[t];
+            a.phase[r * a.ld_phase + (int64_t)rn * a.ldp + m] = make_float2(0.f, 0.f);
+            if (rs != rn) a.phase[r * a.ld_phase + (int64_t)rs * a.ldp + m] = make_float2(0.f, 0.f);
+          }
     return;
   }
   const int lbeg = m + ((cmin - m) & ~1);
-  const int nch = (L + 1 - lbeg + 2 * TS_KC - 1) / (2 * TS_KC);
+  const int nch = (L + 1 - lbeg + CH - 1) / CH;
   const int64_t offa = lm_off(L, m), offc = lm_off(a.Lc, m);
-  if (warp == 0) tc::tmem_alloc(&taddr_s, 64);
+  if (warp == T2_PW) tc::tmem_alloc(&taddr_s, 32 * 2 * T2_TILES);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int i = 0; i < NSTG; ++i) {
+      tc::mbar_init(&full[i], 32 * T2_PW);
+      tc::mbar_init(&empty[i], 1);
+    }
     tc::mbar_fence_init();
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = taddr_s;
-  const uint32_t idesc = tc::idesc_bf16_f32(TS_M, TS_N);
-  // B operands: rows 2 r (re) and 2 r + 1 (im), K index k: l = l0 + 2 k
-  // (+1 for odd).  Each thread owns one task -- right-hand side br, parity
-  // bpar, K group bk8 (8 K values of both rows, two 16-byte stores) -- and
-  // loads the next chunk's coefficients into registers before running the
-  // current chunk's recurrence, so their latency hides behind it.
-  static_assert(TS_RHS * 2 * (TS_KC / 8) == TS_M, "one B task per thread");
-  const int br = tid / (2 * (TS_KC / 8)), brem = tid % (2 * (TS_KC / 8));
-  const int bpar = brem & 1, bk8 = brem >> 1;
-  float2 pa[8];
-  float pc = 0.f, pc2 = 0.f, pf = 0.f;
-  auto prefetch = [&](int l0n) {
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const int l = l0n + 2 * (bk8 * 8 + kk) + bpar;
-      pa[kk] = (br < a.nrhs && l <= L) ? a.alm[br * a.ld_alm + offa + (l - m)] : make_float2(0.f, 0.f);
-    }
-    const int l = l0n + tid;
-    const bool in = l <= L;
-    pc = in ? a.c[offc + (l - m)] : 0.f;
-    if (POLAR) pc2 = in ? a.c2[offc + (l - m)] : 0.f;
-    pf = in ? a.s[offc + (l - m)] * (a.dl ? a.dl[l] : 1.f) : 0.f;
-  };
-  prefetch(lbeg);
-  bool ok = true;  // block-uniform: every wait below is taken by the whole CTA
-  int ncommit = 0;  // chunks whose MMAs have been committed
-  for (int ch = 0; ch < nch; ++ch) {
-    const int stg = ch & 1;
-    uint8_t* AE = tsmem + stg * TS_STAGE;
-    uint8_t* AO = AE + TS_A_BYTES;
-    uint8_t* BE = AO + TS_A_BYTES;
-    uint8_t* BO = BE + TS_B_BYTES;
-    const int l0 = lbeg + ch * 2 * TS_KC;
-    // the MMAs that read this stage two chunks ago must be done
-    if (ch >= 2) ok = tc::mbar_wait_block(&mbar[stg], ((ch - 2) >> 1) & 1, TS_WAIT);
-    if (!ok) break;
-    sc[tid] = pc;
-    if (POLAR) sc2[tid] = pc2;
-    sfac[tid] = pf;
-    __syncthreads();
-    {
-      float vr[8], vi[8];
+  bool ok = true;
+
+  if (producer) {
+    // coefficient-operand task of this thread: right-hand side br, parity
+    // bpar, K group bk8 (8 K values of the Re and Im rows)
+    constexpr int NTASK = 16 * 2 * (KC / 8);
+    const bool btask = tid < NTASK;
+    const int br = tid / (2 * (KC / 8)), brem = tid % (2 * (KC / 8));
+    const int bpar = brem & 1, bk8 = brem >> 1;
+    float2 pa[8];
+    auto prefetch = [&](int l0n) {
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
-        const int j = 2 * (bk8 * 8 + kk) + bpar;  // l - l0
-        vr[kk] = pa[kk].x * sfac[j];
-        vi[kk] = (m == 0) ? 0.f : pa[kk].y * sfac[j];
+        const int l = l0n + 2 * (bk8 * 8 + kk) + bpar;
+        pa[kk] = (btask && br < a.nrhs && l <= L) ? a.alm[br * a.ld_alm + offa + (l - m)] : make_float2(0.f, 0.f);
       }
-      uint8_t* B = bpar ? BO : BE;
-      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * br, bk8 * 8, TS_KC)) =
-          make_uint4(pack_bf16(vr[0], vr[1]), pack_bf16(vr[2], vr[3]), pack_bf16(vr[4], vr[5]), pack_bf16(vr[6], vr[7]));
-      *reinterpret_cast<uint4*>(B + tc::kmajor_offset(2 * br + 1, bk8 * 8, TS_KC)) =
-          make_uint4(pack_bf16(vi[0], vi[1]), pack_bf16(vi[2], vi[3]), pack_bf16(vi[4], vi[5]), pack_bf16(vi[6], vi[7]));
-    }
-    if (ch + 1 < nch) prefetch(l0 + 2 * TS_KC);
-    // A operands: this thread's row, 8 K values (16 l) per 16-byte store;
-    // chunks the pair covers entirely run without per-step checks
-    const bool full = (ls <= l0) && (l0 + 2 * TS_KC - 1 <= L);
-    for (int k8 = 0; k8 < TS_KC / 8; ++k8) {
-      float ve[8], vo[8];
-      if (full) {
+    };
+    // the recurrence coefficients and factors of the next chunk, loaded into
+    // registers one chunk ahead (CH / 32 values per lane and array), so
+    // their latency hides behind the current chunk's recurrence
+    constexpr int PER = CH / 32;
+    float qc[PER], qc2[PER], qf[PER];
+    auto prefetch_coef = [&](int l0n) {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int l = l0n + lane + 32 * u;
+        const bool in = l <= L;
+        qc[u] = in ? a.c[offc + (l - m)] : 0.f;
+        qc2[u] = (POLAR && in) ? a.c2[offc + (l - m)] : 0.f;
+        qf[u] = in ? a.s[offc + (l - m)] * (a.dl ? a.dl[l] : 1.f) : 0.f;
+      }
+    };
+    prefetch(lbeg);
+    prefetch_coef(lbeg);
+    float* sc = s_c[warp];
+    float* sc2 = s_c2[POLAR ? warp : 0];
+    float* sf = s_f[warp];
+    for (int ch = 0; ch < nch; ++ch) {
+      const int stg = ch % NSTG;
+      const int l0 = lbeg + ch * CH;
+      if (ch >= NSTG) {
+        const bool w = tc::mbar_wait(&empty[stg], ((ch / NSTG) - 1) & 1, TS_WAIT);
+        if (!__all_sync(0xffffffffu, w)) {
+          if (lane == 0) s_abort = 1;
+          ok = false;
+          break;
+        }
+      }
+      if (__any_sync(0xffffffffu, s_abort != 0)) {  // warp-uniform
+        ok = false;
+        break;
+      }
+      uint8_t* S = t2smem + stg * Lay::STAGE;
+      // this warp's copy of the chunk's recurrence coefficients and factors
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        sc[lane + 32 * u] = qc[u];
+        if (POLAR) sc2[lane + 32 * u] = qc2[u];
+        sf[lane + 32 * u] = qf[u];
+      }
+      __syncwarp();
+      if (ch + 1 < nch) prefetch_coef(l0 + CH);
+      if (btask) {
+        float vr[8], vi[8];
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
-          const int j = (k8 * 8 + kk) * 2;
-          ve[kk] = tstep<POLAR>(sc[j], POLAR ? sc2[j] : 0.f, zz, P1, P2);
-          vo[kk] = tstep<POLAR>(sc[j + 1], POLAR ? sc2[j + 1] : 0.f, zz, P1, P2);
+          const int j = 2 * (bk8 * 8 + kk) + bpar;
+          vr[kk] = pa[kk].x * sf[j];
+          vi[kk] = (m == 0) ? 0.f : pa[kk].y * sf[j];
         }
-      } else {
+        const uint32_t orow = tc::kmajor_offset(2 * br, bk8 * 8, KC), irow = tc::kmajor_offset(2 * br + 1, bk8 * 8, KC);
+        *reinterpret_cast<uint4*>(S + Lay::b_off(bpar, 0) + orow) = pack8_hi(vr);
+        *reinterpret_cast<uint4*>(S + Lay::b_off(bpar, 0) + irow) = pack8_hi(vi);
+        if (SPLIT) {
+          *reinterpret_cast<uint4*>(S + Lay::b_off(bpar, 1) + orow) = pack8_lo(vr);
+          *reinterpret_cast<uint4*>(S + Lay::b_off(bpar, 1) + irow) = pack8_lo(vi);
+        }
+      }
+      if (ch + 1 < nch) prefetch(l0 + CH);
+      // A operands: both pairs' recurrences in step (two chains), 8 K values
+      // (16 l) per 16-byte store per tile and parity
+      const bool full_chunk = (max(ls[0], ls[1]) <= l0) && (l0 + CH - 1 <= L);
+#pragma unroll 1
+      for (int k8 = 0; k8 < KC / 8; ++k8) {
+        float ve[T2_TILES][8], vo[T2_TILES][8];
+        if (full_chunk) {
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const int j = (k8 * 8 + kk) * 2;
-          const int l = l0 + j;
-          float q0 = 0.f, q1 = 0.f;
-          if (l >= ls && l <= L) q0 = tstep<POLAR>(sc[j], POLAR ? sc2[j] : 0.f, zz, P1, P2);
-          if (l + 1 >= ls && l + 1 <= L) q1 = tstep<POLAR>(sc[j + 1], POLAR ? sc2[j + 1] : 0.f, zz, P1, P2);
-          ve[kk] = q0;
-          vo[kk] = q1;
+          for (int kk = 0; kk < 8; ++kk) {
+            const int j = (k8 * 8 + kk) * 2;
+            const float c0 = sc[j], c1 = sc[j + 1];
+            const float d0 = POLAR ? sc2[j] : 0.f, d1 = POLAR ? sc2[j + 1] : 0.f;
+#pragma unroll
+            for (int t = 0; t < T2_TILES; ++t) {
+              ve[t][kk] = tstep<POLAR>(c0, d0, zz[t], P1[t], P2[t]);
+              vo[t][kk] = tstep<POLAR>(c1, d1, zz[t], P1[t], P2[t]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const int j = (k8 * 8 + kk) * 2;
+            const int l = l0 + j;
+#pragma unroll
+            for (int t = 0; t < T2_TILES; ++t) {
+              float q0 = 0.f, q1 = 0.f;
+              if (l >= ls[t] && l <= L) q0 = tstep<POLAR>(sc[j], POLAR ? sc2[j] : 0.f, zz[t], P1[t], P2[t]);
+              if (l + 1 >= ls[t] && l + 1 <= L)
+                q1 = tstep<POLAR>(sc[j + 1], POLAR ? sc2[j + 1] : 0.f, zz[t], P1[t], P2[t]);
+              ve[t][kk] = q0;
+              vo[t][kk] = q1;
+            }
+          }
+        }
+        const uint32_t row = tc::kmajor_offset(tid, k8 * 8, KC);
+#pragma unroll
+        for (int t = 0; t < T2_TILES; ++t) {
+          *reinterpret_cast<uint4*>(S + Lay::a_off(t, 0, 0) + row) = pack8_hi(ve[t]);
+          *reinterpret_cast<uint4*>(S + Lay::a_off(t, 1, 0) + row) = pack8_hi(vo[t]);
+          if (SPLIT) {
+            *reinterpret_cast<uint4*>(S + Lay::a_off(t, 0, 1) + row) = pack8_lo(ve[t]);
+            *reinterpret_cast<uint4*>(S + Lay::a_off(t, 1, 1) + row) = pack8_lo(vo[t]);
+          }
         }
       }
-      const uint4 pe = make_uint4(pack_bf16(ve[0], ve[1]), pack_bf16(ve[2], ve[3]), pack_bf16(ve[4], ve[5]),
-                                  pack_bf16(ve[6], ve[7]));
-      const uint4 po = make_uint4(pack_bf16(vo[0], vo[1]), pack_bf16(vo[2], vo[3]), pack_bf16(vo[4], vo[5]),
-                                  pack_bf16(vo[6], vo[7]));
-      *reinterpret_cast<uint4*>(AE + tc::kmajor_offset(tid, k8 * 8, TS_KC)) = pe;
-      *reinterpret_cast<uint4*>(AO + tc::kmajor_offset(tid, k8 * 8, TS_KC)) = po;
+      tc::fence_proxy_async();
+      mbar_arrive(&full[stg]);
     }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (tid == 0) {
-      const uint32_t ae = tc::smem_addr(AE), ao = tc::smem_addr(AO), be = tc::smem_addr(BE), bo = tc::smem_addr(BO);
-      const uint32_t sbo_a = (TS_KC / 8) * 128, sbo_b = (TS_KC / 8) * 128;
-      for (int kk = 0; kk < TS_KC / 16; ++kk) {
-        const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
-        tc::mma_bf16(taddr, tc::smem_desc(ae + kk * 256, 128, sbo_a), tc::smem_desc(be + kk * 256, 128, sbo_b), idesc,
-                     acc);
-        tc::mma_bf16(taddr + TS_N, tc::smem_desc(ao + kk * 256, 128, sbo_a), tc::smem_desc(bo + kk * 256, 128, sbo_b),
-                     idesc, acc);
+  } else {
+    // the MMA warp: lane 0 issues, the warp waits together
+    const uint32_t idesc = tc::idesc_bf16_f32(128, 32);
+    const uint32_t sbo_a = (KC / 8) * 128, sbo_b = (KC / 8) * 128;
+    int issued = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int stg = ch % NSTG;
+      const bool w = tc::mbar_wait(&full[stg], (ch / NSTG) & 1, TS_WAIT);
+      if (!__all_sync(0xffffffffu, w) || __any_sync(0xffffffffu, s_abort != 0)) {
+        if (lane == 0) s_abort = 1;
+        ok = false;
+        break;
       }
-      tc::mma_commit(&mbar[stg]);
+      tc::fence_after_sync();
+      if (lane == 0) {
+        const uint32_t S = tc::smem_addr(t2smem + stg * Lay::STAGE);
+#pragma unroll
+        for (int t = 0; t < T2_TILES; ++t)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const uint32_t d = taddr + (uint32_t)((t * 2 + q) * 32);
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk) {
+              const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
+              const uint64_t ah = tc::smem_desc(S + Lay::a_off(t, q, 0) + kk * 256, 128, sbo_a);
+              const uint64_t bh = tc::smem_desc(S + Lay::b_off(q, 0) + kk * 256, 128, sbo_b);
+              tc::mma_bf16(d, ah, bh, idesc, acc);
+              if (SPLIT) {
+                const uint64_t al = tc::smem_desc(S + Lay::a_off(t, q, 1) + kk * 256, 128, sbo_a);
+                const uint64_t bl = tc::smem_desc(S + Lay::b_off(q, 1) + kk * 256, 128, sbo_b);
+                tc::mma_bf16(d, ah, bl, idesc, 1u);
+                tc::mma_bf16(d, al, bh, idesc, 1u);
+              }
+            }
+          }
+        tc::mma_commit(&empty[stg]);
+      }
+      __syncwarp();
+      issued = ch + 1;
     }
-    ncommit = ch + 1;
-    __syncthreads();  // the staged tables are rewritten next chunk
+    // every MMA is complete once the last committed chunk's phase is
+    // (commits are cumulative); also after an abort, before tensor memory
+    // is read or freed
+    if (issued > 0) {
+      const int cl = issued - 1;
+      const bool w = tc::mbar_wait(&empty[cl % NSTG], (cl / NSTG) & 1, TS_WAIT);
+      if (!__all_sync(0xffffffffu, w)) ok = false;
+    }
   }
-  // Commits are cumulative, so the last committed chunk's phase covers every
-  // MMA issued.  This wait also runs after a give-up, so that tensor memory
-  // is not freed while an MMA may still write it.
-  if (ncommit > 0) {
-    const int cl = ncommit - 1;
-    if (!tc::mbar_wait_block(&mbar[cl & 1], (cl >> 1) & 1, TS_WAIT)) ok = false;
-  }
+  tc::fence_before_sync();
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
   tc::fence_after_sync();
-  if (ok) {
-    float ve[32], vo[32];
-    tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), ve);
-    tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + TS_N, vo);
-    if (p < pend) {
-      const int rn = p, rs = a.nring - 1 - p;
+  if (ok && producer) {
 #pragma unroll
-      for (int r = 0; r < TS_RHS; ++r) {
-        if (r < a.nrhs) {
-          const float er = ve[2 * r], ei = ve[2 * r + 1], orr = vo[2 * r], oi = vo[2 * r + 1];
-          a.phase[r * a.ld_phase + (int64_t)rn * a.ldp + m] = make_float2(er + orr, ei + oi);
-          if (rs != rn) a.phase[r * a.ld_phase + (int64_t)rs * a.ldp + m] = make_float2(er - orr, ei - oi);
+    for (int t = 0; t < T2_TILES; ++t) {
+      float ve[32], vo[32];
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)((t * 2 + 0) * 32), ve);
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)((t * 2 + 1) * 32), vo);
+      if (pp[t] < pend) {
+        const int rn = pp[t], rs = a.nring - 1 - pp[t];
+#pragma unroll
+        for (int r = 0; r < TS_RHS; ++r) {
+          if (r < a.nrhs) {
+            const float er = ve[2 * r], ei = ve[2 * r + 1], orr = vo[2 * r], oi = vo[2 * r + 1];
+            a.phase[r * a.ld_phase + (int64_t)rn * a.ldp + m] = make_float2(er + orr, ei + oi);
+            if (rs != rn) a.phase[r * a.ld_phase + (int64_t)rs * a.ldp + m] = make_float2(er - orr, ei - oi);
+          }
         }
       }
     }
-  } else if (tid == 0) {
+  } else if (!ok && tid == 0) {
     atomicExch(a.status, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(taddr, 64);
+  if (warp == T2_PW) tc::tmem_dealloc(taddr, 32 * 2 * T2_TILES);
 }
 
 // F for nrhs <= 16 right-hand sides of FP32 coefficients into phase
 // [nrhs][nring][L+1] (complex64); status: device int set to 1 if a
 // completion wait gave up
+// Shapes of the pipelined synthesis: K per parity per chunk, stages, split
+// operands.  Variant 0: K 32, 2 stages (72 KB: three CTAs per SM); 1: K 32,
+// 3 stages (108 KB: two CTAs per SM); 2: K 16, 3 stages (54 KB).  With split
+// operands K 16 (the stage holds twice the operands).
+template <bool POLAR, int KC, int NSTG, bool SPLIT>
+static int t2_launch(const TsArgs& a, int nb, int nbp, int yoff, int L, cudaStream_t st) {
+  const size_t smem = (size_t)NSTG * T2Layout<KC, SPLIT>::STAGE;
+  CR_CUDA(cudaFuncSetAttribute(tc_synth2_kernel<POLAR, KC, NSTG, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  if (nb) { tc_synth2_kernel<POLAR, KC, NSTG, SPLIT><<<dim3(nb, L + 1), T2_NT, smem, st>>>(a, nbp, yoff); count_launch(); }
+  return CR_OK;
+}
+
+template <int KC, int NSTG, bool SPLIT>
+static int t2_launch_both(const TsArgs& a, int nbp, int nbe, int L, cudaStream_t st) {
+  int rc = t2_launch<true, KC, NSTG, SPLIT>(a, nbp, nbp, 0, L, st);
+  if (!rc) rc = t2_launch<false, KC, NSTG, SPLIT>(a, nbe, nbp, nbp, L, st);
+  return rc;
+}
+
 int launch_tc_synth(const LegArgs<float>& la, const float2* alm, int64_t ld_alm, int nrhs, float2* phase,
                     int* status, cudaStream_t st) {
   if (la.L < 0 || nrhs <= 0) return CR_OK;
   if (nrhs > TS_RHS) return fail(CR_EINVAL, "tensor-core synthesis: at most 16 right-hand sides per launch");
+  if (la.L + 1 > 65535) return fail(CR_EINVAL, "tensor-core synthesis: lmax too large for the grid");
   TsArgs a;
   a.alm = alm;
   a.ld_alm = ld_alm;
@@ -288,15 +435,21 @@ int launch_tc_synth(const LegArgs<float>& la, const float2* alm, int64_t ld_alm,
   a.npairs = la.npairs;
   a.nring = la.nring;
   a.status = status;
-  const int nbp = (la.npolar + TS_M - 1) / TS_M;
-  const int nbe = (la.npairs - la.npolar + TS_M - 1) / TS_M;
-  const size_t smem = 2 * (size_t)TS_STAGE;
-  CR_CUDA(cudaFuncSetAttribute(tc_synth_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CR_CUDA(cudaFuncSetAttribute(tc_synth_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (la.L + 1 > 65535) return fail(CR_EINVAL, "tensor-core synthesis: lmax too large for the grid");
-  if (nbp) { tc_synth_kernel<true><<<dim3(nbp, la.L + 1), TS_M, smem, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { tc_synth_kernel<false><<<dim3(nbe, la.L + 1), TS_M, smem, st>>>(a, nbp, nbp); count_launch(); }
-  CR_CHECK_LAUNCH("tc_synth_kernel");
+  const int per = 128 * T2_TILES;
+  const int nbp = (la.npolar + per - 1) / per;
+  const int nbe = (la.npairs - la.npolar + per - 1) / per;
+  int rc;
+  if (la.tc_split) {
+    rc = t2_launch_both<16, 3, true>(a, nbp, nbe, la.L, st);
+  } else if (la.tc_variant == 1) {
+    rc = t2_launch_both<32, 3, false>(a, nbp, nbe, la.L, st);
+  } else if (la.tc_variant == 2) {
+    rc = t2_launch_both<16, 3, false>(a, nbp, nbe, la.L, st);
+  } else {
+    rc = t2_launch_both<32, 2, false>(a, nbp, nbe, la.L, st);
+  }
+  if (rc) return rc;
+  CR_CHECK_LAUNCH("tc_synth2_kernel");
   return CR_OK;
 }
 

@@ -373,11 +373,23 @@ static int tuned_rp(const Grid& g, int L, int bytes, int stage) {
   return it == g_tune.end() ? 4 : it->second.rp;
 }
 
+// Tensor-core stage shapes are cached under precision 2 (BF16 operands),
+// stage 2 (batched synthesis); the value is the shape variant of
+// launch_tc_synth (default 2: K 16 per parity, 3 stages)
+constexpr int TC_TUNE_BYTES = 2, TC_TUNE_SYNTH = 2, TC_NVARIANT = 3, TC_DEFAULT_VARIANT = 2;
+static int tuned_tc(const Grid& g, int L) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey{g.nring, g.npix, L, TC_TUNE_BYTES, TC_TUNE_SYNTH});
+  return it == g_tune.end() ? TC_DEFAULT_VARIANT : it->second.rp;
+}
+
 template <typename T>
 static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
   LegArgs<T> a;
   a.rp_synth = tuned_rp(g, L, (int)sizeof(T), 0);
   a.rp_adj = tuned_rp(g, L, (int)sizeof(T), 1);
+  a.tc_split = P->tc_split;
+  a.tc_variant = tuned_tc(g, L);
   a.ldp = L + 1;
   a.L = L;
   a.Lc = P->Lcoef;
@@ -631,9 +643,54 @@ static int tune_stage(cr_plan* P, const Grid& g, int L, int stage, int reps) {
   return CR_OK;
 }
 
+// Time the batched tensor-core synthesis (16 right-hand sides of zeros; the
+// work does not depend on the data) on grid g at band limit L for every
+// stage-shape variant and record the fastest.
+static int tune_tc_stage(cr_plan* P, const Grid& g, int L, int reps) {
+  int rc = tc_begin(P, g, L, false, true);
+  if (rc) return rc;
+  float2* alm = nullptr;
+  const int64_t nlm = n_lm(L);
+  CR_CUDA(cudaMalloc(&alm, 16 * nlm * sizeof(float2)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemsetAsync(alm, 0, 16 * nlm * sizeof(float2), P->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) rc = cuda_fail(e, "autotune setup");
+  TuneVal v{TC_DEFAULT_VARIANT, {-1.0, -1.0, -1.0, -1.0}};
+  for (int i = 0; i < TC_NVARIANT && !rc; ++i) {
+    LegArgs<float> la = leg_args<float>(P, g, L);
+    la.tc_variant = i;
+    la.tc_split = 0;
+    auto run = [&]() { return launch_tc_synth(la, alm, nlm, 16, tc_slot(P, g, L, 0), P->d_tc_status, P->stream); };
+    if ((rc = run())) break;
+    if ((e = cudaEventRecord(e0, P->stream)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    for (int k = 0; k < reps && !rc; ++k) rc = run();
+    if (!rc && (e = cudaEventRecord(e1, P->stream)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    if (!rc && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    float ms = 0.f;
+    if (!rc && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
+    v.ms[i] = ms / reps;
+  }
+  if (!rc) {
+    int best = 0;
+    for (int i = 0; i < TC_NVARIANT; ++i)
+      if (v.ms[i] < v.ms[best]) best = i;
+    v.rp = best;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(alm);
+  if (!rc) rc = tc_end(P, "autotune: a tensor-core completion wait gave up");
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[TuneKey{g.nring, g.npix, L, TC_TUNE_BYTES, TC_TUNE_SYNTH}] = v;
+  return CR_OK;
+}
+
 // every (grid, band limit) the plan transforms on: the observation grid at
 // lmax and, with levels, each pixel level's grid and inverse-noise grid at
-// lmax_h; both precisions, both stages
+// lmax_h; both precisions, both stages, and the tensor-core synthesis shape
 int autotune_plan(cr_plan* P, int reps) {
   std::vector<std::pair<const Grid*, int>> todo{{&P->obs, P->lmax}};
   if (P->hier)
@@ -651,6 +708,8 @@ int autotune_plan(cr_plan* P, int reps) {
       if (!rc) rc = tune_stage<double>(P, *t.first, t.second, stage, reps);
       if (rc) return rc;
     }
+    int rc = tune_tc_stage(P, *t.first, t.second, reps);
+    if (rc) return rc;
   }
   return CR_OK;
 }
@@ -672,7 +731,8 @@ int tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* bytes, int* sta
 }
 
 int tune_set(int nring, int64_t npix, int lmax, int bytes, int stage, int rp) {
-  if ((bytes != 4 && bytes != 8) || (stage != 0 && stage != 1) || lmax < 0 || !rp_allowed(rp, bytes, stage))
+  const bool tc = bytes == TC_TUNE_BYTES && stage == TC_TUNE_SYNTH && rp >= 0 && rp < TC_NVARIANT;
+  if (!tc && ((bytes != 4 && bytes != 8) || (stage != 0 && stage != 1) || lmax < 0 || !rp_allowed(rp, bytes, stage)))
     return fail(CR_EINVAL, "cr_tune_set: bad choice");
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[TuneKey{nring, npix, lmax, bytes, stage}] = TuneVal{rp, {0.0, 0.0, 0.0, -1.0}};
@@ -740,6 +800,7 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   P->p = *p;
   P->stream = reinterpret_cast<cudaStream_t>(p->stream);
   P->fp64_df = p->fp64_df ? 1 : 0;
+  P->tc_split = p->tc_split ? 1 : 0;
   P->lmax = p->lmax;
   P->levels.resize(1);
   P->levels[0].lmax_h = p->lmax;

@@ -46,11 +46,14 @@ def test_autotune_records_and_keeps_fastest():
     plan = binding.Plan(lmax, nside=nside, cl=cl, bl=bl, ninv=ninv, levels="default", ridge_bisections=8)
     table = plan.autotune()
     g = geometry.healpix_grid(nside)
-    obs = [t for t in table if t["nring"] == g["nring"] and t["lmax"] == lmax]
+    obs = [t for t in table if t["nring"] == g["nring"] and t["lmax"] == lmax and t["precision"] != "bf16"]
     assert len(obs) == 4
     for t in obs:
         assert all(v > 0 for v in t["ms"].values())
         assert t["pairs_per_thread"] == min(t["ms"], key=t["ms"].get)
+    tc = [t for t in table if t["nring"] == g["nring"] and t["lmax"] == lmax and t["precision"] == "bf16"]
+    assert len(tc) == 1 and sorted(tc[0]["ms"]) == [0, 1, 2]
+    assert tc[0]["variant"] == min(tc[0]["ms"], key=tc[0]["ms"].get)
     # levels' grids are tuned too
     assert len({(t["nring"], t["lmax"]) for t in table}) > 1
     # the tuned plan still solves to the exact answer
@@ -60,3 +63,21 @@ def test_autotune_records_and_keeps_fastest():
     x = torch.zeros_like(b)
     plan.solve(b, x, eps=1e-20, max_cycles=40, mode=binding.CR_MIXED | binding.CR_PCG, check=False)
     assert rel_l2(x.cpu().numpy(), xt.cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_tensor_core_shape_matches_oracle(variant):
+    """Each stage shape of the batched tensor-core synthesis (K per parity
+    and pipeline depth) computes the same transform: 16 right-hand sides
+    within BF16 accuracy of the FP64 oracle."""
+    dev = cuda_device()
+    nside, lmax, nrhs = 64, 191, 16
+    g = geometry.healpix_grid(nside)
+    binding.tune_set(g["nring"], g["npix"], lmax, "bf16", "tc_synthesis", variant)
+    plan = binding.Plan(lmax, nside=nside)
+    a = np.stack([synthetic.random_alm(lmax, seed=40 + j) for j in range(nrhs)])
+    m = torch.empty((nrhs, g["npix"]), dtype=torch.float32, device=dev)
+    plan.sht_synth(torch.from_numpy(a).to(torch.complex64).to(dev), m, tensor_cores=True)
+    mh = m.cpu().numpy().astype(np.float64)
+    for j in range(nrhs):
+        assert rel_l2(mh[j], sht.synth(a[j], lmax, g)) < 5e-3, (variant, j)

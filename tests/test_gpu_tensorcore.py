@@ -14,6 +14,17 @@ def test_tcgen05_tile_matches_cuda_cores(K):
     assert binding.tc_selftest(K) == 0.0
 
 
+@pytest.mark.parametrize("K", [16, 64])
+def test_tcgen05_mn_major_tile(K):
+    """The transposed (MN-major) operand layout with the MN stride in the
+    descriptor's leading byte offset reproduces the CUDA-core product
+    exactly; the other reading of the two offsets does not."""
+    cuda_device()
+    e0, e1 = binding.tc_selftest_mn(K, 0), binding.tc_selftest_mn(K, 1)
+    print("MN-major tile K=%d: max |error| %g (MN stride as leading offset), %g (swapped)" % (K, e0, e1))
+    assert e0 == 0.0 and e1 > 0.0
+
+
 import numpy as np
 import torch
 
@@ -22,20 +33,31 @@ from oracle import geometry, sht
 from paper_1308_5299_gb300 import synthetic
 
 
-@pytest.mark.parametrize("nside,lmax,nrhs", [(8, 23, 3), (32, 95, 20), (64, 191, 16)])
-def test_tensor_core_batched_synthesis_matches_oracle(nside, lmax, nrhs):
+# BF16 operands: the rounding model of tests/test_bf16_error_model.py gives
+# 2.4e-3 relative L2 per transform; hi + lo operands (three MMAs): ~2^-17
+# per product, so the FP32 recurrence's ~1e-6 dominates
+TOL_BF16 = 5e-3
+TOL_SPLIT = 3e-5
+
+
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("nside,lmax,nrhs", [(8, 23, 3), (32, 95, 20), (64, 191, 16), (256, 767, 16)])
+def test_tensor_core_batched_synthesis_matches_oracle(nside, lmax, nrhs, split):
     """Batched synthesis with the Legendre contraction on the tensor cores
-    (BF16 operands, FP32 accumulation): every right-hand side within BF16
-    accuracy of the FP64 oracle."""
+    (BF16 operands, or hi + lo BF16 pairs, FP32 accumulation): every
+    right-hand side within the operands' accuracy of the FP64 oracle."""
     dev = cuda_device()
     g = geometry.healpix_grid(nside)
-    plan = binding.Plan(lmax, nside=nside)
+    plan = binding.Plan(lmax, nside=nside, tc_split=split)
     a = np.stack([synthetic.random_alm(lmax, seed=900 + j) for j in range(nrhs)])
     m = torch.empty((nrhs, g["npix"]), dtype=torch.float32, device=dev)
     plan.sht_synth(torch.from_numpy(a).to(torch.complex64).to(dev), m, tensor_cores=True)
     mh = m.cpu().numpy().astype(np.float64)
-    for j in range(nrhs):
-        assert rel_l2(mh[j], sht.synth(a[j], lmax, g)) < 1e-2, j
+    errs = [rel_l2(mh[j], sht.synth(a[j], lmax, g)) for j in range(nrhs)]
+    print("tensor-core synthesis nside %d lmax %d split %s: max rel L2 %.2e" % (nside, lmax, split, max(errs)))
+    tol = TOL_SPLIT if split else TOL_BF16
+    for j, e in enumerate(errs):
+        assert e < tol, (j, e)
 
 
 def test_tensor_core_batched_synthesis_full_size_sampled_rings():
@@ -55,7 +77,7 @@ def test_tensor_core_batched_synthesis_full_size_sampled_rings():
         ref = sht.synth(a[j], lmax, g, rings=rings)
         mh = m[jj].cpu().numpy().astype(np.float64)
         sel = np.concatenate([np.arange(g["off"][k], g["off"][k] + g["nphi"][k]) for k in rings])
-        assert rel_l2(mh[sel], ref[sel]) < 1e-2
+        assert rel_l2(mh[sel], ref[sel]) < TOL_BF16
     # throughput: 16 right-hand sides on the tensor cores vs 16 FP32 syntheses
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -84,7 +106,7 @@ def test_tensor_core_batched_adjoint_matches_oracle(nside, lmax, nrhs):
     l, m = sht.lm_arrays(lmax)
     assert np.all(oh[:, m == 0].imag == 0)
     for j in range(nrhs):
-        assert rel_l2(oh[j], sht.adjoint(maps[j], lmax, g)) < 1e-2, j
+        assert rel_l2(oh[j], sht.adjoint(maps[j], lmax, g)) < TOL_BF16, j
 
 
 @pytest.mark.parametrize("name,nrhs", [("nside32_lmax95", 18), ("nside16_lmax47", 5)])
@@ -103,7 +125,7 @@ def test_tensor_core_batched_apply_A_matches_oracle(name, nrhs):
     plan.apply_A(torch.from_numpy(xs).to(torch.complex64).to(dev), y, tensor_cores=True)
     yh = y.cpu().numpy().astype(np.complex128)
     for j in range(nrhs):
-        assert rel_l2(yh[j], operators.apply_A(prob, xs[j])) < 1e-2, j
+        assert rel_l2(yh[j], operators.apply_A(prob, xs[j])) < TOL_BF16, j
 
 
 def test_tensor_core_batched_adjoint_full_size_sampled_rings():
@@ -127,7 +149,7 @@ def test_tensor_core_batched_adjoint_full_size_sampled_rings():
     plan.sht_adjoint(mt, out, tensor_cores=True)
     for j, jj in [(0, 0), (1, nrhs - 1)]:
         ref = sht.adjoint(maps[j], lmax, g, rings=rings)
-        assert rel_l2(out[jj].cpu().numpy().astype(np.complex128), ref) < 1e-2
+        assert rel_l2(out[jj].cpu().numpy().astype(np.complex128), ref) < TOL_BF16
     assert float(out[1:nrhs - 1].abs().max()) == 0.0
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
