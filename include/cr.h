@@ -198,8 +198,9 @@ typedef struct cr_params {
    * ridge_factor) and raised under ridge_lambda_target. */
   int smoother;
   /* triangular sweeps of the ICC(0) smoother: 0 = automatic (levels of at
-   * most 16384 tiles run both sweeps of one application in one cooperative
-   * persistent launch, larger levels one launch per colour); 1 = one launch
+   * most 1024 tiles, Nside_h <= 64, run both sweeps of one application in
+   * one cooperative persistent launch, larger levels one launch per
+   * colour); 1 = one launch
    * per colour on every level; 2 = the cooperative launch wherever the
    * device supports it.  The same operator either way. */
   int smoother_sweep;
@@ -396,7 +397,9 @@ int cr_tc_selftest(int K, float* max_abs_err);
  * 8 K rows x 8 MN elements, 128 bytes apart along MN and (MN / 8) * 128
  * bytes apart along K.  swap = 0 passes the MN stride as the descriptor's
  * leading byte offset and the K stride as its stride byte offset, swap = 1
- * the other way round (the operand buffers are large enough for either).
+ * the other way round (the operand buffers are large enough for either);
+ * swap = 1 is the reading the hardware uses for this layout (exact on
+ * GB300), and the batched adjoint's descriptors follow it.
  * Errors: CR_EINVAL, CR_ECUDA. */
 int cr_tc_selftest_mn(int K, int swap, float* max_abs_err);
 

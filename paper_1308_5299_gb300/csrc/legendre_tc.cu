@@ -677,6 +677,262 @@ __global__ void __launch_bounds__(TA_K) tc_adjoint_kernel(TaArgs a, int nbp, int
   if (warp == 0) tc::tmem_dealloc(taddr, TA_N);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised batched adjoint.  The same contraction as
+// tc_adjoint_kernel, D[l, 64] = Q[l, pairs] G[pairs, 64] per chunk of 128 l,
+// with the operands in the MN-major layout (each 16-byte row of a core
+// matrix is 8 consecutive MN elements of one K index), so that a thread --
+// which owns one ring pair, i.e. one K index -- writes 8 consecutive l of
+// its pair (A) or 8 consecutive columns of G (B) in one store and no
+// shuffle transposition is needed.  Three roles:
+//  - warps 0-3 (producers): every thread runs its pair's FP32 recurrence
+//    and writes the chunk's A column; chunks go through two shared-memory
+//    stages (full / empty mbarriers);
+//  - warp 4 (MMA): waits until a stage is full and its accumulator buffer
+//    is free, issues the chunk's K = 128 MMAs (M 128, N 64) into one of two
+//    tensor-memory accumulators and commits to the stage's "empty" and the
+//    accumulator's "full" mbarriers;
+//  - warps 5-8 (epilogue): read a finished accumulator (each warp its lane
+//    quarter: 32 l rows), release it, and write s_lm times the row's parity
+//    half as the partial rows of 16 right-hand sides.
+// The chunk loop has no block-wide barrier; every wait is bounded.
+constexpr int T3_M = 128;                  // l per chunk (rows of D)
+constexpr int T3_K = 128;                  // ring pairs per CTA
+constexpr int T3_N = 64;                   // 16 RHS x (Re, Im) x parity
+constexpr int T3_NT = 32 * 9;
+constexpr int T3_A_BYTES = T3_M * T3_K * 2;   // 32 KB
+constexpr int T3_B_BYTES = T3_N * T3_K * 2;   // 16 KB
+constexpr int T3_NSTG = 2;
+
+// MN-major no-swizzle offset of element (mn, k) of an operand with MN rows:
+// core matrices 128 bytes apart along MN, (MN / 8) * 128 apart along K (the
+// tile self-test cr_tc_selftest_mn checks this layout and which descriptor
+// offset carries which stride)
+__device__ __forceinline__ uint32_t mn_off(int mn, int k, int MN) {
+  return (uint32_t)(((mn >> 3) << 7) + (k >> 3) * (MN / 8) * 128 + ((k & 7) << 4) + ((mn & 7) << 1));
+}
+
+template <bool POLAR>
+__global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, int yoff) {
+  extern __shared__ __align__(1024) uint8_t t3smem[];
+  uint8_t* Bsm = t3smem + T3_NSTG * T3_A_BYTES;
+  __shared__ float s_c[4][T3_M], s_c2[POLAR ? 4 : 1][T3_M];
+  __shared__ uint64_t a_full[T3_NSTG], a_empty[T3_NSTG], d_full[2], d_free[2];
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_min;
+  __shared__ volatile int s_abort;
+  const int m = blockIdx.y;
+  const int L = a.L;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int yb = (int)blockIdx.x + yoff;
+  const int base = POLAR ? yb * T3_K : a.npolar + (yb - nbp) * T3_K;
+  const int pend = POLAR ? a.npolar : a.npairs;
+  const bool producer = warp < 4, mma_warp = warp == 4, epilogue = warp >= 5;
+  const int p = base + tid;  // producers' ring pair
+  int ls = L + 1;
+  float P1 = 0.f, P2 = 0.f, zz = 0.f;
+  if (producer && p < pend) {
+    const int64_t o = (int64_t)m * a.ld_seed + p;
+    zz = POLAR ? a.w[p] : a.z[p];
+    const int l = a.ls[o];
+    if (l <= L) {
+      const float2 st = a.st[o];
+      ls = l;
+      P1 = st.x;
+      P2 = st.y;
+    }
+  }
+  if (tid == 0) {
+    s_min = L + 1;
+    s_abort = 0;
+  }
+  __syncthreads();
+  if (producer && ls <= L) atomicMin(&s_min, ls);
+  __syncthreads();
+  const int cmin = s_min;
+  const int64_t offa = lm_off(L, m), offc = lm_off(a.Lc, m);
+  const int64_t rstride = (int64_t)a.nblk * a.nlm;
+  float2* part = a.partial + (int64_t)yb * a.nlm + offa;
+  const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~1) : L + 1;
+  // rows before the block's earliest start are zero
+  for (int r = 0; r < a.nrhs; ++r)
+    for (int l = m + tid; l < lbeg; l += T3_NT) part[r * rstride + (l - m)] = make_float2(0.f, 0.f);
+  if (cmin > L) return;
+  const int nch = (L + 1 - lbeg + T3_M - 1) / T3_M;
+
+  // B operand (G of this CTA's pairs, all chunks): column n = 2 r (+1 Im)
+  // of the even combination, 32 + 2 r (+1) of the odd one; K = the pair
+  if (producer) {
+    const bool live = p < pend && ls <= L;
+    const int rn = p, rs = a.nring - 1 - p;
+    float ve[32], vo[32];
+#pragma unroll
+    for (int r = 0; r < TS_RHS; ++r) {
+      float2 gn = make_float2(0.f, 0.f), gs = make_float2(0.f, 0.f);
+      if (live && r < a.nrhs) {
+        gn = a.phase[r * a.ld_phase + (int64_t)rn * a.ldp + m];
+        if (rs != rn) gs = a.phase[r * a.ld_phase + (int64_t)rs * a.ldp + m];
+      }
+      ve[2 * r] = gn.x + gs.x;
+      ve[2 * r + 1] = gn.y + gs.y;
+      vo[2 * r] = gn.x - gs.x;
+      vo[2 * r + 1] = gn.y - gs.y;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      *reinterpret_cast<uint4*>(Bsm + mn_off(8 * g, tid, T3_N)) = pack8_hi(ve + 8 * g);
+      *reinterpret_cast<uint4*>(Bsm + mn_off(32 + 8 * g, tid, T3_N)) = pack8_hi(vo + 8 * g);
+    }
+  }
+  if (mma_warp) tc::tmem_alloc(&taddr_s, 2 * T3_N);
+  if (tid == 0) {
+    for (int i = 0; i < T3_NSTG; ++i) {
+      tc::mbar_init(&a_full[i], 128);
+      tc::mbar_init(&a_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&d_full[i], 1);
+      tc::mbar_init(&d_free[i], 128);
+    }
+    tc::mbar_fence_init();
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = taddr_s;
+  bool ok = true;
+
+  if (producer) {
+    float* sc = s_c[warp];
+    float* sc2 = s_c2[POLAR ? warp : 0];
+    float qc[T3_M / 32], qc2[T3_M / 32];
+    auto prefetch_coef = [&](int l0n) {
+#pragma unroll
+      for (int u = 0; u < T3_M / 32; ++u) {
+        const int l = l0n + lane + 32 * u;
+        const bool in = l <= L;
+        qc[u] = in ? a.c[offc + (l - m)] : 0.f;
+        qc2[u] = (POLAR && in) ? a.c2[offc + (l - m)] : 0.f;
+      }
+    };
+    prefetch_coef(lbeg);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int stg = ch % T3_NSTG;
+      const int l0 = lbeg + ch * T3_M;
+      if (ch >= T3_NSTG) {
+        const bool w = tc::mbar_wait(&a_empty[stg], ((ch / T3_NSTG) - 1) & 1, TS_WAIT);
+        if (!__all_sync(0xffffffffu, w)) {
+          if (lane == 0) s_abort = 1;
+          ok = false;
+          break;
+        }
+      }
+      if (__any_sync(0xffffffffu, s_abort != 0)) {
+        ok = false;
+        break;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < T3_M / 32; ++u) {
+        sc[lane + 32 * u] = qc[u];
+        if (POLAR) sc2[lane + 32 * u] = qc2[u];
+      }
+      __syncwarp();
+      if (ch + 1 < nch) prefetch_coef(l0 + T3_M);
+      uint8_t* A = t3smem + stg * T3_A_BYTES;
+      const bool full_chunk = (ls <= l0) && (l0 + T3_M - 1 <= L);
+#pragma unroll 1
+      for (int g = 0; g < T3_M / 8; ++g) {
+        float v[8];
+        if (full_chunk) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = tstep<POLAR>(sc[8 * g + j], POLAR ? sc2[8 * g + j] : 0.f, zz, P1, P2);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int l = l0 + 8 * g + j;
+            v[j] = 0.f;
+            if (l >= ls && l <= L) v[j] = tstep<POLAR>(sc[8 * g + j], POLAR ? sc2[8 * g + j] : 0.f, zz, P1, P2);
+          }
+        }
+        *reinterpret_cast<uint4*>(A + mn_off(8 * g, tid, T3_M)) = pack8_hi(v);
+      }
+      tc::fence_proxy_async();
+      mbar_arrive(&a_full[stg]);
+    }
+  } else if (mma_warp) {
+    // D = A B^T with A (M x K) and B (N x K) both MN-major: transpose bits
+    const uint32_t idesc = tc::idesc_bf16_f32(T3_M, T3_N) | (1u << 15) | (1u << 16);
+    const uint32_t a_kstride = (T3_M / 8) * 128, b_kstride = (T3_N / 8) * 128;
+    const uint32_t bb = tc::smem_addr(Bsm);
+    int issued = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int stg = ch % T3_NSTG, db = ch & 1;
+      bool w = tc::mbar_wait(&a_full[stg], (ch / T3_NSTG) & 1, TS_WAIT);
+      if (w && ch >= 2) w = tc::mbar_wait(&d_free[db], ((ch >> 1) - 1) & 1, TS_WAIT);
+      if (!__all_sync(0xffffffffu, w) || __any_sync(0xffffffffu, s_abort != 0)) {
+        if (lane == 0) s_abort = 1;
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      if (lane == 0) {
+        const uint32_t aa = tc::smem_addr(t3smem + stg * T3_A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < T3_K / 16; ++kk)
+          // MN-major without swizzle: leading byte offset = the K-direction
+          // core-matrix stride, stride byte offset = the MN-direction one
+          tc::mma_bf16(taddr + (uint32_t)(db * T3_N), tc::smem_desc(aa + kk * 2 * a_kstride, a_kstride, 128),
+                       tc::smem_desc(bb + kk * 2 * b_kstride, b_kstride, 128), idesc, kk > 0 ? 1u : 0u);
+        tc::mma_commit(&a_empty[stg]);
+        tc::mma_commit(&d_full[db]);
+      }
+      __syncwarp();
+      issued = ch + 1;
+    }
+    if (issued > 0) {
+      const int cl = issued - 1;
+      const bool w = tc::mbar_wait(&a_empty[cl % T3_NSTG], (cl / T3_NSTG) & 1, TS_WAIT);
+      if (!__all_sync(0xffffffffu, w)) ok = false;
+    }
+  } else {
+    // epilogue: warp 5 + q reads TMEM lanes 32 ((5 + q) % 4) ...
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int db = ch & 1;
+      const bool w = tc::mbar_wait(&d_full[db], (ch >> 1) & 1, TS_WAIT);
+      if (!__all_sync(0xffffffffu, w) || __any_sync(0xffffffffu, s_abort != 0)) {
+        if (lane == 0) s_abort = 1;
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      float ve[32], vo[32];
+      tc::tmem_ld32(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(db * T3_N), ve);
+      tc::tmem_ld32(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(db * T3_N + 32), vo);
+      tc::fence_before_sync();
+      mbar_arrive(&d_free[db]);
+      const int l = lbeg + ch * T3_M + row;
+      if (l <= L) {
+        const float sl = a.s[offc + (l - m)];
+        const bool odd = ((l - m) & 1) != 0;
+#pragma unroll
+        for (int r = 0; r < TS_RHS; ++r)
+          if (r < a.nrhs)
+            part[r * rstride + (l - m)] =
+                make_float2((odd ? vo[2 * r] : ve[2 * r]) * sl, (odd ? vo[2 * r + 1] : ve[2 * r + 1]) * sl);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  tc::fence_after_sync();
+  if (!ok && tid == 0) atomicExch(a.status, 1);
+  if (mma_warp) tc::tmem_dealloc(taddr, 2 * T3_N);
+}
+
 // G of nrhs <= 16 right-hand sides (phase [nrhs][nring][L+1], complex64) ->
 // partial rows [nrhs][nblk][n_lm(L)] (s_lm applied); *nblk receives the
 // number of ring-pair blocks.  status: device int set to 1 if a completion
@@ -715,12 +971,12 @@ int launch_tc_adjoint(const LegArgs<float>& la, const float2* phase, int nrhs, f
   a.npairs = la.npairs;
   a.nring = la.nring;
   a.status = status;
-  const size_t smem = (size_t)TA_A_BYTES + TA_B_BYTES;
-  CR_CUDA(cudaFuncSetAttribute(tc_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CR_CUDA(cudaFuncSetAttribute(tc_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (nbp) { tc_adjoint_kernel<true><<<dim3(nbp, la.L + 1), TA_K, smem, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { tc_adjoint_kernel<false><<<dim3(nbe, la.L + 1), TA_K, smem, st>>>(a, nbp, nbp); count_launch(); }
-  CR_CHECK_LAUNCH("tc_adjoint_kernel");
+  const size_t smem = (size_t)T3_NSTG * T3_A_BYTES + T3_B_BYTES;
+  CR_CUDA(cudaFuncSetAttribute(tc_adjoint2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CR_CUDA(cudaFuncSetAttribute(tc_adjoint2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (nbp) { tc_adjoint2_kernel<true><<<dim3(nbp, la.L + 1), T3_NT, smem, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { tc_adjoint2_kernel<false><<<dim3(nbe, la.L + 1), T3_NT, smem, st>>>(a, nbp, nbp); count_launch(); }
+  CR_CHECK_LAUNCH("tc_adjoint2_kernel");
   return CR_OK;
 }
 

@@ -932,12 +932,13 @@ int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
   return CR_OK;
 }
 
-// Levels with at most SW_MAX_TILES tiles run both triangular sweeps of a
-// smoother application in one cooperative launch of
+// Levels with at most SW_MAX_TILES tiles (Nside_h <= 64) run both
+// triangular sweeps of a smoother application in one cooperative launch of
 // min(SMs, largest colour) CTAs (one per SM: the block slots take most of
-// its shared memory); larger levels keep one launch per colour, whose wide
-// colours stream the factor at close to the HBM rate.
-constexpr int SW_MAX_TILES = 16384;
+// its shared memory); larger levels keep one launch per colour, which is
+// faster there (measured at Nside_h 128 and up: the wide colours stream the
+// factor at close to the HBM rate).
+constexpr int SW_MAX_TILES = 1024;
 
 static int choose_coop_grid(cr_plan* P, PixLevel& lev) {
   lev.coop_grid = 0;

@@ -16,13 +16,16 @@ def test_tcgen05_tile_matches_cuda_cores(K):
 
 @pytest.mark.parametrize("K", [16, 64])
 def test_tcgen05_mn_major_tile(K):
-    """The transposed (MN-major) operand layout with the MN stride in the
-    descriptor's leading byte offset reproduces the CUDA-core product
-    exactly; the other reading of the two offsets does not."""
+    """The transposed (MN-major) operand layout without swizzle, the one the
+    batched adjoint writes: with the K-direction core-matrix stride in the
+    descriptor's leading byte offset and the MN-direction stride in its
+    stride byte offset the tile reproduces the CUDA-core product exactly;
+    the other reading of the two offsets does not."""
     cuda_device()
-    e0, e1 = binding.tc_selftest_mn(K, 0), binding.tc_selftest_mn(K, 1)
-    print("MN-major tile K=%d: max |error| %g (MN stride as leading offset), %g (swapped)" % (K, e0, e1))
-    assert e0 == 0.0 and e1 > 0.0
+    e_mn_lead, e_k_lead = binding.tc_selftest_mn(K, 0), binding.tc_selftest_mn(K, 1)
+    print("MN-major tile K=%d: max |error| %g (K stride as leading offset), %g (MN stride as leading offset)"
+          % (K, e_k_lead, e_mn_lead))
+    assert e_k_lead == 0.0 and e_mn_lead > 0.0
 
 
 import numpy as np
