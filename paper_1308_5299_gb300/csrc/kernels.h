@@ -68,7 +68,6 @@ struct RingArgs {
   int nring = 0;
   const int* rings = nullptr;  // ring indices ordered by FFT size (device)
   int rbase = 0;               // first entry of this launch's class
-  int cls_Mcur = 0;            // FFT buffer length of this launch's class (twiddles follow it)
   int nclass = 0;              // host: FFT-size classes
   const int* cls_M = nullptr;
   const int* cls_start = nullptr;

@@ -27,8 +27,7 @@
 // reduction into the ring length's table of e^{i pi u / n}, u < 2n.
 //
 // One CTA per ring; mode 2 keeps the ring's map in shared memory between the
-// synthesis and the adjoint (map * N^-1 never touches HBM).  The ring's
-// twiddle factors are copied once into shared memory behind the FFT buffer.
+// synthesis and the adjoint (map * N^-1 never touches HBM).
 #include <algorithm>
 #include <cstdio>
 #include <map>
@@ -200,14 +199,6 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
   const int L = a.L;
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
-  // this ring's twiddles e^{-2 pi i j / M}, j < M / 2, copied once into
-  // shared memory behind the FFT buffer (the launch sizes it for the class's
-  // largest M): the butterfly passes then read them without global latency
-  C* twm = buf + a.cls_Mcur;
-  {
-    const int step = a.Mmax / M;
-    for (int j = tid; j < M / 2; j += NT) twm[j] = a.tw[j * step];
-  }
   // e^{i pi (2 k^2 mod 2n) / n}; 2 k^2 < 2^31 for k < 2^15
   auto chirp = [&](int k) -> C { return tab[(int)((2u * (unsigned)k * (unsigned)k) % (unsigned)twon)]; };
 
@@ -285,12 +276,12 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
       for (int k = nh + tid; k < M; k += NT) buf[swz(k)] = mk((T)0, (T)0);
     __syncthreads();
     if (!f.bluestein) {
-      fft_dit(buf, M, lg, +1, twm, M);
+      fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
     } else {
-      fft_dif(buf, M, lg, -1, twm, M);
+      fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
       for (int i = tid; i < M; i += NT) buf[swz(i)] = cmul(buf[swz(i)], vh[i]);
       __syncthreads();
-      fft_dit(buf, M, lg, +1, twm, M);
+      fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
       for (int t = tid; t < nh; t += NT) buf[swz(t)] = cmul(buf[swz(t)], chirp(t));
       __syncthreads();
     }
@@ -327,12 +318,12 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
 
   // forward length-nh DFT of z_t = y_{2t} + i y_{2t+1}
   if (!f.bluestein) {
-    fft_dif(buf, M, lg, -1, twm, M);  // Z'_k at buf[bitrev(k)]
+    fft_dif(buf, M, lg, -1, a.tw, a.Mmax);  // Z'_k at buf[bitrev(k)]
   } else {
-    fft_dif(buf, M, lg, -1, twm, M);
+    fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
     for (int i = tid; i < M; i += NT) buf[swz(i)] = cmul(buf[swz(i)], vh[i]);
     __syncthreads();
-    fft_dit(buf, M, lg, +1, twm, M);  // Z'_k = conj(buf[k] chirp(k))
+    fft_dit(buf, M, lg, +1, a.tw, a.Mmax);  // Z'_k = conj(buf[k] chirp(k))
   }
   auto getZ = [&](int k) -> C {
     return f.bluestein ? cconj(cmul(buf[swz(k)], chirp(k))) : buf[swz(bitrev(k, lg))];
@@ -363,14 +354,12 @@ int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st) {
     const int M = a.cls_M[c];
     const int cnt = a.cls_start[c + 1] - a.cls_start[c];
     if (cnt <= 0) continue;
-    // the FFT buffer and the twiddle table (M / 2 entries)
-    const size_t smem = (size_t)(M + M / 2) * sizeof(C);
+    const size_t smem = (size_t)M * sizeof(C);
     if (smem > 227 * 1024 || M > 65536) return fail(CR_EINVAL, "ring FFT buffer exceeds shared memory");
     // at least 128 threads: small rings split their folds over the idle lanes
     const int nt = std::max(128, std::min(RF_NT, M / 8));
     RingArgs<T> b = a;
     b.rbase = a.cls_start[c];
-    b.cls_Mcur = M;
     switch (mode) {
       case 0:
         CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -485,9 +474,7 @@ int build_fft_tables(Grid& g, cudaStream_t st) {
     f.tab = d.tab;
     f.vhat = d.vhat;
   }
-  // the FP64 ring stage holds the buffer and half as many twiddles
-  if ((size_t)(Mmax + Mmax / 2) * sizeof(double2) > 227 * 1024)
-    return fail(CR_EINVAL, "ring too long for the shared-memory FFT");
+  if ((size_t)Mmax * sizeof(double2) > 227 * 1024) return fail(CR_EINVAL, "ring too long for the shared-memory FFT");
   g.Mmax = Mmax;
   g.tab_len = tab_len;
   g.vhat_len = vhat_len;
