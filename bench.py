@@ -263,6 +263,33 @@ def cpu_baseline(nside, lmax, levels, cycles, full=True):
     return out
 
 
+def oracle_cg_baseline(iterations, workload="nside256_lmax767", k=3):
+    """The oracle's own diagonal-preconditioned CG (plain FP64 direct SHTs on
+    the host cores) on the Nside 256 workload: k iterations timed and priced
+    at the GPU CG's iteration count (the whole solve would take hours).
+    Part of the CPU baseline."""
+    import numpy as np
+
+    from oracle import geometry, operators, solvers
+    from paper_1308_5299_gb300 import synthetic
+
+    cfg, cl, bl, ninv = synthetic.problem_inputs(workload)
+    g = geometry.healpix_grid(cfg["nside"])
+    prob = operators.Problem(cfg["lmax"], cl, bl, ninv, g)
+    l = prob.l
+    with np.errstate(divide="ignore"):
+        sinv = np.where(prob.active, 1.0 / np.where(prob.active, cl[l], 1.0), 0.0)
+    dg = sinv + bl[l] ** 2 * operators.diag_inv_noise_dm0(prob)
+    pc = np.where(prob.active & (dg > 0), 1.0 / np.where(dg > 0, dg, 1.0), 0.0)
+    b = operators.apply_A(prob, prob.clean(synthetic.draw_prior(cl, index=7)))
+    t0 = time.perf_counter()
+    solvers.pcg(lambda v: operators.apply_A(prob, v), b, pc, prob.lmax, tol=0.0, maxiter=k)
+    per_it = (time.perf_counter() - t0) / k
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"workload": workload, "s_per_iteration": per_it, "iterations_timed": k, "cores": cores,
+            "iterations": iterations, "s_extrapolated": per_it * iterations if iterations else None}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the oracle on the machine's host cores.  Once, the
     full-size observation-grid SHT pair and A (a minute or so); then every
@@ -330,33 +357,82 @@ def max_pixel_error(plan, x, x_true, npix, dev):
     return float(m.abs().max())
 
 
-# ALU peaks derived from unit counts and clocks (152 SMs at 2070 MHz): FP32
-# 128 FMA lanes per SM -> 152 * 128 * 2 * 2.07e9 = 80.5 TFLOP/s; FP64 the
-# part's nominal 1.25 TFLOP/s (about 2 FMA per SM per clock).  An FMA-loop
-# probe on this pool measured 74.5 (FP32) and 1.19 (FP64) TFLOP/s.
+# Nominal FMA-pipe rates (152 SMs at 2070 MHz): FP32 128 FMA lanes per SM ->
+# 80.5 TFLOP/s; FP64 the part's 1.25 TFLOP/s.  The roofline uses the rates
+# measured live by the library's FMA probe (cr_probe_fma_peak) and falls back
+# to these only if the probe cannot run.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 
 # stages that time a sequence of kernels rather than one kernel
 COMPOSITE = {"outer_residual"}
 
+# ncu DRAM traffic per launch of the dominant kernels, read from the profile
+# summaries committed under profiles/ (a line "traffic_bytes_per_launch: N"
+# beside the kernel's name and template arguments)
+TRAFFIC_FILES = {"legendre_adjoint_f64": "legendre_adjoint_f64_dram_nside2048_lmax3000.txt",
+                 "legendre_synth_f64": "legendre_synth_f64_dram_nside2048_lmax3000.txt"}
 
-def roofline_of(stages, steps):
+
+def profile_traffic(stage):
+    fn = TRAFFIC_FILES.get(stage)
+    if not fn:
+        return None, None
+    path = os.path.join(ROOT, "profiles", fn)
+    try:
+        vals = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        return float(vals["traffic_bytes_per_launch"]), vals.get("kernel")
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
+def live_peaks(binding):
+    """FMA-pipe peaks measured now on this GPU (TFLOP/s)."""
+    out = {}
+    for k in ("f32", "f32x2", "f64"):
+        try:
+            out[k] = binding.fma_peak(k)
+        except Exception:  # noqa: BLE001 -- report what could be measured
+            out[k] = None
+    return out
+
+
+def roofline_of(stages, exec_work, steps, peaks_live):
     """Roofline of the kernel stage with the largest share of the timed
-    region: Legendre stages against the FP64 / FP32 FMA peak (algorithmic
-    flops 8 per ring pair and (l, m)), ring-FFT stages and the pixel smoother
-    against the measured HBM copy bandwidth (algorithmic bytes)."""
+    region.  Legendre stages are bound by the FMA pipe of their precision:
+    achieved = the flops of the terms the kernel evaluates (8 per ring pair
+    and (l, m) past the start tables) per launch over the launch's CUDA-event
+    time, against the FMA rate measured live on this GPU; the dense count of
+    every ring pair and (l, m) is reported beside it.  Ring-FFT stages and
+    the pixel smoother: algorithmic bytes against the measured HBM copy
+    bandwidth."""
     peaks = measured_peaks()
     kern = {k: v for k, v in stages.items() if k not in COMPOSITE and "." not in k}
     dom = max(kern, key=lambda k: kern[k][0])
     ms, n, work = kern[dom]
+    wex = exec_work.get(dom, 0.0)
+    traffic, traffic_kernel = profile_traffic(dom)
     base = {"kernel": dom, "ms_per_step": ms / steps, "launches_per_step": n / steps,
-            "algorithmic_work_per_launch": work / max(n, 1), "traffic": None}
+            "algorithmic_work_per_launch": (wex or work) / max(n, 1), "traffic": traffic}
+    if traffic_kernel:
+        base["traffic_kernel"] = traffic_kernel
     if dom.startswith("legendre") and work > 0:
-        peak = FP64_PEAK_TFLOPS if dom.endswith("_f64") else FP32_PEAK_TFLOPS
-        ach = work / (ms * 1e-3) / 1e12
+        f64 = dom.endswith("_f64")
+        live = peaks_live.get("f64" if f64 else "f32")
+        peak = live if live else (FP64_PEAK_TFLOPS if f64 else FP32_PEAK_TFLOPS)
+        src = ("measured live: FMA-chain probe on this GPU (cr_probe_fma_peak)" if live else
+               "nominal: 152 SMs x 2070 MHz x FMA lanes x 2")
+        ach_dense = work / (ms * 1e-3) / 1e12
+        ach = (wex if wex > 0 else work) / (ms * 1e-3) / 1e12
         return dict(base, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                    peak_source="derived: 152 SMs x 2070 MHz x (FP32 128 / FP64 2) FMA per SM per clock x 2")
+                    frac_executed=ach / peak, achieved_dense=ach_dense, frac_dense=ach_dense / peak,
+                    work_note="achieved counts the terms the kernel evaluates (past the 2^-60 start of every "
+                              "(m, ring pair)); achieved_dense counts every ring pair and (l, m)",
+                    peak_source=src)
     if work > 0:
         peak = peaks.get("hbm_gbs", 6778.0)
         ach = work / (ms * 1e-3) / 1e9
@@ -554,6 +630,7 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
 
         fp32 = variant(binding.CR_MIXED)
         tc = variant(binding.CR_MIXED | binding.CR_TC_CYCLES)
+        tc_split = variant(binding.CR_MIXED | binding.CR_TC_CYCLES | binding.CR_TC_SPLIT)
         tc_top = variant(binding.CR_MIXED | binding.CR_TC_CYCLES | binding.CR_TC_TOP_F32)
         # batched synthesis of the 16 Nside 1024 solutions: Legendre
         # contraction on the tensor cores vs 16 FP32 syntheses
@@ -591,7 +668,8 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
         rel_tc = float(torch.linalg.vector_norm(y32.to(torch.complex128) - y64) / torch.linalg.vector_norm(y64))
         rel_f32 = float(torch.linalg.vector_norm(yf.to(torch.complex128) - y64) / torch.linalg.vector_norm(y64))
         del y32, yf, y64
-    forms = {"fp32_cycles": fp32, "tensor_core_cycles": tc, "tensor_core_cycles_fp32_top": tc_top}
+    forms = {"fp32_cycles": fp32, "tensor_core_cycles": tc, "tensor_core_cycles_split": tc_split,
+             "tensor_core_cycles_fp32_top": tc_top}
     best = max(forms, key=lambda k: forms[k]["graph_realizations_per_s"])
     return {"workload": "%d x (Nside 1024, lmax 2047) + %d x (Nside 512, lmax 1023)" % (nrhs, nrhs),
             "realizations": total,
@@ -600,6 +678,9 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
             "tensor_core_cycles_fp32_top": dict(tc_top, note="CR_TC_CYCLES | CR_TC_TOP_F32: pixel levels batched on "
                                                             "tcgen05, top-level residuals per right-hand side on the "
                                                             "FP32 CUDA cores"),
+            "tensor_core_cycles_split": dict(tc_split, note="CR_MIXED | CR_TC_CYCLES | CR_TC_SPLIT: the "
+                                                            "tensor-core cycles with hi + lo BF16 operands "
+                                                            "(three MMAs per step)"),
             "tensor_core_cycles": dict(tc, note="CR_MIXED | CR_TC_CYCLES: FP32 cycles of 16 right-hand sides "
                                                 "together, every Legendre stage on tcgen05 (BF16 in, FP32 "
                                                 "accumulation); FP64 outer residual per right-hand side"),
@@ -611,6 +692,70 @@ def batch_measurement(binding, synthetic, dev, args, nrhs=16):
                                         "rel_l2_vs_f64": {"tensor_core": rel_tc, "fp32": rel_f32},
                                         "note": "A = S^-1 + B Y^T N^-1 Y B, both Legendre stages on tcgen05 "
                                                 "vs the FP32 CUDA-core kernels"}}
+
+
+def batch_nside2048(binding, synthetic, dev, args, nrhs=8):
+    """Batched Planck-shaped realizations: nrhs right-hand sides b = A x_true
+    at Nside 2048 / lmax 3000 solved together in one CUDA graph, for the
+    per-right-hand-side FP32 cycles (CR_MIXED) and the tensor-core cycles
+    with plain and with split (hi + lo) BF16 operands; every form with the
+    fewest fixed cycles reaching < 1 uK max-pixel error on every right-hand
+    side.  Reports seconds per realization (graph replay / nrhs), cycles,
+    and the per-right-hand-side errors."""
+    import numpy as np
+    import torch
+
+    st = torch.cuda.Stream(dev)
+    out = {"workload": "%d x (Nside 2048, lmax 3000)" % nrhs, "realizations": nrhs}
+    with torch.cuda.stream(st):
+        cfg, cl, bl, ninv = synthetic.problem_inputs("nside2048_lmax3000")
+        npix = 12 * cfg["nside"] ** 2
+        plan = binding.Plan(cfg["lmax"], nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev),
+                            stream=st, levels="default", autotune=True)
+        xt = torch.from_numpy(np.stack([synthetic.draw_prior(cl, index=300 + j) for j in range(nrhs)])).to(dev)
+        b = torch.empty_like(xt)
+        plan.apply_A(xt, b)
+        x = torch.zeros_like(b)
+
+        def errors():
+            return [max_pixel_error(plan, x[j], xt[j], npix, dev) for j in range(nrhs)]
+
+        for name, mode in (("fp32_cycles", binding.CR_MIXED),
+                           ("tensor_core_cycles_split", binding.CR_MIXED | binding.CR_TC_CYCLES | binding.CR_TC_SPLIT),
+                           ("tensor_core_cycles", binding.CR_MIXED | binding.CR_TC_CYCLES)):
+            cycles, errs = None, None
+            for c in range(1, 9):
+                plan.solve(b, x, eps=0.0, max_cycles=c, mode=mode | binding.CR_FIXED, check=False)
+                errs = errors()
+                if max(errs) < 1.0:
+                    cycles = c
+                    break
+            if cycles is None:
+                out[name] = {"converged_within": 8, "max_pixel_error_uK": max(errs)}
+                continue
+            graph = binding.Batch([plan], [x], [b], cycles, mode)
+            graph.run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            graph.run()
+            e1.record(st)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            errs = errors()
+            out[name] = {"cycles": cycles, "graph_s": t, "s_per_realization": t / nrhs,
+                         "graph_nodes": graph.nodes(),
+                         "max_pixel_error_uK": {"max": max(errs), "median": float(np.median(errs))}}
+            graph.close()
+        del plan, xt, b, x
+        torch.cuda.synchronize()
+    forms = [k for k in ("fp32_cycles", "tensor_core_cycles_split", "tensor_core_cycles")
+             if "s_per_realization" in out.get(k, {})]
+    if forms:
+        best = min(forms, key=lambda k: out[k]["s_per_realization"])
+        out["form"] = best
+        out["s_per_realization"] = out[best]["s_per_realization"]
+    return out
 
 
 def cg_comparison(binding, synthetic, dev, stream, workload="nside256_lmax767"):
@@ -685,6 +830,7 @@ def main():
     cfg, cl, bl, ninv = synthetic.problem_inputs(args.workload)
     nside, lmax = cfg["nside"], cfg["lmax"]
     npix = 12 * nside * nside
+    peaks_live = live_peaks(binding)
     # a created stream (the legacy default stream cannot be captured into a graph)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -783,6 +929,7 @@ def main():
     torch.cuda.synchronize()
     ms_direct = d0.elapsed_time(d1) / args.steps
     stages = plan.timing()
+    stages_exec = plan.timing_exec()
     plan.set_timing(False)
     ms, ms_job = whole_job(ms, world, dev)
     err_timed = max_pixel_error(plan, x, x_true, npix, dev)
@@ -844,6 +991,7 @@ def main():
                                                              x_true, npix)
     cg_cmp = None if args.no_cg else cg_comparison(binding, synthetic, dev, stream)
     batch = None if args.no_batch else batch_measurement(binding, synthetic, dev, args)
+    batch2048 = None if args.no_batch else batch_nside2048(binding, synthetic, dev, args)
 
     if rank != 0:
         return
@@ -872,7 +1020,8 @@ def main():
                 "d2h_bytes_per_step": int(xh.numel() * 16)},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "stages_work_per_step": {k: v[2] / args.steps for k, v in stages.items() if v[2] > 0},
-        "roofline": roofline_of(stages, args.steps),
+        "roofline": roofline_of(stages, stages_exec, args.steps, peaks_live),
+        "fma_peaks_tflops": peaks_live,
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
@@ -884,8 +1033,14 @@ def main():
         out["cg_comparison"] = cg_cmp
     if batch is not None:
         out["batch"] = batch
+    if batch2048 is not None:
+        batch2048["fp64_single_s_per_realization"] = f64_s
+        batch2048["mixed_single_s_per_realization"] = value
+        out["batch_nside2048"] = batch2048
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nside, lmax, level_rows, cyc_mixed)
+        if cg_cmp is not None:
+            out["cpu_baseline"]["oracle_cg_nside256"] = oracle_cg_baseline(cg_cmp["cg_diag_f64"]["iterations"])
     print(json.dumps(out))
 
 

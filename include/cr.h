@@ -94,6 +94,12 @@ extern "C" {
  * tensor cores.  A replayed batch graph keeps the choice it was captured
  * with. */
 #define CR_TC_TOP_F32 64
+/* solve flag (with CR_TC_CYCLES): the cycles' tensor-core contractions with
+ * hi + lo BF16 operands (three MMAs per step, about 2^-17 relative instead
+ * of the 2^-9 of plain BF16), as the plan option tc_split does for every
+ * tensor-core call.  Also accepted by cr_batch_create (a replayed graph
+ * keeps the choice it was captured with). */
+#define CR_TC_SPLIT 128
 
 /* grid kinds */
 #define CR_GRID_HEALPIX 0

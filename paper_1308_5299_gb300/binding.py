@@ -24,6 +24,7 @@ CR_DRAW_FLUCT, CR_DRAW_PLAIN = 1, 2
 CR_TC = 3
 CR_TC_CYCLES = 32
 CR_TC_TOP_F32 = 64
+CR_TC_SPLIT = 128
 CR_PROBE_ALM, CR_PROBE_MAP = 0, 1
 CR_GRID_HEALPIX, CR_GRID_GL = 0, 1
 CR_OBS = 0

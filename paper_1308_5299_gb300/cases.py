@@ -116,15 +116,19 @@ def sht_case(nside, lmax, warmup, reps, dtype):
     return {"case": "sht", "nside": nside, "lmax": lmax, "dtype": dtype, "reps": reps, "ms": res}
 
 
-def apply_case(name, warmup, reps, dtype, tune):
+def apply_case(name, warmup, reps, dtype, tune, pin=None):
     """A x for one right-hand side on the workload's observation grid, timed
     whole and per stage (one realization's outer residual at Nside 2048 is
-    one FP64 call; the FP32 cycles make many FP32 calls)."""
+    one FP64 call; the FP32 cycles make many FP32 calls).  pin: (stage,
+    pairs per thread) fixed for this precision before the plan is made."""
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     cfg, cl, bl, ninv = synthetic.problem_inputs(name)
     lmax = cfg["lmax"]
+    if pin is not None:
+        nside = cfg["nside"]
+        binding.tune_set(4 * nside - 1, 12 * nside * nside, lmax, dtype, pin[0], pin[1])
     plan = binding.Plan(lmax, nside=cfg["nside"], cl=cl, bl=bl, ninv=torch.from_numpy(ninv).to(dev), stream=stream)
     if tune:
         plan.autotune()
@@ -246,6 +250,8 @@ def main(argv=None):
     ap.add_argument("case", choices=["tc", "sht", "apply", "smooth", "diag", "grad"])
     ap.add_argument("--tune", action="store_true", help="apply, tc: autotune the kernel shapes first")
     ap.add_argument("--split", action="store_true", help="tc: hi + lo BF16 operands")
+    ap.add_argument("--pin-adjoint", type=int, default=0,
+                    help="apply: ring pairs per thread of the adjoint Legendre stage (as the autotuner would pin)")
     ap.add_argument("--workload", default="nside256_lmax767")
     ap.add_argument("--cycles", type=int, default=4)
     ap.add_argument("--iters", type=int, default=16)
@@ -260,7 +266,10 @@ def main(argv=None):
     if args.case == "tc":
         print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps, args.tune, args.split)))
     elif args.case == "apply":
-        print(json.dumps(apply_case(args.workload, args.warmup, args.reps, args.dtype, args.tune)))
+        pin = None
+        if args.pin_adjoint:
+            pin = ("adjoint", args.pin_adjoint)
+        print(json.dumps(apply_case(args.workload, args.warmup, args.reps, args.dtype, args.tune, pin)))
     elif args.case == "smooth":
         print(json.dumps(smooth_case(args.workload, args.warmup, args.reps)))
     elif args.case == "diag":

@@ -36,8 +36,9 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
   if (!out || nplans < 1 || !plans || !x || !b || !nrhs || cycles < 1)
     return fail(CR_EINVAL, "cr_batch_create: bad arguments");
   const bool tc = (mode & CR_TC_CYCLES) != 0;
-  if ((mode & ~(3 | CR_TC_CYCLES | CR_TC_TOP_F32)) != 0 || ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) ||
-      (tc && (mode & 3) != CR_MIXED) || ((mode & CR_TC_TOP_F32) && !tc))
+  if ((mode & ~(3 | CR_TC_CYCLES | CR_TC_TOP_F32 | CR_TC_SPLIT)) != 0 ||
+      ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) || (tc && (mode & 3) != CR_MIXED) ||
+      ((mode & (CR_TC_TOP_F32 | CR_TC_SPLIT)) && !tc))
     return fail(CR_EINVAL, "cr_batch_create: mode must be CR_F64 or CR_MIXED (stationary, fixed count), "
                            "CR_TC_CYCLES only with CR_MIXED");
   cudaStream_t st = plans[0] ? plans[0]->stream : nullptr;
@@ -52,12 +53,18 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
   const int fmode = (mode & 3) | CR_FIXED;
   // one uncaptured solve per plan first: it builds the tables created lazily
   // on first use, which must not be allocated inside the capture
-  for (int i = 0; i < nplans; ++i) plans[i]->tc_top_f32 = (mode & CR_TC_TOP_F32) != 0;
+  for (int i = 0; i < nplans; ++i) {
+    plans[i]->tc_top_f32 = (mode & CR_TC_TOP_F32) != 0;
+    plans[i]->tc_split = (mode & CR_TC_SPLIT) ? 1 : plans[i]->tc_split_param;
+  }
   for (int i = 0; i < nplans; ++i) {
     if (nrhs[i] == 0) continue;
     int rc = tc ? solve_tc(plans[i], x[i], b[i], nrhs[i], 0.0, 1, true, nullptr, nullptr, nullptr)
                 : solve(plans[i], x[i], b[i], 0.0, 1, fmode, nullptr, nullptr, nullptr);
-    if (rc) return rc;
+    if (rc) {
+      for (int k = 0; k < nplans; ++k) plans[k]->tc_split = plans[k]->tc_split_param;
+      return rc;
+    }
   }
   CR_CUDA(cudaStreamSynchronize(st));
   cr_batch* bt = new cr_batch();
@@ -65,6 +72,7 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) {
     delete bt;
+    for (int k = 0; k < nplans; ++k) plans[k]->tc_split = plans[k]->tc_split_param;
     return cuda_fail(e, "cudaStreamBeginCapture");
   }
   int rc = CR_OK;
@@ -79,6 +87,7 @@ int cr_batch_create(cr_batch** out, int nplans, cr_plan* const* plans, void* con
     plans[i]->capturing = false;
   }
   e = cudaStreamEndCapture(st, &bt->graph);
+  for (int i = 0; i < nplans; ++i) plans[i]->tc_split = plans[i]->tc_split_param;
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
   if (!rc) {
     e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);

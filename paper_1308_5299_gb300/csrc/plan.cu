@@ -800,7 +800,7 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   P->p = *p;
   P->stream = reinterpret_cast<cudaStream_t>(p->stream);
   P->fp64_df = p->fp64_df ? 1 : 0;
-  P->tc_split = p->tc_split ? 1 : 0;
+  P->tc_split = P->tc_split_param = p->tc_split ? 1 : 0;
   P->lmax = p->lmax;
   P->levels.resize(1);
   P->levels[0].lmax_h = p->lmax;

@@ -154,7 +154,8 @@ struct cr_plan {
   int64_t tc_phase_bytes = 0;
   int* d_tc_status = nullptr;
   bool tc_top_f32 = false;   // batched cycles: top-level residuals on the FP32 CUDA-core kernels
-  int tc_split = 0;          // tensor-core contractions with hi + lo BF16 operands
+  int tc_split = 0;          // tensor-core contractions with hi + lo BF16 operands (in effect)
+  int tc_split_param = 0;    // the plan option (CR_TC_SPLIT turns it on for one solve or batch)
   void* tc_partial = nullptr;  // batched tensor-core adjoint: [16][nblk][n_lm] complex64
   int64_t tc_partial_bytes = 0;
   cr::Hierarchy* hier = nullptr;      // multi-level data (plans created with levels)

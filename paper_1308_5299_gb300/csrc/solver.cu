@@ -1026,7 +1026,9 @@ int cr_solve(cr_plan* plan, void* x, const void* b, int nrhs, double eps, int ma
     if (max_cycles < 1 || !(eps >= 0.0) || nrhs < 0) return fail(CR_EINVAL, "cr_solve: eps / max_cycles / nrhs");
     if (nrhs == 0) return CR_OK;
     plan->tc_top_f32 = (mode & CR_TC_TOP_F32) != 0;
+    plan->tc_split = (mode & CR_TC_SPLIT) ? 1 : plan->tc_split_param;
     rc = solve_tc(plan, x, b, nrhs, eps, max_cycles, (mode & CR_FIXED) != 0, cycles_out, relres_out, history);
+    plan->tc_split = plan->tc_split_param;
     return rc ? rc : sweep_status(plan);
   }
   if ((mode & 3) != CR_F64 && (mode & 3) != CR_MIXED) return fail(CR_EINVAL, "cr_solve: mode precision must be CR_F64 or CR_MIXED");
