@@ -15,6 +15,7 @@ beside it.  Multi-GPU runs are independent replicas (the workload does not
 shard across GPUs).
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -259,7 +260,7 @@ def cpu_baseline(nside, lmax, levels, cycles, full=True):
         out["full_grid_pair_s"] = full_pair
         out["full_grid_apply_A_s"] = apply_s
         out["sampled_estimate_of_that_pair_s"] = sampled_top
-        out["pairs_per_cycle"] = {"%s_%d_%d" % k: v / cycles for k, v in pairs.items()}
+        out["pairs_per_cycle"] = {"_".join(str(x) for x in k): v / cycles for k, v in pairs.items()}
     return out
 
 
@@ -385,6 +386,10 @@ def profile_traffic(stage):
             if ":" in line:
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
+        sha = vals.get("source_sha256")
+        src = os.path.join(ROOT, "paper_1308_5299_gb300", "csrc", "legendre.cu")
+        if sha and hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
+            return None, vals.get("kernel") + " (counters taken on an earlier source: traffic withheld)"
         return float(vals["traffic_bytes_per_launch"]), vals.get("kernel")
     except (OSError, KeyError, ValueError):
         return None, None
@@ -857,7 +862,7 @@ def main():
     t3 = time.perf_counter()
     table = plan.autotune()
     autotune = {"s": time.perf_counter() - t3,
-                "observation_grid": {"%s_%s" % (t["precision"], t["stage"]): t["pairs_per_thread"]
+                "observation_grid": {"%s_%s" % (t["precision"], t["stage"]): t.get("pairs_per_thread", t.get("variant"))
                                      for t in table if t["nring"] == 4 * nside - 1 and t["lmax"] == lmax},
                 "entries": len(table)}
     x_true = torch.from_numpy(synthetic.draw_prior(cl, index=rank)).to(dev)

@@ -30,7 +30,11 @@
 // start test), so the region below the turning point where the functions are
 // negligible costs nothing.
 //
-// Work decomposition: one CTA per (m, block of LEG_NT*RP ring pairs), RP
+// Work decomposition: one CTA per (m, block of LEG_NT*RP ring pairs) with
+// the ring-pair blocks of one m adjacent in launch order (blockIdx.x) and m
+// in blockIdx.y, so the longest CTAs (small m) are dispatched first, the
+// short ones (m near L) last, and the CTAs of one m share its coefficients
+// in L2; RP
 // (2, 4 or 8 pairs per thread: the ring-block size) chosen per grid, band
 // limit and precision by the plan's autotuner (default 4);
 // each warp owns 32*RP consecutive pairs (lane + 32 j), so its pairs'
@@ -84,7 +88,7 @@ __device__ __forceinline__ T rstep(T c, T c2, T zw, T& s1, T& s2) {
 
 // Ring pairs are split into a polar range [0, npolar) and an equatorial
 // range [npolar, npairs); each CTA covers LEG_NT*RP pairs of one range.
-// Block row yb (= blockIdx.y + the launch's row offset) < nbp is polar.
+// Block row yb (= blockIdx.x + the launch's row offset) < nbp is polar.
 template <int RP, int NT = LEG_NT>
 __device__ __forceinline__ int pair_of(int npolar, int nbp, int yb, int warp, int lane, int j) {
   const int base = yb < nbp ? yb * (NT * RP) : npolar + (yb - nbp) * (NT * RP);
@@ -130,7 +134,7 @@ __device__ __forceinline__ bool load_pairs(const LegArgs<T>& a, int m, int yb, i
 template <typename T, bool POLAR, int RP>
 __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
-  const int m = blockIdx.x;
+  const int m = blockIdx.y;
   const int L = a.L;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
     accE[j] = mk((T)0, (T)0);
     accO[j] = mk((T)0, (T)0);
   }
-  const int yb = (int)blockIdx.y + yoff;
+  const int yb = (int)blockIdx.x + yoff;
   int wmin, wmax;
   const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   const int64_t offa = lm_off(L, m);
@@ -316,7 +320,7 @@ template <bool POLAR, int RP>
 __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
   static_assert(RP % 2 == 0, "pairs per thread must be even");
   constexpr int NP = RP / 2;
-  const int m = blockIdx.x;
+  const int m = blockIdx.y;
   const int L = a.L;
   const int lane = threadIdx.x;
   const int warp = 0;
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
   float ex[RP], ey[RP], ox[RP], oy[RP];
 #pragma unroll
   for (int j = 0; j < RP; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
-  const int yb = (int)blockIdx.y + yoff;
+  const int yb = (int)blockIdx.x + yoff;
   int wmin, wmax;
   const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
 template <typename T, bool POLAR, int RP, bool SQ = false>
 __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
-  const int m = blockIdx.x;
+  const int m = blockIdx.y;
   const int L = a.L;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -488,7 +492,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
   T P1[RP], P2[RP], zz[RP];
   int ls[RP], p[RP];
   C GE[RP], GO[RP];
-  const int yb = (int)blockIdx.y + yoff;
+  const int yb = (int)blockIdx.x + yoff;
   int wmin, wmax;
   const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   const int pend = POLAR ? a.npolar : a.npairs;
@@ -614,7 +618,7 @@ template <bool POLAR, int RP>
 __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
   static_assert(RP % 2 == 0, "pairs per thread must be even");
   constexpr int NP = RP / 2;
-  const int m = blockIdx.x;
+  const int m = blockIdx.y;
   const int L = a.L;
   const int lane = threadIdx.x;
   __shared__ float2 sk[LEG_CH];
@@ -623,7 +627,7 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
   float P1[RP], P2[RP], zz[RP];
   int ls[RP], p[RP];
   float2 GE[RP], GO[RP];
-  const int yb = (int)blockIdx.y + yoff;
+  const int yb = (int)blockIdx.x + yoff;
   int wmin, wmax;
   const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, 0, lane, p, ls, P1, P2, zz, &wmin, &wmax);
   auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
@@ -807,22 +811,22 @@ static inline int legal_rp_f32adj(int rp) { return (rp == 2 || rp == 4 || rp == 
 template <typename T, int RP>
 static void synth_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (nbp) { leg_synth_f32x2_kernel<true, RP><<<dim3(a.L + 1, nbp), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_synth_f32x2_kernel<false, RP><<<dim3(a.L + 1, nbe), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    if (nbp) { leg_synth_f32x2_kernel<true, RP><<<dim3(nbp, a.L + 1), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_synth_f32x2_kernel<false, RP><<<dim3(nbe, a.L + 1), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   } else {
-    if (nbp) { leg_synth_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_synth_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    if (nbp) { leg_synth_kernel<T, true, RP><<<dim3(nbp, a.L + 1), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_synth_kernel<T, false, RP><<<dim3(nbe, a.L + 1), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   }
 }
 
 template <typename T, int RP>
 static void adjoint_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (nbp) { leg_adjoint_f32x2_kernel<true, RP><<<dim3(a.L + 1, nbp), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_adjoint_f32x2_kernel<false, RP><<<dim3(a.L + 1, nbe), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    if (nbp) { leg_adjoint_f32x2_kernel<true, RP><<<dim3(nbp, a.L + 1), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_adjoint_f32x2_kernel<false, RP><<<dim3(nbe, a.L + 1), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   } else {
-    if (nbp) { leg_adjoint_kernel<T, true, RP><<<dim3(a.L + 1, nbp), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_adjoint_kernel<T, false, RP><<<dim3(a.L + 1, nbe), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    if (nbp) { leg_adjoint_kernel<T, true, RP><<<dim3(nbp, a.L + 1), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_adjoint_kernel<T, false, RP><<<dim3(nbe, a.L + 1), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   }
 }
 
@@ -902,7 +906,7 @@ int launch_leg_diag(cr_plan* P, const double* ringval, double2* out) {
   a.partial = reinterpret_cast<double2*>(P->ws.partial);
   int nbp, nbe;
   pair_blocks(0, a.npairs, LEG_RP, &nbp, &nbe);
-  { leg_adjoint_kernel<double, false, LEG_RP, true><<<dim3(a.L + 1, nbe), LEG_NT, 0, P->stream>>>(a, 0, 0); count_launch(); }
+  { leg_adjoint_kernel<double, false, LEG_RP, true><<<dim3(nbe, a.L + 1), LEG_NT, 0, P->stream>>>(a, 0, 0); count_launch(); }
   CR_CHECK_LAUNCH("leg_adjoint_kernel<SQ>");
   FinalizeArgs<double> ff;
   ff.partial = a.partial;
