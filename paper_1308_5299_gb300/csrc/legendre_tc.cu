@@ -465,19 +465,11 @@ int launch_tc_synth(const LegArgs<float>& la, const float2* alm, int64_t ld_alm,
 // complete product D[l, 64] = Q[l, pairs] G[pairs, 64] whose 64 columns hold
 // the even-parity combination (16 right-hand sides x re, im) and the odd one:
 // a row keeps the half of its own parity (the other half costs MMA work only,
-// which is far from the bound).  Each thread runs its pair's FP32 recurrence
-// (start tables, polar difference form as in legendre.cu); 8 consecutive l of
-// 8 neighbouring pairs are transposed with warp shuffles so that every lane
-// writes one 16-byte K-major row segment.  G is staged once per CTA the same
-// way.  The product is read back from tensor memory after each chunk, scaled
-// by s_lm and written as one partial row per ring-pair block; a second
-// kernel sums the partial rows in a fixed order per right-hand side.
-
-constexpr int TA_M = 128;    // l per chunk (rows of D)
-constexpr int TA_K = 128;    // ring pairs per CTA
-constexpr int TA_N = 64;     // 16 right-hand sides x (re, im) x parity
-constexpr int TA_A_BYTES = TA_M * TA_K * 2;   // 32 KB
-constexpr int TA_B_BYTES = TA_N * TA_K * 2;   // 16 KB
+// which is far from the bound).  Each producer thread runs its pair's FP32
+// recurrence (start tables, polar difference form as in legendre.cu).  The
+// product is read back from tensor memory per chunk, scaled by s_lm and
+// written as one partial row per ring-pair block; a second kernel sums the
+// partial rows in a fixed order per right-hand side.
 
 struct TaArgs {
   const float2* phase;   // [nrhs][nring][ldp]
@@ -495,191 +487,9 @@ struct TaArgs {
   int* status;
 };
 
-// 8x8 transpose within each group of 8 lanes: on return lane 8 G + i holds,
-// in v[j], the value that lane 8 G + j held in v[i] (three butterfly stages
-// that exchange the off-diagonal blocks of halves, quarters and eighths)
-__device__ __forceinline__ void transpose8(float v[8], int lane) {
-#pragma unroll
-  for (int b = 4; b >= 1; b >>= 1) {
-    const bool hi = (lane & b) != 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (j & b) continue;
-      const float send = hi ? v[j] : v[j | b];
-      const float recv = __shfl_xor_sync(0xffffffffu, send, b);
-      if (hi) v[j] = recv;
-      else v[j | b] = recv;
-    }
-  }
-}
-
-// after transpose8: lane 8 G + i holds row (row0 + i) for the 8 pairs
-// kbase + 8 G .. + 7; one 16-byte store of the K-major segment
-__device__ __forceinline__ void store_rows8(uint8_t* buf, const float v[8], int row0, int kbase, int lane, int K) {
-  *reinterpret_cast<uint4*>(buf + tc::kmajor_offset(row0 + (lane & 7), kbase + 8 * (lane >> 3), K)) =
-      make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-}
-
-template <bool POLAR>
-__global__ void __launch_bounds__(TA_K) tc_adjoint_kernel(TaArgs a, int nbp, int yoff) {
-  extern __shared__ __align__(1024) uint8_t tasmem[];
-  uint8_t* A = tasmem;
-  uint8_t* B = tasmem + TA_A_BYTES;
-  __shared__ float sc[TA_M], sc2[TA_M];
-  __shared__ uint64_t mbar;
-  __shared__ uint32_t taddr_s;
-  __shared__ int s_min;
-  const int m = blockIdx.y;
-  const int L = a.L;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int yb = (int)blockIdx.x + yoff;
-  const int base = POLAR ? yb * TA_K : a.npolar + (yb - nbp) * TA_K;
-  const int pend = POLAR ? a.npolar : a.npairs;
-  const int p = base + tid;
-  int ls = L + 1;
-  float P1 = 0.f, P2 = 0.f, zz = 0.f;
-  if (p < pend) {
-    const int64_t o = (int64_t)m * a.ld_seed + p;
-    zz = POLAR ? a.w[p] : a.z[p];
-    const int l = a.ls[o];
-    if (l <= L) {
-      const float2 s = a.st[o];
-      ls = l;
-      P1 = s.x;
-      P2 = s.y;
-    }
-  }
-  if (tid == 0) s_min = L + 1;
-  __syncthreads();
-  if (ls <= L) atomicMin(&s_min, ls);
-  __syncthreads();
-  const int cmin = s_min;
-  const int64_t offa = lm_off(L, m), offc = lm_off(a.Lc, m);
-  const int64_t rstride = (int64_t)a.nblk * a.nlm;
-  float2* part = a.partial + (int64_t)yb * a.nlm + offa;
-  const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~1) : L + 1;
-  // rows before the block's earliest start are zero
-  for (int r = 0; r < a.nrhs; ++r)
-    for (int l = m + tid; l < lbeg; l += TA_K) part[r * rstride + (l - m)] = make_float2(0.f, 0.f);
-  if (cmin > L) return;
-
-  // B operand: row 2 r / 2 r + 1 = Re / Im of the even combination of
-  // right-hand side r, rows 32 + 2 r / + 1 the odd one; K = this thread's pair
-  {
-    const bool live = p < pend && ls <= L;
-    const int rn = p, rs = a.nring - 1 - p;
-#pragma unroll 1
-    for (int q = 0; q < TS_RHS / 4; ++q) {
-      float ve[8], vo[8];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = 4 * q + i;
-        float2 gn = make_float2(0.f, 0.f), gs = make_float2(0.f, 0.f);
-        if (live && r < a.nrhs) {
-          gn = a.phase[r * a.ld_phase + (int64_t)rn * a.ldp + m];
-          if (rs != rn) gs = a.phase[r * a.ld_phase + (int64_t)rs * a.ldp + m];
-        }
-        ve[2 * i] = gn.x + gs.x;
-        ve[2 * i + 1] = gn.y + gs.y;
-        vo[2 * i] = gn.x - gs.x;
-        vo[2 * i + 1] = gn.y - gs.y;
-      }
-      transpose8(ve, lane);
-      transpose8(vo, lane);
-      store_rows8(B, ve, 8 * q, warp * 32, lane, TA_K);
-      store_rows8(B, vo, 32 + 8 * q, warp * 32, lane, TA_K);
-    }
-  }
-
-  if (warp == 0) tc::tmem_alloc(&taddr_s, TA_N);
-  if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
-    tc::mbar_fence_init();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t taddr = taddr_s;
-  const uint32_t idesc = tc::idesc_bf16_f32(TA_M, TA_N);
-  const int nch = (L + 1 - lbeg + TA_M - 1) / TA_M;
-  bool ok = true;
-  for (int ch = 0; ch < nch; ++ch) {
-    const int l0 = lbeg + ch * TA_M;
-    {
-      const int l = l0 + tid;
-      const bool in = l <= L;
-      sc[tid] = in ? a.c[offc + (l - m)] : 0.f;
-      if (POLAR) sc2[tid] = in ? a.c2[offc + (l - m)] : 0.f;
-    }
-    __syncthreads();
-    // A operand: row t = l - l0, K = this thread's pair; 8 l at a time,
-    // transposed so that each lane stores 8 pairs of one row
-    const bool full = (ls <= l0) && (l0 + TA_M - 1 <= L);
-#pragma unroll 1
-    for (int g = 0; g < TA_M / 8; ++g) {
-      float v[8];
-      if (full) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = tstep<POLAR>(sc[8 * g + j], POLAR ? sc2[8 * g + j] : 0.f, zz, P1, P2);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int l = l0 + 8 * g + j;
-          v[j] = 0.f;
-          if (l >= ls && l <= L) v[j] = tstep<POLAR>(sc[8 * g + j], POLAR ? sc2[8 * g + j] : 0.f, zz, P1, P2);
-        }
-      }
-      transpose8(v, lane);
-      store_rows8(A, v, 8 * g, warp * 32, lane, TA_K);
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (tid == 0) {
-      const uint32_t aa = tc::smem_addr(A), bb = tc::smem_addr(B);
-      const uint32_t sbo = (TA_K / 8) * 128;
-#pragma unroll
-      for (int kk = 0; kk < TA_K / 16; ++kk)
-        tc::mma_bf16(taddr, tc::smem_desc(aa + kk * 256, 128, sbo), tc::smem_desc(bb + kk * 256, 128, sbo), idesc,
-                     kk > 0 ? 1u : 0u);
-      tc::mma_commit(&mbar);
-    }
-    ok = tc::mbar_wait_block(&mbar, ch & 1, TS_WAIT);
-    tc::fence_after_sync();
-    if (!ok) {
-      // one more bounded wait for the MMAs in flight before tensor memory is
-      // freed; the result is reported either way
-      tc::mbar_wait_block(&mbar, ch & 1, TS_WAIT);
-      if (tid == 0) atomicExch(a.status, 1);
-      break;
-    }
-    {
-      float ve[32], vo[32];
-      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), ve);
-      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + 32, vo);
-      const int l = l0 + tid;
-      if (l <= L) {
-        const float sl = a.s[offc + (l - m)];
-        const bool odd = (tid & 1) != 0;  // l0 - m is even
-#pragma unroll
-        for (int r = 0; r < TS_RHS; ++r)
-          if (r < a.nrhs)
-            part[r * rstride + (l - m)] =
-                make_float2((odd ? vo[2 * r] : ve[2 * r]) * sl, (odd ? vo[2 * r + 1] : ve[2 * r + 1]) * sl);
-      }
-    }
-    // every thread's tensor-memory reads are done before the next MMA
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-  }
-  if (warp == 0) tc::tmem_dealloc(taddr, TA_N);
-}
-
 // ---------------------------------------------------------------------------
-// Warp-specialised batched adjoint.  The same contraction as
-// tc_adjoint_kernel, D[l, 64] = Q[l, pairs] G[pairs, 64] per chunk of 128 l,
+// Warp-specialised batched adjoint: D[l, 64] = Q[l, pairs] G[pairs, 64] per
+// chunk of 128 l,
 // with the operands in the MN-major layout (each 16-byte row of a core
 // matrix is 8 consecutive MN elements of one K index), so that a thread --
 // which owns one ring pair, i.e. one K index -- writes 8 consecutive l of
@@ -696,6 +506,10 @@ __global__ void __launch_bounds__(TA_K) tc_adjoint_kernel(TaArgs a, int nbp, int
 //    quarter: 32 l rows), release it, and write s_lm times the row's parity
 //    half as the partial rows of 16 right-hand sides.
 // The chunk loop has no block-wide barrier; every wait is bounded.
+// SPLIT: both operands carried as hi = bf16(v) and lo = bf16(v - hi), each in
+// its own copy of the layout, and every K step issues hi x hi, hi x lo and
+// lo x hi into the same accumulator (the lo x lo term is below FP32 rounding
+// of the sum), which brings the products to about 2^-16 relative.
 constexpr int T3_M = 128;                  // l per chunk (rows of D)
 constexpr int T3_K = 128;                  // ring pairs per CTA
 constexpr int T3_N = 64;                   // 16 RHS x (Re, Im) x parity
@@ -703,6 +517,13 @@ constexpr int T3_NT = 32 * 9;
 constexpr int T3_A_BYTES = T3_M * T3_K * 2;   // 32 KB
 constexpr int T3_B_BYTES = T3_N * T3_K * 2;   // 16 KB
 constexpr int T3_NSTG = 2;
+template <bool SPLIT>
+struct T3Layout {
+  static constexpr int NPART = SPLIT ? 2 : 1;
+  static constexpr int STAGE = NPART * T3_A_BYTES;            // A hi (+ lo) of one stage
+  static constexpr int B0 = T3_NSTG * STAGE;                  // B hi (+ lo) after the stages
+  static constexpr int BYTES = B0 + NPART * T3_B_BYTES;
+};
 
 // MN-major no-swizzle offset of element (mn, k) of an operand with MN rows:
 // core matrices 128 bytes apart along MN, (MN / 8) * 128 apart along K (the
@@ -712,10 +533,11 @@ __device__ __forceinline__ uint32_t mn_off(int mn, int k, int MN) {
   return (uint32_t)(((mn >> 3) << 7) + (k >> 3) * (MN / 8) * 128 + ((k & 7) << 4) + ((mn & 7) << 1));
 }
 
-template <bool POLAR>
+template <bool POLAR, bool SPLIT>
 __global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, int yoff) {
+  using Lay = T3Layout<SPLIT>;
   extern __shared__ __align__(1024) uint8_t t3smem[];
-  uint8_t* Bsm = t3smem + T3_NSTG * T3_A_BYTES;
+  uint8_t* Bsm = t3smem + Lay::B0;
   __shared__ float s_c[4][T3_M], s_c2[POLAR ? 4 : 1][T3_M];
   __shared__ uint64_t a_full[T3_NSTG], a_empty[T3_NSTG], d_full[2], d_free[2];
   __shared__ uint32_t taddr_s;
@@ -782,6 +604,10 @@ __global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, i
     for (int g = 0; g < 4; ++g) {
       *reinterpret_cast<uint4*>(Bsm + mn_off(8 * g, tid, T3_N)) = pack8_hi(ve + 8 * g);
       *reinterpret_cast<uint4*>(Bsm + mn_off(32 + 8 * g, tid, T3_N)) = pack8_hi(vo + 8 * g);
+      if (SPLIT) {
+        *reinterpret_cast<uint4*>(Bsm + T3_B_BYTES + mn_off(8 * g, tid, T3_N)) = pack8_lo(ve + 8 * g);
+        *reinterpret_cast<uint4*>(Bsm + T3_B_BYTES + mn_off(32 + 8 * g, tid, T3_N)) = pack8_lo(vo + 8 * g);
+      }
     }
   }
   if (mma_warp) tc::tmem_alloc(&taddr_s, 2 * T3_N);
@@ -840,7 +666,7 @@ __global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, i
       }
       __syncwarp();
       if (ch + 1 < nch) prefetch_coef(l0 + T3_M);
-      uint8_t* A = t3smem + stg * T3_A_BYTES;
+      uint8_t* A = t3smem + stg * Lay::STAGE;
       const bool full_chunk = (ls <= l0) && (l0 + T3_M - 1 <= L);
 #pragma unroll 1
       for (int g = 0; g < T3_M / 8; ++g) {
@@ -857,6 +683,7 @@ __global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, i
           }
         }
         *reinterpret_cast<uint4*>(A + mn_off(8 * g, tid, T3_M)) = pack8_hi(v);
+        if (SPLIT) *reinterpret_cast<uint4*>(A + T3_A_BYTES + mn_off(8 * g, tid, T3_M)) = pack8_lo(v);
       }
       tc::fence_proxy_async();
       mbar_arrive(&a_full[stg]);
@@ -878,13 +705,20 @@ __global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, i
       }
       tc::fence_after_sync();
       if (lane == 0) {
-        const uint32_t aa = tc::smem_addr(t3smem + stg * T3_A_BYTES);
+        const uint32_t aa = tc::smem_addr(t3smem + stg * Lay::STAGE);
+        const uint32_t dt = taddr + (uint32_t)(db * T3_N);
 #pragma unroll
-        for (int kk = 0; kk < T3_K / 16; ++kk)
+        for (int kk = 0; kk < T3_K / 16; ++kk) {
           // MN-major without swizzle: leading byte offset = the K-direction
           // core-matrix stride, stride byte offset = the MN-direction one
-          tc::mma_bf16(taddr + (uint32_t)(db * T3_N), tc::smem_desc(aa + kk * 2 * a_kstride, a_kstride, 128),
-                       tc::smem_desc(bb + kk * 2 * b_kstride, b_kstride, 128), idesc, kk > 0 ? 1u : 0u);
+          const uint64_t ah = tc::smem_desc(aa + kk * 2 * a_kstride, a_kstride, 128);
+          const uint64_t bh = tc::smem_desc(bb + kk * 2 * b_kstride, b_kstride, 128);
+          tc::mma_bf16(dt, ah, bh, idesc, kk > 0 ? 1u : 0u);
+          if (SPLIT) {
+            tc::mma_bf16(dt, ah, tc::smem_desc(bb + T3_B_BYTES + kk * 2 * b_kstride, b_kstride, 128), idesc, 1u);
+            tc::mma_bf16(dt, tc::smem_desc(aa + T3_A_BYTES + kk * 2 * a_kstride, a_kstride, 128), bh, idesc, 1u);
+          }
+        }
         tc::mma_commit(&a_empty[stg]);
         tc::mma_commit(&d_full[db]);
       }
@@ -933,18 +767,29 @@ __global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, i
   if (mma_warp) tc::tmem_dealloc(taddr, 2 * T3_N);
 }
 
+template <bool SPLIT>
+static int t3_launch_both(const TaArgs& a, int nbp, int nbe, int L, cudaStream_t st) {
+  const size_t smem = (size_t)T3Layout<SPLIT>::BYTES;
+  CR_CUDA(cudaFuncSetAttribute(tc_adjoint2_kernel<true, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CR_CUDA(cudaFuncSetAttribute(tc_adjoint2_kernel<false, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (nbp) { tc_adjoint2_kernel<true, SPLIT><<<dim3(nbp, L + 1), T3_NT, smem, st>>>(a, nbp, 0); count_launch(); }
+  if (nbe) { tc_adjoint2_kernel<false, SPLIT><<<dim3(nbe, L + 1), T3_NT, smem, st>>>(a, nbp, nbp); count_launch(); }
+  CR_CHECK_LAUNCH("tc_adjoint2_kernel");
+  return CR_OK;
+}
+
 // G of nrhs <= 16 right-hand sides (phase [nrhs][nring][L+1], complex64) ->
 // partial rows [nrhs][nblk][n_lm(L)] (s_lm applied); *nblk receives the
 // number of ring-pair blocks.  status: device int set to 1 if a completion
 // wait gave up.
 int tc_adjoint_blocks(int npolar, int npairs) {
-  return (npolar + TA_K - 1) / TA_K + (npairs - npolar + TA_K - 1) / TA_K;
+  return (npolar + T3_K - 1) / T3_K + (npairs - npolar + T3_K - 1) / T3_K;
 }
 
 int launch_tc_adjoint(const LegArgs<float>& la, const float2* phase, int nrhs, float2* partial, int* nblk,
                       int* status, cudaStream_t st) {
-  const int nbp = (la.npolar + TA_K - 1) / TA_K;
-  const int nbe = (la.npairs - la.npolar + TA_K - 1) / TA_K;
+  const int nbp = (la.npolar + T3_K - 1) / T3_K;
+  const int nbe = (la.npairs - la.npolar + T3_K - 1) / T3_K;
   *nblk = nbp + nbe;
   if (la.L < 0 || nrhs <= 0) return CR_OK;
   if (nrhs > TS_RHS) return fail(CR_EINVAL, "tensor-core adjoint: at most 16 right-hand sides per launch");
@@ -971,13 +816,8 @@ int launch_tc_adjoint(const LegArgs<float>& la, const float2* phase, int nrhs, f
   a.npairs = la.npairs;
   a.nring = la.nring;
   a.status = status;
-  const size_t smem = (size_t)T3_NSTG * T3_A_BYTES + T3_B_BYTES;
-  CR_CUDA(cudaFuncSetAttribute(tc_adjoint2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CR_CUDA(cudaFuncSetAttribute(tc_adjoint2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (nbp) { tc_adjoint2_kernel<true><<<dim3(nbp, la.L + 1), T3_NT, smem, st>>>(a, nbp, 0); count_launch(); }
-  if (nbe) { tc_adjoint2_kernel<false><<<dim3(nbe, la.L + 1), T3_NT, smem, st>>>(a, nbp, nbp); count_launch(); }
-  CR_CHECK_LAUNCH("tc_adjoint2_kernel");
-  return CR_OK;
+  if (la.tc_split) return t3_launch_both<true>(a, nbp, nbe, la.L, st);
+  return t3_launch_both<false>(a, nbp, nbe, la.L, st);
 }
 
 }  // namespace cr
