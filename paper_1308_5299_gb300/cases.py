@@ -96,12 +96,15 @@ def tc_case(nside, lmax, nrhs, warmup, reps, tune=False, split=False):
             "ms": res, "tune": [t for t in binding.tune_table() if t["lmax"] == lmax] if tune else None}
 
 
-def sht_case(nside, lmax, warmup, reps, dtype):
+def sht_case(nside, lmax, warmup, reps, dtype, pins=()):
     """One synthesis and one adjoint synthesis (single right-hand side) in
-    FP32 or FP64, default (untuned) ring blocks."""
+    FP32 or FP64, default (untuned) ring blocks unless pinned: pins is a list
+    of (stage, pairs per thread)."""
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
+    for stage, rp in pins:
+        binding.tune_set(4 * nside - 1, 12 * nside * nside, lmax, dtype, stage, rp)
     plan = binding.Plan(lmax, nside=nside, stream=stream)
     cdt, rdt = (torch.complex64, torch.float32) if dtype == "f32" else (torch.complex128, torch.float64)
     a = torch.from_numpy(synthetic.random_alm(lmax, seed=301)).to(cdt).to(dev)
@@ -113,7 +116,8 @@ def sht_case(nside, lmax, warmup, reps, dtype):
             fn()
         torch.cuda.synchronize()
         res[name] = _time(fn, stream, reps)
-    return {"case": "sht", "nside": nside, "lmax": lmax, "dtype": dtype, "reps": reps, "ms": res}
+    return {"case": "sht", "nside": nside, "lmax": lmax, "dtype": dtype, "reps": reps, "pins": list(pins),
+            "ms": res}
 
 
 def apply_case(name, warmup, reps, dtype, tune, pin=None):
@@ -251,7 +255,9 @@ def main(argv=None):
     ap.add_argument("--tune", action="store_true", help="apply, tc: autotune the kernel shapes first")
     ap.add_argument("--split", action="store_true", help="tc: hi + lo BF16 operands")
     ap.add_argument("--pin-adjoint", type=int, default=0,
-                    help="apply: ring pairs per thread of the adjoint Legendre stage (as the autotuner would pin)")
+                    help="apply, sht: ring pairs per thread of the adjoint Legendre stage (as the autotuner would pin)")
+    ap.add_argument("--pin-synth", type=int, default=0,
+                    help="sht: ring pairs per thread of the synthesis Legendre stage")
     ap.add_argument("--workload", default="nside256_lmax767")
     ap.add_argument("--cycles", type=int, default=4)
     ap.add_argument("--iters", type=int, default=16)
@@ -277,7 +283,8 @@ def main(argv=None):
     elif args.case == "grad":
         print(json.dumps(grad_case(args.workload, args.nrhs, args.warmup)))
     else:
-        print(json.dumps(sht_case(args.nside, args.lmax, args.warmup, args.reps, args.dtype)))
+        pins = [(st, rp) for st, rp in (("synthesis", args.pin_synth), ("adjoint", args.pin_adjoint)) if rp]
+        print(json.dumps(sht_case(args.nside, args.lmax, args.warmup, args.reps, args.dtype, pins)))
 
 
 if __name__ == "__main__":

@@ -67,6 +67,8 @@ struct PixLevel {
   int* d_perm = nullptr;   // tile-ordered level pixel -> RING index
   int* d_colour_start = nullptr;  // device copy of pat.colour_start
   int coop_grid = 0;       // CTAs of the one-launch cooperative sweeps (0: one launch per colour)
+  void* d_flow_task = nullptr;  // their per-CTA task lists (smoother.cu)
+  int* d_flow_off = nullptr;
   int64_t* d_row_ptr = nullptr;
   int* d_row_col = nullptr;
   // column lists for the backward solve: blocks (u, p), u > p
@@ -111,7 +113,8 @@ struct Hierarchy {
   void* map_work = nullptr;   // largest level pixel map (double)
   void* map_work2 = nullptr;
   double* d_dot = nullptr;    // dot-product scratch
-  unsigned int* d_sweep_bar = nullptr;  // grid barrier of the cooperative smoother sweeps [2]
+  int* d_sweep_flag = nullptr;          // per-tile progress flags of the cooperative smoother sweeps
+  unsigned int* d_sweep_epoch = nullptr;  // their launch epoch and exit count [2]
   int* d_sweep_status = nullptr;        // set when a wait of those sweeps gave up
   double* d_dot_host = nullptr;
   void* ops_store = nullptr;  // per-level operator arrays (solver.cu)

@@ -540,41 +540,67 @@ __global__ void __launch_bounds__(TKW) bwd_colour_w_kernel(const float* LT, cons
 // cooperatively launched kernel (levels with few tiles per colour, where one
 // launch per colour leaves the GPU waiting on launch and load latency).
 //
-// Each CTA owns tiles p = colour_start[c] + blockIdx.x + k gridDim.x of every
-// colour, forward colours first, then backward.  A tile's factor blocks are
-// contiguous (row p of L: its lower blocks then inv(L_pp); for the backward
-// sweep the transposed column blocks then inv(L_pp)^T in LT), so the CTA's
-// whole sequence of 16 KB blocks is known at launch: thread 0 streams it
-// into a ring of SW_NS shared-memory slots with bulk asynchronous copies
-// (cp.async.bulk, completion counted in bytes on one mbarrier per slot),
-// SW_NS blocks ahead of the arithmetic -- across tile and colour boundaries,
-// so the loads for the next colour run during the grid-wide barrier.  The
-// 256 threads compute each block's product from shared memory as the
-// 256-thread per-colour kernels do.  Colours are separated by a grid barrier
-// (a counter and a generation word in global memory); the work vector y is
-// read through L2 (ld.global.cg) because other SMs wrote it.
+// Work: the host splits the tiles over the CTAs (tile p of colour c goes to
+// CTA (p - colour_start[c]) mod gridDim) and writes each CTA's task list --
+// its forward tiles colour by colour ascending, then its backward tiles
+// colour by colour descending -- with everything a task needs: position,
+// sweep, the neighbours its solve reads and its first factor block.  A
+// tile's factor blocks are contiguous (row p of L: its lower blocks then
+// inv(L_pp); for the backward sweep the transposed column blocks then
+// inv(L_pp)^T in LT), so the CTA's whole sequence of 16 KB blocks is known.
 //
-// Every wait is bounded (slot mbarriers and the grid barrier): on a timeout
-// the CTA records it in *status, waits (bounded) for its copies in flight
-// and leaves; the other CTAs then time out at their next barrier and leave
-// too, and the host reports the status as an error.
-constexpr int SW_NT = 256;
-constexpr int SW_NS = 12;                           // shared-memory block slots
+// Roles: one producer warp streams that sequence into a ring of SF_NS
+// shared-memory slots with bulk asynchronous copies (cp.async.bulk; a "full"
+// mbarrier per slot counts the bytes, an "empty" one the consumer warps done
+// with it), as far ahead as the ring allows; eight consumer warps run the
+// tasks: wait for the inputs, multiply the slots' blocks (256 threads per
+// 64 x 64 block as in the per-colour kernels), synchronise among themselves
+// on a named barrier only.  The consumers never wait for the producer's
+// index arithmetic, only for data.
+//
+// There is no grid-wide barrier between colours: the sweeps run as a data
+// flow over the tiles.  flag[p] becomes 2 e + 1 when tile p's forward solve
+// is in y and 2 e + 2 when its backward solve is, e being the launch's epoch
+// (epoch[0], read by every CTA at its start and advanced by the last CTA to
+// leave, so no reset between launches is needed); a task starts when the
+// flags of the neighbours its solve reads have reached that value, so a
+// tile of colour c waits for its own neighbours only.  Forward
+// solves read lower colours only and backward solves higher colours only;
+// every CTA takes its forward tasks by ascending and its backward tasks by
+// descending colour, and all CTAs are resident (the cooperative launch): so
+// the CTAs holding an unfinished forward tile of the lowest such colour --
+// or, once none is left, an unfinished backward tile of the highest such
+// colour -- are at that task and its inputs are there; the flow cannot
+// stall.  The work vector y is read through L2 (ld.global.cg) because other
+// SMs wrote it.
+//
+// Every wait is bounded (slot mbarriers and tile flags): on a timeout the
+// CTA records it in *status; the producer waits (bounded) for its copies in
+// flight and every role leaves; the CTAs waiting for this CTA's tiles then
+// time out too, and the host reports the status as an error.
+constexpr int SF_CONS = 256;                        // consumer threads
+constexpr int SF_NT = SF_CONS + 32;                 // + the producer warp
+constexpr int SF_NS = 12;                           // shared-memory block slots
+constexpr int SF_MAXT = 192;                        // tasks per CTA
 constexpr int SW_BLOCK_BYTES = TK * TK * (int)sizeof(float);
 constexpr uint32_t SW_WAIT = 1u << 22;              // polls per wait (about a second)
+
+struct FlowTask {
+  int p, sweep, nb, pad;
+  int64_t blk0;   // first factor block (in L for the forward sweep, LT for the backward)
+  int nbr[8];     // positions of the neighbours the solve reads
+};
+static_assert(sizeof(FlowTask) == 56, "FlowTask layout");
 
 struct SweepArgs {
   const float* L;
   const float* LT;
-  const int64_t* row_ptr;
-  const int* row_col;
-  const int64_t* col_ptr;
-  const int* col_row;
   const int* perm;
-  const int* colour_start;  // [ncol + 1]
-  int ncol;
+  const FlowTask* task;     // all CTAs' task lists, CTA b's at [task_off[b], task_off[b + 1])
+  const int* task_off;
   float* y;
-  unsigned int* bar;        // [2]: arrivals, generation (arrivals zero at launch)
+  int* flag;                // [ntile]: 2 epoch + 1 forward done, 2 epoch + 2 backward done
+  unsigned int* epoch;      // [2]: the launch epoch, CTAs that have left this launch
   int* status;
 };
 
@@ -604,166 +630,200 @@ __device__ __forceinline__ bool sw_wait(uint64_t* mbar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ void sw_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sw_smem(mbar)) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-// grid-wide barrier of the cooperative launch; false (for the whole CTA) if
-// the wait gave up
-__device__ bool sw_grid_barrier(unsigned int* bar, unsigned int nblk) {
-  __syncthreads();
-  int ok = 1;
-  if (threadIdx.x == 0) {
-    const unsigned int gen = ld_acquire_gpu(bar + 1);
-    __threadfence();
-    if (atomicAdd(bar, 1u) == nblk - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      uint32_t it = 0;
-      while (ld_acquire_gpu(bar + 1) == gen) {
-        if (++it > SW_WAIT) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  return __syncthreads_and(ok) != 0;
+// barrier of the consumer warps (named barrier 1) that also ANDs a predicate
+__device__ __forceinline__ bool cons_sync_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(SF_CONS)
+      : "memory");
+  return r != 0;
 }
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(SF_CONS) : "memory"); }
 
-// Position in a CTA's block sequence: sweep (0 forward, 1 backward), colour,
-// tile, block within the tile.
-struct SwCursor {
-  int sweep, c, p, j;
-  bool done;
-};
-
-__device__ __forceinline__ int sw_nblk(const SweepArgs& a, int sweep, int p) {
-  return sweep == 0 ? (int)(a.row_ptr[p + 1] - a.row_ptr[p]) : (int)(a.col_ptr[p + 1] - a.col_ptr[p]) + 1;
-}
-__device__ __forceinline__ const float* sw_src(const SweepArgs& a, int sweep, int p, int j) {
-  return sweep == 0 ? a.L + (a.row_ptr[p] + j) * (int64_t)(TK * TK)
-                    : a.LT + (a.col_ptr[p] + p + j) * (int64_t)(TK * TK);
-}
-// first tile of this CTA at or after colour c of the sweep (skipping colours
-// it has no tile in); done when the sequence is exhausted
-__device__ void sw_seek(const SweepArgs& a, SwCursor& u) {
-  for (;;) {
-    if (u.sweep == 0 ? u.c >= a.ncol : u.c < 0) {
-      if (u.sweep == 0) {
-        u.sweep = 1;
-        u.c = a.ncol - 1;
-        continue;
-      }
-      u.done = true;
-      return;
+// rows of the result for consumer threads tid < 64 (sum of the 16 column
+// groups), synchronised on the consumers' barrier
+__device__ __forceinline__ float reduce_groups_c(float4 acc, float4 (*part)[16], int rq, int jg, int tid) {
+  part[jg][rq] = acc;
+  cons_sync();
+  float s = 0.f;
+  if (tid < TK) {
+    const int r = tid >> 2, e = tid & 3;
+#pragma unroll
+    for (int g = 0; g < 16; ++g) {
+      const float4 v = part[g][r];
+      s += (e == 0) ? v.x : (e == 1) ? v.y : (e == 2) ? v.z : v.w;
     }
-    u.p = a.colour_start[u.c] + (int)blockIdx.x;
-    u.j = 0;
-    if (u.p < a.colour_start[u.c + 1]) return;
-    u.c += u.sweep == 0 ? 1 : -1;
   }
-}
-__device__ void sw_advance(const SweepArgs& a, SwCursor& u) {
-  if (++u.j < sw_nblk(a, u.sweep, u.p)) return;
-  u.j = 0;
-  u.p += (int)gridDim.x;
-  if (u.p < a.colour_start[u.c + 1]) return;
-  u.c += u.sweep == 0 ? 1 : -1;
-  sw_seek(a, u);
+  cons_sync();
+  return s;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SW_NT, 1) sweep_coop_kernel(SweepArgs a, const T* map_in, T* map_out) {
+__device__ __forceinline__ void sweep_flow_consumers(const SweepArgs& a, const T* map_in, T* map_out,
+                                                     const FlowTask* tk, int nt, unsigned int fbase, const float* slots,
+                                                     uint64_t* full, uint64_t* empty, float (*vs)[TK], float* ts,
+                                                     float4 (*part)[16], volatile int* s_abort);
+
+template <typename T>
+__global__ void __launch_bounds__(SF_NT, 1) sweep_flow_kernel(SweepArgs a, const T* map_in, T* map_out) {
   extern __shared__ __align__(128) unsigned char sw_raw[];
   float* slots = reinterpret_cast<float*>(sw_raw);
-  __shared__ uint64_t mbar[SW_NS];
+  __shared__ uint64_t full[SF_NS], empty[SF_NS];
+  __shared__ FlowTask tk[SF_MAXT];
   __shared__ float vs[8][TK];
   __shared__ float ts[TK];
   __shared__ float4 part[16][16];
-  const int tid = threadIdx.x, rq = tid & 15, jg = tid >> 4;
-
-  // producer state (thread 0): the next block to load
-  SwCursor pc{0, 0, 0, 0, false};
-  long issued = 0;
+  __shared__ volatile int s_abort;
+  const int tid = threadIdx.x;
+  const int t0 = a.task_off[blockIdx.x], nt = a.task_off[blockIdx.x + 1] - t0;
+  const unsigned int fbase = 2u * *(volatile unsigned int*)a.epoch;  // modulo 2^32
+  // the CTA's task list into shared memory (host-checked: nt <= SF_MAXT)
+  for (int i = tid; i < nt * (int)(sizeof(FlowTask) / 4); i += SF_NT)
+    reinterpret_cast<int*>(tk)[i] = reinterpret_cast<const int*>(a.task + t0)[i];
   if (tid == 0) {
-    for (int i = 0; i < SW_NS; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sw_smem(&mbar[i])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    sw_seek(a, pc);
-    while (!pc.done && issued < SW_NS) {
-      sw_bulk_load(slots + (issued % SW_NS) * (TK * TK), sw_src(a, pc.sweep, pc.p, pc.j), SW_BLOCK_BYTES,
-                   &mbar[issued % SW_NS]);
-      ++issued;
-      sw_advance(a, pc);
+    s_abort = 0;
+    for (int i = 0; i < SF_NS; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sw_smem(&full[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sw_smem(&empty[i])), "r"(SF_CONS / 32) : "memory");
     }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  long used = 0;  // blocks consumed
-  bool ok = true;
-  // wait for the next block; then thread 0 refills the slot freed by the
-  // previous block (every thread has passed the wait's barrier, so all are
-  // done with it)
-  auto next_block = [&]() -> const float* {
-    const int slot = (int)(used % SW_NS);
-    ok = __syncthreads_and(sw_wait(&mbar[slot], (uint32_t)((used / SW_NS) & 1)) ? 1 : 0) != 0;
-    if (!ok) return nullptr;
-    if (tid == 0 && used > 0 && !pc.done) {
-      const long fs = (used - 1) % SW_NS;
-      sw_bulk_load(slots + fs * (TK * TK), sw_src(a, pc.sweep, pc.p, pc.j), SW_BLOCK_BYTES, &mbar[fs]);
-      ++issued;
-      sw_advance(a, pc);
+  if (tid >= SF_CONS) {
+    // producer warp: lane 0 streams the blocks of every task in order
+    if (tid == SF_CONS) {
+      long issued = 0;
+      bool ok = true;
+      for (int t = 0; t < nt && ok; ++t) {
+        const float* base = (tk[t].sweep == 0 ? a.L : a.LT) + tk[t].blk0 * (int64_t)(TK * TK);
+        for (int j = 0; j <= tk[t].nb && ok; ++j) {
+          const int slot = (int)(issued % SF_NS);
+          if (issued >= SF_NS) {
+            ok = sw_wait(&empty[slot], (uint32_t)(((issued / SF_NS) - 1) & 1)) && !s_abort;
+            if (!ok) break;
+          }
+          sw_bulk_load(slots + slot * (TK * TK), base + (int64_t)j * (TK * TK), SW_BLOCK_BYTES, &full[slot]);
+          ++issued;
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicExch(a.status, 1);
+      }
+      // every copy still in flight lands in this CTA's shared memory: wait
+      // (bounded) for the last phase of each slot before the CTA can leave
+      for (long i = issued > SF_NS ? issued - SF_NS : 0; i < issued; ++i)
+        sw_wait(&full[i % SF_NS], (uint32_t)((i / SF_NS) & 1));
     }
-    ++used;
+  } else {
+    sweep_flow_consumers<T>(a, map_in, map_out, tk, nt, fbase, slots, full, empty, vs, ts, part, &s_abort);
+  }
+  // the last CTA to leave advances the epoch for the next launch
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.epoch + 1, 1u) == gridDim.x - 1) {
+      atomicExch(a.epoch + 1, 0u);
+      atomicAdd(a.epoch, 1u);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void sweep_flow_consumers(const SweepArgs& a, const T* map_in, T* map_out,
+                                                     const FlowTask* tk, int nt, unsigned int fbase, const float* slots,
+                                                     uint64_t* full, uint64_t* empty, float (*vs)[TK], float* ts,
+                                                     float4 (*part)[16], volatile int* s_abort) {
+  const int tid = threadIdx.x;
+
+  // consumer warps
+  const int rq = tid & 15, jg = tid >> 4, lane = tid & 31;
+  long used = 0;
+  bool ok = true;
+  auto take = [&]() -> const float* {  // the next block, once it has landed
+    const int slot = (int)(used % SF_NS);
+    ok = sw_wait(&full[slot], (uint32_t)((used / SF_NS) & 1)) && !*s_abort;
     return slots + slot * (TK * TK);
   };
-
-  for (int step = 0; step < 2 * a.ncol && ok; ++step) {
-    const int sweep = step < a.ncol ? 0 : 1;
-    const int c = sweep == 0 ? step : 2 * a.ncol - 1 - step;
-    for (int p = a.colour_start[c] + (int)blockIdx.x; p < a.colour_start[c + 1] && ok; p += (int)gridDim.x) {
-      const int nb = sw_nblk(a, sweep, p) - 1;  // off-diagonal blocks
-      const int64_t b0 = sweep == 0 ? a.row_ptr[p] : a.col_ptr[p];
-      const int* nbr = sweep == 0 ? a.row_col : a.col_row;
-      for (int e = tid; e < nb * TK; e += SW_NT)
-        vs[e / TK][e % TK] = __ldcg(a.y + (int64_t)nbr[b0 + e / TK] * TK + (e % TK));
-      float r = 0.f;
-      if (tid < TK)
-        r = sweep == 0 ? (float)map_in[a.perm[(int64_t)p * TK + tid]] : __ldcg(a.y + (int64_t)p * TK + tid);
-      __syncthreads();
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int k = 0; k < nb; ++k) {
-        const float* B = next_block();
-        if (!ok) break;
-        acc = block_gemv_w_smem(B, vs[k], rq, jg, acc);
-      }
-      if (!ok) break;
-      const float s1 = reduce_groups_w(acc, part, rq, jg, tid);
-      if (tid < TK) ts[tid] = r - s1;
-      const float* D = next_block();  // the barrier inside also publishes ts
-      if (!ok) break;
-      acc = block_gemv_w_smem(D, ts, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
-      const float v = reduce_groups_w(acc, part, rq, jg, tid);
-      if (tid < TK) {
-        a.y[(int64_t)p * TK + tid] = v;
-        if (sweep == 1) map_out[a.perm[(int64_t)p * TK + tid]] = (T)v;
+  auto release = [&]() {  // this warp is done with the current block
+    __syncwarp();
+    if (lane == 0) sw_arrive(&empty[used % SF_NS]);
+    ++used;
+  };
+  for (int t = 0; t < nt && ok; ++t) {
+    const int p = tk[t].p, sweep = tk[t].sweep, nb = tk[t].nb;
+    // the tile's own input and output index first: they wait for no tile
+    float r = 0.f;
+    int pix = 0;
+    if (tid < TK) {
+      pix = a.perm[(int64_t)p * TK + tid];
+      r = sweep == 0 ? (float)map_in[pix] : __ldcg(a.y + (int64_t)p * TK + tid);
+    }
+    bool w = true;
+    if (tid < nb) {
+      const int* f = a.flag + tk[t].nbr[tid];
+      const unsigned int want = fbase + (unsigned int)sweep + 1u;
+      uint32_t it = 0;
+      // flags advance by at most a few epochs: compare modulo 2^32
+      while ((int)((unsigned int)ld_acquire_gpu(f) - want) < 0) {
+        if (++it > SW_WAIT || *s_abort) {
+          w = false;
+          break;
+        }
       }
     }
+    ok = cons_sync_and(w);
     if (!ok) break;
-    if (step + 1 < 2 * a.ncol) ok = sw_grid_barrier(a.bar, gridDim.x);
+    for (int e = tid; e < nb * TK; e += SF_CONS) vs[e / TK][e % TK] = __ldcg(a.y + (int64_t)tk[t].nbr[e / TK] * TK + (e % TK));
+    cons_sync();
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < nb; ++k) {
+      const float* B = take();
+      if (!cons_sync_and(ok)) {
+        ok = false;
+        break;
+      }
+      acc = block_gemv_w_smem(B, vs[k], rq, jg, acc);
+      release();
+    }
+    if (!ok) break;
+    const float s1 = reduce_groups_c(acc, part, rq, jg, tid);
+    if (tid < TK) ts[tid] = r - s1;
+    const float* D = take();
+    ok = cons_sync_and(ok);  // also publishes ts
+    if (!ok) break;
+    acc = block_gemv_w_smem(D, ts, rq, jg, make_float4(0.f, 0.f, 0.f, 0.f));
+    release();
+    const float v = reduce_groups_c(acc, part, rq, jg, tid);
+    if (tid < TK) {
+      a.y[(int64_t)p * TK + tid] = v;
+      if (sweep == 1) map_out[pix] = (T)v;
+    }
+    // publish the tile: every consumer's y stores precede the barrier, and
+    // the release store orders them (cumulatively) before the flag
+    cons_sync();
+    if (tid == 0)
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.flag + p), "r"(fbase + (unsigned int)sweep + 1u) : "memory");
   }
-  if (!ok) {
-    if (tid == 0) atomicExch(a.status, 1);
-    // the copies still in flight land in this CTA's shared memory: wait for
-    // them (bounded) before the CTA leaves
-    for (long b = used; b < issued; ++b) sw_wait(&mbar[b % SW_NS], (uint32_t)((b / SW_NS) & 1));
+  if (!ok && tid == 0) {
+    *s_abort = 1;
+    atomicExch(a.status, 1);
   }
 }
 
@@ -940,7 +1000,12 @@ int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
 // factor at close to the HBM rate).
 constexpr int SW_MAX_TILES = 1024;
 
-static int choose_coop_grid(cr_plan* P, PixLevel& lev) {
+// Plans the cooperative data-flow sweeps of a level: the grid (at most one
+// CTA per SM and no more CTAs than the widest colour has tiles) and every
+// CTA's task list.  coop_grid stays 0 (one launch per colour) when the
+// sweep mode asks for that, the device cannot launch cooperatively, or a CTA
+// would hold more than SF_MAXT tasks.
+static int plan_flow(cr_plan* P, PixLevel& lev, const std::vector<int64_t>& col_ptr, const std::vector<int>& col_row) {
   lev.coop_grid = 0;
   const BlockPattern& pat = lev.pat;
   const int mode = P->hier ? P->hier->sweep_mode : 0;
@@ -950,16 +1015,48 @@ static int choose_coop_grid(cr_plan* P, PixLevel& lev) {
   CR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return CR_OK;
-  const int smem = SW_NS * SW_BLOCK_BYTES;
-  CR_CUDA(cudaFuncSetAttribute(sweep_coop_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  CR_CUDA(cudaFuncSetAttribute(sweep_coop_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_d, sweep_coop_kernel<double>, SW_NT, smem));
-  CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, sweep_coop_kernel<float>, SW_NT, smem));
+  const int smem = SF_NS * SW_BLOCK_BYTES;
+  CR_CUDA(cudaFuncSetAttribute(sweep_flow_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CR_CUDA(cudaFuncSetAttribute(sweep_flow_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_d, sweep_flow_kernel<double>, SF_NT, smem));
+  CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, sweep_flow_kernel<float>, SF_NT, smem));
   if (nb_d < 1 || nb_f < 1) return CR_OK;
+  const int ncol = (int)pat.colour_start.size() - 1;
   int widest = 0;
-  for (size_t c = 0; c + 1 < pat.colour_start.size(); ++c)
-    widest = std::max(widest, pat.colour_start[c + 1] - pat.colour_start[c]);
-  lev.coop_grid = std::max(1, std::min(nsm, widest));
+  for (int c = 0; c < ncol; ++c) widest = std::max(widest, pat.colour_start[c + 1] - pat.colour_start[c]);
+  const int G = std::max(1, std::min(nsm, widest));
+  std::vector<FlowTask> tasks;
+  std::vector<int> off(G + 1, 0);
+  for (int b = 0; b < G; ++b) {
+    off[b] = (int)tasks.size();
+    for (int sweep = 0; sweep < 2; ++sweep)
+      for (int k = 0; k < ncol; ++k) {
+        const int c = sweep == 0 ? k : ncol - 1 - k;
+        for (int p = pat.colour_start[c] + b; p < pat.colour_start[c + 1]; p += G) {
+          FlowTask t{};
+          t.p = p;
+          t.sweep = sweep;
+          if (sweep == 0) {
+            t.nb = (int)(pat.row_ptr[p + 1] - 1 - pat.row_ptr[p]);
+            t.blk0 = pat.row_ptr[p];
+          } else {
+            t.nb = (int)(col_ptr[p + 1] - col_ptr[p]);
+            t.blk0 = col_ptr[p] + p;
+          }
+          if (t.nb > 8) return fail(CR_EINVAL, "smoother: a tile with more than 8 neighbours");
+          for (int j = 0; j < t.nb; ++j)
+            t.nbr[j] = sweep == 0 ? pat.row_col[pat.row_ptr[p] + j] : col_row[col_ptr[p] + j];
+          tasks.push_back(t);
+        }
+      }
+    if ((int)tasks.size() - off[b] > SF_MAXT) return CR_OK;
+  }
+  off[G] = (int)tasks.size();
+  CR_CUDA(cudaMalloc(&lev.d_flow_task, tasks.size() * sizeof(FlowTask)));
+  CR_CUDA(cudaMemcpy(lev.d_flow_task, tasks.data(), tasks.size() * sizeof(FlowTask), cudaMemcpyHostToDevice));
+  int rc = upload_vec(&lev.d_flow_off, off);
+  if (rc) return rc;
+  lev.coop_grid = G;
   return CR_OK;
 }
 
@@ -1042,12 +1139,12 @@ int smoother_structure(cr_plan* P, PixLevel& lev) {
   int rc = CR_OK;
   if ((rc = upload_vec(&lev.d_perm, perm))) return rc;
   if ((rc = upload_vec(&lev.d_colour_start, pat.colour_start))) return rc;
-  if ((rc = choose_coop_grid(P, lev))) return rc;
   if ((rc = upload_vec(&lev.d_row_ptr, pat.row_ptr))) return rc;
   if ((rc = upload_vec(&lev.d_row_col, pat.row_col))) return rc;
   if ((rc = upload_vec(&lev.d_col_ptr, col_ptr))) return rc;
   if ((rc = upload_vec(&lev.d_col_row, col_row))) return rc;
   if ((rc = upload_vec(&lev.d_col_blk, col_blk))) return rc;
+  if ((rc = plan_flow(P, lev, col_ptr, col_row))) return rc;
   if ((rc = upload_vec(&lev.d_upd_ptr, upd_ptr))) return rc;
   if ((rc = upload_vec(&lev.d_tgt_blk, tgt_blk))) return rc;
   if ((rc = upload_vec(&lev.d_tgt_u, tgt_u))) return rc;
@@ -1232,28 +1329,24 @@ int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
     SweepArgs sa;
     sa.L = lev.d_L;
     sa.LT = lev.d_LT;
-    sa.row_ptr = lev.d_row_ptr;
-    sa.row_col = lev.d_row_col;
-    sa.col_ptr = lev.d_col_ptr;
-    sa.col_row = lev.d_col_row;
     sa.perm = lev.d_perm;
-    sa.colour_start = lev.d_colour_start;
-    sa.ncol = nc;
+    sa.task = reinterpret_cast<const FlowTask*>(lev.d_flow_task);
+    sa.task_off = lev.d_flow_off;
     sa.y = y;
-    sa.bar = P->hier->d_sweep_bar;
+    sa.flag = P->hier->d_sweep_flag;
+    sa.epoch = P->hier->d_sweep_epoch;
     sa.status = P->hier->d_sweep_status;
-    CR_CUDA(cudaMemsetAsync(sa.bar, 0, 2 * sizeof(unsigned int), P->stream));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(lev.coop_grid);
-    cfg.blockDim = dim3(SW_NT);
-    cfg.dynamicSmemBytes = (size_t)SW_NS * SW_BLOCK_BYTES;
+    cfg.blockDim = dim3(SF_NT);
+    cfg.dynamicSmemBytes = (size_t)SF_NS * SW_BLOCK_BYTES;
     cfg.stream = P->stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    CR_CUDA(cudaLaunchKernelEx(&cfg, sweep_coop_kernel<T>, sa, (const T*)map_in, map_out));
+    CR_CUDA(cudaLaunchKernelEx(&cfg, sweep_flow_kernel<T>, sa, (const T*)map_in, map_out));
     count_launch();
     return CR_OK;
   }
@@ -1306,7 +1399,7 @@ void free_smoother(PixLevel& lev) {
   void* ptrs[] = {lev.d_A, lev.d_L, lev.d_LT, lev.d_perm, lev.d_colour_start, lev.d_row_ptr, lev.d_row_col,
                   lev.d_col_ptr, lev.d_col_row,
                   lev.d_col_blk, lev.d_upd_ptr, lev.d_tgt_blk, lev.d_tgt_u, lev.d_tgt_ptr, lev.d_pair_a, lev.d_pair_b,
-                  lev.d_fail};
+                  lev.d_fail, lev.d_flow_task, lev.d_flow_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

@@ -470,9 +470,11 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
   CR_CUDA(cudaMalloc(&H.map_work2, max_npix_h * sizeof(double)));
   CR_CUDA(cudaMalloc(&P->hier_tile_work, max_npix_h * sizeof(float)));
   CR_CUDA(cudaMalloc(&H.d_dot, 4 * sizeof(double)));
-  CR_CUDA(cudaMalloc(&H.d_sweep_bar, 2 * sizeof(unsigned int)));
+  CR_CUDA(cudaMalloc(&H.d_sweep_flag, (max_npix_h / 64 + 1) * sizeof(int)));
   CR_CUDA(cudaMalloc(&H.d_sweep_status, sizeof(int)));
-  CR_CUDA(cudaMemset(H.d_sweep_bar, 0, 2 * sizeof(unsigned int)));
+  CR_CUDA(cudaMemset(H.d_sweep_flag, 0, (max_npix_h / 64 + 1) * sizeof(int)));
+  CR_CUDA(cudaMalloc(&H.d_sweep_epoch, 2 * sizeof(unsigned int)));
+  CR_CUDA(cudaMemset(H.d_sweep_epoch, 0, 2 * sizeof(unsigned int)));
   CR_CUDA(cudaMemset(H.d_sweep_status, 0, sizeof(int)));
   for (int i = 0; i < 5; ++i) CR_CUDA(cudaMalloc(&H.krylov[i], n_lm(L) * sizeof(double2)));
   // settings of the C_l-dependent precompute
@@ -590,7 +592,7 @@ void free_hierarchy(cr_plan* P) {
       if (p) cudaFree(p);
   }
   void* ptrs[] = {H.d_Ainv, H.d_Abottom, H.d_dof_lm, H.map_work, H.map_work2, H.d_dot, P->hier_tile_work,
-                  H.d_sweep_bar, H.d_sweep_status};
+                  H.d_sweep_flag, H.d_sweep_epoch, H.d_sweep_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   P->hier_tile_work = nullptr;
