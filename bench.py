@@ -887,8 +887,11 @@ def main():
     t3 = time.perf_counter()
     table = plan.autotune()
     autotune = {"s": time.perf_counter() - t3,
-                "observation_grid": {"%s_%s" % (t["precision"], t["stage"]): t.get("pairs_per_thread", t.get("variant"))
+                "observation_grid": {"%s_%s" % (t["precision"], t["stage"]):
+                                     ({"pairs_per_thread": t["pairs_per_thread"], "m_tile": t["m_tile"]}
+                                      if "pairs_per_thread" in t else {"variant": t["variant"]})
                                      for t in table if t["nring"] == 4 * nside - 1 and t["lmax"] == lmax},
+                "m_tile_2_chosen": sum(1 for t in table if t.get("m_tile") == 2),
                 "entries": len(table)}
     x_true = torch.from_numpy(synthetic.draw_prior(cl, index=rank)).to(dev)
     b = torch.empty_like(x_true)

@@ -232,11 +232,12 @@ int cr_plan_create(cr_plan** out, const cr_params* p);
 /*
  * Autotuner of the Legendre kernels (Section 2.1 transforms): times the
  * FP32 and FP64 synthesis and adjoint Legendre stages with 2, 4 and 8 ring
- * pairs per thread (the ring block of one CTA: 256, 512 or 1024 pairs of one
- * m; 16, i.e. 2048 pairs, too for the FP32 adjoint) on every grid and band
- * limit the plan transforms on, and keeps the fastest.  Choices are cached for the process per (grid shape, band limit,
+ * pairs per thread (the ring block of one CTA; 16 too for the FP32 adjoint),
+ * each with the m tile 1 and 2 (one m per CTA, or m paired with L - m), on
+ * every grid and band limit the plan transforms on, and keeps the fastest
+ * shape.  Choices are cached for the process per (grid shape, band limit,
  * precision, stage) and used by every plan with those shapes; shapes already
- * in the cache are not re-timed.  Untuned shapes use 4.  *nentries (may be
+ * in the cache are not re-timed.  Untuned shapes use 4 and 1.  *nentries (may be
  * NULL) receives the size of the cache.  Synchronous; a few seconds at
  * Nside 2048.  The batched tensor-core synthesis (16 right-hand sides) is
  * tuned too: its stage shape (variant 0: K 32 per parity, 2 pipeline
@@ -244,18 +245,22 @@ int cr_plan_create(cr_plan** out, const cr_params* p);
  * and stage 2.  cr_tune_entry reads cache entry i (0 <= i < size): grid
  * ring and pixel counts, band limit, precision in bytes (4 or 8; 2 for the
  * tensor-core entries), stage (0 synthesis, 1 adjoint, 2 tensor-core
- * synthesis), the chosen pairs per thread (or variant) and the measured ms
- * of the choices 2, 4, 8, 16 pairs per thread (or variants 0, 1, 2) (HOST
- * [4]; -1 where there is no such choice); any output may be NULL.  Errors:
- * CR_EINVAL, CR_ECUDA.
+ * synthesis), the chosen pairs per thread (or variant), the chosen m tile
+ * (1: one m per CTA; 2: each CTA takes m and L - m, so that every CTA has
+ * about the same l range; 1 for the tensor-core entries) and the measured
+ * ms (HOST [8]; -1 where there is no such choice): choices 2, 4, 8, 16 pairs
+ * per thread with m tile 1, then the same with m tile 2 (tensor-core
+ * entries: variants 0, 1, 2 in the first three); any output may be NULL.
+ * Errors: CR_EINVAL, CR_ECUDA.
  */
 int cr_plan_autotune(cr_plan* plan, int* nentries);
 int cr_tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* precision_bytes, int* stage, int* rp,
-                  double* ms);
+                  int* m_tile, double* ms);
 /* Pin the choice for one (grid shape, band limit, precision, stage): rp 2,
- * 4 or 8, or 16 for the FP32 adjoint; precision 2 with stage 2: the
- * tensor-core synthesis variant 0, 1 or 2.  Errors: CR_EINVAL. */
-int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp);
+ * 4 or 8, or 16 for the FP32 adjoint, with m tile 1 or 2; precision 2 with
+ * stage 2: the tensor-core synthesis variant 0, 1 or 2 (m tile 1).  Errors:
+ * CR_EINVAL. */
+int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp, int m_tile);
 
 /*
  * Replace the prior C_l of a plan (HOST [lmax + 1], finite, >= 0) and redo

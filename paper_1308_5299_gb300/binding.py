@@ -85,11 +85,12 @@ _SIGS = {
     "cr_plan_update_cl": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cr_save": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
     "cr_plan_autotune": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
-    "cr_tune_set": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
-                    ctypes.c_int),
+    "cr_tune_set": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                     ctypes.c_int], ctypes.c_int),
     "cr_tune_entry": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
+                      ctypes.c_int),
     "cr_load": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
     "cr_plan_sizes": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -219,19 +220,21 @@ def launch_count():
 def tune_table():
     """The autotuner's cached choices: one dict per (grid, band limit,
     precision, stage).  Legendre stages (precision "f32"/"f64", stage
-    "synthesis"/"adjoint"): the chosen pairs per thread and the measured ms
-    of 2, 4, 8 (and, for the FP32 adjoint, 16) pairs per thread.  The
-    batched tensor-core synthesis (precision "bf16", stage "tc_synthesis"):
-    the chosen stage-shape variant (0: K 32 per parity, 2 stages; 1: K 32,
-    3 stages; 2: K 16, 3 stages) and the measured ms of each."""
+    "synthesis"/"adjoint"): the chosen pairs per thread and m tile (1: one m
+    per CTA, 2: m and L - m per CTA) and the measured ms of 2, 4, 8 (and,
+    for the FP32 adjoint, 16) pairs per thread with m tile 1 (``ms``) and 2
+    (``ms_m_tile2``).  The batched tensor-core synthesis (precision "bf16",
+    stage "tc_synthesis"): the chosen stage-shape variant (0: K 32 per
+    parity, 2 stages; 1: K 32, 3 stages; 2: K 16, 3 stages) and the measured
+    ms of each."""
     out = []
     i = 0
     while True:
-        nring, lmax, nb, stage, rp = (ctypes.c_int() for _ in range(5))
+        nring, lmax, nb, stage, rp, mt = (ctypes.c_int() for _ in range(6))
         npix = ctypes.c_int64()
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 8)()
         if lib().cr_tune_entry(i, ctypes.byref(nring), ctypes.byref(npix), ctypes.byref(lmax), ctypes.byref(nb),
-                               ctypes.byref(stage), ctypes.byref(rp), ms) != 0:
+                               ctypes.byref(stage), ctypes.byref(rp), ctypes.byref(mt), ms) != 0:
             return out
         if nb.value == 2:
             out.append(dict(nring=nring.value, npix=npix.value, lmax=lmax.value, precision="bf16",
@@ -241,17 +244,20 @@ def tune_table():
             out.append(dict(nring=nring.value, npix=npix.value, lmax=lmax.value,
                             precision="f64" if nb.value == 8 else "f32",
                             stage="synthesis" if stage.value == 0 else "adjoint", pairs_per_thread=rp.value,
-                            ms={k: ms[i2] for i2, k in enumerate((2, 4, 8, 16)) if ms[i2] >= 0}))
+                            m_tile=mt.value,
+                            ms={k: ms[i2] for i2, k in enumerate((2, 4, 8, 16)) if ms[i2] >= 0},
+                            ms_m_tile2={k: ms[4 + i2] for i2, k in enumerate((2, 4, 8, 16)) if ms[4 + i2] >= 0}))
         i += 1
 
 
-def tune_set(nring, npix, lmax, precision, stage, pairs_per_thread):
+def tune_set(nring, npix, lmax, precision, stage, pairs_per_thread, m_tile=1):
     """Pin one autotuner choice (``cr_tune_set``): precision "f32"/"f64" with
-    stage "synthesis"/"adjoint" and the pairs per thread, or precision
-    "bf16" with stage "tc_synthesis" and the shape variant (0, 1, 2)."""
+    stage "synthesis"/"adjoint", the pairs per thread and the m tile (1 or
+    2), or precision "bf16" with stage "tc_synthesis" and the shape variant
+    (0, 1, 2)."""
     nb = {"f64": 8, "f32": 4, "bf16": 2}[precision]
     st = {"synthesis": 0, "adjoint": 1, "tc_synthesis": 2}[stage]
-    _check(lib().cr_tune_set(int(nring), int(npix), int(lmax), nb, st, int(pairs_per_thread)))
+    _check(lib().cr_tune_set(int(nring), int(npix), int(lmax), nb, st, int(pairs_per_thread), int(m_tile)))
 
 
 def _tc_code(code, tensor_cores, what):

@@ -99,12 +99,12 @@ def tc_case(nside, lmax, nrhs, warmup, reps, tune=False, split=False):
 def sht_case(nside, lmax, warmup, reps, dtype, pins=()):
     """One synthesis and one adjoint synthesis (single right-hand side) in
     FP32 or FP64, default (untuned) ring blocks unless pinned: pins is a list
-    of (stage, pairs per thread)."""
+    of (stage, pairs per thread, m tile)."""
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    for stage, rp in pins:
-        binding.tune_set(4 * nside - 1, 12 * nside * nside, lmax, dtype, stage, rp)
+    for stage, rp, mt in pins:
+        binding.tune_set(4 * nside - 1, 12 * nside * nside, lmax, dtype, stage, rp, m_tile=mt)
     plan = binding.Plan(lmax, nside=nside, stream=stream)
     cdt, rdt = (torch.complex64, torch.float32) if dtype == "f32" else (torch.complex128, torch.float64)
     a = torch.from_numpy(synthetic.random_alm(lmax, seed=301)).to(cdt).to(dev)
@@ -258,6 +258,7 @@ def main(argv=None):
                     help="apply, sht: ring pairs per thread of the adjoint Legendre stage (as the autotuner would pin)")
     ap.add_argument("--pin-synth", type=int, default=0,
                     help="sht: ring pairs per thread of the synthesis Legendre stage")
+    ap.add_argument("--m-tile", type=int, default=1, help="sht: m tile (1 or 2) of the pinned stages")
     ap.add_argument("--workload", default="nside256_lmax767")
     ap.add_argument("--cycles", type=int, default=4)
     ap.add_argument("--iters", type=int, default=16)
@@ -283,7 +284,8 @@ def main(argv=None):
     elif args.case == "grad":
         print(json.dumps(grad_case(args.workload, args.nrhs, args.warmup)))
     else:
-        pins = [(st, rp) for st, rp in (("synthesis", args.pin_synth), ("adjoint", args.pin_adjoint)) if rp]
+        pins = [(st, rp, args.m_tile) for st, rp in (("synthesis", args.pin_synth), ("adjoint", args.pin_adjoint))
+                if rp]
         print(json.dumps(sht_case(args.nside, args.lmax, args.warmup, args.reps, args.dtype, pins)))
 
 

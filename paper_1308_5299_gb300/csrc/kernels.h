@@ -33,6 +33,7 @@ struct LegArgs {
   typename Tr<T>::C* partial = nullptr;    // adjoint: [nblk][n_lm(L)]
   const T* ringval = nullptr;              // SQ variant: per-ring value
   int rp_synth = 4, rp_adj = 4;            // ring pairs per thread (2, 4, 8) of the two stages
+  int mt_synth = 1, mt_adj = 1;            // m tile: 1 (one m per CTA) or 2 (m and L - m per CTA)
   int tc_variant = 0;                      // tensor-core kernels: stage shape (legendre_tc.cu)
   int tc_split = 0;                        // tensor-core kernels: hi + lo BF16 operands
 };

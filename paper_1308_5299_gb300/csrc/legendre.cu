@@ -131,102 +131,109 @@ __device__ __forceinline__ bool load_pairs(const LegArgs<T>& a, int m, int yb, i
   return *wmin <= a.L;
 }
 
-template <typename T, bool POLAR, int RP>
+template <typename T, bool POLAR, int RP, int MT = 1>
 __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp, int yoff) {
   using C = typename Tr<T>::C;
-  const int m = blockIdx.y;
-  const int L = a.L;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  // each warp stages its own chunks (no block-wide barrier in the loop)
-  __shared__ C sa_all[LEG_NW][LEG_CH];
-  __shared__ T sc_all[LEG_NW][LEG_CH];
-  __shared__ T sc2_all[POLAR ? LEG_NW : 1][LEG_CH];
-  C* sa = sa_all[warp];
-  T* sc = sc_all[warp];
-  T* sc2 = sc2_all[POLAR ? warp : 0];
+  // m tile: this CTA takes m = blockIdx.y and, with MT = 2, then
+  // m = L - blockIdx.y, so that every CTA has about the same l range
+#pragma unroll 1
+  for (int mi = 0; mi < MT; ++mi) {
+    const int m = mi == 0 ? (int)blockIdx.y : a.L - (int)blockIdx.y;
+    if (mi > 0 && m <= (int)blockIdx.y) break;
+    if (mi > 0) __syncthreads();  // the shared buffers of the previous m are free
+    const int L = a.L;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    // each warp stages its own chunks (no block-wide barrier in the loop)
+    __shared__ C sa_all[LEG_NW][LEG_CH];
+    __shared__ T sc_all[LEG_NW][LEG_CH];
+    __shared__ T sc2_all[POLAR ? LEG_NW : 1][LEG_CH];
+    C* sa = sa_all[warp];
+    T* sc = sc_all[warp];
+    T* sc2 = sc2_all[POLAR ? warp : 0];
 
-  T P1[RP], P2[RP], zz[RP];
-  int ls[RP], p[RP];
-  C accE[RP], accO[RP];
-#pragma unroll
-  for (int j = 0; j < RP; ++j) {
-    accE[j] = mk((T)0, (T)0);
-    accO[j] = mk((T)0, (T)0);
-  }
-  const int yb = (int)blockIdx.x + yoff;
-  int wmin, wmax;
-  const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
-  const int64_t offa = lm_off(L, m);
-  const int64_t offc = lm_off(a.Lc, m);
-
-  // chunks start at an offset from m that is a multiple of 8, so l - m and
-  // the group index agree in parity; a warp starts at its earliest pair
-  const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
-  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
-    const int nl = min(LEG_CH, L - l0 + 1);
-    __syncwarp();
-    for (int i = lane; i < nl; i += 32) {
-      const int l = l0 + i;
-      C v = a.alm[offa + (l - m)];
-      if (m == 0) v.y = 0;
-      T f = a.s[offc + (l - m)];
-      if (a.dl) f *= a.dl[l];
-      sa[i] = cscale(v, f);
-      sc[i] = a.c[offc + (l - m)];
-      if (POLAR) sc2[i] = a.c2[offc + (l - m)];
+    T P1[RP], P2[RP], zz[RP];
+    int ls[RP], p[RP];
+    C accE[RP], accO[RP];
+  #pragma unroll
+    for (int j = 0; j < RP; ++j) {
+      accE[j] = mk((T)0, (T)0);
+      accO[j] = mk((T)0, (T)0);
     }
-    __syncwarp();
-    for (int i8 = 0; i8 < nl; i8 += 8) {
-      const int lg = l0 + i8;
-      const int ng = min(8, nl - i8);
-      if (wmin >= lg + ng) continue;  // no pair of the warp has started
-      if (wmax <= lg && ng == 8) {
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
-          const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
-          const C a0 = sa[i8 + u], a1 = sa[i8 + u + 1];
-#pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-            const T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
-            accE[j].x = fma(q0, a0.x, accE[j].x);
-            accE[j].y = fma(q0, a0.y, accE[j].y);
-            accO[j].x = fma(q1, a1.x, accO[j].x);
-            accO[j].y = fma(q1, a1.y, accO[j].y);
-          }
-        }
-      } else {
-        for (int u = 0; u < ng; ++u) {
-          const int l = lg + u;
-          const T c0 = sc[i8 + u];
-          const T d0 = POLAR ? sc2[i8 + u] : (T)0;
-          const C a0 = sa[i8 + u];
-#pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            if (l >= ls[j]) {
+    const int yb = (int)blockIdx.x + yoff;
+    int wmin, wmax;
+    const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+    const int64_t offa = lm_off(L, m);
+    const int64_t offc = lm_off(a.Lc, m);
+
+    // chunks start at an offset from m that is a multiple of 8, so l - m and
+    // the group index agree in parity; a warp starts at its earliest pair
+    const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
+    for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
+      const int nl = min(LEG_CH, L - l0 + 1);
+      __syncwarp();
+      for (int i = lane; i < nl; i += 32) {
+        const int l = l0 + i;
+        C v = a.alm[offa + (l - m)];
+        if (m == 0) v.y = 0;
+        T f = a.s[offc + (l - m)];
+        if (a.dl) f *= a.dl[l];
+        sa[i] = cscale(v, f);
+        sc[i] = a.c[offc + (l - m)];
+        if (POLAR) sc2[i] = a.c2[offc + (l - m)];
+      }
+      __syncwarp();
+      for (int i8 = 0; i8 < nl; i8 += 8) {
+        const int lg = l0 + i8;
+        const int ng = min(8, nl - i8);
+        if (wmin >= lg + ng) continue;  // no pair of the warp has started
+        if (wmax <= lg && ng == 8) {
+  #pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
+            const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
+            const C a0 = sa[i8 + u], a1 = sa[i8 + u + 1];
+  #pragma unroll
+            for (int j = 0; j < RP; ++j) {
               const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-              if (u & 1) {
-                accO[j].x = fma(q0, a0.x, accO[j].x);
-                accO[j].y = fma(q0, a0.y, accO[j].y);
-              } else {
-                accE[j].x = fma(q0, a0.x, accE[j].x);
-                accE[j].y = fma(q0, a0.y, accE[j].y);
+              const T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
+              accE[j].x = fma(q0, a0.x, accE[j].x);
+              accE[j].y = fma(q0, a0.y, accE[j].y);
+              accO[j].x = fma(q1, a1.x, accO[j].x);
+              accO[j].y = fma(q1, a1.y, accO[j].y);
+            }
+          }
+        } else {
+          for (int u = 0; u < ng; ++u) {
+            const int l = lg + u;
+            const T c0 = sc[i8 + u];
+            const T d0 = POLAR ? sc2[i8 + u] : (T)0;
+            const C a0 = sa[i8 + u];
+  #pragma unroll
+            for (int j = 0; j < RP; ++j) {
+              if (l >= ls[j]) {
+                const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+                if (u & 1) {
+                  accO[j].x = fma(q0, a0.x, accO[j].x);
+                  accO[j].y = fma(q0, a0.y, accO[j].y);
+                } else {
+                  accE[j].x = fma(q0, a0.x, accE[j].x);
+                  accE[j].y = fma(q0, a0.y, accE[j].y);
+                }
               }
             }
           }
         }
       }
     }
-  }
-  const int pend = POLAR ? a.npolar : a.npairs;
-#pragma unroll
-  for (int j = 0; j < RP; ++j) {
-    if (p[j] < pend) {
-      const int rn = p[j], rs = a.nring - 1 - p[j];
-      a.phase[(int64_t)rn * a.ldp + m] = cadd(accE[j], accO[j]);
-      if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = csub(accE[j], accO[j]);
+    const int pend = POLAR ? a.npolar : a.npairs;
+  #pragma unroll
+    for (int j = 0; j < RP; ++j) {
+      if (p[j] < pend) {
+        const int rn = p[j], rs = a.nring - 1 - p[j];
+        a.phase[(int64_t)rn * a.ldp + m] = cadd(accE[j], accO[j]);
+        if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = csub(accE[j], accO[j]);
+      }
     }
   }
 }
@@ -277,6 +284,34 @@ __device__ __forceinline__ void warp_reduce8(C v[8]) {
   v[0].y += shfl_x(v[0].y, 1);
 }
 
+// The same reduction through shared memory (one warp's buffer of 8 rows
+// padded to 33 entries, so that the row-wise writes and the strided reads
+// each take the two wavefronts of a 64-bit access): every lane stores its 8
+// values, lane l sums 8 of the 32 entries of row l >> 2 and two shuffle
+// steps add the four quarters.  On return lanes 4u .. 4u + 3 hold the warp
+// sum of value u in v[0].  About 40 instructions instead of the 64 of the
+// shuffle transpose.
+__device__ __forceinline__ void smem_reduce8(float2 v[8], float2 (*buf)[33]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) buf[u][lane] = v[u];
+  __syncwarp();
+  const int u = lane >> 2, k = lane & 3;
+  float2 s = buf[u][8 * k];
+#pragma unroll
+  for (int i = 1; i < 8; ++i) {
+    const float2 t = buf[u][8 * k + i];
+    s.x += t.x;
+    s.y += t.y;
+  }
+  s.x += shfl_x(s.x, 1);
+  s.y += shfl_x(s.y, 1);
+  s.x += shfl_x(s.x, 2);
+  s.y += shfl_x(s.y, 2);
+  __syncwarp();  // the buffer is rewritten by the next group
+  v[0] = s;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 synthesis with packed pairs of FP32 lanes (f32x2 instructions of the
 // sm_100 family: two FP32 operations per issued instruction).  Inside the
@@ -316,423 +351,127 @@ __device__ __forceinline__ u64 add2(u64 a, u64 b) {
 }
 __device__ __forceinline__ u64 lds2(const float2* p) { return *reinterpret_cast<const u64*>(p); }
 
-template <bool POLAR, int RP>
+template <bool POLAR, int RP, int MT = 1>
 __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
   static_assert(RP % 2 == 0, "pairs per thread must be even");
   constexpr int NP = RP / 2;
-  const int m = blockIdx.y;
-  const int L = a.L;
-  const int lane = threadIdx.x;
-  const int warp = 0;
-  __shared__ float2 sax[LEG_CH], say[LEG_CH], sk[LEG_CH];
-  __shared__ float2 sk2[POLAR ? LEG_CH : 1];
+  // m tile: this CTA takes m = blockIdx.y and, with MT = 2, then
+  // m = L - blockIdx.y, so that every CTA has about the same l range
+#pragma unroll 1
+  for (int mi = 0; mi < MT; ++mi) {
+    const int m = mi == 0 ? (int)blockIdx.y : a.L - (int)blockIdx.y;
+    if (mi > 0 && m <= (int)blockIdx.y) break;
+    if (mi > 0) __syncwarp();  // the shared buffers of the previous m are free
+    const int L = a.L;
+    const int lane = threadIdx.x;
+    const int warp = 0;
+    __shared__ float2 sax[LEG_CH], say[LEG_CH], sk[LEG_CH];
+    __shared__ float2 sk2[POLAR ? LEG_CH : 1];
 
-  float P1[RP], P2[RP], zz[RP];
-  int ls[RP], p[RP];
-  float ex[RP], ey[RP], ox[RP], oy[RP];
-#pragma unroll
-  for (int j = 0; j < RP; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
-  const int yb = (int)blockIdx.x + yoff;
-  int wmin, wmax;
-  const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
-  auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
-  if (!POLAR) {
-#pragma unroll
-    for (int j = 0; j < RP; ++j)
-      if (ls[j] <= L) {
-        P1[j] *= sgn(ls[j] - 1);
-        P2[j] *= sgn(ls[j] - 2);
-      }
-  }
-  const int64_t offa = lm_off(L, m);
-  const int64_t offc = lm_off(a.Lc, m);
-  const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
-  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
-    const int nl = min(LEG_CH, L - l0 + 1);
-    __syncwarp();
-    for (int i = lane; i < nl; i += 32) {
-      const int l = l0 + i;
-      float2 v = a.alm[offa + (l - m)];
-      if (m == 0) v.y = 0.f;
-      float f = a.s[offc + (l - m)];
-      if (a.dl) f *= a.dl[l];
-      const float c = a.c[offc + (l - m)];
-      if (POLAR) {
-        sax[i] = make_float2(v.x * f, v.x * f);
-        say[i] = make_float2(v.y * f, v.y * f);
-        sk[i] = make_float2(-c, -c);
-        const float c2 = a.c2[offc + (l - m)];
-        sk2[i] = make_float2(c2, c2);
-      } else {
-        const float g = f * sgn(l);
-        const float al = ((l - m) & 1) ? c : -c;
-        sax[i] = make_float2(v.x * g, v.x * g);
-        say[i] = make_float2(v.y * g, v.y * g);
-        sk[i] = make_float2(al, al);
-      }
+    float P1[RP], P2[RP], zz[RP];
+    int ls[RP], p[RP];
+    float ex[RP], ey[RP], ox[RP], oy[RP];
+  #pragma unroll
+    for (int j = 0; j < RP; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
+    const int yb = (int)blockIdx.x + yoff;
+    int wmin, wmax;
+    const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+    auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
+    if (!POLAR) {
+  #pragma unroll
+      for (int j = 0; j < RP; ++j)
+        if (ls[j] <= L) {
+          P1[j] *= sgn(ls[j] - 1);
+          P2[j] *= sgn(ls[j] - 2);
+        }
     }
-    __syncwarp();
-    for (int i8 = 0; i8 < nl; i8 += 8) {
-      const int lg = l0 + i8;
-      const int ng = min(8, nl - i8);
-      if (wmin >= lg + ng) continue;  // no pair of the warp has started
-      if (wmax <= lg && ng == 8) {
-        u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
-          S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
-          S2[q] = pk2(P2[2 * q], P2[2 * q + 1]);
-          EX[q] = pk2(ex[2 * q], ex[2 * q + 1]);
-          EY[q] = pk2(ey[2 * q], ey[2 * q + 1]);
-          OX[q] = pk2(ox[2 * q], ox[2 * q + 1]);
-          OY[q] = pk2(oy[2 * q], oy[2 * q + 1]);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const u64 K = lds2(&sk[i8 + u]);
-          const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
-          const u64 AX = lds2(&sax[i8 + u]), AY = lds2(&say[i8 + u]);
-#pragma unroll
-          for (int q = 0; q < NP; ++q) {
-            u64 Q;
-            if (POLAR) {
-              const u64 E = fma2(K, Z[q], K2);
-              const u64 D = fma2(E, S1[q], S2[q]);
-              Q = add2(S1[q], D);
-              S2[q] = D;
-            } else {
-              Q = fma2(mul2(K, Z[q]), S1[q], S2[q]);
-              S2[q] = S1[q];
-            }
-            S1[q] = Q;
-            if (u & 1) {
-              OX[q] = fma2(Q, AX, OX[q]);
-              OY[q] = fma2(Q, AY, OY[q]);
-            } else {
-              EX[q] = fma2(Q, AX, EX[q]);
-              EY[q] = fma2(Q, AY, EY[q]);
-            }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
-          upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
-          upk2(EX[q], ex[2 * q], ex[2 * q + 1]);
-          upk2(EY[q], ey[2 * q], ey[2 * q + 1]);
-          upk2(OX[q], ox[2 * q], ox[2 * q + 1]);
-          upk2(OY[q], oy[2 * q], oy[2 * q + 1]);
-        }
-      } else {
-        for (int u = 0; u < ng; ++u) {
-          const int l = lg + u;
-          const float K = sk[i8 + u].x;
-          const float K2 = POLAR ? sk2[i8 + u].x : 0.f;
-          const float ax = sax[i8 + u].x, ay = say[i8 + u].x;
-#pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            if (l >= ls[j]) {
-              float q;
-              if (POLAR) {
-                const float e = fmaf(K, zz[j], K2);
-                const float d = fmaf(e, P1[j], P2[j]);
-                q = P1[j] + d;
-                P2[j] = d;
-              } else {
-                q = fmaf(K * zz[j], P1[j], P2[j]);
-                P2[j] = P1[j];
-              }
-              P1[j] = q;
-              if (u & 1) {
-                ox[j] = fmaf(q, ax, ox[j]);
-                oy[j] = fmaf(q, ay, oy[j]);
-              } else {
-                ex[j] = fmaf(q, ax, ex[j]);
-                ey[j] = fmaf(q, ay, ey[j]);
-              }
-            }
-          }
+    const int64_t offa = lm_off(L, m);
+    const int64_t offc = lm_off(a.Lc, m);
+    const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
+    for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
+      const int nl = min(LEG_CH, L - l0 + 1);
+      __syncwarp();
+      for (int i = lane; i < nl; i += 32) {
+        const int l = l0 + i;
+        float2 v = a.alm[offa + (l - m)];
+        if (m == 0) v.y = 0.f;
+        float f = a.s[offc + (l - m)];
+        if (a.dl) f *= a.dl[l];
+        const float c = a.c[offc + (l - m)];
+        if (POLAR) {
+          sax[i] = make_float2(v.x * f, v.x * f);
+          say[i] = make_float2(v.y * f, v.y * f);
+          sk[i] = make_float2(-c, -c);
+          const float c2 = a.c2[offc + (l - m)];
+          sk2[i] = make_float2(c2, c2);
+        } else {
+          const float g = f * sgn(l);
+          const float al = ((l - m) & 1) ? c : -c;
+          sax[i] = make_float2(v.x * g, v.x * g);
+          say[i] = make_float2(v.y * g, v.y * g);
+          sk[i] = make_float2(al, al);
         }
       }
-    }
-  }
-  const int pend = POLAR ? a.npolar : a.npairs;
-#pragma unroll
-  for (int j = 0; j < RP; ++j) {
-    if (p[j] < pend) {
-      const int rn = p[j], rs = a.nring - 1 - p[j];
-      a.phase[(int64_t)rn * a.ldp + m] = make_float2(ex[j] + ox[j], ey[j] + oy[j]);
-      if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = make_float2(ex[j] - ox[j], ey[j] - oy[j]);
-    }
-  }
-}
-
-// SQ: accumulate P~^2 times a per-ring value (ringval) instead of P~ times
-// the ring's phase G_m: sum_k P~_lm(z_k)^2 v_k, used for the diagonal of
-// Y^T N^-1 Y (the Delta m = 0 term of the ring formula).
-template <typename T, bool POLAR, int RP, bool SQ = false>
-__global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int nbp, int yoff) {
-  using C = typename Tr<T>::C;
-  const int m = blockIdx.y;
-  const int L = a.L;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  // per-warp copies of the recurrence coefficients (staged by each warp),
-  // and per-warp sums of the chunk's l, double-buffered by chunk parity in
-  // FP32 so that one barrier per chunk suffices
-  constexpr int NRB = sizeof(T) == 4 ? 2 : 1;
-  __shared__ T sc_all[LEG_NW][LEG_CH];
-  __shared__ T sc2_all[POLAR ? LEG_NW : 1][LEG_CH];
-  __shared__ C red_all[NRB][LEG_NW][LEG_CH];
-  __shared__ int s_min;
-  T* sc = sc_all[warp];
-  T* sc2 = sc2_all[POLAR ? warp : 0];
-
-  T P1[RP], P2[RP], zz[RP];
-  int ls[RP], p[RP];
-  C GE[RP], GO[RP];
-  const int yb = (int)blockIdx.x + yoff;
-  int wmin, wmax;
-  const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
-  const int pend = POLAR ? a.npolar : a.npairs;
-#pragma unroll
-  for (int j = 0; j < RP; ++j) {
-    GE[j] = mk((T)0, (T)0);
-    GO[j] = mk((T)0, (T)0);
-    if (p[j] < pend && ls[j] <= L) {
-      const int rn = p[j], rs = a.nring - 1 - p[j];
-      if (SQ) {
-        const T v = a.ringval[rn] + ((rs != rn) ? a.ringval[rs] : (T)0);
-        GE[j] = mk(v, (T)0);
-        GO[j] = GE[j];
-      } else {
-        const C gn = a.phase[(int64_t)rn * a.ldp + m];
-        const C gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : mk((T)0, (T)0);
-        GE[j] = cadd(gn, gs);
-        GO[j] = csub(gn, gs);
-      }
-    }
-  }
-  if (tid == 0) s_min = L + 1;
-  __syncthreads();
-  if (lane == 0 && live) atomicMin(&s_min, wmin);
-  __syncthreads();
-  const int cmin = s_min;
-  const int64_t offa = lm_off(L, m);
-  const int64_t offc = lm_off(a.Lc, m);
-  C* part = a.partial + (int64_t)yb * n_lm(L);
-  const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~7) : L + 1;
-  // rows before the block's earliest start are zero
-  for (int l = m + tid; l < lbeg; l += LEG_NT) part[offa + (l - m)] = mk((T)0, (T)0);
-
-  int rb = 0;
-  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
-    const int nl = min(LEG_CH, L - l0 + 1);
-    if (NRB == 1) __syncthreads();  // the previous chunk's sums are read
-    C(*red)[LEG_CH] = red_all[rb];
-    __syncwarp();
-    for (int i = lane; i < nl; i += 32) {
-      sc[i] = a.c[offc + (l0 - m) + i];
-      if (POLAR) sc2[i] = a.c2[offc + (l0 - m) + i];
-    }
-    __syncwarp();
-    for (int i8 = 0; i8 < nl; i8 += 8) {
-      const int lg = l0 + i8;
-      const int ng = min(8, nl - i8);
-      if (!live || wmin >= lg + ng) {
-        // no pair of this warp has started: its share of the sums is zero
-        if (lane < 8) red[warp][i8 + lane] = mk((T)0, (T)0);
-      } else {
-        C acc[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = mk((T)0, (T)0);
+      __syncwarp();
+      for (int i8 = 0; i8 < nl; i8 += 8) {
+        const int lg = l0 + i8;
+        const int ng = min(8, nl - i8);
+        if (wmin >= lg + ng) continue;  // no pair of the warp has started
         if (wmax <= lg && ng == 8) {
-#pragma unroll
-          for (int u = 0; u < 8; u += 2) {
-            const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
-            const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
-#pragma unroll
-            for (int j = 0; j < RP; ++j) {
-              T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-              T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
-              if (SQ) {
-                q0 *= q0;
-                q1 *= q1;
+          u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
+  #pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
+            S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
+            S2[q] = pk2(P2[2 * q], P2[2 * q + 1]);
+            EX[q] = pk2(ex[2 * q], ex[2 * q + 1]);
+            EY[q] = pk2(ey[2 * q], ey[2 * q + 1]);
+            OX[q] = pk2(ox[2 * q], ox[2 * q + 1]);
+            OY[q] = pk2(oy[2 * q], oy[2 * q + 1]);
+          }
+  #pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const u64 K = lds2(&sk[i8 + u]);
+            const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
+            const u64 AX = lds2(&sax[i8 + u]), AY = lds2(&say[i8 + u]);
+  #pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              u64 Q;
+              if (POLAR) {
+                const u64 E = fma2(K, Z[q], K2);
+                const u64 D = fma2(E, S1[q], S2[q]);
+                Q = add2(S1[q], D);
+                S2[q] = D;
+              } else {
+                Q = fma2(mul2(K, Z[q]), S1[q], S2[q]);
+                S2[q] = S1[q];
               }
-              acc[u].x = fma(q0, GE[j].x, acc[u].x);
-              acc[u].y = fma(q0, GE[j].y, acc[u].y);
-              acc[u + 1].x = fma(q1, GO[j].x, acc[u + 1].x);
-              acc[u + 1].y = fma(q1, GO[j].y, acc[u + 1].y);
+              S1[q] = Q;
+              if (u & 1) {
+                OX[q] = fma2(Q, AX, OX[q]);
+                OY[q] = fma2(Q, AY, OY[q]);
+              } else {
+                EX[q] = fma2(Q, AX, EX[q]);
+                EY[q] = fma2(Q, AY, EY[q]);
+              }
             }
+          }
+  #pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
+            upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
+            upk2(EX[q], ex[2 * q], ex[2 * q + 1]);
+            upk2(EY[q], ey[2 * q], ey[2 * q + 1]);
+            upk2(OX[q], ox[2 * q], ox[2 * q + 1]);
+            upk2(OY[q], oy[2 * q], oy[2 * q + 1]);
           }
         } else {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if (u < ng) {
-              const int l = lg + u;
-              const T c0 = sc[i8 + u];
-              const T d0 = POLAR ? sc2[i8 + u] : (T)0;
-#pragma unroll
-              for (int j = 0; j < RP; ++j) {
-                if (l >= ls[j]) {
-                  T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
-                  if (SQ) q0 *= q0;
-                  const C g = (u & 1) ? GO[j] : GE[j];
-                  acc[u].x = fma(q0, g.x, acc[u].x);
-                  acc[u].y = fma(q0, g.y, acc[u].y);
-                }
-              }
-            }
-          }
-        }
-        warp_reduce8(acc);
-        if ((lane & 3) == 0) red[warp][i8 + (lane >> 2)] = acc[0];
-      }
-    }
-    // one barrier per chunk: the warps' sums in a fixed order
-    __syncthreads();
-    for (int i = tid; i < nl; i += LEG_NT) {
-      const int l = l0 + i;
-      C sum = red[0][i];
-#pragma unroll
-      for (int w = 1; w < LEG_NW; ++w) sum = cadd(sum, red[w][i]);
-      const T sc_ = a.s[offc + (l - m)];
-      part[offa + (l - m)] = cscale(sum, SQ ? sc_ * sc_ : sc_);
-    }
-    rb = (rb + 1) % NRB;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 adjoint with packed pairs of FP32 lanes.  Two ring pairs step together
-// in one f32x2 instruction: the recurrence (sign-folded as in the packed
-// synthesis: V_l = sigma_l Q_l, V_l = alpha_l z V_{l-1} + V_{l-2}, so the
-// sums come out multiplied by sigma_l, which the partial-row write undoes;
-// the polar difference form needs no sign change) and the accumulation
-// A_l += V_l G, whose two halves hold the sums over the even and the odd
-// members of the thread's pair list and are added once per 8-l group before
-// the warp's shuffle-transpose reduction.  Up to 16 ring pairs per thread
-// spread the reduction over more terms.
-template <bool POLAR, int RP>
-__global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
-  static_assert(RP % 2 == 0, "pairs per thread must be even");
-  constexpr int NP = RP / 2;
-  const int m = blockIdx.y;
-  const int L = a.L;
-  const int lane = threadIdx.x;
-  __shared__ float2 sk[LEG_CH];
-  __shared__ float2 sk2[POLAR ? LEG_CH : 1];
-
-  float P1[RP], P2[RP], zz[RP];
-  int ls[RP], p[RP];
-  float2 GE[RP], GO[RP];
-  const int yb = (int)blockIdx.x + yoff;
-  int wmin, wmax;
-  const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, 0, lane, p, ls, P1, P2, zz, &wmin, &wmax);
-  auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
-  const int pend = POLAR ? a.npolar : a.npairs;
-#pragma unroll
-  for (int j = 0; j < RP; ++j) {
-    GE[j] = make_float2(0.f, 0.f);
-    GO[j] = make_float2(0.f, 0.f);
-    if (p[j] < pend && ls[j] <= L) {
-      const int rn = p[j], rs = a.nring - 1 - p[j];
-      const float2 gn = a.phase[(int64_t)rn * a.ldp + m];
-      const float2 gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : make_float2(0.f, 0.f);
-      GE[j] = cadd(gn, gs);
-      GO[j] = csub(gn, gs);
-      if (!POLAR) {
-        P1[j] *= sgn(ls[j] - 1);
-        P2[j] *= sgn(ls[j] - 2);
-      }
-    }
-  }
-  const int64_t offa = lm_off(L, m);
-  const int64_t offc = lm_off(a.Lc, m);
-  // this warp's partial row: zero before its first group
-  float2* part = a.partial + (int64_t)yb * n_lm(L);
-  const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
-  for (int l = m + lane; l < lbeg; l += 32) part[offa + (l - m)] = make_float2(0.f, 0.f);
-
-  for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
-    const int nl = min(LEG_CH, L - l0 + 1);
-    __syncwarp();
-    for (int i = lane; i < nl; i += 32) {
-      const int l = l0 + i;
-      const float c = a.c[offc + (l - m)];
-      if (POLAR) {
-        sk[i] = make_float2(-c, -c);
-        const float c2 = a.c2[offc + (l - m)];
-        sk2[i] = make_float2(c2, c2);
-      } else {
-        const float al = ((l - m) & 1) ? c : -c;
-        sk[i] = make_float2(al, al);
-      }
-    }
-    __syncwarp();
-    for (int i8 = 0; i8 < nl; i8 += 8) {
-      const int lg = l0 + i8;
-      const int ng = min(8, nl - i8);
-      float2 acc[8];
-      if (wmax <= lg && ng == 8) {
-        u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
-          S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
-          S2[q] = pk2(P2[2 * q], P2[2 * q + 1]);
-          EX[q] = pk2(GE[2 * q].x, GE[2 * q + 1].x);
-          EY[q] = pk2(GE[2 * q].y, GE[2 * q + 1].y);
-          OX[q] = pk2(GO[2 * q].x, GO[2 * q + 1].x);
-          OY[q] = pk2(GO[2 * q].y, GO[2 * q + 1].y);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const u64 K = lds2(&sk[i8 + u]);
-          const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
-          u64 AX = 0ull, AY = 0ull;
-#pragma unroll
-          for (int q = 0; q < NP; ++q) {
-            u64 Q;
-            if (POLAR) {
-              const u64 E = fma2(K, Z[q], K2);
-              const u64 D = fma2(E, S1[q], S2[q]);
-              Q = add2(S1[q], D);
-              S2[q] = D;
-            } else {
-              Q = fma2(mul2(K, Z[q]), S1[q], S2[q]);
-              S2[q] = S1[q];
-            }
-            S1[q] = Q;
-            if (u & 1) {
-              AX = q ? fma2(Q, OX[q], AX) : mul2(Q, OX[q]);
-              AY = q ? fma2(Q, OY[q], AY) : mul2(Q, OY[q]);
-            } else {
-              AX = q ? fma2(Q, EX[q], AX) : mul2(Q, EX[q]);
-              AY = q ? fma2(Q, EY[q], AY) : mul2(Q, EY[q]);
-            }
-          }
-          float x0, x1, y0, y1;
-          upk2(AX, x0, x1);
-          upk2(AY, y0, y1);
-          acc[u] = make_float2(x0 + x1, y0 + y1);
-        }
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
-          upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (u < ng) {
+          for (int u = 0; u < ng; ++u) {
             const int l = lg + u;
             const float K = sk[i8 + u].x;
             const float K2 = POLAR ? sk2[i8 + u].x : 0.f;
-#pragma unroll
+            const float ax = sax[i8 + u].x, ay = say[i8 + u].x;
+  #pragma unroll
             for (int j = 0; j < RP; ++j) {
               if (l >= ls[j]) {
                 float q;
@@ -746,22 +485,340 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
                   P2[j] = P1[j];
                 }
                 P1[j] = q;
-                const float2 g = (u & 1) ? GO[j] : GE[j];
-                acc[u].x = fmaf(q, g.x, acc[u].x);
-                acc[u].y = fmaf(q, g.y, acc[u].y);
+                if (u & 1) {
+                  ox[j] = fmaf(q, ax, ox[j]);
+                  oy[j] = fmaf(q, ay, oy[j]);
+                } else {
+                  ex[j] = fmaf(q, ax, ex[j]);
+                  ey[j] = fmaf(q, ay, ey[j]);
+                }
               }
             }
           }
         }
       }
-      warp_reduce8(acc);
-      // lane 4 u holds the warp's sum for l = lg + u: scale by s_lm (and the
-      // recurrence's sign) and write it to the row
-      const int u = lane >> 2;
-      if ((lane & 3) == 0 && u < ng) {
-        const int l = lg + u;
-        const float f = a.s[offc + (l - m)] * (POLAR ? 1.f : sgn(l));
-        part[offa + (l - m)] = cscale(acc[0], f);
+    }
+    const int pend = POLAR ? a.npolar : a.npairs;
+  #pragma unroll
+    for (int j = 0; j < RP; ++j) {
+      if (p[j] < pend) {
+        const int rn = p[j], rs = a.nring - 1 - p[j];
+        a.phase[(int64_t)rn * a.ldp + m] = make_float2(ex[j] + ox[j], ey[j] + oy[j]);
+        if (rs != rn) a.phase[(int64_t)rs * a.ldp + m] = make_float2(ex[j] - ox[j], ey[j] - oy[j]);
+      }
+    }
+  }
+}
+
+// SQ: accumulate P~^2 times a per-ring value (ringval) instead of P~ times
+// the ring's phase G_m: sum_k P~_lm(z_k)^2 v_k, used for the diagonal of
+// Y^T N^-1 Y (the Delta m = 0 term of the ring formula).
+template <typename T, bool POLAR, int RP, bool SQ = false, int MT = 1>
+__global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int nbp, int yoff) {
+  using C = typename Tr<T>::C;
+  // m tile: this CTA takes m = blockIdx.y and, with MT = 2, then
+  // m = L - blockIdx.y, so that every CTA has about the same l range
+#pragma unroll 1
+  for (int mi = 0; mi < MT; ++mi) {
+    const int m = mi == 0 ? (int)blockIdx.y : a.L - (int)blockIdx.y;
+    if (mi > 0 && m <= (int)blockIdx.y) break;
+    if (mi > 0) __syncthreads();  // the shared buffers of the previous m are free
+    const int L = a.L;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    // per-warp copies of the recurrence coefficients (staged by each warp),
+    // and per-warp sums of the chunk's l, double-buffered by chunk parity in
+    // FP32 so that one barrier per chunk suffices
+    constexpr int NRB = sizeof(T) == 4 ? 2 : 1;
+    __shared__ T sc_all[LEG_NW][LEG_CH];
+    __shared__ T sc2_all[POLAR ? LEG_NW : 1][LEG_CH];
+    __shared__ C red_all[NRB][LEG_NW][LEG_CH];
+    __shared__ int s_min;
+    T* sc = sc_all[warp];
+    T* sc2 = sc2_all[POLAR ? warp : 0];
+
+    T P1[RP], P2[RP], zz[RP];
+    int ls[RP], p[RP];
+    C GE[RP], GO[RP];
+    const int yb = (int)blockIdx.x + yoff;
+    int wmin, wmax;
+    const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+    const int pend = POLAR ? a.npolar : a.npairs;
+  #pragma unroll
+    for (int j = 0; j < RP; ++j) {
+      GE[j] = mk((T)0, (T)0);
+      GO[j] = mk((T)0, (T)0);
+      if (p[j] < pend && ls[j] <= L) {
+        const int rn = p[j], rs = a.nring - 1 - p[j];
+        if (SQ) {
+          const T v = a.ringval[rn] + ((rs != rn) ? a.ringval[rs] : (T)0);
+          GE[j] = mk(v, (T)0);
+          GO[j] = GE[j];
+        } else {
+          const C gn = a.phase[(int64_t)rn * a.ldp + m];
+          const C gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : mk((T)0, (T)0);
+          GE[j] = cadd(gn, gs);
+          GO[j] = csub(gn, gs);
+        }
+      }
+    }
+    if (tid == 0) s_min = L + 1;
+    __syncthreads();
+    if (lane == 0 && live) atomicMin(&s_min, wmin);
+    __syncthreads();
+    const int cmin = s_min;
+    const int64_t offa = lm_off(L, m);
+    const int64_t offc = lm_off(a.Lc, m);
+    C* part = a.partial + (int64_t)yb * n_lm(L);
+    const int lbeg = (cmin <= L) ? m + ((cmin - m) & ~7) : L + 1;
+    // rows before the block's earliest start are zero
+    for (int l = m + tid; l < lbeg; l += LEG_NT) part[offa + (l - m)] = mk((T)0, (T)0);
+
+    int rb = 0;
+    for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
+      const int nl = min(LEG_CH, L - l0 + 1);
+      if (NRB == 1) __syncthreads();  // the previous chunk's sums are read
+      C(*red)[LEG_CH] = red_all[rb];
+      __syncwarp();
+      for (int i = lane; i < nl; i += 32) {
+        sc[i] = a.c[offc + (l0 - m) + i];
+        if (POLAR) sc2[i] = a.c2[offc + (l0 - m) + i];
+      }
+      __syncwarp();
+      for (int i8 = 0; i8 < nl; i8 += 8) {
+        const int lg = l0 + i8;
+        const int ng = min(8, nl - i8);
+        if (!live || wmin >= lg + ng) {
+          // no pair of this warp has started: its share of the sums is zero
+          if (lane < 8) red[warp][i8 + lane] = mk((T)0, (T)0);
+        } else {
+          C acc[8];
+  #pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] = mk((T)0, (T)0);
+          if (wmax <= lg && ng == 8) {
+  #pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+              const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
+              const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
+  #pragma unroll
+              for (int j = 0; j < RP; ++j) {
+                T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+                T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
+                if (SQ) {
+                  q0 *= q0;
+                  q1 *= q1;
+                }
+                acc[u].x = fma(q0, GE[j].x, acc[u].x);
+                acc[u].y = fma(q0, GE[j].y, acc[u].y);
+                acc[u + 1].x = fma(q1, GO[j].x, acc[u + 1].x);
+                acc[u + 1].y = fma(q1, GO[j].y, acc[u + 1].y);
+              }
+            }
+          } else {
+  #pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (u < ng) {
+                const int l = lg + u;
+                const T c0 = sc[i8 + u];
+                const T d0 = POLAR ? sc2[i8 + u] : (T)0;
+  #pragma unroll
+                for (int j = 0; j < RP; ++j) {
+                  if (l >= ls[j]) {
+                    T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
+                    if (SQ) q0 *= q0;
+                    const C g = (u & 1) ? GO[j] : GE[j];
+                    acc[u].x = fma(q0, g.x, acc[u].x);
+                    acc[u].y = fma(q0, g.y, acc[u].y);
+                  }
+                }
+              }
+            }
+          }
+          warp_reduce8(acc);
+          if ((lane & 3) == 0) red[warp][i8 + (lane >> 2)] = acc[0];
+        }
+      }
+      // one barrier per chunk: the warps' sums in a fixed order
+      __syncthreads();
+      for (int i = tid; i < nl; i += LEG_NT) {
+        const int l = l0 + i;
+        C sum = red[0][i];
+  #pragma unroll
+        for (int w = 1; w < LEG_NW; ++w) sum = cadd(sum, red[w][i]);
+        const T sc_ = a.s[offc + (l - m)];
+        part[offa + (l - m)] = cscale(sum, SQ ? sc_ * sc_ : sc_);
+      }
+      rb = (rb + 1) % NRB;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 adjoint with packed pairs of FP32 lanes.  Two ring pairs step together
+// in one f32x2 instruction: the recurrence (sign-folded as in the packed
+// synthesis: V_l = sigma_l Q_l, V_l = alpha_l z V_{l-1} + V_{l-2}, so the
+// sums come out multiplied by sigma_l, which the partial-row write undoes;
+// the polar difference form needs no sign change) and the accumulation
+// A_l += V_l G, whose two halves hold the sums over the even and the odd
+// members of the thread's pair list and are added once per 8-l group before
+// the warp's shuffle-transpose reduction.  Up to 16 ring pairs per thread
+// spread the reduction over more terms.
+template <bool POLAR, int RP, int MT = 1>
+__global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
+  static_assert(RP % 2 == 0, "pairs per thread must be even");
+  constexpr int NP = RP / 2;
+  // m tile: this CTA takes m = blockIdx.y and, with MT = 2, then
+  // m = L - blockIdx.y, so that every CTA has about the same l range
+#pragma unroll 1
+  for (int mi = 0; mi < MT; ++mi) {
+    const int m = mi == 0 ? (int)blockIdx.y : a.L - (int)blockIdx.y;
+    if (mi > 0 && m <= (int)blockIdx.y) break;
+    if (mi > 0) __syncwarp();  // the shared buffers of the previous m are free
+    const int L = a.L;
+    const int lane = threadIdx.x;
+    __shared__ float2 sk[LEG_CH];
+    __shared__ float2 sk2[POLAR ? LEG_CH : 1];
+    __shared__ float2 rbuf[8][33];
+
+    float P1[RP], P2[RP], zz[RP];
+    int ls[RP], p[RP];
+    float2 GE[RP], GO[RP];
+    const int yb = (int)blockIdx.x + yoff;
+    int wmin, wmax;
+    const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, 0, lane, p, ls, P1, P2, zz, &wmin, &wmax);
+    auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
+    const int pend = POLAR ? a.npolar : a.npairs;
+  #pragma unroll
+    for (int j = 0; j < RP; ++j) {
+      GE[j] = make_float2(0.f, 0.f);
+      GO[j] = make_float2(0.f, 0.f);
+      if (p[j] < pend && ls[j] <= L) {
+        const int rn = p[j], rs = a.nring - 1 - p[j];
+        const float2 gn = a.phase[(int64_t)rn * a.ldp + m];
+        const float2 gs = (rs != rn) ? a.phase[(int64_t)rs * a.ldp + m] : make_float2(0.f, 0.f);
+        GE[j] = cadd(gn, gs);
+        GO[j] = csub(gn, gs);
+        if (!POLAR) {
+          P1[j] *= sgn(ls[j] - 1);
+          P2[j] *= sgn(ls[j] - 2);
+        }
+      }
+    }
+    const int64_t offa = lm_off(L, m);
+    const int64_t offc = lm_off(a.Lc, m);
+    // this warp's partial row: zero before its first group
+    float2* part = a.partial + (int64_t)yb * n_lm(L);
+    const int lbeg = live ? m + ((wmin - m) & ~7) : L + 1;
+    for (int l = m + lane; l < lbeg; l += 32) part[offa + (l - m)] = make_float2(0.f, 0.f);
+
+    for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
+      const int nl = min(LEG_CH, L - l0 + 1);
+      __syncwarp();
+      for (int i = lane; i < nl; i += 32) {
+        const int l = l0 + i;
+        const float c = a.c[offc + (l - m)];
+        if (POLAR) {
+          sk[i] = make_float2(-c, -c);
+          const float c2 = a.c2[offc + (l - m)];
+          sk2[i] = make_float2(c2, c2);
+        } else {
+          const float al = ((l - m) & 1) ? c : -c;
+          sk[i] = make_float2(al, al);
+        }
+      }
+      __syncwarp();
+      for (int i8 = 0; i8 < nl; i8 += 8) {
+        const int lg = l0 + i8;
+        const int ng = min(8, nl - i8);
+        float2 acc[8];
+        if (wmax <= lg && ng == 8) {
+          u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
+  #pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
+            S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
+            S2[q] = pk2(P2[2 * q], P2[2 * q + 1]);
+            EX[q] = pk2(GE[2 * q].x, GE[2 * q + 1].x);
+            EY[q] = pk2(GE[2 * q].y, GE[2 * q + 1].y);
+            OX[q] = pk2(GO[2 * q].x, GO[2 * q + 1].x);
+            OY[q] = pk2(GO[2 * q].y, GO[2 * q + 1].y);
+          }
+  #pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const u64 K = lds2(&sk[i8 + u]);
+            const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
+            u64 AX = 0ull, AY = 0ull;
+  #pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              u64 Q;
+              if (POLAR) {
+                const u64 E = fma2(K, Z[q], K2);
+                const u64 D = fma2(E, S1[q], S2[q]);
+                Q = add2(S1[q], D);
+                S2[q] = D;
+              } else {
+                Q = fma2(mul2(K, Z[q]), S1[q], S2[q]);
+                S2[q] = S1[q];
+              }
+              S1[q] = Q;
+              if (u & 1) {
+                AX = q ? fma2(Q, OX[q], AX) : mul2(Q, OX[q]);
+                AY = q ? fma2(Q, OY[q], AY) : mul2(Q, OY[q]);
+              } else {
+                AX = q ? fma2(Q, EX[q], AX) : mul2(Q, EX[q]);
+                AY = q ? fma2(Q, EY[q], AY) : mul2(Q, EY[q]);
+              }
+            }
+            float x0, x1, y0, y1;
+            upk2(AX, x0, x1);
+            upk2(AY, y0, y1);
+            acc[u] = make_float2(x0 + x1, y0 + y1);
+          }
+  #pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
+            upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
+          }
+        } else {
+  #pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
+  #pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (u < ng) {
+              const int l = lg + u;
+              const float K = sk[i8 + u].x;
+              const float K2 = POLAR ? sk2[i8 + u].x : 0.f;
+  #pragma unroll
+              for (int j = 0; j < RP; ++j) {
+                if (l >= ls[j]) {
+                  float q;
+                  if (POLAR) {
+                    const float e = fmaf(K, zz[j], K2);
+                    const float d = fmaf(e, P1[j], P2[j]);
+                    q = P1[j] + d;
+                    P2[j] = d;
+                  } else {
+                    q = fmaf(K * zz[j], P1[j], P2[j]);
+                    P2[j] = P1[j];
+                  }
+                  P1[j] = q;
+                  const float2 g = (u & 1) ? GO[j] : GE[j];
+                  acc[u].x = fmaf(q, g.x, acc[u].x);
+                  acc[u].y = fmaf(q, g.y, acc[u].y);
+                }
+              }
+            }
+          }
+        }
+        smem_reduce8(acc, rbuf);
+        // lane 4 u holds the warp's sum for l = lg + u: scale by s_lm (and the
+        // recurrence's sign) and write it to the row
+        const int u = lane >> 2;
+        if ((lane & 3) == 0 && u < ng) {
+          const int l = lg + u;
+          const float f = a.s[offc + (l - m)] * (POLAR ? 1.f : sgn(l));
+          part[offa + (l - m)] = cscale(acc[0], f);
+        }
       }
     }
   }
@@ -808,26 +865,41 @@ static inline void pair_blocks(int npolar, int npairs, int rp, int* nbp, int* nb
 static inline int legal_rp(int rp) { return (rp == 2 || rp == 4 || rp == 8) ? rp : LEG_RP; }
 static inline int legal_rp_f32adj(int rp) { return (rp == 2 || rp == 4 || rp == 8 || rp == 16) ? rp : LEG_RP; }
 
-template <typename T, int RP>
-static void synth_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
+// rows of m of a launch: L + 1, or (L + 2) / 2 when each CTA pairs m with L - m
+static inline int m_rows(int L, int mt) { return mt == 2 ? (L + 2) / 2 : L + 1; }
+
+template <typename T, int RP, int MT>
+static void synth_launch_mt(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
+  const int MROWS = m_rows(a.L, MT);
   if constexpr (sizeof(T) == 4) {
-    if (nbp) { leg_synth_f32x2_kernel<true, RP><<<dim3(nbp, a.L + 1), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_synth_f32x2_kernel<false, RP><<<dim3(nbe, a.L + 1), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    if (nbp) { leg_synth_f32x2_kernel<true, RP, MT><<<dim3(nbp, MROWS), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_synth_f32x2_kernel<false, RP, MT><<<dim3(nbe, MROWS), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   } else {
-    if (nbp) { leg_synth_kernel<T, true, RP><<<dim3(nbp, a.L + 1), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_synth_kernel<T, false, RP><<<dim3(nbe, a.L + 1), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+    if (nbp) { leg_synth_kernel<T, true, RP, MT><<<dim3(nbp, MROWS), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_synth_kernel<T, false, RP, MT><<<dim3(nbe, MROWS), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
   }
 }
+template <typename T, int RP>
+static void synth_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
+  if (a.mt_synth == 2) synth_launch_mt<T, RP, 2>(a, nbp, nbe, st);
+  else synth_launch_mt<T, RP, 1>(a, nbp, nbe, st);
+}
 
+template <typename T, int RP, int MT>
+static void adjoint_launch_mt(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
+  const int MROWS = m_rows(a.L, MT);
+  if constexpr (sizeof(T) == 4) {
+    if (nbp) { leg_adjoint_f32x2_kernel<true, RP, MT><<<dim3(nbp, MROWS), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_adjoint_f32x2_kernel<false, RP, MT><<<dim3(nbe, MROWS), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  } else {
+    if (nbp) { leg_adjoint_kernel<T, true, RP, false, MT><<<dim3(nbp, MROWS), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
+    if (nbe) { leg_adjoint_kernel<T, false, RP, false, MT><<<dim3(nbe, MROWS), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
+  }
+}
 template <typename T, int RP>
 static void adjoint_launch(const LegArgs<T>& a, int nbp, int nbe, cudaStream_t st) {
-  if constexpr (sizeof(T) == 4) {
-    if (nbp) { leg_adjoint_f32x2_kernel<true, RP><<<dim3(nbp, a.L + 1), L32_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_adjoint_f32x2_kernel<false, RP><<<dim3(nbe, a.L + 1), L32_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
-  } else {
-    if (nbp) { leg_adjoint_kernel<T, true, RP><<<dim3(nbp, a.L + 1), LEG_NT, 0, st>>>(a, nbp, 0); count_launch(); }
-    if (nbe) { leg_adjoint_kernel<T, false, RP><<<dim3(nbe, a.L + 1), LEG_NT, 0, st>>>(a, nbp, nbp); count_launch(); }
-  }
+  if (a.mt_adj == 2) adjoint_launch_mt<T, RP, 2>(a, nbp, nbe, st);
+  else adjoint_launch_mt<T, RP, 1>(a, nbp, nbe, st);
 }
 
 template <typename T>

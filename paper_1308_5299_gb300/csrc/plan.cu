@@ -357,7 +357,8 @@ struct TuneKey {
 };
 struct TuneVal {
   int rp;
-  double ms[4];  // measured ms for 2, 4, 8, 16 pairs per thread (-1: not a choice of this stage)
+  int mt;         // m tile: 1 (one m per CTA) or 2 (m and L - m per CTA)
+  double ms[8];   // measured ms for 2, 4, 8, 16 pairs per thread, m tile 1 then 2 (-1: not a choice)
 };
 
 // 16 ring pairs per thread exist for the packed FP32 adjoint only
@@ -367,10 +368,12 @@ static bool rp_allowed(int rp, int bytes, int stage) {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune;
 
-static int tuned_rp(const Grid& g, int L, int bytes, int stage) {
+// the cached (pairs per thread, m tile) of a stage; (4, 1) when not tuned
+static void tuned_shape(const Grid& g, int L, int bytes, int stage, int* rp, int* mt) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(TuneKey{g.nring, g.npix, L, bytes, stage});
-  return it == g_tune.end() ? 4 : it->second.rp;
+  *rp = it == g_tune.end() ? 4 : it->second.rp;
+  *mt = it == g_tune.end() ? 1 : it->second.mt;
 }
 
 // Tensor-core stage shapes are cached under precision 2 (BF16 operands),
@@ -386,8 +389,8 @@ static int tuned_tc(const Grid& g, int L) {
 template <typename T>
 static LegArgs<T> leg_args(cr_plan* P, const Grid& g, int L) {
   LegArgs<T> a;
-  a.rp_synth = tuned_rp(g, L, (int)sizeof(T), 0);
-  a.rp_adj = tuned_rp(g, L, (int)sizeof(T), 1);
+  tuned_shape(g, L, (int)sizeof(T), 0, &a.rp_synth, &a.mt_synth);
+  tuned_shape(g, L, (int)sizeof(T), 1, &a.rp_adj, &a.mt_adj);
   a.tc_split = P->tc_split;
   a.tc_variant = tuned_tc(g, L);
   a.ldp = L + 1;
@@ -593,9 +596,10 @@ static const Grid* grid_of(cr_plan* P, int grid, int* L) {
 }
 
 // Time one Legendre stage of grid g at band limit L for 2, 4 and 8 ring
-// pairs per thread (one untimed launch, then `reps` timed with CUDA events on
-// the plan's stream; native kernels, zero coefficients -- the work does not
-// depend on the data) and record the fastest.
+// pairs per thread (16 for the FP32 adjoint), each with one m per CTA and
+// with m paired with L - m (one untimed launch, then `reps` timed with CUDA
+// events on the plan's stream; native kernels, zero coefficients -- the work
+// does not depend on the data) and record the fastest shape.
 template <typename T>
 static int tune_stage(cr_plan* P, const Grid& g, int L, int stage, int reps) {
   using C = typename Tr<T>::C;
@@ -608,14 +612,17 @@ static int tune_stage(cr_plan* P, const Grid& g, int L, int stage, int reps) {
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) rc = cuda_fail(e, "autotune setup");
-  TuneVal v{4, {0.0, 0.0, 0.0, -1.0}};
+  TuneVal v{4, 1, {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0}};
   const int rps[4] = {2, 4, 8, 16};
   const int nchoice = rp_allowed(16, (int)sizeof(T), stage) ? 4 : 3;
-  for (int i = 0; i < nchoice && !rc; ++i) {
+  for (int ci = 0; ci < 8 && !rc; ++ci) {
+    const int i = ci & 3, mt = 1 + (ci >> 2);
+    if (i >= nchoice) continue;
     LegArgs<T> a = leg_args<T>(P, g, L);
     a.df = 0;
     a.alm = alm;
     a.rp_synth = a.rp_adj = rps[i];
+    a.mt_synth = a.mt_adj = mt;
     FinalizeArgs<T> f;
     f.out = alm;
     auto run = [&]() { return stage == 0 ? launch_leg_synth<T>(a, P->stream) : launch_leg_adjoint<T>(a, f, P->stream); };
@@ -626,13 +633,14 @@ static int tune_stage(cr_plan* P, const Grid& g, int L, int stage, int reps) {
     if (!rc && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
     float ms = 0.f;
     if (!rc && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) rc = cuda_fail(e, "autotune event");
-    v.ms[i] = ms / reps;
+    v.ms[ci] = ms / reps;
   }
   if (!rc) {
     int best = 1;
-    for (int i = 0; i < nchoice; ++i)
-      if (v.ms[i] < v.ms[best]) best = i;
-    v.rp = rps[best];
+    for (int ci = 0; ci < 8; ++ci)
+      if (v.ms[ci] >= 0.0 && v.ms[ci] < v.ms[best]) best = ci;
+    v.rp = rps[best & 3];
+    v.mt = 1 + (best >> 2);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -657,7 +665,7 @@ static int tune_tc_stage(cr_plan* P, const Grid& g, int L, int reps) {
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) rc = cuda_fail(e, "autotune setup");
-  TuneVal v{TC_DEFAULT_VARIANT, {-1.0, -1.0, -1.0, -1.0}};
+  TuneVal v{TC_DEFAULT_VARIANT, 1, {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0}};
   for (int i = 0; i < TC_NVARIANT && !rc; ++i) {
     LegArgs<float> la = leg_args<float>(P, g, L);
     la.tc_variant = i;
@@ -714,7 +722,7 @@ int autotune_plan(cr_plan* P, int reps) {
   return CR_OK;
 }
 
-int tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* bytes, int* stage, int* rp, double* ms) {
+int tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* bytes, int* stage, int* rp, int* mt, double* ms) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (i < 0 || i >= (int)g_tune.size()) return fail(CR_EINVAL, "cr_tune_entry: index out of range");
   auto it = g_tune.begin();
@@ -725,17 +733,19 @@ int tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* bytes, int* sta
   if (bytes) *bytes = it->first.bytes;
   if (stage) *stage = it->first.stage;
   if (rp) *rp = it->second.rp;
+  if (mt) *mt = it->second.mt;
   if (ms)
-    for (int k = 0; k < 4; ++k) ms[k] = it->second.ms[k];
+    for (int k = 0; k < 8; ++k) ms[k] = it->second.ms[k];
   return CR_OK;
 }
 
-int tune_set(int nring, int64_t npix, int lmax, int bytes, int stage, int rp) {
-  const bool tc = bytes == TC_TUNE_BYTES && stage == TC_TUNE_SYNTH && rp >= 0 && rp < TC_NVARIANT;
-  if (!tc && ((bytes != 4 && bytes != 8) || (stage != 0 && stage != 1) || lmax < 0 || !rp_allowed(rp, bytes, stage)))
+int tune_set(int nring, int64_t npix, int lmax, int bytes, int stage, int rp, int mt) {
+  const bool tc = bytes == TC_TUNE_BYTES && stage == TC_TUNE_SYNTH && rp >= 0 && rp < TC_NVARIANT && mt == 1;
+  if (!tc && ((bytes != 4 && bytes != 8) || (stage != 0 && stage != 1) || lmax < 0 || !rp_allowed(rp, bytes, stage) ||
+              (mt != 1 && mt != 2)))
     return fail(CR_EINVAL, "cr_tune_set: bad choice");
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[TuneKey{nring, npix, lmax, bytes, stage}] = TuneVal{rp, {0.0, 0.0, 0.0, -1.0}};
+  g_tune[TuneKey{nring, npix, lmax, bytes, stage}] = TuneVal{rp, mt, {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0}};
   return CR_OK;
 }
 
@@ -895,12 +905,12 @@ int cr_plan_autotune(cr_plan* plan, int* nentries) {
 }
 
 int cr_tune_entry(int i, int* nring, int64_t* npix, int* lmax, int* precision_bytes, int* stage, int* rp,
-                  double* ms) {
-  return tune_entry(i, nring, npix, lmax, precision_bytes, stage, rp, ms);
+                  int* m_tile, double* ms) {
+  return tune_entry(i, nring, npix, lmax, precision_bytes, stage, rp, m_tile, ms);
 }
 
-int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp) {
-  return tune_set(nring, npix, lmax, precision_bytes, stage, rp);
+int cr_tune_set(int nring, int64_t npix, int lmax, int precision_bytes, int stage, int rp, int m_tile) {
+  return tune_set(nring, npix, lmax, precision_bytes, stage, rp, m_tile);
 }
 
 int cr_plan_update_cl(cr_plan* plan, const double* cl) {

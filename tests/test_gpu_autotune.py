@@ -1,7 +1,7 @@
-"""The Legendre autotuner (ring pairs per thread 2, 4, 8 per grid, band
-limit, precision and stage): every choice computes the same transforms (FP64
-within 1e-10 of the oracle, FP32 within 1e-5), and the tuner records a
-measured time for each choice and keeps the fastest."""
+"""The Legendre autotuner (ring pairs per thread 2, 4, 8 and the m tile 1 or
+2 per grid, band limit, precision and stage): every choice computes the same
+transforms (FP64 within 1e-10 of the oracle, FP32 within 1e-5), and the
+tuner records a measured time for each choice and keeps the fastest."""
 import numpy as np
 import pytest
 import torch
@@ -13,17 +13,19 @@ from paper_1308_5299_gb300 import binding, synthetic
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("mt", [1, 2])
 @pytest.mark.parametrize("rp", [2, 4, 8, 16])
-@pytest.mark.parametrize("nside,lmax", [(32, 95), (64, 191), (512, 1023)])
-def test_every_ring_block_choice_matches_oracle(nside, lmax, rp):
+@pytest.mark.parametrize("nside,lmax", [(32, 95), (64, 191), (512, 1023), (64, 128)])
+def test_every_ring_block_choice_matches_oracle(nside, lmax, rp, mt):
     """(16 pairs per thread exists for the FP32 adjoint only; the other
-    stages keep 8 in that case.)"""
+    stages keep 8 in that case.  The m tile pairs m with L - m: odd and even
+    band limits, so that the middle m is paired with itself once.)"""
     dev = cuda_device()
     g = geometry.healpix_grid(nside)
     for prec in ("f32", "f64"):
         for stage in ("synthesis", "adjoint"):
             binding.tune_set(g["nring"], g["npix"], lmax, prec, stage,
-                             rp if (rp < 16 or (prec, stage) == ("f32", "adjoint")) else 8)
+                             rp if (rp < 16 or (prec, stage) == ("f32", "adjoint")) else 8, m_tile=mt)
     plan = binding.Plan(lmax, nside=nside)
     a = synthetic.random_alm(lmax, seed=31)
     mp = synthetic.random_map(g["npix"], seed=32)
@@ -49,8 +51,11 @@ def test_autotune_records_and_keeps_fastest():
     obs = [t for t in table if t["nring"] == g["nring"] and t["lmax"] == lmax and t["precision"] != "bf16"]
     assert len(obs) == 4
     for t in obs:
-        assert all(v > 0 for v in t["ms"].values())
-        assert t["pairs_per_thread"] == min(t["ms"], key=t["ms"].get)
+        assert all(v > 0 for v in t["ms"].values()) and all(v > 0 for v in t["ms_m_tile2"].values())
+        assert sorted(t["ms"]) == sorted(t["ms_m_tile2"])
+        shapes = {(rp, 1): v for rp, v in t["ms"].items()}
+        shapes.update({(rp, 2): v for rp, v in t["ms_m_tile2"].items()})
+        assert (t["pairs_per_thread"], t["m_tile"]) == min(shapes, key=shapes.get)
     tc = [t for t in table if t["nring"] == g["nring"] and t["lmax"] == lmax and t["precision"] == "bf16"]
     assert len(tc) == 1 and sorted(tc[0]["ms"]) == [0, 1, 2]
     assert tc[0]["variant"] == min(tc[0]["ms"], key=tc[0]["ms"].get)
