@@ -71,120 +71,134 @@ __device__ __forceinline__ void bf_dif(C& a, C& b, C w) {
   b = cmul(csub(u, b), w);
 }
 
-// In-place radix-2 decimation-in-time FFT: bit-reversed input, natural output.
-// sign = -1 forward (e^{-2 pi i jk/M}), +1 inverse (unnormalised).  Up to
-// three consecutive stages (spans h, 2h, 4h) run per pass on 8 elements
-// j0 + t h held in registers, one barrier per pass.
-template <typename C>
-__device__ void fft_dit(C* buf, int M, int logM, int sign, const C* __restrict__ tw, int Mmax) {
-  int lh = 0;
-  while (lh < logM) {
-    const int h = 1 << lh;
-    const int ns = min(3, logM - lh);
-    const int ng = M >> ns;
-    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-      const int k = g & (h - 1);
-      const int j0 = ((g - k) << ns) + k;
-      if (ns == 3) {
-        C e[8];
+// e^{-2 pi i v / 32}, v < 16: the constant factors of the twiddles inside
+// one pass (cos and sin of 2 pi v / 32)
+__device__ constexpr double RC32[16] = {1.0, 0.980785280403230449126, 0.923879532511286756128, 0.831469612302545237079,
+                                        0.707106781186547524401, 0.555570233019602224743, 0.382683432365089771728,
+                                        0.195090322016128267848, 0.0, -0.195090322016128267848, -0.382683432365089771728,
+                                        -0.555570233019602224743, -0.707106781186547524401, -0.831469612302545237079,
+                                        -0.923879532511286756128, -0.980785280403230449126};
+__device__ constexpr double RS32[16] = {0.0, 0.195090322016128267848, 0.382683432365089771728, 0.555570233019602224743,
+                                        0.707106781186547524401, 0.831469612302545237079, 0.923879532511286756128,
+                                        0.980785280403230449126, 1.0, 0.980785280403230449126, 0.923879532511286756128,
+                                        0.831469612302545237079, 0.707106781186547524401, 0.555570233019602224743,
+                                        0.382683432365089771728, 0.195090322016128267848};
+
+// One pass of NS consecutive radix-2 stages on groups of 2^NS elements
+// j0 + t h (t < 2^NS) held in registers.  Stage s of the pass has span
+// 2^s h; its butterfly on (t, t + 2^s), u = t mod 2^s, uses the twiddle
+// e^{-+2 pi i (k + u h) / (2^(s+1) h)}.  With CTW (computed twiddles) that
+// is base_s e^{-+2 pi i u / 2^(s+1)}: one table value per stage and group
+// (base_s, index k Mmax / (2^(s+1) h)) times a compile-time root of unity --
+// fewer loads for a few FP32 multiplies; without, every distinct twiddle
+// is a table value (FP64, where a multiply costs more than a cached load).
+// DIT runs the stages with spans h, 2h, ... (bit-reversed input, natural
+// output); DIF the reverse (natural input, bit-reversed output).  post (may
+// be null): every element is multiplied by post[its position] before it is
+// stored (the pointwise product of a convolution, fused into the last pass).
+template <typename C, int NS, bool DIT, bool CTW>
+__device__ __forceinline__ void fft_pass(C* buf, int M, int lh, int sign, const C* __restrict__ tw, int Mmax,
+                                         const C* __restrict__ post) {
+  using T = decltype(C().x);
+  constexpr int R = 1 << NS;
+  const int h = 1 << lh;
+  const int ng = M >> NS;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    const int k = g & (h - 1);
+    const int j0 = ((g - k) << NS) + k;
+    C base[NS];
+    if (CTW) {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) e[t] = buf[swz(j0 + t * h)];
-        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2), s3 = Mmax >> (lh + 3);
-        const C w1 = twid(tw, k * s1, sign);
-        bf_dit(e[0], e[1], w1);
-        bf_dit(e[2], e[3], w1);
-        bf_dit(e[4], e[5], w1);
-        bf_dit(e[6], e[7], w1);
-        const C w2a = twid(tw, k * s2, sign), w2b = twid(tw, (k + h) * s2, sign);
-        bf_dit(e[0], e[2], w2a);
-        bf_dit(e[1], e[3], w2b);
-        bf_dit(e[4], e[6], w2a);
-        bf_dit(e[5], e[7], w2b);
+      for (int s = 0; s < NS; ++s) base[s] = twid(tw, k * (Mmax >> (lh + s + 1)), sign);
+    }
+    C e[R];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) bf_dit(e[t], e[t + 4], twid(tw, (k + t * h) * s3, sign));
+    for (int t = 0; t < R; ++t) e[t] = buf[swz(j0 + t * h)];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) buf[swz(j0 + t * h)] = e[t];
-      } else if (ns == 2) {
-        C e[4];
+    for (int si = 0; si < NS; ++si) {
+      const int s = DIT ? si : NS - 1 - si;
+      const int S = 1 << s;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) e[t] = buf[swz(j0 + t * h)];
-        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2);
-        const C w1 = twid(tw, k * s1, sign);
-        bf_dit(e[0], e[1], w1);
-        bf_dit(e[2], e[3], w1);
-        bf_dit(e[0], e[2], twid(tw, k * s2, sign));
-        bf_dit(e[1], e[3], twid(tw, (k + h) * s2, sign));
-#pragma unroll
-        for (int t = 0; t < 4; ++t) buf[swz(j0 + t * h)] = e[t];
-      } else {
-        C a = buf[swz(j0)], b = buf[swz(j0 + h)];
-        bf_dit(a, b, twid(tw, k * (Mmax >> (lh + 1)), sign));
-        buf[swz(j0)] = a;
-        buf[swz(j0 + h)] = b;
+      for (int t = 0; t < R; ++t) {
+        if (t & S) continue;
+        const int u = t & (S - 1);
+        C w;
+        if (CTW) {
+          w = base[s];
+          if (u) {
+            const int v = u << (4 - s);
+            const T cr = (T)RC32[v], ci = (T)(sign > 0 ? RS32[v] : -RS32[v]);
+            w = mk(w.x * cr - w.y * ci, w.x * ci + w.y * cr);
+          }
+        } else {
+          w = twid(tw, (k + u * h) * (Mmax >> (lh + s + 1)), sign);
+        }
+        if (DIT) bf_dit(e[t], e[t + S], w);
+        else bf_dif(e[t], e[t + S], w);
       }
     }
+    if (post) {
+#pragma unroll
+      for (int t = 0; t < R; ++t) e[t] = cmul(e[t], post[j0 + t * h]);
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) buf[swz(j0 + t * h)] = e[t];
+  }
+}
+
+// BIG: up to 4 stages per pass with computed twiddles (FP32 rings with
+// M >= 4096: fewer barriers and shared-memory round trips, at 75 registers);
+// otherwise up to 3 with table twiddles (fewer registers, so more CTAs per
+// SM, which the small rings need).  Never more stages than leave one group
+// per thread.
+template <bool BIG>
+__device__ __forceinline__ int fft_pass_cap(int logM) {
+  const int lt = 31 - __clz((int)blockDim.x);
+  return max(1, min(BIG ? 4 : 3, logM - lt));
+}
+
+template <typename C, bool DIT, bool BIG>
+__device__ __forceinline__ void fft_pass_ns(int ns, C* buf, int M, int lh, int sign, const C* __restrict__ tw,
+                                            int Mmax, const C* __restrict__ post) {
+  if (BIG && ns == 4) fft_pass<C, 4, DIT, true>(buf, M, lh, sign, tw, Mmax, post);
+  else if (ns >= 3) fft_pass<C, 3, DIT, BIG>(buf, M, lh, sign, tw, Mmax, post);
+  else if (ns == 2) fft_pass<C, 2, DIT, BIG>(buf, M, lh, sign, tw, Mmax, post);
+  else fft_pass<C, 1, DIT, BIG>(buf, M, lh, sign, tw, Mmax, post);
+}
+
+// In-place radix-2 decimation-in-time FFT: bit-reversed input, natural output.
+// sign = -1 forward (e^{-2 pi i jk/M}), +1 inverse (unnormalised).  Passes
+// of several consecutive stages, one barrier per pass.
+template <bool BIG = false, typename C>
+__device__ void fft_dit(C* buf, int M, int logM, int sign, const C* __restrict__ tw, int Mmax) {
+  const int cap = fft_pass_cap<BIG>(logM);
+  int lh = 0;
+  while (lh < logM) {
+    const int ns = min(cap, logM - lh);
+    fft_pass_ns<C, true, BIG>(ns, buf, M, lh, sign, tw, Mmax, nullptr);
     __syncthreads();
     lh += ns;
   }
 }
 
 // In-place radix-2 decimation-in-frequency FFT: natural input, bit-reversed
-// output; passes of up to three stages (spans 4h, 2h, h).
-template <typename C>
-__device__ void fft_dif(C* buf, int M, int logM, int sign, const C* __restrict__ tw, int Mmax) {
+// output; passes of several stages (largest span first).  post (may be
+// null): multiply the output, in its bit-reversed positions, by post.
+template <bool BIG = false, typename C>
+__device__ void fft_dif(C* buf, int M, int logM, int sign, const C* __restrict__ tw, int Mmax,
+                        const C* __restrict__ post = nullptr) {
+  const int cap = fft_pass_cap<BIG>(logM);
   int lt = logM;  // stages with span >= 2^lt are done
   while (lt > 0) {
-    const int ns = min(3, lt);
+    const int ns = min(cap, lt);
     const int lh = lt - ns;  // smallest span of this pass
-    const int h = 1 << lh;
-    const int ng = M >> ns;
-    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-      const int k = g & (h - 1);
-      const int j0 = ((g - k) << ns) + k;
-      if (ns == 3) {
-        C e[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) e[t] = buf[swz(j0 + t * h)];
-        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2), s3 = Mmax >> (lh + 3);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) bf_dif(e[t], e[t + 4], twid(tw, (k + t * h) * s3, sign));
-        const C w2a = twid(tw, k * s2, sign), w2b = twid(tw, (k + h) * s2, sign);
-        bf_dif(e[0], e[2], w2a);
-        bf_dif(e[1], e[3], w2b);
-        bf_dif(e[4], e[6], w2a);
-        bf_dif(e[5], e[7], w2b);
-        const C w1 = twid(tw, k * s1, sign);
-        bf_dif(e[0], e[1], w1);
-        bf_dif(e[2], e[3], w1);
-        bf_dif(e[4], e[5], w1);
-        bf_dif(e[6], e[7], w1);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) buf[swz(j0 + t * h)] = e[t];
-      } else if (ns == 2) {
-        C e[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) e[t] = buf[swz(j0 + t * h)];
-        const int s1 = Mmax >> (lh + 1), s2 = Mmax >> (lh + 2);
-        bf_dif(e[0], e[2], twid(tw, k * s2, sign));
-        bf_dif(e[1], e[3], twid(tw, (k + h) * s2, sign));
-        const C w1 = twid(tw, k * s1, sign);
-        bf_dif(e[0], e[1], w1);
-        bf_dif(e[2], e[3], w1);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) buf[swz(j0 + t * h)] = e[t];
-      } else {
-        C a = buf[swz(j0)], b = buf[swz(j0 + h)];
-        bf_dif(a, b, twid(tw, k * (Mmax >> (lh + 1)), sign));
-        buf[swz(j0)] = a;
-        buf[swz(j0 + h)] = b;
-      }
-    }
+    fft_pass_ns<C, false, BIG>(ns, buf, M, lh, sign, tw, Mmax, lh == 0 ? post : nullptr);
     __syncthreads();
     lt = lh;
   }
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool BIG>
 __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
   using C = typename Tr<T>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -276,26 +290,23 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
       for (int k = nh + tid; k < M; k += NT) buf[swz(k)] = mk((T)0, (T)0);
     __syncthreads();
     if (!f.bluestein) {
-      fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
+      fft_dit<BIG>(buf, M, lg, +1, a.tw, a.Mmax);
     } else {
-      fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
-      for (int i = tid; i < M; i += NT) buf[swz(i)] = cmul(buf[swz(i)], vh[i]);
-      __syncthreads();
-      fft_dit(buf, M, lg, +1, a.tw, a.Mmax);
-      for (int t = tid; t < nh; t += NT) buf[swz(t)] = cmul(buf[swz(t)], chirp(t));
-      __syncthreads();
+      fft_dif<BIG>(buf, M, lg, -1, a.tw, a.Mmax, vh);  // times the kernel spectrum
+      fft_dit<BIG>(buf, M, lg, +1, a.tw, a.Mmax);
     }
-    // buf[t] = z_t = (map_{2t}, map_{2t+1})
+    // z_t = (map_{2t}, map_{2t+1}) = buf[t] (times the chirp for Bluestein rings)
+    auto z_of = [&](int t) -> C { return f.bluestein ? cmul(buf[swz(t)], chirp(t)) : buf[swz(t)]; };
     if (MODE == 0) {
       C* out = reinterpret_cast<C*>(a.map_out + f.off);
-      for (int t = tid; t < nh; t += NT) out[t] = buf[swz(t)];
+      for (int t = tid; t < nh; t += NT) out[t] = z_of(t);
       return;
     }
     // MODE 2: multiply by the pixel diagonal and continue with the adjoint.
     const C* dg = reinterpret_cast<const C*>(a.pixdiag + f.off);
     C* mo = a.map_out ? reinterpret_cast<C*>(a.map_out + f.off) : nullptr;
     for (int t = tid; t < nh; t += NT) {
-      C z = buf[swz(t)];
+      C z = z_of(t);
       if (mo) mo[t] = z;
       const C d = dg[t];
       z.x *= d.x;
@@ -318,12 +329,10 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
 
   // forward length-nh DFT of z_t = y_{2t} + i y_{2t+1}
   if (!f.bluestein) {
-    fft_dif(buf, M, lg, -1, a.tw, a.Mmax);  // Z'_k at buf[bitrev(k)]
+    fft_dif<BIG>(buf, M, lg, -1, a.tw, a.Mmax);  // Z'_k at buf[bitrev(k)]
   } else {
-    fft_dif(buf, M, lg, -1, a.tw, a.Mmax);
-    for (int i = tid; i < M; i += NT) buf[swz(i)] = cmul(buf[swz(i)], vh[i]);
-    __syncthreads();
-    fft_dit(buf, M, lg, +1, a.tw, a.Mmax);  // Z'_k = conj(buf[k] chirp(k))
+    fft_dif<BIG>(buf, M, lg, -1, a.tw, a.Mmax, vh);  // times the kernel spectrum
+    fft_dit<BIG>(buf, M, lg, +1, a.tw, a.Mmax);      // Z'_k = conj(buf[k] chirp(k))
   }
   auto getZ = [&](int k) -> C {
     return f.bluestein ? cconj(cmul(buf[swz(k)], chirp(k))) : buf[swz(bitrev(k, lg))];
@@ -345,6 +354,25 @@ __global__ void __launch_bounds__(RF_NT) ring_fft_kernel(RingArgs<T> a) {
   }
 }
 
+template <typename T, bool BIG>
+static int ring_fft_launch(const RingArgs<T>& b, int mode, int cnt, int nt, size_t smem, cudaStream_t st) {
+  switch (mode) {
+    case 0:
+      CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 0, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      { ring_fft_kernel<T, 0, BIG><<<cnt, nt, smem, st>>>(b); count_launch(); }
+      break;
+    case 1:
+      CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 1, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      { ring_fft_kernel<T, 1, BIG><<<cnt, nt, smem, st>>>(b); count_launch(); }
+      break;
+    default:
+      CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 2, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      { ring_fft_kernel<T, 2, BIG><<<cnt, nt, smem, st>>>(b); count_launch(); }
+      break;
+  }
+  return CR_OK;
+}
+
 // One launch per FFT-size class (rings ordered by their FFT size M), each
 // with the shared memory and block size its rings need.
 template <typename T>
@@ -360,20 +388,14 @@ int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st) {
     const int nt = std::max(128, std::min(RF_NT, M / 8));
     RingArgs<T> b = a;
     b.rbase = a.cls_start[c];
-    switch (mode) {
-      case 0:
-        CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        { ring_fft_kernel<T, 0><<<cnt, nt, smem, st>>>(b); count_launch(); }
-        break;
-      case 1:
-        CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        { ring_fft_kernel<T, 1><<<cnt, nt, smem, st>>>(b); count_launch(); }
-        break;
-      default:
-        CR_CUDA(cudaFuncSetAttribute(ring_fft_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        { ring_fft_kernel<T, 2><<<cnt, nt, smem, st>>>(b); count_launch(); }
-        break;
-    }
+    // FP32 rings with M >= 4096: the 4-stage passes with computed twiddles
+    int rc;
+    if constexpr (sizeof(T) == 4)
+      rc = M >= 4096 ? ring_fft_launch<T, true>(b, mode, cnt, nt, smem, st)
+                     : ring_fft_launch<T, false>(b, mode, cnt, nt, smem, st);
+    else
+      rc = ring_fft_launch<T, false>(b, mode, cnt, nt, smem, st);
+    if (rc) return rc;
     CR_CHECK_LAUNCH("ring_fft_kernel");
   }
   return CR_OK;
