@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
     T P1[RP], P2[RP], zz[RP];
     int ls[RP], p[RP];
     C accE[RP], accO[RP];
-  #pragma unroll
+#pragma unroll
     for (int j = 0; j < RP; ++j) {
       accE[j] = mk((T)0, (T)0);
       accO[j] = mk((T)0, (T)0);
@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
         const int ng = min(8, nl - i8);
         if (wmin >= lg + ng) continue;  // no pair of the warp has started
         if (wmax <= lg && ng == 8) {
-  #pragma unroll
+#pragma unroll
           for (int u = 0; u < 8; u += 2) {
             const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
             const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
             const C a0 = sa[i8 + u], a1 = sa[i8 + u + 1];
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < RP; ++j) {
               const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
               const T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
             const T c0 = sc[i8 + u];
             const T d0 = POLAR ? sc2[i8 + u] : (T)0;
             const C a0 = sa[i8 + u];
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < RP; ++j) {
               if (l >= ls[j]) {
                 const T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_synth_kernel(LegArgs<T> a, int nbp
       }
     }
     const int pend = POLAR ? a.npolar : a.npairs;
-  #pragma unroll
+#pragma unroll
     for (int j = 0; j < RP; ++j) {
       if (p[j] < pend) {
         const int rn = p[j], rs = a.nring - 1 - p[j];
@@ -371,14 +371,14 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
     float P1[RP], P2[RP], zz[RP];
     int ls[RP], p[RP];
     float ex[RP], ey[RP], ox[RP], oy[RP];
-  #pragma unroll
+#pragma unroll
     for (int j = 0; j < RP; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
     const int yb = (int)blockIdx.x + yoff;
     int wmin, wmax;
     const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
     auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
     if (!POLAR) {
-  #pragma unroll
+#pragma unroll
       for (int j = 0; j < RP; ++j)
         if (ls[j] <= L) {
           P1[j] *= sgn(ls[j] - 1);
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
         if (wmin >= lg + ng) continue;  // no pair of the warp has started
         if (wmax <= lg && ng == 8) {
           u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
-  #pragma unroll
+#pragma unroll
           for (int q = 0; q < NP; ++q) {
             Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
             S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
@@ -429,12 +429,12 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
             OX[q] = pk2(ox[2 * q], ox[2 * q + 1]);
             OY[q] = pk2(oy[2 * q], oy[2 * q + 1]);
           }
-  #pragma unroll
+#pragma unroll
           for (int u = 0; u < 8; ++u) {
             const u64 K = lds2(&sk[i8 + u]);
             const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
             const u64 AX = lds2(&sax[i8 + u]), AY = lds2(&say[i8 + u]);
-  #pragma unroll
+#pragma unroll
             for (int q = 0; q < NP; ++q) {
               u64 Q;
               if (POLAR) {
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
               }
             }
           }
-  #pragma unroll
+#pragma unroll
           for (int q = 0; q < NP; ++q) {
             upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
             upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
             const float K = sk[i8 + u].x;
             const float K2 = POLAR ? sk2[i8 + u].x : 0.f;
             const float ax = sax[i8 + u].x, ay = say[i8 + u].x;
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < RP; ++j) {
               if (l >= ls[j]) {
                 float q;
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> 
       }
     }
     const int pend = POLAR ? a.npolar : a.npairs;
-  #pragma unroll
+#pragma unroll
     for (int j = 0; j < RP; ++j) {
       if (p[j] < pend) {
         const int rn = p[j], rs = a.nring - 1 - p[j];
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
     int wmin, wmax;
     const bool live = load_pairs<T, POLAR, RP>(a, m, yb, nbp, warp, lane, p, ls, P1, P2, zz, &wmin, &wmax);
     const int pend = POLAR ? a.npolar : a.npairs;
-  #pragma unroll
+#pragma unroll
     for (int j = 0; j < RP; ++j) {
       GE[j] = mk((T)0, (T)0);
       GO[j] = mk((T)0, (T)0);
@@ -593,14 +593,14 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
           if (lane < 8) red[warp][i8 + lane] = mk((T)0, (T)0);
         } else {
           C acc[8];
-  #pragma unroll
+#pragma unroll
           for (int u = 0; u < 8; ++u) acc[u] = mk((T)0, (T)0);
           if (wmax <= lg && ng == 8) {
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < 8; u += 2) {
               const T c0 = sc[i8 + u], c1 = sc[i8 + u + 1];
               const T d0 = POLAR ? sc2[i8 + u] : (T)0, d1 = POLAR ? sc2[i8 + u + 1] : (T)0;
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < RP; ++j) {
                 T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
                 T q1 = rstep<T, POLAR>(c1, d1, zz[j], P1[j], P2[j]);
@@ -615,13 +615,13 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
               }
             }
           } else {
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < 8; ++u) {
               if (u < ng) {
                 const int l = lg + u;
                 const T c0 = sc[i8 + u];
                 const T d0 = POLAR ? sc2[i8 + u] : (T)0;
-  #pragma unroll
+#pragma unroll
                 for (int j = 0; j < RP; ++j) {
                   if (l >= ls[j]) {
                     T q0 = rstep<T, POLAR>(c0, d0, zz[j], P1[j], P2[j]);
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
       for (int i = tid; i < nl; i += LEG_NT) {
         const int l = l0 + i;
         C sum = red[0][i];
-  #pragma unroll
+#pragma unroll
         for (int w = 1; w < LEG_NW; ++w) sum = cadd(sum, red[w][i]);
         const T sc_ = a.s[offc + (l - m)];
         part[offa + (l - m)] = cscale(sum, SQ ? sc_ * sc_ : sc_);
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
     const bool live = load_pairs<float, POLAR, RP, L32_NT>(a, m, yb, nbp, 0, lane, p, ls, P1, P2, zz, &wmin, &wmax);
     auto sgn = [&](int l) -> float { return ((l - m) & 2) ? -1.f : 1.f; };
     const int pend = POLAR ? a.npolar : a.npairs;
-  #pragma unroll
+#pragma unroll
     for (int j = 0; j < RP; ++j) {
       GE[j] = make_float2(0.f, 0.f);
       GO[j] = make_float2(0.f, 0.f);
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
         float2 acc[8];
         if (wmax <= lg && ng == 8) {
           u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
-  #pragma unroll
+#pragma unroll
           for (int q = 0; q < NP; ++q) {
             Z[q] = pk2(zz[2 * q], zz[2 * q + 1]);
             S1[q] = pk2(P1[2 * q], P1[2 * q + 1]);
@@ -743,12 +743,12 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
             OX[q] = pk2(GO[2 * q].x, GO[2 * q + 1].x);
             OY[q] = pk2(GO[2 * q].y, GO[2 * q + 1].y);
           }
-  #pragma unroll
+#pragma unroll
           for (int u = 0; u < 8; ++u) {
             const u64 K = lds2(&sk[i8 + u]);
             const u64 K2 = POLAR ? lds2(&sk2[i8 + u]) : 0ull;
             u64 AX = 0ull, AY = 0ull;
-  #pragma unroll
+#pragma unroll
             for (int q = 0; q < NP; ++q) {
               u64 Q;
               if (POLAR) {
@@ -774,21 +774,21 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
             upk2(AY, y0, y1);
             acc[u] = make_float2(x0 + x1, y0 + y1);
           }
-  #pragma unroll
+#pragma unroll
           for (int q = 0; q < NP; ++q) {
             upk2(S1[q], P1[2 * q], P1[2 * q + 1]);
             upk2(S2[q], P2[2 * q], P2[2 * q + 1]);
           }
         } else {
-  #pragma unroll
+#pragma unroll
           for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
-  #pragma unroll
+#pragma unroll
           for (int u = 0; u < 8; ++u) {
             if (u < ng) {
               const int l = lg + u;
               const float K = sk[i8 + u].x;
               const float K2 = POLAR ? sk2[i8 + u].x : 0.f;
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < RP; ++j) {
                 if (l >= ls[j]) {
                   float q;
