@@ -177,7 +177,7 @@ typedef struct cr_params {
    * quadrature-weighted map w_j (sum_{L<=2 lmax_h} xi_LM Y_LM)(n_j),
    * xi = Y_obs^T n: the same operator (exact by the Gaunt expansion, up to
    * rounding) at O(lmax_h^3) cost.  0 = on for levels whose GL grid has at
-   * most half the observation grid's rings, 1 = on for every pixel level,
+   * most 3/5 of the observation grid's rings, 1 = on for every pixel level,
    * -1 = off. */
   int gl_downgrade;
   /* fp64_df: 1 = evaluate the FP64 Legendre stages (FP64 transforms, FP64

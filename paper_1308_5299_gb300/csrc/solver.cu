@@ -424,7 +424,10 @@ int build_hierarchy(cr_plan* P, const cr_params* p) {
     int Lneed = P->Lcoef;
     for (int i = 0; i < H.H; ++i) {
       const int Lh = specs[i].lmax_h;
-      use_gl[i] = p->gl_downgrade > 0 || (p->gl_downgrade == 0 && 2 * Lh + 1 <= P->obs.nring / 2);
+      // automatic: where the GL grid has at most 3/5 of the observation
+      // grid's rings (the Legendre stages cost in proportion to the rings;
+      // the GL grid's power-of-two rings need no Bluestein FFTs)
+      use_gl[i] = p->gl_downgrade > 0 || (p->gl_downgrade == 0 && 5 * (2 * Lh + 1) <= 3 * P->obs.nring);
       if (use_gl[i]) Lneed = std::max(Lneed, 2 * Lh);
     }
     const bool recoef = Lneed > P->Lcoef, reseed = Lneed > P->obs.Lseed;
