@@ -491,6 +491,15 @@ int cr_prolong_add(cr_plan* plan, int h, const void* c_H, void* x_h, int dtype);
  * pixel-correction-1..3), or the additive Schwarz smoother of the plan
  * option `smoother`.  c is overwritten. */
 int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype);
+/* map_out = M_h map_in for nrhs maps (1 <= nrhs <= 16) of pixel level h >= 1:
+ * the pixel-space smoother of Section 3.5 (Eqs. pixel-correction-2, the
+ * block incomplete-Cholesky solve L^-T L^-1 in the tiles' elimination
+ * order, or the additive Schwarz form).  map_in, map_out: DEVICE
+ * [nrhs][12 nside_h^2], RING order of the level's grid, FP32 or FP64 (the
+ * factor is FP32).  With several maps every factor block is read once for
+ * all of them (the form the batched cycles use).  Errors: CR_EINVAL,
+ * CR_ESTATE, CR_ECUDA. */
+int cr_pixel_smoother(cr_plan* plan, int h, const void* map_in, void* map_out, int nrhs, int dtype);
 /* x = A_bottom^-1 b on the bottom level (l <= lmax_dense), dense (FP64). */
 int cr_bottom_solve(cr_plan* plan, const void* b, void* x, int dtype);
 /* The assembled real-basis matrix of the bottom level (before factorising):

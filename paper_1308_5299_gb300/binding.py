@@ -134,6 +134,8 @@ _SIGS = {
     "cr_restrict": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_prolong_add": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_smooth": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "cr_pixel_smoother": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+                          ctypes.c_int),
     "cr_bottom_solve": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "cr_bottom_matrix": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
                          ctypes.c_int),
@@ -548,6 +550,13 @@ class Plan:
 
     def smooth(self, h, r, out):
         _check(lib().cr_smooth(self._h, h, _dev(r), _dev(out), _dtype_code(r)))
+        return out
+
+    def pixel_smoother(self, h, maps, out):
+        """out = M_h maps (``cr_pixel_smoother``): the pixel-space smoother
+        of level h on 1-16 maps [nrhs][12 nside_h^2] (RING order)."""
+        nrhs = 1 if maps.dim() == 1 else maps.shape[0]
+        _check(lib().cr_pixel_smoother(self._h, h, _dev(maps), _dev(out), nrhs, _dtype_code(maps)))
         return out
 
     def bottom_solve(self, b, out):

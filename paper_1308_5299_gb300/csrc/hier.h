@@ -132,6 +132,12 @@ struct Hierarchy {
   std::vector<double> ridge_fixed;  // given ridges per pixel level, or empty
   bool numeric_ready = false;       // smoothers, top diagonal and bottom built
   int smoother_kind = 0;            // 0 multicolour block ICC(0), 1 additive Schwarz (block Jacobi)
+  // batch buffers of the many-map pixel smoother (smoother.cu): tile work
+  // vectors and two map panels of 16 x the largest level, made on first use
+  float* d_mr_y = nullptr;
+  float* d_mr_m1 = nullptr;
+  float* d_mr_m2 = nullptr;
+  int64_t mr_y_len = 0;
   int sweep_mode = 0;               // ICC(0) sweeps: 0 auto, 1 one launch per colour, 2 cooperative
 };
 

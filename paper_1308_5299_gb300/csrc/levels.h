@@ -37,6 +37,9 @@ int smoother_structure(cr_plan* P, PixLevel& lev);
 int smoother_numeric(cr_plan* P, PixLevel& lev, double ridge_factor, int bisections, double fixed_alpha);
 int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok);
 template <typename T> int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out);
+template <typename T>
+int apply_smoother_mr(cr_plan* P, PixLevel& lev, int nr, const T* map_in, T* map_out, int64_t ld);
+int ensure_smoother_batch(cr_plan* P);
 int sweep_status(cr_plan* P);
 void free_smoother(PixLevel& lev);
 

@@ -827,6 +827,120 @@ __device__ __forceinline__ void sweep_flow_consumers(const SweepArgs& a, const T
   }
 }
 
+// ---------------------------------------------------------------------------
+// The triangular sweeps for up to SM_NR right-hand sides at once (the
+// batched cycles): every factor block is read once from HBM for all of them
+// and multiplied into a 64 x nr panel of vectors -- the fine levels' sweeps,
+// HBM-bound for one right-hand side, become a small dense product per block.
+// One CTA of 256 threads per tile of a colour: thread (i, g) = (tid & 63,
+// tid >> 6) owns row i of right-hand sides 4 g .. 4 g + 3; the block is staged
+// in shared memory (coalesced float4 loads) and read by column, the panel of
+// the neighbours' vectors is kept transposed [k][j][r] (rows padded to 17, so
+// the coalesced global reads along j store without bank conflicts) and read
+// as broadcasts.  y: [SM_NR][ntile * 64] at stride ly; maps at stride ld.
+constexpr int SM_NR = 16;
+constexpr int MR_NT = 256;
+constexpr int SM_VP = SM_NR + 1;  // padded panel row
+constexpr size_t SM_SMEM = (size_t)(TK * TK + 8 * TK * SM_VP + TK * SM_VP) * sizeof(float);
+
+__device__ __forceinline__ void mr_stage_block(float* Bs, const float* __restrict__ B) {
+  const float4* B4 = reinterpret_cast<const float4*>(B);
+  float4* S4 = reinterpret_cast<float4*>(Bs);
+#pragma unroll
+  for (int e = threadIdx.x; e < TK * TK / 4; e += MR_NT) S4[e] = __ldg(B4 + e);
+}
+
+// acc[c] += sum_j B(i, j) V[j][4 g + c] with B column-major in Bs
+__device__ __forceinline__ void mr_block_panel(const float* Bs, const float* V, int i, int g, float acc[4]) {
+#pragma unroll 8
+  for (int j = 0; j < TK; ++j) {
+    const float b = Bs[j * TK + i];
+    const float* v = V + j * SM_VP + 4 * g;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = fmaf(b, v[c], acc[c]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MR_NT) fwd_colour_mr_kernel(const float* L, const int64_t* row_ptr,
+                                                             const int* row_col, const int* perm, const T* map_in,
+                                                             int64_t ld, float* y, int64_t ly, int nr, int p0) {
+  extern __shared__ __align__(16) float mr_smem[];
+  float* Bs = mr_smem;
+  float* vs = Bs + TK * TK;       // [8][TK][SM_VP]
+  float* ts = vs + 8 * TK * SM_VP;  // [TK][SM_VP]
+  const int p = p0 + blockIdx.x;
+  const int tid = threadIdx.x, i = tid & (TK - 1), g = tid >> 6;
+  const int64_t b0 = row_ptr[p];
+  const int nb = (int)(row_ptr[p + 1] - 1 - b0);
+  for (int e = tid; e < nb * SM_NR * TK; e += MR_NT) {
+    const int j = e & (TK - 1), r = (e >> 6) & (SM_NR - 1), k = e >> 10;
+    vs[(k * TK + j) * SM_VP + r] = r < nr ? y[r * ly + (int64_t)row_col[b0 + k] * TK + j] : 0.f;
+  }
+  const int pix = perm[(int64_t)p * TK + i];
+  float rin[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) rin[c] = (4 * g + c < nr) ? (float)map_in[(4 * g + c) * ld + pix] : 0.f;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < nb; ++k) {
+    mr_stage_block(Bs, L + (b0 + k) * TK * TK);
+    __syncthreads();  // also publishes the panel on the first pass
+    mr_block_panel(Bs, vs + k * TK * SM_VP, i, g, acc);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) ts[i * SM_VP + 4 * g + c] = rin[c] - acc[c];
+  mr_stage_block(Bs, L + (b0 + nb) * TK * TK);
+  __syncthreads();
+  float out[4] = {0.f, 0.f, 0.f, 0.f};
+  mr_block_panel(Bs, ts, i, g, out);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    if (4 * g + c < nr) y[(4 * g + c) * ly + (int64_t)p * TK + i] = out[c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MR_NT) bwd_colour_mr_kernel(const float* LT, const int64_t* col_ptr,
+                                                             const int* col_row, const int* perm, float* y,
+                                                             int64_t ly, T* map_out, int64_t ld, int nr, int p0) {
+  extern __shared__ __align__(16) float mr_smem[];
+  float* Bs = mr_smem;
+  float* vs = Bs + TK * TK;
+  float* ts = vs + 8 * TK * SM_VP;
+  const int p = p0 + blockIdx.x;
+  const int tid = threadIdx.x, i = tid & (TK - 1), g = tid >> 6;
+  const int64_t c0 = col_ptr[p];
+  const int nc = (int)(col_ptr[p + 1] - c0);
+  for (int e = tid; e < nc * SM_NR * TK; e += MR_NT) {
+    const int j = e & (TK - 1), r = (e >> 6) & (SM_NR - 1), k = e >> 10;
+    vs[(k * TK + j) * SM_VP + r] = r < nr ? y[r * ly + (int64_t)col_row[c0 + k] * TK + j] : 0.f;
+  }
+  float tin[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) tin[c] = (4 * g + c < nr) ? y[(4 * g + c) * ly + (int64_t)p * TK + i] : 0.f;
+  const float* Lp = LT + (c0 + p) * TK * TK;  // column p's transposed blocks, then inv(L_pp)^T
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < nc; ++k) {
+    mr_stage_block(Bs, Lp + (int64_t)k * TK * TK);
+    __syncthreads();
+    mr_block_panel(Bs, vs + k * TK * SM_VP, i, g, acc);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) ts[i * SM_VP + 4 * g + c] = tin[c] - acc[c];
+  mr_stage_block(Bs, Lp + (int64_t)nc * TK * TK);
+  __syncthreads();
+  float out[4] = {0.f, 0.f, 0.f, 0.f};
+  mr_block_panel(Bs, ts, i, g, out);
+  const int pix = perm[(int64_t)p * TK + i];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    if (4 * g + c < nr) {
+      y[(4 * g + c) * ly + (int64_t)p * TK + i] = out[c];
+      map_out[(4 * g + c) * ld + pix] = (T)out[c];
+    }
+}
+
 // LT[col_ptr[p] + p + k] = (block (col_row[..], p))^T for column p's entries,
 // then LT[col_ptr[p + 1] + p] = (inv(L_pp))^T; one CTA per position p.
 __global__ void transpose_blocks_kernel(const float* L, const int64_t* row_ptr, const int64_t* col_ptr,
@@ -982,7 +1096,7 @@ int factorise(cr_plan* P, PixLevel& lev, float alpha, bool* ok) {
   lev.lt_valid = false;
   for (size_t c = 0; c + 1 < pat.colour_start.size(); ++c) {
     const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
-    if (p1 > p0) { icc_colour_kernel<<<p1 - p0, SM_NT, smem, P->stream>>>(a, p0); count_launch(); }
+    if (p1 > p0) { icc_colour_kernel<<<p1 - p0, MR_NT, smem, P->stream>>>(a, p0); count_launch(); }
   }
   CR_CHECK_LAUNCH("icc_colour_kernel");
   int fail = 0;
@@ -1247,7 +1361,7 @@ int smoother_numeric(cr_plan* P, PixLevel& lev, double ridge_factor, int bisecti
       ab.blk_q = sb.d_blk_q + b0;
       ab.cobs_ptr = sb.d_cobs_ptr + b0;
       ab.A = out + b0 * TK * TK;
-      { assemble_kernel<<<nb, SM_NT, 0, P->stream>>>(ab); count_launch(); }
+      { assemble_kernel<<<nb, MR_NT, 0, P->stream>>>(ab); count_launch(); }
     }
   };
   // the inverse-noise term B_h Y^T N^-1 Y B_h (observation-dependent) is
@@ -1307,6 +1421,18 @@ int smoother_numeric(cr_plan* P, PixLevel& lev, double ridge_factor, int bisecti
   return CR_OK;
 }
 
+// the backward sweep's transposed copy of the factor, made on first use
+static int ensure_lt(cr_plan* P, PixLevel& lev) {
+  if (lev.lt_valid) return CR_OK;
+  const BlockPattern& pat = lev.pat;
+  if (!lev.d_LT) CR_CUDA(cudaMalloc(&lev.d_LT, (size_t)pat.nblocks * TK * TK * sizeof(float)));
+  { transpose_blocks_kernel<<<pat.ntile, 256, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_col_ptr, lev.d_col_blk,
+                                                                lev.d_LT); count_launch(); }
+  CR_CHECK_LAUNCH("transpose_blocks_kernel");
+  lev.lt_valid = true;
+  return CR_OK;
+}
+
 template <typename T>
 int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
   const BlockPattern& pat = lev.pat;
@@ -1315,13 +1441,8 @@ int apply_smoother(cr_plan* P, PixLevel& lev, T* map_in, T* map_out) {
     CR_CHECK_LAUNCH("schwarz_apply_kernel");
     return CR_OK;
   }
-  if (!lev.lt_valid) {
-    if (!lev.d_LT) CR_CUDA(cudaMalloc(&lev.d_LT, (size_t)pat.nblocks * TK * TK * sizeof(float)));
-    { transpose_blocks_kernel<<<pat.ntile, 256, 0, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_col_ptr, lev.d_col_blk,
-                                                                  lev.d_LT); count_launch(); }
-    CR_CHECK_LAUNCH("transpose_blocks_kernel");
-    lev.lt_valid = true;
-  }
+  int rc = ensure_lt(P, lev);
+  if (rc) return rc;
   float* y = reinterpret_cast<float*>(P->hier_tile_work);
   const int nc = (int)pat.colour_start.size() - 1;
   if (lev.coop_grid > 0) {
@@ -1392,6 +1513,68 @@ int sweep_status(cr_plan* P) {
 
 template int apply_smoother<double>(cr_plan*, PixLevel&, double*, double*);
 template int apply_smoother<float>(cr_plan*, PixLevel&, float*, float*);
+
+// The pixel smoother of one level for nr <= SM_NR maps at once (map_in,
+// map_out: [nr][npix_h] at stride ld): the ICC(0) sweeps with every factor
+// block read once for all maps; the Schwarz form, and a single map, take
+// the one-map path per map.  The tile work vectors of the batch live in
+// the hierarchy's batch buffer (ensure_smoother_batch).
+template <typename T>
+int apply_smoother_mr(cr_plan* P, PixLevel& lev, int nr, const T* map_in, T* map_out, int64_t ld) {
+  if (nr < 1 || nr > SM_NR) return fail(CR_EINVAL, "pixel smoother: 1 to 16 maps per call");
+  Hierarchy& H = *P->hier;
+  if (H.smoother_kind == 1 || nr == 1) {
+    for (int r = 0; r < nr; ++r) {
+      int rc = apply_smoother<T>(P, lev, const_cast<T*>(map_in) + r * ld, map_out + r * ld);
+      if (rc) return rc;
+    }
+    return CR_OK;
+  }
+  const BlockPattern& pat = lev.pat;
+  const int64_t ly = (int64_t)pat.ntile * TK;
+  if (!H.d_mr_y || H.mr_y_len < ly) return fail(CR_ESTATE, "pixel smoother: batch buffer missing");
+  int rc = ensure_lt(P, lev);
+  if (rc) return rc;
+  CR_CUDA(cudaFuncSetAttribute(fwd_colour_mr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_SMEM));
+  CR_CUDA(cudaFuncSetAttribute(bwd_colour_mr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_SMEM));
+  float* y = H.d_mr_y;
+  const int nc = (int)pat.colour_start.size() - 1;
+  for (int c = 0; c < nc; ++c) {
+    const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
+    if (p1 <= p0) continue;
+    { fwd_colour_mr_kernel<T><<<p1 - p0, MR_NT, SM_SMEM, P->stream>>>(lev.d_L, lev.d_row_ptr, lev.d_row_col,
+                                                                     lev.d_perm, map_in, ld, y, ly, nr, p0); count_launch(); }
+  }
+  CR_CHECK_LAUNCH("fwd_colour_mr_kernel");
+  for (int c = nc - 1; c >= 0; --c) {
+    const int p0 = pat.colour_start[c], p1 = pat.colour_start[c + 1];
+    if (p1 <= p0) continue;
+    { bwd_colour_mr_kernel<T><<<p1 - p0, MR_NT, SM_SMEM, P->stream>>>(lev.d_LT, lev.d_col_ptr, lev.d_col_row,
+                                                                     lev.d_perm, y, ly, map_out, ld, nr, p0); count_launch(); }
+  }
+  CR_CHECK_LAUNCH("bwd_colour_mr_kernel");
+  return CR_OK;
+}
+template int apply_smoother_mr<double>(cr_plan*, PixLevel&, int, const double*, double*, int64_t);
+template int apply_smoother_mr<float>(cr_plan*, PixLevel&, int, const float*, float*, int64_t);
+
+// batch buffers of the many-map smoother: tile work vectors and two map
+// panels, SM_NR x the largest level
+int ensure_smoother_batch(cr_plan* P) {
+  Hierarchy& H = *P->hier;
+  int64_t need = 0;
+  for (const PixLevel& lev : H.pix) need = std::max(need, (int64_t)lev.pat.ntile * TK);
+  if (H.d_mr_y && H.mr_y_len >= need) return CR_OK;
+  void* q[] = {H.d_mr_y, H.d_mr_m1, H.d_mr_m2};
+  for (void* x : q)
+    if (x) cudaFree(x);
+  H.d_mr_y = H.d_mr_m1 = H.d_mr_m2 = nullptr;
+  CR_CUDA(cudaMalloc(&H.d_mr_y, (size_t)SM_NR * need * sizeof(float)));
+  CR_CUDA(cudaMalloc(&H.d_mr_m1, (size_t)SM_NR * need * sizeof(float)));
+  CR_CUDA(cudaMalloc(&H.d_mr_m2, (size_t)SM_NR * need * sizeof(float)));
+  H.mr_y_len = need;
+  return CR_OK;
+}
 
 void free_smoother(PixLevel& lev) {
   delete lev.sb;

@@ -142,6 +142,8 @@ static int cycle(cr_plan* P, int h, void* x, const void* b, bool x_zero, const v
 
 static int ensure_tc_work(cr_plan* P) {
   Hierarchy& H = *P->hier;
+  int rc = ensure_smoother_batch(P);
+  if (rc) return rc;
   if ((int)H.tcw.size() == H.H + 2) return CR_OK;
   H.tcw.assign(H.H + 2, Hierarchy::TcWork());
   for (int h = 0; h <= H.H + 1; ++h) {
@@ -198,7 +200,18 @@ static int smooth_add_tc(cr_plan* P, int h, int nr, float2* X, const float2* R) 
   float* m2 = reinterpret_cast<float*>(H.map_work2);
   int rc = tc_begin(P, g, L, true, false);
   if (!rc) rc = tc_synth_stage(P, g, L, R, nr, nullptr);
-  for (int r = 0; r < nr && !rc; ++r) {
+  if (!rc && H.smoother_kind == 0 && nr > 1) {
+    // every right-hand side's map, then the sweeps for all of them at once
+    const int64_t np = g.npix;
+    for (int r = 0; r < nr && !rc; ++r) rc = tc_ring(P, g, L, r, 0, nullptr, H.d_mr_m1 + r * np);
+    if (!rc) {
+      const double bytes = 2.0 * lev.pat.nblocks * 64.0 * 64.0 * sizeof(float);
+      TimerScope ts(P->timing, P->stream, "pixel_smoother", bytes);
+      rc = apply_smoother_mr<float>(P, lev, nr, H.d_mr_m1, H.d_mr_m2, np);
+    }
+    for (int r = 0; r < nr && !rc; ++r) rc = tc_ring(P, g, L, r, 1, H.d_mr_m2 + r * np, nullptr);
+  }
+  for (int r = 0; r < nr && !rc && !(H.smoother_kind == 0 && nr > 1); ++r) {
     if ((rc = tc_ring(P, g, L, r, 0, nullptr, m1))) break;
     {
       const double bytes = H.smoother_kind == 1 ? lev.pat.ntile * 64.0 * 64.0 * sizeof(float)
@@ -595,6 +608,7 @@ void free_hierarchy(cr_plan* P) {
       if (p) cudaFree(p);
   }
   void* ptrs[] = {H.d_Ainv, H.d_Abottom, H.d_dof_lm, H.map_work, H.map_work2, H.d_dot, P->hier_tile_work,
+                  H.d_mr_y, H.d_mr_m1, H.d_mr_m2,
                   H.d_sweep_flag, H.d_sweep_epoch, H.d_sweep_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -972,6 +986,20 @@ int cr_prolong_add(cr_plan* plan, int h, const void* c_H, void* x_h, int dtype) 
   if (rc) return rc;
   if (h < 0 || h > plan->hier->H) return fail(CR_EINVAL, "cr_prolong_add: level out of range");
   return dtype == CR_F64 ? level_prolong<double>(plan, h, c_H, x_h) : level_prolong<float>(plan, h, c_H, x_h);
+}
+
+int cr_pixel_smoother(cr_plan* plan, int h, const void* map_in, void* map_out, int nrhs, int dtype) {
+  int rc = check_hier(plan, "cr_pixel_smoother", true);
+  if (rc) return rc;
+  if (h < 1 || h > plan->hier->H) return fail(CR_EINVAL, "cr_pixel_smoother: level out of range");
+  if (nrhs < 1 || nrhs > 16) return fail(CR_EINVAL, "cr_pixel_smoother: 1 to 16 maps");
+  if (!map_in || !map_out) return fail(CR_EINVAL, "cr_pixel_smoother: null map");
+  if ((rc = ensure_smoother_batch(plan))) return rc;
+  PixLevel& lev = plan->hier->pix[h - 1];
+  const int64_t np = lev.grid->npix;
+  rc = dtype == CR_F64 ? apply_smoother_mr<double>(plan, lev, nrhs, (const double*)map_in, (double*)map_out, np)
+                       : apply_smoother_mr<float>(plan, lev, nrhs, (const float*)map_in, (float*)map_out, np);
+  return rc ? rc : sweep_status(plan);
 }
 
 int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype) {

@@ -128,13 +128,16 @@ def test_tensor_core_cycles_in_a_graph_match_direct(top_f32):
         batch.close()
 
 
-@pytest.mark.parametrize("mode,cycles", [(binding.CR_MIXED, 3), (binding.CR_MIXED | binding.CR_TC_CYCLES, 4)])
+@pytest.mark.parametrize("mode,cycles", [(binding.CR_MIXED, 3),
+                                         (binding.CR_MIXED | binding.CR_TC_CYCLES | binding.CR_TC_SPLIT, 3),
+                                         (binding.CR_MIXED | binding.CR_TC_CYCLES, 6)])
 def test_batch_graph_at_the_mixed_resolution_sizes(mode, cycles):
     """The batch of the benchmark's mixed-resolution measurement at its sizes
     (Nside 1024 / lmax 2047 and Nside 512 / lmax 1023, the first two of its
-    realizations each, the cycle counts it reports): the graph replay equals
-    the uncaptured solves and every realization is within 1 uK max-pixel of
-    its exact answer x_true of b = A x_true."""
+    realizations each, the cycle counts it reports for the FP32 cycles, the
+    split tensor-core cycles and the plain-BF16 ones): the graph replay
+    equals the uncaptured solves and every realization is within 1 uK
+    max-pixel of its exact answer x_true of b = A x_true."""
     dev = cuda_device()
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):

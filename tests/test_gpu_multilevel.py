@@ -210,6 +210,27 @@ def test_sweep_forms_identical(dev):
             assert torch.equal(c1, c2), h
 
 
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_pixel_smoother_many_maps(case32, dev, h):
+    """M_h applied to several maps at once (every factor block read once for
+    all of them, the form of the batched cycles) against the oracle's
+    incomplete-Cholesky solve of each map (same ridge; FP32 factor), and
+    against the one-map sweeps map by map."""
+    H, plan = case32["H"], case32["plan"]
+    lev = H.pix[h - 1]
+    npix = lev.grid["npix"]
+    rng = np.random.default_rng(600 + h)
+    maps = rng.normal(size=(5, npix))
+    out = torch.empty((5, npix), dtype=torch.float32, device=dev)
+    plan.pixel_smoother(h, torch.from_numpy(maps).to(torch.float32).to(dev), out)
+    got = out.cpu().numpy().astype(np.float64)
+    one = torch.empty(npix, dtype=torch.float32, device=dev)
+    for j in range(5):
+        assert rel_l2(got[j], lev.apply_M(maps[j])) < 2e-4, j
+        plan.pixel_smoother(h, torch.from_numpy(maps[j]).to(torch.float32).to(dev), one)
+        assert rel_l2(got[j], one.cpu().numpy().astype(np.float64)) < 1e-5, j
+
+
 def _levels_of(H):
     return [dict(nside_h=l["nside_h"], lmax_h=l["lmax_h"], n_rec=l["n_rec"], fl=l["fl"]) for l in H.levels]
 
