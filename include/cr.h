@@ -458,7 +458,10 @@ int cr_sht_adjoint(cr_plan* plan, int grid, const void* map, void* alm, int nrhs
  * diagonals.  level 0 is the full system; level h >= 1 applies the level
  * operator A_h = D_h + B_h Y^T N^-1 Y B_h (Section 3.2, Eq. A_h) at that
  * level's band limit.  x, y: [nrhs][N_lm]; x and y must not overlap.
- * dtype CR_F64, CR_F32, or at level 0 CR_TC (batched, tensor cores).
+ * dtype CR_F64, CR_F32, or at level 0 CR_TC (batched, tensor cores).  With
+ * CR_F64 at level 0 and several right-hand sides the two Legendre stages run
+ * 8 right-hand sides at a time (one evaluation of the recurrence for all of
+ * them; the same FP64 operator, summed in another order).
  * Requires a plan created with cl.  Errors: CR_EINVAL, CR_ESTATE, CR_ECUDA.
  */
 int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int dtype);

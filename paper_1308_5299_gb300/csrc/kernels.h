@@ -105,6 +105,17 @@ int tc_sandwich(cr_plan* P, const Grid& g, int L, int nr, const float2* x, const
 template <typename T> int launch_leg_finalize(const FinalizeArgs<T>& f, cudaStream_t st);
 int launch_leg_synth_df(const LegArgs<double>& a, cudaStream_t st);
 int launch_leg_adjoint_df(const LegArgs<double>& a, int* nblk, cudaStream_t st);
+// FP64 stages of up to 8 right-hand sides at once (legendre_mr.cu)
+int mr_blocks(int npairs);
+int launch_leg_synth_mr(const LegArgs<double>& a, const double2* alm, int64_t ld_alm, int nr, double2* phase,
+                        int64_t ld_phase, cudaStream_t st);
+int launch_leg_adjoint_mr(const LegArgs<double>& a, const double2* phase, int64_t ld_phase, int nr, double2* partial,
+                          int* nblk, cudaStream_t st);
+// y_r = dl_out Y^T diag(pix) Y (dl_in x_r) + dadd x_r, or bsub_r - that, in
+// FP64 for nr <= 8 right-hand sides at stride n_lm(L) (plan.cu)
+int do_sandwich_mr(cr_plan* P, const Grid& g, int L, int nr, const double2* x, double2* y, const double* dl_in,
+                   const double* pix, const double* dl_out, const double* dadd, const double2* bsub);
+int ensure_mr_workspace(cr_plan* P, const Grid& g, int L);
 int launch_leg_diag(cr_plan* P, const double* ringval, double2* out);
 template <typename T> int launch_ring_fft(const RingArgs<T>& a, int mode, cudaStream_t st);
 

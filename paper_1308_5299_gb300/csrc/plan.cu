@@ -326,7 +326,8 @@ static void plan_free(cr_plan* P) {
     delete g;
   }
   void* ptrs[] = {P->d_c, P->d_s, P->d_c32, P->d_c2_32, P->d_s32, P->d_bl, P->d_sinv, P->d_bl32, P->d_sinv32,
-                  P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial, P->d_pcinv, P->cgv[0], P->cgv[1],
+                  P->d_ninv, P->d_ninv32, P->ws.phase, P->ws.partial, P->ws_mr.phase, P->ws_mr.partial, P->d_tc_r64, P->d_pcinv,
+                  P->cgv[0], P->cgv[1],
                   P->cgv[2], P->cgv[3], P->d_cgdot, P->tc_phase, P->d_tc_status, P->tc_partial, P->d_dotpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -569,6 +570,77 @@ int do_sandwich(cr_plan* P, const Grid& g, int L, const void* x, void* y, const 
   TimerScope ts(P->timing, P->stream, std::string("legendre_adjoint") + ptag<T>(), leg_work(g, L),
                   leg_work_exec(P, g, L));
   return launch_leg_adjoint<T>(a, f, P->stream);
+}
+
+// FP64 y_r = dl_out Y^T diag(pix) Y (dl_in x_r) + dadd x_r (or bsub_r - that)
+// for nr <= 8 right-hand sides at stride n_lm(L): the two Legendre stages of
+// all of them at once (legendre_mr.cu), the ring FFTs and the finalisation
+// per right-hand side.  The phase slots and partial rows of the batch live
+// in ws_mr.
+int ensure_mr_workspace(cr_plan* P, const Grid& g, int L) {
+  const int64_t nlm = n_lm(L), ld_phase = (int64_t)g.nring * (L + 1);
+  const int nblk = mr_blocks(g.npairs);
+  const int64_t phase = 8 * ld_phase * (int64_t)sizeof(double2);
+  const int64_t partial = 8 * (int64_t)nblk * nlm * (int64_t)sizeof(double2);
+  if (phase > P->ws_mr.phase_bytes || partial > P->ws_mr.partial_bytes) {
+    if (P->capturing) return fail(CR_ESTATE, "FP64 batch: buffers missing (run once outside a capture)");
+    if (phase > P->ws_mr.phase_bytes) {
+      if (P->ws_mr.phase) cudaFree(P->ws_mr.phase);
+      P->ws_mr.phase = nullptr;
+      CR_CUDA(cudaMalloc(&P->ws_mr.phase, phase));
+      P->ws_mr.phase_bytes = phase;
+    }
+    if (partial > P->ws_mr.partial_bytes) {
+      if (P->ws_mr.partial) cudaFree(P->ws_mr.partial);
+      P->ws_mr.partial = nullptr;
+      CR_CUDA(cudaMalloc(&P->ws_mr.partial, partial));
+      P->ws_mr.partial_bytes = partial;
+    }
+  }
+  return CR_OK;
+}
+
+int do_sandwich_mr(cr_plan* P, const Grid& g, int L, int nr, const double2* x, double2* y, const double* dl_in,
+                   const double* pix, const double* dl_out, const double* dadd, const double2* bsub) {
+  if (nr < 1 || nr > 8) return fail(CR_EINVAL, "FP64 batch: 1 to 8 right-hand sides");
+  int rc = ensure_mr_workspace(P, g, L);
+  if (rc) return rc;
+  const int64_t nlm = n_lm(L), ld_phase = (int64_t)g.nring * (L + 1);
+  double2* ph = reinterpret_cast<double2*>(P->ws_mr.phase);
+  double2* part = reinterpret_cast<double2*>(P->ws_mr.partial);
+  LegArgs<double> a = leg_args<double>(P, g, L);
+  a.dl = dl_in;
+  {
+    TimerScope ts(P->timing, P->stream, "legendre_synth_f64", leg_work(g, L) * nr, leg_work_exec(P, g, L) * nr);
+    rc = launch_leg_synth_mr(a, x, nlm, nr, ph, ld_phase, P->stream);
+  }
+  for (int r = 0; r < nr && !rc; ++r) {
+    RingArgs<double> ra = ring_args<double>(P, g, L);
+    ra.phase = ph + r * ld_phase;
+    ra.pixdiag = pix;
+    TimerScope ts(P->timing, P->stream, "ring_fft_apply_f64",
+                  fft_bytes<double>(g, L, 1) + (double)g.nring * (L + 1) * sizeof(double2));
+    rc = launch_ring_fft<double>(ra, 2, P->stream);
+  }
+  if (rc) return rc;
+  int nb = 0;
+  {
+    TimerScope ts(P->timing, P->stream, "legendre_adjoint_f64", leg_work(g, L) * nr, leg_work_exec(P, g, L) * nr);
+    rc = launch_leg_adjoint_mr(a, ph, ld_phase, nr, part, &nb, P->stream);
+  }
+  for (int r = 0; r < nr && !rc; ++r) {
+    FinalizeArgs<double> f;
+    f.partial = part + (int64_t)r * nb * nlm;
+    f.nblk = nb;
+    f.L = L;
+    f.dl_out = dl_out;
+    f.dadd = dadd;
+    f.xadd = x + r * nlm;
+    f.bsub = bsub ? bsub + r * nlm : nullptr;
+    f.out = y + r * nlm;
+    rc = launch_leg_finalize<double>(f, P->stream);
+  }
+  return rc;
 }
 
 template int do_synth<double>(cr_plan*, const Grid&, int, const void*, void*, const double*);
@@ -1202,6 +1274,16 @@ int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int d
   if (x == y) return fail(CR_EINVAL, "cr_apply_A: x and y must not overlap");
   const int L = plan->lmax;
   const size_t es = dtype == CR_F64 ? 8 : 4;
+  if (dtype == CR_F64 && nrhs > 1 && !plan->fp64_df) {
+    // several right-hand sides: the FP64 stages 8 at a time
+    const int64_t nlm = n_lm(L);
+    for (int r0 = 0; r0 < nrhs; r0 += 8) {
+      int rc = do_sandwich_mr(plan, plan->obs, L, std::min(8, nrhs - r0), (const double2*)x + r0 * nlm,
+                              (double2*)y + r0 * nlm, plan->d_bl, plan->d_ninv, plan->d_bl, plan->d_sinv, nullptr);
+      if (rc) return rc;
+    }
+    return CR_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const char* xr = (const char*)x + (size_t)r * n_lm(L) * 2 * es;
     char* yr = (char*)y + (size_t)r * n_lm(L) * 2 * es;

@@ -71,7 +71,8 @@ struct Grid {
   std::map<int, double> exec_terms;
 };
 
-// Scratch sizes for transforms at band limit L on a grid.
+// Scratch sizes for transforms at band limit L on a grid (ws_mr: the FP64
+// stages of several right-hand sides, [8][...] of each).
 struct Workspace {
   void* phase = nullptr;   // [nring][ldp] complex (sized for double2)
   void* partial = nullptr; // [nblk][n_lm] complex (sized for double2)
@@ -147,6 +148,8 @@ struct cr_plan {
   double* d_ninv = nullptr;  // [npix] obs grid
   float* d_ninv32 = nullptr;
   cr::Workspace ws;
+  cr::Workspace ws_mr;
+  double2* d_tc_r64 = nullptr;  // FP64 residuals of a batch of 16 right-hand sides
   cr::Timing timing;
   int fp64_df = 0;  // FP64 Legendre stages in double-float arithmetic
   bool capturing = false;  // inside a CUDA-graph capture: no host synchronisation

@@ -144,6 +144,7 @@ static int ensure_tc_work(cr_plan* P) {
   Hierarchy& H = *P->hier;
   int rc = ensure_smoother_batch(P);
   if (rc) return rc;
+  if (!P->d_tc_r64) CR_CUDA(cudaMalloc(&P->d_tc_r64, (size_t)16 * n_lm(P->lmax) * sizeof(double2)));
   if ((int)H.tcw.size() == H.H + 2) return CR_OK;
   H.tcw.assign(H.H + 2, Hierarchy::TcWork());
   for (int h = 0; h <= H.H + 1; ++h) {
@@ -789,6 +790,7 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
 static int tc_prepare_all(cr_plan* P) {
   Hierarchy& H = *P->hier;
   int rc = ensure_tc_work(P);
+  if (!rc) rc = ensure_mr_workspace(P, P->obs, P->lmax);
   if (!rc) rc = tc_begin(P, P->obs, P->lmax, true, true);
   for (int h = 1; h <= H.H && !rc; ++h) {
     const float* pix = nullptr;
@@ -815,7 +817,7 @@ int solve_tc(cr_plan* P, void* x, const void* b, int nrhs, double eps, int max_c
     return fail(CR_ESTATE, "solve: batched cycle buffers missing (run the solve once outside a capture)");
   CR_CUDA(cudaMemsetAsync(P->d_tc_status, 0, sizeof(int), P->stream));
   Hierarchy::TcWork& w0 = H.tcw[0];
-  void* r64 = H.work[0].r;
+  void* r64 = H.work[0].r;  // (a batch's FP64 residuals are in P->d_tc_r64)
   bool capped = false;
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int nr = std::min(16, nrhs - r0);
@@ -842,8 +844,23 @@ int solve_tc(cr_plan* P, void* x, const void* b, int nrhs, double eps, int max_c
         break;
       }
       bool all = true;
+      // FP64 residuals: up to 8 right-hand sides per pass of the batched
+      // FP64 stages (one evaluation of the recurrence for all of them)
+      const bool batched = nr > 1 && !P->fp64_df && P->d_tc_r64;
+      if (batched) {
+        TimerScope ts(P->timing, P->stream, "outer_residual");
+        LevelOps& o = ops_of(P).ops[0];
+        const double* pix = nullptr;
+        const Grid& g0 = noise_grid<double>(P, 0, &pix);
+        for (int j0 = 0; j0 < nr && !rc; j0 += 8)
+          rc = do_sandwich_mr(P, g0, L, std::min(8, nr - j0), X + j0 * nlm, P->d_tc_r64 + j0 * nlm,
+                              o.b.get<double>(), pix, o.b.get<double>(), o.d.get<double>(), B + j0 * nlm);
+        if (rc) return rc;
+      }
       for (int j = 0; j < nr; ++j) {
-        {
+        if (batched) {
+          r64 = P->d_tc_r64 + j * nlm;
+        } else {
           TimerScope ts(P->timing, P->stream, "outer_residual");
           if ((rc = residual<double>(P, 0, X + j * nlm, B + j * nlm, r64))) return rc;
         }
