@@ -17,10 +17,11 @@ with a 60 arcmin beam and unit noise).
 ``sht``: one synthesis and one adjoint synthesis of a single right-hand side
 in FP32 or FP64.
 
-``apply``: A = S^-1 + B Y^T N^-1 Y B of a single right-hand side in FP32
-or FP64 on a named workload (``--workload``), with the per-stage CUDA-event
-times of the plan (Legendre synthesis, fused ring FFTs with N^-1, Legendre
-adjoint) and the stages' dense and executed Legendre flops.
+``apply``: A = S^-1 + B Y^T N^-1 Y B in FP32 or FP64 on a named workload
+(``--workload``), with the per-stage CUDA-event times of the plan (Legendre
+synthesis, fused ring FFTs with N^-1, Legendre adjoint) and the stages'
+dense and executed Legendre flops; ``--nrhs N`` applies it to N prior draws
+at once (FP64: the Legendre stages 8 right-hand sides at a time).
 
 ``smooth``: one pixel-smoother application (Y_h^T M_h Y_h r in FP32) per
 pixel level of a named workload's default hierarchy, with the ICC(0)
@@ -120,7 +121,7 @@ def sht_case(nside, lmax, warmup, reps, dtype, pins=()):
             "ms": res}
 
 
-def apply_case(name, warmup, reps, dtype, tune, pin=None):
+def apply_case(name, warmup, reps, dtype, tune, pin=None, nrhs=1):
     """A x for one right-hand side on the workload's observation grid, timed
     whole and per stage (one realization's outer residual at Nside 2048 is
     one FP64 call; the FP32 cycles make many FP32 calls).  pin: (stage,
@@ -138,6 +139,8 @@ def apply_case(name, warmup, reps, dtype, tune, pin=None):
         plan.autotune()
     cdt = torch.complex64 if dtype == "f32" else torch.complex128
     x = torch.from_numpy(synthetic.draw_prior(cl, index=1)).to(cdt).to(dev)
+    if nrhs > 1:  # several right-hand sides (FP64: the batched Legendre stages)
+        x = torch.stack([torch.from_numpy(synthetic.draw_prior(cl, index=1 + j)).to(cdt) for j in range(nrhs)]).to(dev)
     y = torch.empty_like(x)
     fn = lambda: plan.apply_A(x, y)
     for _ in range(warmup):
@@ -152,7 +155,7 @@ def apply_case(name, warmup, reps, dtype, tune, pin=None):
     plan.set_timing(False)
     stages = {k: {"ms_per_call": v[0] / reps, "work_dense": v[2] / reps, "work_exec": ex.get(k, 0.0) / reps}
               for k, v in st.items()}
-    return {"case": "apply", "workload": name, "dtype": dtype, "reps": reps, "autotuned": bool(tune),
+    return {"case": "apply", "workload": name, "dtype": dtype, "reps": reps, "autotuned": bool(tune), "nrhs": nrhs,
             "ms_per_call": ms, "stages": stages,
             "tune": [t for t in binding.tune_table() if t["lmax"] == lmax] if tune else None}
 
@@ -265,24 +268,25 @@ def main(argv=None):
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--nside", type=int, default=512)
     ap.add_argument("--lmax", type=int, default=1023)
-    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (tc, grad: default 16; apply: 1)")
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
+    nrhs = args.nrhs if args.nrhs is not None else (1 if args.case == "apply" else 16)
     binding.lib()
     if args.case == "tc":
-        print(json.dumps(tc_case(args.nside, args.lmax, args.nrhs, args.warmup, args.reps, args.tune, args.split)))
+        print(json.dumps(tc_case(args.nside, args.lmax, nrhs, args.warmup, args.reps, args.tune, args.split)))
     elif args.case == "apply":
         pin = None
         if args.pin_adjoint:
             pin = ("adjoint", args.pin_adjoint)
-        print(json.dumps(apply_case(args.workload, args.warmup, args.reps, args.dtype, args.tune, pin)))
+        print(json.dumps(apply_case(args.workload, args.warmup, args.reps, args.dtype, args.tune, pin, nrhs)))
     elif args.case == "smooth":
         print(json.dumps(smooth_case(args.workload, args.warmup, args.reps)))
     elif args.case == "diag":
         print(json.dumps(diag_case(args.workload, args.cycles, args.iters)))
     elif args.case == "grad":
-        print(json.dumps(grad_case(args.workload, args.nrhs, args.warmup)))
+        print(json.dumps(grad_case(args.workload, nrhs, args.warmup)))
     else:
         pins = [(st, rp, args.m_tile) for st, rp in (("synthesis", args.pin_synth), ("adjoint", args.pin_adjoint))
                 if rp]
