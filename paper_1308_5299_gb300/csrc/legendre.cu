@@ -284,34 +284,6 @@ __device__ __forceinline__ void warp_reduce8(C v[8]) {
   v[0].y += shfl_x(v[0].y, 1);
 }
 
-// The same reduction through shared memory (one warp's buffer of 8 rows
-// padded to 33 entries, so that the row-wise writes and the strided reads
-// each take the two wavefronts of a 64-bit access): every lane stores its 8
-// values, lane l sums 8 of the 32 entries of row l >> 2 and two shuffle
-// steps add the four quarters.  On return lanes 4u .. 4u + 3 hold the warp
-// sum of value u in v[0].  About 40 instructions instead of the 64 of the
-// shuffle transpose.
-__device__ __forceinline__ void smem_reduce8(float2 v[8], float2 (*buf)[33]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) buf[u][lane] = v[u];
-  __syncwarp();
-  const int u = lane >> 2, k = lane & 3;
-  float2 s = buf[u][8 * k];
-#pragma unroll
-  for (int i = 1; i < 8; ++i) {
-    const float2 t = buf[u][8 * k + i];
-    s.x += t.x;
-    s.y += t.y;
-  }
-  s.x += shfl_x(s.x, 1);
-  s.y += shfl_x(s.y, 1);
-  s.x += shfl_x(s.x, 2);
-  s.y += shfl_x(s.y, 2);
-  __syncwarp();  // the buffer is rewritten by the next group
-  v[0] = s;
-}
-
 // ---------------------------------------------------------------------------
 // FP32 synthesis with packed pairs of FP32 lanes (f32x2 instructions of the
 // sm_100 family: two FP32 operations per issued instruction).  Inside the
@@ -350,6 +322,34 @@ __device__ __forceinline__ u64 add2(u64 a, u64 b) {
   return d;
 }
 __device__ __forceinline__ u64 lds2(const float2* p) { return *reinterpret_cast<const u64*>(p); }
+
+// The same reduction through shared memory, one warp's buffer of 8 rows.
+// Each lane has stored its value u in buf[u][lane] as soon as it was complete
+// (so no array of 8 sums stays live in registers); here lane l sums the
+// entries k, k + 4, ..., k + 28 (k = l & 3) of row l >> 2 and two shuffle
+// steps add the four residues.  Rows are SMEM_RS = 36 entries apart: a
+// half-warp's 64-bit reads then fall on 16 distinct 8-byte bank pairs
+// (4 u + k mod 16), and the row-wise writes are contiguous, so every access
+// takes the two wavefronts of a 64-bit warp access.  The real and imaginary
+// parts are added by one packed f32x2 add per entry.  About 30 instructions
+// instead of the 64 of the shuffle transpose.
+constexpr int SMEM_RS = 36;
+__device__ __forceinline__ float2 smem_rows8_sum(float2 (*buf)[SMEM_RS]) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  const int u = lane >> 2, k = lane & 3;
+  u64 acc = lds2(&buf[u][k]);
+#pragma unroll
+  for (int i = 1; i < 8; ++i) acc = add2(acc, lds2(&buf[u][k + 4 * i]));
+  float2 s;
+  upk2(acc, s.x, s.y);
+  s.x += shfl_x(s.x, 1);
+  s.y += shfl_x(s.y, 1);
+  s.x += shfl_x(s.x, 2);
+  s.y += shfl_x(s.y, 2);
+  __syncwarp();  // the buffer is rewritten by the next group
+  return s;
+}
 
 template <bool POLAR, int RP, int MT = 1>
 __global__ void __launch_bounds__(L32_NT) leg_synth_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
@@ -660,9 +660,12 @@ __global__ void __launch_bounds__(LEG_NT) leg_adjoint_kernel(LegArgs<T> a, int n
 // sums come out multiplied by sigma_l, which the partial-row write undoes;
 // the polar difference form needs no sign change) and the accumulation
 // A_l += V_l G, whose two halves hold the sums over the even and the odd
-// members of the thread's pair list and are added once per 8-l group before
-// the warp's shuffle-transpose reduction.  Up to 16 ring pairs per thread
-// spread the reduction over more terms.
+// members of the thread's pair list and are added once per 8-l group, each
+// sum going straight to the warp's shared-memory transpose buffer.  Up to 16
+// ring pairs per thread spread the reduction over more terms.  The chunk's
+// recurrence coefficients and output scales s_lm (with the recurrence's sign)
+// are staged in shared memory with their global loads issued four per lane
+// at a time, so the per-group row write reads no global memory.
 template <bool POLAR, int RP, int MT = 1>
 __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float> a, int nbp, int yoff) {
   static_assert(RP % 2 == 0, "pairs per thread must be even");
@@ -678,7 +681,8 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
     const int lane = threadIdx.x;
     __shared__ float2 sk[LEG_CH];
     __shared__ float2 sk2[POLAR ? LEG_CH : 1];
-    __shared__ float2 rbuf[8][33];
+    __shared__ float sf[LEG_CH];
+    __shared__ float2 rbuf[8][SMEM_RS];
 
     float P1[RP], P2[RP], zz[RP];
     int ls[RP], p[RP];
@@ -714,23 +718,46 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
     for (int l0 = lbeg; l0 <= L; l0 += LEG_CH) {
       const int nl = min(LEG_CH, L - l0 + 1);
       __syncwarp();
-      for (int i = lane; i < nl; i += 32) {
-        const int l = l0 + i;
-        const float c = a.c[offc + (l - m)];
-        if (POLAR) {
-          sk[i] = make_float2(-c, -c);
-          const float c2 = a.c2[offc + (l - m)];
-          sk2[i] = make_float2(c2, c2);
-        } else {
-          const float al = ((l - m) & 1) ? c : -c;
-          sk[i] = make_float2(al, al);
+      {
+        const float* cg = a.c + offc + (l0 - m);
+        const float* c2g = POLAR ? a.c2 + offc + (l0 - m) : nullptr;
+        const float* sg = a.s + offc + (l0 - m);
+        constexpr int SB = POLAR ? 2 : 4;  // loads in flight per array and lane
+#pragma unroll
+        for (int k0 = 0; k0 < LEG_CH / 32; k0 += SB) {
+          float cv[SB], c2v[SB], sv[SB];
+#pragma unroll
+          for (int k = 0; k < SB; ++k) {
+            const int i = lane + 32 * (k0 + k);
+            cv[k] = c2v[k] = sv[k] = 0.f;
+            if (i < nl) {
+              cv[k] = cg[i];
+              if (POLAR) c2v[k] = c2g[i];
+              sv[k] = sg[i];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < SB; ++k) {
+            const int i = lane + 32 * (k0 + k);
+            if (i < nl) {
+              const int l = l0 + i;
+              if (POLAR) {
+                sk[i] = make_float2(-cv[k], -cv[k]);
+                sk2[i] = make_float2(c2v[k], c2v[k]);
+                sf[i] = sv[k];
+              } else {
+                const float al = ((l - m) & 1) ? cv[k] : -cv[k];
+                sk[i] = make_float2(al, al);
+                sf[i] = sv[k] * sgn(l);
+              }
+            }
+          }
         }
       }
       __syncwarp();
       for (int i8 = 0; i8 < nl; i8 += 8) {
         const int lg = l0 + i8;
         const int ng = min(8, nl - i8);
-        float2 acc[8];
         if (wmax <= lg && ng == 8) {
           u64 Z[NP], S1[NP], S2[NP], EX[NP], EY[NP], OX[NP], OY[NP];
 #pragma unroll
@@ -772,7 +799,7 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
             float x0, x1, y0, y1;
             upk2(AX, x0, x1);
             upk2(AY, y0, y1);
-            acc[u] = make_float2(x0 + x1, y0 + y1);
+            rbuf[u][lane] = make_float2(x0 + x1, y0 + y1);
           }
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
@@ -781,9 +808,8 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
           }
         } else {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
-#pragma unroll
           for (int u = 0; u < 8; ++u) {
+            float2 acc = make_float2(0.f, 0.f);
             if (u < ng) {
               const int l = lg + u;
               const float K = sk[i8 + u].x;
@@ -803,22 +829,19 @@ __global__ void __launch_bounds__(L32_NT) leg_adjoint_f32x2_kernel(LegArgs<float
                   }
                   P1[j] = q;
                   const float2 g = (u & 1) ? GO[j] : GE[j];
-                  acc[u].x = fmaf(q, g.x, acc[u].x);
-                  acc[u].y = fmaf(q, g.y, acc[u].y);
+                  acc.x = fmaf(q, g.x, acc.x);
+                  acc.y = fmaf(q, g.y, acc.y);
                 }
               }
             }
+            rbuf[u][lane] = acc;
           }
         }
-        smem_reduce8(acc, rbuf);
+        const float2 sum = smem_rows8_sum(rbuf);
         // lane 4 u holds the warp's sum for l = lg + u: scale by s_lm (and the
         // recurrence's sign) and write it to the row
         const int u = lane >> 2;
-        if ((lane & 3) == 0 && u < ng) {
-          const int l = lg + u;
-          const float f = a.s[offc + (l - m)] * (POLAR ? 1.f : sgn(l));
-          part[offa + (l - m)] = cscale(acc[0], f);
-        }
+        if ((lane & 3) == 0 && u < ng) part[offa + (lg + u - m)] = cscale(sum, sf[i8 + u]);
       }
     }
   }
