@@ -470,7 +470,8 @@ int cr_apply_A(cr_plan* plan, int level, const void* x, void* y, int nrhs, int d
  * Multi-level solver (Section 3.2, Fig. code:mg).  Levels are numbered
  * h = 0 (top, lmax, diagonal smoother), 1..H (pixel levels), H + 1 (bottom
  * dense level).  Vectors of level h use that level's band limit lmax_h.
- * All entry points below need a plan created with levels.
+ * All entry points below need a plan created with levels; a dtype argument
+ * is CR_F64 or CR_F32 (anything else: CR_EINVAL).
  */
 /* Number of pixel levels H. */
 int cr_plan_nlevels(cr_plan* plan, int* H);

@@ -1242,6 +1242,11 @@ int smoother_structure(cr_plan* P, PixLevel& lev) {
     }
     col_ptr[p + 1] = (int64_t)col_row.size();
   }
+  // every sweep kernel stages the vectors of at most 8 neighbours of a tile
+  // (a HEALPix tile has at most 8), below and above it in the order
+  for (int p = 0; p < nt; ++p)
+    if (pat.row_ptr[p + 1] - 1 - pat.row_ptr[p] > 8 || col_ptr[p + 1] - col_ptr[p] > 8)
+      return fail(CR_EINVAL, "smoother: a tile with more than 8 neighbours");
   // tile-ordered level pixel -> RING index
   const int64_t npix_h = 12LL * lev.nside_h * lev.nside_h;
   std::vector<int> perm(npix_h);

@@ -923,6 +923,11 @@ using namespace cr;
 
 extern "C" {
 
+static int check_dtype(int dtype, const char* who) {
+  if (dtype != CR_F64 && dtype != CR_F32) return fail(CR_EINVAL, std::string(who) + ": dtype must be CR_F64 or CR_F32");
+  return CR_OK;
+}
+
 static int check_hier(cr_plan* plan, const char* who, bool numeric = false) {
   if (!plan) return fail(CR_EINVAL, std::string(who) + ": null plan");
   if (!plan->hier) return fail(CR_ESTATE, std::string(who) + ": plan was created without levels");
@@ -986,6 +991,7 @@ int cr_plan_level_grid(const cr_plan* cplan, int h, int* kind, int* nring, int64
 
 int cr_level_apply(cr_plan* plan, int h, const void* x, void* y, int dtype) {
   int rc = check_hier(plan, "cr_level_apply");
+  if (!rc) rc = check_dtype(dtype, "cr_level_apply");
   if (rc) return rc;
   if (h < 0 || h > plan->hier->H + 1) return fail(CR_EINVAL, "cr_level_apply: level out of range");
   return dtype == CR_F64 ? level_apply<double>(plan, h, x, y) : level_apply<float>(plan, h, x, y);
@@ -993,6 +999,7 @@ int cr_level_apply(cr_plan* plan, int h, const void* x, void* y, int dtype) {
 
 int cr_restrict(cr_plan* plan, int h, const void* r_h, void* r_H, int dtype) {
   int rc = check_hier(plan, "cr_restrict");
+  if (!rc) rc = check_dtype(dtype, "cr_restrict");
   if (rc) return rc;
   if (h < 0 || h > plan->hier->H) return fail(CR_EINVAL, "cr_restrict: level out of range");
   return dtype == CR_F64 ? level_restrict<double>(plan, h, r_h, r_H) : level_restrict<float>(plan, h, r_h, r_H);
@@ -1000,6 +1007,7 @@ int cr_restrict(cr_plan* plan, int h, const void* r_h, void* r_H, int dtype) {
 
 int cr_prolong_add(cr_plan* plan, int h, const void* c_H, void* x_h, int dtype) {
   int rc = check_hier(plan, "cr_prolong_add");
+  if (!rc) rc = check_dtype(dtype, "cr_prolong_add");
   if (rc) return rc;
   if (h < 0 || h > plan->hier->H) return fail(CR_EINVAL, "cr_prolong_add: level out of range");
   return dtype == CR_F64 ? level_prolong<double>(plan, h, c_H, x_h) : level_prolong<float>(plan, h, c_H, x_h);
@@ -1007,6 +1015,7 @@ int cr_prolong_add(cr_plan* plan, int h, const void* c_H, void* x_h, int dtype) 
 
 int cr_pixel_smoother(cr_plan* plan, int h, const void* map_in, void* map_out, int nrhs, int dtype) {
   int rc = check_hier(plan, "cr_pixel_smoother", true);
+  if (!rc) rc = check_dtype(dtype, "cr_pixel_smoother");
   if (rc) return rc;
   if (h < 1 || h > plan->hier->H) return fail(CR_EINVAL, "cr_pixel_smoother: level out of range");
   if (nrhs < 1 || nrhs > 16) return fail(CR_EINVAL, "cr_pixel_smoother: 1 to 16 maps");
@@ -1021,6 +1030,7 @@ int cr_pixel_smoother(cr_plan* plan, int h, const void* map_in, void* map_out, i
 
 int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype) {
   int rc = check_hier(plan, "cr_smooth", true);
+  if (!rc) rc = check_dtype(dtype, "cr_smooth");
   if (rc) return rc;
   if (h < 0 || h > plan->hier->H) return fail(CR_EINVAL, "cr_smooth: level out of range");
   rc = dtype == CR_F64 ? level_smooth<double>(plan, h, r, c) : level_smooth<float>(plan, h, r, c);
@@ -1029,6 +1039,7 @@ int cr_smooth(cr_plan* plan, int h, const void* r, void* c, int dtype) {
 
 int cr_bottom_solve(cr_plan* plan, const void* b, void* x, int dtype) {
   int rc = check_hier(plan, "cr_bottom_solve", true);
+  if (!rc) rc = check_dtype(dtype, "cr_bottom_solve");
   if (rc) return rc;
   return dtype == CR_F64 ? bottom_solve<double>(plan, *plan->hier, b, x)
                          : bottom_solve<float>(plan, *plan->hier, b, x);
@@ -1042,7 +1053,9 @@ int cr_bottom_matrix(cr_plan* plan, double* host, int* nd) {
 
 int cr_wcycle(cr_plan* plan, void* x, const void* b, int nrhs, int dtype) {
   int rc = check_hier(plan, "cr_wcycle", true);
+  if (!rc) rc = check_dtype(dtype, "cr_wcycle");
   if (rc) return rc;
+  if (nrhs < 0) return fail(CR_EINVAL, "cr_wcycle: nrhs must be >= 0");
   const int64_t nlm = n_lm(plan->lmax);
   const size_t es = dtype == CR_F64 ? sizeof(double2) : sizeof(float2);
   for (int i = 0; i < nrhs; ++i) {
