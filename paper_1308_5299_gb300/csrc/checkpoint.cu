@@ -15,6 +15,7 @@
 // The identity fields must match the plan a checkpoint is loaded into.
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -43,10 +44,20 @@ struct Hash {
   }
 };
 
+// Writer and Reader own their FILE: close() ends it, the destructor closes it
+// on any other way out (an error return or a host allocation failure)
 struct Writer {
   FILE* f = nullptr;
   Hash hash;
   bool ok = true;
+  ~Writer() {
+    if (f) std::fclose(f);
+  }
+  bool close() {
+    const bool c = std::fclose(f) == 0;
+    f = nullptr;
+    return c;
+  }
   void put(const void* p, size_t n) {
     if (!ok || n == 0) return;
     hash.add(p, n);
@@ -59,6 +70,13 @@ struct Reader {
   FILE* f = nullptr;
   Hash hash;
   bool ok = true;
+  ~Reader() {
+    if (f) std::fclose(f);
+  }
+  void close() {
+    std::fclose(f);
+    f = nullptr;
+  }
   void get(void* p, size_t n) {
     if (!ok || n == 0) return;
     ok = std::fread(p, 1, n, f) == n;
@@ -115,9 +133,7 @@ int plan_identity(cr_plan* P, Identity& id) {
 
 using namespace cr;
 
-extern "C" {
-
-int cr_save(cr_plan* plan, const char* path) {
+static int save_impl(cr_plan* plan, const char* path) {
   if (!plan || !path) return fail(CR_EINVAL, "cr_save: null argument");
   if (!plan->hier) return fail(CR_EINVAL, "cr_save: plan was created without levels");
   Hierarchy& H = *plan->hier;
@@ -155,10 +171,7 @@ int cr_save(cr_plan* plan, const char* path) {
       const int64_t n = std::min(slice, nel - o);
       fbuf.resize(n);
       cudaError_t e = cudaMemcpy(fbuf.data(), lev.d_L + o, n * sizeof(float), cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) {
-        std::fclose(w.f);
-        return cuda_fail(e, "cr_save: factor copy");
-      }
+      if (e != cudaSuccess) return cuda_fail(e, "cr_save: factor copy");
       w.put(fbuf.data(), n * sizeof(float));
     }
   }
@@ -167,10 +180,7 @@ int cr_save(cr_plan* plan, const char* path) {
   {
     std::vector<double> hv(n_lm(plan->lmax));
     cudaError_t e = cudaMemcpy(hv.data(), H.inv_diag_hp.d, hv.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-      std::fclose(w.f);
-      return cuda_fail(e, "cr_save: top smoother copy");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "cr_save: top smoother copy");
     w.put(hv.data(), hv.size() * sizeof(double));
   }
   w.val<int32_t>(H.nd);
@@ -181,22 +191,19 @@ int cr_save(cr_plan* plan, const char* path) {
     cudaError_t e = cudaMemcpy(a.data(), H.d_Abottom, nn * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(ai.data(), H.d_Ainv, nn * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(dofs.data(), H.d_dof_lm, dofs.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-      std::fclose(w.f);
-      return cuda_fail(e, "cr_save: bottom copy");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "cr_save: bottom copy");
     w.put(a.data(), nn * sizeof(double));
     w.put(ai.data(), nn * sizeof(double));
     w.put(dofs.data(), dofs.size() * sizeof(int32_t));
   }
   const uint64_t trailer = w.hash.h;
   if (w.ok) w.ok = std::fwrite(&trailer, 1, sizeof(trailer), w.f) == sizeof(trailer);
-  const bool closed = std::fclose(w.f) == 0;
+  const bool closed = w.close();
   if (!w.ok || !closed) return fail(CR_EIO, std::string("cr_save: write failed: ") + path);
   return CR_OK;
 }
 
-int cr_load(cr_plan* plan, const char* path) {
+static int load_impl(cr_plan* plan, const char* path) {
   if (!plan || !path) return fail(CR_EINVAL, "cr_load: null argument");
   if (!plan->hier) return fail(CR_EINVAL, "cr_load: plan was created without levels");
   Hierarchy& H = *plan->hier;
@@ -206,10 +213,7 @@ int cr_load(cr_plan* plan, const char* path) {
   Reader r;
   r.f = std::fopen(path, "rb");
   if (!r.f) return fail(CR_EIO, std::string("cr_load: cannot open ") + path);
-  auto bad = [&](int code, const std::string& why) {
-    std::fclose(r.f);
-    return fail(code, "cr_load: " + why);
-  };
+  auto bad = [&](int code, const std::string& why) { return fail(code, "cr_load: " + why); };
   char magic[8];
   r.get(magic, sizeof(magic));
   const uint32_t ver = r.val<uint32_t>();
@@ -258,7 +262,13 @@ int cr_load(cr_plan* plan, const char* path) {
   std::vector<double> hv(n_lm(plan->lmax));
   r.get(hv.data(), hv.size() * sizeof(double));
   const int32_t nd = r.val<int32_t>();
-  if (!r.ok || nd < 0 || nd > (1 << 16)) return bad(CR_EIO, "truncated or corrupt body");
+  if (!r.ok || nd < 0) return bad(CR_EIO, "truncated or corrupt body");
+  // the bottom dof map indexes device vectors in the dense solve: it must be
+  // exactly the map the plan builds from its own C_l and band limit, not
+  // merely one of the same length (checked before the bottom arrays, whose
+  // size nd^2 comes from the file, are allocated)
+  const std::vector<int32_t> dofs_plan = bottom_dof_map(plan, H.ld);
+  if ((size_t)nd * 3 != dofs_plan.size()) return bad(CR_EINVAL, "bottom level does not match the plan's C_l");
   std::vector<double> a((size_t)nd * nd), ai((size_t)nd * nd);
   std::vector<int32_t> dofs(3 * (size_t)nd);
   r.get(a.data(), a.size() * sizeof(double));
@@ -269,13 +279,8 @@ int cr_load(cr_plan* plan, const char* path) {
   const bool got = std::fread(&trailer, 1, sizeof(trailer), r.f) == sizeof(trailer);
   if (!r.ok || !got) return bad(CR_EIO, "truncated body");
   if (trailer != want) return bad(CR_EIO, "checksum mismatch");
-  std::fclose(r.f);
-  // the bottom dof map indexes device vectors in the dense solve: it must be
-  // exactly the map the plan builds from its own C_l and band limit, not
-  // merely one of the same length
-  const std::vector<int32_t> dofs_plan = bottom_dof_map(plan, H.ld);
-  if ((size_t)nd * 3 != dofs_plan.size() || dofs != dofs_plan)
-    return fail(CR_EINVAL, "cr_load: bottom level does not match the plan's C_l");
+  r.close();
+  if (dofs != dofs_plan) return fail(CR_EINVAL, "cr_load: bottom level does not match the plan's C_l");
   // upload
   CR_CUDA(cudaStreamSynchronize(plan->stream));
   H.numeric_ready = false;
@@ -298,4 +303,21 @@ int cr_load(cr_plan* plan, const char* path) {
   return CR_OK;
 }
 
-}  // extern "C"
+// The file is staged through host memory (the fine levels' factors are
+// gigabytes at Nside 2048): a failed host allocation is reported, not thrown
+// across the C ABI.
+extern "C" int cr_save(cr_plan* plan, const char* path) {
+  try {
+    return save_impl(plan, path);
+  } catch (const std::bad_alloc&) {
+    return fail(CR_ENOMEM, "cr_save: host allocation");
+  }
+}
+
+extern "C" int cr_load(cr_plan* plan, const char* path) {
+  try {
+    return load_impl(plan, path);
+  } catch (const std::bad_alloc&) {
+    return fail(CR_ENOMEM, "cr_load: host allocation");
+  }
+}
