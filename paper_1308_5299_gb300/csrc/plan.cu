@@ -860,25 +860,9 @@ static int upload_prior(cr_plan* P) {
   return rc;
 }
 
-int cr_plan_create(cr_plan** out, const cr_params* p) {
-  if (!out || !p) return fail(CR_EINVAL, "cr_plan_create: null argument");
-  if (p->struct_size != (int)sizeof(cr_params)) return fail(CR_EINVAL, "cr_plan_create: struct_size mismatch");
-  if (p->lmax < 0 || p->lmax > 16384) return fail(CR_EINVAL, "cr_plan_create: lmax out of range");
-  if (p->grid_kind == CR_GRID_HEALPIX) {
-    if (p->nside < 1 || (p->nside & (p->nside - 1)) || p->nside > 16384)
-      return fail(CR_EINVAL, "cr_plan_create: nside must be a power of two in [1, 16384]");
-  } else if (p->grid_kind == CR_GRID_GL) {
-    if (p->gl_ntheta < 1 || p->gl_nphi < 2 || (p->gl_nphi & 1))
-      return fail(CR_EINVAL, "cr_plan_create: GL grid needs ntheta >= 1 and even nphi >= 2");
-  } else {
-    return fail(CR_EINVAL, "cr_plan_create: unknown grid kind");
-  }
-  cr_plan* P = nullptr;
-  try {
-    P = new cr_plan();
-  } catch (std::bad_alloc&) {
-    return fail(CR_ENOMEM, "cr_plan_create: host allocation");
-  }
+// Everything of cr_plan_create after the argument checks; on an error the
+// caller frees the partly built plan.
+static int plan_init(cr_plan* P, const cr_params* p) {
   P->p = *p;
   P->stream = reinterpret_cast<cudaStream_t>(p->stream);
   P->fp64_df = p->fp64_df ? 1 : 0;
@@ -887,13 +871,8 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
   P->levels.resize(1);
   P->levels[0].lmax_h = p->lmax;
   int rc = CR_OK;
-  try {
-    if (p->grid_kind == CR_GRID_HEALPIX) healpix_rings(P->obs, p->nside);
-    else gl_rings(P->obs, p->gl_ntheta, p->gl_nphi, nullptr);
-  } catch (std::bad_alloc&) {
-    delete P;
-    return fail(CR_ENOMEM, "cr_plan_create: host allocation");
-  }
+  if (p->grid_kind == CR_GRID_HEALPIX) healpix_rings(P->obs, p->nside);
+  else gl_rings(P->obs, p->gl_ntheta, p->gl_nphi, nullptr);
   rc = grid_upload(P->obs, P->lmax, P->stream);
   if (!rc) rc = build_coef(P, P->lmax);
   if (!rc) rc = build_start_tables(P, P->obs);
@@ -959,6 +938,34 @@ int cr_plan_create(cr_plan** out, const cr_params* p) {
     }
   }
   if (!rc && p->autotune) rc = autotune_plan(P, 3);
+  return rc;
+}
+
+int cr_plan_create(cr_plan** out, const cr_params* p) {
+  if (!out || !p) return fail(CR_EINVAL, "cr_plan_create: null argument");
+  if (p->struct_size != (int)sizeof(cr_params)) return fail(CR_EINVAL, "cr_plan_create: struct_size mismatch");
+  if (p->lmax < 0 || p->lmax > 16384) return fail(CR_EINVAL, "cr_plan_create: lmax out of range");
+  if (p->grid_kind == CR_GRID_HEALPIX) {
+    if (p->nside < 1 || (p->nside & (p->nside - 1)) || p->nside > 16384)
+      return fail(CR_EINVAL, "cr_plan_create: nside must be a power of two in [1, 16384]");
+  } else if (p->grid_kind == CR_GRID_GL) {
+    if (p->gl_ntheta < 1 || p->gl_nphi < 2 || (p->gl_nphi & 1))
+      return fail(CR_EINVAL, "cr_plan_create: GL grid needs ntheta >= 1 and even nphi >= 2");
+  } else {
+    return fail(CR_EINVAL, "cr_plan_create: unknown grid kind");
+  }
+  cr_plan* P = nullptr;
+  try {
+    P = new cr_plan();
+  } catch (std::bad_alloc&) {
+    return fail(CR_ENOMEM, "cr_plan_create: host allocation");
+  }
+  int rc = CR_OK;
+  try {
+    rc = plan_init(P, p);
+  } catch (const std::bad_alloc&) {
+    rc = fail(CR_ENOMEM, "cr_plan_create: host allocation");
+  }
   if (rc) {
     plan_free(P);
     delete P;
@@ -1002,7 +1009,11 @@ int cr_plan_update_cl(cr_plan* plan, const double* cl) {
   }
   if (plan->hier) {
     TimerScope ts(plan->timing, plan->stream, "precompute_cl");
-    rc = build_numeric(plan);
+    try {
+      rc = build_numeric(plan);
+    } catch (const std::bad_alloc&) {
+      rc = fail(CR_ENOMEM, "cr_plan_update_cl: host allocation");
+    }
   }
   return rc;
 }
