@@ -371,8 +371,7 @@ COMPOSITE = {"outer_residual"}
 # ncu DRAM traffic per launch of the dominant kernels, read from the profile
 # summaries committed under profiles/ (a line "traffic_bytes_per_launch: N"
 # beside the kernel's name and template arguments)
-TRAFFIC_FILES = {"legendre_adjoint_f64": "legendre_adjoint_f64_dram_nside2048_lmax3000.txt",
-                 "legendre_synth_f64": "legendre_synth_f64_dram_nside2048_lmax3000.txt"}
+TRAFFIC_FILES = {"legendre_adjoint_f64": "legendre_adjoint_f64_dram_nside2048_lmax3000.txt"}
 
 
 def profile_traffic(stage):
