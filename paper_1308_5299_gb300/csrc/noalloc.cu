@@ -166,8 +166,9 @@ typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
 typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
 
 // Unique id of the calling thread's current context (0 if none or if the
-// driver cannot report it).  The driver functions are reached through the
-// runtime's entry-point query, so the library does not link libcuda.
+// CUDA driver cannot report it).  The CUDA driver API functions are reached
+// through the runtime's entry-point query, so the library does not link
+// libcuda.
 static unsigned long long current_ctx_id() {
   static CtxGetCurrentFn get_cur = nullptr;
   static CtxGetIdFn get_id = nullptr;
