@@ -111,8 +111,8 @@ def measured_peaks():
 def gl_noise_grid(nside, lmax_h):
     """Gauss-Legendre grid the library uses for a level's inverse-noise term
     (auto rule): 2 lmax_h + 1 rings, nphi the power of two >= 4 lmax_h + 1,
-    when that is at most half the observation grid's rings; else None."""
-    if 2 * lmax_h + 1 > (4 * nside - 1) // 2:
+    when that is at most 3/5 of the observation grid's rings; else None."""
+    if 5 * (2 * lmax_h + 1) > 3 * (4 * nside - 1):
         return None
     nphi = 2
     while nphi < 4 * lmax_h + 1:

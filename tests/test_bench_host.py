@@ -73,3 +73,17 @@ def test_fewest_cycles_from_any_start(start):
 def test_fewest_cycles_none_when_the_cap_is_too_small():
     s = _Solver()
     assert bench.fewest_cycles(s.solve, s.worst, 1, 2) is None
+
+
+def test_cpu_baseline_prices_the_library_noise_grids():
+    """The CPU baseline prices each level's inverse-noise term on the grid the
+    library uses (Section 3.4's GL downgrade where the GL grid has at most
+    3/5 of the observation rings): at Nside 2048 the first level (lmax 3000)
+    stays on the observation grid, the second (lmax 2048) and below go to GL."""
+    assert bench.gl_noise_grid(2048, 3000) is None
+    assert bench.gl_noise_grid(2048, 2048) == (4097, 16384)
+    assert bench.gl_noise_grid(2048, 1280) == (2561, 8192)
+    assert bench.gl_noise_grid(32, 95) is None  # 191 rings > 3/5 of 127
+    for nside, lh in [(2048, 2457), (2048, 2458), (256, 230), (256, 231)]:
+        expect = 5 * (2 * lh + 1) <= 3 * (4 * nside - 1)
+        assert (bench.gl_noise_grid(nside, lh) is not None) == expect
