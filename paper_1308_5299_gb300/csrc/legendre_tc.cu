@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(T3_NT) tc_adjoint2_kernel(TaArgs a, int nbp, i
   const int yb = (int)blockIdx.x + yoff;
   const int base = POLAR ? yb * T3_K : a.npolar + (yb - nbp) * T3_K;
   const int pend = POLAR ? a.npolar : a.npairs;
-  const bool producer = warp < 4, mma_warp = warp == 4, epilogue = warp >= 5;
+  const bool producer = warp < 4, mma_warp = warp == 4;  // warps 5-8: the epilogue
   const int p = base + tid;  // producers' ring pair
   int ls = L + 1;
   float P1 = 0.f, P2 = 0.f, zz = 0.f;

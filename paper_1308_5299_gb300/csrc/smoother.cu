@@ -108,14 +108,12 @@ __global__ void __launch_bounds__(SM_NT) assemble_kernel(AssembleArgs a) {
   __shared__ float No[TK];
   __shared__ __align__(16) float Bi[TK][TK + 4];
   __shared__ __align__(16) float Bj[TK][TK + 4];
-  __shared__ int ovf;
   if (tid == 0) {
     double v[3];
     tile_pixel_vec(a.nside_h, (int64_t)a.order[p] * TK, v);
     ref[0] = v[0];
     ref[1] = v[1];
     ref[2] = v[2];
-    ovf = 0;
   }
   __syncthreads();
   if (tid < 2 * TK) {

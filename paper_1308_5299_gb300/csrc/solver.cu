@@ -731,7 +731,7 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
   void* r32 = H.work[0].b; // FP32 residual (mixed mode)
   CR_CUDA(cudaMemsetAsync(x, 0, nlm * sizeof(double2), P->stream));
   CR_CUDA(cudaMemcpyAsync(r, b, nlm * sizeof(double2), cudaMemcpyDeviceToDevice, P->stream));
-  double prev = 1.0, prev2 = 1.0;
+  double prev = 1.0;
   int grow = 0;
   int k = 0;
   double rel = 1.0;
@@ -775,10 +775,8 @@ int solve(cr_plan* P, void* x, const void* b, double eps, int max_cycles, int mo
       if (relres_out) *relres_out = rel;
       return fail(CR_EDIVERGED, "solve: residual grew over two consecutive cycles");
     }
-    prev2 = prev;
     prev = rel;
   }
-  (void)prev2;
   if (cycles_out) *cycles_out = std::min(k, max_cycles);
   if (relres_out) *relres_out = rel;
   if (k > max_cycles && !(mode & CR_FIXED)) return fail(CR_EMAXITER, "solve: cycle cap reached before the tolerance");
