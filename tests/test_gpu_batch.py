@@ -7,7 +7,7 @@ import pytest
 import torch
 
 from gpu_util import cuda_device
-from oracle import geometry, sht
+from oracle import sht
 from paper_1308_5299_gb300 import binding, synthetic
 
 pytestmark = pytest.mark.gpu

@@ -6,7 +6,6 @@ Section 2.3): a dropped term, a wrong sqrt(2) or a wrong N^-1/2 fails it."""
 import math
 
 import numpy as np
-import pytest
 import scipy.stats
 
 from oracle import draw, geometry, operators, sht

@@ -2,7 +2,6 @@
 nested indexing and tiles, the addition theorem against explicit transforms,
 ICC(0) against its defining properties, and the cycle's fixed point against
 the dense solve."""
-import math
 
 import numpy as np
 import scipy.linalg

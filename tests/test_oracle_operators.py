@@ -2,10 +2,8 @@
 system-explicit / cr-system; Section 2.4; Section 3.3, Eq. Ni-dense):
 symmetry and definiteness, closed-form solutions, and two independent routes
 to the explicit matrix (probing vs the ring formula)."""
-import math
 
 import numpy as np
-import pytest
 
 from oracle import geometry, operators, sht, solvers
 from paper_1308_5299_gb300 import synthetic
